@@ -1,0 +1,634 @@
+/*
+ * epd_lb_oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, FP64 CPU restatement of one time step of the hybrid
+ * Lattice-Boltzmann / External-Potential-Dynamics method of Heuser, Sevink and
+ * Schmid (arXiv:1804.02883).  It exists to check the CUDA path; nothing in the
+ * product may call it.  Only the tests, __graft_entry__.smoke() and the CPU
+ * baseline leg of bench.py load this library.
+ *
+ * It shares no code, header, table or constant with the CUDA library: it has
+ * its own FFT (radix-2, pinned against a naive DFT), its own propagator, its
+ * own LB collision written in moment space, and its own implementation of the
+ * splitmix64 counter generator used for the initial noise.
+ *
+ * Every operation follows the paper's statement directly, without blocking or
+ * fusion.  The readings taken where the paper is silent are marked READING.
+ *
+ * Grid layout: row-major [y][x], x fastest; x is the flow axis.  Fields of the
+ * three species are stacked as [A, B, S].  LB populations are stacked as
+ * [i][y][x] with the D2Q9 velocity order
+ *   0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1).
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cplx;
+
+/* Parameters of the problem statement (Sec. 2 and Sec. 3).  Lengths in R_G,
+ * times in tau = R_G^2/D_S, the LB part in lattice units. */
+typedef struct {
+    int32_t nx, ny;       /* grid sites, each a power of two                 */
+    int32_t ns;           /* contour steps N_s                               */
+    int32_t pad0;
+    double dx, dt, rg;    /* grid spacing, time step, gyration radius R_G    */
+    double n_seg;         /* segments per chain N                            */
+    double f_a;           /* A-fraction q_A of the diblock                   */
+    double phi_p;         /* mean polymer volume fraction; solvent 1 - phi_p */
+    double chi_ab, chi_as, chi_bs, kappa_h;
+    double d_s, d_p;      /* diffusion constants of solvent and monomers     */
+    double inv_beta_v;    /* 1/(beta v)                                      */
+    double gamma_s, gamma_b, gamma_g; /* MRT relaxation parameters           */
+    double f0;            /* reverse-Poiseuille amplitude in units of f*     */
+    double noise_amp;     /* amplitude of the initial uniform noise on omega */
+    uint64_t seed;
+} or_params;
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* FFT (textbook iterative radix-2 Cooley-Tukey) and the naive DFT.          */
+/* Convention: forward  X[k] = sum_n x[n] exp(-2 pi i k n / N),             */
+/*             backward x[n] = sum_k X[k] exp(+2 pi i k n / N)   (no 1/N).  */
+/* ------------------------------------------------------------------------ */
+
+void or_dft_naive(const cplx *x, cplx *out, int n, int sign)
+{
+    for (int k = 0; k < n; k++) {
+        long double re = 0.0L, im = 0.0L;
+        for (int j = 0; j < n; j++) {
+            /* reduce k*j mod n first so the angle stays accurate */
+            long long kj = ((long long)k * j) % n;
+            long double ang = sign * 2.0L * (long double)M_PI * (long double)kj / (long double)n;
+            long double c = cosl(ang), s = sinl(ang);
+            long double xr = creal(x[j]), xi = cimag(x[j]);
+            re += xr * c - xi * s;
+            im += xr * s + xi * c;
+        }
+        out[k] = (double)re + I * (double)im;
+    }
+}
+
+void or_fft1d(cplx *x, int n, int sign)
+{
+    if (n <= 1) return;
+    /* bit-reversal permutation */
+    for (int i = 1, j = 0; i < n; i++) {
+        int bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) { cplx t = x[i]; x[i] = x[j]; x[j] = t; }
+    }
+    /* twiddles exp(sign 2 pi i t / n), t < n/2 */
+    cplx *tw = (cplx *)malloc(sizeof(cplx) * (size_t)(n / 2));
+    for (int t = 0; t < n / 2; t++) {
+        double ang = sign * 2.0 * M_PI * (double)t / (double)n;
+        tw[t] = cos(ang) + I * sin(ang);
+    }
+    for (int len = 2; len <= n; len <<= 1) {
+        int half = len / 2, step = n / len;
+        for (int i = 0; i < n; i += len) {
+            for (int k = 0; k < half; k++) {
+                cplx a = x[i + k];
+                cplx b = x[i + k + half] * tw[k * step];
+                x[i + k] = a + b;
+                x[i + k + half] = a - b;
+            }
+        }
+    }
+    free(tw);
+}
+
+/* 2D transform of a [ny][nx] array: all rows, then all columns. */
+void or_fft2d(cplx *a, int ny, int nx, int sign)
+{
+    for (int y = 0; y < ny; y++) or_fft1d(a + (size_t)y * nx, nx, sign);
+    cplx *col = (cplx *)malloc(sizeof(cplx) * (size_t)ny);
+    for (int x = 0; x < nx; x++) {
+        for (int y = 0; y < ny; y++) col[y] = a[(size_t)y * nx + x];
+        or_fft1d(col, ny, sign);
+        for (int y = 0; y < ny; y++) a[(size_t)y * nx + x] = col[y];
+    }
+    free(col);
+}
+
+/* Angular wavenumber of FFT index m on an axis of n sites and spacing dx.
+ * READING (spectral derivatives): the Nyquist index n/2 carries k = pi/dx in
+ * even operators (the Laplacian, the propagator's Fourier factor) and is
+ * zeroed in odd ones (first derivatives), since i*k has no real-valued
+ * representation there. */
+static double wavenumber(int m, int n, double dx)
+{
+    int mm = (m <= n / 2) ? m : m - n;
+    return 2.0 * M_PI * (double)mm / ((double)n * dx);
+}
+static double wavenumber_odd(int m, int n, double dx)
+{
+    if (2 * m == n) return 0.0;
+    return wavenumber(m, n, dx);
+}
+
+/* Spectral derivative of a real field: order 1 along axis (0 = x, 1 = y)
+ * multiplies by i*k_axis; order 2 by -k_axis^2; order 0 with axis 2 by
+ * -|k|^2 (the Laplacian). */
+void or_spectral_op(const or_params *p, const double *f, double *out, int axis, int order)
+{
+    int nx = p->nx, ny = p->ny;
+    size_t n = (size_t)nx * ny;
+    cplx *a = (cplx *)malloc(sizeof(cplx) * n);
+    for (size_t i = 0; i < n; i++) a[i] = f[i];
+    or_fft2d(a, ny, nx, -1);
+    for (int y = 0; y < ny; y++)
+        for (int x = 0; x < nx; x++) {
+            size_t i = (size_t)y * nx + x;
+            cplx m;
+            if (axis == 2) {
+                double kx = wavenumber(x, nx, p->dx), ky = wavenumber(y, ny, p->dx);
+                m = -(kx * kx + ky * ky);
+            } else if (order == 1) {
+                double k = axis == 0 ? wavenumber_odd(x, nx, p->dx) : wavenumber_odd(y, ny, p->dx);
+                m = I * k;
+            } else {
+                double k = axis == 0 ? wavenumber(x, nx, p->dx) : wavenumber(y, ny, p->dx);
+                m = -k * k;
+            }
+            a[i] *= m;
+        }
+    or_fft2d(a, ny, nx, +1);
+    for (size_t i = 0; i < n; i++) out[i] = creal(a[i]) / (double)n;
+    free(a);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Single-chain statistics: Sec. 2, Eqs. (6)-(11).                          */
+/* ------------------------------------------------------------------------ */
+
+/* READING: N_A = round(q_A N_s) contour intervals belong to the A block;
+ * contour node j (s_j = j/N_s) carries omega_A iff s_j < q_A, i.e. j < N_A,
+ * and omega_B otherwise (the junction node takes omega_B, as the paper's
+ * "otherwise" states). */
+int or_n_a(const or_params *p)
+{
+    return (int)lround(p->f_a * (double)p->ns);
+}
+
+/* Propagate one chain.  Eq. (8): the contour step from s to s + ds is
+ *   g(s+ds) = exp(-N w(s+ds) ds / 2) exp(R_G^2 Laplacian ds) exp(-N w(s) ds / 2) g(s),
+ * with the Laplacian factor applied in Fourier space as exp(-R_G^2 |k|^2 ds).
+ * field_of_node[j] points to the field acting at contour node j.
+ * hist receives g at nodes 0..ns; g at node 0 is g0 (1 for Eqs. (6)-(7)). */
+static void propagate_chain(const or_params *p, const double *const *field_of_node,
+                            const double *g0, double *hist)
+{
+    int nx = p->nx, ny = p->ny, ns = p->ns;
+    size_t n = (size_t)nx * ny;
+    double ds = 1.0 / (double)ns;
+    double nseg = p->n_seg;
+    cplx *work = (cplx *)malloc(sizeof(cplx) * n);
+    double *kfac = (double *)malloc(sizeof(double) * n);
+    for (int y = 0; y < ny; y++)
+        for (int x = 0; x < nx; x++) {
+            double kx = wavenumber(x, nx, p->dx), ky = wavenumber(y, ny, p->dx);
+            kfac[(size_t)y * nx + x] = exp(-p->rg * p->rg * (kx * kx + ky * ky) * ds);
+        }
+    for (size_t i = 0; i < n; i++) hist[i] = g0[i];
+    for (int j = 0; j < ns; j++) {
+        const double *g = hist + (size_t)j * n;
+        double *gnext = hist + (size_t)(j + 1) * n;
+        const double *wj = field_of_node[j], *wj1 = field_of_node[j + 1];
+        for (size_t i = 0; i < n; i++) work[i] = exp(-nseg * wj[i] * ds / 2.0) * g[i];
+        or_fft2d(work, ny, nx, -1);
+        for (size_t i = 0; i < n; i++) work[i] *= kfac[i];
+        or_fft2d(work, ny, nx, +1);
+        for (size_t i = 0; i < n; i++)
+            gnext[i] = exp(-nseg * wj1[i] * ds / 2.0) * creal(work[i]) / (double)n;
+    }
+    free(work);
+    free(kfac);
+}
+
+/* Forward propagator g (from the A end, Eq. (6)) and backward propagator g'
+ * (from the B end, Eq. (7)).  READING: g' sees the field of contour position
+ * 1 - s, i.e. at its node j the field of node ns - j; both start from 1.
+ * g_hist, gp_hist: (ns+1)*n each.  If g0 is NULL both start from 1,
+ * otherwise g starts from g0 and g' from 1. */
+void or_propagate(const or_params *p, const double *w_a, const double *w_b,
+                  const double *g0, double *g_hist, double *gp_hist)
+{
+    int ns = p->ns, na = or_n_a(p);
+    size_t n = (size_t)p->nx * p->ny;
+    const double **fw = (const double **)malloc(sizeof(double *) * (size_t)(ns + 1));
+    const double **bw = (const double **)malloc(sizeof(double *) * (size_t)(ns + 1));
+    for (int j = 0; j <= ns; j++) {
+        fw[j] = (j < na) ? w_a : w_b;
+        int jf = ns - j;
+        bw[j] = (jf < na) ? w_a : w_b;
+    }
+    double *ones = (double *)malloc(sizeof(double) * n);
+    for (size_t i = 0; i < n; i++) ones[i] = 1.0;
+    propagate_chain(p, fw, g0 ? g0 : ones, g_hist);
+    propagate_chain(p, bw, ones, gp_hist);
+    free(ones);
+    free(fw);
+    free(bw);
+}
+
+/* READING (contour quadrature, not stated in the paper): the trapezoid rule on
+ * [0, s_{N_A}] for the A block and on [s_{N_A}, 1] for the B block. */
+static double weight_a(int j, int na, double ds)
+{
+    if (na == 0 || j > na) return 0.0;
+    return (j == 0 || j == na) ? 0.5 * ds : ds;
+}
+static double weight_b(int j, int na, int ns, double ds)
+{
+    if (na == ns || j < na) return 0.0;
+    return (j == na || j == ns) ? 0.5 * ds : ds;
+}
+
+/* Densities, Eqs. (9)-(11), with the partition functions Q_P, Q_S taken as
+ * spatial means (READING: the volume V cancels between Q and the prefactor).
+ * omega: [A, B, S] fields; phi: [A, B, S] out; q[0] = Q_P, q[1] = Q_S. */
+void or_solve(const or_params *p, const double *omega, double *phi, double *q)
+{
+    int ns = p->ns, na = or_n_a(p);
+    size_t n = (size_t)p->nx * p->ny;
+    double ds = 1.0 / (double)ns;
+    double *g = (double *)malloc(sizeof(double) * n * (size_t)(ns + 1));
+    double *gp = (double *)malloc(sizeof(double) * n * (size_t)(ns + 1));
+    or_propagate(p, omega, omega + n, NULL, g, gp);
+
+    double q_p = 0.0;
+    for (size_t i = 0; i < n; i++) q_p += g[(size_t)ns * n + i];
+    q_p /= (double)n;
+
+    for (size_t i = 0; i < n; i++) {
+        double ia = 0.0, ib = 0.0;
+        for (int j = 0; j <= ns; j++) {
+            double prod = g[(size_t)j * n + i] * gp[(size_t)(ns - j) * n + i];
+            ia += weight_a(j, na, ds) * prod;
+            ib += weight_b(j, na, ns, ds) * prod;
+        }
+        phi[i] = p->phi_p * ia / q_p;
+        phi[n + i] = p->phi_p * ib / q_p;
+    }
+
+    const double *w_s = omega + 2 * n;
+    double q_s = 0.0;
+    for (size_t i = 0; i < n; i++) q_s += exp(-w_s[i]);
+    q_s /= (double)n;
+    for (size_t i = 0; i < n; i++) phi[2 * n + i] = (1.0 - p->phi_p) * exp(-w_s[i]) / q_s;
+
+    q[0] = q_p;
+    q[1] = q_s;
+    free(g);
+    free(gp);
+}
+
+/* ------------------------------------------------------------------------ */
+/* EPD dynamics: Sec. 2, Eqs. (1), (5), and App. C.                          */
+/* ------------------------------------------------------------------------ */
+
+/* READING: mu_I = dF/dPhi_I of Eq. (1) with omega as the conjugate field,
+ *   mu_I = sum_{J != I} chi_IJ Phi_J + kappa_H (sum_J Phi_J - 1) - omega_I. */
+void or_mu(const or_params *p, const double *phi, const double *omega, double *mu)
+{
+    size_t n = (size_t)p->nx * p->ny;
+    for (size_t i = 0; i < n; i++) {
+        double pa = phi[i], pb = phi[n + i], ps = phi[2 * n + i];
+        double incompress = p->kappa_h * (pa + pb + ps - 1.0);
+        mu[i] = p->chi_ab * pb + p->chi_as * ps + incompress - omega[i];
+        mu[n + i] = p->chi_ab * pa + p->chi_bs * ps + incompress - omega[n + i];
+        mu[2 * n + i] = p->chi_as * pa + p->chi_bs * pb + incompress - omega[2 * n + i];
+    }
+}
+
+/* Auxiliary convection of omega (App. C, comment 1).  READING: the advective
+ * form omega~ = omega - dt v . grad omega, forward Euler, spectral gradient,
+ * with the LB velocity converted to physical units v = u_lat dx/dt. */
+void or_aux_convection(const or_params *p, const double *omega, const double *vel_lat,
+                       double *omega_tilde)
+{
+    size_t n = (size_t)p->nx * p->ny;
+    double vscale = p->dx / p->dt;
+    double *gx = (double *)malloc(sizeof(double) * n);
+    double *gy = (double *)malloc(sizeof(double) * n);
+    for (int s = 0; s < 3; s++) {
+        const double *w = omega + (size_t)s * n;
+        or_spectral_op(p, w, gx, 0, 1);
+        or_spectral_op(p, w, gy, 1, 1);
+        for (size_t i = 0; i < n; i++) {
+            double vx = vel_lat[i] * vscale, vy = vel_lat[n + i] * vscale;
+            omega_tilde[(size_t)s * n + i] = w[i] - p->dt * (vx * gx[i] + vy * gy[i]);
+        }
+    }
+    free(gx);
+    free(gy);
+}
+
+/* Diffusion step of Eq. (5): omega(t+dt) = omega~ - dt D_I Laplacian mu_I,
+ * with mu evaluated at the intermediate densities (App. C, last comment). */
+void or_diffusion_update(const or_params *p, const double *omega_tilde, const double *mu,
+                         double *omega_new)
+{
+    size_t n = (size_t)p->nx * p->ny;
+    double *lap = (double *)malloc(sizeof(double) * n);
+    for (int s = 0; s < 3; s++) {
+        double d = (s == 2) ? p->d_s : p->d_p;
+        or_spectral_op(p, mu + (size_t)s * n, lap, 2, 0);
+        for (size_t i = 0; i < n; i++)
+            omega_new[(size_t)s * n + i] = omega_tilde[(size_t)s * n + i] - p->dt * d * lap[i];
+    }
+    free(lap);
+}
+
+/* Unit of force density f* = rho R_G / tau^2 in LB lattice units
+ * (dx = dt = rho = 1 on the lattice; tau = R_G^2 / D_S). */
+double or_fstar_lattice(const or_params *p)
+{
+    double tau = p->rg * p->rg / p->d_s;
+    double r = p->dt / tau;
+    return (p->rg / p->dx) * r * r;
+}
+
+/* Force reconstruction, Sec. 2, Eqs. (19)-(20): for each species
+ *   f_I(k) = (1/(beta v)) dPhi_I^D(k) / (D_I dt) * i k / |k|^2,
+ * summed over I; f(k=0) = 0.  Output in LB lattice units (f* -> lattice).
+ * dphi: [A, B, S] composition change over the diffusion step. */
+void or_force(const or_params *p, const double *dphi, double *force_lat)
+{
+    int nx = p->nx, ny = p->ny;
+    size_t n = (size_t)nx * ny;
+    cplx *fx = (cplx *)malloc(sizeof(cplx) * n);
+    cplx *fy = (cplx *)malloc(sizeof(cplx) * n);
+    double fstar = or_fstar_lattice(p);
+    for (size_t i = 0; i < n; i++) { fx[i] = 0.0; fy[i] = 0.0; }
+    cplx *a = (cplx *)malloc(sizeof(cplx) * n);
+    for (int s = 0; s < 3; s++) {
+        double d = (s == 2) ? p->d_s : p->d_p;
+        for (size_t i = 0; i < n; i++) a[i] = dphi[(size_t)s * n + i];
+        or_fft2d(a, ny, nx, -1);
+        for (int y = 0; y < ny; y++)
+            for (int x = 0; x < nx; x++) {
+                size_t i = (size_t)y * nx + x;
+                double kx = wavenumber(x, nx, p->dx), ky = wavenumber(y, ny, p->dx);
+                double k2 = kx * kx + ky * ky;
+                if (k2 == 0.0) continue;
+                cplx c = p->inv_beta_v * a[i] / (d * p->dt) / k2;
+                fx[i] += c * I * wavenumber_odd(x, nx, p->dx);
+                fy[i] += c * I * wavenumber_odd(y, ny, p->dx);
+            }
+    }
+    or_fft2d(fx, ny, nx, +1);
+    or_fft2d(fy, ny, nx, +1);
+    for (size_t i = 0; i < n; i++) {
+        force_lat[i] = creal(fx[i]) / (double)n * fstar;
+        force_lat[n + i] = creal(fy[i]) / (double)n * fstar;
+    }
+    free(a);
+    free(fx);
+    free(fy);
+}
+
+/* ------------------------------------------------------------------------ */
+/* D2Q9 Lattice Boltzmann: Sec. 2, Eqs. (12), (14)-(16), in lattice units.   */
+/* ------------------------------------------------------------------------ */
+
+static const int CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static const double WGT[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                              1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+#define CS2 (1.0 / 3.0)
+
+/* The three D2Q9 ghost-mode basis functions, orthogonal (with weights WGT)
+ * to 1, c_a and c_a c_b - c_s^2 delta_ab. */
+static double ghost_basis(int g, int i)
+{
+    double c2 = (double)(CX[i] * CX[i] + CY[i] * CY[i]);
+    if (g == 0) return (3.0 * c2 - 4.0) * CX[i];
+    if (g == 1) return (3.0 * c2 - 4.0) * CY[i];
+    return 4.5 * c2 * c2 - 7.5 * c2 + 1.0;
+}
+
+/* Reverse-Poiseuille body force, Eq. (23), in lattice units.
+ * READING: node y represents position y + 1/2, so the force flips between
+ * nodes ny/2 - 1 and ny/2 (and between ny - 1 and 0). */
+double or_poiseuille_force(const or_params *p, int y)
+{
+    double a = p->f0 * or_fstar_lattice(p);
+    return (y < p->ny / 2) ? -a : a;
+}
+
+/* Shear viscosity from gamma_s, Eq. (16), lattice units (rho = 1). */
+double or_eta(const or_params *p)
+{
+    return 0.5 * CS2 * (1.0 + p->gamma_s) / (1.0 - p->gamma_s);
+}
+
+/* One LB update: collision with force, Eqs. (14)-(15), then streaming,
+ * Eq. (12).  pop: pre-collision populations [9][ny][nx], replaced by the
+ * populations at t + dt.  force: total force density [2][ny][nx].
+ * vel_out: the fluid velocity at the collision, [2][ny][nx].
+ *
+ * READING (velocity and forcing, after the Dunweg-Ladd mode form the paper
+ * cites): u = (j + f/2)/rho; the mass and momentum modes are conserved except
+ * j* = j + f; the stress relaxes about Pi_eq(u) = rho c_s^2 I + rho u u with
+ * its traceless part scaled by gamma_s and its trace by gamma_b; the force
+ * adds Sigma of Eq. (15); the ghost modes relax to zero with gamma_g.
+ * READING (Eq. (15) in d = 2): the printed 2/3 and 1/3 are the d = 3 values
+ * of 2/d and 1/d; here Sigma = (1+gamma_s)/2 [u f + f u - (u.f) I]
+ *                            + (1+gamma_b)/2 (u.f) I. */
+void or_lb_step(const or_params *p, double *pop, const double *force, double *vel_out)
+{
+    int nx = p->nx, ny = p->ny;
+    size_t n = (size_t)nx * ny;
+    double *post = (double *)malloc(sizeof(double) * 9 * n);
+    for (size_t s = 0; s < n; s++) {
+        double nloc[9];
+        for (int i = 0; i < 9; i++) nloc[i] = pop[(size_t)i * n + s];
+        /* moments */
+        double rho = 0, jx = 0, jy = 0, pxx = 0, pyy = 0, pxy = 0, mg[3] = {0, 0, 0};
+        for (int i = 0; i < 9; i++) {
+            rho += nloc[i];
+            jx += nloc[i] * CX[i];
+            jy += nloc[i] * CY[i];
+            pxx += nloc[i] * CX[i] * CX[i];
+            pyy += nloc[i] * CY[i] * CY[i];
+            pxy += nloc[i] * CX[i] * CY[i];
+            for (int g = 0; g < 3; g++) mg[g] += nloc[i] * ghost_basis(g, i);
+        }
+        double fx = force[s], fy = force[n + s];
+        double ux = (jx + 0.5 * fx) / rho, uy = (jy + 0.5 * fy) / rho;
+        vel_out[s] = ux;
+        vel_out[n + s] = uy;
+        /* equilibrium and non-equilibrium stress */
+        double exx = rho * CS2 + rho * ux * ux, eyy = rho * CS2 + rho * uy * uy, exy = rho * ux * uy;
+        double nxx = pxx - exx, nyy = pyy - eyy, nxy = pxy - exy;
+        double tr = nxx + nyy;
+        double rxx = p->gamma_s * (nxx - 0.5 * tr) + p->gamma_b * 0.5 * tr;
+        double ryy = p->gamma_s * (nyy - 0.5 * tr) + p->gamma_b * 0.5 * tr;
+        double rxy = p->gamma_s * nxy;
+        /* force contribution Sigma, Eq. (15) read in d = 2 */
+        double uf = ux * fx + uy * fy;
+        double hs = 0.5 * (1.0 + p->gamma_s), hb = 0.5 * (1.0 + p->gamma_b);
+        double sxx = hs * (2.0 * ux * fx - uf) + hb * uf;
+        double syy = hs * (2.0 * uy * fy - uf) + hb * uf;
+        double sxy = hs * (ux * fy + uy * fx);
+        /* post-collision moments */
+        double jxs = jx + fx, jys = jy + fy;
+        double mxx = exx + rxx + sxx - rho * CS2; /* Pi* - rho c_s^2 I */
+        double myy = eyy + ryy + syy - rho * CS2;
+        double mxy = exy + rxy + sxy;
+        double gnorm[3] = {2.0 / 3.0, 2.0 / 3.0, 4.0};
+        for (int i = 0; i < 9; i++) {
+            double qxx = CX[i] * CX[i] - CS2, qyy = CY[i] * CY[i] - CS2, qxy = (double)(CX[i] * CY[i]);
+            double v = rho + (jxs * CX[i] + jys * CY[i]) / CS2
+                     + (mxx * qxx + myy * qyy + 2.0 * mxy * qxy) / (2.0 * CS2 * CS2);
+            for (int g = 0; g < 3; g++) v += p->gamma_g * mg[g] * ghost_basis(g, i) / gnorm[g];
+            post[(size_t)i * n + s] = WGT[i] * v;
+        }
+    }
+    /* streaming, Eq. (12): n_i(r + c_i, t + 1) = n_i*(r, t), periodic */
+    for (int i = 0; i < 9; i++)
+        for (int y = 0; y < ny; y++)
+            for (int x = 0; x < nx; x++) {
+                int xd = (x + CX[i] + nx) % nx, yd = (y + CY[i] + ny) % ny;
+                pop[(size_t)i * n + (size_t)yd * nx + xd] = post[(size_t)i * n + (size_t)y * nx + x];
+            }
+    free(post);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Initial state: Sec. 3 (quench), Sec. 4 (flow initialised with Eq. (24)).  */
+/* ------------------------------------------------------------------------ */
+
+/* splitmix64 (Steele, Lea and Flood 2014): state += golden gamma, then the
+ * variant-13 finaliser. */
+uint64_t or_splitmix64(uint64_t x)
+{
+    x += 0x9E3779B97F4A7C15ULL;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
+    return x ^ (x >> 31);
+}
+
+/* READING (the "very small random noise" of Sec. 3): omega_I = a u with u
+ * uniform in [-1, 1), independently per species and site; u comes from the
+ * top 53 bits of splitmix64(seed ^ splitmix64(counter)), with
+ * counter = (species * ny + y) * nx + x. */
+double or_noise(uint64_t seed, uint64_t counter)
+{
+    uint64_t h = or_splitmix64(seed ^ or_splitmix64(counter));
+    double u01 = (double)(h >> 11) * (1.0 / 9007199254740992.0);
+    return 2.0 * u01 - 1.0;
+}
+
+/* Flow field of Eq. (24) at position Y (lattice units). */
+double or_flow_profile(const or_params *p, double yy)
+{
+    double a = p->f0 * or_fstar_lattice(p);
+    double ly = (double)p->ny;
+    double d = yy - 0.5 * ly;
+    return -(a / (2.0 * or_eta(p))) * d * (fabs(d) - 0.5 * ly);
+}
+
+/* The LB velocity of the exact discrete steady state of the reverse-Poiseuille
+ * flow on nodes at Y = y + 1/2 (derived for gamma_g = 0): Eq. (24) plus
+ * f_P(y) (1 - 1/(8 eta)). */
+double or_discrete_profile(const or_params *p, int y)
+{
+    double fp = or_poiseuille_force(p, y);
+    return or_flow_profile(p, (double)y + 0.5) + fp * (1.0 - 1.0 / (8.0 * or_eta(p)));
+}
+
+/* omega: 3n, pop: 9n (pre-collision), vel: 2n (velocity used by the first
+ * convection step).  READING (Sec. 4, "initialized with the flow field"):
+ * rho = 1 and pre-collision populations at second-order equilibrium with
+ * momentum j = v(y) - f_P(y)/2, so that the first collision sees u = v(y). */
+void or_init(const or_params *p, double *omega, double *pop, double *vel)
+{
+    int nx = p->nx, ny = p->ny;
+    size_t n = (size_t)nx * ny;
+    for (int s = 0; s < 3; s++)
+        for (int y = 0; y < ny; y++)
+            for (int x = 0; x < nx; x++) {
+                uint64_t ctr = ((uint64_t)s * (uint64_t)ny + (uint64_t)y) * (uint64_t)nx + (uint64_t)x;
+                omega[(size_t)s * n + (size_t)y * nx + x] = p->noise_amp * or_noise(p->seed, ctr);
+            }
+    for (int y = 0; y < ny; y++) {
+        double v = or_discrete_profile(p, y);
+        double jx = v - 0.5 * or_poiseuille_force(p, y), jy = 0.0;
+        for (int x = 0; x < nx; x++) {
+            size_t s = (size_t)y * nx + x;
+            vel[s] = v;
+            vel[n + s] = 0.0;
+            for (int i = 0; i < 9; i++) {
+                double cj = CX[i] * jx + CY[i] * jy;
+                double jj = jx * jx + jy * jy;
+                pop[(size_t)i * n + s] = WGT[i] * (1.0 + cj / CS2 + cj * cj / (2.0 * CS2 * CS2) - jj / (2.0 * CS2));
+            }
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* One coupled EPD/LB time step (App. C), CG inversion truncated to its       */
+/* starting guess (the auxiliary convection of omega).                        */
+/* ------------------------------------------------------------------------ */
+
+/* State in/out: omega (3n), pop (9n), vel (2n).  Outputs: phi (3n) = Phi at
+ * t + dt, q[2] = (Q_P, Q_S) of that solve, force (2n) = the polymer force
+ * handed to LB (lattice units), phi_tilde (3n, may be NULL). */
+void or_step(const or_params *p, double *omega, double *pop, double *vel,
+             double *phi, double *q, double *force, double *phi_tilde_out)
+{
+    int nx = p->nx, ny = p->ny;
+    size_t n = (size_t)nx * ny;
+    double *wt = (double *)malloc(sizeof(double) * 3 * n);
+    double *pt = (double *)malloc(sizeof(double) * 3 * n);
+    double *mu = (double *)malloc(sizeof(double) * 3 * n);
+    double *dphi = (double *)malloc(sizeof(double) * 3 * n);
+    double *ftot = (double *)malloc(sizeof(double) * 2 * n);
+    double qt[2];
+
+    /* (1) auxiliary convection of omega with the current flow */
+    or_aux_convection(p, omega, vel, wt);
+    /* (2) densities at the intermediate fields */
+    or_solve(p, wt, pt, qt);
+    /* (3) diffusion step of omega with mu at the intermediate densities */
+    or_mu(p, pt, wt, mu);
+    or_diffusion_update(p, wt, mu, omega);
+    /* (4) densities at t + dt */
+    or_solve(p, omega, phi, q);
+    /* (5) force from the composition change of the diffusion step */
+    for (size_t i = 0; i < 3 * n; i++) dphi[i] = phi[i] - pt[i];
+    or_force(p, dphi, force);
+    /* (6) LB update driven by the polymer force plus the body force */
+    for (int y = 0; y < ny; y++)
+        for (int x = 0; x < nx; x++) {
+            size_t s = (size_t)y * nx + x;
+            ftot[s] = force[s] + or_poiseuille_force(p, y);
+            ftot[n + s] = force[n + s];
+        }
+    or_lb_step(p, pop, ftot, vel);
+    if (phi_tilde_out) memcpy(phi_tilde_out, pt, sizeof(double) * 3 * n);
+    free(wt);
+    free(pt);
+    free(mu);
+    free(dphi);
+    free(ftot);
+}
+
+/* Observables: sigma of Eq. (21) = mean |Phi_A + Phi_B - phi_p|. */
+double or_sigma(const or_params *p, const double *phi)
+{
+    size_t n = (size_t)p->nx * p->ny;
+    double s = 0.0;
+    for (size_t i = 0; i < n; i++) s += fabs(phi[i] + phi[n + i] - p->phi_p);
+    return s / (double)n;
+}
