@@ -1,0 +1,336 @@
+#!/usr/bin/env python3
+"""Throughput of the hybrid LB/EPD time step on GB300.
+
+Workload (N = 1 per GPU): four independent 256 x 512 runs (flow along the
+512-site axis), N_s = 64, polymer fraction 0.2, one per reverse-Poiseuille
+amplitude 0, 1e-6, 4e-6, 1.6e-5 f*, seeded +-1e-3 noise (the paper's
+synthetic quench), mixed precision (FP32 propagators and LB, FP64 fields,
+contour sums, Q and EPD transforms).  One step = one coupled EPD/LB time step
+of all four runs: 2 single-chain solves x 2 chains x N_s contour steps plus
+the EPD update, the force and one D2Q9 collide-stream per run.
+
+Metric: propagator site.contour-step updates/s (nx ny N_s x 2 chains x
+2 solves x runs per step / time); LB MLUPS and the FP64-plain path reported
+beside it.  Under torchrun every rank steps its own batch (replicas, no
+collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "propagator site·contour-step updates/s + LB MLUPS, 1 GB300, vs FP64 plain"
+UNIT = "site·contour-steps/s"
+HBM_FALLBACK = 6800.0
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK, "fallback"
+
+
+def units_per_step(runs) -> float:
+    return float(sum(r.nx * r.ny * r.ns * 2 * 2 for r in runs))
+
+
+def sites_per_step(runs) -> float:
+    return float(sum(r.nx * r.ny for r in runs))
+
+
+def launches_per_step(runs) -> int:
+    # per batch of equal runs: aux convection 2, two solves of (2 N_s + 3),
+    # diffusion 2, force 3, LB 1
+    seen = {}
+    for r in runs:
+        key = (r.nx, r.ny, r.ns, r.precision)
+        seen[key] = r.ns
+    return sum(4 * ns + 14 for ns in seen.values())
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.out.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_step_time(run, nsteps: int = 1) -> float:
+    """Seconds per oracle coupled step of one run (single host thread)."""
+    import oracle as O
+
+    p = O.Params(**{k: getattr(run, k) for k in O.Params.__dataclass_fields__})
+    st = O.initial_state(p)
+    t0 = time.perf_counter()
+    O.step(p, st, nsteps)
+    return (time.perf_counter() - t0) / nsteps
+
+
+def run_reference(args) -> None:
+    """The oracle (plain FP64 C, one host thread) on the same workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1804_02883_gb300 import workloads as W
+    import oracle as O
+
+    O.build()
+    runs = W.channel_256x512()
+    for _ in range(min(args.warmup, 1)):
+        oracle_step_time(runs[0], 1)
+    t = 0.0
+    units = 0.0
+    for k in range(args.steps):
+        r = runs[k % len(runs)]
+        t += oracle_step_time(r, 1)
+        units += r.nx * r.ny * r.ns * 4
+    value = units / t
+    sample = f"{args.steps} oracle coupled steps, one 256x512 N_s=64 run each (cycling the 4 shear amplitudes)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "256x512 channel, N_s=64, shear amplitudes 0/1e-6/4e-6/1.6e-5 f*", "precision": "fp64"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def time_steps(h, stream, steps, flush, with_kernels=False):
+    import torch
+
+    per_step, kern = [], []
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.add_(1.0)  # write a buffer larger than L2 between timed steps
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        h.step(1)
+        b.record(stream)
+        b.synchronize()
+        per_step.append(a.elapsed_time(b))
+        if with_kernels:
+            kern.append(h.kernel_times())
+    return per_step, kern
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+
+    import paper_1804_02883_gb300 as P
+    from paper_1804_02883_gb300 import workloads as W
+
+    P.lib()
+    runs = W.channel_256x512(P.MIXED_FP32, seed=2 + 7919 * rank)
+    h = P.EpdLb(runs)
+    h.enable_timing(True)
+    stream = h.stream
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
+
+    for _ in range(args.warmup):
+        h.step(1)
+    h.sync()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    with Clocks(local) as clk:
+        t0 = time.perf_counter()
+        per_step, kern = time_steps(h, stream, args.steps, flush, with_kernels=True)
+        barrier()
+        wall = time.perf_counter() - t0
+    h.sync()
+    dev_ms = float(sum(per_step))
+    if dist is not None:
+        t = torch.tensor([dev_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_ms = float(t.item())
+    units = units_per_step(runs) * args.steps * world
+    value = units / (dev_ms * 1e-3)
+    ms_per_step = dev_ms / args.steps
+    lb_mlups = sites_per_step(runs) * args.steps * world / (dev_ms * 1e-3) / 1e6
+
+    # kernel durations inside the timed steps (event nodes in the step graph)
+    nsite = sites_per_step(runs)
+    kt = {k: statistics.mean(d[k] for d in kern) for k in kern[0]}
+    bytes_per_site = {"prop_row_accumulate": 64.0, "prop_row_store": 32.0, "prop_col": 16.0, "lb_collide_stream": 88.0}
+    hbm, peak_kind = peaks()
+    kernels = {}
+    for k, bps in bytes_per_site.items():
+        gbs = bps * nsite / (kt[k] * 1e-3) / 1e9
+        kernels[k] = {"ms": kt[k], "bytes_per_site": bps, "achieved_gbs": gbs, "frac": gbs / hbm}
+    dom = "prop_row_accumulate"
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": kernels[dom]["achieved_gbs"], "peak": hbm,
+                "unit": "GB/s", "frac": kernels[dom]["achieved_gbs"] / hbm, "traffic": None,
+                "peak_source": f"{peak_kind} hbm_gbs (copy)"}
+
+    # end to end through the C ABI with host buffers: upload omega of every
+    # run from pinned memory, one step, read Phi and Q of every run back
+    n = runs[0].nx * runs[0].ny
+    host_om = [torch.empty(3 * n, dtype=torch.float64, pin_memory=True) for _ in runs]
+    host_phi = [torch.empty(3 * n, dtype=torch.float64, pin_memory=True) for _ in runs]
+    host_q = [torch.empty(2, dtype=torch.float64, pin_memory=True) for _ in runs]
+    for k in range(len(runs)):
+        om, _, _ = h.get_state(k)
+        host_om[k].copy_(torch.from_numpy(om.ravel()))
+    h.enable_timing(False)
+    h.step(1)
+    h.sync()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        for k in range(len(runs)):
+            h.set_state_ptr(k, host_om[k].data_ptr(), None, None)
+        h.step(1)
+        for k in range(len(runs)):
+            h.densities_ptr(k, host_phi[k].data_ptr(), host_q[k].data_ptr())
+    barrier()
+    e2e_t = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_t], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    e2e = {"value": units_per_step(runs) * args.e2e_steps * world / e2e_t, "unit": UNIT,
+           "h2d_bytes_per_step": int(len(runs) * 3 * n * 8),
+           "d2h_bytes_per_step": int(len(runs) * (3 * n * 8 + 16))}
+
+    # FP64-plain path on the same workload
+    runs64 = W.channel_256x512(P.PLAIN_FP64, seed=2 + 7919 * rank)
+    h.close()
+    del h
+    h64 = P.EpdLb(runs64)
+    h64.step(1)
+    h64.sync()
+    per64, _ = time_steps(h64, h64.stream, args.fp64_steps, flush)
+    ms64 = sum(per64) / len(per64)
+    fp64 = {"value": units_per_step(runs64) / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
+            "lb_mlups": sites_per_step(runs64) / (ms64 * 1e-3) / 1e6, "steps": args.fp64_steps}
+    h64.close()
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            import oracle as O
+
+            O.build()
+            t1 = oracle_step_time(runs[1], 1)
+            cpu = {"value": runs[1].nx * runs[1].ny * runs[1].ns * 4 / t1, "unit": UNIT, "cores": 1,
+                   "kind": "oracle", "sample": "1 oracle coupled step of one 256x512 N_s=64 run (f0 = 1e-6 f*)",
+                   "seconds": t1}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "4 runs of 256x512 (ny x nx), N_s=64, phi_p=0.2, f_A=0.5, "
+                                   "shear amplitudes 0/1e-6/4e-6/1.6e-5 f*, seeded +-1e-3 noise",
+                       "precision": "mixed (FP32 propagator and LB; FP64 fields, contour sums, Q, EPD transforms)",
+                       "l2": "flushed (256 MB write) before every timed step", "parallelism": f"replicas x{world}"},
+            "lb_mlups": lb_mlups,
+            "fp64_plain": fp64,
+            "speedup_vs_fp64_plain": value / fp64["value"],
+            "wall_s": wall,
+            "kernels": kernels,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches_per_step(runs) * args.steps,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,191 @@
+/*
+ * epd_lb.h -- C ABI of the GB300 (sm_103a) hybrid Lattice-Boltzmann /
+ * External-Potential-Dynamics time stepper of Heuser, Sevink and Schmid,
+ * "Self-assembly of polymeric particles in Poiseuille flow: a hybrid Lattice
+ * Boltzmann / External Potential Dynamics simulation study" (arXiv:1804.02883).
+ *
+ * One call of epd_lb_step advances every run of a handle by one time step of
+ * the method (App. C, flow chart, with the omega-from-Phi inversion taken at
+ * its starting guess, the auxiliary convection of omega):
+ *   1. omega~ = omega - dt v . grad omega                    (App. C, item 1)
+ *   2. Phi~ from omega~ by the single-chain solve           (Sec. 2, Eqs. (6)-(11))
+ *   3. omega(t+dt) = omega~ - dt D_I Lap mu_I(Phi~)          (Sec. 2, Eq. (5); App. C)
+ *   4. Phi(t+dt) from omega(t+dt)                            (Eqs. (6)-(11))
+ *   5. polymer force from Phi(t+dt) - Phi~                   (Sec. 2, Eqs. (19)-(20))
+ *   6. D2Q9 MRT collide-stream with that force plus the
+ *      reverse-Poiseuille body force                         (Eqs. (12), (14)-(16), (23))
+ *
+ * Conventions for every entry point:
+ *  - Return EPD_LB_OK (0) on success or a negative EPD_LB_E* code; the text
+ *    of the last error of a handle is available from epd_lb_last_error.
+ *  - Field layout is [field][y][x] with x fastest; x is the flow axis and y
+ *    runs across the channel.  Species fields are ordered [A, B, S], velocity
+ *    components [x, y], LB populations [i] in the D2Q9 order
+ *      0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1).
+ *  - Host buffers are caller-owned FP64 arrays; the library never frees caller
+ *    memory.  *_dev variants take device pointers and work on the handle's
+ *    stream.  Calls on one handle must not run concurrently.
+ *  - Units: lengths in R_G, times in tau = R_G^2/D_S for the EPD part; the
+ *    LB part is in lattice units (dx = dt = rho0 = 1).
+ */
+#ifndef EPD_LB_H
+#define EPD_LB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    EPD_LB_OK = 0,
+    EPD_LB_EINVAL = -1,      /* invalid argument or parameter set            */
+    EPD_LB_ENOMEM = -2,      /* workspace too small or allocation failed     */
+    EPD_LB_ECUDA = -3,       /* a CUDA runtime call failed                   */
+    EPD_LB_ENONFINITE = -4,  /* non-finite value or Q <= 0 detected on device */
+    EPD_LB_EUNSTABLE = -5,   /* Mach-number pre-flight refused the run       */
+    EPD_LB_ETIMEOUT = -6,    /* a bounded device wait gave up                */
+    EPD_LB_ENOTCONV = -7     /* reserved: iterative inversion did not converge */
+};
+
+enum {
+    EPD_LB_PLAIN_FP64 = 0,   /* every field and transform in FP64            */
+    EPD_LB_MIXED_FP32 = 1    /* propagators and LB populations in FP32; fields
+                                omega and Phi, contour sums, Q, masses and the
+                                EPD/force transforms in FP64                 */
+};
+
+/*
+ * Parameters of one run (Sec. 2 model, Sec. 3 and Sec. 4 set-up).
+ *  nx, ny      grid sites, each a power of two in [8, 2048]; nx is the flow axis
+ *  ns          contour steps N_s (even, 2..512)
+ *  precision   EPD_LB_PLAIN_FP64 or EPD_LB_MIXED_FP32
+ *  dx, dt, rg  grid spacing, time step, gyration radius R_G (paper: 1/3, 0.002, 1)
+ *  n_seg       segments per chain N (paper: 17); the Boltzmann factor is exp(-N w ds/2)
+ *  f_a         A-fraction q_A; the A block covers round(f_a ns) contour intervals
+ *  phi_p       mean polymer volume fraction; the solvent has 1 - phi_p
+ *  chi_*, kappa_h  Flory-Huggins and Helfand parameters of Eq. (1)
+ *  d_s, d_p    diffusion constants of solvent and of both monomer species
+ *  inv_beta_v  1/(beta v), the prefactor of the force of Eq. (20)
+ *  gamma_s, gamma_b, gamma_g  MRT relaxation of shear, bulk and ghost modes
+ *              (0, 0, 0 is BGK with tau = 1)
+ *  f0          reverse-Poiseuille amplitude of Eq. (23) in units of f* = rho R_G / tau^2
+ *  noise_amp   amplitude a of the initial noise omega_I = a U(-1, 1)
+ *  seed        seed of the counter-based noise (splitmix64)
+ */
+typedef struct epd_lb_params {
+    int32_t nx, ny, ns, precision;
+    double dx, dt, rg, n_seg, f_a, phi_p;
+    double chi_ab, chi_as, chi_bs, kappa_h;
+    double d_s, d_p, inv_beta_v;
+    double gamma_s, gamma_b, gamma_g;
+    double f0;
+    double noise_amp;
+    uint64_t seed;
+} epd_lb_params;
+
+typedef struct epd_lb epd_lb; /* opaque, library-owned */
+
+/* Device workspace needed by epd_lb_init for nruns runs described by the
+ * array p[0..nruns-1].  Runs may differ in every parameter; runs sharing grid,
+ * contour length, precision and model parameters are stepped as one batch. */
+int epd_lb_workspace_bytes(const epd_lb_params *p, int32_t nruns, size_t *bytes);
+
+/* Create a handle for nruns runs.  workspace: device memory of at least
+ * epd_lb_workspace_bytes bytes, 256-byte aligned, owned by the caller and kept
+ * alive until epd_lb_destroy; NULL lets the library cudaMalloc its own.
+ * cuda_stream: a cudaStream_t created by the caller (not the legacy default
+ * stream) on which every call of this handle is ordered; NULL lets the library
+ * create a non-blocking stream.  Initialises every run (Sec. 3: omega noise
+ * from the seed; Sec. 4: flow at the steady reverse-Poiseuille profile of
+ * Eq. (24)) and solves Phi(0).  Fails with EPD_LB_EUNSTABLE when the expected
+ * peak flow exceeds Mach 0.3. */
+int epd_lb_init(const epd_lb_params *p, int32_t nruns, void *workspace, size_t workspace_bytes,
+                void *cuda_stream, epd_lb **out);
+
+/* Advance every run by nsteps time steps (the six operations listed at the
+ * top).  Asynchronous on the handle's stream; the step sequence is captured
+ * once into a CUDA graph and replayed. */
+int epd_lb_step(epd_lb *h, int64_t nsteps);
+
+/* Wait for the handle's stream and report device-side errors
+ * (EPD_LB_ENONFINITE when a solve produced Q <= 0 or a non-finite Q). */
+int epd_lb_sync(epd_lb *h);
+
+/* Phi_{A,B,S}(t) of run `run` (3*ny*nx doubles) and q[0] = Q_P, q[1] = Q_S of
+ * the solve that produced it (Q as spatial means, Eqs. (9)-(11)).  Either
+ * pointer may be NULL.  Synchronous. */
+int epd_lb_densities(epd_lb *h, int32_t run, double *phi, double *q);
+
+/* Fluid velocity u = (j + f/2)/rho of the last collision, lattice units,
+ * 2*ny*nx doubles.  Synchronous. */
+int epd_lb_velocity(epd_lb *h, int32_t run, double *v);
+
+/* Device-pointer variants of the two calls above: asynchronous copies on the
+ * handle's stream into caller device memory of the same layout (FP64). */
+int epd_lb_densities_dev(epd_lb *h, int32_t run, double *phi_dev, double *q_dev);
+int epd_lb_velocity_dev(epd_lb *h, int32_t run, double *v_dev);
+
+/* Full state of a run: omega (3n), pre-collision LB populations (9n, the
+ * populations about to be collided at the next step) and the velocity handed
+ * to the next convection step (2n).  Any pointer may be NULL.  Synchronous. */
+int epd_lb_get_state(epd_lb *h, int32_t run, double *omega, double *pop, double *vel);
+
+/* Replace the state of a run (same layout as epd_lb_get_state).  A NULL
+ * pointer keeps that part of the state.  Phi is not recomputed here: the next
+ * epd_lb_step derives it from the new omega (epd_lb_solve gives it at once).
+ * In EPD_LB_MIXED_FP32 the populations and velocity are rounded to FP32.  Host
+ * buffers; the copies are staged through the workspace.  Synchronous. */
+int epd_lb_set_state(epd_lb *h, int32_t run, const double *omega, const double *pop, const double *vel);
+
+/* One single-chain solve, Eqs. (6)-(11), of run `run`'s grid and parameters
+ * for the host fields omega (3n): phi (3n) and q[2] = (Q_P, Q_S).  Does not
+ * change the run's state.  Synchronous. */
+int epd_lb_solve(epd_lb *h, int32_t run, const double *omega, double *phi, double *q);
+
+/* Per-run observables of the current state: out[0] = <Phi_A>, out[1] = <Phi_B>,
+ * out[2] = <Phi_S>, out[3] = sigma of Eq. (21), out[4] = LB mass / sites,
+ * out[5] = max |u| (lattice), out[6] = Q_P, out[7] = Q_S.  Synchronous. */
+int epd_lb_observables(epd_lb *h, int32_t run, double *out);
+
+/* Checkpoint: serialise every run's state (parameters, omega, the stored LB
+ * populations in the library's internal representation, velocity) to buf.
+ * With buf == NULL only *len is set to the size needed.  Restoring with
+ * epd_lb_load into a handle created with the same parameters recomputes Phi
+ * and continues bit-identically. */
+int epd_lb_save(epd_lb *h, void *buf, size_t *len);
+int epd_lb_load(epd_lb *h, const void *buf, size_t len);
+
+/* Kernel timing inside the captured step.  epd_lb_enable_timing(h, 1)
+ * re-captures the step graph with CUDA event-record nodes around four
+ * launches of the first batch: the propagator row pass of contour node
+ * N_s/4 (history store) and 3 N_s/4 (contour accumulation) of the second
+ * solve, the column pass before the latter, and the LB collide-stream.
+ * epd_lb_kernel_times waits for the stream and writes the durations of the
+ * most recent step, in milliseconds, to ms[0..3] in that order. */
+int epd_lb_enable_timing(epd_lb *h, int32_t on);
+int epd_lb_kernel_times(epd_lb *h, double *ms);
+
+/* Text of the last error on the handle (never NULL). */
+const char *epd_lb_last_error(const epd_lb *h);
+
+/* Release the handle (and its workspace if the library allocated it). */
+void epd_lb_destroy(epd_lb *h);
+
+/*
+ * Stateless single-chain solve on device pointers (Sec. 2, Eqs. (6)-(11)):
+ * omega_dev (3*ny*nx doubles) -> phi_dev (3*ny*nx doubles), q_dev[2] =
+ * (Q_P, Q_S).  workspace_dev of epd_prop_solve_workspace_bytes bytes holds the
+ * propagator history and the transform buffers; cuda_stream may be NULL (the
+ * legacy default stream).  Asynchronous.
+ */
+int epd_prop_solve_workspace_bytes(const epd_lb_params *p, size_t *bytes);
+int epd_prop_solve(const epd_lb_params *p, const double *omega_dev, double *phi_dev, double *q_dev,
+                   void *workspace_dev, size_t workspace_bytes, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EPD_LB_H */

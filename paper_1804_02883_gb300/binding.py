@@ -1,0 +1,314 @@
+"""Thin ctypes binding of ``include/epd_lb.h`` (libepd_lb.so).
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+PyTorch supplies device memory (the workspace) and the stream.  There is no
+CPU fallback: if the library is missing or no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field, fields
+
+import numpy as np
+
+from . import build as _build
+
+EPD_LB_OK = 0
+ERRORS = {
+    -1: "EPD_LB_EINVAL",
+    -2: "EPD_LB_ENOMEM",
+    -3: "EPD_LB_ECUDA",
+    -4: "EPD_LB_ENONFINITE",
+    -5: "EPD_LB_EUNSTABLE",
+    -6: "EPD_LB_ETIMEOUT",
+    -7: "EPD_LB_ENOTCONV",
+}
+PLAIN_FP64 = 0
+MIXED_FP32 = 1
+
+# Exported symbols declared in include/epd_lb.h.
+SYMBOLS = (
+    "epd_lb_workspace_bytes", "epd_lb_init", "epd_lb_step", "epd_lb_sync", "epd_lb_densities",
+    "epd_lb_velocity", "epd_lb_densities_dev", "epd_lb_velocity_dev", "epd_lb_get_state",
+    "epd_lb_set_state", "epd_lb_solve", "epd_lb_observables", "epd_lb_save", "epd_lb_load",
+    "epd_lb_last_error", "epd_lb_destroy", "epd_prop_solve_workspace_bytes", "epd_prop_solve",
+    "epd_lb_enable_timing", "epd_lb_kernel_times",
+)
+
+
+class CParams(ctypes.Structure):
+    """Mirror of ``epd_lb_params``."""
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("ns", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("dx", ctypes.c_double), ("dt", ctypes.c_double), ("rg", ctypes.c_double), ("n_seg", ctypes.c_double),
+        ("f_a", ctypes.c_double), ("phi_p", ctypes.c_double), ("chi_ab", ctypes.c_double),
+        ("chi_as", ctypes.c_double), ("chi_bs", ctypes.c_double), ("kappa_h", ctypes.c_double),
+        ("d_s", ctypes.c_double), ("d_p", ctypes.c_double), ("inv_beta_v", ctypes.c_double),
+        ("gamma_s", ctypes.c_double), ("gamma_b", ctypes.c_double), ("gamma_g", ctypes.c_double),
+        ("f0", ctypes.c_double), ("noise_amp", ctypes.c_double), ("seed", ctypes.c_uint64),
+    ]
+
+
+@dataclass
+class RunParams:
+    """Parameters of one run (see ``epd_lb_params``).  Defaults: the paper's
+    model set of Sec. 3 (N = 17, kappa_H = 1.176, chi_AB = 1.05,
+    chi_AS = 1.20, chi_BS = 0.75, D_S = 1, D_P = D_S/N, dx = R_G/3,
+    dt = 0.002 tau), LB relaxation 0 (BGK tau = 1), f0 in units of f*."""
+    nx: int = 64
+    ny: int = 64
+    ns: int = 32
+    precision: int = PLAIN_FP64
+    dx: float = 1.0 / 3.0
+    dt: float = 0.002
+    rg: float = 1.0
+    n_seg: float = 17.0
+    f_a: float = 0.5
+    phi_p: float = 0.3
+    chi_ab: float = 1.05
+    chi_as: float = 1.20
+    chi_bs: float = 0.75
+    kappa_h: float = 1.176
+    d_s: float = 1.0
+    d_p: float = 1.0 / 17.0
+    inv_beta_v: float = 1.0
+    gamma_s: float = 0.0
+    gamma_b: float = 0.0
+    gamma_g: float = 0.0
+    f0: float = 0.0
+    noise_amp: float = 1e-3
+    seed: int = 1
+
+    def c(self) -> CParams:
+        p = CParams()
+        for f in fields(self):
+            setattr(p, f.name, getattr(self, f.name))
+        return p
+
+    @property
+    def n(self) -> int:
+        return self.nx * self.ny
+
+
+_lib = None
+
+
+def lib():
+    """Load libepd_lb.so (building it if the sources are newer)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        P = ctypes.POINTER(CParams)
+        vp, dp, i32, i64 = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_int64
+        szp = ctypes.POINTER(ctypes.c_size_t)
+        sig = {
+            "epd_lb_workspace_bytes": (ctypes.c_int, [P, i32, szp]),
+            "epd_lb_init": (ctypes.c_int, [P, i32, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]),
+            "epd_lb_step": (ctypes.c_int, [vp, i64]),
+            "epd_lb_sync": (ctypes.c_int, [vp]),
+            "epd_lb_densities": (ctypes.c_int, [vp, i32, vp, vp]),
+            "epd_lb_velocity": (ctypes.c_int, [vp, i32, vp]),
+            "epd_lb_densities_dev": (ctypes.c_int, [vp, i32, vp, vp]),
+            "epd_lb_velocity_dev": (ctypes.c_int, [vp, i32, vp]),
+            "epd_lb_get_state": (ctypes.c_int, [vp, i32, vp, vp, vp]),
+            "epd_lb_set_state": (ctypes.c_int, [vp, i32, vp, vp, vp]),
+            "epd_lb_solve": (ctypes.c_int, [vp, i32, vp, vp, vp]),
+            "epd_lb_observables": (ctypes.c_int, [vp, i32, vp]),
+            "epd_lb_save": (ctypes.c_int, [vp, vp, szp]),
+            "epd_lb_load": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
+            "epd_lb_last_error": (ctypes.c_char_p, [vp]),
+            "epd_lb_destroy": (None, [vp]),
+            "epd_prop_solve_workspace_bytes": (ctypes.c_int, [P, szp]),
+            "epd_prop_solve": (ctypes.c_int, [P, vp, vp, vp, vp, ctypes.c_size_t, vp]),
+            "epd_lb_enable_timing": (ctypes.c_int, [vp, i32]),
+            "epd_lb_kernel_times": (ctypes.c_int, [vp, vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class EpdLbError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str = ""):
+        super().__init__(f"{where}: {ERRORS.get(code, code)} {msg}".strip())
+        self.code = code
+
+
+def _params_array(runs):
+    arr = (CParams * len(runs))()
+    for i, r in enumerate(runs):
+        arr[i] = r.c()
+    return arr
+
+
+def _ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+# --- C-ABI names -----------------------------------------------------------
+
+def epd_lb_workspace_bytes(runs) -> int:
+    n = ctypes.c_size_t()
+    rc = lib().epd_lb_workspace_bytes(_params_array(runs), len(runs), ctypes.byref(n))
+    if rc:
+        raise EpdLbError(rc, "epd_lb_workspace_bytes")
+    return n.value
+
+
+def epd_prop_solve_workspace_bytes(run: RunParams) -> int:
+    n = ctypes.c_size_t()
+    rc = lib().epd_prop_solve_workspace_bytes(ctypes.byref(run.c()), ctypes.byref(n))
+    if rc:
+        raise EpdLbError(rc, "epd_prop_solve_workspace_bytes")
+    return n.value
+
+
+def epd_prop_solve(run: RunParams, omega_dev: int, phi_dev: int, q_dev: int, workspace_dev: int,
+                   workspace_bytes: int, stream: int = 0) -> None:
+    rc = lib().epd_prop_solve(ctypes.byref(run.c()), omega_dev, phi_dev, q_dev, workspace_dev, workspace_bytes, stream)
+    if rc:
+        raise EpdLbError(rc, "epd_prop_solve")
+
+
+class EpdLb:
+    """Handle over ``epd_lb_*``: a batch of runs stepped on one GPU.
+
+    The workspace is a torch uint8 tensor on the device and the handle's
+    calls are ordered on a dedicated torch stream."""
+
+    def __init__(self, runs, device: str = "cuda"):
+        import torch
+
+        if isinstance(runs, RunParams):
+            runs = [runs]
+        self.runs = list(runs)
+        self.torch = torch
+        nbytes = epd_lb_workspace_bytes(self.runs)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) & ~255
+        self.stream = torch.cuda.Stream(device=device)
+        h = ctypes.c_void_p()
+        rc = lib().epd_lb_init(_params_array(self.runs), len(self.runs), aligned, nbytes,
+                               self.stream.cuda_stream, ctypes.byref(h))
+        if rc:
+            raise EpdLbError(rc, "epd_lb_init")
+        self.h = h
+
+    # -- checked call ------------------------------------------------------
+    def _ck(self, rc: int, where: str):
+        if rc:
+            msg = lib().epd_lb_last_error(self.h)
+            raise EpdLbError(rc, where, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().epd_lb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def n(self, run: int = 0) -> int:
+        return self.runs[run].n
+
+    def shape(self, run: int = 0):
+        return self.runs[run].ny, self.runs[run].nx
+
+    # -- the C-ABI calls ----------------------------------------------------
+    def step(self, nsteps: int = 1):
+        self._ck(lib().epd_lb_step(self.h, nsteps), "epd_lb_step")
+
+    def sync(self):
+        self._ck(lib().epd_lb_sync(self.h), "epd_lb_sync")
+
+    def densities(self, run: int = 0):
+        ny, nx = self.shape(run)
+        phi = np.empty((3, ny, nx))
+        q = np.empty(2)
+        self._ck(lib().epd_lb_densities(self.h, run, _ptr(phi), _ptr(q)), "epd_lb_densities")
+        return phi, q
+
+    def velocity(self, run: int = 0):
+        ny, nx = self.shape(run)
+        v = np.empty((2, ny, nx))
+        self._ck(lib().epd_lb_velocity(self.h, run, _ptr(v)), "epd_lb_velocity")
+        return v
+
+    def densities_dev(self, run: int, phi_dev, q_dev):
+        self._ck(lib().epd_lb_densities_dev(self.h, run, phi_dev.data_ptr(), q_dev.data_ptr()), "epd_lb_densities_dev")
+
+    def velocity_dev(self, run: int, v_dev):
+        self._ck(lib().epd_lb_velocity_dev(self.h, run, v_dev.data_ptr()), "epd_lb_velocity_dev")
+
+    def get_state(self, run: int = 0):
+        ny, nx = self.shape(run)
+        om = np.empty((3, ny, nx))
+        pop = np.empty((9, ny, nx))
+        vel = np.empty((2, ny, nx))
+        self._ck(lib().epd_lb_get_state(self.h, run, _ptr(om), _ptr(pop), _ptr(vel)), "epd_lb_get_state")
+        return om, pop, vel
+
+    def set_state(self, run: int, omega=None, pop=None, vel=None):
+        """Replace omega, pre-collision populations and/or velocity (None keeps)."""
+        args = []
+        for a, k in ((omega, 3), (pop, 9), (vel, 2)):
+            if a is None:
+                args.append(None)
+            else:
+                a = np.ascontiguousarray(a, dtype=np.float64)
+                assert a.size == k * self.n(run)
+                args.append(a)
+        ptrs = [None if a is None else _ptr(a) for a in args]
+        self._ck(lib().epd_lb_set_state(self.h, run, *ptrs), "epd_lb_set_state")
+
+    def set_state_ptr(self, run: int, omega_ptr: int, pop_ptr: int, vel_ptr: int):
+        """set_state from raw host pointers (e.g. pinned torch tensors)."""
+        self._ck(lib().epd_lb_set_state(self.h, run, omega_ptr, pop_ptr, vel_ptr), "epd_lb_set_state")
+
+    def densities_ptr(self, run: int, phi_ptr: int, q_ptr: int):
+        self._ck(lib().epd_lb_densities(self.h, run, phi_ptr, q_ptr), "epd_lb_densities")
+
+    def solve(self, run: int, omega):
+        ny, nx = self.shape(run)
+        om = np.ascontiguousarray(omega, dtype=np.float64)
+        phi = np.empty((3, ny, nx))
+        q = np.empty(2)
+        self._ck(lib().epd_lb_solve(self.h, run, _ptr(om), _ptr(phi), _ptr(q)), "epd_lb_solve")
+        return phi, q
+
+    def observables(self, run: int = 0) -> dict:
+        out = np.empty(8)
+        self._ck(lib().epd_lb_observables(self.h, run, _ptr(out)), "epd_lb_observables")
+        keys = ("mean_phi_a", "mean_phi_b", "mean_phi_s", "sigma", "lb_mass", "max_u", "q_p", "q_s")
+        return dict(zip(keys, out.tolist()))
+
+    def enable_timing(self, on: bool = True):
+        self._ck(lib().epd_lb_enable_timing(self.h, int(on)), "epd_lb_enable_timing")
+
+    def kernel_times(self) -> dict:
+        """Durations (ms) inside the last step: row pass storing history, row
+        pass accumulating the contour sums, column pass, LB collide-stream."""
+        out = np.empty(4)
+        self._ck(lib().epd_lb_kernel_times(self.h, _ptr(out)), "epd_lb_kernel_times")
+        return dict(zip(("prop_row_store", "prop_row_accumulate", "prop_col", "lb_collide_stream"), out.tolist()))
+
+    def save(self) -> bytes:
+        n = ctypes.c_size_t()
+        self._ck(lib().epd_lb_save(self.h, None, ctypes.byref(n)), "epd_lb_save")
+        buf = ctypes.create_string_buffer(n.value)
+        self._ck(lib().epd_lb_save(self.h, buf, ctypes.byref(n)), "epd_lb_save")
+        return buf.raw[: n.value]
+
+    def load(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        self._ck(lib().epd_lb_load(self.h, buf, len(blob)), "epd_lb_load")

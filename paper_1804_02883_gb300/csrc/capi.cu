@@ -1,0 +1,775 @@
+// capi.cu -- C ABI (include/epd_lb.h) and the engine around the kernels:
+// parameter validation, workspace layout, transform tables, CUDA-graph capture
+// of the time step, state access and checkpoints.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "engine.h"
+
+namespace epdlb {
+
+cudaError_t configure_prop_kernels();
+cudaError_t configure_epd_kernels();
+
+cudaError_t configure_kernels()
+{
+    static bool done = false;
+    static cudaError_t status = cudaSuccess;
+    if (done) return status;
+    status = configure_prop_kernels();
+    if (status == cudaSuccess) status = configure_epd_kernels();
+    done = true;
+    return status;
+}
+
+static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Carve (or size, with base == nullptr) the buffers of one group.
+size_t carve_group(Group &G, char *base, size_t off)
+{
+    const size_t n = (size_t)G.g.n, R = (size_t)G.g.nruns;
+    const size_t tb = G.prec == EPD_LB_MIXED_FP32 ? sizeof(float) : sizeof(double);
+    auto take = [&](size_t bytes) -> void * {
+        off = align_up(off);
+        void *p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    };
+    G.omega = (double *)take(R * 3 * n * sizeof(double));
+    G.omega_t = (double *)take(R * 3 * n * sizeof(double));
+    G.phi = (double *)take(R * 3 * n * sizeof(double));
+    G.phi_t = (double *)take(R * 3 * n * sizeof(double));
+    G.q = (double *)take(R * 2 * sizeof(double));
+    G.q_t = (double *)take(R * 2 * sizeof(double));
+    G.ia = (double *)take(R * n * sizeof(double));
+    G.ib = (double *)take(R * n * sizeof(double));
+    G.cz = (double2 *)take(R * 4 * n * sizeof(double2));
+    G.part = (double *)take(R * kMaxPart * sizeof(double));
+    G.f0_lat = (double *)take(R * sizeof(double));
+    G.stage = (double *)take(std::max<size_t>(9 * n, 2 * R + 16) * sizeof(double));
+    G.chain = take(R * n * 2 * tb);
+    G.hist = take(R * (size_t)(G.g.half_lo + 1) * n * 2 * tb);
+    G.efac = take(R * n * 2 * tb);
+    G.pop[0] = take(R * 9 * n * tb);
+    G.pop[1] = take(R * 9 * n * tb);
+    G.vel = take(R * n * 2 * tb);
+    G.force = take(R * n * 2 * tb);
+    G.twx = take((size_t)G.g.nx / 2 * 2 * tb);
+    G.twy = take((size_t)G.g.ny / 2 * 2 * tb);
+    G.kx = take((size_t)G.g.nx * tb);
+    G.ky = take((size_t)G.g.ny * tb);
+    G.twx_d = (double2 *)take((size_t)G.g.nx / 2 * sizeof(double2));
+    G.twy_d = (double2 *)take((size_t)G.g.ny / 2 * sizeof(double2));
+    return align_up(off);
+}
+
+// View of one run of a group (all per-run buffers offset, nruns = 1).
+static Group run_view(const Group &G, int r)
+{
+    Group V = G;
+    const size_t n = (size_t)G.g.n;
+    const size_t tb = G.prec == EPD_LB_MIXED_FP32 ? sizeof(float) : sizeof(double);
+    V.g.nruns = 1;
+    V.omega += (size_t)r * 3 * n;
+    V.omega_t += (size_t)r * 3 * n;
+    V.phi += (size_t)r * 3 * n;
+    V.phi_t += (size_t)r * 3 * n;
+    V.q += 2 * r;
+    V.q_t += 2 * r;
+    V.ia += (size_t)r * n;
+    V.ib += (size_t)r * n;
+    V.cz += (size_t)r * 4 * n;
+    V.part += (size_t)r * kMaxPart;
+    V.f0_lat += r;
+    V.chain = (char *)V.chain + (size_t)r * n * 2 * tb;
+    V.hist = (char *)V.hist + (size_t)r * (G.g.half_lo + 1) * n * 2 * tb;
+    V.efac = (char *)V.efac + (size_t)r * n * 2 * tb;
+    V.pop[0] = (char *)V.pop[0] + (size_t)r * 9 * n * tb;
+    V.pop[1] = (char *)V.pop[1] + (size_t)r * 9 * n * tb;
+    V.vel = (char *)V.vel + (size_t)r * n * 2 * tb;
+    V.force = (char *)V.force + (size_t)r * n * 2 * tb;
+    return V;
+}
+
+static double fstar_lattice(const epd_lb_params &p)
+{
+    const double tau = p.rg * p.rg / p.d_s;
+    const double r = p.dt / tau;
+    return (p.rg / p.dx) * r * r;
+}
+
+static void fill_geom(Group &G)
+{
+    const epd_lb_params &p = G.p;
+    GroupGeom &g = G.g;
+    g.nx = p.nx;
+    g.ny = p.ny;
+    g.logx = ilog2(p.nx);
+    g.logy = ilog2(p.ny);
+    g.ns = p.ns;
+    g.na = (int)std::lround(p.f_a * (double)p.ns);
+    g.half_lo = p.ns / 2;
+    g.half_hi = (p.ns + 1) / 2;
+    g.nruns = (int)G.run_ids.size();
+    g.n = (long long)p.nx * p.ny;
+    g.dx = p.dx;
+    g.dt = p.dt;
+    g.rg = p.rg;
+    g.nseg = p.n_seg;
+    g.phi_p = p.phi_p;
+    g.ds = 1.0 / (double)p.ns;
+    g.chi_ab = p.chi_ab;
+    g.chi_as = p.chi_as;
+    g.chi_bs = p.chi_bs;
+    g.kappa_h = p.kappa_h;
+    g.d_s = p.d_s;
+    g.d_p = p.d_p;
+    g.inv_beta_v = p.inv_beta_v;
+    g.gamma_s = p.gamma_s;
+    g.gamma_b = p.gamma_b;
+    g.gamma_g = p.gamma_g;
+    g.fstar = fstar_lattice(p);
+    g.vscale = p.dx / p.dt;
+}
+
+// Launch shapes: about 2048 points per CTA, column tiles at least 32 bytes wide.
+static void default_shapes(Group &G)
+{
+    const int nx = G.g.nx, ny = G.g.ny;
+    const bool f32 = G.prec == EPD_LB_MIXED_FP32;
+    G.sh.rows_prop = std::max(1, std::min(ny, 2048 / nx));
+    G.sh.cols_prop = std::min(nx, std::max(f32 ? 4 : 2, 2048 / ny));
+    G.sh.rows_epd = std::max(1, std::min(ny, 2048 / nx));
+    G.sh.cols_epd = std::min(nx, std::max(2, 2048 / ny));
+}
+
+// Twiddles exp(-2 pi i t / n), t < n/2, and Fourier factors
+// exp(-R_G^2 k^2 ds) / n of the propagator (Eq. (8)), on the host in FP64.
+template <typename T>
+static void host_tables(const Group &G, std::vector<T> &twx, std::vector<T> &twy, std::vector<T> &kx, std::vector<T> &ky,
+                        std::vector<double> &twxd, std::vector<double> &twyd)
+{
+    const double pi = 3.14159265358979323846;
+    auto tw = [&](int n, std::vector<T> &out, std::vector<double> &outd) {
+        out.resize(n);
+        outd.resize(n);
+        for (int t = 0; t < n / 2; ++t) {
+            const double a = 2.0 * pi * (double)t / (double)n;
+            outd[2 * t] = std::cos(a);
+            outd[2 * t + 1] = -std::sin(a);
+            out[2 * t] = (T)outd[2 * t];
+            out[2 * t + 1] = (T)outd[2 * t + 1];
+        }
+    };
+    tw(G.g.nx, twx, twxd);
+    tw(G.g.ny, twy, twyd);
+    auto kf = [&](int n, std::vector<T> &out) {
+        out.resize(n);
+        for (int m = 0; m < n; ++m) {
+            const int mm = m <= n / 2 ? m : m - n;
+            const double k = 2.0 * pi * (double)mm / ((double)n * G.g.dx);
+            out[m] = (T)(std::exp(-G.g.rg * G.g.rg * k * k * G.g.ds) / (double)n);
+        }
+    };
+    kf(G.g.nx, kx);
+    kf(G.g.ny, ky);
+}
+
+template <typename T>
+static cudaError_t upload_tables_t(Group &G, cudaStream_t s)
+{
+    std::vector<T> twx, twy, kx, ky;
+    std::vector<double> twxd, twyd;
+    host_tables<T>(G, twx, twy, kx, ky, twxd, twyd);
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(G.twx, twx.data(), twx.size() * sizeof(T), cudaMemcpyHostToDevice, s))) return e;
+    if ((e = cudaMemcpyAsync(G.twy, twy.data(), twy.size() * sizeof(T), cudaMemcpyHostToDevice, s))) return e;
+    if ((e = cudaMemcpyAsync(G.kx, kx.data(), kx.size() * sizeof(T), cudaMemcpyHostToDevice, s))) return e;
+    if ((e = cudaMemcpyAsync(G.ky, ky.data(), ky.size() * sizeof(T), cudaMemcpyHostToDevice, s))) return e;
+    if ((e = cudaMemcpyAsync(G.twx_d, twxd.data(), twxd.size() * sizeof(double), cudaMemcpyHostToDevice, s))) return e;
+    if ((e = cudaMemcpyAsync(G.twy_d, twyd.data(), twyd.size() * sizeof(double), cudaMemcpyHostToDevice, s))) return e;
+    std::vector<double> f0(G.g.nruns);
+    for (int r = 0; r < G.g.nruns; ++r) f0[r] = G.run_params[r].f0 * G.g.fstar;
+    if ((e = cudaMemcpyAsync(G.f0_lat, f0.data(), f0.size() * sizeof(double), cudaMemcpyHostToDevice, s))) return e;
+    return cudaStreamSynchronize(s);
+}
+
+static cudaError_t upload_tables_e(Group &G, cudaStream_t s)
+{
+    return G.prec == EPD_LB_MIXED_FP32 ? upload_tables_t<float>(G, s) : upload_tables_t<double>(G, s);
+}
+
+void upload_tables(Group &G, cudaStream_t s) { (void)upload_tables_e(G, s); }
+
+static bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+static std::string validate(const epd_lb_params &p)
+{
+    char buf[256];
+    if (!pow2(p.nx) || !pow2(p.ny) || p.nx < kMinN || p.ny < kMinN || p.nx > kMaxN || p.ny > kMaxN) {
+        std::snprintf(buf, sizeof buf, "nx=%d, ny=%d: each must be a power of two in [%d, %d]", p.nx, p.ny, kMinN, kMaxN);
+        return buf;
+    }
+    if (p.ns < 2 || p.ns > 512 || (p.ns & 1)) {
+        std::snprintf(buf, sizeof buf, "ns=%d: must be even and in [2, 512]", p.ns);
+        return buf;
+    }
+    if (p.precision != EPD_LB_PLAIN_FP64 && p.precision != EPD_LB_MIXED_FP32) return "precision must be 0 (PLAIN_FP64) or 1 (MIXED_FP32)";
+    if (!(p.dx > 0) || !(p.dt > 0) || !(p.rg > 0) || !(p.n_seg > 0) || !(p.d_s > 0) || !(p.d_p > 0))
+        return "dx, dt, rg, n_seg, d_s and d_p must be positive";
+    if (!(p.f_a >= 0 && p.f_a <= 1)) return "f_a must be in [0, 1]";
+    if (!(p.phi_p > 0 && p.phi_p < 1)) return "phi_p must be in (0, 1)";
+    if (!(std::fabs(p.gamma_s) < 1) || !(std::fabs(p.gamma_b) < 1) || !(std::fabs(p.gamma_g) < 1))
+        return "gamma_s, gamma_b and gamma_g must be in (-1, 1)";
+    if (!std::isfinite(p.f0) || !std::isfinite(p.noise_amp) || !std::isfinite(p.inv_beta_v)) return "f0, noise_amp, inv_beta_v must be finite";
+    return "";
+}
+
+// Peak of Eq. (24) in lattice units, f0 L_y^2 / (32 eta): refuse above Mach 0.3.
+static bool mach_ok(const epd_lb_params &p, double *vmax)
+{
+    const double eta = (1.0 / 6.0) * (1.0 + p.gamma_s) / (1.0 - p.gamma_s);
+    const double a = std::fabs(p.f0) * fstar_lattice(p);
+    *vmax = a * (double)p.ny * p.ny / (32.0 * eta);
+    return *vmax <= 0.3 * std::sqrt(1.0 / 3.0);
+}
+
+static bool same_group(const epd_lb_params &a, const epd_lb_params &b)
+{
+    return a.nx == b.nx && a.ny == b.ny && a.ns == b.ns && a.precision == b.precision && a.dx == b.dx && a.dt == b.dt &&
+           a.rg == b.rg && a.n_seg == b.n_seg && a.f_a == b.f_a && a.phi_p == b.phi_p && a.chi_ab == b.chi_ab &&
+           a.chi_as == b.chi_as && a.chi_bs == b.chi_bs && a.kappa_h == b.kappa_h && a.d_s == b.d_s && a.d_p == b.d_p &&
+           a.inv_beta_v == b.inv_beta_v && a.gamma_s == b.gamma_s && a.gamma_b == b.gamma_b && a.gamma_g == b.gamma_g;
+}
+
+static void form_groups(const epd_lb_params *p, int nruns, std::vector<Group> &groups, std::vector<std::pair<int, int>> &where)
+{
+    groups.clear();
+    where.assign(nruns, {-1, -1});
+    for (int r = 0; r < nruns; ++r) {
+        int gi = -1;
+        for (size_t k = 0; k < groups.size(); ++k)
+            if (same_group(groups[k].p, p[r])) { gi = (int)k; break; }
+        if (gi < 0) {
+            Group G = Group();
+            G.p = p[r];
+            G.prec = p[r].precision;
+            groups.push_back(G);
+            gi = (int)groups.size() - 1;
+        }
+        where[r] = {gi, (int)groups[gi].run_ids.size()};
+        groups[gi].run_ids.push_back(r);
+        groups[gi].run_params.push_back(p[r]);
+    }
+    for (auto &G : groups) {
+        fill_geom(G);
+        default_shapes(G);
+    }
+}
+
+} // namespace epdlb
+
+using namespace epdlb;
+
+struct epd_lb {
+    std::vector<Group> groups;
+    std::vector<std::pair<int, int>> where;  // run -> (group, member)
+    int nruns = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void *ws = nullptr;
+    bool own_ws = false;
+    int *err = nullptr;
+    double *obs = nullptr;
+    int parity = 0;
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    bool timing = false;
+    cudaEvent_t ev[7] = {};
+    std::string last_error;
+};
+
+static int fail(epd_lb *h, int code, const std::string &msg)
+{
+    if (h) h->last_error = msg;
+    return code;
+}
+
+static int cuda_fail(epd_lb *h, cudaError_t e, const char *where)
+{
+    return fail(h, EPD_LB_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                  \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, where); \
+    } while (0)
+
+extern "C" int epd_lb_workspace_bytes(const epd_lb_params *p, int32_t nruns, size_t *bytes)
+{
+    if (!p || nruns <= 0 || !bytes) return EPD_LB_EINVAL;
+    for (int r = 0; r < nruns; ++r)
+        if (!validate(p[r]).empty()) return EPD_LB_EINVAL;
+    std::vector<Group> groups;
+    std::vector<std::pair<int, int>> where;
+    form_groups(p, nruns, groups, where);
+    size_t off = 512;  // error word and observables
+    for (auto &G : groups) off = carve_group(G, nullptr, off);
+    *bytes = off;
+    return EPD_LB_OK;
+}
+
+// Record the whole time step of every group (App. C order) on stream s.
+static cudaError_t enqueue_step(epd_lb *h, int parity, cudaStream_t s)
+{
+    cudaError_t e;
+    for (size_t gi = 0; gi < h->groups.size(); ++gi) {
+        Group &G = h->groups[gi];
+        SolveProbe probe;
+        const bool timed = h->timing && gi == 0;
+        if (timed) {
+            for (int k = 0; k < 5; ++k) probe.ev[k] = h->ev[k];
+            probe.m_store = std::max(1, G.g.ns / 4);
+            probe.m_acc = std::min(G.g.ns, (3 * G.g.ns) / 4 + 1);
+        }
+        if ((e = launch_aux_convection(G, s))) return e;                      // omega -> omega~
+        if ((e = launch_solve(G, G.omega_t, G.phi_t, G.q_t, s))) return e;     // Phi~
+        if ((e = launch_diffusion(G, s))) return e;                           // omega(t+dt)
+        if ((e = launch_solve(G, G.omega, G.phi, G.q, s, timed ? &probe : nullptr))) return e;  // Phi(t+dt)
+        if ((e = launch_force(G, s))) return e;                               // polymer force
+        if (timed && (e = cudaEventRecordWithFlags(h->ev[5], s, cudaEventRecordExternal))) return e;
+        if ((e = launch_lb(G, parity, s))) return e;                          // collide-stream
+        if (timed && (e = cudaEventRecordWithFlags(h->ev[6], s, cudaEventRecordExternal))) return e;
+    }
+    return cudaSuccess;
+}
+
+static int build_graphs(epd_lb *h)
+{
+    for (int par = 0; par < 2; ++par) {
+        if (h->exec[par]) {
+            cudaGraphExecDestroy(h->exec[par]);
+            h->exec[par] = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+        cudaError_t e = enqueue_step(h, par, h->stream);
+        cudaError_t e2 = cudaStreamEndCapture(h->stream, &graph);
+        if (e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_fail(h, e, "capturing the time step");
+        }
+        CK(e2, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&h->exec[par], graph, 0);
+        cudaGraphDestroy(graph);
+        CK(e, "cudaGraphInstantiate");
+    }
+    return EPD_LB_OK;
+}
+
+extern "C" int epd_lb_init(const epd_lb_params *p, int32_t nruns, void *workspace, size_t workspace_bytes,
+                           void *cuda_stream, epd_lb **out)
+{
+    if (!out) return EPD_LB_EINVAL;
+    *out = nullptr;
+    epd_lb *h = new (std::nothrow) epd_lb();
+    if (!h) return EPD_LB_ENOMEM;
+    if (!p || nruns <= 0) {
+        delete h;
+        return EPD_LB_EINVAL;
+    }
+    for (int r = 0; r < nruns; ++r) {
+        std::string msg = validate(p[r]);
+        if (!msg.empty()) {
+            delete h;
+            return EPD_LB_EINVAL;
+        }
+        double vmax;
+        if (!mach_ok(p[r], &vmax)) {
+            delete h;
+            return EPD_LB_EUNSTABLE;
+        }
+    }
+    h->nruns = nruns;
+    form_groups(p, nruns, h->groups, h->where);
+    size_t need = 512;
+    for (auto &G : h->groups) need = carve_group(G, nullptr, need);
+    auto bail = [&](int code) {
+        epd_lb_destroy(h);
+        return code;
+    };
+    if (cudaError_t e = configure_kernels()) {
+        (void)e;
+        return bail(EPD_LB_ECUDA);
+    }
+    if (workspace) {
+        if (workspace_bytes < need || ((uintptr_t)workspace & 255)) return bail(EPD_LB_ENOMEM);
+        h->ws = workspace;
+    } else {
+        if (cudaMalloc(&h->ws, need) != cudaSuccess) {
+            h->ws = nullptr;
+            return bail(EPD_LB_ENOMEM);
+        }
+        h->own_ws = true;
+    }
+    if (cuda_stream) {
+        h->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(EPD_LB_ECUDA);
+        h->own_stream = true;
+    }
+    char *base = (char *)h->ws;
+    h->err = (int *)base;
+    h->obs = (double *)(base + 256);
+    size_t off = 512;
+    for (auto &G : h->groups) {
+        off = carve_group(G, base, off);
+        G.err = h->err;
+    }
+    if (cudaMemsetAsync(h->err, 0, sizeof(int), h->stream) != cudaSuccess) return bail(EPD_LB_ECUDA);
+    for (auto &G : h->groups) {
+        if (upload_tables_e(G, h->stream) != cudaSuccess) return bail(EPD_LB_ECUDA);
+        if (launch_init_state(G, h->stream) != cudaSuccess) return bail(EPD_LB_ECUDA);
+        if (launch_solve(G, G.omega, G.phi, G.q, h->stream) != cudaSuccess) return bail(EPD_LB_ECUDA);
+    }
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(EPD_LB_ECUDA);
+    h->parity = 0;
+    if (int rc = build_graphs(h)) return bail(rc);
+    *out = h;
+    return EPD_LB_OK;
+}
+
+extern "C" int epd_lb_step(epd_lb *h, int64_t nsteps)
+{
+    if (!h || nsteps < 0) return EPD_LB_EINVAL;
+    for (int64_t k = 0; k < nsteps; ++k) {
+        CK(cudaGraphLaunch(h->exec[h->parity], h->stream), "cudaGraphLaunch");
+        h->parity ^= 1;
+    }
+    return EPD_LB_OK;
+}
+
+extern "C" int epd_lb_sync(epd_lb *h)
+{
+    if (!h) return EPD_LB_EINVAL;
+    CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    int err = 0;
+    CK(cudaMemcpy(&err, h->err, sizeof(int), cudaMemcpyDeviceToHost), "reading the device error word");
+    if (err & 1) return fail(h, EPD_LB_ENONFINITE, "a single-chain solve produced Q <= 0 or a non-finite Q");
+    return EPD_LB_OK;
+}
+
+static int locate(epd_lb *h, int run, Group **G, int *m)
+{
+    if (!h || run < 0 || run >= h->nruns) return fail(h, EPD_LB_EINVAL, "run index out of range");
+    *G = &h->groups[h->where[run].first];
+    *m = h->where[run].second;
+    return EPD_LB_OK;
+}
+
+extern "C" int epd_lb_densities_dev(epd_lb *h, int32_t run, double *phi_dev, double *q_dev)
+{
+    Group *G;
+    int m;
+    if (int rc = locate(h, run, &G, &m)) return rc;
+    const size_t n = (size_t)G->g.n;
+    if (phi_dev) CK(cudaMemcpyAsync(phi_dev, G->phi + (size_t)m * 3 * n, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream), "copy phi");
+    if (q_dev) CK(cudaMemcpyAsync(q_dev, G->q + 2 * m, 2 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream), "copy q");
+    return EPD_LB_OK;
+}
+
+extern "C" int epd_lb_densities(epd_lb *h, int32_t run, double *phi, double *q)
+{
+    Group *G;
+    int m;
+    if (int rc = locate(h, run, &G, &m)) return rc;
+    const size_t n = (size_t)G->g.n;
+    if (phi) CK(cudaMemcpyAsync(phi, G->phi + (size_t)m * 3 * n, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy phi");
+    if (q) CK(cudaMemcpyAsync(q, G->q + 2 * m, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy q");
+    CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    return EPD_LB_OK;
+}
+
+extern "C" int epd_lb_velocity_dev(epd_lb *h, int32_t run, double *v_dev)
+{
+    Group *G;
+    int m;
+    if (int rc = locate(h, run, &G, &m)) return rc;
+    if (!v_dev) return fail(h, EPD_LB_EINVAL, "v_dev is NULL");
+    CK(launch_vel_to_f64(*G, m, v_dev, h->stream), "velocity conversion");
+    return EPD_LB_OK;
+}
+
+extern "C" int epd_lb_velocity(epd_lb *h, int32_t run, double *v)
+{
+    Group *G;
+    int m;
+    if (int rc = locate(h, run, &G, &m)) return rc;
+    if (!v) return fail(h, EPD_LB_EINVAL, "v is NULL");
+    const size_t n = (size_t)G->g.n;
+    CK(launch_vel_to_f64(*G, m, G->stage, h->stream), "velocity conversion");
+    CK(cudaMemcpyAsync(v, G->stage, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy velocity");
+    CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    return EPD_LB_OK;
+}
+
+extern "C" int epd_lb_get_state(epd_lb *h, int32_t run, double *omega, double *pop, double *vel)
+{
+    Group *G;
+    int m;
+    if (int rc = locate(h, run, &G, &m)) return rc;
+    const size_t n = (size_t)G->g.n;
+    if (omega) CK(cudaMemcpyAsync(omega, G->omega + (size_t)m * 3 * n, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy omega");
+    if (pop) {
+        CK(launch_gather_pre_collision(*G, m, h->parity, G->stage, h->stream), "gathering populations");
+        CK(cudaMemcpyAsync(pop, G->stage, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy populations");
+        CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    }
+    if (vel) {
+        CK(launch_vel_to_f64(*G, m, G->stage, h->stream), "velocity conversion");
+        CK(cudaMemcpyAsync(vel, G->stage, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy velocity");
+    }
+    CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    return EPD_LB_OK;
+}
+
+extern "C" int epd_lb_set_state(epd_lb *h, int32_t run, const double *omega, const double *pop, const double *vel)
+{
+    Group *G;
+    int m;
+    if (int rc = locate(h, run, &G, &m)) return rc;
+    const size_t n = (size_t)G->g.n;
+    if (omega)
+        CK(cudaMemcpyAsync(G->omega + (size_t)m * 3 * n, omega, 3 * n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy omega");
+    if (pop) {
+        CK(cudaMemcpyAsync(G->stage, pop, 9 * n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy populations");
+        CK(launch_scatter_pre_collision(*G, m, h->parity, G->stage, h->stream), "scattering populations");
+    }
+    if (vel) {
+        // the staging buffer is reused: order the velocity upload after the scatter
+        CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+        CK(cudaMemcpyAsync(G->stage, vel, 2 * n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy velocity");
+        CK(launch_vel_from_f64(*G, m, G->stage, h->stream), "velocity conversion");
+    }
+    CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    return EPD_LB_OK;
+}
+
+extern "C" int epd_lb_solve(epd_lb *h, int32_t run, const double *omega, double *phi, double *q)
+{
+    Group *G;
+    int m;
+    if (int rc = locate(h, run, &G, &m)) return rc;
+    if (!omega || !phi || !q) return fail(h, EPD_LB_EINVAL, "omega, phi and q are required");
+    const size_t n = (size_t)G->g.n;
+    Group V = run_view(*G, m);
+    // omega~ and Phi~ are scratch between steps
+    CK(cudaMemcpyAsync(V.omega_t, omega, 3 * n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy omega");
+    CK(launch_solve(V, V.omega_t, V.phi_t, V.q_t, h->stream), "solve");
+    CK(cudaMemcpyAsync(phi, V.phi_t, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy phi");
+    CK(cudaMemcpyAsync(q, V.q_t, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy q");
+    CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    return EPD_LB_OK;
+}
+
+extern "C" int epd_lb_observables(epd_lb *h, int32_t run, double *out)
+{
+    Group *G;
+    int m;
+    if (int rc = locate(h, run, &G, &m)) return rc;
+    if (!out) return fail(h, EPD_LB_EINVAL, "out is NULL");
+    CK(launch_observables(*G, m, h->parity, h->obs, h->stream), "observables");
+    CK(cudaMemcpyAsync(out, h->obs, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy observables");
+    CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    return EPD_LB_OK;
+}
+
+// Checkpoint format: magic, version, nruns, then per run its parameters and,
+// as FP64, omega (3n), the stored post-collision population deviations (9n,
+// the library's internal representation, copied exactly) and the velocity
+// (2n).
+static const uint64_t kMagic = 0x3130444C42445045ULL;  // "EPDLB01" little-endian
+
+extern "C" int epd_lb_save(epd_lb *h, void *buf, size_t *len)
+{
+    if (!h || !len) return EPD_LB_EINVAL;
+    size_t need = 3 * sizeof(uint64_t);
+    for (int r = 0; r < h->nruns; ++r) {
+        const Group &G = h->groups[h->where[r].first];
+        need += sizeof(epd_lb_params) + 14 * (size_t)G.g.n * sizeof(double);
+    }
+    if (!buf) {
+        *len = need;
+        return EPD_LB_OK;
+    }
+    if (*len < need) return fail(h, EPD_LB_ENOMEM, "checkpoint buffer too small");
+    char *c = (char *)buf;
+    uint64_t hdr[3] = {kMagic, 2, (uint64_t)h->nruns};
+    std::memcpy(c, hdr, sizeof hdr);
+    c += sizeof hdr;
+    for (int r = 0; r < h->nruns; ++r) {
+        Group &G = h->groups[h->where[r].first];
+        const int m = h->where[r].second;
+        const size_t n = (size_t)G.g.n;
+        std::memcpy(c, &G.run_params[m], sizeof(epd_lb_params));
+        c += sizeof(epd_lb_params);
+        double *om = (double *)c, *pop = om + 3 * n, *vel = pop + 9 * n;
+        if (int rc = epd_lb_get_state(h, r, om, nullptr, vel)) return rc;
+        CK(launch_pop_raw(G, m, h->parity, G.stage, nullptr, h->stream), "copying populations");
+        CK(cudaMemcpyAsync(pop, G.stage, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy populations");
+        CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+        c += 14 * n * sizeof(double);
+    }
+    *len = need;
+    return EPD_LB_OK;
+}
+
+extern "C" int epd_lb_load(epd_lb *h, const void *buf, size_t len)
+{
+    if (!h || !buf) return EPD_LB_EINVAL;
+    const char *c = (const char *)buf;
+    uint64_t hdr[3];
+    if (len < sizeof hdr) return fail(h, EPD_LB_EINVAL, "checkpoint truncated");
+    std::memcpy(hdr, c, sizeof hdr);
+    if (hdr[0] != kMagic || hdr[1] != 2 || hdr[2] != (uint64_t)h->nruns) return fail(h, EPD_LB_EINVAL, "checkpoint does not match this handle");
+    c += sizeof hdr;
+    size_t left = len - sizeof hdr;
+    for (int r = 0; r < h->nruns; ++r) {
+        Group &G = h->groups[h->where[r].first];
+        const int m = h->where[r].second;
+        const size_t n = (size_t)G.g.n;
+        const size_t need = sizeof(epd_lb_params) + 14 * n * sizeof(double);
+        if (left < need) return fail(h, EPD_LB_EINVAL, "checkpoint truncated");
+        epd_lb_params p;
+        std::memcpy(&p, c, sizeof p);
+        if (std::memcmp(&p, &G.run_params[m], sizeof p) != 0)
+            return fail(h, EPD_LB_EINVAL, "checkpoint parameters differ from this handle's");
+        c += sizeof p;
+        const double *om = (const double *)c, *pop = om + 3 * n, *vel = pop + 9 * n;
+        if (int rc = epd_lb_set_state(h, r, om, nullptr, vel)) return rc;
+        CK(cudaMemcpyAsync(G.stage, pop, 9 * n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy populations");
+        CK(launch_pop_raw(G, m, h->parity, nullptr, G.stage, h->stream), "copying populations");
+        Group V = run_view(G, m);
+        CK(launch_solve(V, V.omega, V.phi, V.q, h->stream), "solve");
+        CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+        c += 14 * n * sizeof(double);
+        left -= need;
+    }
+    return EPD_LB_OK;
+}
+
+extern "C" int epd_lb_enable_timing(epd_lb *h, int32_t on)
+{
+    if (!h) return EPD_LB_EINVAL;
+    CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    if (on && !h->ev[0])
+        for (int k = 0; k < 7; ++k) CK(cudaEventCreate(&h->ev[k]), "cudaEventCreate");
+    h->timing = on != 0;
+    return build_graphs(h);
+}
+
+extern "C" int epd_lb_kernel_times(epd_lb *h, double *ms)
+{
+    if (!h || !ms) return EPD_LB_EINVAL;
+    if (!h->timing) return fail(h, EPD_LB_EINVAL, "timing is not enabled");
+    CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    const int pairs[4][2] = {{0, 1}, {3, 4}, {2, 3}, {5, 6}};
+    for (int k = 0; k < 4; ++k) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, h->ev[pairs[k][0]], h->ev[pairs[k][1]]), "cudaEventElapsedTime");
+        ms[k] = (double)t;
+    }
+    return EPD_LB_OK;
+}
+
+extern "C" const char *epd_lb_last_error(const epd_lb *h)
+{
+    if (!h) return "null handle";
+    return h->last_error.c_str();
+}
+
+extern "C" void epd_lb_destroy(epd_lb *h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (int k = 0; k < 2; ++k)
+        if (h->exec[k]) cudaGraphExecDestroy(h->exec[k]);
+    for (int k = 0; k < 7; ++k)
+        if (h->ev[k]) cudaEventDestroy(h->ev[k]);
+    if (h->own_ws && h->ws) cudaFree(h->ws);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+// ---------------------------------------------------------------------------
+// Stateless single-chain solve on device pointers.
+// ---------------------------------------------------------------------------
+
+// Only the buffers a solve touches: chain, history, factors, contour sums,
+// partials and tables.
+static size_t carve_solve(Group &G, char *base)
+{
+    const size_t n = (size_t)G.g.n;
+    const size_t tb = G.prec == EPD_LB_MIXED_FP32 ? sizeof(float) : sizeof(double);
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> void * {
+        off = align_up(off);
+        void *p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    };
+    G.err = (int *)take(256);
+    G.ia = (double *)take(n * sizeof(double));
+    G.ib = (double *)take(n * sizeof(double));
+    G.part = (double *)take(kMaxPart * sizeof(double));
+    G.f0_lat = (double *)take(sizeof(double));
+    G.chain = take(n * 2 * tb);
+    G.hist = take((size_t)(G.g.half_lo + 1) * n * 2 * tb);
+    G.efac = take(n * 2 * tb);
+    G.twx = take((size_t)G.g.nx / 2 * 2 * tb);
+    G.twy = take((size_t)G.g.ny / 2 * 2 * tb);
+    G.kx = take((size_t)G.g.nx * tb);
+    G.ky = take((size_t)G.g.ny * tb);
+    G.twx_d = (double2 *)take((size_t)G.g.nx / 2 * sizeof(double2));
+    G.twy_d = (double2 *)take((size_t)G.g.ny / 2 * sizeof(double2));
+    return align_up(off);
+}
+
+static bool solve_group(const epd_lb_params *p, Group &G)
+{
+    if (!p || !validate(*p).empty()) return false;
+    std::vector<Group> groups;
+    std::vector<std::pair<int, int>> where;
+    form_groups(p, 1, groups, where);
+    G = groups[0];
+    return true;
+}
+
+extern "C" int epd_prop_solve_workspace_bytes(const epd_lb_params *p, size_t *bytes)
+{
+    Group G;
+    if (!bytes || !solve_group(p, G)) return EPD_LB_EINVAL;
+    *bytes = carve_solve(G, nullptr);
+    return EPD_LB_OK;
+}
+
+extern "C" int epd_prop_solve(const epd_lb_params *p, const double *omega_dev, double *phi_dev, double *q_dev,
+                              void *workspace_dev, size_t workspace_bytes, void *cuda_stream)
+{
+    Group G;
+    if (!solve_group(p, G) || !omega_dev || !phi_dev || !q_dev || !workspace_dev) return EPD_LB_EINVAL;
+    if (workspace_bytes < carve_solve(G, nullptr) || ((uintptr_t)workspace_dev & 255)) return EPD_LB_ENOMEM;
+    if (configure_kernels() != cudaSuccess) return EPD_LB_ECUDA;
+    carve_solve(G, (char *)workspace_dev);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (cudaMemsetAsync(G.err, 0, sizeof(int), s) != cudaSuccess) return EPD_LB_ECUDA;
+    if (upload_tables_e(G, s) != cudaSuccess) return EPD_LB_ECUDA;
+    if (launch_solve(G, omega_dev, phi_dev, q_dev, s) != cudaSuccess) return EPD_LB_ECUDA;
+    return EPD_LB_OK;
+}

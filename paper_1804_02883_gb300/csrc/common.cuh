@@ -1,0 +1,126 @@
+// common.cuh -- shared device types and the in-shared-memory FFT used by the
+// propagator, EPD and force passes of the hybrid LB/EPD step (arXiv:1804.02883).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace epdlb {
+
+// ---------------------------------------------------------------------------
+// complex pairs
+// ---------------------------------------------------------------------------
+template <typename T> struct V2Of;
+template <> struct V2Of<float> { using type = float2; };
+template <> struct V2Of<double> { using type = double2; };
+template <typename T> using V2 = typename V2Of<T>::type;
+
+template <typename T> __host__ __device__ __forceinline__ V2<T> mk(T x, T y) { V2<T> r; r.x = x; r.y = y; return r; }
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { a.x += b.x; a.y += b.y; return a; }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b)
+{
+    V r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+template <typename V, typename S> __device__ __forceinline__ V cscale(V a, S s) { a.x *= s; a.y *= s; return a; }
+
+// ---------------------------------------------------------------------------
+// Batched radix-2 Stockham FFT in shared memory.
+//
+// The batch holds B sequences of N = 2^logN complex points; point k of
+// sequence b sits at x[b*sb + k*sn].  Each stage reads the pair (r, r + N/2)
+// of every sequence and writes the autosorted pair (2r - (r mod stride),
+// +stride), so no bit reversal is needed; the result is in natural order and
+// unnormalised.  tw holds exp(-2 pi i t / N), t < N/2; INVERSE conjugates it.
+// BATCH_FAST maps consecutive threads to consecutive sequences (for the
+// column layout, sn > 1), otherwise to consecutive points (row layout).
+// Every thread of the block must call it; it ends with a __syncthreads and
+// returns the buffer that holds the result (x or y).
+// ---------------------------------------------------------------------------
+template <typename T, bool INVERSE, bool BATCH_FAST>
+__device__ __forceinline__ V2<T> *fft_smem(V2<T> *x, V2<T> *y, int logN, int logB, int sb, int sn,
+                                           const V2<T> *tw)
+{
+    const int half = 1 << (logN - 1);
+    const int total = half << logB;
+    for (int s = 0; s < logN; ++s) {
+        const int stride = 1 << s;
+        for (int t = threadIdx.x; t < total; t += blockDim.x) {
+            int b, r;
+            if (BATCH_FAST) {
+                b = t & ((1 << logB) - 1);
+                r = t >> logB;
+            } else {
+                b = t >> (logN - 1);
+                r = t & (half - 1);
+            }
+            const int q = r & (stride - 1);
+            const int base = b * sb;
+            V2<T> a = x[base + r * sn];
+            V2<T> c = x[base + (r + half) * sn];
+            V2<T> w = tw[r - q];
+            if (INVERSE) w.y = -w.y;
+            const int o = base + (2 * r - q) * sn;
+            y[o] = cadd(a, c);
+            y[o + stride * sn] = cmul(csub(a, c), w);
+        }
+        __syncthreads();
+        V2<T> *tmp = x;
+        x = y;
+        y = tmp;
+    }
+    return x;
+}
+
+// Block-wide sum of one double per thread (blockDim.x a multiple of 32, at
+// most 1024).  Fixed order: deterministic.  Result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double *scratch32)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) scratch32[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        r = lane < nw ? scratch32[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    }
+    return r;
+}
+
+// Sum of cnt partial sums, identical in every block that calls it (the
+// warp-0 lanes take fixed strided slices).  Result valid in thread 0 of warp 0
+// and broadcast through the returned value of every thread after the call.
+__device__ __forceinline__ double sum_partials(const double *part, int cnt, int stride_el, double *bcast)
+{
+    if (threadIdx.x < 32) {
+        double v = 0.0;
+        for (int i = threadIdx.x; i < cnt; i += 32) v += part[(size_t)i * stride_el];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) *bcast = v;
+    }
+    __syncthreads();
+    double r = *bcast;
+    __syncthreads();
+    return r;
+}
+
+__host__ __device__ __forceinline__ int ilog2(int v)
+{
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+// Signed index of FFT bin m on an axis of n points.
+__device__ __forceinline__ int signed_bin(int m, int n) { return m <= (n >> 1) ? m : m - n; }
+
+constexpr int kThreads = 256;
+
+} // namespace epdlb

@@ -1,0 +1,109 @@
+// engine.h -- host-side description of a batch of runs ("group") and the
+// launchers of the kernels that make up one hybrid LB/EPD time step.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/epd_lb.h"
+
+namespace epdlb {
+
+// Parameters every kernel of a group needs, by value.
+struct GroupGeom {
+    int nx, ny, logx, logy;
+    int ns, na;          // contour steps, A-block intervals round(f_a ns)
+    int half_lo, half_hi;  // nodes 0..half_lo are stored; nodes >= half_hi accumulate
+    int nruns;
+    long long n;         // sites per run
+    double dx, dt, rg, nseg, phi_p, ds;
+    double chi_ab, chi_as, chi_bs, kappa_h, d_s, d_p, inv_beta_v;
+    double gamma_s, gamma_b, gamma_g;
+    double fstar;        // f* in lattice units
+    double vscale;       // lattice velocity -> R_G/tau
+};
+
+// Launch shapes of the transform passes (chosen at init, see tune_shapes).
+struct Shapes {
+    int rows_prop, cols_prop;  // rows per CTA of the propagator row pass, columns per CTA of its column pass
+    int rows_epd, cols_epd;    // the same for the FP64 EPD/force passes
+};
+
+// One batch of runs with identical grid, contour and model parameters.
+struct Group {
+    epd_lb_params p;   // parameters of the first run (f0 and seed may differ per run)
+    GroupGeom g;
+    Shapes sh;
+    int prec;          // EPD_LB_PLAIN_FP64 or EPD_LB_MIXED_FP32
+    std::vector<int> run_ids;  // handle-level run index of each member
+    std::vector<epd_lb_params> run_params;
+
+    // FP64 fields, [run][species][n]
+    double *omega, *omega_t, *phi, *phi_t;
+    double *q, *q_t;   // [run][2]
+    double *ia, *ib;   // contour sums, [run][n]
+    double2 *cz;       // 4 complex FP64 scratch planes per run: [run][4][n]
+    double *part;      // reduction partials, [run][kMaxPart]
+    double *f0_lat;    // [run]
+    double *stage;     // host<->device staging, 9 n doubles (one run)
+    // bulk-precision buffers (float or double, by prec)
+    void *chain;       // packed (g, g') of the running contour step, [run][n] complex
+    void *hist;        // (g, g') at nodes 0..half_lo, [run][half_lo+1][n] complex
+    void *efac;        // (E_A, E_B), [run][n] complex
+    void *pop[2];      // post-collision populations, [run][9][n]
+    void *vel;         // velocity of the last collision, [run][n] complex (x, y)
+    void *force;       // polymer force (lattice units), [run][n] complex (x, y)
+    // transform tables
+    void *twx, *twy, *kx, *ky;     // bulk precision: twiddles, exp(-rg^2 k^2 ds)/N
+    double2 *twx_d, *twy_d;        // FP64 twiddles for the EPD/force passes
+    int *err;                      // device error word (shared by the handle)
+};
+
+constexpr int kMaxPart = 4096;     // partial sums per run and reduction
+
+// Workspace layout: compute (dry run with base == nullptr) or carve.
+size_t carve_group(Group &G, char *base, size_t off);
+
+// Tables and initial state.
+void upload_tables(Group &G, cudaStream_t s);
+cudaError_t launch_init_state(Group &G, cudaStream_t s);
+
+// Optional CUDA events recorded around single launches of a solve (for timing
+// inside a captured step): ev[0], ev[1] bracket the row pass of node m_store;
+// ev[2], ev[3] the column pass before node m_acc and ev[3], ev[4] its row pass.
+struct SolveProbe {
+    cudaEvent_t ev[5];
+    int m_store, m_acc;
+};
+
+// Single-chain solve, Eqs. (6)-(11): omega (3n per run, FP64) -> phi (3n),
+// q (2 per run).  All runs of the group.
+cudaError_t launch_solve(Group &G, const double *omega, double *phi, double *q, cudaStream_t s,
+                         const SolveProbe *probe = nullptr);
+
+// EPD parts of the step.
+cudaError_t launch_aux_convection(Group &G, cudaStream_t s);   // omega, vel -> omega_t
+cudaError_t launch_diffusion(Group &G, cudaStream_t s);        // phi_t, omega_t -> omega
+cudaError_t launch_force(Group &G, cudaStream_t s);            // phi, phi_t -> force
+cudaError_t launch_lb(Group &G, int parity, cudaStream_t s);   // pop[parity] -> pop[1-parity], vel
+
+// State access helpers (one run).
+cudaError_t launch_gather_pre_collision(Group &G, int run, int parity, double *dst, cudaStream_t s);
+cudaError_t launch_scatter_pre_collision(Group &G, int run, int parity, const double *src, cudaStream_t s);
+cudaError_t launch_vel_to_f64(Group &G, int run, double *dst, cudaStream_t s);
+cudaError_t launch_vel_from_f64(Group &G, int run, const double *src, cudaStream_t s);
+cudaError_t launch_observables(Group &G, int run, int parity, double *out_dev, cudaStream_t s);
+// Exact copy of a run's stored populations to (dst) or from (src) FP64.
+cudaError_t launch_pop_raw(Group &G, int run, int parity, double *dst, const double *src, cudaStream_t s);
+
+// Kernel attributes (dynamic shared memory limits), once per process.
+cudaError_t configure_kernels();
+
+// Smallest/largest supported sizes.
+constexpr int kMinN = 8, kMaxN = 2048;
+
+} // namespace epdlb

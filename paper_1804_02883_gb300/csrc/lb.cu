@@ -1,0 +1,413 @@
+// lb.cu -- D2Q9 multi-relaxation-time Lattice Boltzmann of the hybrid LB/EPD
+// step (Sec. 2, Eqs. (12), (14)-(16); Sec. 4, Eq. (23) of arXiv:1804.02883),
+// the initial state (Sec. 3 noise, Sec. 4 flow of Eq. (24)) and state access.
+//
+// One fused pull pass per step: each thread gathers the nine post-collision
+// populations streamed into its site, collides them with the polymer force
+// plus the reverse-Poiseuille body force, and writes its own post-collision
+// populations (SoA planes [run][i][site]) and velocity.  Populations are kept
+// as deviations d_i = n_i - w_i from the rest state so that FP32 storage
+// resolves small flows; every moment below is formed from the deviations.
+//
+// Collision (Dunweg-Ladd mode form): u = (j + f/2)/rho; mass and momentum are
+// conserved except j* = j + f; the stress relaxes about rho u u (deviation form
+// of Pi_eq = rho c_s^2 I + rho u u) with its traceless part scaled by gamma_s
+// and its trace by gamma_b; the force adds Sigma of Eq. (15) in d = 2; the
+// remaining (ghost) part of the populations is scaled by gamma_g.
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+#include "engine.h"
+
+namespace epdlb {
+
+__constant__ int c_cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+__constant__ int c_cy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+
+template <typename T> struct LbK {
+    int nx, ny, logx;
+    long long n;
+    const T *pin;
+    T *pout;
+    const V2<T> *force;
+    V2<T> *vel;
+    const double *f0_lat;
+    T gs, gb, gg;
+};
+
+__host__ __device__ __forceinline__ double lb_weight(int i) { return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0); }
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) lb_collide_stream(LbK<T> k)
+{
+    const int run = blockIdx.y;
+    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= k.n) return;
+    const int x = (int)(site & (k.nx - 1)), y = (int)(site >> k.logx);
+    const int xm = (x - 1) & (k.nx - 1), xp = (x + 1) & (k.nx - 1);
+    const int ym = (y - 1) & (k.ny - 1), yp = (y + 1) & (k.ny - 1);
+    const long long n = k.n;
+    const T *src = k.pin + (size_t)run * 9 * n;
+    // pull: population i arrives from site - c_i
+    const long long r0 = (long long)y * k.nx, rm = (long long)ym * k.nx, rp = (long long)yp * k.nx;
+    const T d0 = src[0 * n + r0 + x];
+    const T d1 = src[1 * n + r0 + xm];
+    const T d2 = src[2 * n + rm + x];
+    const T d3 = src[3 * n + r0 + xp];
+    const T d4 = src[4 * n + rp + x];
+    const T d5 = src[5 * n + rm + xm];
+    const T d6 = src[6 * n + rm + xp];
+    const T d7 = src[7 * n + rp + xp];
+    const T d8 = src[8 * n + rp + xm];
+
+    const T drho = d0 + d1 + d2 + d3 + d4 + d5 + d6 + d7 + d8;
+    const T rho = (T)1 + drho;
+    const T jx = (d1 - d3) + (d5 - d6) + (d8 - d7);
+    const T jy = (d2 - d4) + (d5 + d6) - (d7 + d8);
+    const T sxx = d1 + d3 + d5 + d6 + d7 + d8;
+    const T syy = d2 + d4 + d5 + d6 + d7 + d8;
+    const T sxy = (d5 + d7) - (d6 + d8);
+    const T third = (T)(1.0 / 3.0);
+    // M = Pi - rho c_s^2 I from the deviations
+    const T mxx = sxx - third * drho, myy = syy - third * drho, mxy = sxy;
+
+    const V2<T> fp = k.force[(size_t)run * n + site];
+    const T fpx = (T)((y < (k.ny >> 1)) ? -k.f0_lat[run] : k.f0_lat[run]);
+    const T fx = fp.x + fpx, fy = fp.y;
+    const T inv_rho = (T)1 / rho;
+    const T ux = (jx + (T)0.5 * fx) * inv_rho, uy = (jy + (T)0.5 * fy) * inv_rho;
+    k.vel[(size_t)run * n + site] = mk<T>(ux, uy);
+
+    // non-equilibrium stress about rho u u, relaxed
+    const T exx = rho * ux * ux, eyy = rho * uy * uy, exy = rho * ux * uy;
+    const T nxx = mxx - exx, nyy = myy - eyy, nxy = mxy - exy;
+    const T htr = (T)0.5 * (nxx + nyy);
+    const T rxx = k.gs * (nxx - htr) + k.gb * htr;
+    const T ryy = k.gs * (nyy - htr) + k.gb * htr;
+    const T rxy = k.gs * nxy;
+    // Sigma of Eq. (15) with the d = 2 constants
+    const T uf = ux * fx + uy * fy;
+    const T hs = (T)0.5 * ((T)1 + k.gs), hb = (T)0.5 * ((T)1 + k.gb);
+    const T qxx = hs * ((T)2 * ux * fx - uf) + hb * uf;
+    const T qyy = hs * ((T)2 * uy * fy - uf) + hb * uf;
+    const T qxy = hs * (ux * fy + uy * fx);
+    // post-collision moments
+    const T pxx = exx + rxx + qxx, pyy = eyy + ryy + qyy, pxy = exy + rxy + qxy;
+    const T jxs = jx + fx, jys = jy + fy;
+
+    // d_i* = w_i [drho + 3 j*.c_i + 4.5 M*:Q_i] + gamma_g (d_i - w_i [drho + 3 j.c_i + 4.5 M:Q_i])
+    const T dd[9] = {d0, d1, d2, d3, d4, d5, d6, d7, d8};
+    T *dst = k.pout + (size_t)run * 9 * n + site;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int cx = (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+        const int cy = (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+        const T w = (T)lb_weight(i);
+        const T qx = (T)(cx * cx) - third, qy = (T)(cy * cy) - third, qc = (T)(cx * cy);
+        const T post = drho + (T)3 * (jxs * cx + jys * cy) + (T)4.5 * (pxx * qx + pyy * qy + (T)2 * pxy * qc);
+        T v = w * post;
+        if (k.gg != (T)0) {
+            const T pre = drho + (T)3 * (jx * cx + jy * cy) + (T)4.5 * (mxx * qx + myy * qy + (T)2 * mxy * qc);
+            v += k.gg * (dd[i] - w * pre);
+        }
+        dst[(size_t)i * n] = v;
+    }
+}
+
+template <typename T>
+static cudaError_t lb_t(Group &G, int parity, cudaStream_t s)
+{
+    LbK<T> k;
+    k.nx = G.g.nx;
+    k.ny = G.g.ny;
+    k.logx = G.g.logx;
+    k.n = G.g.n;
+    k.pin = reinterpret_cast<const T *>(G.pop[parity]);
+    k.pout = reinterpret_cast<T *>(G.pop[1 - parity]);
+    k.force = reinterpret_cast<const V2<T> *>(G.force);
+    k.vel = reinterpret_cast<V2<T> *>(G.vel);
+    k.f0_lat = G.f0_lat;
+    k.gs = (T)G.g.gamma_s;
+    k.gb = (T)G.g.gamma_b;
+    k.gg = (T)G.g.gamma_g;
+    const dim3 grid((unsigned)((G.g.n + kThreads - 1) / kThreads), G.g.nruns);
+    lb_collide_stream<T><<<grid, kThreads, 0, s>>>(k);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lb(Group &G, int parity, cudaStream_t s)
+{
+    if (G.prec == EPD_LB_MIXED_FP32) return lb_t<float>(G, parity, s);
+    return lb_t<double>(G, parity, s);
+}
+
+// ---------------------------------------------------------------------------
+// Initial state
+// ---------------------------------------------------------------------------
+
+// splitmix64 (Steele, Lea and Flood, OOPSLA 2014): add the golden gamma, then
+// the variant-13 finaliser.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z)
+{
+    z += 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// Uniform value in [-1, 1) for (seed, counter): top 53 bits of
+// splitmix64(seed ^ splitmix64(counter)).
+__device__ __forceinline__ double uniform_pm1(unsigned long long seed, unsigned long long ctr)
+{
+    const unsigned long long h = splitmix64(seed ^ splitmix64(ctr));
+    return 2.0 * ((double)(h >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+}
+
+struct InitK {
+    GroupGeom g;
+    double *omega;
+    const unsigned long long *seeds;
+    const double *noise;
+    const double *f0_lat;
+    void *post;
+    void *vel;
+    int bulk_double;
+};
+
+// Velocity of the steady reverse-Poiseuille flow on nodes at Y = y + 1/2:
+// Eq. (24) plus f_P(y) (1 - 1/(8 eta)) (the scheme's discrete correction).
+__device__ __forceinline__ double steady_profile(const GroupGeom &g, double a, int y)
+{
+    const double eta = (1.0 / 6.0) * (1.0 + g.gamma_s) / (1.0 - g.gamma_s);
+    const double ly = (double)g.ny, d = (double)y + 0.5 - 0.5 * ly;
+    const double fp = (y < g.ny / 2) ? -a : a;
+    return -(a / (2.0 * eta)) * d * (fabs(d) - 0.5 * ly) + fp * (1.0 - 1.0 / (8.0 * eta));
+}
+
+__global__ void __launch_bounds__(kThreads) init_state(InitK k)
+{
+    const int run = blockIdx.y;
+    const long long n = k.g.n;
+    const unsigned long long seed = k.seeds[run];
+    const double amp = k.noise[run], a = k.f0_lat[run];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i & (k.g.nx - 1)), y = (int)(i >> k.g.logx);
+        for (int sp = 0; sp < 3; ++sp) {
+            const unsigned long long ctr = ((unsigned long long)sp * k.g.ny + y) * (unsigned long long)k.g.nx + x;
+            k.omega[((size_t)run * 3 + sp) * n + i] = amp * uniform_pm1(seed, ctr);
+        }
+        // post-collision populations at t = -1, so that the first pull sees the
+        // pre-collision equilibrium with j = v(y) - f_P(y)/2 at every site
+        for (int q = 0; q < 9; ++q) {
+            const int yy = (y + c_cy[q]) & (k.g.ny - 1);
+            const double v = steady_profile(k.g, a, yy);
+            const double fp = (yy < k.g.ny / 2) ? -a : a;
+            const double jx = v - 0.5 * fp;
+            const double cj = c_cx[q] * jx;
+            const double d = lb_weight(q) * (3.0 * cj + 4.5 * cj * cj - 1.5 * jx * jx);
+            const size_t o = ((size_t)run * 9 + q) * n + i;
+            if (k.bulk_double) reinterpret_cast<double *>(k.post)[o] = d;
+            else reinterpret_cast<float *>(k.post)[o] = (float)d;
+        }
+        const double v = steady_profile(k.g, a, y);
+        if (k.bulk_double) reinterpret_cast<double2 *>(k.vel)[(size_t)run * n + i] = make_double2(v, 0.0);
+        else reinterpret_cast<float2 *>(k.vel)[(size_t)run * n + i] = make_float2((float)v, 0.0f);
+    }
+}
+
+cudaError_t launch_init_state(Group &G, cudaStream_t s)
+{
+    // per-run seeds and noise amplitudes staged through the staging buffer
+    const int nr = G.g.nruns;
+    unsigned long long *seeds = reinterpret_cast<unsigned long long *>(G.stage);
+    double *noise = G.stage + nr;
+    std::vector<unsigned long long> hs(nr);
+    std::vector<double> hn(nr);
+    for (int r = 0; r < nr; ++r) {
+        hs[r] = G.run_params[r].seed;
+        hn[r] = G.run_params[r].noise_amp;
+    }
+    cudaError_t e = cudaMemcpyAsync(seeds, hs.data(), nr * sizeof(unsigned long long), cudaMemcpyHostToDevice, s);
+    if (e) return e;
+    e = cudaMemcpyAsync(noise, hn.data(), nr * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e) return e;
+    InitK k;
+    k.g = G.g;
+    k.omega = G.omega;
+    k.seeds = seeds;
+    k.noise = noise;
+    k.f0_lat = G.f0_lat;
+    k.post = G.pop[0];
+    k.vel = G.vel;
+    k.bulk_double = G.prec == EPD_LB_PLAIN_FP64;
+    long long b = (G.g.n + kThreads - 1) / kThreads;
+    if (b > 1024) b = 1024;
+    init_state<<<dim3((unsigned)b, nr), kThreads, 0, s>>>(k);
+    e = cudaGetLastError();
+    if (e) return e;
+    // the host vectors must outlive the copies
+    return cudaStreamSynchronize(s);
+}
+
+// ---------------------------------------------------------------------------
+// State access
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void gather_pre(const T *post, double *dst, int nx, int ny, int logx, long long n)
+{
+    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int q = blockIdx.y;
+    if (site >= n) return;
+    const int x = (int)(site & (nx - 1)), y = (int)(site >> logx);
+    const int sx = (x - c_cx[q]) & (nx - 1), sy = (y - c_cy[q]) & (ny - 1);
+    dst[(size_t)q * n + site] = (double)post[(size_t)q * n + (long long)sy * nx + sx] + lb_weight(q);
+}
+
+template <typename T>
+__global__ void scatter_pre(T *post, const double *src, int nx, int ny, int logx, long long n)
+{
+    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int q = blockIdx.y;
+    if (site >= n) return;
+    const int x = (int)(site & (nx - 1)), y = (int)(site >> logx);
+    const int sx = (x + c_cx[q]) & (nx - 1), sy = (y + c_cy[q]) & (ny - 1);
+    post[(size_t)q * n + site] = (T)(src[(size_t)q * n + (long long)sy * nx + sx] - lb_weight(q));
+}
+
+cudaError_t launch_gather_pre_collision(Group &G, int run, int parity, double *dst, cudaStream_t s)
+{
+    const dim3 grid((unsigned)((G.g.n + kThreads - 1) / kThreads), 9);
+    if (G.prec == EPD_LB_MIXED_FP32)
+        gather_pre<float><<<grid, kThreads, 0, s>>>(reinterpret_cast<const float *>(G.pop[parity]) + (size_t)run * 9 * G.g.n, dst,
+                                                    G.g.nx, G.g.ny, G.g.logx, G.g.n);
+    else
+        gather_pre<double><<<grid, kThreads, 0, s>>>(reinterpret_cast<const double *>(G.pop[parity]) + (size_t)run * 9 * G.g.n, dst,
+                                                     G.g.nx, G.g.ny, G.g.logx, G.g.n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_pre_collision(Group &G, int run, int parity, const double *src, cudaStream_t s)
+{
+    const dim3 grid((unsigned)((G.g.n + kThreads - 1) / kThreads), 9);
+    if (G.prec == EPD_LB_MIXED_FP32)
+        scatter_pre<float><<<grid, kThreads, 0, s>>>(reinterpret_cast<float *>(G.pop[parity]) + (size_t)run * 9 * G.g.n, src,
+                                                     G.g.nx, G.g.ny, G.g.logx, G.g.n);
+    else
+        scatter_pre<double><<<grid, kThreads, 0, s>>>(reinterpret_cast<double *>(G.pop[parity]) + (size_t)run * 9 * G.g.n, src,
+                                                      G.g.nx, G.g.ny, G.g.logx, G.g.n);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void vel_convert(const V2<T> *vin, double *vout, V2<T> *vback, const double *vsrc, long long n)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (vout) {
+        const V2<T> v = vin[i];
+        vout[i] = (double)v.x;
+        vout[n + i] = (double)v.y;
+    } else {
+        vback[i] = mk<T>((T)vsrc[i], (T)vsrc[n + i]);
+    }
+}
+
+cudaError_t launch_vel_to_f64(Group &G, int run, double *dst, cudaStream_t s)
+{
+    const unsigned b = (unsigned)((G.g.n + kThreads - 1) / kThreads);
+    if (G.prec == EPD_LB_MIXED_FP32)
+        vel_convert<float><<<b, kThreads, 0, s>>>(reinterpret_cast<const float2 *>(G.vel) + (size_t)run * G.g.n, dst, nullptr, nullptr, G.g.n);
+    else
+        vel_convert<double><<<b, kThreads, 0, s>>>(reinterpret_cast<const double2 *>(G.vel) + (size_t)run * G.g.n, dst, nullptr, nullptr, G.g.n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vel_from_f64(Group &G, int run, const double *src, cudaStream_t s)
+{
+    const unsigned b = (unsigned)((G.g.n + kThreads - 1) / kThreads);
+    if (G.prec == EPD_LB_MIXED_FP32)
+        vel_convert<float><<<b, kThreads, 0, s>>>(nullptr, nullptr, reinterpret_cast<float2 *>(G.vel) + (size_t)run * G.g.n, src, G.g.n);
+    else
+        vel_convert<double><<<b, kThreads, 0, s>>>(nullptr, nullptr, reinterpret_cast<double2 *>(G.vel) + (size_t)run * G.g.n, src, G.g.n);
+    return cudaGetLastError();
+}
+
+// Raw copy of a run's stored populations (post-collision deviations from the
+// rest weights, [i][site]) to or from FP64, for exact checkpoints.
+template <typename T>
+__global__ void pop_raw(T *pop, double *dst, const double *src, long long cnt)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cnt) return;
+    if (dst) dst[i] = (double)pop[i];
+    else pop[i] = (T)src[i];
+}
+
+cudaError_t launch_pop_raw(Group &G, int run, int parity, double *dst, const double *src, cudaStream_t s)
+{
+    const long long cnt = 9 * G.g.n;
+    const unsigned b = (unsigned)((cnt + kThreads - 1) / kThreads);
+    if (G.prec == EPD_LB_MIXED_FP32)
+        pop_raw<float><<<b, kThreads, 0, s>>>(reinterpret_cast<float *>(G.pop[parity]) + (size_t)run * cnt, dst, src, cnt);
+    else
+        pop_raw<double><<<b, kThreads, 0, s>>>(reinterpret_cast<double *>(G.pop[parity]) + (size_t)run * cnt, dst, src, cnt);
+    return cudaGetLastError();
+}
+
+// Observables of one run, one block, fixed order: <Phi_A>, <Phi_B>, <Phi_S>,
+// sigma (Eq. (21)), LB mass / sites, max |u|, Q_P, Q_S.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) observables(const double *phi, const T *post, const V2<T> *vel, const double *q,
+                                                    double phi_p, long long n, double *out)
+{
+    __shared__ double red[32];
+    double sa = 0, sb = 0, ss = 0, sg = 0, sm = 0, vmax = 0;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+        const double a = phi[i], b = phi[n + i];
+        sa += a;
+        sb += b;
+        ss += phi[2 * n + i];
+        sg += fabs(a + b - phi_p);
+        double m = 0;
+        for (int qq = 0; qq < 9; ++qq) m += (double)post[(size_t)qq * n + i];
+        sm += m;
+        const V2<T> v = vel[i];
+        const double vv = sqrt((double)v.x * v.x + (double)v.y * v.y);
+        vmax = vv > vmax ? vv : vmax;
+    }
+    const double inv = 1.0 / (double)n;
+    double r;
+    r = block_sum(sa, red); if (threadIdx.x == 0) out[0] = r * inv;
+    r = block_sum(sb, red); if (threadIdx.x == 0) out[1] = r * inv;
+    r = block_sum(ss, red); if (threadIdx.x == 0) out[2] = r * inv;
+    r = block_sum(sg, red); if (threadIdx.x == 0) out[3] = r * inv;
+    r = block_sum(sm, red); if (threadIdx.x == 0) out[4] = 1.0 + r * inv;
+    // max reduction
+    for (int o = 16; o > 0; o >>= 1) vmax = fmax(vmax, __shfl_down_sync(0xffffffffu, vmax, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = vmax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+        out[5] = m;
+        out[6] = q[0];
+        out[7] = q[1];
+    }
+}
+
+cudaError_t launch_observables(Group &G, int run, int parity, double *out_dev, cudaStream_t s)
+{
+    const long long n = G.g.n;
+    if (G.prec == EPD_LB_MIXED_FP32)
+        observables<float><<<1, kThreads, 0, s>>>(G.phi + (size_t)run * 3 * n, reinterpret_cast<const float *>(G.pop[parity]) + (size_t)run * 9 * n,
+                                                  reinterpret_cast<const float2 *>(G.vel) + (size_t)run * n, G.q + 2 * run, G.g.phi_p, n, out_dev);
+    else
+        observables<double><<<1, kThreads, 0, s>>>(G.phi + (size_t)run * 3 * n, reinterpret_cast<const double *>(G.pop[parity]) + (size_t)run * 9 * n,
+                                                   reinterpret_cast<const double2 *>(G.vel) + (size_t)run * n, G.q + 2 * run, G.g.phi_p, n, out_dev);
+    return cudaGetLastError();
+}
+
+} // namespace epdlb

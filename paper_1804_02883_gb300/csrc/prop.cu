@@ -1,0 +1,274 @@
+// prop.cu -- single-chain solve of the hybrid LB/EPD step (Sec. 2, Eqs. (6)-(11)
+// of arXiv:1804.02883) on sm_103a.
+//
+// Both propagators advance together: the forward propagator g (from the A end,
+// Eq. (6)) and the backward propagator g' (from the B end, Eq. (7)) are real, so
+// they travel as the real and imaginary parts of one complex field z = g + i g'.
+// The Fourier factor exp(-R_G^2 |k|^2 ds) of the split step, Eq. (8), is
+// separable, exp(-R_G^2 kx^2 ds) exp(-R_G^2 ky^2 ds), and maps real fields to
+// real fields, so one contour step is
+//   column pass : z <- IFFT_y[ Ky * FFT_y[ z ] ]              (all columns)
+//   row pass    : h <- IFFT_x[ Kx * FFT_x[ z ] ]              (all rows)
+//                 z_{j+1} = E(s_{j+1}) h  (g and g' each with its own node field),
+//                 store or consume the contour history,
+//                 z <- E(s_{j+1}) z_{j+1} (first half of the next step)
+// with E = exp(-N w ds / 2).  Only nodes 0..floor(N_s/2) are stored: while the
+// chains run through the second half, node m of g meets node N_s - m of g' from
+// the history (and vice versa), and the trapezoid sums of Eqs. (9)-(10) are
+// accumulated in FP64 on the fly.
+#include <cmath>
+
+#include "common.cuh"
+#include "engine.h"
+
+namespace epdlb {
+
+template <typename T> struct PropK {
+    GroupGeom g;
+    V2<T> *chain;
+    V2<T> *hist;
+    const V2<T> *efac;
+    double *ia, *ib, *part;
+    const V2<T> *twx, *twy;
+    const T *kx, *ky;
+    int rows, logc;
+};
+
+// Trapezoid weights on [0, s_{N_A}] (block A) and [s_{N_A}, 1] (block B).
+__device__ __forceinline__ double weight_a(int j, int na, double ds)
+{
+    if (na == 0 || j > na) return 0.0;
+    return (j == 0 || j == na) ? 0.5 * ds : ds;
+}
+__device__ __forceinline__ double weight_b(int j, int na, int ns, double ds)
+{
+    if (na == ns || j < na) return 0.0;
+    return (j == na || j == ns) ? 0.5 * ds : ds;
+}
+
+// Node j of g carries w_A iff j < N_A; node j of g' carries the field of node ns - j.
+template <typename T> __device__ __forceinline__ T fac_g(V2<T> e, int j, int na) { return j < na ? e.x : e.y; }
+template <typename T> __device__ __forceinline__ T fac_gp(V2<T> e, int j, int ns, int na) { return (ns - j) < na ? e.x : e.y; }
+
+template <typename T> __device__ __forceinline__ T exp_t(T v);
+template <> __device__ __forceinline__ float exp_t<float>(float v) { return expf(v); }
+template <> __device__ __forceinline__ double exp_t<double>(double v) { return exp(v); }
+
+// Boltzmann factors E_{A,B} = exp(-N w_{A,B} ds / 2) in the bulk precision;
+// exp(-w_S) into the S slot of phi_out and its block sums for Q_S.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) prop_prep(GroupGeom g, const double *omega, V2<T> *efac, double *phi_out, double *part)
+{
+    __shared__ double red[32];
+    const int run = blockIdx.y;
+    const long long n = g.n;
+    const double *wa = omega + (size_t)run * 3 * n, *wb = wa + n, *ws = wb + n;
+    double *es = phi_out + (size_t)run * 3 * n + 2 * n;
+    const double c = -0.5 * g.nseg * g.ds;
+    double acc = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        efac[(size_t)run * n + i] = mk<T>(exp_t<T>((T)(c * wa[i])), exp_t<T>((T)(c * wb[i])));
+        const double e = exp(-ws[i]);
+        es[i] = e;
+        acc += e;
+    }
+    const double s = block_sum(acc, red);
+    if (threadIdx.x == 0) part[(size_t)run * kMaxPart + kMaxPart / 2 + blockIdx.x] = s;
+}
+
+// Node 0: g = g' = 1 stored; chain <- E(s_0) z_0.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) prop_start(PropK<T> k)
+{
+    const int run = blockIdx.y;
+    const long long n = k.g.n;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const V2<T> e = k.efac[(size_t)run * n + i];
+        k.hist[(size_t)run * (k.g.half_lo + 1) * n + i] = mk<T>((T)1, (T)1);
+        k.chain[(size_t)run * n + i] = mk<T>(fac_g<T>(e, 0, k.g.na), fac_gp<T>(e, 0, k.g.ns, k.g.na));
+    }
+}
+
+// Column pass: Ty = IFFT_y Ky FFT_y on a tile of 2^logc adjacent columns.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) prop_col(PropK<T> k)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ny = k.g.ny, nx = k.g.nx, logy = k.g.logy, logc = k.logc, C = 1 << logc;
+    const int tile = ny << logc;
+    V2<T> *a = reinterpret_cast<V2<T> *>(smem_raw);
+    V2<T> *b = a + tile;
+    V2<T> *tw = b + tile;
+    T *ky = reinterpret_cast<T *>(tw + ny / 2);
+    const int run = blockIdx.y, x0 = blockIdx.x << logc;
+    V2<T> *data = k.chain + (size_t)run * k.g.n;
+    for (int i = threadIdx.x; i < tile; i += blockDim.x) a[i] = data[(size_t)(i >> logc) * nx + x0 + (i & (C - 1))];
+    for (int i = threadIdx.x; i < ny / 2; i += blockDim.x) tw[i] = k.twy[i];
+    for (int i = threadIdx.x; i < ny; i += blockDim.x) ky[i] = k.ky[i];
+    __syncthreads();
+    V2<T> *r = fft_smem<T, false, true>(a, b, logy, logc, 1, C, tw);
+    V2<T> *o = (r == a) ? b : a;
+    for (int i = threadIdx.x; i < tile; i += blockDim.x) r[i] = cscale(r[i], ky[i >> logc]);
+    __syncthreads();
+    r = fft_smem<T, true, true>(r, o, logy, logc, 1, C, tw);
+    for (int i = threadIdx.x; i < tile; i += blockDim.x) data[(size_t)(i >> logc) * nx + x0 + (i & (C - 1))] = r[i];
+}
+
+// Row pass producing contour node m (1 <= m <= ns): Tx, node factors, history
+// store / contour accumulation, Q_P partial sums at m = ns, next half step.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) prop_row(PropK<T> k, int m)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[32];
+    const int nx = k.g.nx, logx = k.g.logx, rows = k.rows;
+    const int tile = rows * nx;
+    V2<T> *a = reinterpret_cast<V2<T> *>(smem_raw);
+    V2<T> *b = a + tile;
+    V2<T> *tw = b + tile;
+    T *kx = reinterpret_cast<T *>(tw + nx / 2);
+    const int run = blockIdx.y;
+    const long long n = k.g.n;
+    const long long base = (long long)blockIdx.x * tile;
+    V2<T> *data = k.chain + (size_t)run * n + base;
+    for (int i = threadIdx.x; i < tile; i += blockDim.x) a[i] = data[i];
+    for (int i = threadIdx.x; i < nx / 2; i += blockDim.x) tw[i] = k.twx[i];
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) kx[i] = k.kx[i];
+    __syncthreads();
+    const int logb = ilog2(rows);
+    V2<T> *r = fft_smem<T, false, false>(a, b, logx, logb, nx, 1, tw);
+    V2<T> *o = (r == a) ? b : a;
+    for (int i = threadIdx.x; i < tile; i += blockDim.x) r[i] = cscale(r[i], kx[i & (nx - 1)]);
+    __syncthreads();
+    r = fft_smem<T, true, false>(r, o, logx, logb, nx, 1, tw);
+
+    const int ns = k.g.ns, na = k.g.na, hlo = k.g.half_lo, hhi = k.g.half_hi;
+    const double ds = k.g.ds;
+    const V2<T> *efac = k.efac + (size_t)run * n + base;
+    V2<T> *hist = k.hist + (size_t)run * (hlo + 1) * n + base;
+    double *ia = k.ia + (size_t)run * n + base, *ib = k.ib + (size_t)run * n + base;
+    double qsum = 0.0;
+    for (int i = threadIdx.x; i < tile; i += blockDim.x) {
+        const V2<T> e = efac[i];
+        const T eg = fac_g<T>(e, m, na), egp = fac_gp<T>(e, m, ns, na);
+        const V2<T> h = r[i];
+        const V2<T> z = mk<T>(eg * h.x, egp * h.y);
+        if (m <= hlo) hist[(size_t)m * n + i] = z;
+        if (m >= hhi) {
+            const int s2 = ns - m;
+            const V2<T> hv = (s2 == m) ? z : hist[(size_t)s2 * n + i];
+            const double t1 = (double)z.x * (double)hv.y;  // g(s_m) g'(1 - s_m)
+            double va = weight_a(m, na, ds) * t1, vb = weight_b(m, na, ns, ds) * t1;
+            if (s2 != m) {
+                const double t2 = (double)hv.x * (double)z.y;  // g(s_{ns-m}) g'(s_m)
+                va += weight_a(s2, na, ds) * t2;
+                vb += weight_b(s2, na, ns, ds) * t2;
+            }
+            if (m == hhi) { ia[i] = va; ib[i] = vb; }
+            else { ia[i] += va; ib[i] += vb; }
+        }
+        if (m == ns) qsum += (double)z.x;
+        else data[i] = mk<T>(eg * z.x, egp * z.y);
+    }
+    if (m == ns) {
+        const double s = block_sum(qsum, red);
+        if (threadIdx.x == 0) k.part[(size_t)run * kMaxPart + blockIdx.x] = s;
+    }
+}
+
+// Normalisation, Eqs. (9)-(11) with Q as spatial means.
+__global__ void __launch_bounds__(kThreads) prop_finalize(GroupGeom g, int nrow_blocks, int nprep_blocks, const double *ia,
+                                                      const double *ib, const double *part, double *phi, double *q,
+                                                      int *err)
+{
+    __shared__ double bc;
+    const int run = blockIdx.y;
+    const long long n = g.n;
+    const double *pr = part + (size_t)run * kMaxPart;
+    const double qp = sum_partials(pr, nrow_blocks, 1, &bc) / (double)n;
+    const double qs = sum_partials(pr + kMaxPart / 2, nprep_blocks, 1, &bc) / (double)n;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        q[2 * run] = qp;
+        q[2 * run + 1] = qs;
+        if (!(qp > 0.0) || !(qs > 0.0) || !isfinite(qp) || !isfinite(qs)) atomicOr(err, 1);
+    }
+    const double cp = g.phi_p / qp, cs = (1.0 - g.phi_p) / qs;
+    double *pa = phi + (size_t)run * 3 * n, *pb = pa + n, *ps = pb + n;
+    const double *ja = ia + (size_t)run * n, *jb = ib + (size_t)run * n;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        pa[i] = cp * ja[i];
+        pb[i] = cp * jb[i];
+        ps[i] = cs * ps[i];
+    }
+}
+
+static int grid_for(long long n)
+{
+    long long b = (n + kThreads - 1) / kThreads;
+    if (b > 1024) b = 1024;
+    return (int)b;
+}
+
+template <typename T>
+static size_t col_smem(const Group &G) { return (size_t)2 * (G.g.ny * G.sh.cols_prop) * sizeof(V2<T>) + (G.g.ny / 2) * sizeof(V2<T>) + G.g.ny * sizeof(T); }
+template <typename T>
+static size_t row_smem(const Group &G) { return (size_t)2 * (G.sh.rows_prop * G.g.nx) * sizeof(V2<T>) + (G.g.nx / 2) * sizeof(V2<T>) + G.g.nx * sizeof(T); }
+
+template <typename T>
+static cudaError_t solve_t(Group &G, const double *omega, double *phi, double *q, cudaStream_t s, const SolveProbe *probe)
+{
+    const GroupGeom &g = G.g;
+    PropK<T> k;
+    k.g = g;
+    k.chain = reinterpret_cast<V2<T> *>(G.chain);
+    k.hist = reinterpret_cast<V2<T> *>(G.hist);
+    k.efac = reinterpret_cast<const V2<T> *>(G.efac);
+    k.ia = G.ia;
+    k.ib = G.ib;
+    k.part = G.part;
+    k.twx = reinterpret_cast<const V2<T> *>(G.twx);
+    k.twy = reinterpret_cast<const V2<T> *>(G.twy);
+    k.kx = reinterpret_cast<const T *>(G.kx);
+    k.ky = reinterpret_cast<const T *>(G.ky);
+    k.rows = G.sh.rows_prop;
+    k.logc = ilog2(G.sh.cols_prop);
+
+    const int pg = grid_for(g.n);
+    prop_prep<T><<<dim3(pg, g.nruns), kThreads, 0, s>>>(g, omega, reinterpret_cast<V2<T> *>(G.efac), phi, G.part);
+    prop_start<T><<<dim3(pg, g.nruns), kThreads, 0, s>>>(k);
+    const dim3 gc(g.nx / G.sh.cols_prop, g.nruns), gr(g.ny / G.sh.rows_prop, g.nruns);
+    const size_t sc = col_smem<T>(G), sr = row_smem<T>(G);
+    for (int m = 1; m <= g.ns; ++m) {
+        const bool pa = probe && m == probe->m_acc, ps = probe && m == probe->m_store;
+        if (pa) cudaEventRecordWithFlags(probe->ev[2], s, cudaEventRecordExternal);
+        prop_col<T><<<gc, kThreads, sc, s>>>(k);
+        if (pa) cudaEventRecordWithFlags(probe->ev[3], s, cudaEventRecordExternal);
+        if (ps) cudaEventRecordWithFlags(probe->ev[0], s, cudaEventRecordExternal);
+        prop_row<T><<<gr, kThreads, sr, s>>>(k, m);
+        if (ps) cudaEventRecordWithFlags(probe->ev[1], s, cudaEventRecordExternal);
+        if (pa) cudaEventRecordWithFlags(probe->ev[4], s, cudaEventRecordExternal);
+    }
+    prop_finalize<<<dim3(pg, g.nruns), kThreads, 0, s>>>(g, gr.x, pg, G.ia, G.ib, G.part, phi, q, G.err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solve(Group &G, const double *omega, double *phi, double *q, cudaStream_t s, const SolveProbe *probe)
+{
+    if (G.prec == EPD_LB_MIXED_FP32) return solve_t<float>(G, omega, phi, q, s, probe);
+    return solve_t<double>(G, omega, phi, q, s, probe);
+}
+
+cudaError_t configure_prop_kernels()
+{
+    cudaError_t e = cudaSuccess;
+    const int lim = 200 * 1024;
+    e = cudaFuncSetAttribute(prop_col<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (e) return e;
+    e = cudaFuncSetAttribute(prop_row<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (e) return e;
+    e = cudaFuncSetAttribute(prop_col<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (e) return e;
+    return cudaFuncSetAttribute(prop_row<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+}
+
+} // namespace epdlb

@@ -1,0 +1,198 @@
+"""GPU coupled EPD/LB step against the FP64 oracle: initial state, single
+steps from arbitrary states, multi-step runs, the full-size batch that the
+benchmark times, invariants, checkpoints and error handling."""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1804_02883_gb300 as P
+from paper_1804_02883_gb300 import workloads as W
+from helpers import fluct_err, oracle_params, rel_err, vel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build(oracle_lib):
+    P.lib()
+
+
+def oracle_state_from(r, omega, pop, vel):
+    p = oracle_params(r)
+    phi, q = O.solve(p, omega)
+    return p, O.State(omega.copy(), pop.copy(), vel.copy(), phi, q, np.zeros((2, r.ny, r.nx)))
+
+
+@pytest.mark.parametrize("prec", [P.PLAIN_FP64, P.MIXED_FP32])
+def test_initial_state_matches_oracle(prec):
+    r = W.with_(W.plain_small(), nx=32, ny=16, ns=8, precision=prec, f0=200.0, seed=77)
+    h = P.EpdLb([r])
+    om, pop, vel = h.get_state(0)
+    oom, opop, ovel = O.init(oracle_params(r))
+    assert np.array_equal(om, oom)  # same counter-based generator, same FP64 ops
+    tol = 1e-15 if prec == P.PLAIN_FP64 else 1e-7
+    assert np.abs(pop - opop).max() < tol
+    assert np.abs(vel - ovel).max() < tol * max(1e-30, np.abs(ovel).max()) + 1e-20
+    phi, q = h.densities(0)
+    ophi, oq = O.solve(oracle_params(r), oom)
+    assert rel_err(phi, ophi) < (1e-10 if prec == P.PLAIN_FP64 else 2e-5)
+    h.close()
+
+
+@pytest.mark.parametrize("ny,nx,ns", [(16, 32, 8), (64, 32, 12), (8, 128, 6)])
+def test_single_step_from_random_state_fp64(ny, nx, ns):
+    r = P.RunParams(nx=nx, ny=ny, ns=ns, precision=P.PLAIN_FP64, f_a=0.5, phi_p=0.2, f0=10.0)
+    omega = W.random_omega(ny, nx, seed=5, amp=0.05)
+    pop = W.random_populations(ny, nx, seed=6)
+    vel = W.random_velocity(ny, nx, seed=7, amp=0.02)
+    h = P.EpdLb([r])
+    h.set_state(0, omega, pop, vel)
+    h.step(1)
+    h.sync()
+    p, st = oracle_state_from(r, omega, pop, vel)
+    O.step(p, st)
+    gom, gpop, gvel = h.get_state(0)
+    gphi, gq = h.densities(0)
+    assert fluct_err(gom, st.omega) < 1e-10
+    assert rel_err(gphi, st.phi) < 1e-10
+    assert rel_err(gq, st.q) < 1e-12
+    assert rel_err(gvel, st.vel) < 1e-10
+    assert np.abs(gpop - st.pop).max() < 1e-14
+    h.close()
+
+
+def test_single_step_mixed_precision():
+    ny, nx, ns = 32, 64, 16
+    r = P.RunParams(nx=nx, ny=ny, ns=ns, precision=P.MIXED_FP32, f_a=0.5, phi_p=0.2, f0=10.0)
+    omega = W.random_omega(ny, nx, seed=15, amp=0.05)
+    pop = W.random_populations(ny, nx, seed=16)
+    vel = W.random_velocity(ny, nx, seed=17, amp=0.02)
+    h = P.EpdLb([r])
+    h.set_state(0, omega, pop, vel)
+    h.step(1)
+    p, st = oracle_state_from(r, omega, pop, vel)
+    O.step(p, st)
+    gom, gpop, gvel = h.get_state(0)
+    gphi, _ = h.densities(0)
+    assert fluct_err(gom, st.omega) < 2e-6
+    assert rel_err(gphi, st.phi) < 2e-6
+    assert rel_err(gvel, st.vel) < 2e-3  # force from a difference of two FP32 solves
+    assert np.abs(gpop - st.pop).max() < 1e-7
+    h.close()
+
+
+def test_multi_step_from_init_fp64():
+    # the small FP64 configuration (64 x 64, N_s = 32) for 20 steps
+    r = W.plain_small()
+    h = P.EpdLb([r])
+    p = oracle_params(r)
+    st = O.initial_state(p)
+    for k in range(4):
+        h.step(5)
+        O.step(p, st, 5)
+        gphi, gq = h.densities(0)
+        gom, gpop, gvel = h.get_state(0)
+        assert rel_err(gphi, st.phi) < 1e-10, k
+        assert fluct_err(gphi[0] + gphi[1], st.phi[0] + st.phi[1]) < 1e-8, k
+        assert fluct_err(gom, st.omega) < 1e-9, k
+        assert vel_err(gvel, st.vel, 1e-9) < 1, k
+    h.close()
+
+
+def test_full_size_batch_first_run_matches_oracle():
+    # The launch configuration the benchmark times: four 256 x 512 runs,
+    # N_s = 64, mixed precision.  One step from a random state of run 0
+    # against one oracle step; the other runs by invariants.
+    runs = W.channel_256x512(P.MIXED_FP32)
+    h = P.EpdLb(runs)
+    r = runs[2]
+    omega = W.random_omega(r.ny, r.nx, seed=21, amp=0.02)
+    pop = W.random_populations(r.ny, r.nx, seed=22, amp=1e-4)
+    vel = W.random_velocity(r.ny, r.nx, seed=23, amp=1e-3)
+    h.set_state(2, omega, pop, vel)
+    h.step(1)
+    p, st = oracle_state_from(r, omega, pop, vel)
+    O.step(p, st)
+    gphi, gq = h.densities(2)
+    gom, gpop, gvel = h.get_state(2)
+    assert rel_err(gphi, st.phi) < 2e-6
+    assert fluct_err(gom, st.omega) < 2e-6
+    # the force is (1/beta v) dPhi^D / (D dt) with dPhi^D ~ 2e-3 a difference
+    # of two FP32 solves (error ~1e-7 each): ~1e-4 relative, see design notes
+    assert rel_err(gvel, st.vel) < 2e-3
+    for k in (0, 1, 3):
+        ob = h.observables(k)
+        assert abs((ob["mean_phi_a"] + ob["mean_phi_b"]) / runs[k].phi_p - 1) < 1e-6
+        assert abs(ob["lb_mass"] - 1) < 1e-6
+    h.close()
+
+
+def test_batch_equals_single_runs():
+    runs = [W.with_(W.plain_small(), nx=32, ny=32, ns=8, seed=s, f0=f) for s, f in ((1, 0.0), (2, 20.0), (3, 50.0))]
+    hb = P.EpdLb(runs)
+    hb.step(3)
+    for k, r in enumerate(runs):
+        hs = P.EpdLb([r])
+        hs.step(3)
+        a, _ = hb.densities(k)
+        b, _ = hs.densities(0)
+        assert np.array_equal(a, b)
+        hs.close()
+    hb.close()
+
+
+def test_uneven_batch_groups_match_single_runs():
+    runs = [P.RunParams(nx=32, ny=16, ns=8, precision=P.MIXED_FP32, seed=1),
+            P.RunParams(nx=16, ny=32, ns=12, precision=P.MIXED_FP32, seed=2),
+            P.RunParams(nx=32, ny=16, ns=8, precision=P.MIXED_FP32, seed=3, f0=100.0)]
+    hb = P.EpdLb(runs)
+    hb.step(4)
+    for k, r in enumerate(runs):
+        hs = P.EpdLb([r])
+        hs.step(4)
+        assert np.array_equal(hb.densities(k)[0], hs.densities(0)[0])
+        hs.close()
+    hb.close()
+
+
+def test_invariants_over_many_steps_mixed():
+    r = W.with_(W.plain_small(), precision=P.MIXED_FP32, f0=10.0)
+    h = P.EpdLb([r])
+    h.step(200)
+    h.sync()
+    ob = h.observables(0)
+    assert abs((ob["mean_phi_a"] + ob["mean_phi_b"]) / r.phi_p - 1) < 1e-6
+    assert abs(ob["mean_phi_s"] / (1 - r.phi_p) - 1) < 1e-12
+    assert abs(ob["lb_mass"] - 1) < 1e-6
+    assert np.isfinite(ob["sigma"]) and ob["q_p"] > 0
+    h.close()
+
+
+def test_checkpoint_resume_is_bitwise():
+    r = W.with_(W.plain_small(), nx=32, ny=32, ns=8, f0=50.0)
+    a = P.EpdLb([r])
+    a.step(3)
+    blob = a.save()
+    a.step(4)
+    b = P.EpdLb([r])
+    b.load(blob)
+    b.step(4)
+    assert np.array_equal(a.densities(0)[0], b.densities(0)[0])
+    assert np.array_equal(a.velocity(0), b.velocity(0))
+    a.close()
+    b.close()
+
+
+def test_supersonic_poiseuille_refused():
+    r = W.with_(W.plain_small(), f0=1e9)
+    with pytest.raises(P.EpdLbError) as ei:
+        P.EpdLb([r])
+    assert ei.value.code == -5
+
+
+def test_decoupled_run_keeps_fluid_at_rest():
+    r = W.with_(W.plain_small(), nx=32, ny=32, ns=8, f0=0.0, inv_beta_v=0.0, noise_amp=1e-2)
+    h = P.EpdLb([r])
+    h.step(5)
+    assert np.all(h.velocity(0) == 0)
+    h.close()
