@@ -46,7 +46,9 @@ enum {
     EPD_LB_ENONFINITE = -4,  /* non-finite value or Q <= 0 detected on device */
     EPD_LB_EUNSTABLE = -5,   /* Mach-number pre-flight refused the run       */
     EPD_LB_ETIMEOUT = -6,    /* a bounded device wait gave up                */
-    EPD_LB_ENOTCONV = -7     /* reserved: iterative inversion did not converge */
+    EPD_LB_ENOTCONV = -7,    /* reserved: iterative inversion did not converge */
+    EPD_LB_ETOOLARGE = -8    /* problem needs more than the fixed scratch of
+                                epd_prop_solve_noalloc                        */
 };
 
 enum {
@@ -183,6 +185,45 @@ void epd_lb_destroy(epd_lb *h);
 int epd_prop_solve_workspace_bytes(const epd_lb_params *p, size_t *bytes);
 int epd_prop_solve(const epd_lb_params *p, const double *omega_dev, double *phi_dev, double *q_dev,
                    void *workspace_dev, size_t workspace_bytes, void *cuda_stream);
+
+/*
+ * Allocation-free variant of epd_prop_solve (the paper has no counterpart;
+ * this is a service for callers).
+ *
+ * Some callers cannot allocate device memory at the moment they need a
+ * solve: code running while another part of the program captures a CUDA
+ * graph (cudaMalloc and cudaFree are not allowed then), plug-ins whose host
+ * framework owns every byte of the device through its own pool, and
+ * real-time loops that must not pay for, or be serialised by, cudaMalloc /
+ * cudaFree.  This entry point takes the same inputs and outputs as
+ * epd_prop_solve (device pointers, caller-owned) but no workspace: its
+ * scratch (propagator history, contour sums, transform tables, partial sums)
+ * lives in one fixed array of EPD_PROP_SOLVE_NOALLOC_MAX_BYTES in the
+ * library's device image.  Every GPU that loads the library holds that array
+ * until the process exits.  The call makes no cudaMalloc, cudaFree or other
+ * allocating call, on the device or through any library.
+ *
+ * Limits and behaviour:
+ *  - The scratch needed is about nx*ny*(16 + (ns/2 + 3)*2*b) + 40 KiB bytes,
+ *    b = 4 (EPD_LB_MIXED_FP32) or 8 (EPD_LB_PLAIN_FP64): e.g. 128 x 128 with
+ *    ns = 64 fits in either precision, 256 x 512 does not.  A problem that
+ *    does not fit is rejected with EPD_LB_ETOOLARGE before any work.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress, which may load the library's device code) with
+ *    that device current; make that first call before any stream capture
+ *    starts.  Later calls reuse the address.
+ *  - All calls on one device share the array and it keeps the contents of
+ *    the last call; each call re-initialises what it reads.  Two calls that
+ *    can overlap on the GPU (different streams without ordering between
+ *    them, or different host threads) race on the scratch and give wrong
+ *    results: order them on one stream or serialise them.
+ *  - Asynchronous on cuda_stream (NULL: the legacy default stream).  Returns
+ *    EPD_LB_EINVAL for bad parameters or NULL pointers, EPD_LB_ECUDA if a
+ *    CUDA call fails.
+ */
+#define EPD_PROP_SOLVE_NOALLOC_MAX_BYTES (16u << 20)
+int epd_prop_solve_noalloc(const epd_lb_params *p, const double *omega_dev, double *phi_dev, double *q_dev,
+                           void *cuda_stream);
 
 #ifdef __cplusplus
 }

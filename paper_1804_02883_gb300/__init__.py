@@ -14,6 +14,7 @@ from .binding import (  # noqa: F401
     RunParams,
     epd_lb_workspace_bytes,
     epd_prop_solve,
+    epd_prop_solve_noalloc,
     epd_prop_solve_workspace_bytes,
     lib,
 )

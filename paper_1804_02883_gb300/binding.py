@@ -23,6 +23,7 @@ ERRORS = {
     -5: "EPD_LB_EUNSTABLE",
     -6: "EPD_LB_ETIMEOUT",
     -7: "EPD_LB_ENOTCONV",
+    -8: "EPD_LB_ETOOLARGE",
 }
 PLAIN_FP64 = 0
 MIXED_FP32 = 1
@@ -33,7 +34,7 @@ SYMBOLS = (
     "epd_lb_velocity", "epd_lb_densities_dev", "epd_lb_velocity_dev", "epd_lb_get_state",
     "epd_lb_set_state", "epd_lb_solve", "epd_lb_observables", "epd_lb_save", "epd_lb_load",
     "epd_lb_last_error", "epd_lb_destroy", "epd_prop_solve_workspace_bytes", "epd_prop_solve",
-    "epd_lb_enable_timing", "epd_lb_kernel_times",
+    "epd_lb_enable_timing", "epd_lb_kernel_times", "epd_prop_solve_noalloc",
 )
 
 
@@ -124,6 +125,7 @@ def lib():
             "epd_prop_solve": (ctypes.c_int, [P, vp, vp, vp, vp, ctypes.c_size_t, vp]),
             "epd_lb_enable_timing": (ctypes.c_int, [vp, i32]),
             "epd_lb_kernel_times": (ctypes.c_int, [vp, vp]),
+            "epd_prop_solve_noalloc": (ctypes.c_int, [P, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -174,6 +176,16 @@ def epd_prop_solve(run: RunParams, omega_dev: int, phi_dev: int, q_dev: int, wor
     rc = lib().epd_prop_solve(ctypes.byref(run.c()), omega_dev, phi_dev, q_dev, workspace_dev, workspace_bytes, stream)
     if rc:
         raise EpdLbError(rc, "epd_prop_solve")
+
+
+def epd_prop_solve_noalloc(run: RunParams, omega_dev: int, phi_dev: int, q_dev: int, stream: int = 0) -> None:
+    """The single-chain solve of epd_prop_solve without a workspace: its scratch
+    is a fixed array inside the library (for callers that cannot allocate device
+    memory at that point; see include/epd_lb.h for the size limit and the rule
+    that overlapping calls race)."""
+    rc = lib().epd_prop_solve_noalloc(ctypes.byref(run.c()), omega_dev, phi_dev, q_dev, stream)
+    if rc:
+        raise EpdLbError(rc, "epd_prop_solve_noalloc")
 
 
 class EpdLb:

@@ -2,6 +2,7 @@
 // parameter validation, workspace layout, transform tables, CUDA-graph capture
 // of the time step, state access and checkpoints.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -770,6 +771,87 @@ extern "C" int epd_prop_solve(const epd_lb_params *p, const double *omega_dev, d
     cudaStream_t s = (cudaStream_t)cuda_stream;
     if (cudaMemsetAsync(G.err, 0, sizeof(int), s) != cudaSuccess) return EPD_LB_ECUDA;
     if (upload_tables_e(G, s) != cudaSuccess) return EPD_LB_ECUDA;
+    if (launch_solve(G, omega_dev, phi_dev, q_dev, s) != cudaSuccess) return EPD_LB_ECUDA;
+    return EPD_LB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free single-chain solve: the scratch of epd_prop_solve lives in a
+// fixed array in the device image instead of a caller workspace.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr size_t kNoallocBytes = EPD_PROP_SOLVE_NOALLOC_MAX_BYTES;
+constexpr int kNoallocDevices = 64;
+
+// One copy per device that loads this library, held until the process exits.
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+// Device address of g_noalloc_scratch on each device (host code must not use
+// the symbol itself as an address).
+std::atomic<void *> g_noalloc_addr[kNoallocDevices];
+
+// Twiddles exp(-2 pi i t / n), t < n/2, and Fourier factors
+// exp(-R_G^2 k^2 ds) / n (Eq. (8)), computed on the device in FP64.
+template <typename T>
+__global__ void noalloc_tables(int nx, int ny, double dx, double rg, double ds, V2<T> *twx, V2<T> *twy, T *kx, T *ky)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    auto twiddle = [](int t, int n, V2<T> *out) {
+        double s, c;
+        sincospi(2.0 * (double)t / (double)n, &s, &c);
+        out[t] = mk<T>((T)c, (T)(-s));
+    };
+    auto factor = [&](int m, int n, T *out) {
+        const double k = 2.0 * 3.14159265358979323846 * (double)signed_bin(m, n) / ((double)n * dx);
+        out[m] = (T)(exp(-rg * rg * k * k * ds) / (double)n);
+    };
+    if (i < nx / 2) twiddle(i, nx, twx);
+    if (i < ny / 2) twiddle(i, ny, twy);
+    if (i < nx) factor(i, nx, kx);
+    if (i < ny) factor(i, ny, ky);
+}
+
+template <typename T>
+cudaError_t noalloc_launch_tables(Group &G, cudaStream_t s)
+{
+    const int m = std::max(G.g.nx, G.g.ny);
+    noalloc_tables<T><<<(m + kThreads - 1) / kThreads, kThreads, 0, s>>>(
+        G.g.nx, G.g.ny, G.g.dx, G.g.rg, G.g.ds, reinterpret_cast<V2<T> *>(G.twx), reinterpret_cast<V2<T> *>(G.twy),
+        reinterpret_cast<T *>(G.kx), reinterpret_cast<T *>(G.ky));
+    return cudaGetLastError();
+}
+
+} // namespace
+
+extern "C" int epd_prop_solve_noalloc(const epd_lb_params *p, const double *omega_dev, double *phi_dev, double *q_dev,
+                                      void *cuda_stream)
+{
+    if (!p || !omega_dev || !phi_dev || !q_dev || !validate(*p).empty()) return EPD_LB_EINVAL;
+    Group G = Group();
+    G.p = *p;
+    G.prec = p->precision;
+    fill_geom(G);
+    G.g.nruns = 1;
+    default_shapes(G);
+    if (carve_solve(G, nullptr) > kNoallocBytes) return EPD_LB_ETOOLARGE;
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocDevices) return EPD_LB_ECUDA;
+    void *base = g_noalloc_addr[dev].load();
+    if (!base) {
+        if (cudaGetSymbolAddress(&base, g_noalloc_scratch) != cudaSuccess || !base) return EPD_LB_ECUDA;
+        g_noalloc_addr[dev].store(base);
+    }
+    if (configure_kernels() != cudaSuccess) return EPD_LB_ECUDA;
+    carve_solve(G, (char *)base);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    // the error word must start at zero; every other scratch buffer is written
+    // before it is read within the call
+    if (cudaMemsetAsync(G.err, 0, sizeof(int), s) != cudaSuccess) return EPD_LB_ECUDA;
+    const cudaError_t e = G.prec == EPD_LB_MIXED_FP32 ? noalloc_launch_tables<float>(G, s) : noalloc_launch_tables<double>(G, s);
+    if (e != cudaSuccess) return EPD_LB_ECUDA;
     if (launch_solve(G, omega_dev, phi_dev, q_dev, s) != cudaSuccess) return EPD_LB_ECUDA;
     return EPD_LB_OK;
 }
