@@ -18,6 +18,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -31,6 +32,8 @@ sys.path.insert(0, ROOT)
 METRIC = "propagator site·contour-step updates/s + LB MLUPS, 1 GB300, vs FP64 plain"
 UNIT = "site·contour-steps/s"
 HBM_FALLBACK = 6800.0
+# FP32 (non-tensor) units of a GB300 at its maximum SM clock
+FP32_SMS, FP32_LANES, FP32_MHZ = 152, 128, 2070.0
 
 
 def peaks():
@@ -242,16 +245,32 @@ def main():
     # kernel durations inside the timed steps (event nodes in the step graph)
     nsite = sites_per_step(runs)
     kt = {k: statistics.mean(d[k] for d in kern) for k in kern[0]}
-    bytes_per_site = {"prop_row_accumulate": 64.0, "prop_row_store": 32.0, "prop_col": 16.0, "lb_collide_stream": 88.0}
     hbm, peak_kind = peaks()
     kernels = {}
-    for k, bps in bytes_per_site.items():
-        gbs = bps * nsite / (kt[k] * 1e-3) / 1e9
-        kernels[k] = {"ms": kt[k], "bytes_per_site": bps, "achieved_gbs": gbs, "frac": gbs / hbm}
-    dom = "prop_row_accumulate"
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": kernels[dom]["achieved_gbs"], "peak": hbm,
-                "unit": "GB/s", "frac": kernels[dom]["achieved_gbs"] / hbm, "traffic": None,
-                "peak_source": f"{peak_kind} hbm_gbs (copy)"}
+    lb_bps = 88.0
+    kernels["lb_collide_stream"] = {"ms": kt["lb_collide_stream"], "bytes_per_site": lb_bps,
+                                    "achieved_gbs": lb_bps * nsite / (kt["lb_collide_stream"] * 1e-3) / 1e9}
+    kernels["lb_collide_stream"]["frac"] = kernels["lb_collide_stream"]["achieved_gbs"] / hbm
+    if "prop_cluster" in kt:
+        # one cluster-resident launch = one single-chain solve of every run:
+        # per run and contour step, forward + inverse transforms along both
+        # axes, 10 n log2(n) flops (5 N log2 N per transform of length N)
+        flops = sum(10.0 * r.nx * r.ny * math.log2(r.nx * r.ny) * r.ns for r in runs)
+        tf = flops / (kt["prop_cluster"] * 1e-3) / 1e12
+        peak_tf = FP32_SMS * FP32_LANES * 2 * FP32_MHZ * 1e6 / 1e12
+        kernels["prop_cluster"] = {"ms": kt["prop_cluster"], "flops": flops, "achieved_tflops": tf, "frac": tf / peak_tf}
+        roofline = {"bound": "alu", "kernel": "prop_cluster (one single-chain solve of all runs)", "achieved": tf,
+                    "peak": peak_tf, "unit": "TFLOP/s", "frac": tf / peak_tf, "traffic": None,
+                    "peak_source": "derived FP32 peak: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
+    else:
+        bytes_per_site = {"prop_row_accumulate": 64.0, "prop_row_store": 32.0, "prop_col": 16.0}
+        for k, bps in bytes_per_site.items():
+            gbs = bps * nsite / (kt[k] * 1e-3) / 1e9
+            kernels[k] = {"ms": kt[k], "bytes_per_site": bps, "achieved_gbs": gbs, "frac": gbs / hbm}
+        dom = "prop_row_accumulate"
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": kernels[dom]["achieved_gbs"], "peak": hbm,
+                    "unit": "GB/s", "frac": kernels[dom]["achieved_gbs"] / hbm, "traffic": None,
+                    "peak_source": f"{peak_kind} hbm_gbs (copy)"}
 
     # end to end through the C ABI with host buffers: upload omega of every
     # run from pinned memory, one step, read Phi and Q of every run back

@@ -160,12 +160,15 @@ int epd_lb_save(epd_lb *h, void *buf, size_t *len);
 int epd_lb_load(epd_lb *h, const void *buf, size_t len);
 
 /* Kernel timing inside the captured step.  epd_lb_enable_timing(h, 1)
- * re-captures the step graph with CUDA event-record nodes around four
- * launches of the first batch: the propagator row pass of contour node
- * N_s/4 (history store) and 3 N_s/4 (contour accumulation) of the second
- * solve, the column pass before the latter, and the LB collide-stream.
+ * re-captures the step graph with CUDA event-record nodes around launches of
+ * the first batch's second single-chain solve and its LB collide-stream.
  * epd_lb_kernel_times waits for the stream and writes the durations of the
- * most recent step, in milliseconds, to ms[0..3] in that order. */
+ * most recent step in milliseconds: ms[0..2] the propagator kernels, ms[3]
+ * the LB collide-stream, ms[4] a flag.  With the streaming transform passes
+ * (ms[4] = 0): ms[0] the row pass of contour node N_s/4 (history store),
+ * ms[1] the row pass of node 3 N_s/4 + 1 (contour accumulation), ms[2] the
+ * column pass before it.  With the cluster-resident solve (ms[4] = 1): ms[0]
+ * its single launch (the whole contour), ms[1] = ms[2] = 0. */
 int epd_lb_enable_timing(epd_lb *h, int32_t on);
 int epd_lb_kernel_times(epd_lb *h, double *ms);
 

@@ -308,11 +308,15 @@ class EpdLb:
         self._ck(lib().epd_lb_enable_timing(self.h, int(on)), "epd_lb_enable_timing")
 
     def kernel_times(self) -> dict:
-        """Durations (ms) inside the last step: row pass storing history, row
-        pass accumulating the contour sums, column pass, LB collide-stream."""
-        out = np.empty(4)
+        """Durations (ms) inside the last step: the propagator kernels of the
+        second solve (the cluster-resident launch, or the row pass storing
+        history, the row pass accumulating contour sums and a column pass) and
+        the LB collide-stream."""
+        out = np.empty(5)
         self._ck(lib().epd_lb_kernel_times(self.h, _ptr(out)), "epd_lb_kernel_times")
-        return dict(zip(("prop_row_store", "prop_row_accumulate", "prop_col", "lb_collide_stream"), out.tolist()))
+        if out[4] == 1.0:
+            return {"prop_cluster": float(out[0]), "lb_collide_stream": float(out[3])}
+        return dict(zip(("prop_row_store", "prop_row_accumulate", "prop_col", "lb_collide_stream"), out[:4].tolist()))
 
     def save(self) -> bytes:
         n = ctypes.c_size_t()

@@ -60,6 +60,7 @@ struct Group {
     // transform tables
     void *twx, *twy, *kx, *ky;     // bulk precision: twiddles, exp(-rg^2 k^2 ds)/N
     double2 *twx_d, *twy_d;        // FP64 twiddles for the EPD/force passes
+    float2 *twx_full, *twy_full;   // FP32 twiddles exp(-2 pi i j/N), j < N (cluster solve); may be null
     int *err;                      // device error word (shared by the handle)
 };
 
@@ -75,9 +76,12 @@ cudaError_t launch_init_state(Group &G, cudaStream_t s);
 // Optional CUDA events recorded around single launches of a solve (for timing
 // inside a captured step): ev[0], ev[1] bracket the row pass of node m_store;
 // ev[2], ev[3] the column pass before node m_acc and ev[3], ev[4] its row pass.
+// With the cluster-resident solve, ev[0], ev[1] bracket its single launch and
+// `cluster` is set.
 struct SolveProbe {
     cudaEvent_t ev[5];
     int m_store, m_acc;
+    mutable bool cluster = false;
 };
 
 // Single-chain solve, Eqs. (6)-(11): omega (3n per run, FP64) -> phi (3n),
@@ -99,6 +103,12 @@ cudaError_t launch_vel_from_f64(Group &G, int run, const double *src, cudaStream
 cudaError_t launch_observables(Group &G, int run, int parity, double *out_dev, cudaStream_t s);
 // Exact copy of a run's stored populations to (dst) or from (src) FP64.
 cudaError_t launch_pop_raw(Group &G, int run, int parity, double *dst, const double *src, cudaStream_t s);
+
+// Cluster-resident solve (prop_cluster.cu): availability for the group's
+// shape and precision, its launch, and its CTAs per run.
+bool cluster_solve_supported(const Group &G);
+cudaError_t launch_cluster_solve(Group &G, cudaStream_t s, const void *twx_full, const void *twy_full);
+int cluster_ctas(const Group &G);
 
 // Kernel attributes (dynamic shared memory limits), once per process.
 cudaError_t configure_kernels();

@@ -235,6 +235,18 @@ static cudaError_t solve_t(Group &G, const double *omega, double *phi, double *q
 
     const int pg = grid_for(g.n);
     prop_prep<T><<<dim3(pg, g.nruns), kThreads, 0, s>>>(g, omega, reinterpret_cast<V2<T> *>(G.efac), phi, G.part);
+    if (sizeof(T) == sizeof(float) && G.twx_full && cluster_solve_supported(G)) {
+        // whole contour in one cluster-resident launch
+        if (probe) {
+            probe->cluster = true;
+            cudaEventRecordWithFlags(probe->ev[0], s, cudaEventRecordExternal);
+        }
+        cudaError_t e = launch_cluster_solve(G, s, G.twx_full, G.twy_full);
+        if (e != cudaSuccess) return e;
+        if (probe) cudaEventRecordWithFlags(probe->ev[1], s, cudaEventRecordExternal);
+        prop_finalize<<<dim3(pg, g.nruns), kThreads, 0, s>>>(g, cluster_ctas(G), pg, G.ia, G.ib, G.part, phi, q, G.err);
+        return cudaGetLastError();
+    }
     prop_start<T><<<dim3(pg, g.nruns), kThreads, 0, s>>>(k);
     const dim3 gc(g.nx / G.sh.cols_prop, g.nruns), gr(g.ny / G.sh.rows_prop, g.nruns);
     const size_t sc = col_smem<T>(G), sr = row_smem<T>(G);

@@ -18,7 +18,11 @@ def _build(oracle_lib):
     P.lib()
 
 
-SHAPES = [(8, 8, 4), (16, 32, 8), (64, 64, 32), (32, 256, 16), (256, 16, 12), (8, 2048, 6), (1024, 8, 10)]
+# includes every grid of the cluster-resident solve (MIXED_FP32) and grids
+# that take the streaming passes
+SHAPES = [(8, 8, 4), (16, 32, 8), (64, 64, 32), (32, 256, 16), (256, 16, 12), (8, 2048, 6), (1024, 8, 10),
+          (64, 128, 10), (128, 64, 14), (128, 128, 16), (256, 128, 32), (128, 256, 12), (128, 512, 24),
+          (512, 128, 8), (256, 256, 20), (256, 512, 64), (512, 256, 8)]
 
 
 @pytest.mark.parametrize("prec", [P.PLAIN_FP64, P.MIXED_FP32])
