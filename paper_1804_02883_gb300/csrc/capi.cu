@@ -53,6 +53,7 @@ size_t carve_group(Group &G, char *base, size_t off)
     G.cz = (double2 *)take(R * 4 * n * sizeof(double2));
     G.part = (double *)take(R * kMaxPart * sizeof(double));
     G.f0_lat = (double *)take(R * sizeof(double));
+    G.f0_bulk = take(R * tb);
     G.stage = (double *)take(std::max<size_t>(9 * n, 2 * R + 16) * sizeof(double));
     G.chain = take(R * n * 2 * tb);
     G.hist = take(R * (size_t)(G.g.half_lo + 1) * n * 2 * tb);
@@ -90,6 +91,7 @@ static Group run_view(const Group &G, int r)
     V.cz += (size_t)r * 4 * n;
     V.part += (size_t)r * kMaxPart;
     V.f0_lat += r;
+    V.f0_bulk = (char *)V.f0_bulk + (size_t)r * tb;
     V.chain = (char *)V.chain + (size_t)r * n * 2 * tb;
     V.hist = (char *)V.hist + (size_t)r * (G.g.half_lo + 1) * n * 2 * tb;
     V.efac = (char *)V.efac + (size_t)r * n * 2 * tb;
@@ -216,6 +218,8 @@ static cudaError_t upload_tables_t(Group &G, cudaStream_t s)
     std::vector<double> f0(G.g.nruns);
     for (int r = 0; r < G.g.nruns; ++r) f0[r] = G.run_params[r].f0 * G.g.fstar;
     if ((e = cudaMemcpyAsync(G.f0_lat, f0.data(), f0.size() * sizeof(double), cudaMemcpyHostToDevice, s))) return e;
+    std::vector<T> f0b(f0.begin(), f0.end());
+    if (G.f0_bulk && (e = cudaMemcpyAsync(G.f0_bulk, f0b.data(), f0b.size() * sizeof(T), cudaMemcpyHostToDevice, s))) return e;
     return cudaStreamSynchronize(s);
 }
 

@@ -49,6 +49,7 @@ struct Group {
     double2 *cz;       // 4 complex FP64 scratch planes per run: [run][4][n]
     double *part;      // reduction partials, [run][kMaxPart]
     double *f0_lat;    // [run]
+    void *f0_bulk;     // [run], the same in the bulk type
     double *stage;     // host<->device staging, 9 n doubles (one run)
     // bulk-precision buffers (float or double, by prec)
     void *chain;       // packed (g, g') of the running contour step, [run][n] complex

@@ -32,7 +32,7 @@ template <typename T> struct LbK {
     T *pout;
     const V2<T> *force;
     V2<T> *vel;
-    const double *f0_lat;
+    const T *f0;  // body-force amplitude per run, lattice units, bulk type
     T gs, gb, gg;
 };
 
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(kThreads) lb_collide_stream(LbK<T> k)
     const T mxx = sxx - third * drho, myy = syy - third * drho, mxy = sxy;
 
     const V2<T> fp = k.force[(size_t)run * n + site];
-    const T fpx = (T)((y < (k.ny >> 1)) ? -k.f0_lat[run] : k.f0_lat[run]);
+    const T fpx = (y < (k.ny >> 1)) ? -k.f0[run] : k.f0[run];
     const T fx = fp.x + fpx, fy = fp.y;
     const T inv_rho = (T)1 / rho;
     const T ux = (jx + (T)0.5 * fx) * inv_rho, uy = (jy + (T)0.5 * fy) * inv_rho;
@@ -127,7 +127,7 @@ static cudaError_t lb_t(Group &G, int parity, cudaStream_t s)
     k.pout = reinterpret_cast<T *>(G.pop[1 - parity]);
     k.force = reinterpret_cast<const V2<T> *>(G.force);
     k.vel = reinterpret_cast<V2<T> *>(G.vel);
-    k.f0_lat = G.f0_lat;
+    k.f0 = reinterpret_cast<const T *>(G.f0_bulk);
     k.gs = (T)G.g.gamma_s;
     k.gb = (T)G.g.gamma_b;
     k.gg = (T)G.g.gamma_g;

@@ -54,8 +54,10 @@ template <typename T> __device__ __forceinline__ T exp_t(T v);
 template <> __device__ __forceinline__ float exp_t<float>(float v) { return expf(v); }
 template <> __device__ __forceinline__ double exp_t<double>(double v) { return exp(v); }
 
-// Boltzmann factors E_{A,B} = exp(-N w_{A,B} ds / 2) in the bulk precision;
-// exp(-w_S) into the S slot of phi_out and its block sums for Q_S.
+// Boltzmann factors E_{A,B} = exp(-N w_{A,B} ds / 2) and exp(-w_S) in the bulk
+// precision; exp(-w_S) into the S slot of phi_out and its block sums for Q_S
+// (per-thread sums of at most a few terms in the bulk type, FP64 across
+// threads and blocks).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) prop_prep(GroupGeom g, const double *omega, V2<T> *efac, double *phi_out, double *part)
 {
@@ -64,15 +66,16 @@ __global__ void __launch_bounds__(kThreads) prop_prep(GroupGeom g, const double 
     const long long n = g.n;
     const double *wa = omega + (size_t)run * 3 * n, *wb = wa + n, *ws = wb + n;
     double *es = phi_out + (size_t)run * 3 * n + 2 * n;
-    const double c = -0.5 * g.nseg * g.ds;
-    double acc = 0.0;
+    const T c = (T)(-0.5 * g.nseg * g.ds);
+    T acc = 0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        efac[(size_t)run * n + i] = mk<T>(exp_t<T>((T)(c * wa[i])), exp_t<T>((T)(c * wb[i])));
-        const double e = exp(-ws[i]);
-        es[i] = e;
+        efac[(size_t)run * n + i] = mk<T>(exp_t<T>(c * (T)wa[i]), exp_t<T>(c * (T)wb[i]));
+        // exp(-w_S) in the bulk precision (FP32 in MIXED_FP32), kept in FP64
+        const T e = exp_t<T>(-(T)ws[i]);
+        es[i] = (double)e;
         acc += e;
     }
-    const double s = block_sum(acc, red);
+    const double s = block_sum((double)acc, red);
     if (threadIdx.x == 0) part[(size_t)run * kMaxPart + kMaxPart / 2 + blockIdx.x] = s;
 }
 
