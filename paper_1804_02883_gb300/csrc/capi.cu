@@ -50,6 +50,8 @@ size_t carve_group(Group &G, char *base, size_t off)
     G.q_t = (double *)take(R * 2 * sizeof(double));
     G.ia = (double *)take(R * n * sizeof(double));
     G.ib = (double *)take(R * n * sizeof(double));
+    G.ia2 = (double *)take(R * n * sizeof(double));
+    G.ib2 = (double *)take(R * n * sizeof(double));
     G.cz = (double2 *)take(R * 4 * n * sizeof(double2));
     G.part = (double *)take(R * kMaxPart * sizeof(double));
     G.f0_lat = (double *)take(R * sizeof(double));
@@ -88,6 +90,8 @@ static Group run_view(const Group &G, int r)
     V.q_t += 2 * r;
     V.ia += (size_t)r * n;
     V.ib += (size_t)r * n;
+    V.ia2 += (size_t)r * n;
+    V.ib2 += (size_t)r * n;
     V.cz += (size_t)r * 4 * n;
     V.part += (size_t)r * kMaxPart;
     V.f0_lat += r;

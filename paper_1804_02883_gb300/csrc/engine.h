@@ -46,6 +46,7 @@ struct Group {
     double *omega, *omega_t, *phi, *phi_t;
     double *q, *q_t;   // [run][2]
     double *ia, *ib;   // contour sums, [run][n]
+    double *ia2, *ib2; // contour sums of the g' chain's terms (cluster solve), [run][n]
     double2 *cz;       // 4 complex FP64 scratch planes per run: [run][4][n]
     double *part;      // reduction partials, [run][kMaxPart]
     double *f0_lat;    // [run]

@@ -180,9 +180,10 @@ __global__ void __launch_bounds__(kThreads) prop_row(PropK<T> k, int m)
 }
 
 // Normalisation, Eqs. (9)-(11) with Q as spatial means.
+// ia2/ib2 (may be null): sums of the second chain's terms (cluster solve).
 __global__ void __launch_bounds__(kThreads) prop_finalize(GroupGeom g, int nrow_blocks, int nprep_blocks, const double *ia,
-                                                      const double *ib, const double *part, double *phi, double *q,
-                                                      int *err)
+                                                      const double *ib, const double *ia2, const double *ib2,
+                                                      const double *part, double *phi, double *q, int *err)
 {
     __shared__ double bc;
     const int run = blockIdx.y;
@@ -198,9 +199,10 @@ __global__ void __launch_bounds__(kThreads) prop_finalize(GroupGeom g, int nrow_
     const double cp = g.phi_p / qp, cs = (1.0 - g.phi_p) / qs;
     double *pa = phi + (size_t)run * 3 * n, *pb = pa + n, *ps = pb + n;
     const double *ja = ia + (size_t)run * n, *jb = ib + (size_t)run * n;
+    const double *ja2 = ia2 ? ia2 + (size_t)run * n : nullptr, *jb2 = ib2 ? ib2 + (size_t)run * n : nullptr;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        pa[i] = cp * ja[i];
-        pb[i] = cp * jb[i];
+        pa[i] = cp * (ja2 ? ja[i] + ja2[i] : ja[i]);
+        pb[i] = cp * (jb2 ? jb[i] + jb2[i] : jb[i]);
         ps[i] = cs * ps[i];
     }
 }
@@ -247,7 +249,7 @@ static cudaError_t solve_t(Group &G, const double *omega, double *phi, double *q
         cudaError_t e = launch_cluster_solve(G, s, G.twx_full, G.twy_full);
         if (e != cudaSuccess) return e;
         if (probe) cudaEventRecordWithFlags(probe->ev[1], s, cudaEventRecordExternal);
-        prop_finalize<<<dim3(pg, g.nruns), kThreads, 0, s>>>(g, cluster_ctas(G), pg, G.ia, G.ib, G.part, phi, q, G.err);
+        prop_finalize<<<dim3(pg, g.nruns), kThreads, 0, s>>>(g, cluster_ctas(G), pg, G.ia, G.ib, G.ia2, G.ib2, G.part, phi, q, G.err);
         return cudaGetLastError();
     }
     prop_start<T><<<dim3(pg, g.nruns), kThreads, 0, s>>>(k);
@@ -263,7 +265,7 @@ static cudaError_t solve_t(Group &G, const double *omega, double *phi, double *q
         if (ps) cudaEventRecordWithFlags(probe->ev[1], s, cudaEventRecordExternal);
         if (pa) cudaEventRecordWithFlags(probe->ev[4], s, cudaEventRecordExternal);
     }
-    prop_finalize<<<dim3(pg, g.nruns), kThreads, 0, s>>>(g, gr.x, pg, G.ia, G.ib, G.part, phi, q, G.err);
+    prop_finalize<<<dim3(pg, g.nruns), kThreads, 0, s>>>(g, gr.x, pg, G.ia, G.ib, nullptr, nullptr, G.part, phi, q, G.err);
     return cudaGetLastError();
 }
 
