@@ -318,6 +318,10 @@ struct epd_lb {
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
     bool timing = false;
     bool timed_cluster = false;  // the timed solve ran as one cluster-resident launch
+    // one stream per group beyond the first, forked from and joined to the
+    // handle's stream inside the captured step so that groups run concurrently
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> fork_ev, join_ev;
     cudaEvent_t ev[7] = {};
     std::string last_error;
 };
@@ -354,28 +358,44 @@ extern "C" int epd_lb_workspace_bytes(const epd_lb_params *p, int32_t nruns, siz
 }
 
 // Record the whole time step of every group (App. C order) on stream s.
+static cudaError_t enqueue_group(epd_lb *h, size_t gi, int parity, cudaStream_t s)
+{
+    cudaError_t e;
+    Group &G = h->groups[gi];
+    SolveProbe probe;
+    const bool timed = h->timing && gi == 0;
+    if (timed) {
+        for (int k = 0; k < 5; ++k) probe.ev[k] = h->ev[k];
+        probe.m_store = std::max(1, G.g.ns / 4);
+        probe.m_acc = std::min(G.g.ns, (3 * G.g.ns) / 4 + 1);
+    }
+    if ((e = launch_aux_convection(G, s))) return e;                      // omega -> omega~
+    if ((e = launch_solve(G, G.omega_t, G.phi_t, G.q_t, s))) return e;     // Phi~
+    if ((e = launch_diffusion(G, s))) return e;                           // omega(t+dt)
+    if ((e = launch_solve(G, G.omega, G.phi, G.q, s, timed ? &probe : nullptr))) return e;  // Phi(t+dt)
+    if (timed) h->timed_cluster = probe.cluster;
+    if ((e = launch_force(G, s))) return e;                               // polymer force
+    if (timed && (e = cudaEventRecordWithFlags(h->ev[5], s, cudaEventRecordExternal))) return e;
+    if ((e = launch_lb(G, parity, s))) return e;                          // collide-stream
+    if (timed && (e = cudaEventRecordWithFlags(h->ev[6], s, cudaEventRecordExternal))) return e;
+    return cudaSuccess;
+}
+
+// Record the whole time step of every group (App. C order); group 0 on the
+// handle's stream, the others on their own streams forked from it.
 static cudaError_t enqueue_step(epd_lb *h, int parity, cudaStream_t s)
 {
     cudaError_t e;
-    for (size_t gi = 0; gi < h->groups.size(); ++gi) {
-        Group &G = h->groups[gi];
-        SolveProbe probe;
-        const bool timed = h->timing && gi == 0;
-        if (timed) {
-            for (int k = 0; k < 5; ++k) probe.ev[k] = h->ev[k];
-            probe.m_store = std::max(1, G.g.ns / 4);
-            probe.m_acc = std::min(G.g.ns, (3 * G.g.ns) / 4 + 1);
-        }
-        if ((e = launch_aux_convection(G, s))) return e;                      // omega -> omega~
-        if ((e = launch_solve(G, G.omega_t, G.phi_t, G.q_t, s))) return e;     // Phi~
-        if ((e = launch_diffusion(G, s))) return e;                           // omega(t+dt)
-        if ((e = launch_solve(G, G.omega, G.phi, G.q, s, timed ? &probe : nullptr))) return e;  // Phi(t+dt)
-        if (timed) h->timed_cluster = probe.cluster;
-        if ((e = launch_force(G, s))) return e;                               // polymer force
-        if (timed && (e = cudaEventRecordWithFlags(h->ev[5], s, cudaEventRecordExternal))) return e;
-        if ((e = launch_lb(G, parity, s))) return e;                          // collide-stream
-        if (timed && (e = cudaEventRecordWithFlags(h->ev[6], s, cudaEventRecordExternal))) return e;
+    const size_t ng = h->groups.size();
+    for (size_t gi = 1; gi < ng; ++gi) {
+        if ((e = cudaEventRecord(h->fork_ev[gi - 1], s))) return e;
+        if ((e = cudaStreamWaitEvent(h->side[gi - 1], h->fork_ev[gi - 1], 0))) return e;
+        if ((e = enqueue_group(h, gi, parity, h->side[gi - 1]))) return e;
+        if ((e = cudaEventRecord(h->join_ev[gi - 1], h->side[gi - 1]))) return e;
     }
+    if ((e = enqueue_group(h, 0, parity, s))) return e;
+    for (size_t gi = 1; gi < ng; ++gi)
+        if ((e = cudaStreamWaitEvent(s, h->join_ev[gi - 1], 0))) return e;
     return cudaSuccess;
 }
 
@@ -468,6 +488,16 @@ extern "C" int epd_lb_init(const epd_lb_params *p, int32_t nruns, void *workspac
         if (launch_solve(G, G.omega, G.phi, G.q, h->stream) != cudaSuccess) return bail(EPD_LB_ECUDA);
     }
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(EPD_LB_ECUDA);
+    for (size_t gi = 1; gi < h->groups.size(); ++gi) {
+        cudaStream_t st;
+        cudaEvent_t a, b;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return bail(EPD_LB_ECUDA);
+        h->side.push_back(st);
+        if (cudaEventCreateWithFlags(&a, cudaEventDisableTiming) != cudaSuccess) return bail(EPD_LB_ECUDA);
+        h->fork_ev.push_back(a);
+        if (cudaEventCreateWithFlags(&b, cudaEventDisableTiming) != cudaSuccess) return bail(EPD_LB_ECUDA);
+        h->join_ev.push_back(b);
+    }
     h->parity = 0;
     if (int rc = build_graphs(h)) return bail(rc);
     *out = h;
@@ -736,6 +766,9 @@ extern "C" void epd_lb_destroy(epd_lb *h)
         if (h->exec[k]) cudaGraphExecDestroy(h->exec[k]);
     for (int k = 0; k < 7; ++k)
         if (h->ev[k]) cudaEventDestroy(h->ev[k]);
+    for (auto e : h->fork_ev) cudaEventDestroy(e);
+    for (auto e : h->join_ev) cudaEventDestroy(e);
+    for (auto st : h->side) cudaStreamDestroy(st);
     if (h->own_ws && h->ws) cudaFree(h->ws);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
