@@ -172,6 +172,55 @@ int epd_lb_load(epd_lb *h, const void *buf, size_t len);
 int epd_lb_enable_timing(epd_lb *h, int32_t on);
 int epd_lb_kernel_times(epd_lb *h, double *ms);
 
+/*
+ * Learned density surrogate: a convolutional network that approximates the
+ * map omega -> (Phi_A, Phi_B) of the single-chain solve, Eqs. (6)-(10), with
+ * the exact means and the exact solvent density of Eq. (11).  Network: 3x3
+ * convolutions with circular padding, channels 3 -> 32 -> 32 -> 32 -> 2, tanh
+ * after the first three; input s_in (omega_c - <omega_c>), output Phi_c =
+ * <Phi_c> + s_out (y_c - <y_c>).  Parameters: epd_sur_num_params() FP32
+ * values, per layer W[co][ci][3][3] (tap = 3 (dy+1) + (dx+1)) then b[co].
+ * Tensor-core kernels read BF16 copies of weights and activations and
+ * accumulate in FP32.  Fields are [batch][species][ny][nx] FP64 on the device;
+ * every call is asynchronous on cuda_stream; the workspace is caller-owned
+ * device memory of epd_sur_workspace_bytes (training = 1 for the gradient and
+ * training calls).  nx must be a multiple of 16 and ny of 8.
+ */
+int32_t epd_sur_num_params(void);
+int epd_sur_workspace_bytes(int32_t ny, int32_t nx, int32_t batch, int32_t training, size_t *bytes);
+/* Densities of the surrogate for batch fields omega_dev -> phi_dev.  p gives
+ * the grid, phi_p and the A-block fraction of the exact means. */
+int epd_sur_forward(const epd_lb_params *p, int32_t batch, const float *params_dev, double s_in, double s_out,
+                    const double *omega_dev, double *phi_dev, void *workspace, size_t workspace_bytes, void *cuda_stream);
+/* Loss L = mean over batch, A/B channels and sites of (y_c - (Phi_c - <Phi_c>)/s_out)^2
+ * for the target densities phi_dev, and its gradient dL/dparams (FP32,
+ * epd_sur_num_params values) to grad_dev; L to loss_dev[0]. */
+int epd_sur_gradients(const epd_lb_params *p, int32_t batch, const float *params_dev, double s_in, double s_out,
+                      const double *omega_dev, const double *phi_dev, float *grad_dev, double *loss_dev, void *workspace,
+                      size_t workspace_bytes, void *cuda_stream);
+/* epd_sur_gradients followed by one Adam step (beta 0.9, 0.999, eps 1e-8;
+ * step counts from 1) on params_dev with moments adam_m_dev, adam_v_dev. */
+int epd_sur_train_step(const epd_lb_params *p, int32_t batch, float *params_dev, float *adam_m_dev, float *adam_v_dev,
+                       int32_t step, float lr, double s_in, double s_out, const double *omega_dev, const double *phi_dev,
+                       double *loss_dev, void *workspace, size_t workspace_bytes, void *cuda_stream);
+
+/* Let the surrogate stand in for both single-chain solves of epd_lb_step:
+ * every exact_every-th step (and while falling back) the exact step runs and
+ * also evaluates the surrogate at omega~; if the RMS difference of the
+ * densities (max over runs) exceeds residual_tol the following steps stay
+ * exact until a check passes.  On the other steps both solves are the
+ * surrogate (Q_P, Q_S keep their last exact values).  params_host: the
+ * network's FP32 parameters (copied).  workspace: device memory of
+ * epd_lb_surrogate_workspace_bytes bytes, caller-owned, kept alive while the
+ * surrogate is attached.  exact_every = 0 detaches it. */
+int epd_lb_surrogate_workspace_bytes(epd_lb *h, size_t *bytes);
+int epd_lb_set_surrogate(epd_lb *h, const float *params_host, double s_in, double s_out, int32_t exact_every,
+                         double residual_tol, void *workspace, size_t workspace_bytes);
+/* out[0] steps taken with the surrogate attached, out[1] exact steps,
+ * out[2] surrogate steps, out[3] exact steps forced by a failed check,
+ * out[4] last residual, out[5] 1 if currently falling back. */
+int epd_lb_surrogate_stats(epd_lb *h, double *out);
+
 /* Text of the last error on the handle (never NULL). */
 const char *epd_lb_last_error(const epd_lb *h);
 

@@ -35,6 +35,8 @@ SYMBOLS = (
     "epd_lb_set_state", "epd_lb_solve", "epd_lb_observables", "epd_lb_save", "epd_lb_load",
     "epd_lb_last_error", "epd_lb_destroy", "epd_prop_solve_workspace_bytes", "epd_prop_solve",
     "epd_lb_enable_timing", "epd_lb_kernel_times", "epd_prop_solve_noalloc",
+    "epd_sur_num_params", "epd_sur_workspace_bytes", "epd_sur_forward", "epd_sur_gradients", "epd_sur_train_step",
+    "epd_lb_surrogate_workspace_bytes", "epd_lb_set_surrogate", "epd_lb_surrogate_stats",
 )
 
 
@@ -126,6 +128,17 @@ def lib():
             "epd_lb_enable_timing": (ctypes.c_int, [vp, i32]),
             "epd_lb_kernel_times": (ctypes.c_int, [vp, vp]),
             "epd_prop_solve_noalloc": (ctypes.c_int, [P, vp, vp, vp, vp]),
+            "epd_sur_num_params": (ctypes.c_int32, []),
+            "epd_sur_workspace_bytes": (ctypes.c_int, [i32, i32, i32, i32, szp]),
+            "epd_sur_forward": (ctypes.c_int, [P, i32, vp, ctypes.c_double, ctypes.c_double, vp, vp, vp, ctypes.c_size_t, vp]),
+            "epd_sur_gradients": (ctypes.c_int, [P, i32, vp, ctypes.c_double, ctypes.c_double, vp, vp, vp, vp, vp,
+                                                 ctypes.c_size_t, vp]),
+            "epd_sur_train_step": (ctypes.c_int, [P, i32, vp, vp, vp, i32, ctypes.c_float, ctypes.c_double, ctypes.c_double,
+                                                  vp, vp, vp, vp, ctypes.c_size_t, vp]),
+            "epd_lb_surrogate_workspace_bytes": (ctypes.c_int, [vp, szp]),
+            "epd_lb_set_surrogate": (ctypes.c_int, [vp, vp, ctypes.c_double, ctypes.c_double, i32, ctypes.c_double, vp,
+                                                    ctypes.c_size_t]),
+            "epd_lb_surrogate_stats": (ctypes.c_int, [vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -317,6 +330,27 @@ class EpdLb:
         if out[4] == 1.0:
             return {"prop_cluster": float(out[0]), "lb_collide_stream": float(out[3])}
         return dict(zip(("prop_row_store", "prop_row_accumulate", "prop_col", "lb_collide_stream"), out[:4].tolist()))
+
+    def set_surrogate(self, params, s_in: float, s_out: float, exact_every: int = 8, residual_tol: float = 1e-3):
+        """Attach the learned surrogate (FP32 parameters, host array or torch
+        tensor) with its workspace on the device; exact_every = 0 detaches."""
+        torch = self.torch
+        if exact_every <= 0:
+            self._ck(lib().epd_lb_set_surrogate(self.h, None, 0.0, 0.0, 0, 0.0, None, 0), "epd_lb_set_surrogate")
+            return
+        nb = ctypes.c_size_t()
+        self._ck(lib().epd_lb_surrogate_workspace_bytes(self.h, ctypes.byref(nb)), "epd_lb_surrogate_workspace_bytes")
+        self.sur_workspace = torch.empty(nb.value + 256, dtype=torch.uint8, device=self.workspace.device)
+        ptr = (self.sur_workspace.data_ptr() + 255) & ~255
+        hp = np.ascontiguousarray(params.detach().cpu().numpy() if hasattr(params, "detach") else params, dtype=np.float32)
+        self._ck(lib().epd_lb_set_surrogate(self.h, hp.ctypes.data_as(ctypes.c_void_p), s_in, s_out, exact_every,
+                                            residual_tol, ptr, nb.value), "epd_lb_set_surrogate")
+
+    def surrogate_stats(self) -> dict:
+        out = np.empty(6)
+        self._ck(lib().epd_lb_surrogate_stats(self.h, _ptr(out)), "epd_lb_surrogate_stats")
+        keys = ("steps", "exact", "surrogate", "forced_exact", "last_residual", "falling_back")
+        return dict(zip(keys, out.tolist()))
 
     def save(self) -> bytes:
         n = ctypes.c_size_t()

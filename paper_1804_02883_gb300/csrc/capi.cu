@@ -12,6 +12,7 @@
 
 #include "common.cuh"
 #include "engine.h"
+#include "surrogate.h"
 
 namespace epdlb {
 
@@ -322,6 +323,17 @@ struct epd_lb {
     // handle's stream inside the captured step so that groups run concurrently
     std::vector<cudaStream_t> side;
     std::vector<cudaEvent_t> fork_ev, join_ev;
+    // learned surrogate (attached with epd_lb_set_surrogate)
+    bool sur_on = false;
+    int sur_every = 0;
+    double sur_tol = 0.0, sur_s_in = 1.0, sur_s_out = 1.0;
+    float *sur_params = nullptr;               // device copy
+    std::vector<epdlb::sur::Work> sur_work;    // one per group
+    double *sur_resid = nullptr;               // [groups + 1] device: per group residual, scratch
+    cudaGraphExec_t exec_sur[2] = {nullptr, nullptr}, exec_chk[2] = {nullptr, nullptr};
+    long long sur_steps = 0, sur_exact = 0, sur_used = 0, sur_forced = 0;
+    double sur_last = 0.0;
+    bool sur_fallback = false;
     cudaEvent_t ev[7] = {};
     std::string last_error;
 };
@@ -358,10 +370,31 @@ extern "C" int epd_lb_workspace_bytes(const epd_lb_params *p, int32_t nruns, siz
 }
 
 // Record the whole time step of every group (App. C order) on stream s.
-static cudaError_t enqueue_group(epd_lb *h, size_t gi, int parity, cudaStream_t s)
+enum StepMode { STEP_EXACT = 0, STEP_SURROGATE = 1, STEP_CHECK = 2 };
+
+static void sur_means(const Group &G, double &pa, double &pb, double &ps)
+{
+    const double fa = (double)G.g.na / (double)G.g.ns;
+    pa = G.g.phi_p * fa;
+    pb = G.g.phi_p * (1.0 - fa);
+    ps = 1.0 - G.g.phi_p;
+}
+
+static cudaError_t enqueue_group(epd_lb *h, size_t gi, int parity, cudaStream_t s, int mode = STEP_EXACT)
 {
     cudaError_t e;
     Group &G = h->groups[gi];
+    if (mode == STEP_SURROGATE) {
+        double pa, pb, ps;
+        sur_means(G, pa, pb, ps);
+        sur::Work &W = h->sur_work[gi];
+        if ((e = launch_aux_convection(G, s))) return e;
+        if ((e = sur::forward(W, h->sur_params, G.omega_t, G.phi_t, h->sur_s_in, h->sur_s_out, pa, pb, ps, s))) return e;
+        if ((e = launch_diffusion(G, s))) return e;
+        if ((e = sur::forward(W, h->sur_params, G.omega, G.phi, h->sur_s_in, h->sur_s_out, pa, pb, ps, s))) return e;
+        if ((e = launch_force(G, s))) return e;
+        return launch_lb(G, parity, s);
+    }
     SolveProbe probe;
     const bool timed = h->timing && gi == 0;
     if (timed) {
@@ -371,6 +404,14 @@ static cudaError_t enqueue_group(epd_lb *h, size_t gi, int parity, cudaStream_t 
     }
     if ((e = launch_aux_convection(G, s))) return e;                      // omega -> omega~
     if ((e = launch_solve(G, G.omega_t, G.phi_t, G.q_t, s))) return e;     // Phi~
+    if (mode == STEP_CHECK) {
+        // the surrogate at omega~ into the EPD scratch, residual against Phi~
+        double pa, pb, ps;
+        sur_means(G, pa, pb, ps);
+        double *phi_sur = reinterpret_cast<double *>(G.cz);
+        if ((e = sur::forward(h->sur_work[gi], h->sur_params, G.omega_t, phi_sur, h->sur_s_in, h->sur_s_out, pa, pb, ps, s))) return e;
+        if ((e = sur::residual_rms(phi_sur, G.phi_t, G.g.n, G.g.nruns, G.part, h->sur_resid + gi, s))) return e;
+    }
     if ((e = launch_diffusion(G, s))) return e;                           // omega(t+dt)
     if ((e = launch_solve(G, G.omega, G.phi, G.q, s, timed ? &probe : nullptr))) return e;  // Phi(t+dt)
     if (timed) h->timed_cluster = probe.cluster;
@@ -383,41 +424,51 @@ static cudaError_t enqueue_group(epd_lb *h, size_t gi, int parity, cudaStream_t 
 
 // Record the whole time step of every group (App. C order); group 0 on the
 // handle's stream, the others on their own streams forked from it.
-static cudaError_t enqueue_step(epd_lb *h, int parity, cudaStream_t s)
+static cudaError_t enqueue_step(epd_lb *h, int parity, cudaStream_t s, int mode = STEP_EXACT)
 {
     cudaError_t e;
     const size_t ng = h->groups.size();
     for (size_t gi = 1; gi < ng; ++gi) {
         if ((e = cudaEventRecord(h->fork_ev[gi - 1], s))) return e;
         if ((e = cudaStreamWaitEvent(h->side[gi - 1], h->fork_ev[gi - 1], 0))) return e;
-        if ((e = enqueue_group(h, gi, parity, h->side[gi - 1]))) return e;
+        if ((e = enqueue_group(h, gi, parity, h->side[gi - 1], mode))) return e;
         if ((e = cudaEventRecord(h->join_ev[gi - 1], h->side[gi - 1]))) return e;
     }
-    if ((e = enqueue_group(h, 0, parity, s))) return e;
+    if ((e = enqueue_group(h, 0, parity, s, mode))) return e;
     for (size_t gi = 1; gi < ng; ++gi)
         if ((e = cudaStreamWaitEvent(s, h->join_ev[gi - 1], 0))) return e;
     return cudaSuccess;
 }
 
+static int capture(epd_lb *h, int par, int mode, cudaGraphExec_t *out)
+{
+    if (*out) {
+        cudaGraphExecDestroy(*out);
+        *out = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+    cudaError_t e = enqueue_step(h, par, h->stream, mode);
+    cudaError_t e2 = cudaStreamEndCapture(h->stream, &graph);
+    if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(h, e, "capturing the time step");
+    }
+    CK(e2, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(e, "cudaGraphInstantiate");
+    return EPD_LB_OK;
+}
+
 static int build_graphs(epd_lb *h)
 {
     for (int par = 0; par < 2; ++par) {
-        if (h->exec[par]) {
-            cudaGraphExecDestroy(h->exec[par]);
-            h->exec[par] = nullptr;
+        if (int rc = capture(h, par, STEP_EXACT, &h->exec[par])) return rc;
+        if (h->sur_on) {
+            if (int rc = capture(h, par, STEP_SURROGATE, &h->exec_sur[par])) return rc;
+            if (int rc = capture(h, par, STEP_CHECK, &h->exec_chk[par])) return rc;
         }
-        cudaGraph_t graph = nullptr;
-        CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
-        cudaError_t e = enqueue_step(h, par, h->stream);
-        cudaError_t e2 = cudaStreamEndCapture(h->stream, &graph);
-        if (e != cudaSuccess) {
-            if (graph) cudaGraphDestroy(graph);
-            return cuda_fail(h, e, "capturing the time step");
-        }
-        CK(e2, "cudaStreamEndCapture");
-        e = cudaGraphInstantiate(&h->exec[par], graph, 0);
-        cudaGraphDestroy(graph);
-        CK(e, "cudaGraphInstantiate");
     }
     return EPD_LB_OK;
 }
@@ -508,7 +559,26 @@ extern "C" int epd_lb_step(epd_lb *h, int64_t nsteps)
 {
     if (!h || nsteps < 0) return EPD_LB_EINVAL;
     for (int64_t k = 0; k < nsteps; ++k) {
-        CK(cudaGraphLaunch(h->exec[h->parity], h->stream), "cudaGraphLaunch");
+        if (!h->sur_on) {
+            CK(cudaGraphLaunch(h->exec[h->parity], h->stream), "cudaGraphLaunch");
+        } else if (h->sur_fallback || h->sur_steps % h->sur_every == 0) {
+            // exact step that also checks the surrogate
+            CK(cudaGraphLaunch(h->exec_chk[h->parity], h->stream), "cudaGraphLaunch");
+            std::vector<double> r(h->groups.size());
+            CK(cudaMemcpyAsync(r.data(), h->sur_resid, r.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "reading the residual");
+            CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+            double m = 0.0;
+            for (double v : r) m = v > m ? v : m;
+            if (h->sur_fallback) ++h->sur_forced;
+            ++h->sur_exact;
+            h->sur_last = m;
+            h->sur_fallback = !(m <= h->sur_tol);
+            ++h->sur_steps;
+        } else {
+            CK(cudaGraphLaunch(h->exec_sur[h->parity], h->stream), "cudaGraphLaunch");
+            ++h->sur_used;
+            ++h->sur_steps;
+        }
         h->parity ^= 1;
     }
     return EPD_LB_OK;
@@ -762,8 +832,11 @@ extern "C" void epd_lb_destroy(epd_lb *h)
 {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < 2; ++k) {
         if (h->exec[k]) cudaGraphExecDestroy(h->exec[k]);
+        if (h->exec_sur[k]) cudaGraphExecDestroy(h->exec_sur[k]);
+        if (h->exec_chk[k]) cudaGraphExecDestroy(h->exec_chk[k]);
+    }
     for (int k = 0; k < 7; ++k)
         if (h->ev[k]) cudaEventDestroy(h->ev[k]);
     for (auto e : h->fork_ev) cudaEventDestroy(e);
@@ -919,5 +992,143 @@ extern "C" int epd_prop_solve_noalloc(const epd_lb_params *p, const double *omeg
     const cudaError_t e = G.prec == EPD_LB_MIXED_FP32 ? noalloc_launch_tables<float>(G, s) : noalloc_launch_tables<double>(G, s);
     if (e != cudaSuccess) return EPD_LB_ECUDA;
     if (launch_solve(G, omega_dev, phi_dev, q_dev, s) != cudaSuccess) return EPD_LB_ECUDA;
+    return EPD_LB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Learned density surrogate
+// ---------------------------------------------------------------------------
+
+static bool sur_shape_ok(const epd_lb_params *p, int batch)
+{
+    return p && validate(*p).empty() && batch > 0 && p->nx % 16 == 0 && p->ny % 8 == 0;
+}
+
+extern "C" int32_t epd_sur_num_params(void) { return sur::num_params(); }
+
+extern "C" int epd_sur_workspace_bytes(int32_t ny, int32_t nx, int32_t batch, int32_t training, size_t *bytes)
+{
+    if (!bytes || batch <= 0 || nx % 16 || ny % 8 || nx <= 0 || ny <= 0) return EPD_LB_EINVAL;
+    sur::Work w;
+    *bytes = sur::carve(w, nullptr, batch, ny, nx, training != 0);
+    return EPD_LB_OK;
+}
+
+static int sur_setup(const epd_lb_params *p, int32_t batch, bool training, void *workspace, size_t bytes, sur::Work &w)
+{
+    if (!sur_shape_ok(p, batch) || !workspace || ((uintptr_t)workspace & 255)) return EPD_LB_EINVAL;
+    if (sur::carve(w, nullptr, batch, p->ny, p->nx, training) > bytes) return EPD_LB_ENOMEM;
+    sur::carve(w, (char *)workspace, batch, p->ny, p->nx, training);
+    return EPD_LB_OK;
+}
+
+extern "C" int epd_sur_forward(const epd_lb_params *p, int32_t batch, const float *params_dev, double s_in, double s_out,
+                               const double *omega_dev, double *phi_dev, void *workspace, size_t workspace_bytes, void *cuda_stream)
+{
+    sur::Work w;
+    if (!params_dev || !omega_dev || !phi_dev) return EPD_LB_EINVAL;
+    if (int rc = sur_setup(p, batch, false, workspace, workspace_bytes, w)) return rc;
+    const double na = (double)std::lround(p->f_a * (double)p->ns) / (double)p->ns;
+    const cudaError_t e = sur::forward(w, params_dev, omega_dev, phi_dev, s_in, s_out, p->phi_p * na, p->phi_p * (1.0 - na),
+                                       1.0 - p->phi_p, (cudaStream_t)cuda_stream);
+    return e == cudaSuccess ? EPD_LB_OK : EPD_LB_ECUDA;
+}
+
+extern "C" int epd_sur_gradients(const epd_lb_params *p, int32_t batch, const float *params_dev, double s_in, double s_out,
+                                 const double *omega_dev, const double *phi_dev, float *grad_dev, double *loss_dev, void *workspace,
+                                 size_t workspace_bytes, void *cuda_stream)
+{
+    sur::Work w;
+    if (!params_dev || !omega_dev || !phi_dev || !grad_dev || !loss_dev) return EPD_LB_EINVAL;
+    if (int rc = sur_setup(p, batch, true, workspace, workspace_bytes, w)) return rc;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (sur::gradients(w, params_dev, omega_dev, phi_dev, s_in, s_out, loss_dev, s) != cudaSuccess) return EPD_LB_ECUDA;
+    if (cudaMemcpyAsync(grad_dev, w.grad, (size_t)sur::num_params() * sizeof(float), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return EPD_LB_ECUDA;
+    return EPD_LB_OK;
+}
+
+extern "C" int epd_sur_train_step(const epd_lb_params *p, int32_t batch, float *params_dev, float *adam_m_dev, float *adam_v_dev,
+                                  int32_t step, float lr, double s_in, double s_out, const double *omega_dev, const double *phi_dev,
+                                  double *loss_dev, void *workspace, size_t workspace_bytes, void *cuda_stream)
+{
+    sur::Work w;
+    if (!params_dev || !adam_m_dev || !adam_v_dev || !omega_dev || !phi_dev || !loss_dev || step < 1) return EPD_LB_EINVAL;
+    if (int rc = sur_setup(p, batch, true, workspace, workspace_bytes, w)) return rc;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (sur::gradients(w, params_dev, omega_dev, phi_dev, s_in, s_out, loss_dev, s) != cudaSuccess) return EPD_LB_ECUDA;
+    if (sur::adam_step(w, params_dev, adam_m_dev, adam_v_dev, step, lr, s) != cudaSuccess) return EPD_LB_ECUDA;
+    return EPD_LB_OK;
+}
+
+static size_t handle_sur_bytes(epd_lb *h)
+{
+    size_t off = 0;
+    off = align_up(off + (size_t)sur::num_params() * sizeof(float));
+    off = align_up(off + (h->groups.size() + 1) * sizeof(double));
+    for (auto &G : h->groups) {
+        sur::Work w;
+        off = align_up(off + sur::carve(w, nullptr, G.g.nruns, G.g.ny, G.g.nx, false));
+    }
+    return off;
+}
+
+extern "C" int epd_lb_surrogate_workspace_bytes(epd_lb *h, size_t *bytes)
+{
+    if (!h || !bytes) return EPD_LB_EINVAL;
+    for (auto &G : h->groups)
+        if (G.g.nx % 16 || G.g.ny % 8) return fail(h, EPD_LB_EINVAL, "the surrogate needs nx % 16 == 0 and ny % 8 == 0");
+    *bytes = handle_sur_bytes(h);
+    return EPD_LB_OK;
+}
+
+extern "C" int epd_lb_set_surrogate(epd_lb *h, const float *params_host, double s_in, double s_out, int32_t exact_every,
+                                    double residual_tol, void *workspace, size_t workspace_bytes)
+{
+    if (!h) return EPD_LB_EINVAL;
+    CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    if (exact_every <= 0) {
+        h->sur_on = false;
+        return EPD_LB_OK;
+    }
+    size_t need = 0;
+    if (int rc = epd_lb_surrogate_workspace_bytes(h, &need)) return rc;
+    if (!params_host || !workspace || workspace_bytes < need || ((uintptr_t)workspace & 255))
+        return fail(h, EPD_LB_EINVAL, "surrogate parameters or workspace missing or too small");
+    char *base = (char *)workspace;
+    size_t off = 0;
+    h->sur_params = (float *)(base + off);
+    off = align_up(off + (size_t)sur::num_params() * sizeof(float));
+    h->sur_resid = (double *)(base + off);
+    off = align_up(off + (h->groups.size() + 1) * sizeof(double));
+    h->sur_work.assign(h->groups.size(), sur::Work());
+    for (size_t gi = 0; gi < h->groups.size(); ++gi) {
+        Group &G = h->groups[gi];
+        const size_t b = sur::carve(h->sur_work[gi], base + off, G.g.nruns, G.g.ny, G.g.nx, false);
+        off = align_up(off + b);
+    }
+    CK(cudaMemcpyAsync(h->sur_params, params_host, (size_t)sur::num_params() * sizeof(float), cudaMemcpyHostToDevice, h->stream),
+       "copy surrogate parameters");
+    CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    h->sur_on = true;
+    h->sur_every = exact_every;
+    h->sur_tol = residual_tol;
+    h->sur_s_in = s_in;
+    h->sur_s_out = s_out;
+    h->sur_steps = h->sur_exact = h->sur_used = h->sur_forced = 0;
+    h->sur_fallback = false;
+    h->sur_last = 0.0;
+    return build_graphs(h);
+}
+
+extern "C" int epd_lb_surrogate_stats(epd_lb *h, double *out)
+{
+    if (!h || !out) return EPD_LB_EINVAL;
+    out[0] = (double)h->sur_steps;
+    out[1] = (double)h->sur_exact;
+    out[2] = (double)h->sur_used;
+    out[3] = (double)h->sur_forced;
+    out[4] = h->sur_last;
+    out[5] = h->sur_fallback ? 1.0 : 0.0;
     return EPD_LB_OK;
 }

@@ -1,0 +1,632 @@
+// surrogate.cu -- learned stand-in for the single-chain solve (a small
+// convolutional network from the fields omega to the polymer densities) with
+// BF16 tensor-core training and inference kernels, FP32 accumulation.
+//
+// Network (periodic grid, 3x3 kernels, circular padding):
+//   x0 = s_in (omega_c - <omega_c>), c = A, B, S          (3 channels)
+//   y_l = tanh(W_l * y_{l-1} + b_l), l = 1, 2, 3          (32 channels)
+//   y_4 = W_4 * y_3 + b_4                                 (2 channels)
+//   Phi_A = <Phi_A> + s_out (y_4,0 - <y_4,0>), Phi_B likewise with y_4,1, where
+//   <Phi_A> = phi_p N_A/N_s and <Phi_B> = phi_p (1 - N_A/N_s) are the exact
+//   means (Sec. 2, Eqs. (9)-(10) conserve them); Phi_S is the exact local
+//   expression of Eq. (11).
+//
+// Every convolution is an implicit GEMM on mma.sync m16n8k16 (BF16 inputs,
+// FP32 accumulation): activations are NHWC BF16 with the channel count padded
+// to a multiple of 16, a CTA computes an 8 x 16 pixel tile for all output
+// channels from a shared-memory halo tile, K runs over taps x input channels.
+// The input gradient is the same convolution of the output gradient with the
+// flipped, transposed weights; the weight gradient is a GEMM over pixels per
+// tap.  Rounding to BF16 happens where the tensor cores read: weights,
+// activations and the output gradients.
+#include <cstdint>
+#include <algorithm>
+#include <cmath>
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "engine.h"
+#include "surrogate.h"
+
+namespace epdlb {
+namespace sur {
+
+constexpr int TH = 8, TW = 16, TP = TH * TW;  // pixel tile
+constexpr int HH = TH + 2, HW = TW + 2;       // halo tile
+
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b)
+{
+    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Epilogue modes of the convolution.
+enum { EP_TANH = 0, EP_LINEAR = 1, EP_DX = 2 };
+
+struct ConvArgs {
+    const __nv_bfloat16 *in;    // [b][y][x][KP] (KP = input channels, padded)
+    const __nv_bfloat16 *w;     // [tap][NP][KP]
+    const float *bias;          // [NP] (EP_TANH, EP_LINEAR) or null
+    __nv_bfloat16 *out_bf;      // [b][y][x][NP] BF16 output (EP_TANH, EP_DX)
+    float *out_f;               // [b][y][x][NP] FP32 output (EP_TANH when training, EP_LINEAR)
+    const float *yprev;         // EP_DX: tanh output of the layer below, [b][y][x][NP] FP32
+    int nx, ny, logx, logy;
+    int nreal;                  // output channels actually used (the rest are written as 0)
+};
+
+// One 8 x 16 pixel tile, all NP output channels; 4 warps, warp w owns pixel
+// rows 2w and 2w+1 (two m16 tiles).  KP, NP multiples of 16 and 8.
+template <int KP, int NP, int MODE>
+__global__ void __launch_bounds__(128) conv3x3(ConvArgs a)
+{
+    constexpr int KS = KP + 8;  // padded channel stride in shared memory (halves)
+    __shared__ __align__(16) __nv_bfloat16 tile[HH * HW * KS];
+    __shared__ __align__(16) __nv_bfloat16 wsm[9 * NP * KS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tx0 = blockIdx.x * TW, ty0 = blockIdx.y * TH, b = blockIdx.z;
+    const long long n = (long long)a.nx * a.ny;
+    const __nv_bfloat16 *in = a.in + (size_t)b * n * KP;
+    // halo tile with circular wrap, 16-byte chunks of channels
+    for (int e = tid; e < HH * HW * (KP / 8); e += 128) {
+        const int pix = e / (KP / 8), ch = (e % (KP / 8)) * 8;
+        const int hy = pix / HW, hx = pix % HW;
+        const int gy = (ty0 + hy - 1) & (a.ny - 1), gx = (tx0 + hx - 1) & (a.nx - 1);
+        *reinterpret_cast<uint4 *>(&tile[pix * KS + ch]) = *reinterpret_cast<const uint4 *>(&in[((size_t)gy * a.nx + gx) * KP + ch]);
+    }
+    for (int e = tid; e < 9 * NP * (KP / 8); e += 128) {
+        const int row = e / (KP / 8), ch = (e % (KP / 8)) * 8;
+        *reinterpret_cast<uint4 *>(&wsm[row * KS + ch]) = *reinterpret_cast<const uint4 *>(&a.w[(size_t)row * KP + ch]);
+    }
+    __syncthreads();
+
+    const int g = lane >> 2, t = lane & 3;
+    float acc[2][NP / 8][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < NP / 8; ++nt)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[mt][nt][i] = 0.f;
+
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+        const int dy = tap / 3, dx = tap % 3;  // halo offsets 0..2 (i.e. -1..+1)
+#pragma unroll
+        for (int kc = 0; kc < KP / 16; ++kc) {
+            uint32_t af[2][4];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                const int py = 2 * warp + mt;  // pixel row in the tile
+                const int p0 = ((py + dy) * HW + g + dx) * KS + kc * 16 + 2 * t;
+                const int p1 = ((py + dy) * HW + g + 8 + dx) * KS + kc * 16 + 2 * t;
+                af[mt][0] = *reinterpret_cast<const uint32_t *>(&tile[p0]);
+                af[mt][1] = *reinterpret_cast<const uint32_t *>(&tile[p1]);
+                af[mt][2] = *reinterpret_cast<const uint32_t *>(&tile[p0 + 8]);
+                af[mt][3] = *reinterpret_cast<const uint32_t *>(&tile[p1 + 8]);
+            }
+#pragma unroll
+            for (int nt = 0; nt < NP / 8; ++nt) {
+                uint32_t bf[2];
+                const int q = (tap * NP + nt * 8 + g) * KS + kc * 16 + 2 * t;
+                bf[0] = *reinterpret_cast<const uint32_t *>(&wsm[q]);
+                bf[1] = *reinterpret_cast<const uint32_t *>(&wsm[q + 8]);
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) mma16816(acc[mt][nt], af[mt], bf);
+            }
+        }
+    }
+
+    // epilogue: rows g (c0, c1) and g + 8 (c2, c3) of each m tile, channels 2t, 2t+1
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+        const int py = ty0 + 2 * warp + mt;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int px = tx0 + g + 8 * half;
+            const size_t pix = (size_t)b * n + (size_t)py * a.nx + px;
+#pragma unroll
+            for (int nt = 0; nt < NP / 8; ++nt) {
+                const int c = nt * 8 + 2 * t;
+                float v0 = acc[mt][nt][2 * half], v1 = acc[mt][nt][2 * half + 1];
+                if (MODE != EP_DX && a.bias) {
+                    if (c < a.nreal) v0 += a.bias[c];
+                    if (c + 1 < a.nreal) v1 += a.bias[c + 1];
+                }
+                if (MODE == EP_TANH) {
+                    v0 = tanhf(v0);
+                    v1 = tanhf(v1);
+                } else if (MODE == EP_DX) {
+                    // dZ of the layer below: dY (1 - y^2)
+                    const float2 yp = *reinterpret_cast<const float2 *>(&a.yprev[pix * NP + c]);
+                    v0 *= 1.f - yp.x * yp.x;
+                    v1 *= 1.f - yp.y * yp.y;
+                }
+                if (c >= a.nreal) v0 = 0.f;
+                if (c + 1 >= a.nreal) v1 = 0.f;
+                if (a.out_bf)
+                    *reinterpret_cast<uint32_t *>(&a.out_bf[pix * NP + c]) = pack2(__float2bfloat16_rn(v0), __float2bfloat16_rn(v1));
+                if (a.out_f) *reinterpret_cast<float2 *>(&a.out_f[pix * NP + c]) = make_float2(v0, v1);
+            }
+        }
+    }
+}
+
+// Weight gradient of one layer: dW[tap][co][ci] = sum_p dZ[p][co] x[p + off(tap)][ci]
+// over an 8 x 16 tile per step, `tiles` consecutive tiles per CTA; 9 warps, warp
+// = tap.  Partial sums per CTA to part[blk][tap][co][ci] (deterministic
+// reduction later).  CO, CI multiples of 16 and 8.
+template <int CI, int CO>
+__global__ void __launch_bounds__(288) conv3x3_dw(const __nv_bfloat16 *x, const __nv_bfloat16 *dz, float *part, int nx, int ny,
+                                                 int tiles_x, int tiles_per_cta, int ntiles_total)
+{
+    constexpr int CS = CI + 8, DS = TP + 8;
+    __shared__ __align__(16) __nv_bfloat16 tile[HH * HW * CS];
+    __shared__ __align__(16) __nv_bfloat16 dzt[CO * DS];  // [co][p], transposed
+    const int tid = threadIdx.x, lane = tid & 31, tap = tid >> 5;
+    const int g = lane >> 2, t = lane & 3, dy = tap / 3, dx = tap % 3;
+    const long long n = (long long)nx * ny;
+    float acc[CO / 16][CI / 8][4];
+#pragma unroll
+    for (int mt = 0; mt < CO / 16; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < CI / 8; ++nt)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[mt][nt][i] = 0.f;
+    const int tiles_per_img = tiles_x * (ny / TH);
+    for (int it = 0; it < tiles_per_cta; ++it) {
+        const int tidx = blockIdx.x * tiles_per_cta + it;
+        if (tidx >= ntiles_total) break;
+        const int b = tidx / tiles_per_img, r = tidx % tiles_per_img;
+        const int ty0 = (r / tiles_x) * TH, tx0 = (r % tiles_x) * TW;
+        const __nv_bfloat16 *xin = x + (size_t)b * n * CI;
+        const __nv_bfloat16 *dzin = dz + (size_t)b * n * CO;
+        __syncthreads();
+        for (int e = tid; e < HH * HW * (CI / 8); e += 288) {
+            const int pix = e / (CI / 8), ch = (e % (CI / 8)) * 8;
+            const int hy = pix / HW, hx = pix % HW;
+            const int gy = (ty0 + hy - 1) & (ny - 1), gx = (tx0 + hx - 1) & (nx - 1);
+            *reinterpret_cast<uint4 *>(&tile[pix * CS + ch]) = *reinterpret_cast<const uint4 *>(&xin[((size_t)gy * nx + gx) * CI + ch]);
+        }
+        for (int e = tid; e < TP * CO; e += 288) {
+            const int p = e / CO, co = e % CO;
+            const int gy = ty0 + p / TW, gx = tx0 + p % TW;
+            dzt[co * DS + p] = dzin[((size_t)gy * nx + gx) * CO + co];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kc = 0; kc < TP / 16; ++kc) {  // 16 pixels = one tile row
+            const int py = kc;
+            uint32_t af[CO / 16][4];
+#pragma unroll
+            for (int mt = 0; mt < CO / 16; ++mt) {
+                const int r0 = (mt * 16 + g) * DS + kc * 16 + 2 * t, r1 = r0 + 8 * DS;
+                af[mt][0] = *reinterpret_cast<const uint32_t *>(&dzt[r0]);
+                af[mt][1] = *reinterpret_cast<const uint32_t *>(&dzt[r1]);
+                af[mt][2] = *reinterpret_cast<const uint32_t *>(&dzt[r0 + 8]);
+                af[mt][3] = *reinterpret_cast<const uint32_t *>(&dzt[r1 + 8]);
+            }
+#pragma unroll
+            for (int nt = 0; nt < CI / 8; ++nt) {
+                const int ci = nt * 8 + g;
+                const int k0 = 2 * t, k1 = 2 * t + 8;  // pixel columns in the row
+                const __nv_bfloat16 *row = &tile[((py + dy) * HW + dx) * CS + ci];
+                uint32_t bf[2];
+                bf[0] = pack2(row[(k0)*CS], row[(k0 + 1) * CS]);
+                bf[1] = pack2(row[(k1)*CS], row[(k1 + 1) * CS]);
+#pragma unroll
+                for (int mt = 0; mt < CO / 16; ++mt) mma16816(acc[mt][nt], af[mt], bf);
+            }
+        }
+    }
+    float *out = part + (size_t)blockIdx.x * 9 * CO * CI + (size_t)tap * CO * CI;
+#pragma unroll
+    for (int mt = 0; mt < CO / 16; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < CI / 8; ++nt) {
+            const int co = mt * 16 + g, ci = nt * 8 + 2 * t;
+            out[co * CI + ci] = acc[mt][nt][0];
+            out[co * CI + ci + 1] = acc[mt][nt][1];
+            out[(co + 8) * CI + ci] = acc[mt][nt][2];
+            out[(co + 8) * CI + ci + 1] = acc[mt][nt][3];
+        }
+}
+
+// ---------------------------------------------------------------------------
+// small kernels: input preparation, output, loss, reductions, optimiser
+// ---------------------------------------------------------------------------
+
+// Per (sample, channel) mean of a planar FP64 field: one block each, fixed order.
+__global__ void __launch_bounds__(256) channel_means(const double *f, int nch, long long n, double *mean)
+{
+    __shared__ double red[32];
+    const double *p = f + (size_t)blockIdx.x * n;
+    double s = 0.0;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) s += p[i];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) mean[blockIdx.x] = s / (double)n;
+}
+
+// x0[b][p][16] = s_in (omega_c - <omega_c>) for c < 3, 0 for the padding.
+__global__ void prep_input(const double *omega, const double *mean, double s_in, long long n, int nb, __nv_bfloat16 *x0)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * nb) return;
+    const long long b = i / n, p = i % n;
+    __align__(16) __nv_bfloat16 v[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16_rn(0.f);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[c] = __float2bfloat16_rn((float)(s_in * (omega[(b * 3 + c) * n + p] - mean[b * 3 + c])));
+    uint4 *dst = reinterpret_cast<uint4 *>(x0 + (size_t)i * 16);
+    dst[0] = *reinterpret_cast<uint4 *>(&v[0]);
+    dst[1] = *reinterpret_cast<uint4 *>(&v[8]);
+}
+
+// Mean of the two output channels of y4 ([b][p][8] FP32): one block per (b, c).
+__global__ void __launch_bounds__(256) out_means(const float *y4, long long n, double *mean)
+{
+    __shared__ double red[32];
+    const int b = blockIdx.x / 2, c = blockIdx.x % 2;
+    double s = 0.0;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) s += (double)y4[((size_t)b * n + i) * 8 + c];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) mean[blockIdx.x] = s / (double)n;
+}
+
+// Densities from the network output: Phi_A, Phi_B with exact means, Phi_S from
+// Eq. (11) (exp(-w_S) in FP64, Q_S from the per-sample sums in qs_sum).
+__global__ void densities_out(const float *y4, const double *ymean, const double *omega, const double *qs_mean, double s_out,
+                              double pa_bar, double pb_bar, double ps_bar, long long n, int nb, double *phi)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * nb) return;
+    const long long b = i / n, p = i % n;
+    const float2 y = *reinterpret_cast<const float2 *>(&y4[(size_t)i * 8]);
+    phi[(b * 3 + 0) * n + p] = pa_bar + s_out * ((double)y.x - ymean[2 * b]);
+    phi[(b * 3 + 1) * n + p] = pb_bar + s_out * ((double)y.y - ymean[2 * b + 1]);
+    phi[(b * 3 + 2) * n + p] = ps_bar * exp(-omega[(b * 3 + 2) * n + p]) / qs_mean[b];
+}
+
+__global__ void __launch_bounds__(256) solvent_q(const double *omega, long long n, double *qs_mean)
+{
+    __shared__ double red[32];
+    const double *w = omega + ((size_t)blockIdx.x * 3 + 2) * n;
+    double s = 0.0;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) s += exp(-w[i]);
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) qs_mean[blockIdx.x] = s / (double)n;
+}
+
+// Loss and output gradient: targets t_c = (Phi_c - <Phi_c>) / s_out for
+// c = A, B; loss = mean over samples, channels, pixels of (y - t)^2; dZ4 =
+// 2 (y - t) / count in BF16 ([b][p][16], channels >= 2 zero).  Per-block
+// partial loss sums to lpart.
+__global__ void __launch_bounds__(256) loss_grad(const float *y4, const double *phi_t, const double *tmean, double s_out, long long n,
+                                                 int nb, __nv_bfloat16 *dz4, double *lpart)
+{
+    __shared__ double red[32];
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double l = 0.0;
+    if (i < n * nb) {
+        const long long b = i / n, p = i % n;
+        const double cnt = 2.0 * (double)n * (double)nb;
+        __align__(16) __nv_bfloat16 v[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16_rn(0.f);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const double tc = (phi_t[(b * 3 + c) * n + p] - tmean[b * 3 + c]) / s_out;
+            const double d = (double)y4[(size_t)i * 8 + c] - tc;
+            l += d * d;
+            v[c] = __float2bfloat16_rn((float)(2.0 * d / cnt));
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(dz4 + (size_t)i * 16);
+        dst[0] = *reinterpret_cast<uint4 *>(&v[0]);
+        dst[1] = *reinterpret_cast<uint4 *>(&v[8]);
+    }
+    l = block_sum(l, red);
+    if (threadIdx.x == 0) lpart[blockIdx.x] = l;
+}
+
+// Sum of `cnt` per-block partials (fixed order) -> out[0] / denom.
+__global__ void __launch_bounds__(256) sum_parts(const double *part, int cnt, double denom, double *out)
+{
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) s += part[i];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) out[0] = s / denom;
+}
+
+// Reduce dW partials [nblk][9][CO][CI] and dB (sum of dZ over pixels) into the
+// gradient of the packed master parameters of one layer.
+__global__ void reduce_dw(const float *part, int nblk, int co_real, int ci_real, int CO, int CI, float *gw)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;  // over co_real * ci_real * 9 (master layout [co][ci][tap])
+    if (i >= co_real * ci_real * 9) return;
+    const int co = i / (ci_real * 9), ci = (i / 9) % ci_real, tap = i % 9;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += (double)part[((size_t)b * 9 + tap) * CO * CI + (size_t)co * CI + ci];
+    gw[i] = (float)s;
+}
+
+__global__ void __launch_bounds__(256) bias_grad(const __nv_bfloat16 *dz, long long npix, int CO, int co_real, float *gb)
+{
+    __shared__ double red[32];
+    const int co = blockIdx.x;
+    double s = 0.0;
+    for (long long p = threadIdx.x; p < npix; p += blockDim.x) s += (double)__bfloat162float(dz[(size_t)p * CO + co]);
+    s = block_sum(s, red);
+    if (threadIdx.x == 0 && co < co_real) gb[co] = (float)s;
+}
+
+// Adam on the FP32 master parameters (Kingma and Ba, 2015).
+__global__ void adam(float *w, const float *gw, float *m, float *v, int np, float lr, float b1, float b2, float eps, float c1, float c2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    const float gi = gw[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi, vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// Pack master weights [co][ci][tap] of one layer to the forward layout
+// [tap][NP][KP] (BF16) and, if wb is given, the input-gradient layout
+// [tap][KP2][NP2] = flipped taps, transposed channels.
+__global__ void pack_weights(const float *wm, int co_real, int ci_real, int NP, int KP, __nv_bfloat16 *wf, __nv_bfloat16 *wb, int NPB,
+                             int KPB)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int tot_f = 9 * NP * KP;
+    if (i < tot_f) {
+        const int tap = i / (NP * KP), co = (i / KP) % NP, ci = i % KP;
+        const float v = (co < co_real && ci < ci_real) ? wm[((size_t)co * ci_real + ci) * 9 + tap] : 0.f;
+        wf[i] = __float2bfloat16_rn(v);
+    }
+    if (wb && i < 9 * NPB * KPB) {
+        // input-gradient conv: output channel = ci (< NPB), input channel = co (< KPB)
+        const int tap = i / (NPB * KPB), ci = (i / KPB) % NPB, co = i % KPB;
+        const int ftap = 8 - tap;
+        const float v = (co < co_real && ci < ci_real) ? wm[((size_t)co * ci_real + ci) * 9 + ftap] : 0.f;
+        wb[i] = __float2bfloat16_rn(v);
+    }
+}
+
+} // namespace sur
+} // namespace epdlb
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+namespace epdlb {
+namespace sur {
+
+// storage channels (padded) of each layer's input and output
+static const int kKP[kLayers] = {16, 32, 32, 32};
+static const int kNP[kLayers] = {32, 32, 32, 8};
+
+int num_params()
+{
+    int s = 0;
+    for (int l = 0; l < kLayers; ++l) s += kCout[l] * kCin[l] * 9 + kCout[l];
+    return s;
+}
+int param_offset_w(int layer)
+{
+    int s = 0;
+    for (int l = 0; l < layer; ++l) s += kCout[l] * kCin[l] * 9 + kCout[l];
+    return s;
+}
+int param_offset_b(int layer) { return param_offset_w(layer) + kCout[layer] * kCin[layer] * 9; }
+
+static size_t al(size_t v) { return (v + 255) & ~(size_t)255; }
+
+size_t carve(Work &w, char *base, int nb, int ny, int nx, bool training)
+{
+    w.nb = nb;
+    w.nx = nx;
+    w.ny = ny;
+    w.n = (long long)nx * ny;
+    w.training = training;
+    const size_t np = (size_t)nb * w.n;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> void * {
+        off = al(off);
+        void *p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    };
+    w.x0 = take(np * 16 * 2);
+    for (int l = 0; l < 3; ++l) w.y[l] = take(np * 32 * 2);
+    w.y4 = take(np * 8 * 4);
+    for (int l = 0; l < kLayers; ++l) w.wf[l] = take((size_t)9 * kNP[l] * kKP[l] * 2);
+    w.means = (double *)take((size_t)nb * 3 * sizeof(double));
+    w.ymean = (double *)take((size_t)nb * 2 * sizeof(double));
+    w.qs = (double *)take((size_t)nb * sizeof(double));
+    if (training) {
+        for (int l = 0; l < 3; ++l) w.yf[l] = take(np * 32 * 4);
+        w.dz[0] = take(np * 32 * 2);
+        w.dz[1] = take(np * 32 * 2);
+        w.dz4 = take(np * 16 * 2);
+        for (int l = 1; l < kLayers; ++l) w.wb[l] = take((size_t)9 * 32 * kNP[l] * 2 + (size_t)9 * 32 * 16 * 2);
+        const long long tiles = (long long)nb * (nx / TW) * (ny / TH);
+        w.nblk_dw = (int)std::min<long long>(512, tiles);
+        w.dwpart = (float *)take((size_t)w.nblk_dw * 9 * 32 * 32 * sizeof(float));
+        w.grad = (float *)take((size_t)num_params() * sizeof(float));
+        w.tmean = (double *)take((size_t)nb * 3 * sizeof(double));
+        w.lpart = (double *)take((size_t)((np + 255) / 256 + 1) * sizeof(double));
+    } else {
+        for (int l = 0; l < 3; ++l) w.yf[l] = nullptr;
+        w.dz[0] = w.dz[1] = w.dz4 = nullptr;
+        for (int l = 0; l < kLayers; ++l) w.wb[l] = nullptr;
+        w.dwpart = w.grad = nullptr;
+        w.tmean = w.lpart = nullptr;
+        w.nblk_dw = 0;
+    }
+    return al(off);
+}
+
+static unsigned blocks(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+static cudaError_t pack_all(Work &w, const float *params, bool backward, cudaStream_t s)
+{
+    for (int l = 0; l < kLayers; ++l) {
+        const int tot_f = 9 * kNP[l] * kKP[l];
+        // input-gradient weights: output channels = this layer's inputs (32),
+        // input channels = this layer's outputs as stored (dZ: 32, or 16 for the last layer)
+        const int npb = 32, kpb = (l == kLayers - 1) ? 16 : 32;
+        const bool bw = backward && l > 0;
+        const int tot = bw ? std::max(tot_f, 9 * npb * kpb) : tot_f;
+        pack_weights<<<blocks(tot), 256, 0, s>>>(params + param_offset_w(l), kCout[l], kCin[l], kNP[l], kKP[l],
+                                                 reinterpret_cast<__nv_bfloat16 *>(w.wf[l]),
+                                                 bw ? reinterpret_cast<__nv_bfloat16 *>(w.wb[l]) : nullptr, npb, kpb);
+    }
+    return cudaGetLastError();
+}
+
+template <int KP, int NP, int MODE>
+static void conv(Work &w, const void *in, const void *wt, const float *bias, void *out_bf, float *out_f, const float *yprev, int nreal,
+                 cudaStream_t s)
+{
+    ConvArgs a;
+    a.in = reinterpret_cast<const __nv_bfloat16 *>(in);
+    a.w = reinterpret_cast<const __nv_bfloat16 *>(wt);
+    a.bias = bias;
+    a.out_bf = reinterpret_cast<__nv_bfloat16 *>(out_bf);
+    a.out_f = out_f;
+    a.yprev = yprev;
+    a.nx = w.nx;
+    a.ny = w.ny;
+    a.logx = ilog2(w.nx);
+    a.logy = ilog2(w.ny);
+    a.nreal = nreal;
+    conv3x3<KP, NP, MODE><<<dim3(w.nx / TW, w.ny / TH, w.nb), 128, 0, s>>>(a);
+}
+
+static cudaError_t forward_layers(Work &w, const float *params, cudaStream_t s)
+{
+    const bool tr = w.training;
+    conv<16, 32, EP_TANH>(w, w.x0, w.wf[0], params + param_offset_b(0), w.y[0], tr ? (float *)w.yf[0] : nullptr, nullptr, 32, s);
+    conv<32, 32, EP_TANH>(w, w.y[0], w.wf[1], params + param_offset_b(1), w.y[1], tr ? (float *)w.yf[1] : nullptr, nullptr, 32, s);
+    conv<32, 32, EP_TANH>(w, w.y[1], w.wf[2], params + param_offset_b(2), w.y[2], tr ? (float *)w.yf[2] : nullptr, nullptr, 32, s);
+    conv<32, 8, EP_LINEAR>(w, w.y[2], w.wf[3], params + param_offset_b(3), nullptr, (float *)w.y4, nullptr, 2, s);
+    return cudaGetLastError();
+}
+
+cudaError_t forward(Work &w, const float *params, const double *omega, double *phi, double s_in, double s_out, double pa_bar,
+                    double pb_bar, double ps_bar, cudaStream_t s)
+{
+    cudaError_t e;
+    if ((e = pack_all(w, params, false, s))) return e;
+    channel_means<<<w.nb * 3, 256, 0, s>>>(omega, 3, w.n, w.means);
+    prep_input<<<blocks(w.n * w.nb), 256, 0, s>>>(omega, w.means, s_in, w.n, w.nb, reinterpret_cast<__nv_bfloat16 *>(w.x0));
+    if ((e = forward_layers(w, params, s))) return e;
+    out_means<<<w.nb * 2, 256, 0, s>>>((const float *)w.y4, w.n, w.ymean);
+    solvent_q<<<w.nb, 256, 0, s>>>(omega, w.n, w.qs);
+    densities_out<<<blocks(w.n * w.nb), 256, 0, s>>>((const float *)w.y4, w.ymean, omega, w.qs, s_out, pa_bar, pb_bar, ps_bar, w.n, w.nb,
+                                                     phi);
+    return cudaGetLastError();
+}
+
+template <int CI, int CO>
+static void dw(Work &w, const void *x, const void *dzp, cudaStream_t s)
+{
+    const int tiles_x = w.nx / TW;
+    const int ntiles = w.nb * tiles_x * (w.ny / TH);
+    const int per = (ntiles + w.nblk_dw - 1) / w.nblk_dw;
+    const int nblk = (ntiles + per - 1) / per;
+    conv3x3_dw<CI, CO><<<nblk, 288, 0, s>>>(reinterpret_cast<const __nv_bfloat16 *>(x), reinterpret_cast<const __nv_bfloat16 *>(dzp),
+                                            w.dwpart, w.nx, w.ny, tiles_x, per, ntiles);
+    w.nblk_dw = nblk;
+}
+
+static void layer_grads(Work &w, int l, const void *x, const void *dzp, int CO, int CI, cudaStream_t s)
+{
+    const int ntiles_cap = w.nblk_dw;
+    if (CI == 16 && CO == 32) dw<16, 32>(w, x, dzp, s);
+    else if (CI == 32 && CO == 32) dw<32, 32>(w, x, dzp, s);
+    else dw<32, 16>(w, x, dzp, s);
+    const int nw = kCout[l] * kCin[l] * 9;
+    reduce_dw<<<blocks(nw), 256, 0, s>>>(w.dwpart, w.nblk_dw, kCout[l], kCin[l], CO, CI, w.grad + param_offset_w(l));
+    bias_grad<<<CO, 256, 0, s>>>(reinterpret_cast<const __nv_bfloat16 *>(dzp), (long long)w.nb * w.n, CO, kCout[l],
+                                 w.grad + param_offset_b(l));
+    w.nblk_dw = ntiles_cap;
+}
+
+cudaError_t gradients(Work &w, const float *params, const double *omega, const double *phi_t, double s_in, double s_out,
+                      double *loss_dev, cudaStream_t s)
+{
+    cudaError_t e;
+    if ((e = pack_all(w, params, true, s))) return e;
+    channel_means<<<w.nb * 3, 256, 0, s>>>(omega, 3, w.n, w.means);
+    prep_input<<<blocks(w.n * w.nb), 256, 0, s>>>(omega, w.means, s_in, w.n, w.nb, reinterpret_cast<__nv_bfloat16 *>(w.x0));
+    if ((e = forward_layers(w, params, s))) return e;
+    channel_means<<<w.nb * 3, 256, 0, s>>>(phi_t, 3, w.n, w.tmean);
+    const unsigned lb = blocks(w.n * w.nb);
+    loss_grad<<<lb, 256, 0, s>>>((const float *)w.y4, phi_t, w.tmean, s_out, w.n, w.nb, reinterpret_cast<__nv_bfloat16 *>(w.dz4),
+                                 w.lpart);
+    sum_parts<<<1, 256, 0, s>>>(w.lpart, (int)lb, 2.0 * (double)w.n * w.nb, loss_dev);
+    // layer 4: dW from y3 and dZ4; dZ3 = (W4^T dZ4) (1 - y3^2)
+    layer_grads(w, 3, w.y[2], w.dz4, 16, 32, s);
+    conv<16, 32, EP_DX>(w, w.dz4, w.wb[3], nullptr, w.dz[0], nullptr, (const float *)w.yf[2], 32, s);
+    // layer 3
+    layer_grads(w, 2, w.y[1], w.dz[0], 32, 32, s);
+    conv<32, 32, EP_DX>(w, w.dz[0], w.wb[2], nullptr, w.dz[1], nullptr, (const float *)w.yf[1], 32, s);
+    // layer 2
+    layer_grads(w, 1, w.y[0], w.dz[1], 32, 32, s);
+    conv<32, 32, EP_DX>(w, w.dz[1], w.wb[1], nullptr, w.dz[0], nullptr, (const float *)w.yf[0], 32, s);
+    // layer 1
+    layer_grads(w, 0, w.x0, w.dz[0], 32, 16, s);
+    return cudaGetLastError();
+}
+
+cudaError_t adam_step(Work &w, float *params, float *m, float *v, int step, float lr, cudaStream_t s)
+{
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - (float)std::pow((double)b1, (double)step), c2 = 1.f - (float)std::pow((double)b2, (double)step);
+    const int np = num_params();
+    adam<<<blocks(np), 256, 0, s>>>(params, w.grad, m, v, np, lr, b1, b2, 1e-8f, c1, c2);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) rms_diff(const double *a, const double *b, long long n3, double *out)
+{
+    __shared__ double red[32];
+    const double *pa = a + (size_t)blockIdx.x * n3, *pb = b + (size_t)blockIdx.x * n3;
+    double s = 0.0;
+    for (long long i = threadIdx.x; i < n3; i += blockDim.x) {
+        const double d = pa[i] - pb[i];
+        s += d * d;
+    }
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) out[blockIdx.x] = sqrt(s / (double)n3);
+}
+
+__global__ void max_of(const double *v, int cnt, double *out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double m = 0.0;
+        for (int i = 0; i < cnt; ++i) m = v[i] > m ? v[i] : m;
+        out[0] = m;
+    }
+}
+
+cudaError_t residual_rms(const double *phi_a, const double *phi_b, long long n, int nb, double *tmp, double *out, cudaStream_t s)
+{
+    rms_diff<<<nb, 256, 0, s>>>(phi_a, phi_b, 3 * n, tmp);
+    max_of<<<1, 32, 0, s>>>(tmp, nb, out);
+    return cudaGetLastError();
+}
+
+} // namespace sur
+} // namespace epdlb

@@ -1,0 +1,118 @@
+"""Learned density surrogate on the GPU: forward and gradients against the
+oracle's FP64 restatement (with the GPU's bfloat16 rounding points), training
+on exact (omega, Phi) pairs, its gain over the trivial prediction, and the
+exact-every-k controller of the time stepper."""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1804_02883_gb300 as P
+from paper_1804_02883_gb300 import surrogate as S
+from paper_1804_02883_gb300 import workloads as W
+from oracle import surrogate as OS
+from helpers import oracle_params
+
+pytestmark = pytest.mark.gpu
+
+
+def rand_params(seed):
+    rng = np.random.default_rng(seed)
+    parts = []
+    for ci, co in OS.LAYERS:
+        parts += [rng.standard_normal(co * ci * 9) / np.sqrt(9 * ci), 0.1 * rng.standard_normal(co)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    P.lib()
+    return t
+
+
+@pytest.mark.parametrize("ny,nx", [(32, 64), (64, 32), (16, 16)])
+def test_forward_matches_oracle(torch, ny, nx):
+    run = P.RunParams(nx=nx, ny=ny, ns=8, precision=P.MIXED_FP32, phi_p=0.2, f_a=0.5)
+    p = rand_params(11)
+    om = 0.01 * np.random.default_rng(ny + nx).standard_normal((2, 3, ny, nx))
+    sur = S.Surrogate(run, 2, params=p, s_in=100.0, s_out=1e-3)
+    phi = sur.forward(torch.from_numpy(om).cuda()).cpu().numpy()
+    for b in range(2):
+        want = OS.densities(p.astype(np.float64), om[b], 100.0, 1e-3, 0.2, 0.5, emulate_bf16=True)
+        for c in range(2):
+            spread = np.abs(want[c] - want[c].mean()).max()
+            # FP32 accumulation order and tanhf vs the FP64 oracle can move a value
+            # across a bfloat16 rounding boundary (relative 2^-8) here and there
+            assert np.abs(phi[b, c] - want[c]).max() < 3e-3 * spread
+            assert abs(phi[b, c].mean() - want[c].mean()) < 1e-15
+        assert np.abs(phi[b, 2] - want[2]).max() < 1e-6 * want[2].max()
+
+
+def test_gradients_match_oracle(torch):
+    run = P.RunParams(nx=64, ny=32, ns=8, precision=P.MIXED_FP32, phi_p=0.2)
+    p = rand_params(11)
+    rng = np.random.default_rng(0)
+    om = 0.01 * rng.standard_normal((2, 3, 32, 64))
+    phs = np.stack([OS.densities(rand_params(12).astype(np.float64), om[b], 100.0, 1e-3, 0.2, 0.5) for b in range(2)])
+    sur = S.Surrogate(run, 2, params=p, s_in=100.0, s_out=1e-3)
+    g, loss = sur.gradients(torch.from_numpy(om).cuda(), torch.from_numpy(phs).cuda())
+    g = g.cpu().numpy()
+    lo, go = OS.loss_and_grad(p.astype(np.float64), list(om), list(phs), 100.0, 1e-3, emulate_bf16=True)
+    assert abs(loss / lo - 1) < 1e-5
+    assert np.linalg.norm(g - go) / np.linalg.norm(go) < 1e-3
+
+
+def exact_pairs(torch, run, count, seed):
+    """(omega, Phi) of exact single-chain solves on quench-like fields."""
+    h = P.EpdLb([run])
+    oms, phs = [], []
+    for k in range(count):
+        om = W.random_omega(run.ny, run.nx, seed=seed + k, amp=3e-3)
+        phi, _ = h.solve(0, om)
+        oms.append(om)
+        phs.append(phi)
+    h.close()
+    return np.stack(oms), np.stack(phs)
+
+
+def test_training_beats_the_trivial_prediction(torch):
+    # what the network gains over the method without it: after training on
+    # exact pairs, its densities on held-out fields are much closer to the
+    # exact solve than the homogeneous prediction Phi = <Phi>
+    run = P.RunParams(nx=64, ny=64, ns=16, precision=P.MIXED_FP32, phi_p=0.2, f_a=0.5)
+    om, ph = exact_pairs(torch, run, 40, seed=100)
+    ot, pt = exact_pairs(torch, run, 8, seed=900)
+    s_in, s_out = S.scales_from(om, ph)
+    sur = S.Surrogate(run, 8, s_in=s_in, s_out=s_out, seed=3)
+    om_d, ph_d = torch.from_numpy(om).cuda(), torch.from_numpy(ph).cuda()
+    first = None
+    for it in range(400):
+        k = (it * 8) % 40
+        idx = torch.arange(k, k + 8) % 40
+        loss = float(sur.train_step(om_d[idx], ph_d[idx], lr=3e-3).item())
+        first = loss if first is None else first
+    assert loss < 0.2 * first
+    pred = sur.forward(torch.from_numpy(ot).cuda()).cpu().numpy()
+    res = np.sqrt(((pred[:, :2] - pt[:, :2]) ** 2).mean())
+    trivial = np.sqrt(((pt[:, :2] - pt[:, :2].mean(axis=(2, 3), keepdims=True)) ** 2).mean())
+    assert res < 0.5 * trivial, (res, trivial)
+
+
+def test_controller_exact_every_k(torch):
+    run = W.with_(W.plain_small(), precision=P.MIXED_FP32, f0=0.0)
+    h = P.EpdLb([run])
+    params = S.init_params(seed=1, out_scale=0.0)  # predicts the exact means
+    h.set_surrogate(params, s_in=300.0, s_out=1e-3, exact_every=8, residual_tol=1.0)
+    h.step(24)
+    st = h.surrogate_stats()
+    assert st["steps"] == 24 and st["exact"] == 3 and st["surrogate"] == 21 and st["forced_exact"] == 0
+    ob = h.observables(0)
+    assert abs((ob["mean_phi_a"] + ob["mean_phi_b"]) / run.phi_p - 1) < 1e-12
+    # a residual tolerance that cannot be met forces exact steps
+    h.set_surrogate(params, s_in=300.0, s_out=1e-3, exact_every=8, residual_tol=0.0)
+    h.step(5)
+    st = h.surrogate_stats()
+    assert st["exact"] == 5 and st["surrogate"] == 0 and st["forced_exact"] == 4 and st["falling_back"] == 1
+    h.set_surrogate(None, 0, 0, exact_every=0)
+    h.step(2)
+    h.close()
