@@ -198,6 +198,64 @@ def time_steps(h, stream, steps, flush, with_kernels=False):
     return per_step, kern
 
 
+def surrogate_section(P, W, torch, runs, h, flush, args):
+    """Train the density surrogate on exact pairs from the workload's own
+    trajectory, then step it (exact every 8th step) against an exact run from
+    the same initial state: time per step and density error."""
+    import numpy as np
+
+    from paper_1804_02883_gb300 import surrogate as S
+
+    n_runs, (ny, nx) = len(runs), (runs[0].ny, runs[0].nx)
+    he = P.EpdLb(runs)
+    om = torch.empty((24 * n_runs, 3, ny, nx), dtype=torch.float64, device="cuda")
+    ph = torch.empty_like(om)
+    k = 0
+    for _ in range(24):
+        he.step(1)
+        for r in range(n_runs):
+            he.fields_dev(r, om[k], ph[k])
+            k += 1
+    he.sync()
+    s_in, s_out = S.scales_from(om[:8].cpu().numpy(), ph[:8].cpu().numpy())
+    sm = S.Surrogate(runs[0], n_runs, s_in=s_in, s_out=s_out, seed=5)
+    t0 = time.perf_counter()
+    iters = 300
+    for it in range(iters):
+        idx = torch.randint(0, om.shape[0], (n_runs,), device="cuda")
+        loss = sm.train_step(om[idx], ph[idx], lr=2e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    # exact and surrogate runs from the same initial state
+    ha, hb = P.EpdLb(runs), P.EpdLb(runs)
+    hb.set_surrogate(sm.params, s_in, s_out, exact_every=8, residual_tol=1e-3)
+    per, _ = time_steps(hb, hb.stream, args.surrogate_steps, flush)
+    ha.step(args.surrogate_steps)
+    ha.sync()
+    hb.sync()
+    errs = []
+    for r in range(n_runs):
+        pa, _ = ha.densities(r)
+        pb, _ = hb.densities(r)
+        for c in range(3):
+            spread = np.abs(pa[c] - pa[c].mean()).max()
+            errs.append(float(np.abs(pb[c] - pa[c]).max() / spread))
+    st = hb.surrogate_stats()
+    ms = float(np.median(per))
+    out = {"ms_per_step": float(sum(per) / len(per)), "median_ms_per_step": ms, "steps": args.surrogate_steps,
+           "exact_every": 8, "residual_tol": 1e-3, "stats": st,
+           "value_equivalent": units_per_step(runs) / (sum(per) / len(per) * 1e-3),
+           "density_error_vs_exact": max(errs),
+           "density_error_definition": "max |Phi_sur - Phi_exact| / max |Phi_exact - <Phi_exact>| over runs and species "
+                                       "after the timed steps, both runs from the same initial state",
+           "training": {"pairs": int(om.shape[0]), "iterations": iters, "batch": n_runs, "seconds": train_s,
+                        "final_loss": float(loss.item())}}
+    ha.close()
+    hb.close()
+    he.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -207,6 +265,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--surrogate-steps", type=int, default=40)
     ap.add_argument("--workload", default="channel", choices=sorted(WORKLOADS),
                     help="channel (default): the 4 x 256x512 batch the metric is quoted on; ensemble32 and "
                          "vesicle are the other configurations")
@@ -323,6 +382,10 @@ def main():
            "h2d_bytes_per_step": int(sum(3 * r.nx * r.ny * 8 for r in runs)),
            "d2h_bytes_per_step": int(sum(3 * r.nx * r.ny * 8 + 16 for r in runs))}
 
+    # learned surrogate (exact every 8th step) on the same workload
+    sur = None
+    if args.surrogate_steps > 0 and all(r.nx % 16 == 0 and r.ny % 8 == 0 for r in runs) and len({(r.nx, r.ny) for r in runs}) == 1:
+        sur = surrogate_section(P, W, torch, runs, h, flush, args)
     # FP64-plain path on the same workload
     h.close()
     del h
@@ -338,6 +401,9 @@ def main():
                 "lb_mlups": sites_per_step(runs64) / (ms64 * 1e-3) / 1e6, "steps": args.fp64_steps}
         h64.close()
 
+    if sur is not None:
+        sur["speedup_vs_exact_mixed"] = ms_per_step / sur["ms_per_step"]
+        sur["speedup_vs_fp64_plain"] = fp64["ms_per_step"] / sur["ms_per_step"] if fp64 else None
     line = None
     if rank == 0:
         cpu = None
@@ -363,6 +429,7 @@ def main():
             "wall_s": wall,
             "kernels": kernels,
             "roofline": roofline,
+            "surrogate": sur,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches_per_step(runs) * args.steps,

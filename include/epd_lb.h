@@ -120,6 +120,10 @@ int epd_lb_sync(epd_lb *h);
  * pointer may be NULL.  Synchronous. */
 int epd_lb_densities(epd_lb *h, int32_t run, double *phi, double *q);
 
+/* omega (3*ny*nx) and Phi (3*ny*nx) of run `run` into caller device memory
+ * (FP64, asynchronous on the handle's stream); either pointer may be NULL. */
+int epd_lb_fields_dev(epd_lb *h, int32_t run, double *omega_dev, double *phi_dev);
+
 /* Fluid velocity u = (j + f/2)/rho of the last collision, lattice units,
  * 2*ny*nx doubles.  Synchronous. */
 int epd_lb_velocity(epd_lb *h, int32_t run, double *v);

@@ -36,7 +36,7 @@ SYMBOLS = (
     "epd_lb_last_error", "epd_lb_destroy", "epd_prop_solve_workspace_bytes", "epd_prop_solve",
     "epd_lb_enable_timing", "epd_lb_kernel_times", "epd_prop_solve_noalloc",
     "epd_sur_num_params", "epd_sur_workspace_bytes", "epd_sur_forward", "epd_sur_gradients", "epd_sur_train_step",
-    "epd_lb_surrogate_workspace_bytes", "epd_lb_set_surrogate", "epd_lb_surrogate_stats",
+    "epd_lb_surrogate_workspace_bytes", "epd_lb_set_surrogate", "epd_lb_surrogate_stats", "epd_lb_fields_dev",
 )
 
 
@@ -139,6 +139,7 @@ def lib():
             "epd_lb_set_surrogate": (ctypes.c_int, [vp, vp, ctypes.c_double, ctypes.c_double, i32, ctypes.c_double, vp,
                                                     ctypes.c_size_t]),
             "epd_lb_surrogate_stats": (ctypes.c_int, [vp, vp]),
+            "epd_lb_fields_dev": (ctypes.c_int, [vp, i32, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -268,6 +269,12 @@ class EpdLb:
         v = np.empty((2, ny, nx))
         self._ck(lib().epd_lb_velocity(self.h, run, _ptr(v)), "epd_lb_velocity")
         return v
+
+    def fields_dev(self, run: int, omega_dev=None, phi_dev=None):
+        """omega and Phi of a run into device tensors (3, ny, nx) FP64, on the
+        handle's stream."""
+        self._ck(lib().epd_lb_fields_dev(self.h, run, None if omega_dev is None else omega_dev.data_ptr(),
+                                         None if phi_dev is None else phi_dev.data_ptr()), "epd_lb_fields_dev")
 
     def densities_dev(self, run: int, phi_dev, q_dev):
         self._ck(lib().epd_lb_densities_dev(self.h, run, phi_dev.data_ptr(), q_dev.data_ptr()), "epd_lb_densities_dev")

@@ -613,6 +613,19 @@ extern "C" int epd_lb_densities_dev(epd_lb *h, int32_t run, double *phi_dev, dou
     return EPD_LB_OK;
 }
 
+extern "C" int epd_lb_fields_dev(epd_lb *h, int32_t run, double *omega_dev, double *phi_dev)
+{
+    Group *G;
+    int m;
+    if (int rc = locate(h, run, &G, &m)) return rc;
+    const size_t n = (size_t)G->g.n;
+    if (omega_dev)
+        CK(cudaMemcpyAsync(omega_dev, G->omega + (size_t)m * 3 * n, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream), "copy omega");
+    if (phi_dev)
+        CK(cudaMemcpyAsync(phi_dev, G->phi + (size_t)m * 3 * n, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream), "copy phi");
+    return EPD_LB_OK;
+}
+
 extern "C" int epd_lb_densities(epd_lb *h, int32_t run, double *phi, double *q)
 {
     Group *G;

@@ -57,7 +57,7 @@ struct ConvArgs {
     __nv_bfloat16 *out_bf;      // [b][y][x][NP] BF16 output (EP_TANH, EP_DX)
     float *out_f;               // [b][y][x][NP] FP32 output (EP_TANH when training, EP_LINEAR)
     const float *yprev;         // EP_DX: tanh output of the layer below, [b][y][x][NP] FP32
-    int nx, ny, logx, logy;
+    int nx, ny, logx, logy, nb;
     int nreal;                  // output channels actually used (the rest are written as 0)
 };
 
@@ -70,19 +70,24 @@ __global__ void __launch_bounds__(128) conv3x3(ConvArgs a)
     __shared__ __align__(16) __nv_bfloat16 tile[HH * HW * KS];
     __shared__ __align__(16) __nv_bfloat16 wsm[9 * NP * KS];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tx0 = blockIdx.x * TW, ty0 = blockIdx.y * TH, b = blockIdx.z;
     const long long n = (long long)a.nx * a.ny;
+    // weights once per CTA; the CTA then walks over pixel tiles
+    for (int e = tid; e < 9 * NP * (KP / 8); e += 128) {
+        const int row = e / (KP / 8), ch = (e % (KP / 8)) * 8;
+        *reinterpret_cast<uint4 *>(&wsm[row * KS + ch]) = *reinterpret_cast<const uint4 *>(&a.w[(size_t)row * KP + ch]);
+    }
+    const int tiles_x = a.nx / TW, tiles_img = tiles_x * (a.ny / TH);
+    for (int tix = blockIdx.x; tix < tiles_img * a.nb; tix += gridDim.x) {
+    const int b = tix / tiles_img, rr = tix % tiles_img;
+    const int tx0 = (rr % tiles_x) * TW, ty0 = (rr / tiles_x) * TH;
     const __nv_bfloat16 *in = a.in + (size_t)b * n * KP;
+    __syncthreads();  // the previous tile's reads of `tile` are done
     // halo tile with circular wrap, 16-byte chunks of channels
     for (int e = tid; e < HH * HW * (KP / 8); e += 128) {
         const int pix = e / (KP / 8), ch = (e % (KP / 8)) * 8;
         const int hy = pix / HW, hx = pix % HW;
         const int gy = (ty0 + hy - 1) & (a.ny - 1), gx = (tx0 + hx - 1) & (a.nx - 1);
         *reinterpret_cast<uint4 *>(&tile[pix * KS + ch]) = *reinterpret_cast<const uint4 *>(&in[((size_t)gy * a.nx + gx) * KP + ch]);
-    }
-    for (int e = tid; e < 9 * NP * (KP / 8); e += 128) {
-        const int row = e / (KP / 8), ch = (e % (KP / 8)) * 8;
-        *reinterpret_cast<uint4 *>(&wsm[row * KS + ch]) = *reinterpret_cast<const uint4 *>(&a.w[(size_t)row * KP + ch]);
     }
     __syncthreads();
 
@@ -155,6 +160,7 @@ __global__ void __launch_bounds__(128) conv3x3(ConvArgs a)
                 if (a.out_f) *reinterpret_cast<float2 *>(&a.out_f[pix * NP + c]) = make_float2(v0, v1);
             }
         }
+    }
     }
 }
 
@@ -242,15 +248,45 @@ __global__ void __launch_bounds__(288) conv3x3_dw(const __nv_bfloat16 *x, const 
 // small kernels: input preparation, output, loss, reductions, optimiser
 // ---------------------------------------------------------------------------
 
-// Per (sample, channel) mean of a planar FP64 field: one block each, fixed order.
-__global__ void __launch_bounds__(256) channel_means(const double *f, int nch, long long n, double *mean)
+constexpr int kRedBlocks = 64;  // blocks per plane of the two-pass reductions
+
+// Two-pass, fixed-order sums over planes of n values: pass 1, grid
+// (kRedBlocks, planes), writes part[plane][block]; KIND 0: the FP64 values,
+// 1: exp(-v) in FP32 (solvent weight of Eq. (11)), 2: channel c = plane % 2
+// of the FP32 [sample][pixel][8] network output.
+template <int KIND>
+__global__ void __launch_bounds__(256) plane_partials(const void *f, long long n, double *part)
 {
     __shared__ double red[32];
-    const double *p = f + (size_t)blockIdx.x * n;
+    const int plane = blockIdx.y;
     double s = 0.0;
-    for (long long i = threadIdx.x; i < n; i += blockDim.x) s += p[i];
+    const long long chunk = (n + kRedBlocks - 1) / kRedBlocks, lo = blockIdx.x * chunk;
+    const long long hi = lo + chunk < n ? lo + chunk : n;
+    if (KIND == 0) {
+        const double *p = reinterpret_cast<const double *>(f) + (size_t)plane * n;
+        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) s += p[i];
+    } else if (KIND == 1) {
+        const double *p = reinterpret_cast<const double *>(f) + ((size_t)plane * 3 + 2) * n;
+        float acc = 0.f;
+        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) acc += expf(-(float)p[i]);
+        s = (double)acc;
+    } else {
+        const float *p = reinterpret_cast<const float *>(f) + (size_t)(plane / 2) * n * 8 + (plane % 2);
+        float acc = 0.f;
+        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) acc += p[(size_t)i * 8];
+        s = (double)acc;
+    }
     s = block_sum(s, red);
-    if (threadIdx.x == 0) mean[blockIdx.x] = s / (double)n;
+    if (threadIdx.x == 0) part[(size_t)plane * kRedBlocks + blockIdx.x] = s;
+}
+
+__global__ void plane_finish(const double *part, int planes, double scale, double *out)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= planes) return;
+    double s = 0.0;
+    for (int b = 0; b < kRedBlocks; ++b) s += part[(size_t)p * kRedBlocks + b];
+    out[p] = s * scale;
 }
 
 // x0[b][p][16] = s_in (omega_c - <omega_c>) for c < 3, 0 for the padding.
@@ -269,19 +305,8 @@ __global__ void prep_input(const double *omega, const double *mean, double s_in,
     dst[1] = *reinterpret_cast<uint4 *>(&v[8]);
 }
 
-// Mean of the two output channels of y4 ([b][p][8] FP32): one block per (b, c).
-__global__ void __launch_bounds__(256) out_means(const float *y4, long long n, double *mean)
-{
-    __shared__ double red[32];
-    const int b = blockIdx.x / 2, c = blockIdx.x % 2;
-    double s = 0.0;
-    for (long long i = threadIdx.x; i < n; i += blockDim.x) s += (double)y4[((size_t)b * n + i) * 8 + c];
-    s = block_sum(s, red);
-    if (threadIdx.x == 0) mean[blockIdx.x] = s / (double)n;
-}
-
 // Densities from the network output: Phi_A, Phi_B with exact means, Phi_S from
-// Eq. (11) (exp(-w_S) in FP64, Q_S from the per-sample sums in qs_sum).
+// Eq. (11) (exp(-w_S) in FP32, Q_S the per-sample mean of the same values).
 __global__ void densities_out(const float *y4, const double *ymean, const double *omega, const double *qs_mean, double s_out,
                               double pa_bar, double pb_bar, double ps_bar, long long n, int nb, double *phi)
 {
@@ -291,17 +316,7 @@ __global__ void densities_out(const float *y4, const double *ymean, const double
     const float2 y = *reinterpret_cast<const float2 *>(&y4[(size_t)i * 8]);
     phi[(b * 3 + 0) * n + p] = pa_bar + s_out * ((double)y.x - ymean[2 * b]);
     phi[(b * 3 + 1) * n + p] = pb_bar + s_out * ((double)y.y - ymean[2 * b + 1]);
-    phi[(b * 3 + 2) * n + p] = ps_bar * exp(-omega[(b * 3 + 2) * n + p]) / qs_mean[b];
-}
-
-__global__ void __launch_bounds__(256) solvent_q(const double *omega, long long n, double *qs_mean)
-{
-    __shared__ double red[32];
-    const double *w = omega + ((size_t)blockIdx.x * 3 + 2) * n;
-    double s = 0.0;
-    for (long long i = threadIdx.x; i < n; i += blockDim.x) s += exp(-w[i]);
-    s = block_sum(s, red);
-    if (threadIdx.x == 0) qs_mean[blockIdx.x] = s / (double)n;
+    phi[(b * 3 + 2) * n + p] = ps_bar * (double)expf(-(float)omega[(b * 3 + 2) * n + p]) / qs_mean[b];
 }
 
 // Loss and output gradient: targets t_c = (Phi_c - <Phi_c>) / s_out for
@@ -453,6 +468,7 @@ size_t carve(Work &w, char *base, int nb, int ny, int nx, bool training)
     w.means = (double *)take((size_t)nb * 3 * sizeof(double));
     w.ymean = (double *)take((size_t)nb * 2 * sizeof(double));
     w.qs = (double *)take((size_t)nb * sizeof(double));
+    w.red = (double *)take((size_t)nb * 3 * kRedBlocks * sizeof(double));
     if (training) {
         for (int l = 0; l < 3; ++l) w.yf[l] = take(np * 32 * 4);
         w.dz[0] = take(np * 32 * 2);
@@ -477,6 +493,16 @@ size_t carve(Work &w, char *base, int nb, int ny, int nx, bool training)
 }
 
 static unsigned blocks(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// Means over `planes` planes of n values (kind: see plane_partials).
+static void plane_means(const void *f, int kind, int planes, long long n, double *red, double *out, cudaStream_t s)
+{
+    const dim3 g(kRedBlocks, planes);
+    if (kind == 0) plane_partials<0><<<g, 256, 0, s>>>(f, n, red);
+    else if (kind == 1) plane_partials<1><<<g, 256, 0, s>>>(f, n, red);
+    else plane_partials<2><<<g, 256, 0, s>>>(f, n, red);
+    plane_finish<<<(planes + 63) / 64, 64, 0, s>>>(red, planes, 1.0 / (double)n, out);
+}
 
 static cudaError_t pack_all(Work &w, const float *params, bool backward, cudaStream_t s)
 {
@@ -510,7 +536,9 @@ static void conv(Work &w, const void *in, const void *wt, const float *bias, voi
     a.logx = ilog2(w.nx);
     a.logy = ilog2(w.ny);
     a.nreal = nreal;
-    conv3x3<KP, NP, MODE><<<dim3(w.nx / TW, w.ny / TH, w.nb), 128, 0, s>>>(a);
+    a.nb = w.nb;
+    const int tiles = w.nb * (w.nx / TW) * (w.ny / TH);
+    conv3x3<KP, NP, MODE><<<std::min(tiles, 8 * 152), 128, 0, s>>>(a);
 }
 
 static cudaError_t forward_layers(Work &w, const float *params, cudaStream_t s)
@@ -528,11 +556,11 @@ cudaError_t forward(Work &w, const float *params, const double *omega, double *p
 {
     cudaError_t e;
     if ((e = pack_all(w, params, false, s))) return e;
-    channel_means<<<w.nb * 3, 256, 0, s>>>(omega, 3, w.n, w.means);
+    plane_means(omega, 0, w.nb * 3, w.n, w.red, w.means, s);
     prep_input<<<blocks(w.n * w.nb), 256, 0, s>>>(omega, w.means, s_in, w.n, w.nb, reinterpret_cast<__nv_bfloat16 *>(w.x0));
     if ((e = forward_layers(w, params, s))) return e;
-    out_means<<<w.nb * 2, 256, 0, s>>>((const float *)w.y4, w.n, w.ymean);
-    solvent_q<<<w.nb, 256, 0, s>>>(omega, w.n, w.qs);
+    plane_means(w.y4, 2, w.nb * 2, w.n, w.red, w.ymean, s);
+    plane_means(omega, 1, w.nb, w.n, w.red, w.qs, s);
     densities_out<<<blocks(w.n * w.nb), 256, 0, s>>>((const float *)w.y4, w.ymean, omega, w.qs, s_out, pa_bar, pb_bar, ps_bar, w.n, w.nb,
                                                      phi);
     return cudaGetLastError();
@@ -568,10 +596,10 @@ cudaError_t gradients(Work &w, const float *params, const double *omega, const d
 {
     cudaError_t e;
     if ((e = pack_all(w, params, true, s))) return e;
-    channel_means<<<w.nb * 3, 256, 0, s>>>(omega, 3, w.n, w.means);
+    plane_means(omega, 0, w.nb * 3, w.n, w.red, w.means, s);
     prep_input<<<blocks(w.n * w.nb), 256, 0, s>>>(omega, w.means, s_in, w.n, w.nb, reinterpret_cast<__nv_bfloat16 *>(w.x0));
     if ((e = forward_layers(w, params, s))) return e;
-    channel_means<<<w.nb * 3, 256, 0, s>>>(phi_t, 3, w.n, w.tmean);
+    plane_means(phi_t, 0, w.nb * 3, w.n, w.red, w.tmean, s);
     const unsigned lb = blocks(w.n * w.nb);
     loss_grad<<<lb, 256, 0, s>>>((const float *)w.y4, phi_t, w.tmean, s_out, w.n, w.nb, reinterpret_cast<__nv_bfloat16 *>(w.dz4),
                                  w.lpart);

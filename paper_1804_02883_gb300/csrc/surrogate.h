@@ -26,7 +26,7 @@ struct Work {
     void *x0, *y[3], *y4, *yf[3], *dz[2], *dz4;
     void *wf[kLayers], *wb[kLayers];
     float *dwpart, *grad;
-    double *means, *ymean, *qs, *tmean, *lpart;
+    double *means, *ymean, *qs, *tmean, *lpart, *red;
     int nblk_dw;
 };
 
