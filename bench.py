@@ -421,7 +421,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload],
-                       "precision": "mixed (FP32 propagator and LB; FP64 fields, contour sums, Q, EPD transforms)",
+                       "precision": "mixed (FP32 propagator, LB and EPD transforms; FP64 fields, contour sums, Q)",
                        "l2": "flushed (256 MB write) before every timed step", "parallelism": f"replicas x{world}"},
             "lb_mlups": lb_mlups,
             "fp64_plain": fp64,

@@ -53,9 +53,9 @@ enum {
 
 enum {
     EPD_LB_PLAIN_FP64 = 0,   /* every field and transform in FP64            */
-    EPD_LB_MIXED_FP32 = 1    /* propagators and LB populations in FP32; fields
-                                omega and Phi, contour sums, Q, masses and the
-                                EPD/force transforms in FP64                 */
+    EPD_LB_MIXED_FP32 = 1    /* propagators, LB populations and the EPD/force
+                                transforms in FP32; fields omega and Phi,
+                                contour sums, Q and masses in FP64           */
 };
 
 /*
