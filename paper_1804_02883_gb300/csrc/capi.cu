@@ -73,6 +73,19 @@ size_t carve_group(Group &G, char *base, size_t off)
     G.twy_d = (double2 *)take((size_t)G.g.ny / 2 * sizeof(double2));
     G.twx_full = (float2 *)take((size_t)G.g.nx * sizeof(float2));
     G.twy_full = (float2 *)take((size_t)G.g.ny * sizeof(float2));
+    // reference + differential solve pair of the cluster solve (MIXED_FP32)
+    G.hist1 = nullptr;
+    G.defac = nullptr;
+    G.dia = G.dib = G.dia2 = G.dib2 = nullptr;
+    if (G.prec == EPD_LB_MIXED_FP32 && cluster_shape_exists(G.g.logx, G.g.logy)) {
+        G.hist1 = take(R * 2 * (size_t)(G.g.ns + 1) * n * sizeof(float));
+        G.defac = take(R * n * sizeof(float2));
+        G.dia = (double *)take(R * n * sizeof(double));
+        G.dib = (double *)take(R * n * sizeof(double));
+        G.dia2 = (double *)take(R * n * sizeof(double));
+        G.dib2 = (double *)take(R * n * sizeof(double));
+    }
+    G.diff = false;  // set once the cluster solve is known to launch
     return align_up(off);
 }
 
@@ -104,6 +117,14 @@ static Group run_view(const Group &G, int r)
     V.pop[1] = (char *)V.pop[1] + (size_t)r * 9 * n * tb;
     V.vel = (char *)V.vel + (size_t)r * n * 2 * tb;
     V.force = (char *)V.force + (size_t)r * n * 2 * tb;
+    if (G.hist1) {
+        V.hist1 = (char *)V.hist1 + (size_t)r * 2 * (G.g.ns + 1) * n * sizeof(float);
+        V.defac = (char *)V.defac + (size_t)r * n * sizeof(float2);
+        V.dia += (size_t)r * n;
+        V.dib += (size_t)r * n;
+        V.dia2 += (size_t)r * n;
+        V.dib2 += (size_t)r * n;
+    }
     return V;
 }
 
@@ -403,7 +424,7 @@ static cudaError_t enqueue_group(epd_lb *h, size_t gi, int parity, cudaStream_t 
         probe.m_acc = std::min(G.g.ns, (3 * G.g.ns) / 4 + 1);
     }
     if ((e = launch_aux_convection(G, s))) return e;                      // omega -> omega~
-    if ((e = launch_solve(G, G.omega_t, G.phi_t, G.q_t, s))) return e;     // Phi~
+    if ((e = launch_solve(G, G.omega_t, G.phi_t, G.q_t, s, nullptr, G.diff))) return e;  // Phi~
     if (mode == STEP_CHECK) {
         // the surrogate at omega~ into the EPD scratch, residual against Phi~
         double pa, pb, ps;
@@ -413,7 +434,11 @@ static cudaError_t enqueue_group(epd_lb *h, size_t gi, int parity, cudaStream_t 
         if ((e = sur::residual_rms(phi_sur, G.phi_t, G.g.n, G.g.nruns, G.part, h->sur_resid + gi, s))) return e;
     }
     if ((e = launch_diffusion(G, s))) return e;                           // omega(t+dt)
-    if ((e = launch_solve(G, G.omega, G.phi, G.q, s, timed ? &probe : nullptr))) return e;  // Phi(t+dt)
+    if (G.diff) {  // Phi(t+dt) as Phi~ plus the change from the diffusion update
+        if ((e = launch_solve_delta(G, s, timed ? &probe : nullptr))) return e;
+    } else if ((e = launch_solve(G, G.omega, G.phi, G.q, s, timed ? &probe : nullptr))) {
+        return e;  // Phi(t+dt)
+    }
     if (timed) h->timed_cluster = probe.cluster;
     if ((e = launch_force(G, s))) return e;                               // polymer force
     if (timed && (e = cudaEventRecordWithFlags(h->ev[5], s, cudaEventRecordExternal))) return e;
@@ -537,6 +562,7 @@ extern "C" int epd_lb_init(const epd_lb_params *p, int32_t nruns, void *workspac
         if (upload_tables_e(G, h->stream) != cudaSuccess) return bail(EPD_LB_ECUDA);
         if (launch_init_state(G, h->stream) != cudaSuccess) return bail(EPD_LB_ECUDA);
         if (launch_solve(G, G.omega, G.phi, G.q, h->stream) != cudaSuccess) return bail(EPD_LB_ECUDA);
+        G.diff = G.hist1 != nullptr && cluster_solve_supported(G);
     }
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(EPD_LB_ECUDA);
     for (size_t gi = 1; gi < h->groups.size(); ++gi) {

@@ -47,6 +47,11 @@ struct Group {
     double *q, *q_t;   // [run][2]
     double *ia, *ib;   // contour sums, [run][n]
     double *ia2, *ib2; // contour sums of the g' chain's terms (cluster solve), [run][n]
+    // differential second solve (MIXED_FP32 with the cluster solve)
+    bool diff = false;        // the step uses the reference + differential solve pair
+    void *hist1 = nullptr;    // reference solve, every node of both chains, [run][2][ns+1][n] float
+    void *defac = nullptr;    // (dE_A, dE_B), [run][n] float2
+    double *dia = nullptr, *dib = nullptr, *dia2 = nullptr, *dib2 = nullptr;  // contour sums of the difference, [run][n]
     double2 *cz;       // 4 complex FP64 scratch planes per run: [run][4][n]
     double *part;      // reduction partials, [run][kMaxPart]
     double *f0_lat;    // [run]
@@ -88,8 +93,13 @@ struct SolveProbe {
 
 // Single-chain solve, Eqs. (6)-(11): omega (3n per run, FP64) -> phi (3n),
 // q (2 per run).  All runs of the group.
+// reference = true keeps every node of both chains for a following
+// launch_solve_delta (cluster solve only).
 cudaError_t launch_solve(Group &G, const double *omega, double *phi, double *q, cudaStream_t s,
-                         const SolveProbe *probe = nullptr);
+                         const SolveProbe *probe = nullptr, bool reference = false);
+// Second solve of the step as a difference from the reference solve at
+// omega~ (phi_t, q_t): Phi(t+dt) = Phi~ + dPhi, Q likewise (G.diff only).
+cudaError_t launch_solve_delta(Group &G, cudaStream_t s, const SolveProbe *probe = nullptr);
 
 // EPD parts of the step.
 cudaError_t launch_aux_convection(Group &G, cudaStream_t s);   // omega, vel -> omega_t
@@ -109,7 +119,9 @@ cudaError_t launch_pop_raw(Group &G, int run, int parity, double *dst, const dou
 // Cluster-resident solve (prop_cluster.cu): availability for the group's
 // shape and precision, its launch, and its CTAs per run.
 bool cluster_solve_supported(const Group &G);
-cudaError_t launch_cluster_solve(Group &G, cudaStream_t s, const void *twx_full, const void *twy_full);
+bool cluster_shape_exists(int logx, int logy);
+// mode 0: plain, 1: reference (full history kept), 2: differential
+cudaError_t launch_cluster_solve(Group &G, cudaStream_t s, const void *twx_full, const void *twy_full, int mode);
 int cluster_ctas(const Group &G);
 
 // Kernel attributes (dynamic shared memory limits), once per process.

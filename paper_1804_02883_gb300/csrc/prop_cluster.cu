@@ -40,9 +40,22 @@ namespace cg = cooperative_groups;
 
 namespace epdlb {
 
+// Solve modes of the cluster kernel.
+//  0: plain solve; first-half history in `hist`.
+//  1: reference solve: every node of both chains kept in `hist1` (for a
+//     following differential solve), mirrored products read from it.
+//  2: differential solve at omega + d omega given the reference solve at
+//     omega: the chain carries d a_j = E_j dg_j + dE_j (g_j + dg_j), the
+//     epilogue forms dg_{j+1} = E_{j+1} T(d a_j) + dE_{j+1} (g_{j+1}/E_{j+1} + T(d a_j))
+//     (g, E of the reference solve; dE the change of the node factors), and
+//     the contour sums collect g dg' + dg g' + dg dg' (exact algebra of the
+//     two solves' difference, rounded relative to the difference itself).
 struct PropCK {
     GroupGeom g;
-    float *hist;         // [run][chain][half_lo + 1][n] real
+    float *hist;         // [run][chain][half_lo + 1][n] real (modes 0 and 2)
+    float *hist1;        // [run][chain][N_s + 1][n] real (reference solve, modes 1 and 2)
+    const float2 *defac; // (dE_A, dE_B) [run][n] (mode 2)
+    int mode;
     float2 *state;       // [run][chain][n / 2] packed rows, E z at node half_lo
     const float2 *efac;  // [run][n] (E_A, E_B)
     double *ia0, *ib0;   // contour sums of the g chain's terms, [run][n]
@@ -288,7 +301,7 @@ struct ClusterGeom {
     static constexpr size_t SMEM = (size_t)(R2 * PITCH + P + TABX + TABY) * sizeof(float2) + (NX + NY) * sizeof(float);
 };
 
-template <int LOGX, int LOGY, int C, int T>
+template <int LOGX, int LOGY, int C, int T, bool DIFF>
 __global__ void __launch_bounds__(T, 1024 / T) prop_cluster(PropCK k)
 {
     using G = ClusterGeom<LOGX, LOGY, C, T>;
@@ -320,8 +333,15 @@ __global__ void __launch_bounds__(T, 1024 / T) prop_cluster(PropCK k)
     for (int i = tid; i < NX; i += T) kx[i] = k.kx[i];
     for (int i = tid; i < NY; i += T) ky[i] = k.ky[i];
     const float2 *efac = k.efac + (size_t)run * n;
-    float *hist_me = k.hist + (size_t)(run * 2 + chain) * (hlo + 1) * n;
-    const float *hist_other = k.hist + (size_t)(run * 2 + (1 - chain)) * (hlo + 1) * n;
+    const float2 *defac = DIFF ? k.defac + (size_t)run * n : nullptr;
+    const int mode = DIFF ? 2 : k.mode;
+    const int hp = mode == 1 ? ns + 1 : hlo + 1;  // history pitch in nodes
+    float *hbase = mode == 1 ? k.hist1 : k.hist;
+    float *hist_me = hbase + (size_t)(run * 2 + chain) * hp * n;
+    const float *hist_other = hbase + (size_t)(run * 2 + (1 - chain)) * hp * n;
+    // reference solve's chains (mode 2)
+    const float *ref_me = DIFF ? k.hist1 + (size_t)(run * 2 + chain) * (ns + 1) * n : nullptr;
+    const float *ref_other = DIFF ? k.hist1 + (size_t)(run * 2 + (1 - chain)) * (ns + 1) * n : nullptr;
     float2 *state = k.state + (size_t)(run * 2 + chain) * (n / 2);
     __syncthreads();
 
@@ -334,9 +354,15 @@ __global__ void __launch_bounds__(T, 1024 / T) prop_cluster(PropCK k)
         for (int e = tid; e < P; e += T) {
             const int b = e / NX, x = e % NX;
             const long long site = (long long)(2 * (krow0 + b)) * NX + x;
-            hist_me[site] = 1.f;
-            hist_me[site + NX] = 1.f;
-            rowbuf[RL::at(b, x)] = f2(sel(efac[site], 0), sel(efac[site + NX], 0));
+            if (DIFF) {  // dg_0 = 0, d a_0 = dE_0 g_0
+                hist_me[site] = 0.f;
+                hist_me[site + NX] = 0.f;
+                rowbuf[RL::at(b, x)] = f2(sel(defac[site], 0), sel(defac[site + NX], 0));
+            } else {
+                hist_me[site] = 1.f;
+                hist_me[site + NX] = 1.f;
+                rowbuf[RL::at(b, x)] = f2(sel(efac[site], 0), sel(efac[site + NX], 0));
+            }
         }
         m0 = 1;
         m1 = hlo;
@@ -407,7 +433,13 @@ __global__ void __launch_bounds__(T, 1024 / T) prop_cluster(PropCK k)
 #pragma unroll
                 for (int cp = 0; cp < 2; ++cp) {
                     const long long site = (long long)(2 * (krow0 + b) + cp) * NX + t + r * PER_L;
-                    acc[j][r][cp] += hist_me[(size_t)hlo * n + site] * hist_other[(size_t)hlo * n + site];
+                    const float a = hist_me[(size_t)hlo * n + site], o = hist_other[(size_t)hlo * n + site];
+                    if (DIFF) {
+                        const float ga = ref_me[(size_t)hlo * n + site], go = ref_other[(size_t)hlo * n + site];
+                        acc[j][r][cp] += ga * o + a * go + a * o;
+                    } else {
+                        acc[j][r][cp] += a * o;
+                    }
                 }
         }
         nacc = 1;
@@ -495,16 +527,37 @@ __global__ void __launch_bounds__(T, 1024 / T) prop_cluster(PropCK k)
                 const int x = tt[j] + r * PER_L;
                 const long long site0 = (long long)(2 * (krow0 + bb[j])) * NX + x;
                 const float e0 = sel(efac[site0], m), e1 = sel(efac[site0 + NX], m);
-                const float z0 = e0 * h[j][r].x, z1 = e1 * h[j][r].y;
-                if (!acc_node) {
-                    hist_me[(size_t)m * n + site0] = z0;
-                    hist_me[(size_t)m * n + site0 + NX] = z1;
+                if (!DIFF) {
+                    const float z0 = e0 * h[j][r].x, z1 = e1 * h[j][r].y;
+                    if (!acc_node || mode == 1) {
+                        hist_me[(size_t)m * n + site0] = z0;
+                        hist_me[(size_t)m * n + site0 + NX] = z1;
+                    }
+                    if (acc_node) {
+                        acc[j][r][0] += z0 * hist_other[(size_t)(ns - m) * n + site0];
+                        acc[j][r][1] += z1 * hist_other[(size_t)(ns - m) * n + site0 + NX];
+                        if (m == ns) qsum += z0 + z1;
+                    }
+                    if (m < ns) rowbuf[RL::at(bb[j], x)] = f2(e0 * z0, e1 * z1);
                 } else {
-                    acc[j][r][0] += z0 * hist_other[(size_t)(ns - m) * n + site0];
-                    acc[j][r][1] += z1 * hist_other[(size_t)(ns - m) * n + site0 + NX];
-                    if (m == ns) qsum += z0 + z1;
+                    const float d0 = sel(defac[site0], m), d1 = sel(defac[site0 + NX], m);
+                    const float g0 = ref_me[(size_t)m * n + site0], g1 = ref_me[(size_t)m * n + site0 + NX];
+                    // dg = E T(da) + dE (T(a) + T(da)), T(a) = g / E of the reference solve
+                    const float dg0 = e0 * h[j][r].x + d0 * (g0 / e0 + h[j][r].x);
+                    const float dg1 = e1 * h[j][r].y + d1 * (g1 / e1 + h[j][r].y);
+                    if (!acc_node) {
+                        hist_me[(size_t)m * n + site0] = dg0;
+                        hist_me[(size_t)m * n + site0 + NX] = dg1;
+                    } else {
+                        const size_t mo = (size_t)(ns - m) * n + site0;
+                        const float o0 = hist_other[mo], o1 = hist_other[mo + NX];
+                        const float q0 = ref_other[mo], q1 = ref_other[mo + NX];
+                        acc[j][r][0] += g0 * o0 + dg0 * q0 + dg0 * o0;
+                        acc[j][r][1] += g1 * o1 + dg1 * q1 + dg1 * o1;
+                        if (m == ns) qsum += dg0 + dg1;
+                    }
+                    if (m < ns) rowbuf[RL::at(bb[j], x)] = f2(e0 * dg0 + d0 * (g0 + dg0), e1 * dg1 + d1 * (g1 + dg1));
                 }
-                if (m < ns) rowbuf[RL::at(bb[j], x)] = f2(e0 * z0, e1 * z1);
             }
         }
         if (acc_node && m == ns) {
@@ -532,14 +585,16 @@ __global__ void __launch_bounds__(T, 1024 / T) prop_cluster(PropCK k)
 
 struct ClusterShape {
     int logx, logy, c, t;
-    const void *fn;
+    const void *fn;       // plain and reference solves
+    const void *fn_diff;  // differential solve
     size_t smem;
 };
 
 template <int LOGX, int LOGY, int C, int T>
 static ClusterShape shape_of()
 {
-    return ClusterShape{LOGX, LOGY, C, T, (const void *)prop_cluster<LOGX, LOGY, C, T>, ClusterGeom<LOGX, LOGY, C, T>::SMEM};
+    return ClusterShape{LOGX, LOGY, C, T, (const void *)prop_cluster<LOGX, LOGY, C, T, false>,
+                        (const void *)prop_cluster<LOGX, LOGY, C, T, true>, ClusterGeom<LOGX, LOGY, C, T>::SMEM};
 }
 
 // Instantiated grids (log2 nx, log2 ny): 4096 packed points per CTA with 256
@@ -578,31 +633,39 @@ bool cluster_solve_supported(const Group &G)
     int &st = checked[s->logx][s->logy];
     if (st == 0) {
         st = 2;
-        if (cudaFuncSetAttribute(s->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem) == cudaSuccess &&
-            (s->c <= 8 || cudaFuncSetAttribute(s->fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess)) {
+        auto ok = [&](const void *fn) {
+            if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem) != cudaSuccess) return false;
+            if (s->c > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+                return false;
             cudaLaunchConfig_t cfg = {};
             cudaLaunchAttribute attr;
             set_cluster_cfg(cfg, attr, s, 1);
             int nclusters = 0;
-            if (cudaOccupancyMaxActiveClusters(&nclusters, s->fn, &cfg) == cudaSuccess && nclusters > 0) st = 1;
-        }
+            return cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) == cudaSuccess && nclusters > 0;
+        };
+        if (ok(s->fn) && ok(s->fn_diff)) st = 1;
         cudaGetLastError();
     }
     return st == 1;
 }
 
-cudaError_t launch_cluster_solve(Group &G, cudaStream_t s, const void *twx_full, const void *twy_full)
+bool cluster_shape_exists(int logx, int logy) { return find_shape(logx, logy) != nullptr; }
+
+cudaError_t launch_cluster_solve(Group &G, cudaStream_t s, const void *twx_full, const void *twy_full, int mode)
 {
     const ClusterShape *sh = find_shape(G.g.logx, G.g.logy);
     PropCK k;
     k.g = G.g;
     k.hist = reinterpret_cast<float *>(G.hist);
+    k.hist1 = reinterpret_cast<float *>(G.hist1);
+    k.defac = reinterpret_cast<const float2 *>(G.defac);
+    k.mode = mode;
     k.state = reinterpret_cast<float2 *>(G.chain);
     k.efac = reinterpret_cast<const float2 *>(G.efac);
-    k.ia0 = G.ia;
-    k.ib0 = G.ib;
-    k.ia1 = G.ia2;
-    k.ib1 = G.ib2;
+    k.ia0 = mode == 2 ? G.dia : G.ia;
+    k.ib0 = mode == 2 ? G.dib : G.ib;
+    k.ia1 = mode == 2 ? G.dia2 : G.ia2;
+    k.ib1 = mode == 2 ? G.dib2 : G.ib2;
     k.part = G.part;
     k.twx = reinterpret_cast<const float2 *>(twx_full);
     k.twy = reinterpret_cast<const float2 *>(twy_full);
@@ -615,7 +678,7 @@ cudaError_t launch_cluster_solve(Group &G, cudaStream_t s, const void *twx_full,
     for (int half = 0; half < 2; ++half) {
         k.half = half;
         void *args[] = {&k};
-        const cudaError_t e = cudaLaunchKernelExC(&cfg, sh->fn, args);
+        const cudaError_t e = cudaLaunchKernelExC(&cfg, mode == 2 ? sh->fn_diff : sh->fn, args);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

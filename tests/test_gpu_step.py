@@ -76,9 +76,53 @@ def test_single_step_mixed_precision():
     gphi, _ = h.densities(0)
     assert fluct_err(gom, st.omega) < 2e-6
     assert rel_err(gphi, st.phi) < 2e-6
-    assert rel_err(gvel, st.vel) < 2e-3  # force from a difference of two FP32 solves
+    # 64 x 32 takes the streaming solve: two independent FP32 solves whose
+    # difference dPhi^D ~ 2e-3 drives the force, ~1e-4 relative error
+    assert rel_err(gvel, st.vel) < 2e-3
     assert np.abs(gpop - st.pop).max() < 1e-7
     h.close()
+
+
+@pytest.mark.parametrize("ny,nx,ns", [(64, 64, 16), (64, 128, 9), (128, 64, 20)])
+def test_single_step_mixed_differential_solve(ny, nx, ns):
+    # cluster-solve grids: the second solve is carried as the change from the
+    # first, so dPhi^D and the force it drives keep FP32 precision relative
+    # to themselves (1e-7 of dPhi^D, not of Phi)
+    r = P.RunParams(nx=nx, ny=ny, ns=ns, precision=P.MIXED_FP32, f_a=0.3, phi_p=0.2, f0=10.0)
+    omega = W.random_omega(ny, nx, seed=31, amp=0.05)
+    pop = W.random_populations(ny, nx, seed=32)
+    vel = W.random_velocity(ny, nx, seed=33, amp=0.02)
+    h = P.EpdLb([r])
+    h.set_state(0, omega, pop, vel)
+    h.step(1)
+    p, st = oracle_state_from(r, omega, pop, vel)
+    O.step(p, st)
+    gom, gpop, gvel = h.get_state(0)
+    gphi, gq = h.densities(0)
+    assert rel_err(gphi, st.phi) < 2e-6
+    assert rel_err(gq, st.q) < 2e-6
+    assert fluct_err(gom, st.omega) < 2e-6
+    assert rel_err(gvel, st.vel) < 1e-5
+    assert np.abs(gpop - st.pop).max() < 1e-7
+    h.close()
+
+
+def test_mixed_tracks_fp64_over_100_steps():
+    # 64 x 64, N_s = 32 from the seeded quench: MIXED and PLAIN_FP64 side by
+    # side; the remaining velocity difference comes from the FP32 resolution
+    # of the density fluctuations (~1e-7 of Phi against fluctuations ~1e-4)
+    r64 = W.plain_small()
+    a = P.EpdLb([r64])
+    b = P.EpdLb([W.with_(r64, precision=P.MIXED_FP32)])
+    a.step(100)
+    b.step(100)
+    pa, qa = a.densities(0)
+    pb, qb = b.densities(0)
+    assert rel_err(pb, pa) < 1e-6
+    assert rel_err(qb, qa) < 1e-6
+    assert rel_err(b.velocity(0), a.velocity(0)) < 5e-3
+    a.close()
+    b.close()
 
 
 def test_multi_step_from_init_fp64():
@@ -117,9 +161,9 @@ def test_full_size_batch_first_run_matches_oracle():
     gom, gpop, gvel = h.get_state(2)
     assert rel_err(gphi, st.phi) < 2e-6
     assert fluct_err(gom, st.omega) < 2e-6
-    # the force is (1/beta v) dPhi^D / (D dt) with dPhi^D ~ 2e-3 a difference
-    # of two FP32 solves (error ~1e-7 each): ~1e-4 relative, see design notes
-    assert rel_err(gvel, st.vel) < 2e-3
+    # the second solve is the change from the first (differential solve), so
+    # the force keeps FP32 precision relative to dPhi^D (measured 2.5e-7)
+    assert rel_err(gvel, st.vel) < 1e-5
     for k in (0, 1, 3):
         ob = h.observables(k)
         assert abs((ob["mean_phi_a"] + ob["mean_phi_b"]) / runs[k].phi_p - 1) < 1e-6
