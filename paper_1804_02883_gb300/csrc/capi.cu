@@ -73,17 +73,14 @@ size_t carve_group(Group &G, char *base, size_t off)
     G.twy_d = (double2 *)take((size_t)G.g.ny / 2 * sizeof(double2));
     G.twx_full = (float2 *)take((size_t)G.g.nx * sizeof(float2));
     G.twy_full = (float2 *)take((size_t)G.g.ny * sizeof(float2));
-    // reference + differential solve pair of the cluster solve (MIXED_FP32)
-    G.hist1 = nullptr;
-    G.defac = nullptr;
-    G.dia = G.dib = G.dia2 = G.dib2 = nullptr;
+    // cluster solve (MIXED_FP32): stored states of both chains, and the
+    // differential second solve's buffers
+    G.hc = G.hd = G.defac = nullptr;
     if (G.prec == EPD_LB_MIXED_FP32 && cluster_shape_exists(G.g.logx, G.g.logy)) {
-        G.hist1 = take(R * 2 * (size_t)(G.g.ns + 1) * n * sizeof(float));
+        const size_t hs = R * cluster_state_floats2(G.g.nx, G.g.ny, G.g.ns) * sizeof(float2);
+        G.hc = take(hs);
+        G.hd = take(hs);
         G.defac = take(R * n * sizeof(float2));
-        G.dia = (double *)take(R * n * sizeof(double));
-        G.dib = (double *)take(R * n * sizeof(double));
-        G.dia2 = (double *)take(R * n * sizeof(double));
-        G.dib2 = (double *)take(R * n * sizeof(double));
     }
     G.diff = false;  // set once the cluster solve is known to launch
     return align_up(off);
@@ -117,13 +114,11 @@ static Group run_view(const Group &G, int r)
     V.pop[1] = (char *)V.pop[1] + (size_t)r * 9 * n * tb;
     V.vel = (char *)V.vel + (size_t)r * n * 2 * tb;
     V.force = (char *)V.force + (size_t)r * n * 2 * tb;
-    if (G.hist1) {
-        V.hist1 = (char *)V.hist1 + (size_t)r * 2 * (G.g.ns + 1) * n * sizeof(float);
+    if (G.hc) {
+        const size_t hs = cluster_state_floats2(G.g.nx, G.g.ny, G.g.ns) * sizeof(float2);
+        V.hc = (char *)V.hc + (size_t)r * hs;
+        V.hd = (char *)V.hd + (size_t)r * hs;
         V.defac = (char *)V.defac + (size_t)r * n * sizeof(float2);
-        V.dia += (size_t)r * n;
-        V.dib += (size_t)r * n;
-        V.dia2 += (size_t)r * n;
-        V.dib2 += (size_t)r * n;
     }
     return V;
 }
@@ -424,7 +419,7 @@ static cudaError_t enqueue_group(epd_lb *h, size_t gi, int parity, cudaStream_t 
         probe.m_acc = std::min(G.g.ns, (3 * G.g.ns) / 4 + 1);
     }
     if ((e = launch_aux_convection(G, s))) return e;                      // omega -> omega~
-    if ((e = launch_solve(G, G.omega_t, G.phi_t, G.q_t, s, nullptr, G.diff))) return e;  // Phi~
+    if ((e = launch_solve(G, G.omega_t, G.phi_t, G.q_t, s))) return e;    // Phi~
     if (mode == STEP_CHECK) {
         // the surrogate at omega~ into the EPD scratch, residual against Phi~
         double pa, pb, ps;
@@ -562,7 +557,7 @@ extern "C" int epd_lb_init(const epd_lb_params *p, int32_t nruns, void *workspac
         if (upload_tables_e(G, h->stream) != cudaSuccess) return bail(EPD_LB_ECUDA);
         if (launch_init_state(G, h->stream) != cudaSuccess) return bail(EPD_LB_ECUDA);
         if (launch_solve(G, G.omega, G.phi, G.q, h->stream) != cudaSuccess) return bail(EPD_LB_ECUDA);
-        G.diff = G.hist1 != nullptr && cluster_solve_supported(G);
+        G.diff = G.hd != nullptr && G.twx_full != nullptr && cluster_solve_supported(G);
     }
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(EPD_LB_ECUDA);
     for (size_t gi = 1; gi < h->groups.size(); ++gi) {

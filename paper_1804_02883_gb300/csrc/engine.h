@@ -48,10 +48,12 @@ struct Group {
     double *ia, *ib;   // contour sums, [run][n]
     double *ia2, *ib2; // contour sums of the g' chain's terms (cluster solve), [run][n]
     // differential second solve (MIXED_FP32 with the cluster solve)
-    bool diff = false;        // the step uses the reference + differential solve pair
-    void *hist1 = nullptr;    // reference solve, every node of both chains, [run][2][ns+1][n] float
+    // cluster solve (MIXED_FP32): states of both chains at every node, in the
+    // padded row layout [run][chain][ns+1][ny/2][nx + nx/8] float2
+    void *hc = nullptr;       // plain / reference solve
+    void *hd = nullptr;       // differential second solve
     void *defac = nullptr;    // (dE_A, dE_B), [run][n] float2
-    double *dia = nullptr, *dib = nullptr, *dia2 = nullptr, *dib2 = nullptr;  // contour sums of the difference, [run][n]
+    bool diff = false;        // the step uses the reference + differential solve pair
     double2 *cz;       // 4 complex FP64 scratch planes per run: [run][4][n]
     double *part;      // reduction partials, [run][kMaxPart]
     double *f0_lat;    // [run]
@@ -93,10 +95,8 @@ struct SolveProbe {
 
 // Single-chain solve, Eqs. (6)-(11): omega (3n per run, FP64) -> phi (3n),
 // q (2 per run).  All runs of the group.
-// reference = true keeps every node of both chains for a following
-// launch_solve_delta (cluster solve only).
 cudaError_t launch_solve(Group &G, const double *omega, double *phi, double *q, cudaStream_t s,
-                         const SolveProbe *probe = nullptr, bool reference = false);
+                         const SolveProbe *probe = nullptr);
 // Second solve of the step as a difference from the reference solve at
 // omega~ (phi_t, q_t): Phi(t+dt) = Phi~ + dPhi, Q likewise (G.diff only).
 cudaError_t launch_solve_delta(Group &G, cudaStream_t s, const SolveProbe *probe = nullptr);
@@ -120,8 +120,11 @@ cudaError_t launch_pop_raw(Group &G, int run, int parity, double *dst, const dou
 // shape and precision, its launch, and its CTAs per run.
 bool cluster_solve_supported(const Group &G);
 bool cluster_shape_exists(int logx, int logy);
-// mode 0: plain, 1: reference (full history kept), 2: differential
-cudaError_t launch_cluster_solve(Group &G, cudaStream_t s, const void *twx_full, const void *twy_full, int mode);
+size_t cluster_state_floats2(int nx, int ny, int ns);  // per run, both chains
+// Chain launch plus contour sums and normalisation into phi, q (diff: the
+// differential solve into G.phi, G.q).  nprep_blocks: solvent partials.
+cudaError_t launch_cluster_solve(Group &G, cudaStream_t s, bool diff, int nprep_blocks, double *phi, double *q,
+                                 const SolveProbe *probe);
 int cluster_ctas(const Group &G);
 
 // Kernel attributes (dynamic shared memory limits), once per process.

@@ -239,37 +239,6 @@ __global__ void __launch_bounds__(kThreads) prop_prep_delta(GroupGeom g, const d
     if (threadIdx.x == 0) part[(size_t)run * kMaxPart + kMaxPart / 2 + blockIdx.x] = s;
 }
 
-// Phi = Phi~ + (phi_p dI - Phi~ dQ) / (Q~ + dQ) per species, the exact
-// rearrangement of phi_p I / Q - phi_p I~ / Q~ (Eqs. (9)-(11)); the solvent
-// likewise with (1 - phi_p) de.
-__global__ void __launch_bounds__(kThreads) prop_finalize_delta(GroupGeom g, int nrow_blocks, int nprep_blocks,
-                                                                const double *dia, const double *dib, const double *dia2,
-                                                                const double *dib2, const double *part, const double *phi_t,
-                                                                const double *q_t, double *phi, double *q, int *err)
-{
-    __shared__ double bc;
-    const int run = blockIdx.y;
-    const long long n = g.n;
-    const double *pr = part + (size_t)run * kMaxPart;
-    const double dqp = sum_partials(pr, nrow_blocks, 1, &bc) / (double)n;
-    const double dqs = sum_partials(pr + kMaxPart / 2, nprep_blocks, 1, &bc) / (double)n;
-    const double qp = q_t[2 * run] + dqp, qs = q_t[2 * run + 1] + dqs;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        q[2 * run] = qp;
-        q[2 * run + 1] = qs;
-        if (!(qp > 0.0) || !(qs > 0.0) || !isfinite(qp) || !isfinite(qs)) atomicOr(err, 1);
-    }
-    const double *ta = phi_t + (size_t)run * 3 * n, *tb = ta + n, *ts = tb + n;
-    double *pa = phi + (size_t)run * 3 * n, *pb = pa + n, *ps = pb + n;
-    const double *ja = dia + (size_t)run * n, *jb = dib + (size_t)run * n;
-    const double *ja2 = dia2 + (size_t)run * n, *jb2 = dib2 + (size_t)run * n;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        pa[i] = ta[i] + (g.phi_p * (ja[i] + ja2[i]) - ta[i] * dqp) / qp;
-        pb[i] = tb[i] + (g.phi_p * (jb[i] + jb2[i]) - tb[i] * dqp) / qp;
-        ps[i] = ts[i] + ((1.0 - g.phi_p) * ps[i] - ts[i] * dqs) / qs;
-    }
-}
-
 static int grid_for(long long n)
 {
     long long b = (n + kThreads - 1) / kThreads;
@@ -283,8 +252,7 @@ template <typename T>
 static size_t row_smem(const Group &G) { return (size_t)2 * (G.sh.rows_prop * G.g.nx) * sizeof(V2<T>) + (G.g.nx / 2) * sizeof(V2<T>) + G.g.nx * sizeof(T); }
 
 template <typename T>
-static cudaError_t solve_t(Group &G, const double *omega, double *phi, double *q, cudaStream_t s, const SolveProbe *probe,
-                           bool reference)
+static cudaError_t solve_t(Group &G, const double *omega, double *phi, double *q, cudaStream_t s, const SolveProbe *probe)
 {
     const GroupGeom &g = G.g;
     PropK<T> k;
@@ -304,19 +272,9 @@ static cudaError_t solve_t(Group &G, const double *omega, double *phi, double *q
 
     const int pg = grid_for(g.n);
     prop_prep<T><<<dim3(pg, g.nruns), kThreads, 0, s>>>(g, omega, reinterpret_cast<V2<T> *>(G.efac), phi, G.part);
-    if (reference && !(sizeof(T) == sizeof(float) && G.hist1 && G.twx_full && cluster_solve_supported(G)))
-        return cudaErrorInvalidValue;
-    if (sizeof(T) == sizeof(float) && G.twx_full && cluster_solve_supported(G)) {
-        // whole contour in one cluster-resident launch
-        if (probe) {
-            probe->cluster = true;
-            cudaEventRecordWithFlags(probe->ev[0], s, cudaEventRecordExternal);
-        }
-        cudaError_t e = launch_cluster_solve(G, s, G.twx_full, G.twy_full, reference ? 1 : 0);
-        if (e != cudaSuccess) return e;
-        if (probe) cudaEventRecordWithFlags(probe->ev[1], s, cudaEventRecordExternal);
-        prop_finalize<<<dim3(pg, g.nruns), kThreads, 0, s>>>(g, cluster_ctas(G), pg, G.ia, G.ib, G.ia2, G.ib2, G.part, phi, q, G.err);
-        return cudaGetLastError();
+    if (sizeof(T) == sizeof(float) && G.hc && G.twx_full && cluster_solve_supported(G)) {
+        // whole contour in one cluster-resident launch, then the contour sums
+        return launch_cluster_solve(G, s, false, pg, phi, q, probe);
     }
     prop_start<T><<<dim3(pg, g.nruns), kThreads, 0, s>>>(k);
     const dim3 gc(g.nx / G.sh.cols_prop, g.nruns), gr(g.ny / G.sh.rows_prop, g.nruns);
@@ -335,30 +293,20 @@ static cudaError_t solve_t(Group &G, const double *omega, double *phi, double *q
     return cudaGetLastError();
 }
 
-cudaError_t launch_solve(Group &G, const double *omega, double *phi, double *q, cudaStream_t s, const SolveProbe *probe,
-                         bool reference)
+cudaError_t launch_solve(Group &G, const double *omega, double *phi, double *q, cudaStream_t s, const SolveProbe *probe)
 {
-    if (G.prec == EPD_LB_MIXED_FP32) return solve_t<float>(G, omega, phi, q, s, probe, reference);
-    return solve_t<double>(G, omega, phi, q, s, probe, reference);
+    if (G.prec == EPD_LB_MIXED_FP32) return solve_t<float>(G, omega, phi, q, s, probe);
+    return solve_t<double>(G, omega, phi, q, s, probe);
 }
 
 cudaError_t launch_solve_delta(Group &G, cudaStream_t s, const SolveProbe *probe)
 {
-    if (!G.diff || !G.hist1) return cudaErrorInvalidValue;
+    if (!G.diff || !G.hd) return cudaErrorInvalidValue;
     const GroupGeom &g = G.g;
     const int pg = grid_for(g.n);
     prop_prep_delta<<<dim3(pg, g.nruns), kThreads, 0, s>>>(g, G.omega, G.omega_t, reinterpret_cast<const float2 *>(G.efac),
                                                           reinterpret_cast<float2 *>(G.defac), G.phi, G.part);
-    if (probe) {
-        probe->cluster = true;
-        cudaEventRecordWithFlags(probe->ev[0], s, cudaEventRecordExternal);
-    }
-    cudaError_t e = launch_cluster_solve(G, s, G.twx_full, G.twy_full, 2);
-    if (e != cudaSuccess) return e;
-    if (probe) cudaEventRecordWithFlags(probe->ev[1], s, cudaEventRecordExternal);
-    prop_finalize_delta<<<dim3(pg, g.nruns), kThreads, 0, s>>>(g, cluster_ctas(G), pg, G.dia, G.dib, G.dia2, G.dib2, G.part,
-                                                               G.phi_t, G.q_t, G.phi, G.q, G.err);
-    return cudaGetLastError();
+    return launch_cluster_solve(G, s, true, pg, G.phi, G.q, probe);
 }
 
 cudaError_t configure_prop_kernels()

@@ -1,28 +1,28 @@
-// prop_cluster.cu -- cluster-resident single-chain solve (Sec. 2, Eqs. (6)-(10)
+// prop_cluster.cu -- cluster-resident single-chain solve (Sec. 2, Eqs. (6)-(11)
 // of arXiv:1804.02883) for grids whose propagator field fits in the shared
 // memory of one thread-block cluster (FP32 bulk precision).
 //
-// One cluster of C CTAs carries one chain of one run: the forward propagator
-// g (Eq. (6)) or the backward propagator g' (Eq. (7)), so a launch holds
-// 2 x runs clusters.  The real field of the chain lives on chip in two
-// packings: CTA c owns complex rows [c R2, (c+1) R2), each holding the real
-// rows (2k, 2k+1) as (re, im), in its row buffer, and complex columns
-// [c W2, (c+1) W2), each holding the real columns (2j, 2j+1), in its column
-// buffer.  The Fourier factor of Eq. (8) is real, even and separable, so it
-// acts on each packed row / column as on two real ones.  One contour step:
+// One cluster of C CTAs carries one chain of one run through the whole
+// contour: the forward propagator g (Eq. (6)) or the backward propagator g'
+// (Eq. (7)), so a launch holds 2 x runs clusters.  The real field of the
+// chain lives on chip in two packings: CTA c owns complex rows
+// [c R2, (c+1) R2), each holding the real rows (2k, 2k+1) as (re, im), in its
+// row buffer, and complex columns [c W2, (c+1) W2), each holding the real
+// columns (2j, 2j+1), in its column buffer.  The Fourier factor of Eq. (8) is
+// real, even and separable, so it acts on each packed row / column as on two
+// real ones.  One contour step:
 //   gather rows -> my columns (distributed shared memory, 2 x 2 re/im
 //   transposes), column transform Ky, cluster barrier, gather columns -> my
-//   rows, row transform Kx, node factor, history or contour sums.
-// Two cluster barriers per contour step.
+//   rows, row transform Kx, node factors: a_m = E_m g_m = E_m^2 T(a_{m-1}).
+// Two cluster barriers per contour step.  The row buffer, which holds a_m
+// after the step, goes to global memory as one bulk asynchronous copy (TMA)
+// per step, in its padded on-chip layout; the copy overlaps the next step.
 //
-// The contour sums of Eqs. (9)-(10) need g and g' at mirrored nodes.  A solve
-// is two launches: the first runs nodes 1..N_s/2 of both chains and stores
-// them (history) plus the chain state; the second runs nodes N_s/2+1..N_s,
-// where the g cluster adds g(s_m) g'(1 - s_m) (node m) and the g' cluster
-// adds g(s_{N_s-m}) g'(s_m) (node N_s - m), reading the other chain's
-// first-half history; node N_s/2 itself is added by the g cluster from the
-// two histories.  Products and partial sums over up to 8 nodes with equal
-// trapezoid weights in FP32 registers, added into per-chain FP64 sums.
+// The contour sums of Eqs. (9)-(10) pair node m of g with node N_s - m of g'
+// at every site: a separate pass (prop_contour) reads both chains' stored
+// states, forms g_m g'_{N_s-m} = a_m a'_{N_s-m} / E_m^2 (both chains see the
+// same node factor at mirrored nodes), sums the trapezoid weights and
+// normalises (Eq. (11)).
 //
 // Transforms: register-resident radix-8 (one radix-2/4 pass where log2 N is
 // not a multiple of 3) Stockham passes in shared memory, in place.  The
@@ -31,6 +31,16 @@
 // thread); the inverse's last pass hands its points to the per-site
 // epilogue.  Twiddles come from per-pass tables laid out [k][p] so that
 // consecutive threads read consecutive entries.
+//
+// Differential solve (DIFF): the step's second solve differs from its first
+// (the reference, states a~) only by the diffusion update d omega of Eq. (5).
+// It propagates the change d a_m = a_m - a~_m through the same transforms:
+// with u = T(d a_{m-1}) and h~ = T(a~_{m-1}) = a~_m / E_m^2,
+//   dg_m  = E_m u + dE_m (h~ + u),
+//   d a_m = E_m dg_m + dE_m (g~_m + dg_m),
+// dE = E expm1(-N d omega ds / 2) from the FP64 difference; prop_contour_delta
+// then sums g~ dg' + dg g~' + dg dg'.  Exact algebra of the second solve;
+// only the rounding changes: FP32 relative to the change, not to Phi.
 #include <cooperative_groups.h>
 
 #include "common.cuh"
@@ -40,30 +50,15 @@ namespace cg = cooperative_groups;
 
 namespace epdlb {
 
-// Solve modes of the cluster kernel.
-//  0: plain solve; first-half history in `hist`.
-//  1: reference solve: every node of both chains kept in `hist1` (for a
-//     following differential solve), mirrored products read from it.
-//  2: differential solve at omega + d omega given the reference solve at
-//     omega: the chain carries d a_j = E_j dg_j + dE_j (g_j + dg_j), the
-//     epilogue forms dg_{j+1} = E_{j+1} T(d a_j) + dE_{j+1} (g_{j+1}/E_{j+1} + T(d a_j))
-//     (g, E of the reference solve; dE the change of the node factors), and
-//     the contour sums collect g dg' + dg g' + dg dg' (exact algebra of the
-//     two solves' difference, rounded relative to the difference itself).
 struct PropCK {
     GroupGeom g;
-    float *hist;         // [run][chain][half_lo + 1][n] real (modes 0 and 2)
-    float *hist1;        // [run][chain][N_s + 1][n] real (reference solve, modes 1 and 2)
-    const float2 *defac; // (dE_A, dE_B) [run][n] (mode 2)
-    int mode;
-    float2 *state;       // [run][chain][n / 2] packed rows, E z at node half_lo
-    const float2 *efac;  // [run][n] (E_A, E_B)
-    double *ia0, *ib0;   // contour sums of the g chain's terms, [run][n]
-    double *ia1, *ib1;   // contour sums of the g' chain's terms, [run][n]
-    double *part;
+    float2 *hout;         // stored states a_m (or d a_m): [run][chain][N_s + 1][NY/2][PITCH]
+    const float2 *href;   // reference states a~_m (DIFF)
+    const float2 *efac;   // (E_A, E_B) [run][n]
+    const float2 *defac;  // (dE_A, dE_B) [run][n] (DIFF)
+    double *part;         // Q partials [run][kMaxPart], first C entries
     const float2 *twx, *twy;  // exp(-2 pi i j / N), j < N
     const float *kx, *ky;     // exp(-R_G^2 k^2 ds) / N
-    int half;                 // 0: nodes 1..half_lo; 1: nodes half_lo..N_s
 };
 
 // Radix plan: passes of radix 8, the last forward pass takes the remainder.
@@ -278,40 +273,41 @@ __device__ __forceinline__ void fill_tables(float2 *tabs, const float2 *tw, int 
     }
 }
 
-__device__ __forceinline__ float wclass_a(int j, int na)
-{
-    if (na == 0 || j > na) return 0.f;
-    return (j == 0 || j == na) ? 0.5f : 1.f;
-}
-__device__ __forceinline__ float wclass_b(int j, int na, int ns)
-{
-    if (na == ns || j < na) return 0.f;
-    return (j == na || j == ns) ? 0.5f : 1.f;
-}
-
 template <int LOGX, int LOGY, int C, int T>
 struct ClusterGeom {
     static constexpr int NX = 1 << LOGX, NY = 1 << LOGY, R2 = NY / 2 / C, W2 = NX / 2 / C;
     static constexpr int P = R2 * NX;  // complex points per CTA in either packing
     static constexpr int PITCH = NX + NX / 8;
+    static constexpr int HN = NY / 2 * PITCH;  // stored complex slots per chain and node
     static constexpr int TABX = tabs_total(LOGX), TABY = tabs_total(LOGY);
-    // shared memory: row buffer, column buffer, twiddle tables, Fourier
-    // factors (at most ~110 KB, so that two CTAs fit on one SM and a launch's
-    // 16-CTA clusters are co-resident)
     static constexpr size_t SMEM = (size_t)(R2 * PITCH + P + TABX + TABY) * sizeof(float2) + (NX + NY) * sizeof(float);
+    static constexpr unsigned STORE_BYTES = (unsigned)(R2 * PITCH * sizeof(float2));
 };
 
-template <int LOGX, int LOGY, int C, int T, bool DIFF>
-__global__ void __launch_bounds__(T, 1024 / T) prop_cluster(PropCK k)
+// Bulk asynchronous copies (TMA, non-tensor form): shared -> global.
+__device__ __forceinline__ void bulk_store(void *gdst, const void *ssrc, unsigned bytes)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(ssrc);
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(s), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// MINB: CTAs per SM the register budget is sized for (65536 / (T MINB) each)
+template <int LOGX, int LOGY, int C, int T, int MINB, bool DIFF>
+__global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
 {
     using G = ClusterGeom<LOGX, LOGY, C, T>;
-    constexpr int NX = G::NX, NY = G::NY, R2 = G::R2, W2 = G::W2, P = G::P;
+    constexpr int NX = G::NX, NY = G::NY, R2 = G::R2, W2 = G::W2, P = G::P, HN = G::HN;
     static_assert(P == W2 * NY, "layout sizes");
     static_assert(P % (8 * T) == 0, "every pass gives each thread whole butterflies");
     static_assert(LOGX >= 4 && LOGY >= 4 && R2 >= 1 && W2 >= 1, "tile shape");
+    static_assert(G::STORE_BYTES % 16 == 0 && (HN * sizeof(float2)) % 16 == 0, "bulk copies of whole 16-byte units");
     using RL = RowLayout<LOGX>;
     using CL = ColLayout<LOGY, W2>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     float2 *rowbuf = reinterpret_cast<float2 *>(smem_raw);
     float2 *colbuf = rowbuf + R2 * G::PITCH;
     float2 *tabx = colbuf + P;
@@ -324,8 +320,7 @@ __global__ void __launch_bounds__(T, 1024 / T) prop_cluster(PropCK k)
     const int crank = (int)cl.block_rank();
     const int cidx = blockIdx.x / C, run = cidx >> 1, chain = cidx & 1;
     const int tid = threadIdx.x;
-    const long long n = k.g.n;
-    const int ns = k.g.ns, na = k.g.na, hlo = k.g.half_lo, hhi = k.g.half_hi;
+    const int n = (int)k.g.n, ns = k.g.ns, na = k.g.na;
     const int krow0 = crank * R2;  // first packed row of this CTA
 
     fill_tables<LOGX, 0>(tabx, k.twx, tid, T);
@@ -334,119 +329,35 @@ __global__ void __launch_bounds__(T, 1024 / T) prop_cluster(PropCK k)
     for (int i = tid; i < NY; i += T) ky[i] = k.ky[i];
     const float2 *efac = k.efac + (size_t)run * n;
     const float2 *defac = DIFF ? k.defac + (size_t)run * n : nullptr;
-    const int mode = DIFF ? 2 : k.mode;
-    const int hp = mode == 1 ? ns + 1 : hlo + 1;  // history pitch in nodes
-    float *hbase = mode == 1 ? k.hist1 : k.hist;
-    float *hist_me = hbase + (size_t)(run * 2 + chain) * hp * n;
-    const float *hist_other = hbase + (size_t)(run * 2 + (1 - chain)) * hp * n;
-    // reference solve's chains (mode 2)
-    const float *ref_me = DIFF ? k.hist1 + (size_t)(run * 2 + chain) * (ns + 1) * n : nullptr;
-    const float *ref_other = DIFF ? k.hist1 + (size_t)(run * 2 + (1 - chain)) * (ns + 1) * n : nullptr;
-    float2 *state = k.state + (size_t)(run * 2 + chain) * (n / 2);
-    __syncthreads();
+    // this CTA's block of the stored states of node m: hout + m * HN
+    float2 *hout = k.hout + (size_t)(run * 2 + chain) * (ns + 1) * HN + (size_t)crank * R2 * G::PITCH;
+    const float2 *href = DIFF ? k.href + (size_t)(run * 2 + chain) * (ns + 1) * HN + (size_t)crank * R2 * G::PITCH : nullptr;
 
     // node factor of this chain at contour node j: g carries w_A iff j < N_A,
     // g' sees the field of node N_s - j
-    auto sel = [&](float2 e, int j) { return ((chain == 0 ? j : ns - j) < na) ? e.x : e.y; };
+    auto blk_b = [&](int j) { return (chain == 0 ? j : ns - j) >= na; };
 
-    int m0, m1;
-    if (k.half == 0) {
-        for (int e = tid; e < P; e += T) {
-            const int b = e / NX, x = e % NX;
-            const long long site = (long long)(2 * (krow0 + b)) * NX + x;
-            if (DIFF) {  // dg_0 = 0, d a_0 = dE_0 g_0
-                hist_me[site] = 0.f;
-                hist_me[site + NX] = 0.f;
-                rowbuf[RL::at(b, x)] = f2(sel(defac[site], 0), sel(defac[site + NX], 0));
-            } else {
-                hist_me[site] = 1.f;
-                hist_me[site + NX] = 1.f;
-                rowbuf[RL::at(b, x)] = f2(sel(efac[site], 0), sel(efac[site + NX], 0));
-            }
-        }
-        m0 = 1;
-        m1 = hlo;
-    } else {
-        for (int e = tid; e < P; e += T) {
-            const int b = e / NX, x = e % NX;
-            rowbuf[RL::at(b, x)] = state[(size_t)(krow0 + b) * NX + x];
-        }
-        m0 = hlo + 1;
-        m1 = ns;
+    // node 0: g_0 = 1, a_0 = E_0 (d a_0 = dE_0)
+    for (int e = tid; e < P; e += T) {
+        const int b = e / NX, x = e % NX;
+        const int site = 2 * (krow0 + b) * NX + x;
+        const float2 f0 = DIFF ? defac[site] : efac[site], f1 = DIFF ? defac[site + NX] : efac[site + NX];
+        rowbuf[RL::at(b, x)] = blk_b(0) ? f2(f0.y, f1.y) : f2(f0.x, f1.x);
     }
+    fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) bulk_store(hout, rowbuf, G::STORE_BYTES);
 
     // epilogue geometry: the inverse row transform's last pass
     constexpr int RLOG_L = inv_rlog(LOGX, npasses(LOGX) - 1), RR = 1 << RLOG_L, PER_L = NX / RR;
     constexpr int NB_L = P / RR / T;
-    // one FP32 partial sum per real site over a group of at most 8 nodes that
-    // share the trapezoid weights (w_A, w_B); a group is added to the FP64
-    // sums with its weights when it is full or the weights change
-    float acc[NB_L][RR][2];
-#pragma unroll
-    for (int j = 0; j < NB_L; ++j)
-#pragma unroll
-        for (int r = 0; r < RR; ++r) acc[j][r][0] = acc[j][r][1] = 0.f;
-    int nacc = 0;
-    float gwa = 0.f, gwb = 0.f;
+    // node factors of this thread's epilogue sites, reloaded when the block changes
+    float ec[NB_L][RR][2];
+    int cur_b = -1;
     float qsum = 0.f;
-    double *ia = chain == 0 ? k.ia0 : k.ia1, *ib = chain == 0 ? k.ib0 : k.ib1;
-    ia += (size_t)run * n;
-    ib += (size_t)run * n;
 
-    auto flush = [&](int bb_j, int tt_j, int j) {
-        const double ca = k.g.ds * (double)gwa, cb = k.g.ds * (double)gwb;
-#pragma unroll
-        for (int r = 0; r < RR; ++r)
-#pragma unroll
-            for (int cp = 0; cp < 2; ++cp) {
-                const long long site = (long long)(2 * (krow0 + bb_j) + cp) * NX + tt_j + r * PER_L;
-                const double v = (double)acc[j][r][cp];
-                if (gwa != 0.f) ia[site] += ca * v;
-                if (gwb != 0.f) ib[site] += cb * v;
-                acc[j][r][cp] = 0.f;
-            }
-    };
-
-    if (k.half == 1) {
-        // this chain's FP64 sums start at zero
-        for (int e = tid; e < P; e += T) {
-            const int b = e / NX, x = e % NX;
-            const long long site = (long long)(2 * (krow0 + b)) * NX + x;
-            ia[site] = 0.0;
-            ib[site] = 0.0;
-            ia[site + NX] = 0.0;
-            ib[site + NX] = 0.0;
-        }
-        __syncthreads();
-    }
-
-    // node N_s/2 (even N_s): both chains are in the histories; the g cluster adds it
-    if (k.half == 1 && chain == 0 && hhi == hlo) {
-        gwa = wclass_a(hlo, na);
-        gwb = wclass_b(hlo, na, ns);
-#pragma unroll
-        for (int j = 0; j < NB_L; ++j) {
-            int b, t;
-            RL::template split<PER_L>(tid + j * T, b, t);
-#pragma unroll
-            for (int r = 0; r < RR; ++r)
-#pragma unroll
-                for (int cp = 0; cp < 2; ++cp) {
-                    const long long site = (long long)(2 * (krow0 + b) + cp) * NX + t + r * PER_L;
-                    const float a = hist_me[(size_t)hlo * n + site], o = hist_other[(size_t)hlo * n + site];
-                    if (DIFF) {
-                        const float ga = ref_me[(size_t)hlo * n + site], go = ref_other[(size_t)hlo * n + site];
-                        acc[j][r][cp] += ga * o + a * go + a * o;
-                    } else {
-                        acc[j][r][cp] += a * o;
-                    }
-                }
-        }
-        nacc = 1;
-    }
-
-    for (int m = m0; m <= m1; ++m) {
-        cl.sync();  // every row buffer holds E z of node m-1; column buffers are free
+    for (int m = 1; m <= ns; ++m) {
+        cl.sync();  // every row buffer holds a_{m-1}; column buffers are free
         // packed rows -> my packed columns: real rows (2kk, 2kk+1), real columns (2jj, 2jj+1);
         // all remote loads of a thread are issued before its stores
         {
@@ -479,7 +390,10 @@ __global__ void __launch_bounds__(T, 1024 / T) prop_cluster(PropCK k)
 #pragma unroll
                 for (int r = 0; r < (1 << RLOG_C); ++r) colbuf[CL::at(bb[j], tt[j] + r * (NY >> RLOG_C))] = x[j][r];
         }
-        cl.sync();  // every column buffer holds Ty E z; row buffers are free
+        // the bulk copy of a_{m-1} has finished reading the row buffer before
+        // this CTA arrives (the row buffer is rewritten below)
+        if (tid == 0) bulk_wait_read();
+        cl.sync();  // every column buffer holds Ty a; row buffers are free
         // packed columns -> my packed rows
         {
             constexpr int NG = R2 * (NX / 2) / T;
@@ -505,78 +419,195 @@ __global__ void __launch_bounds__(T, 1024 / T) prop_cluster(PropCK k)
         int bb[NB_L], tt[NB_L];
         last_inverse<LOGX, NB_L, T, RL>(rowbuf, h, bb, tt, tid);
 
-        const bool acc_node = k.half == 1;
-        const int jn = chain == 0 ? m : ns - m;  // contour node of this chain's term
-        if (acc_node) {
-            const float wa = wclass_a(jn, na), wb = wclass_b(jn, na, ns);
-            if (nacc > 0 && (wa != gwa || wb != gwb || nacc == 8)) {
+        const int bm = blk_b(m) ? 1 : 0;
+        if (bm != cur_b) {
+            cur_b = bm;
 #pragma unroll
-                for (int j = 0; j < NB_L; ++j) flush(bb[j], tt[j], j);
-                nacc = 0;
-            }
-            if (nacc == 0) {
-                gwa = wa;
-                gwb = wb;
-            }
-            ++nacc;
+            for (int j = 0; j < NB_L; ++j)
+#pragma unroll
+                for (int r = 0; r < RR; ++r) {
+                    const int site0 = 2 * (krow0 + bb[j]) * NX + tt[j] + r * PER_L;
+                    const float2 e0 = efac[site0], e1 = efac[site0 + NX];
+                    ec[j][r][0] = bm ? e0.y : e0.x;
+                    ec[j][r][1] = bm ? e1.y : e1.x;
+                }
         }
 #pragma unroll
         for (int j = 0; j < NB_L; ++j) {
 #pragma unroll
             for (int r = 0; r < RR; ++r) {
                 const int x = tt[j] + r * PER_L;
-                const long long site0 = (long long)(2 * (krow0 + bb[j])) * NX + x;
-                const float e0 = sel(efac[site0], m), e1 = sel(efac[site0 + NX], m);
+                const float e0 = ec[j][r][0], e1 = ec[j][r][1];
                 if (!DIFF) {
-                    const float z0 = e0 * h[j][r].x, z1 = e1 * h[j][r].y;
-                    if (!acc_node || mode == 1) {
-                        hist_me[(size_t)m * n + site0] = z0;
-                        hist_me[(size_t)m * n + site0 + NX] = z1;
-                    }
-                    if (acc_node) {
-                        acc[j][r][0] += z0 * hist_other[(size_t)(ns - m) * n + site0];
-                        acc[j][r][1] += z1 * hist_other[(size_t)(ns - m) * n + site0 + NX];
-                        if (m == ns) qsum += z0 + z1;
-                    }
-                    if (m < ns) rowbuf[RL::at(bb[j], x)] = f2(e0 * z0, e1 * z1);
+                    const float z0 = e0 * h[j][r].x, z1 = e1 * h[j][r].y;  // g_m
+                    if (m == ns) qsum += z0 + z1;
+                    rowbuf[RL::at(bb[j], x)] = f2(e0 * z0, e1 * z1);
                 } else {
-                    const float d0 = sel(defac[site0], m), d1 = sel(defac[site0 + NX], m);
-                    const float g0 = ref_me[(size_t)m * n + site0], g1 = ref_me[(size_t)m * n + site0 + NX];
-                    // dg = E T(da) + dE (T(a) + T(da)), T(a) = g / E of the reference solve
-                    const float dg0 = e0 * h[j][r].x + d0 * (g0 / e0 + h[j][r].x);
-                    const float dg1 = e1 * h[j][r].y + d1 * (g1 / e1 + h[j][r].y);
-                    if (!acc_node) {
-                        hist_me[(size_t)m * n + site0] = dg0;
-                        hist_me[(size_t)m * n + site0 + NX] = dg1;
-                    } else {
-                        const size_t mo = (size_t)(ns - m) * n + site0;
-                        const float o0 = hist_other[mo], o1 = hist_other[mo + NX];
-                        const float q0 = ref_other[mo], q1 = ref_other[mo + NX];
-                        acc[j][r][0] += g0 * o0 + dg0 * q0 + dg0 * o0;
-                        acc[j][r][1] += g1 * o1 + dg1 * q1 + dg1 * o1;
-                        if (m == ns) qsum += dg0 + dg1;
-                    }
-                    if (m < ns) rowbuf[RL::at(bb[j], x)] = f2(e0 * dg0 + d0 * (g0 + dg0), e1 * dg1 + d1 * (g1 + dg1));
+                    const int site0 = 2 * (krow0 + bb[j]) * NX + x;
+                    const float2 dd0 = defac[site0], dd1 = defac[site0 + NX];
+                    const float d0 = bm ? dd0.y : dd0.x, d1 = bm ? dd1.y : dd1.x;
+                    const float2 ar = href[(size_t)m * HN + RL::at(bb[j], x)];
+                    const float ri0 = __frcp_rn(e0), ri1 = __frcp_rn(e1);
+                    const float g0 = ar.x * ri0, g1 = ar.y * ri1;  // g~_m
+                    const float hr0 = g0 * ri0, hr1 = g1 * ri1;    // T(a~_{m-1})
+                    const float u0 = h[j][r].x, u1 = h[j][r].y;
+                    const float dg0 = e0 * u0 + d0 * (hr0 + u0), dg1 = e1 * u1 + d1 * (hr1 + u1);
+                    if (m == ns) qsum += dg0 + dg1;
+                    rowbuf[RL::at(bb[j], x)] = f2(e0 * dg0 + d0 * (g0 + dg0), e1 * dg1 + d1 * (g1 + dg1));
                 }
             }
         }
-        if (acc_node && m == ns) {
-#pragma unroll
-            for (int j = 0; j < NB_L; ++j) flush(bb[j], tt[j], j);
-            nacc = 0;
-        }
-    }
-    if (k.half == 0) {
+        fence_proxy_async();
         __syncthreads();
-        for (int e = tid; e < P; e += T) {
-            const int b = e / NX, x = e % NX;
-            state[(size_t)(krow0 + b) * NX + x] = rowbuf[RL::at(b, x)];
-        }
-    } else if (chain == 0) {
+        if (tid == 0) bulk_store(hout + (size_t)m * HN, rowbuf, G::STORE_BYTES);
+    }
+    if (chain == 0) {
         const double s = block_sum((double)qsum, red);
         if (tid == 0) k.part[(size_t)run * kMaxPart + crank] = s;
     }
+    if (tid == 0) bulk_wait_all();
     cl.sync();  // no CTA leaves while others may still read its shared memory
+}
+
+// ---------------------------------------------------------------------------
+// Contour sums and normalisation, Eqs. (9)-(11)
+// ---------------------------------------------------------------------------
+
+struct ContourK {
+    GroupGeom g;
+    int pitch, hn;          // stored layout: row pitch and slots per node
+    int nq, ns_part;        // Q partials (first nq entries), solvent partials (from kMaxPart/2)
+    const float2 *hc;       // states a_m (reference / plain solve)
+    const float2 *hd;       // changes d a_m (differential solve)
+    const float2 *efac, *defac;
+    const double *part;
+    const double *phi_t, *q_t;  // first solve's densities (differential solve)
+    double *phi, *q;
+    int *err;
+};
+
+// Trapezoid weights over [0, s_{N_A}] and [s_{N_A}, 1] in units of ds.
+__device__ __forceinline__ void node_weights(int j, int na, int ns, float &wa, float &wb)
+{
+    wa = (na == 0 || j > na) ? 0.f : ((j == 0 || j == na) ? 0.5f : 1.f);
+    wb = (na == ns || j < na) ? 0.f : ((j == na || j == ns) ? 0.5f : 1.f);
+}
+
+// One thread per packed site (real rows 2kk and 2kk+1 at column x).
+// Products in FP32, partial sums over at most 8 nodes of equal weights in
+// FP32, then FP64.
+template <bool DIFF>
+__global__ void __launch_bounds__(kThreads) prop_contour(ContourK k)
+{
+    __shared__ double bc;
+    const int run = blockIdx.y;
+    const int nx = k.g.nx, ny = k.g.ny, ns = k.g.ns, na = k.g.na;
+    const long long n = k.g.n;
+    const double *pr = k.part + (size_t)run * kMaxPart;
+    const double sq = sum_partials(pr, k.nq, 1, &bc) / (double)n;
+    const double ss = sum_partials(pr + kMaxPart / 2, k.ns_part, 1, &bc) / (double)n;
+    double qp, qs;
+    if (DIFF) {
+        qp = k.q_t[2 * run] + sq;
+        qs = k.q_t[2 * run + 1] + ss;
+    } else {
+        qp = sq;
+        qs = ss;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        k.q[2 * run] = qp;
+        k.q[2 * run + 1] = qs;
+        if (!(qp > 0.0) || !(qs > 0.0) || !isfinite(qp) || !isfinite(qs)) atomicOr(k.err, 1);
+    }
+    const int npk = nx * ny / 2;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npk) return;
+    const int kk = i / nx, x = i % nx;
+    const int s0 = 2 * kk * nx + x, s1 = s0 + nx;
+    const int slot = kk * k.pitch + x + (x >> 3);
+    const float2 *efac = k.efac + (size_t)run * n;
+    const float2 e0 = efac[s0], e1 = efac[s1];
+    const size_t cs = (size_t)(ns + 1) * k.hn;  // one chain's states
+    const float2 *c0 = k.hc + (size_t)run * 2 * cs + slot, *c1 = c0 + cs;
+    const float2 *d0 = DIFF ? k.hd + (size_t)run * 2 * cs + slot : nullptr, *d1 = DIFF ? d0 + cs : nullptr;
+    // per block (A, B) of the contour: 1 / E^2 (plain); 1 / E, dE, 1 / (E + dE) (DIFF)
+    float r2[2][2], ri[2][2], dd[2][2], rs[2][2];
+    {
+        const float e[2][2] = {{e0.x, e1.x}, {e0.y, e1.y}};
+        float2 de0 = f2(0.f, 0.f), de1 = f2(0.f, 0.f);
+        if (DIFF) {
+            const float2 *defac = k.defac + (size_t)run * n;
+            de0 = defac[s0];
+            de1 = defac[s1];
+        }
+        const float d[2][2] = {{de0.x, de1.x}, {de0.y, de1.y}};
+#pragma unroll
+        for (int bk = 0; bk < 2; ++bk)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                r2[bk][c] = 1.f / (e[bk][c] * e[bk][c]);
+                ri[bk][c] = 1.f / e[bk][c];
+                dd[bk][c] = d[bk][c];
+                rs[bk][c] = 1.f / (e[bk][c] + d[bk][c]);
+            }
+    }
+    double ia0 = 0.0, ib0 = 0.0, ia1 = 0.0, ib1 = 0.0;
+    float pa0 = 0.f, pa1 = 0.f, gwa = 0.f, gwb = 0.f;
+    int cnt = 0;
+    for (int m = 0; m <= ns; ++m) {
+        float wa, wb;
+        node_weights(m, na, ns, wa, wb);
+        if (cnt > 0 && (wa != gwa || wb != gwb || cnt == 8)) {
+            ia0 += (double)gwa * pa0;
+            ib0 += (double)gwb * pa0;
+            ia1 += (double)gwa * pa1;
+            ib1 += (double)gwb * pa1;
+            pa0 = pa1 = 0.f;
+            cnt = 0;
+        }
+        gwa = wa;
+        gwb = wb;
+        ++cnt;
+        const int bk = m >= na ? 1 : 0;  // g at node m and g' at node N_s - m see the same field
+        const float2 a = c0[(size_t)m * k.hn], b = c1[(size_t)(ns - m) * k.hn];
+        if (!DIFF) {
+            pa0 += a.x * b.x * r2[bk][0];
+            pa1 += a.y * b.y * r2[bk][1];
+        } else {
+            const float2 da = d0[(size_t)m * k.hn], db = d1[(size_t)(ns - m) * k.hn];
+            // g~ and dg of both chains: dg = (d a - dE g~) / (E + dE)
+            const float ga0 = a.x * ri[bk][0], ga1 = a.y * ri[bk][1], gb0 = b.x * ri[bk][0], gb1 = b.y * ri[bk][1];
+            const float dga0 = (da.x - dd[bk][0] * ga0) * rs[bk][0], dga1 = (da.y - dd[bk][1] * ga1) * rs[bk][1];
+            const float dgb0 = (db.x - dd[bk][0] * gb0) * rs[bk][0], dgb1 = (db.y - dd[bk][1] * gb1) * rs[bk][1];
+            pa0 += ga0 * dgb0 + dga0 * gb0 + dga0 * dgb0;
+            pa1 += ga1 * dgb1 + dga1 * gb1 + dga1 * dgb1;
+        }
+    }
+    ia0 += (double)gwa * pa0;
+    ib0 += (double)gwb * pa0;
+    ia1 += (double)gwa * pa1;
+    ib1 += (double)gwb * pa1;
+    const double ds = k.g.ds, php = k.g.phi_p;
+    double *pa = k.phi + (size_t)run * 3 * n, *pb = pa + n, *ps = pb + n;
+    if (!DIFF) {
+        const double c = php * ds / qp;
+        pa[s0] = c * ia0;
+        pb[s0] = c * ib0;
+        pa[s1] = c * ia1;
+        pb[s1] = c * ib1;
+        const double cs_ = (1.0 - php) / qs;
+        ps[s0] *= cs_;
+        ps[s1] *= cs_;
+    } else {
+        // Phi = Phi~ + (phi_p dI - Phi~ dQ) / (Q~ + dQ), the solvent with de
+        const double *ta = k.phi_t + (size_t)run * 3 * n, *tb = ta + n, *tsol = tb + n;
+        pa[s0] = ta[s0] + (php * ds * ia0 - ta[s0] * sq) / qp;
+        pb[s0] = tb[s0] + (php * ds * ib0 - tb[s0] * sq) / qp;
+        pa[s1] = ta[s1] + (php * ds * ia1 - ta[s1] * sq) / qp;
+        pb[s1] = tb[s1] + (php * ds * ib1 - tb[s1] * sq) / qp;
+        ps[s0] = tsol[s0] + ((1.0 - php) * ps[s0] - tsol[s0] * ss) / qs;
+        ps[s1] = tsol[s1] + ((1.0 - php) * ps[s1] - tsol[s1] * ss) / qs;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -590,15 +621,14 @@ struct ClusterShape {
     size_t smem;
 };
 
-template <int LOGX, int LOGY, int C, int T>
+template <int LOGX, int LOGY, int C, int T, int MINB = 1024 / T>
 static ClusterShape shape_of()
 {
-    return ClusterShape{LOGX, LOGY, C, T, (const void *)prop_cluster<LOGX, LOGY, C, T, false>,
-                        (const void *)prop_cluster<LOGX, LOGY, C, T, true>, ClusterGeom<LOGX, LOGY, C, T>::SMEM};
+    return ClusterShape{LOGX, LOGY, C, T, (const void *)prop_chain<LOGX, LOGY, C, T, MINB, false>,
+                        (const void *)prop_chain<LOGX, LOGY, C, T, MINB, true>, ClusterGeom<LOGX, LOGY, C, T>::SMEM};
 }
 
-// Instantiated grids (log2 nx, log2 ny): 4096 packed points per CTA with 256
-// threads (two CTAs fit on one SM), fewer on the smallest grids.
+// Instantiated grids (log2 nx, log2 ny).
 static const ClusterShape *find_shape(int logx, int logy)
 {
     static const ClusterShape shapes[] = {
@@ -651,43 +681,66 @@ bool cluster_solve_supported(const Group &G)
 
 bool cluster_shape_exists(int logx, int logy) { return find_shape(logx, logy) != nullptr; }
 
-cudaError_t launch_cluster_solve(Group &G, cudaStream_t s, const void *twx_full, const void *twy_full, int mode)
+size_t cluster_state_floats2(int nx, int ny, int ns) { return (size_t)2 * (ns + 1) * (ny / 2) * (nx + nx / 8); }
+
+int cluster_ctas(const Group &G)
 {
     const ClusterShape *sh = find_shape(G.g.logx, G.g.logy);
+    return sh ? sh->c : 0;
+}
+
+cudaError_t launch_cluster_solve(Group &G, cudaStream_t s, bool diff, int nprep_blocks, double *phi, double *q,
+                                 const SolveProbe *probe)
+{
+    const ClusterShape *sh = find_shape(G.g.logx, G.g.logy);
+    if (!sh || !G.hc || (diff && !G.hd)) return cudaErrorInvalidValue;
     PropCK k;
     k.g = G.g;
-    k.hist = reinterpret_cast<float *>(G.hist);
-    k.hist1 = reinterpret_cast<float *>(G.hist1);
-    k.defac = reinterpret_cast<const float2 *>(G.defac);
-    k.mode = mode;
-    k.state = reinterpret_cast<float2 *>(G.chain);
+    k.hout = reinterpret_cast<float2 *>(diff ? G.hd : G.hc);
+    k.href = reinterpret_cast<const float2 *>(G.hc);
     k.efac = reinterpret_cast<const float2 *>(G.efac);
-    k.ia0 = mode == 2 ? G.dia : G.ia;
-    k.ib0 = mode == 2 ? G.dib : G.ib;
-    k.ia1 = mode == 2 ? G.dia2 : G.ia2;
-    k.ib1 = mode == 2 ? G.dib2 : G.ib2;
+    k.defac = reinterpret_cast<const float2 *>(G.defac);
     k.part = G.part;
-    k.twx = reinterpret_cast<const float2 *>(twx_full);
-    k.twy = reinterpret_cast<const float2 *>(twy_full);
+    k.twx = reinterpret_cast<const float2 *>(G.twx_full);
+    k.twy = reinterpret_cast<const float2 *>(G.twy_full);
     k.kx = reinterpret_cast<const float *>(G.kx);
     k.ky = reinterpret_cast<const float *>(G.ky);
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr;
     set_cluster_cfg(cfg, attr, sh, 2 * G.g.nruns);
     cfg.stream = s;
-    for (int half = 0; half < 2; ++half) {
-        k.half = half;
-        void *args[] = {&k};
-        const cudaError_t e = cudaLaunchKernelExC(&cfg, mode == 2 ? sh->fn_diff : sh->fn, args);
-        if (e != cudaSuccess) return e;
+    if (probe) {
+        probe->cluster = true;
+        cudaEventRecordWithFlags(probe->ev[0], s, cudaEventRecordExternal);
     }
-    return cudaSuccess;
-}
+    void *args[] = {&k};
+    cudaError_t e = cudaLaunchKernelExC(&cfg, diff ? sh->fn_diff : sh->fn, args);
+    if (e != cudaSuccess) return e;
+    if (probe) cudaEventRecordWithFlags(probe->ev[1], s, cudaEventRecordExternal);
 
-int cluster_ctas(const Group &G)
-{
-    const ClusterShape *sh = find_shape(G.g.logx, G.g.logy);
-    return sh ? sh->c : 0;
+    ContourK c;
+    c.g = G.g;
+    c.pitch = G.g.nx + G.g.nx / 8;
+    c.hn = G.g.ny / 2 * c.pitch;
+    c.nq = sh->c;
+    c.ns_part = nprep_blocks;
+    c.hc = reinterpret_cast<const float2 *>(G.hc);
+    c.hd = reinterpret_cast<const float2 *>(G.hd);
+    c.efac = reinterpret_cast<const float2 *>(G.efac);
+    c.defac = reinterpret_cast<const float2 *>(G.defac);
+    c.part = G.part;
+    c.phi_t = G.phi_t;
+    c.q_t = G.q_t;
+    c.phi = phi;
+    c.q = q;
+    c.err = G.err;
+    const int npk = G.g.nx * G.g.ny / 2;
+    const dim3 grid((npk + kThreads - 1) / kThreads, G.g.nruns);
+    if (diff)
+        prop_contour<true><<<grid, kThreads, 0, s>>>(c);
+    else
+        prop_contour<false><<<grid, kThreads, 0, s>>>(c);
+    return cudaGetLastError();
 }
 
 } // namespace epdlb
