@@ -304,6 +304,7 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
     static_assert(P == W2 * NY, "layout sizes");
     static_assert(P % (8 * T) == 0, "every pass gives each thread whole butterflies");
     static_assert(LOGX >= 4 && LOGY >= 4 && R2 >= 1 && W2 >= 1, "tile shape");
+    static_assert(T % 32 == 0 && (NY / 2 * 2 * W2) % T == 0, "whole warps, whole gather steps");
     static_assert(G::STORE_BYTES % 16 == 0 && (HN * sizeof(float2)) % 16 == 0, "bulk copies of whole 16-byte units");
     using RL = RowLayout<LOGX>;
     using CL = ColLayout<LOGY, W2>;
@@ -358,24 +359,26 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
 
     for (int m = 1; m <= ns; ++m) {
         cl.sync();  // every row buffer holds a_{m-1}; column buffers are free
-        // packed rows -> my packed columns: real rows (2kk, 2kk+1), real columns (2jj, 2jj+1);
-        // all remote loads of a thread are issued before its stores
+        // packed rows -> my packed columns: real rows (2kk, 2kk+1), real columns (2jj, 2jj+1).
+        // Each thread loads one point per step, consecutive threads consecutive
+        // real columns x of packed row kk; lanes (2i, 2i+1) hold columns (x0, x0+1)
+        // and swap halves, the even lane forming real row 2kk, the odd lane 2kk+1.
+        // All remote loads of a thread are issued before its stores.
         {
-            constexpr int NG = NY / 2 * W2 / T;
-            float2 a[NG], c[NG];
+            constexpr int NG = NY / 2 * 2 * W2 / T;
+            float2 v[NG];
 #pragma unroll
             for (int u = 0; u < NG; ++u) {
-                const int e = tid + u * T, kk = e / W2, jl = e % W2;
-                const int src = kk / R2, bl = kk % R2, x0 = 2 * (crank * W2 + jl);
-                const float2 *rb = cl.map_shared_rank(rowbuf, src);
-                a[u] = rb[RL::at(bl, x0)];
-                c[u] = rb[RL::at(bl, x0 + 1)];
+                const int e = tid + u * T, kk = e / (2 * W2), xl = e % (2 * W2);
+                const float2 *rb = cl.map_shared_rank(rowbuf, kk / R2);
+                v[u] = rb[RL::at(kk % R2, 2 * crank * W2 + xl)];
             }
+            const bool odd = tid & 1;
 #pragma unroll
             for (int u = 0; u < NG; ++u) {
-                const int e = tid + u * T, kk = e / W2, jl = e % W2;
-                colbuf[CL::at(jl, 2 * kk)] = f2(a[u].x, c[u].x);
-                colbuf[CL::at(jl, 2 * kk + 1)] = f2(a[u].y, c[u].y);
+                const int e = tid + u * T, kk = e / (2 * W2), xl = e % (2 * W2);
+                const float t = __shfl_xor_sync(0xffffffffu, odd ? v[u].x : v[u].y, 1);
+                colbuf[CL::at(xl >> 1, 2 * kk + (odd ? 1 : 0))] = odd ? f2(t, v[u].y) : f2(v[u].x, t);
             }
         }
         __syncthreads();
