@@ -612,6 +612,7 @@ extern "C" int epd_lb_sync(epd_lb *h)
     int err = 0;
     CK(cudaMemcpy(&err, h->err, sizeof(int), cudaMemcpyDeviceToHost), "reading the device error word");
     if (err & 1) return fail(h, EPD_LB_ENONFINITE, "a single-chain solve produced Q <= 0 or a non-finite Q");
+    if (err & 4) return fail(h, EPD_LB_ETIMEOUT, "an exchange wait of the cluster solve gave up");
     return EPD_LB_OK;
 }
 

@@ -14,9 +14,11 @@
 //   gather rows -> my columns (distributed shared memory, 2 x 2 re/im
 //   transposes), column transform Ky, cluster barrier, gather columns -> my
 //   rows, row transform Kx, node factors: a_m = E_m g_m = E_m^2 T(a_{m-1}).
-// Two cluster barriers per contour step.  The row buffer, which holds a_m
-// after the step, goes to global memory as one bulk asynchronous copy (TMA)
-// per step, in its padded on-chip layout; the copy overlaps the next step.
+// The exchanges are pushes: each CTA writes its points into the owners'
+// buffers with st.async, counted as transaction bytes on the owner's
+// mbarrier, and a buffer is rewritten only after every CTA has passed the
+// relaxed cluster barrier that follows its last read of that buffer.  The
+// epilogue stores a_m (coalesced, fire-and-forget) for the contour sums.
 //
 // The contour sums of Eqs. (9)-(10) pair node m of g with node N_s - m of g'
 // at every site: a separate pass (prop_contour) reads both chains' stored
@@ -52,11 +54,12 @@ namespace epdlb {
 
 struct PropCK {
     GroupGeom g;
-    float2 *hout;         // stored states a_m (or d a_m): [run][chain][N_s + 1][NY/2][PITCH]
+    float2 *hout;         // stored states a_m (or d a_m): [run][chain][N_s + 1][NY/2][NX] (packed rows)
     const float2 *href;   // reference states a~_m (DIFF)
     const float2 *efac;   // (E_A, E_B) [run][n]
     const float2 *defac;  // (dE_A, dE_B) [run][n] (DIFF)
     double *part;         // Q partials [run][kMaxPart], first C entries
+    int *err;             // bit 2: an exchange wait gave up
     const float2 *twx, *twy;  // exp(-2 pi i j / N), j < N
     const float *kx, *ky;     // exp(-R_G^2 k^2 ds) / N
 };
@@ -128,18 +131,48 @@ template <bool INV> struct Dft<3, INV> {
     }
 };
 
-// Shared-memory layouts.  Row layout: sequence b (a packed row), point x,
-// padded by one slot per 8 points against bank conflicts.  Column layout:
-// point y of sequence c (a packed column) at y * W + c.
+// Shared-memory layouts.  Row layout: sequence b (a packed row), point x.
+// Rows of 128 points or more are unpadded with the low four bits of x
+// XOR-ed by the next four (x ^ ((x >> 4) & 15)): every access pattern of the
+// radix-8 passes then hits each 8-byte bank pair at most twice per warp
+// (almost all once) and 16-point groups stay aligned and contiguous;
+// 64-point rows are padded by one slot per 8 points.  Column layout: point y
+// of sequence c (a packed column) at y * W + c.
 template <int LOGN> struct RowLayout {
-    static constexpr int N = 1 << LOGN, PITCH = N + N / 8;
-    static __device__ __forceinline__ int at(int b, int x) { return b * PITCH + x + (x >> 3); }
+    static constexpr int N = 1 << LOGN, PITCH = LOGN >= 7 ? N : N + N / 8;
+    static __device__ __forceinline__ int at(int b, int x)
+    {
+        if constexpr (LOGN >= 7)
+            return b * PITCH + (x ^ ((x >> 4) & 15));
+        else
+            return b * PITCH + x + (x >> 3);
+    }
     template <int PER> static __device__ __forceinline__ void split(int bf, int &b, int &t) { b = bf / PER; t = bf % PER; }
 };
 template <int LOGN, int W> struct ColLayout {
     static __device__ __forceinline__ int at(int c, int y) { return y * W + c; }
     template <int PER> static __device__ __forceinline__ void split(int bf, int &b, int &t) { b = bf % W; t = bf / W; }
 };
+
+// Twiddles w[k] = w1^k, k = 1..R-1, of one butterfly from a pass table laid
+// out [k-1][p] (row length M): radix 8 reads w1, w2, w4 and forms the rest by
+// products (at most two roundings more than a table entry).
+template <int R>
+__device__ __forceinline__ void twiddles(float2 (&w)[R], const float2 *tab, int M, int p)
+{
+    if constexpr (R == 8) {
+        w[1] = tab[p];
+        w[2] = tab[M + p];
+        w[4] = tab[3 * M + p];
+        w[3] = fmul(w[1], w[2]);
+        w[5] = fmul(w[1], w[4]);
+        w[6] = fmul(w[2], w[4]);
+        w[7] = fmul(w[3], w[4]);
+    } else {
+#pragma unroll
+        for (int k = 1; k < R; ++k) w[k] = tab[(k - 1) * M + p];
+    }
+}
 
 // One in-place Stockham pass (radix 2^RLOG, stride 2^SLOG): load, wait, write.
 // tab: this pass's twiddles [k-1][p] (unused in a forward last pass).
@@ -161,11 +194,10 @@ __device__ __forceinline__ void pass(float2 *buf, const float2 *tab, int tid)
         Dft<RLOG, INV>::run(x[j]);
         const int q = tt[j] & (S - 1), p = tt[j] >> SLOG;
         if (M > 1) {
+            float2 w[R];
+            twiddles<R>(w, tab, M, p);
 #pragma unroll
-            for (int k = 1; k < R; ++k) {
-                const float2 w = tab[(k - 1) * M + p];
-                x[j][k] = INV ? fmulc(x[j][k], w) : fmul(x[j][k], w);
-            }
+            for (int k = 1; k < R; ++k) x[j][k] = INV ? fmulc(x[j][k], w[k]) : fmul(x[j][k], w[k]);
         }
 #pragma unroll
         for (int k = 0; k < R; ++k) buf[L::at(bb[j], q + R * S * p + S * k)] = x[j][k];
@@ -197,8 +229,10 @@ __device__ __forceinline__ void middle(float2 *buf, const float2 *tab_inv0, cons
             x[j][k].y *= f;
         }
         Dft<RLOG, true>::run(x[j]);
+        float2 w[R];
+        twiddles<R>(w, tab_inv0, PER, tt[j]);
 #pragma unroll
-        for (int k = 1; k < R; ++k) x[j][k] = fmulc(x[j][k], tab_inv0[(k - 1) * PER + tt[j]]);
+        for (int k = 1; k < R; ++k) x[j][k] = fmulc(x[j][k], w[k]);
 #pragma unroll
         for (int k = 0; k < R; ++k) buf[L::at(bb[j], R * tt[j] + k)] = x[j][k];
     }
@@ -277,23 +311,60 @@ template <int LOGX, int LOGY, int C, int T>
 struct ClusterGeom {
     static constexpr int NX = 1 << LOGX, NY = 1 << LOGY, R2 = NY / 2 / C, W2 = NX / 2 / C;
     static constexpr int P = R2 * NX;  // complex points per CTA in either packing
-    static constexpr int PITCH = NX + NX / 8;
-    static constexpr int HN = NY / 2 * PITCH;  // stored complex slots per chain and node
+    static constexpr int PITCH = RowLayout<LOGX>::PITCH;
+    static constexpr int HN = NY / 2 * NX;  // stored complex points per chain and node
     static constexpr int TABX = tabs_total(LOGX), TABY = tabs_total(LOGY);
     static constexpr size_t SMEM = (size_t)(R2 * PITCH + P + TABX + TABY) * sizeof(float2) + (NX + NY) * sizeof(float);
-    static constexpr unsigned STORE_BYTES = (unsigned)(R2 * PITCH * sizeof(float2));
 };
 
-// Bulk asynchronous copies (TMA, non-tensor form): shared -> global.
-__device__ __forceinline__ void bulk_store(void *gdst, const void *ssrc, unsigned bytes)
+// Distributed-shared-memory pushes: st.async of 8 bytes into a CTA of the
+// cluster, counted as transaction bytes on that CTA's mbarrier.
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned map_rank(unsigned addr, int rank)
 {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(ssrc);
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(s), "r"(bytes) : "memory");
-    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
 }
-__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void push_f2(unsigned raddr, float2 v, unsigned rbar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(raddr), "f"(v.x),
+                 "f"(v.y), "r"(rbar)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(unsigned bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for the phase with the given parity to complete, giving up after about
+// 2^31 cycles: then `failed` is set and every later wait returns at once (the
+// kernel runs to its end with the same barrier sequence and reports the error).
+__device__ __forceinline__ void mbar_wait(unsigned bar, unsigned parity, int &failed)
+{
+    if (failed) return;
+    const long long t0 = clock64();
+    while (!mbar_test(bar, parity))
+        if (clock64() - t0 > (1ll << 31)) {
+            failed = 1;
+            return;
+        }
+}
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.aligned;" ::: "memory"); }
 
 // MINB: CTAs per SM the register budget is sized for (65536 / (T MINB) each)
 template <int LOGX, int LOGY, int C, int T, int MINB, bool DIFF>
@@ -304,8 +375,7 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
     static_assert(P == W2 * NY, "layout sizes");
     static_assert(P % (8 * T) == 0, "every pass gives each thread whole butterflies");
     static_assert(LOGX >= 4 && LOGY >= 4 && R2 >= 1 && W2 >= 1, "tile shape");
-    static_assert(T % 32 == 0 && (NY / 2 * 2 * W2) % T == 0, "whole warps, whole gather steps");
-    static_assert(G::STORE_BYTES % 16 == 0 && (HN * sizeof(float2)) % 16 == 0, "bulk copies of whole 16-byte units");
+    static_assert(T % 32 == 0 && P % T == 0 && NX % 2 == 0, "whole warps, whole exchange steps, lane pairs");
     using RL = RowLayout<LOGX>;
     using CL = ColLayout<LOGY, W2>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -331,23 +401,36 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
     const float2 *efac = k.efac + (size_t)run * n;
     const float2 *defac = DIFF ? k.defac + (size_t)run * n : nullptr;
     // this CTA's block of the stored states of node m: hout + m * HN
-    float2 *hout = k.hout + (size_t)(run * 2 + chain) * (ns + 1) * HN + (size_t)crank * R2 * G::PITCH;
-    const float2 *href = DIFF ? k.href + (size_t)(run * 2 + chain) * (ns + 1) * HN + (size_t)crank * R2 * G::PITCH : nullptr;
+    float2 *hout = k.hout + (size_t)(run * 2 + chain) * (ns + 1) * HN + (size_t)krow0 * NX;
+    const float2 *href = DIFF ? k.href + (size_t)(run * 2 + chain) * (ns + 1) * HN + (size_t)krow0 * NX : nullptr;
 
     // node factor of this chain at contour node j: g carries w_A iff j < N_A,
     // g' sees the field of node N_s - j
     auto blk_b = [&](int j) { return (chain == 0 ? j : ns - j) >= na; };
+
+    // exchange barriers: [0] my column buffer, [1] my row buffer; each
+    // completes once per contour step when all P points have arrived
+    __shared__ __align__(8) unsigned long long mbar[2];
+    const unsigned bar_col = smem_u32(&mbar[0]), bar_row = smem_u32(&mbar[1]);
+    constexpr unsigned XBYTES = (unsigned)(P * sizeof(float2));
+    if (tid == 0) {
+        mbar_init(bar_col, 1);
+        mbar_init(bar_row, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_expect(bar_col, XBYTES);
+        mbar_expect(bar_row, XBYTES);
+    }
 
     // node 0: g_0 = 1, a_0 = E_0 (d a_0 = dE_0)
     for (int e = tid; e < P; e += T) {
         const int b = e / NX, x = e % NX;
         const int site = 2 * (krow0 + b) * NX + x;
         const float2 f0 = DIFF ? defac[site] : efac[site], f1 = DIFF ? defac[site + NX] : efac[site + NX];
-        rowbuf[RL::at(b, x)] = blk_b(0) ? f2(f0.y, f1.y) : f2(f0.x, f1.x);
+        const float2 a0 = blk_b(0) ? f2(f0.y, f1.y) : f2(f0.x, f1.x);
+        rowbuf[RL::at(b, x)] = a0;
+        hout[e] = a0;
     }
-    fence_proxy_async();
-    __syncthreads();
-    if (tid == 0) bulk_store(hout, rowbuf, G::STORE_BYTES);
+    cl.sync();  // every CTA's barriers are initialised, every row buffer holds a_0
 
     // epilogue geometry: the inverse row transform's last pass
     constexpr int RLOG_L = inv_rlog(LOGX, npasses(LOGX) - 1), RR = 1 << RLOG_L, PER_L = NX / RR;
@@ -356,32 +439,32 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
     float ec[NB_L][RR][2];
     int cur_b = -1;
     float qsum = 0.f;
+    int failed = 0;
+    const bool odd = tid & 1;
+    constexpr int NG = P / T;  // points each thread pushes per exchange
 
+    // One contour step.  The two exchanges push (st.async) into the owners'
+    // buffers; a buffer is rewritten only after every CTA has arrived at the
+    // relaxed cluster barrier that follows its last read of that buffer.
     for (int m = 1; m <= ns; ++m) {
-        cl.sync();  // every row buffer holds a_{m-1}; column buffers are free
-        // packed rows -> my packed columns: real rows (2kk, 2kk+1), real columns (2jj, 2jj+1).
-        // Each thread loads one point per step, consecutive threads consecutive
-        // real columns x of packed row kk; lanes (2i, 2i+1) hold columns (x0, x0+1)
-        // and swap halves, the even lane forming real row 2kk, the odd lane 2kk+1.
-        // All remote loads of a thread are issued before its stores.
-        {
-            constexpr int NG = NY / 2 * 2 * W2 / T;
-            float2 v[NG];
+        const unsigned par = (unsigned)(m - 1) & 1u;
+        if (m > 1) cluster_wait();  // every column buffer has been read out
+        // my packed rows -> the owners' packed columns.  Consecutive threads
+        // take consecutive real columns x of packed row kk; lanes (2i, 2i+1)
+        // hold columns (x0, x0+1) and swap halves, the even lane forming real
+        // row 2kk of packed column x0/2, the odd lane real row 2kk+1.
 #pragma unroll
-            for (int u = 0; u < NG; ++u) {
-                const int e = tid + u * T, kk = e / (2 * W2), xl = e % (2 * W2);
-                const float2 *rb = cl.map_shared_rank(rowbuf, kk / R2);
-                v[u] = rb[RL::at(kk % R2, 2 * crank * W2 + xl)];
-            }
-            const bool odd = tid & 1;
-#pragma unroll
-            for (int u = 0; u < NG; ++u) {
-                const int e = tid + u * T, kk = e / (2 * W2), xl = e % (2 * W2);
-                const float t = __shfl_xor_sync(0xffffffffu, odd ? v[u].x : v[u].y, 1);
-                colbuf[CL::at(xl >> 1, 2 * kk + (odd ? 1 : 0))] = odd ? f2(t, v[u].y) : f2(v[u].x, t);
-            }
+        for (int u = 0; u < NG; ++u) {
+            const int e = tid + u * T, bl = e / NX, x = e % NX;
+            const float2 v = rowbuf[RL::at(bl, x)];
+            const float t = __shfl_xor_sync(0xffffffffu, odd ? v.x : v.y, 1);
+            const int jj = x >> 1, dst = jj / W2;
+            const unsigned ra = map_rank(smem_u32(colbuf + CL::at(jj % W2, 2 * (krow0 + bl) + (odd ? 1 : 0))), dst);
+            push_f2(ra, odd ? f2(t, v.y) : f2(v.x, t), map_rank(bar_col, dst));
         }
-        __syncthreads();
+        cluster_arrive();  // my row buffer is read out
+        mbar_wait(bar_col, par, failed);
+        if (tid == 0 && m < ns) mbar_expect(bar_col, XBYTES);
         transform_pair<LOGY, T, CL, P>(colbuf, taby, ky, tid);
         {
             constexpr int RLOG_C = inv_rlog(LOGY, npasses(LOGY) - 1), NB_C = P / (1 << RLOG_C) / T;
@@ -393,30 +476,23 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
 #pragma unroll
                 for (int r = 0; r < (1 << RLOG_C); ++r) colbuf[CL::at(bb[j], tt[j] + r * (NY >> RLOG_C))] = x[j][r];
         }
-        // the bulk copy of a_{m-1} has finished reading the row buffer before
-        // this CTA arrives (the row buffer is rewritten below)
-        if (tid == 0) bulk_wait_read();
-        cl.sync();  // every column buffer holds Ty a; row buffers are free
-        // packed columns -> my packed rows
-        {
-            constexpr int NG = R2 * (NX / 2) / T;
-            float2 a[NG], c[NG];
-#pragma unroll
-            for (int u = 0; u < NG; ++u) {
-                const int e = tid + u * T, bl = e / (NX / 2), jj = e % (NX / 2);
-                const int src = jj / W2, jl = jj % W2, kk = krow0 + bl;
-                const float2 *cb = cl.map_shared_rank(colbuf, src);
-                a[u] = cb[CL::at(jl, 2 * kk)];
-                c[u] = cb[CL::at(jl, 2 * kk + 1)];
-            }
-#pragma unroll
-            for (int u = 0; u < NG; ++u) {
-                const int e = tid + u * T, bl = e / (NX / 2), jj = e % (NX / 2);
-                rowbuf[RL::at(bl, 2 * jj)] = f2(a[u].x, c[u].x);
-                rowbuf[RL::at(bl, 2 * jj + 1)] = f2(a[u].y, c[u].y);
-            }
-        }
         __syncthreads();
+        cluster_wait();  // every row buffer has been read out
+        // my packed columns -> the owners' packed rows: lanes (2i, 2i+1) hold
+        // real rows (2kk, 2kk+1) of packed column jl and swap halves, the even
+        // lane forming point x0 = 2 (c W2 + jl) of packed row kk, the odd lane x0+1.
+#pragma unroll
+        for (int u = 0; u < NG; ++u) {
+            const int e = tid + u * T, kk = e / (2 * W2), jl = (e % (2 * W2)) >> 1;
+            const float2 v = colbuf[CL::at(jl, 2 * kk + (odd ? 1 : 0))];
+            const float t = __shfl_xor_sync(0xffffffffu, odd ? v.x : v.y, 1);
+            const int dst = kk / R2;
+            const unsigned ra = map_rank(smem_u32(rowbuf + RL::at(kk % R2, 2 * (crank * W2 + jl) + (odd ? 1 : 0))), dst);
+            push_f2(ra, odd ? f2(t, v.y) : f2(v.x, t), map_rank(bar_row, dst));
+        }
+        cluster_arrive();  // my column buffer is read out
+        mbar_wait(bar_row, par, failed);
+        if (tid == 0 && m < ns) mbar_expect(bar_row, XBYTES);
         transform_pair<LOGX, T, RL, P>(rowbuf, tabx, kx, tid);
         float2 h[NB_L][RR];
         int bb[NB_L], tt[NB_L];
@@ -444,31 +520,34 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
                 if (!DIFF) {
                     const float z0 = e0 * h[j][r].x, z1 = e1 * h[j][r].y;  // g_m
                     if (m == ns) qsum += z0 + z1;
-                    rowbuf[RL::at(bb[j], x)] = f2(e0 * z0, e1 * z1);
+                    const float2 a = f2(e0 * z0, e1 * z1);
+                    rowbuf[RL::at(bb[j], x)] = a;
+                    hout[(size_t)m * HN + bb[j] * NX + x] = a;
                 } else {
                     const int site0 = 2 * (krow0 + bb[j]) * NX + x;
                     const float2 dd0 = defac[site0], dd1 = defac[site0 + NX];
                     const float d0 = bm ? dd0.y : dd0.x, d1 = bm ? dd1.y : dd1.x;
-                    const float2 ar = href[(size_t)m * HN + RL::at(bb[j], x)];
+                    const float2 ar = href[(size_t)m * HN + bb[j] * NX + x];
                     const float ri0 = __frcp_rn(e0), ri1 = __frcp_rn(e1);
                     const float g0 = ar.x * ri0, g1 = ar.y * ri1;  // g~_m
                     const float hr0 = g0 * ri0, hr1 = g1 * ri1;    // T(a~_{m-1})
                     const float u0 = h[j][r].x, u1 = h[j][r].y;
                     const float dg0 = e0 * u0 + d0 * (hr0 + u0), dg1 = e1 * u1 + d1 * (hr1 + u1);
                     if (m == ns) qsum += dg0 + dg1;
-                    rowbuf[RL::at(bb[j], x)] = f2(e0 * dg0 + d0 * (g0 + dg0), e1 * dg1 + d1 * (g1 + dg1));
+                    const float2 a = f2(e0 * dg0 + d0 * (g0 + dg0), e1 * dg1 + d1 * (g1 + dg1));
+                    rowbuf[RL::at(bb[j], x)] = a;
+                    hout[(size_t)m * HN + bb[j] * NX + x] = a;
                 }
             }
         }
-        fence_proxy_async();
         __syncthreads();
-        if (tid == 0) bulk_store(hout + (size_t)m * HN, rowbuf, G::STORE_BYTES);
     }
+    cluster_wait();  // pairs the last arrival
+    if (failed) atomicOr(k.err, 4);
     if (chain == 0) {
         const double s = block_sum((double)qsum, red);
         if (tid == 0) k.part[(size_t)run * kMaxPart + crank] = s;
     }
-    if (tid == 0) bulk_wait_all();
     cl.sync();  // no CTA leaves while others may still read its shared memory
 }
 
@@ -478,7 +557,7 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
 
 struct ContourK {
     GroupGeom g;
-    int pitch, hn;          // stored layout: row pitch and slots per node
+    int hn;                 // stored points per chain and node
     int nq, ns_part;        // Q partials (first nq entries), solvent partials (from kMaxPart/2)
     const float2 *hc;       // states a_m (reference / plain solve)
     const float2 *hd;       // changes d a_m (differential solve)
@@ -527,7 +606,7 @@ __global__ void __launch_bounds__(kThreads) prop_contour(ContourK k)
     if (i >= npk) return;
     const int kk = i / nx, x = i % nx;
     const int s0 = 2 * kk * nx + x, s1 = s0 + nx;
-    const int slot = kk * k.pitch + x + (x >> 3);
+    const int slot = kk * nx + x;
     const float2 *efac = k.efac + (size_t)run * n;
     const float2 e0 = efac[s0], e1 = efac[s1];
     const size_t cs = (size_t)(ns + 1) * k.hn;  // one chain's states
@@ -684,7 +763,7 @@ bool cluster_solve_supported(const Group &G)
 
 bool cluster_shape_exists(int logx, int logy) { return find_shape(logx, logy) != nullptr; }
 
-size_t cluster_state_floats2(int nx, int ny, int ns) { return (size_t)2 * (ns + 1) * (ny / 2) * (nx + nx / 8); }
+size_t cluster_state_floats2(int nx, int ny, int ns) { return (size_t)2 * (ns + 1) * (ny / 2) * nx; }
 
 int cluster_ctas(const Group &G)
 {
@@ -704,6 +783,7 @@ cudaError_t launch_cluster_solve(Group &G, cudaStream_t s, bool diff, int nprep_
     k.efac = reinterpret_cast<const float2 *>(G.efac);
     k.defac = reinterpret_cast<const float2 *>(G.defac);
     k.part = G.part;
+    k.err = G.err;
     k.twx = reinterpret_cast<const float2 *>(G.twx_full);
     k.twy = reinterpret_cast<const float2 *>(G.twy_full);
     k.kx = reinterpret_cast<const float *>(G.kx);
@@ -723,8 +803,7 @@ cudaError_t launch_cluster_solve(Group &G, cudaStream_t s, bool diff, int nprep_
 
     ContourK c;
     c.g = G.g;
-    c.pitch = G.g.nx + G.g.nx / 8;
-    c.hn = G.g.ny / 2 * c.pitch;
+    c.hn = G.g.ny / 2 * G.g.nx;
     c.nq = sh->c;
     c.ns_part = nprep_blocks;
     c.hc = reinterpret_cast<const float2 *>(G.hc);
