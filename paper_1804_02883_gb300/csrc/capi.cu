@@ -75,12 +75,12 @@ size_t carve_group(Group &G, char *base, size_t off)
     G.twy_full = (float2 *)take((size_t)G.g.ny * sizeof(float2));
     // cluster solve (MIXED_FP32): stored states of both chains, and the
     // differential second solve's buffers
-    G.hc = G.hd = G.defac = nullptr;
+    G.hc = G.hd = G.rho = nullptr;
     if (G.prec == EPD_LB_MIXED_FP32 && cluster_shape_exists(G.g.logx, G.g.logy)) {
         const size_t hs = R * cluster_state_floats2(G.g.nx, G.g.ny, G.g.ns) * sizeof(float2);
         G.hc = take(hs);
         G.hd = take(hs);
-        G.defac = take(R * n * sizeof(float2));
+        G.rho = take(R * n * sizeof(float2));
     }
     G.diff = false;  // set once the cluster solve is known to launch
     return align_up(off);
@@ -118,7 +118,7 @@ static Group run_view(const Group &G, int r)
         const size_t hs = cluster_state_floats2(G.g.nx, G.g.ny, G.g.ns) * sizeof(float2);
         V.hc = (char *)V.hc + (size_t)r * hs;
         V.hd = (char *)V.hd + (size_t)r * hs;
-        V.defac = (char *)V.defac + (size_t)r * n * sizeof(float2);
+        V.rho = (char *)V.rho + (size_t)r * n * sizeof(float2);
     }
     return V;
 }

@@ -52,7 +52,7 @@ struct Group {
     // padded row layout [run][chain][ns+1][ny/2][nx + nx/8] float2
     void *hc = nullptr;       // plain / reference solve
     void *hd = nullptr;       // differential second solve
-    void *defac = nullptr;    // (dE_A, dE_B), [run][n] float2
+    void *rho = nullptr;      // (rho_A, rho_B) = expm1(-N d omega ds / 2), [run][n] float2
     bool diff = false;        // the step uses the reference + differential solve pair
     double2 *cz;       // 4 complex FP64 scratch planes per run: [run][4][n]
     double *part;      // reduction partials, [run][kMaxPart]

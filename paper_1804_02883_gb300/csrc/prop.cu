@@ -209,13 +209,13 @@ __global__ void __launch_bounds__(kThreads) prop_finalize(GroupGeom g, int nrow_
 
 // Differential second solve (MIXED_FP32, cluster solve).  The step's second
 // solve differs from its first only by the diffusion update d omega = omega -
-// omega~ (Eq. (5)), small next to omega.  Its node factors are E~ (1 + expm1(
-// -N d omega ds / 2)) and its solvent factor e~ (1 + expm1(-d omega_S)), so the
-// changes dE, de follow from the FP64 difference with the rounding of FP32
-// relative to the change itself.  de goes to the S slot of phi, its block sums
-// to the S partials.
+// omega~ (Eq. (5)), small next to omega.  Its node factors are E~ (1 + rho),
+// rho = expm1(-N d omega ds / 2), and its solvent factor e~ (1 + expm1(
+// -d omega_S)), so the changes follow from the FP64 difference with the
+// rounding of FP32 relative to the change itself.  The solvent change de goes
+// to the S slot of phi, its block sums to the S partials.
 __global__ void __launch_bounds__(kThreads) prop_prep_delta(GroupGeom g, const double *omega, const double *omega_t,
-                                                            const float2 *efac, float2 *defac, double *phi_out, double *part)
+                                                            float2 *rho, double *phi_out, double *part)
 {
     __shared__ double red[32];
     const int run = blockIdx.y;
@@ -226,9 +226,8 @@ __global__ void __launch_bounds__(kThreads) prop_prep_delta(GroupGeom g, const d
     const float c = (float)(-0.5 * g.nseg * g.ds);
     float acc = 0.f;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const float2 e = efac[(size_t)run * n + i];
         const float da = (float)(wa[i] - ta[i]), db = (float)(wb[i] - tb[i]);
-        defac[(size_t)run * n + i] = make_float2(e.x * expm1f(c * da), e.y * expm1f(c * db));
+        rho[(size_t)run * n + i] = make_float2(expm1f(c * da), expm1f(c * db));
         // e~_S exactly as the first solve formed it
         const float es = expf(-(float)ts[i]);
         const float de = es * expm1f(-(float)(ws[i] - ts[i]));
@@ -304,8 +303,8 @@ cudaError_t launch_solve_delta(Group &G, cudaStream_t s, const SolveProbe *probe
     if (!G.diff || !G.hd) return cudaErrorInvalidValue;
     const GroupGeom &g = G.g;
     const int pg = grid_for(g.n);
-    prop_prep_delta<<<dim3(pg, g.nruns), kThreads, 0, s>>>(g, G.omega, G.omega_t, reinterpret_cast<const float2 *>(G.efac),
-                                                          reinterpret_cast<float2 *>(G.defac), G.phi, G.part);
+    prop_prep_delta<<<dim3(pg, g.nruns), kThreads, 0, s>>>(g, G.omega, G.omega_t, reinterpret_cast<float2 *>(G.rho), G.phi,
+                                                          G.part);
     return launch_cluster_solve(G, s, true, pg, G.phi, G.q, probe);
 }
 

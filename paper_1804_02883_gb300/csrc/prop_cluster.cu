@@ -18,7 +18,8 @@
 // buffers with st.async, counted as transaction bytes on the owner's
 // mbarrier, and a buffer is rewritten only after every CTA has passed the
 // relaxed cluster barrier that follows its last read of that buffer.  The
-// epilogue stores a_m (coalesced, fire-and-forget) for the contour sums.
+// first exchange also stores a_{m-1} (coalesced, fire-and-forget) for the
+// contour sums.
 //
 // The contour sums of Eqs. (9)-(10) pair node m of g with node N_s - m of g'
 // at every site: a separate pass (prop_contour) reads both chains' stored
@@ -35,14 +36,16 @@
 // consecutive threads read consecutive entries.
 //
 // Differential solve (DIFF): the step's second solve differs from its first
-// (the reference, states a~) only by the diffusion update d omega of Eq. (5).
-// It propagates the change d a_m = a_m - a~_m through the same transforms:
-// with u = T(d a_{m-1}) and h~ = T(a~_{m-1}) = a~_m / E_m^2,
-//   dg_m  = E_m u + dE_m (h~ + u),
-//   d a_m = E_m dg_m + dE_m (g~_m + dg_m),
-// dE = E expm1(-N d omega ds / 2) from the FP64 difference; prop_contour_delta
-// then sums g~ dg' + dg g~' + dg dg'.  Exact algebra of the second solve;
-// only the rounding changes: FP32 relative to the change, not to Phi.
+// (the reference, states a~) only by the diffusion update d omega of Eq. (5):
+// its node factors are E' = E (1 + rho), rho = expm1(-N d omega ds / 2) from
+// the FP64 difference.  It propagates the change d a_m = a_m - a~_m through
+// the same transforms: with U = T(d a_{m-1}) and T(a~_{m-1}) = a~_m / E^2,
+//   d a_m = E'^2 U + rho (2 + rho) a~_m,
+// the exact difference of a_m = E'^2 T(a_{m-1}) and a~_m = E^2 T(a~_{m-1}),
+// both terms of the size of the change.  prop_contour<DIFF> recovers
+// dg = (d a - rho a~) / E' and sums g~ dg' + dg g~' + dg dg'.  Exact algebra
+// of the second solve; only the rounding changes: FP32 relative to the
+// change, not to Phi.
 #include <cooperative_groups.h>
 
 #include "common.cuh"
@@ -57,8 +60,7 @@ struct PropCK {
     float2 *hout;         // stored states a_m (or d a_m): [run][chain][N_s + 1][NY/2][NX] (packed rows)
     const float2 *href;   // reference states a~_m (DIFF)
     const float2 *efac;   // (E_A, E_B) [run][n]
-    const float2 *defac;  // (dE_A, dE_B) [run][n] (DIFF)
-    double *part;         // Q partials [run][kMaxPart], first C entries
+    const float2 *rho;    // (rho_A, rho_B) [run][n] (DIFF)
     int *err;             // bit 2: an exchange wait gave up
     const float2 *twx, *twy;  // exp(-2 pi i j / N), j < N
     const float *kx, *ky;     // exp(-R_G^2 k^2 ds) / N
@@ -71,8 +73,10 @@ __host__ __device__ constexpr int fwd_slog(int logn, int i) { return i == 0 ? 0 
 __host__ __device__ constexpr int inv_rlog(int logn, int i) { return fwd_rlog(logn, npasses(logn) - 1 - i); }
 __host__ __device__ constexpr int inv_slog(int logn, int i) { return i == 0 ? 0 : inv_slog(logn, i - 1) + inv_rlog(logn, i - 1); }
 // Twiddle tables: one per pass that needs twiddles (forward passes
-// 0..np-2, inverse passes 0..np-2), (R-1) x M entries, M = N / (S R).
-__host__ __device__ constexpr int tab_len(int logn, int slog, int rlog) { return ((1 << rlog) - 1) * ((1 << logn) >> (slog + rlog)); }
+// 0..np-2, inverse passes 0..np-2), rows x M entries, M = N / (S R): rows
+// k = 1, 2, 4 for radix 8 (the others are products), k = 1..R-1 otherwise.
+__host__ __device__ constexpr int tab_rows(int rlog) { return rlog == 3 ? 3 : (1 << rlog) - 1; }
+__host__ __device__ constexpr int tab_len(int logn, int slog, int rlog) { return tab_rows(rlog) * ((1 << logn) >> (slog + rlog)); }
 __host__ __device__ constexpr int fwd_off(int logn, int i) { return i == 0 ? 0 : fwd_off(logn, i - 1) + tab_len(logn, fwd_slog(logn, i - 1), fwd_rlog(logn, i - 1)); }
 __host__ __device__ constexpr int inv_off(int logn, int i)
 {
@@ -155,7 +159,7 @@ template <int LOGN, int W> struct ColLayout {
 };
 
 // Twiddles w[k] = w1^k, k = 1..R-1, of one butterfly from a pass table laid
-// out [k-1][p] (row length M): radix 8 reads w1, w2, w4 and forms the rest by
+// out [row][p] (row length M): radix 8 reads w1, w2, w4 and forms the rest by
 // products (at most two roundings more than a table entry).
 template <int R>
 __device__ __forceinline__ void twiddles(float2 (&w)[R], const float2 *tab, int M, int p)
@@ -163,7 +167,7 @@ __device__ __forceinline__ void twiddles(float2 (&w)[R], const float2 *tab, int 
     if constexpr (R == 8) {
         w[1] = tab[p];
         w[2] = tab[M + p];
-        w[4] = tab[3 * M + p];
+        w[4] = tab[2 * M + p];
         w[3] = fmul(w[1], w[2]);
         w[5] = fmul(w[1], w[4]);
         w[6] = fmul(w[2], w[4]);
@@ -298,9 +302,10 @@ __device__ __forceinline__ void fill_tables(float2 *tabs, const float2 *tw, int 
         constexpr int SLOG = INVP ? inv_slog(LOGN, PI) : fwd_slog(LOGN, PI);
         constexpr int RLOG = INVP ? inv_rlog(LOGN, PI) : fwd_rlog(LOGN, PI);
         constexpr int OFF = INVP ? inv_off(LOGN, PI) : fwd_off(LOGN, PI);
-        constexpr int M = (1 << LOGN) >> (SLOG + RLOG), LEN = ((1 << RLOG) - 1) * M;
+        constexpr int M = (1 << LOGN) >> (SLOG + RLOG), LEN = tab_rows(RLOG) * M;
         for (int e = tid; e < LEN; e += nthreads) {
-            const int k = e / M + 1, p = e % M;
+            const int row = e / M, p = e % M;
+            const int k = RLOG == 3 ? (1 << row) : row + 1;
             tabs[OFF + e] = tw[(p << SLOG) * k];
         }
         fill_tables<LOGN, I + 1>(tabs, tw, tid, nthreads);
@@ -315,6 +320,8 @@ struct ClusterGeom {
     static constexpr int HN = NY / 2 * NX;  // stored complex points per chain and node
     static constexpr int TABX = tabs_total(LOGX), TABY = tabs_total(LOGY);
     static constexpr size_t SMEM = (size_t)(R2 * PITCH + P + TABX + TABY) * sizeof(float2) + (NX + NY) * sizeof(float);
+    // the differential solve adds one float per real site: rho (2 + rho)
+    static constexpr size_t SMEM_DIFF = SMEM + (size_t)2 * P * sizeof(float);
 };
 
 // Distributed-shared-memory pushes: st.async of 8 bytes into a CTA of the
@@ -385,8 +392,7 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
     float2 *taby = tabx + G::TABX;
     float *kx = reinterpret_cast<float *>(taby + G::TABY);
     float *ky = kx + NX;
-    __shared__ double red[32];
-
+    float *c2s = ky + NY;  // DIFF: rho (2 + rho) of the epilogue sites, [(j RR + r) 2 + cp][T]
     cg::cluster_group cl = cg::this_cluster();
     const int crank = (int)cl.block_rank();
     const int cidx = blockIdx.x / C, run = cidx >> 1, chain = cidx & 1;
@@ -399,7 +405,7 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
     for (int i = tid; i < NX; i += T) kx[i] = k.kx[i];
     for (int i = tid; i < NY; i += T) ky[i] = k.ky[i];
     const float2 *efac = k.efac + (size_t)run * n;
-    const float2 *defac = DIFF ? k.defac + (size_t)run * n : nullptr;
+    const float2 *rho = DIFF ? k.rho + (size_t)run * n : nullptr;
     // this CTA's block of the stored states of node m: hout + m * HN
     float2 *hout = k.hout + (size_t)(run * 2 + chain) * (ns + 1) * HN + (size_t)krow0 * NX;
     const float2 *href = DIFF ? k.href + (size_t)(run * 2 + chain) * (ns + 1) * HN + (size_t)krow0 * NX : nullptr;
@@ -421,24 +427,30 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
         mbar_expect(bar_row, XBYTES);
     }
 
-    // node 0: g_0 = 1, a_0 = E_0 (d a_0 = dE_0)
+    // node 0: g_0 = 1, a_0 = E_0 (d a_0 = rho_0 E_0)
     for (int e = tid; e < P; e += T) {
         const int b = e / NX, x = e % NX;
         const int site = 2 * (krow0 + b) * NX + x;
-        const float2 f0 = DIFF ? defac[site] : efac[site], f1 = DIFF ? defac[site + NX] : efac[site + NX];
-        const float2 a0 = blk_b(0) ? f2(f0.y, f1.y) : f2(f0.x, f1.x);
+        const bool bk = blk_b(0);
+        const float2 f0 = efac[site], f1 = efac[site + NX];
+        float2 a0 = bk ? f2(f0.y, f1.y) : f2(f0.x, f1.x);
+        if (DIFF) {
+            const float2 r0 = rho[site], r1 = rho[site + NX];
+            a0.x *= bk ? r0.y : r0.x;
+            a0.y *= bk ? r1.y : r1.x;
+        }
         rowbuf[RL::at(b, x)] = a0;
-        hout[e] = a0;
     }
     cl.sync();  // every CTA's barriers are initialised, every row buffer holds a_0
 
     // epilogue geometry: the inverse row transform's last pass
     constexpr int RLOG_L = inv_rlog(LOGX, npasses(LOGX) - 1), RR = 1 << RLOG_L, PER_L = NX / RR;
     constexpr int NB_L = P / RR / T;
-    // node factors of this thread's epilogue sites, reloaded when the block changes
-    float ec[NB_L][RR][2];
+    // per-site factors of this thread's epilogue sites, reloaded when the
+    // block (A or B) changes: E^2 (plain) or E'^2 (DIFF) in registers,
+    // rho (2 + rho) (DIFF) in shared memory
+    float c1[NB_L][RR][2];
     int cur_b = -1;
-    float qsum = 0.f;
     int failed = 0;
     const bool odd = tid & 1;
     constexpr int NG = P / T;  // points each thread pushes per exchange
@@ -457,6 +469,7 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
         for (int u = 0; u < NG; ++u) {
             const int e = tid + u * T, bl = e / NX, x = e % NX;
             const float2 v = rowbuf[RL::at(bl, x)];
+            hout[(size_t)(m - 1) * HN + e] = v;  // a_{m-1} for the contour sums
             const float t = __shfl_xor_sync(0xffffffffu, odd ? v.x : v.y, 1);
             const int jj = x >> 1, dst = jj / W2;
             const unsigned ra = map_rank(smem_u32(colbuf + CL::at(jj % W2, 2 * (krow0 + bl) + (odd ? 1 : 0))), dst);
@@ -465,6 +478,17 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
         cluster_arrive();  // my row buffer is read out
         mbar_wait(bar_col, par, failed);
         if (tid == 0 && m < ns) mbar_expect(bar_col, XBYTES);
+        if (DIFF) {
+            // a~_m for this thread's epilogue sites, into L1 ahead of use
+#pragma unroll
+            for (int j = 0; j < NB_L; ++j) {
+                int b, t;
+                RL::template split<PER_L>(tid + j * T, b, t);
+#pragma unroll
+                for (int r = 0; r < RR; ++r)
+                    asm volatile("prefetch.global.L1 [%0];" ::"l"(href + (size_t)m * HN + b * NX + t + r * PER_L));
+            }
+        }
         transform_pair<LOGY, T, CL, P>(colbuf, taby, ky, tid);
         {
             constexpr int RLOG_C = inv_rlog(LOGY, npasses(LOGY) - 1), NB_C = P / (1 << RLOG_C) / T;
@@ -506,9 +530,19 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
 #pragma unroll
                 for (int r = 0; r < RR; ++r) {
                     const int site0 = 2 * (krow0 + bb[j]) * NX + tt[j] + r * PER_L;
-                    const float2 e0 = efac[site0], e1 = efac[site0 + NX];
-                    ec[j][r][0] = bm ? e0.y : e0.x;
-                    ec[j][r][1] = bm ? e1.y : e1.x;
+#pragma unroll
+                    for (int cp = 0; cp < 2; ++cp) {
+                        const float2 ef = efac[site0 + cp * NX];
+                        const float e = bm ? ef.y : ef.x;
+                        if (!DIFF) {
+                            c1[j][r][cp] = e * e;
+                        } else {
+                            const float2 rf = rho[site0 + cp * NX];
+                            const float q = bm ? rf.y : rf.x, ep = e * (1.f + q);
+                            c1[j][r][cp] = ep * ep;
+                            c2s[((j * RR + r) * 2 + cp) * T + tid] = q * (2.f + q);
+                        }
+                    }
                 }
         }
 #pragma unroll
@@ -516,38 +550,22 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
 #pragma unroll
             for (int r = 0; r < RR; ++r) {
                 const int x = tt[j] + r * PER_L;
-                const float e0 = ec[j][r][0], e1 = ec[j][r][1];
+                float2 a;
                 if (!DIFF) {
-                    const float z0 = e0 * h[j][r].x, z1 = e1 * h[j][r].y;  // g_m
-                    if (m == ns) qsum += z0 + z1;
-                    const float2 a = f2(e0 * z0, e1 * z1);
-                    rowbuf[RL::at(bb[j], x)] = a;
-                    hout[(size_t)m * HN + bb[j] * NX + x] = a;
+                    a = f2(c1[j][r][0] * h[j][r].x, c1[j][r][1] * h[j][r].y);
                 } else {
-                    const int site0 = 2 * (krow0 + bb[j]) * NX + x;
-                    const float2 dd0 = defac[site0], dd1 = defac[site0 + NX];
-                    const float d0 = bm ? dd0.y : dd0.x, d1 = bm ? dd1.y : dd1.x;
-                    const float2 ar = href[(size_t)m * HN + bb[j] * NX + x];
-                    const float ri0 = __frcp_rn(e0), ri1 = __frcp_rn(e1);
-                    const float g0 = ar.x * ri0, g1 = ar.y * ri1;  // g~_m
-                    const float hr0 = g0 * ri0, hr1 = g1 * ri1;    // T(a~_{m-1})
-                    const float u0 = h[j][r].x, u1 = h[j][r].y;
-                    const float dg0 = e0 * u0 + d0 * (hr0 + u0), dg1 = e1 * u1 + d1 * (hr1 + u1);
-                    if (m == ns) qsum += dg0 + dg1;
-                    const float2 a = f2(e0 * dg0 + d0 * (g0 + dg0), e1 * dg1 + d1 * (g1 + dg1));
-                    rowbuf[RL::at(bb[j], x)] = a;
-                    hout[(size_t)m * HN + bb[j] * NX + x] = a;
+                    const float2 ar = href[(size_t)m * HN + bb[j] * NX + x];  // a~_m
+                    const float q0 = c2s[((j * RR + r) * 2) * T + tid], q1 = c2s[((j * RR + r) * 2 + 1) * T + tid];
+                    a = f2(c1[j][r][0] * h[j][r].x + q0 * ar.x, c1[j][r][1] * h[j][r].y + q1 * ar.y);
                 }
+                rowbuf[RL::at(bb[j], x)] = a;
             }
         }
         __syncthreads();
     }
+    for (int e = tid; e < P; e += T) hout[(size_t)ns * HN + e] = rowbuf[RL::at(e / NX, e % NX)];  // a_{N_s}
     cluster_wait();  // pairs the last arrival
     if (failed) atomicOr(k.err, 4);
-    if (chain == 0) {
-        const double s = block_sum((double)qsum, red);
-        if (tid == 0) k.part[(size_t)run * kMaxPart + crank] = s;
-    }
     cl.sync();  // no CTA leaves while others may still read its shared memory
 }
 
@@ -555,14 +573,16 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
 // Contour sums and normalisation, Eqs. (9)-(11)
 // ---------------------------------------------------------------------------
 
+constexpr int kQBlocks = 32;  // blocks (and partials) of prop_qsum per run
+
 struct ContourK {
     GroupGeom g;
     int hn;                 // stored points per chain and node
     int nq, ns_part;        // Q partials (first nq entries), solvent partials (from kMaxPart/2)
     const float2 *hc;       // states a_m (reference / plain solve)
     const float2 *hd;       // changes d a_m (differential solve)
-    const float2 *efac, *defac;
-    const double *part;
+    const float2 *efac, *rho;
+    double *part;
     const double *phi_t, *q_t;  // first solve's densities (differential solve)
     double *phi, *q;
     int *err;
@@ -573,6 +593,40 @@ __device__ __forceinline__ void node_weights(int j, int na, int ns, float &wa, f
 {
     wa = (na == 0 || j > na) ? 0.f : ((j == 0 || j == na) ? 0.5f : 1.f);
     wb = (na == ns || j < na) ? 0.f : ((j == na || j == ns) ? 0.5f : 1.f);
+}
+
+// Q partials from node N_s of the g chain: Q_P = mean g_{N_s} with
+// g = a / E (plain); dQ_P = mean dg_{N_s}, dg = (d a - rho a~) / E' (DIFF).
+// Block sums into part[run][block].
+template <bool DIFF>
+__global__ void __launch_bounds__(kThreads) prop_qsum(ContourK k)
+{
+    __shared__ double red[32];
+    const int run = blockIdx.y;
+    const int nx = k.g.nx, ns = k.g.ns, na = k.g.na;
+    const long long n = k.g.n;
+    const int npk = nx * k.g.ny / 2;
+    const bool bm = ns >= na;  // node N_s of g carries w_B unless N_A = N_s
+    const size_t cs = (size_t)(ns + 1) * k.hn;
+    const float2 *a_ns = k.hc + (size_t)run * 2 * cs + (size_t)ns * k.hn;
+    const float2 *d_ns = DIFF ? k.hd + (size_t)run * 2 * cs + (size_t)ns * k.hn : nullptr;
+    const float2 *efac = k.efac + (size_t)run * n;
+    const float2 *rho = DIFF ? k.rho + (size_t)run * n : nullptr;
+    float acc = 0.f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npk; i += gridDim.x * blockDim.x) {
+        const int kk = i / nx, x = i % nx, s0 = 2 * kk * nx + x, s1 = s0 + nx;
+        const float2 e0 = efac[s0], e1 = efac[s1], a = a_ns[i];
+        const float E0 = bm ? e0.y : e0.x, E1 = bm ? e1.y : e1.x;
+        if (!DIFF) {
+            acc += a.x / E0 + a.y / E1;
+        } else {
+            const float2 r0 = rho[s0], r1 = rho[s1], d = d_ns[i];
+            const float q0 = bm ? r0.y : r0.x, q1 = bm ? r1.y : r1.x;
+            acc += (d.x - q0 * a.x) / (E0 * (1.f + q0)) + (d.y - q1 * a.y) / (E1 * (1.f + q1));
+        }
+    }
+    const double s = block_sum((double)acc, red);
+    if (threadIdx.x == 0) k.part[(size_t)run * kMaxPart + blockIdx.x] = s;
 }
 
 // One thread per packed site (real rows 2kk and 2kk+1 at column x).
@@ -612,25 +666,25 @@ __global__ void __launch_bounds__(kThreads) prop_contour(ContourK k)
     const size_t cs = (size_t)(ns + 1) * k.hn;  // one chain's states
     const float2 *c0 = k.hc + (size_t)run * 2 * cs + slot, *c1 = c0 + cs;
     const float2 *d0 = DIFF ? k.hd + (size_t)run * 2 * cs + slot : nullptr, *d1 = DIFF ? d0 + cs : nullptr;
-    // per block (A, B) of the contour: 1 / E^2 (plain); 1 / E, dE, 1 / (E + dE) (DIFF)
+    // per block (A, B) of the contour: 1 / E^2 (plain); 1 / E, rho, 1 / E' (DIFF)
     float r2[2][2], ri[2][2], dd[2][2], rs[2][2];
     {
         const float e[2][2] = {{e0.x, e1.x}, {e0.y, e1.y}};
-        float2 de0 = f2(0.f, 0.f), de1 = f2(0.f, 0.f);
+        float2 q0 = f2(0.f, 0.f), q1 = f2(0.f, 0.f);
         if (DIFF) {
-            const float2 *defac = k.defac + (size_t)run * n;
-            de0 = defac[s0];
-            de1 = defac[s1];
+            const float2 *rho = k.rho + (size_t)run * n;
+            q0 = rho[s0];
+            q1 = rho[s1];
         }
-        const float d[2][2] = {{de0.x, de1.x}, {de0.y, de1.y}};
+        const float q[2][2] = {{q0.x, q1.x}, {q0.y, q1.y}};
 #pragma unroll
         for (int bk = 0; bk < 2; ++bk)
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
                 r2[bk][c] = 1.f / (e[bk][c] * e[bk][c]);
                 ri[bk][c] = 1.f / e[bk][c];
-                dd[bk][c] = d[bk][c];
-                rs[bk][c] = 1.f / (e[bk][c] + d[bk][c]);
+                dd[bk][c] = q[bk][c];
+                rs[bk][c] = 1.f / (e[bk][c] * (1.f + q[bk][c]));
             }
     }
     double ia0 = 0.0, ib0 = 0.0, ia1 = 0.0, ib1 = 0.0;
@@ -657,10 +711,10 @@ __global__ void __launch_bounds__(kThreads) prop_contour(ContourK k)
             pa1 += a.y * b.y * r2[bk][1];
         } else {
             const float2 da = d0[(size_t)m * k.hn], db = d1[(size_t)(ns - m) * k.hn];
-            // g~ and dg of both chains: dg = (d a - dE g~) / (E + dE)
+            // g~ = a~ / E and dg = (d a - rho a~) / E' of both chains
             const float ga0 = a.x * ri[bk][0], ga1 = a.y * ri[bk][1], gb0 = b.x * ri[bk][0], gb1 = b.y * ri[bk][1];
-            const float dga0 = (da.x - dd[bk][0] * ga0) * rs[bk][0], dga1 = (da.y - dd[bk][1] * ga1) * rs[bk][1];
-            const float dgb0 = (db.x - dd[bk][0] * gb0) * rs[bk][0], dgb1 = (db.y - dd[bk][1] * gb1) * rs[bk][1];
+            const float dga0 = (da.x - dd[bk][0] * a.x) * rs[bk][0], dga1 = (da.y - dd[bk][1] * a.y) * rs[bk][1];
+            const float dgb0 = (db.x - dd[bk][0] * b.x) * rs[bk][0], dgb1 = (db.y - dd[bk][1] * b.y) * rs[bk][1];
             pa0 += ga0 * dgb0 + dga0 * gb0 + dga0 * dgb0;
             pa1 += ga1 * dgb1 + dga1 * gb1 + dga1 * dgb1;
         }
@@ -700,14 +754,15 @@ struct ClusterShape {
     int logx, logy, c, t;
     const void *fn;       // plain and reference solves
     const void *fn_diff;  // differential solve
-    size_t smem;
+    size_t smem, smem_diff;
 };
 
 template <int LOGX, int LOGY, int C, int T, int MINB = 1024 / T>
 static ClusterShape shape_of()
 {
     return ClusterShape{LOGX, LOGY, C, T, (const void *)prop_chain<LOGX, LOGY, C, T, MINB, false>,
-                        (const void *)prop_chain<LOGX, LOGY, C, T, MINB, true>, ClusterGeom<LOGX, LOGY, C, T>::SMEM};
+                        (const void *)prop_chain<LOGX, LOGY, C, T, MINB, true>, ClusterGeom<LOGX, LOGY, C, T>::SMEM,
+                        ClusterGeom<LOGX, LOGY, C, T>::SMEM_DIFF};
 }
 
 // Instantiated grids (log2 nx, log2 ny).
@@ -723,7 +778,8 @@ static const ClusterShape *find_shape(int logx, int logy)
     return nullptr;
 }
 
-static void set_cluster_cfg(cudaLaunchConfig_t &cfg, cudaLaunchAttribute &attr, const ClusterShape *s, int nclusters)
+static void set_cluster_cfg(cudaLaunchConfig_t &cfg, cudaLaunchAttribute &attr, const ClusterShape *s, int nclusters,
+                            bool diff)
 {
     attr.id = cudaLaunchAttributeClusterDimension;
     attr.val.clusterDim.x = s->c;
@@ -731,7 +787,7 @@ static void set_cluster_cfg(cudaLaunchConfig_t &cfg, cudaLaunchAttribute &attr, 
     attr.val.clusterDim.z = 1;
     cfg.gridDim = dim3(s->c * nclusters, 1, 1);
     cfg.blockDim = dim3(s->t, 1, 1);
-    cfg.dynamicSmemBytes = s->smem;
+    cfg.dynamicSmemBytes = diff ? s->smem_diff : s->smem;
     cfg.attrs = &attr;
     cfg.numAttrs = 1;
 }
@@ -745,17 +801,19 @@ bool cluster_solve_supported(const Group &G)
     int &st = checked[s->logx][s->logy];
     if (st == 0) {
         st = 2;
-        auto ok = [&](const void *fn) {
-            if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->smem) != cudaSuccess) return false;
+        auto ok = [&](bool diff) {
+            const void *fn = diff ? s->fn_diff : s->fn;
+            const size_t sm = diff ? s->smem_diff : s->smem;
+            if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return false;
             if (s->c > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
                 return false;
             cudaLaunchConfig_t cfg = {};
             cudaLaunchAttribute attr;
-            set_cluster_cfg(cfg, attr, s, 1);
+            set_cluster_cfg(cfg, attr, s, 1, diff);
             int nclusters = 0;
             return cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) == cudaSuccess && nclusters > 0;
         };
-        if (ok(s->fn) && ok(s->fn_diff)) st = 1;
+        if (ok(false) && ok(true)) st = 1;
         cudaGetLastError();
     }
     return st == 1;
@@ -781,8 +839,7 @@ cudaError_t launch_cluster_solve(Group &G, cudaStream_t s, bool diff, int nprep_
     k.hout = reinterpret_cast<float2 *>(diff ? G.hd : G.hc);
     k.href = reinterpret_cast<const float2 *>(G.hc);
     k.efac = reinterpret_cast<const float2 *>(G.efac);
-    k.defac = reinterpret_cast<const float2 *>(G.defac);
-    k.part = G.part;
+    k.rho = reinterpret_cast<const float2 *>(G.rho);
     k.err = G.err;
     k.twx = reinterpret_cast<const float2 *>(G.twx_full);
     k.twy = reinterpret_cast<const float2 *>(G.twy_full);
@@ -790,7 +847,7 @@ cudaError_t launch_cluster_solve(Group &G, cudaStream_t s, bool diff, int nprep_
     k.ky = reinterpret_cast<const float *>(G.ky);
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr;
-    set_cluster_cfg(cfg, attr, sh, 2 * G.g.nruns);
+    set_cluster_cfg(cfg, attr, sh, 2 * G.g.nruns, diff);
     cfg.stream = s;
     if (probe) {
         probe->cluster = true;
@@ -804,12 +861,12 @@ cudaError_t launch_cluster_solve(Group &G, cudaStream_t s, bool diff, int nprep_
     ContourK c;
     c.g = G.g;
     c.hn = G.g.ny / 2 * G.g.nx;
-    c.nq = sh->c;
+    c.nq = kQBlocks;
     c.ns_part = nprep_blocks;
     c.hc = reinterpret_cast<const float2 *>(G.hc);
     c.hd = reinterpret_cast<const float2 *>(G.hd);
     c.efac = reinterpret_cast<const float2 *>(G.efac);
-    c.defac = reinterpret_cast<const float2 *>(G.defac);
+    c.rho = reinterpret_cast<const float2 *>(G.rho);
     c.part = G.part;
     c.phi_t = G.phi_t;
     c.q_t = G.q_t;
@@ -817,11 +874,14 @@ cudaError_t launch_cluster_solve(Group &G, cudaStream_t s, bool diff, int nprep_
     c.q = q;
     c.err = G.err;
     const int npk = G.g.nx * G.g.ny / 2;
-    const dim3 grid((npk + kThreads - 1) / kThreads, G.g.nruns);
-    if (diff)
+    const dim3 grid((npk + kThreads - 1) / kThreads, G.g.nruns), gq(kQBlocks, G.g.nruns);
+    if (diff) {
+        prop_qsum<true><<<gq, kThreads, 0, s>>>(c);
         prop_contour<true><<<grid, kThreads, 0, s>>>(c);
-    else
+    } else {
+        prop_qsum<false><<<gq, kThreads, 0, s>>>(c);
         prop_contour<false><<<grid, kThreads, 0, s>>>(c);
+    }
     return cudaGetLastError();
 }
 
