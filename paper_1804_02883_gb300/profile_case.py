@@ -1,0 +1,34 @@
+"""Run a few coupled steps of a benchmark workload without timing or L2
+flushes, for kernel profilers:
+
+    python -m paper_1804_02883_gb300.profile_case --workload channel --steps 2
+"""
+from __future__ import annotations
+
+import argparse
+
+from . import binding as B
+from . import workloads as W
+
+WORKLOADS = {
+    "channel": lambda: W.channel_256x512(B.MIXED_FP32),
+    "ensemble32": lambda: W.ensemble_32(B.MIXED_FP32),
+    "vesicle": lambda: [W.vesicle_1024x2048(B.MIXED_FP32)],
+    "plain_small": lambda: [W.plain_small()],
+}
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="channel", choices=sorted(WORKLOADS))
+    ap.add_argument("--steps", type=int, default=2)
+    args = ap.parse_args()
+    h = B.EpdLb(WORKLOADS[args.workload]())
+    h.step(args.steps)
+    h.sync()
+    h.close()
+    print("ok")
+
+
+if __name__ == "__main__":
+    main()
