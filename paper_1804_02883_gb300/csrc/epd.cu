@@ -18,6 +18,7 @@
 
 #include "common.cuh"
 #include "engine.h"
+#include "fft8.cuh"
 
 namespace epdlb {
 
@@ -33,6 +34,7 @@ struct EpdK {
     void *force;
     int bulk_double;
     const void *twx, *twy;  // twiddles of the transform type
+    const float2 *twx_full, *twy_full;  // exp(-2 pi i j / N), j < N (FP32 radix-8 kernels)
     int rows, logc;
     double kunit_x, kunit_y;  // 2 pi / (n dx) per axis
     double mu_ref[3];         // mu_I at the homogeneous composition, omega = 0
@@ -228,6 +230,246 @@ __global__ void __launch_bounds__(kThreads) epd_col(EpdK k)
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 radix-8 versions of the row and column passes (MIXED_FP32, grids with
+// 64..2048 points per axis): the same operators and data flow as epd_row /
+// epd_col above, transforms from fft8.cuh.  A row tile holds 2048 points
+// (max(1, 2048 / nx) rows), a column tile 16 columns (8 from 1024 rows on).
+// ---------------------------------------------------------------------------
+
+template <int LOGX> struct RowTile {
+    static constexpr int NX = 1 << LOGX, ROWS = NX >= 2048 ? 1 : 2048 / NX, P = ROWS * NX, T = P / 8;
+    static constexpr int TAB = tabs_total(LOGX);
+    static constexpr size_t SMEM = (size_t)(ROWS * RowLayout<LOGX>::PITCH + TAB) * sizeof(float2);
+};
+template <int LOGY> struct ColTile {
+    static constexpr int NY = 1 << LOGY, C = LOGY >= 10 ? 8 : 16, P = C * NY, T = P / 8 > 512 ? 512 : P / 8;
+    static constexpr int TAB = tabs_total(LOGY);
+    static constexpr size_t SMEM = (size_t)(P + TAB) * sizeof(float2);
+};
+
+// i k / n (first derivative, Nyquist bin dropped) and -k^2 / n along one axis
+struct OpGrad {
+    int n;
+    float unit, inv_n;
+    __device__ __forceinline__ float2 operator()(int, int bin, float2 v) const
+    {
+        const float kk = (2 * bin == n ? 0.f : unit * (float)signed_bin(bin, n)) * inv_n;
+        return f2(-kk * v.y, kk * v.x);
+    }
+};
+struct OpLap {
+    int n;
+    float unit, inv_n;
+    __device__ __forceinline__ float2 operator()(int, int bin, float2 v) const
+    {
+        const float kk = unit * (float)signed_bin(bin, n), f = -kk * kk * inv_n;
+        return f2(v.x * f, v.y * f);
+    }
+};
+// force of Eq. (20) on a column of the row spectrum: c (i kx - ky) / |k|^2
+struct OpForce {
+    int nx, ny, x0;
+    float ux, uy, cforce;
+    __device__ __forceinline__ float2 operator()(int c, int my, float2 v) const
+    {
+        const int mx = x0 + c;
+        const float kx = ux * (float)signed_bin(mx, nx), ky = uy * (float)signed_bin(my, ny);
+        const float k2 = kx * kx + ky * ky;
+        if (k2 == 0.f) return f2(0.f, 0.f);
+        const float cc = cforce / k2;
+        const float kxo = 2 * mx == nx ? 0.f : kx, kyo = 2 * my == ny ? 0.f : ky;
+        return fmul(v, f2(-cc * kyo, cc * kxo));
+    }
+};
+
+template <int LOGX, int MODE>
+__global__ void __launch_bounds__(RowTile<LOGX>::T) epd_row8(EpdK k)
+{
+    using RT = RowTile<LOGX>;
+    using RL = RowLayout<LOGX>;
+    constexpr int NX = RT::NX, P = RT::P, T = RT::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *buf = reinterpret_cast<float2 *>(smem_raw);
+    float2 *tab = buf + RT::ROWS * RL::PITCH;
+    const GroupGeom &g = k.g;
+    const int run = blockIdx.y, pair = blockIdx.z, tid = threadIdx.x;
+    const long long n = g.n;
+    const long long base = (long long)blockIdx.x * P;
+    float2 *cz = reinterpret_cast<float2 *>(k.cz);
+    fill_tables<LOGX, 0>(tab, k.twx_full, tid, T);
+    for (int i = tid; i < P; i += T) {
+        const long long s = base + i;
+        float2 v;
+        if (MODE == ROW_GRAD) {
+            const double *om = k.omega + (size_t)run * 3 * n;
+            v = pair == 0 ? f2((float)om[s], (float)om[n + s]) : f2((float)om[2 * n + s], 0.f);
+        } else if (MODE == ROW_LAP) {
+            const double2 mu = mu_pair(k, k.phi_t + (size_t)run * 3 * n, k.omega_t + (size_t)run * 3 * n, n, s, pair);
+            v = f2((float)mu.x, (float)mu.y);
+        } else if (MODE == ROW_FWD_S) {
+            const double *p1 = k.phi + (size_t)run * 3 * n, *p0 = k.phi_t + (size_t)run * 3 * n;
+            const double sa = (p1[s] - p0[s]) + (p1[n + s] - p0[n + s]);
+            v = f2((float)(sa / g.d_p + (p1[2 * n + s] - p0[2 * n + s]) / g.d_s), 0.f);
+        } else {
+            v = cz[((size_t)run * 4 + 2) * n + s];
+        }
+        buf[RL::at(i / NX, i % NX)] = v;
+    }
+    __syncthreads();
+    if (MODE == ROW_FWD_S) {
+        forward<LOGX, T, RL, P>(buf, tab, tid);
+        for (int i = tid; i < P; i += T) cz[((size_t)run * 4 + 2) * n + base + i] = buf[RL::at(i / NX, i % NX)];
+        return;
+    }
+    const float unit = (float)k.kunit_x, inv_n = 1.f / (float)NX;
+    if (MODE == ROW_GRAD)
+        transform_pair<LOGX, T, RL, P>(buf, tab, OpGrad{NX, unit, inv_n}, tid);
+    else if (MODE == ROW_LAP)
+        transform_pair<LOGX, T, RL, P>(buf, tab, OpLap{NX, unit, inv_n}, tid);
+    else
+        inverse_open<LOGX, T, RL, P>(buf, tab, tid);
+    constexpr int RLOG_L = inv_rlog(LOGX, npasses(LOGX) - 1), RR = 1 << RLOG_L, PER_L = NX / RR, NB_L = P / RR / T;
+    float2 h[NB_L][RR];
+    int bb[NB_L], tt[NB_L];
+    last_inverse<LOGX, NB_L, T, RL>(buf, h, bb, tt, tid);
+#pragma unroll
+    for (int j = 0; j < NB_L; ++j)
+#pragma unroll
+        for (int r = 0; r < RR; ++r) {
+            const long long s = base + (long long)bb[j] * NX + tt[j] + r * PER_L;
+            if (MODE == ROW_INV_FORCE) {
+                const float2 f = f2(h[j][r].x * inv_n, h[j][r].y * inv_n);
+                if (k.bulk_double) reinterpret_cast<double2 *>(k.force)[(size_t)run * n + s] = make_double2((double)f.x, (double)f.y);
+                else reinterpret_cast<float2 *>(k.force)[(size_t)run * n + s] = f;
+            } else {
+                cz[((size_t)run * 4 + pair) * n + s] = h[j][r];
+            }
+        }
+}
+
+template <int LOGY, int MODE>
+__global__ void __launch_bounds__(ColTile<LOGY>::T) epd_col8(EpdK k)
+{
+    using CT = ColTile<LOGY>;
+    using CL = ColLayout<LOGY, CT::C>;
+    constexpr int NY = CT::NY, C = CT::C, P = CT::P, T = CT::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *buf = reinterpret_cast<float2 *>(smem_raw);
+    float2 *tab = buf + P;
+    const GroupGeom &g = k.g;
+    const int nx = g.nx, run = blockIdx.y, pair = blockIdx.z, x0 = blockIdx.x * C, tid = threadIdx.x;
+    const long long n = g.n;
+    float2 *cz = reinterpret_cast<float2 *>(k.cz);
+    fill_tables<LOGY, 0>(tab, k.twy_full, tid, T);
+    for (int i = tid; i < P; i += T) {
+        const long long s = (long long)(i / C) * nx + x0 + (i % C);
+        float2 v;
+        if (MODE == COL_CONVECT) {
+            const double *om = k.omega + (size_t)run * 3 * n;
+            v = pair == 0 ? f2((float)om[s], (float)om[n + s]) : f2((float)om[2 * n + s], 0.f);
+        } else if (MODE == COL_DIFFUSE) {
+            const double2 mu = mu_pair(k, k.phi_t + (size_t)run * 3 * n, k.omega_t + (size_t)run * 3 * n, n, s, pair);
+            v = f2((float)mu.x, (float)mu.y);
+        } else {
+            v = cz[((size_t)run * 4 + 2) * n + s];
+        }
+        buf[i] = v;  // CL::at(i % C, i / C)
+    }
+    __syncthreads();
+    const float uy = (float)k.kunit_y, inv_n = 1.f / (float)NY;
+    if (MODE == COL_CONVECT)
+        transform_pair<LOGY, T, CL, P>(buf, tab, OpGrad{NY, uy, inv_n}, tid);
+    else if (MODE == COL_DIFFUSE)
+        transform_pair<LOGY, T, CL, P>(buf, tab, OpLap{NY, uy, inv_n}, tid);
+    else
+        transform_pair<LOGY, T, CL, P>(
+            buf, tab, OpForce{nx, NY, x0, (float)k.kunit_x, uy, (float)(g.inv_beta_v * g.fstar / (g.dt * (double)NY))}, tid);
+    constexpr int RLOG_L = inv_rlog(LOGY, npasses(LOGY) - 1), RR = 1 << RLOG_L, PER_L = NY / RR, NB_L = P / RR / T;
+    float2 h[NB_L][RR];
+    int bb[NB_L], tt[NB_L];
+    last_inverse<LOGY, NB_L, T, CL>(buf, h, bb, tt, tid);
+#pragma unroll
+    for (int j = 0; j < NB_L; ++j)
+#pragma unroll
+        for (int r = 0; r < RR; ++r) {
+            const long long s = (long long)(tt[j] + r * PER_L) * nx + x0 + bb[j];
+            if (MODE == COL_FORCE) {
+                cz[((size_t)run * 4 + 2) * n + s] = h[j][r];
+            } else if (MODE == COL_CONVECT) {
+                // omega~ = omega - dt v . grad omega, v = u_lat dx/dt
+                const float2 dyf = h[j][r], dxf = cz[((size_t)run * 4 + pair) * n + s];
+                const double2 u = vel_at(k, (size_t)run * n + s);
+                const double vx = u.x * g.vscale, vy = u.y * g.vscale;
+                const double *om = k.omega + (size_t)run * 3 * n;
+                double *ot = k.omega_dst + (size_t)run * 3 * n;
+                if (pair == 0) {
+                    ot[s] = om[s] - g.dt * (vx * (double)dxf.x + vy * (double)dyf.x);
+                    ot[n + s] = om[n + s] - g.dt * (vx * (double)dxf.y + vy * (double)dyf.y);
+                } else {
+                    ot[2 * n + s] = om[2 * n + s] - g.dt * (vx * (double)dxf.x + vy * (double)dyf.x);
+                }
+            } else {
+                // omega(t+dt) = omega~ - dt D_I Lap mu_I
+                const float2 dyf = h[j][r], lxf = cz[((size_t)run * 4 + pair) * n + s];
+                const double *ot = k.omega_t + (size_t)run * 3 * n;
+                double *om = k.omega_dst + (size_t)run * 3 * n;
+                if (pair == 0) {
+                    om[s] = ot[s] - g.dt * g.d_p * ((double)lxf.x + (double)dyf.x);
+                    om[n + s] = ot[n + s] - g.dt * g.d_p * ((double)lxf.y + (double)dyf.y);
+                } else {
+                    om[2 * n + s] = ot[2 * n + s] - g.dt * g.d_s * ((double)lxf.x + (double)dyf.x);
+                }
+            }
+        }
+}
+
+// Launch of the radix-8 row / column pass for the group's grid, or false
+// when the grid has no radix-8 instantiation.
+template <int MODE, int L>
+static bool row8_at(int logx, const EpdK &k, dim3 grid_yz, cudaStream_t s)
+{
+    if constexpr (L > 11) {
+        return false;
+    } else {
+        if (logx != L) return row8_at<MODE, L + 1>(logx, k, grid_yz, s);
+        using RT = RowTile<L>;
+        static bool conf = false;
+        if (!conf) {
+            conf = cudaFuncSetAttribute(epd_row8<L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RT::SMEM) == cudaSuccess;
+            if (!conf) return false;
+        }
+        const int blocks = (int)(k.g.n / RT::P);
+        epd_row8<L, MODE><<<dim3(blocks, grid_yz.y, grid_yz.z), RT::T, RT::SMEM, s>>>(k);
+        return true;
+    }
+}
+template <int MODE, int L>
+static bool col8_at(int logy, const EpdK &k, dim3 grid_yz, cudaStream_t s)
+{
+    if constexpr (L > 11) {
+        return false;
+    } else {
+        if (logy != L) return col8_at<MODE, L + 1>(logy, k, grid_yz, s);
+        using CT = ColTile<L>;
+        if (k.g.nx % CT::C) return false;
+        static bool conf = false;
+        if (!conf) {
+            conf = cudaFuncSetAttribute(epd_col8<L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CT::SMEM) == cudaSuccess;
+            if (!conf) return false;
+        }
+        epd_col8<L, MODE><<<dim3(k.g.nx / CT::C, grid_yz.y, grid_yz.z), CT::T, CT::SMEM, s>>>(k);
+        return true;
+    }
+}
+// radix-8 passes apply to MIXED_FP32 groups with 64 <= nx, ny <= 2048 and at
+// least 2048 sites
+static bool use_r8(const Group &G)
+{
+    return G.prec == EPD_LB_MIXED_FP32 && G.twx_full && G.twy_full && G.g.logx >= 6 && G.g.logy >= 6 && G.g.logx <= 11 &&
+           G.g.logy <= 11 && G.g.n >= 2048;
+}
+
 static EpdK make_k(Group &G)
 {
     EpdK k;
@@ -244,6 +486,8 @@ static EpdK make_k(Group &G)
     // FP32 transforms use the bulk (FP32) twiddle tables, FP64 ones the FP64 tables
     k.twx = k.bulk_double ? (const void *)G.twx_d : G.twx;
     k.twy = k.bulk_double ? (const void *)G.twy_d : G.twy;
+    k.twx_full = reinterpret_cast<const float2 *>(G.twx_full);
+    k.twy_full = reinterpret_cast<const float2 *>(G.twy_full);
     k.rows = G.sh.rows_epd;
     k.logc = ilog2(G.sh.cols_epd);
     const double pi = 3.14159265358979323846;
@@ -266,6 +510,11 @@ template <typename TT> static cudaError_t aux_t(Group &G, cudaStream_t s)
 {
     EpdK k = make_k(G);
     k.omega_dst = G.omega_t;
+    if (use_r8(G)) {
+        const dim3 gz(1, G.g.nruns, 2);
+        if (row8_at<ROW_GRAD, 6>(G.g.logx, k, gz, s) && col8_at<COL_CONVECT, 6>(G.g.logy, k, gz, s)) return cudaGetLastError();
+        return cudaErrorInvalidConfiguration;
+    }
     epd_row<TT, ROW_GRAD><<<dim3(G.g.ny / G.sh.rows_epd, G.g.nruns, 2), kThreads, row_smem<TT>(G), s>>>(k);
     epd_col<TT, COL_CONVECT><<<dim3(G.g.nx / G.sh.cols_epd, G.g.nruns, 2), kThreads, col_smem<TT>(G), s>>>(k);
     return cudaGetLastError();
@@ -275,6 +524,11 @@ template <typename TT> static cudaError_t diffusion_t(Group &G, cudaStream_t s)
 {
     EpdK k = make_k(G);
     k.omega_dst = G.omega;
+    if (use_r8(G)) {
+        const dim3 gz(1, G.g.nruns, 2);
+        if (row8_at<ROW_LAP, 6>(G.g.logx, k, gz, s) && col8_at<COL_DIFFUSE, 6>(G.g.logy, k, gz, s)) return cudaGetLastError();
+        return cudaErrorInvalidConfiguration;
+    }
     epd_row<TT, ROW_LAP><<<dim3(G.g.ny / G.sh.rows_epd, G.g.nruns, 2), kThreads, row_smem<TT>(G), s>>>(k);
     epd_col<TT, COL_DIFFUSE><<<dim3(G.g.nx / G.sh.cols_epd, G.g.nruns, 2), kThreads, col_smem<TT>(G), s>>>(k);
     return cudaGetLastError();
@@ -283,6 +537,13 @@ template <typename TT> static cudaError_t diffusion_t(Group &G, cudaStream_t s)
 template <typename TT> static cudaError_t force_t(Group &G, cudaStream_t s)
 {
     EpdK k = make_k(G);
+    if (use_r8(G)) {
+        const dim3 gz(1, G.g.nruns, 1);
+        if (row8_at<ROW_FWD_S, 6>(G.g.logx, k, gz, s) && col8_at<COL_FORCE, 6>(G.g.logy, k, gz, s) &&
+            row8_at<ROW_INV_FORCE, 6>(G.g.logx, k, gz, s))
+            return cudaGetLastError();
+        return cudaErrorInvalidConfiguration;
+    }
     epd_row<TT, ROW_FWD_S><<<dim3(G.g.ny / G.sh.rows_epd, G.g.nruns, 1), kThreads, row_smem<TT>(G), s>>>(k);
     epd_col<TT, COL_FORCE><<<dim3(G.g.nx / G.sh.cols_epd, G.g.nruns, 1), kThreads, col_smem<TT>(G), s>>>(k);
     epd_row<TT, ROW_INV_FORCE><<<dim3(G.g.ny / G.sh.rows_epd, G.g.nruns, 1), kThreads, row_smem<TT>(G), s>>>(k);

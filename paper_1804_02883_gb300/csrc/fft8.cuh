@@ -1,0 +1,317 @@
+// fft8.cuh -- register-resident radix-8 Stockham transforms in shared memory
+// (FP32), shared by the cluster-resident solve and the EPD passes of the
+// hybrid LB/EPD step (arXiv:1804.02883, Sec. 2 and App. C).
+//
+// A tile holds sequences of N = 2^LOGN complex points in a layout L
+// (RowLayout: sequence-major; ColLayout: point-major).  Passes are in place:
+// every thread loads its points of the pass, the block synchronises, every
+// thread writes its results.  Radix 8, with one radix-2/4 pass where log2 N is
+// not a multiple of 3; twiddles from per-pass tables (fill_tables) laid out
+// [row][p] so that consecutive threads read consecutive entries.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace epdlb {
+
+// Radix plan: passes of radix 8, the last forward pass takes the remainder.
+__host__ __device__ constexpr int npasses(int logn) { return (logn + 2) / 3; }
+__host__ __device__ constexpr int fwd_rlog(int logn, int i) { return i < npasses(logn) - 1 ? 3 : logn - 3 * (npasses(logn) - 1); }
+__host__ __device__ constexpr int fwd_slog(int logn, int i) { return i == 0 ? 0 : fwd_slog(logn, i - 1) + fwd_rlog(logn, i - 1); }
+__host__ __device__ constexpr int inv_rlog(int logn, int i) { return fwd_rlog(logn, npasses(logn) - 1 - i); }
+__host__ __device__ constexpr int inv_slog(int logn, int i) { return i == 0 ? 0 : inv_slog(logn, i - 1) + inv_rlog(logn, i - 1); }
+// Twiddle tables: one per pass that needs twiddles (forward passes
+// 0..np-2, inverse passes 0..np-2), rows x M entries, M = N / (S R): rows
+// k = 1, 2, 4 for radix 8 (the others are products), k = 1..R-1 otherwise.
+__host__ __device__ constexpr int tab_rows(int rlog) { return rlog == 3 ? 3 : (1 << rlog) - 1; }
+__host__ __device__ constexpr int tab_len(int logn, int slog, int rlog) { return tab_rows(rlog) * ((1 << logn) >> (slog + rlog)); }
+__host__ __device__ constexpr int fwd_off(int logn, int i) { return i == 0 ? 0 : fwd_off(logn, i - 1) + tab_len(logn, fwd_slog(logn, i - 1), fwd_rlog(logn, i - 1)); }
+__host__ __device__ constexpr int inv_off(int logn, int i)
+{
+    return i == 0 ? fwd_off(logn, npasses(logn) - 1) : inv_off(logn, i - 1) + tab_len(logn, inv_slog(logn, i - 1), inv_rlog(logn, i - 1));
+}
+__host__ __device__ constexpr int tabs_total(int logn) { return inv_off(logn, npasses(logn) - 1); }
+
+__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ float2 fadd(float2 a, float2 b) { return f2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 fsub(float2 a, float2 b) { return f2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 fmul(float2 a, float2 b) { return f2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ float2 fmulc(float2 a, float2 b) { return f2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y); }  // a * conj(b)
+template <bool INV> __device__ __forceinline__ float2 rot90(float2 a) { return INV ? f2(-a.y, a.x) : f2(a.y, -a.x); }
+
+// In-register DFT of length 2^RLOG, natural order in and out; forward uses
+// exp(-2 pi i / R), inverse exp(+2 pi i / R).
+template <int RLOG, bool INV> struct Dft;
+template <bool INV> struct Dft<1, INV> {
+    static __device__ __forceinline__ void run(float2 *x)
+    {
+        const float2 a = x[0], b = x[1];
+        x[0] = fadd(a, b);
+        x[1] = fsub(a, b);
+    }
+};
+template <bool INV> struct Dft<2, INV> {
+    static __device__ __forceinline__ void run(float2 *x)
+    {
+        const float2 s02 = fadd(x[0], x[2]), d02 = fsub(x[0], x[2]);
+        const float2 s13 = fadd(x[1], x[3]), d13 = rot90<INV>(fsub(x[1], x[3]));
+        x[0] = fadd(s02, s13);
+        x[2] = fsub(s02, s13);
+        x[1] = fadd(d02, d13);
+        x[3] = fsub(d02, d13);
+    }
+};
+template <bool INV> struct Dft<3, INV> {
+    static __device__ __forceinline__ void run(float2 *x)
+    {
+        float2 e[4] = {x[0], x[2], x[4], x[6]};
+        float2 o[4] = {x[1], x[3], x[5], x[7]};
+        Dft<2, INV>::run(e);
+        Dft<2, INV>::run(o);
+        const float h = 0.70710678118654752440f;
+        const float2 o1 = INV ? f2(h * (o[1].x - o[1].y), h * (o[1].x + o[1].y)) : f2(h * (o[1].x + o[1].y), h * (o[1].y - o[1].x));
+        const float2 o2 = rot90<INV>(o[2]);
+        const float2 o3 = INV ? f2(-h * (o[3].x + o[3].y), h * (o[3].x - o[3].y)) : f2(h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y));
+        x[0] = fadd(e[0], o[0]);
+        x[4] = fsub(e[0], o[0]);
+        x[1] = fadd(e[1], o1);
+        x[5] = fsub(e[1], o1);
+        x[2] = fadd(e[2], o2);
+        x[6] = fsub(e[2], o2);
+        x[3] = fadd(e[3], o3);
+        x[7] = fsub(e[3], o3);
+    }
+};
+
+// Shared-memory layouts.  Row layout: sequence b (a packed row), point x.
+// Rows of 128 points or more are unpadded with the low four bits of x
+// XOR-ed by the next four (x ^ ((x >> 4) & 15)): every access pattern of the
+// radix-8 passes then hits each 8-byte bank pair at most twice per warp
+// (almost all once) and 16-point groups stay aligned and contiguous;
+// 64-point rows are padded by one slot per 8 points.  Column layout: point y
+// of sequence c (a packed column) at y * W + c.
+template <int LOGN> struct RowLayout {
+    static constexpr int N = 1 << LOGN, PITCH = LOGN >= 7 ? N : N + N / 8;
+    static __device__ __forceinline__ int at(int b, int x)
+    {
+        if constexpr (LOGN >= 7)
+            return b * PITCH + (x ^ ((x >> 4) & 15));
+        else
+            return b * PITCH + x + (x >> 3);
+    }
+    template <int PER> static __device__ __forceinline__ void split(int bf, int &b, int &t) { b = bf / PER; t = bf % PER; }
+};
+template <int LOGN, int W> struct ColLayout {
+    static __device__ __forceinline__ int at(int c, int y) { return y * W + c; }
+    template <int PER> static __device__ __forceinline__ void split(int bf, int &b, int &t) { b = bf % W; t = bf / W; }
+};
+
+// Twiddles w[k] = w1^k, k = 1..R-1, of one butterfly from a pass table laid
+// out [row][p] (row length M): radix 8 reads w1, w2, w4 and forms the rest by
+// products (at most two roundings more than a table entry).
+template <int R>
+__device__ __forceinline__ void twiddles(float2 (&w)[R], const float2 *tab, int M, int p)
+{
+    if constexpr (R == 8) {
+        w[1] = tab[p];
+        w[2] = tab[M + p];
+        w[4] = tab[2 * M + p];
+        w[3] = fmul(w[1], w[2]);
+        w[5] = fmul(w[1], w[4]);
+        w[6] = fmul(w[2], w[4]);
+        w[7] = fmul(w[3], w[4]);
+    } else {
+#pragma unroll
+        for (int k = 1; k < R; ++k) w[k] = tab[(k - 1) * M + p];
+    }
+}
+
+// One in-place Stockham pass (radix 2^RLOG, stride 2^SLOG): load, wait, write.
+// tab: this pass's twiddles [k-1][p] (unused in a forward last pass).
+template <int LOGN, int SLOG, int RLOG, bool INV, int NB, int T, class L>
+__device__ __forceinline__ void pass(float2 *buf, const float2 *tab, int tid)
+{
+    constexpr int N = 1 << LOGN, R = 1 << RLOG, S = 1 << SLOG, PER = N / R, M = N / (S * R);
+    float2 x[NB][R];
+    int bb[NB], tt[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        L::template split<PER>(tid + j * T, bb[j], tt[j]);
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[j][r] = buf[L::at(bb[j], tt[j] + r * PER)];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        Dft<RLOG, INV>::run(x[j]);
+        const int q = tt[j] & (S - 1), p = tt[j] >> SLOG;
+        if (M > 1) {
+            float2 w[R];
+            twiddles<R>(w, tab, M, p);
+#pragma unroll
+            for (int k = 1; k < R; ++k) x[j][k] = INV ? fmulc(x[j][k], w[k]) : fmul(x[j][k], w[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) buf[L::at(bb[j], q + R * S * p + S * k)] = x[j][k];
+    }
+    __syncthreads();
+}
+
+// Forward last pass, spectral operator, inverse first pass (same points per
+// thread).  op(b, bin, v) returns the operator applied to bin `bin` (natural
+// order) of sequence b.
+template <int LOGN, int RLOG, int NB, int T, class L, class Op>
+__device__ __forceinline__ void middle(float2 *buf, const float2 *tab_inv0, const Op &op, int tid)
+{
+    constexpr int N = 1 << LOGN, R = 1 << RLOG, PER = N / R;
+    float2 x[NB][R];
+    int bb[NB], tt[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        L::template split<PER>(tid + j * T, bb[j], tt[j]);
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[j][r] = buf[L::at(bb[j], tt[j] + r * PER)];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        Dft<RLOG, false>::run(x[j]);
+#pragma unroll
+        for (int k = 0; k < R; ++k) x[j][k] = op(bb[j], tt[j] + k * PER, x[j][k]);
+        Dft<RLOG, true>::run(x[j]);
+        float2 w[R];
+        twiddles<R>(w, tab_inv0, PER, tt[j]);
+#pragma unroll
+        for (int k = 1; k < R; ++k) x[j][k] = fmulc(x[j][k], w[k]);
+#pragma unroll
+        for (int k = 0; k < R; ++k) buf[L::at(bb[j], R * tt[j] + k)] = x[j][k];
+    }
+    __syncthreads();
+}
+
+// Inverse first pass alone (input: a spectrum in natural order).
+template <int LOGN, int RLOG, int NB, int T, class L>
+__device__ __forceinline__ void inverse_first(float2 *buf, const float2 *tab_inv0, int tid)
+{
+    constexpr int N = 1 << LOGN, R = 1 << RLOG, PER = N / R;
+    float2 x[NB][R];
+    int bb[NB], tt[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        L::template split<PER>(tid + j * T, bb[j], tt[j]);
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[j][r] = buf[L::at(bb[j], tt[j] + r * PER)];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        Dft<RLOG, true>::run(x[j]);
+        float2 w[R];
+        twiddles<R>(w, tab_inv0, PER, tt[j]);
+#pragma unroll
+        for (int k = 1; k < R; ++k) x[j][k] = fmulc(x[j][k], w[k]);
+#pragma unroll
+        for (int k = 0; k < R; ++k) buf[L::at(bb[j], R * tt[j] + k)] = x[j][k];
+    }
+    __syncthreads();
+}
+
+template <int LOGN, int I, int T, class L, int P>
+struct FwdPasses {
+    static __device__ __forceinline__ void run(float2 *buf, const float2 *tabs, int tid)
+    {
+        if constexpr (I < npasses(LOGN) - 1) {
+            constexpr int RLOG = fwd_rlog(LOGN, I);
+            pass<LOGN, fwd_slog(LOGN, I), RLOG, false, P / (1 << RLOG) / T, T, L>(buf, tabs + fwd_off(LOGN, I), tid);
+            FwdPasses<LOGN, I + 1, T, L, P>::run(buf, tabs, tid);
+        }
+    }
+};
+template <int LOGN, int I, int T, class L, int P>
+struct InvPasses {
+    static __device__ __forceinline__ void run(float2 *buf, const float2 *tabs, int tid)
+    {
+        if constexpr (I < npasses(LOGN) - 1) {
+            constexpr int RLOG = inv_rlog(LOGN, I);
+            pass<LOGN, inv_slog(LOGN, I), RLOG, true, P / (1 << RLOG) / T, T, L>(buf, tabs + inv_off(LOGN, I), tid);
+            InvPasses<LOGN, I + 1, T, L, P>::run(buf, tabs, tid);
+        }
+    }
+};
+
+// Full transform pair (forward, spectral operator, inverse) up to the
+// inverse's last pass, whose loads and DFT are left to the caller.
+template <int LOGN, int T, class L, int P, class Op>
+__device__ __forceinline__ void transform_pair(float2 *buf, const float2 *tabs, const Op &op, int tid)
+{
+    FwdPasses<LOGN, 0, T, L, P>::run(buf, tabs, tid);
+    constexpr int RM = fwd_rlog(LOGN, npasses(LOGN) - 1);
+    middle<LOGN, RM, P / (1 << RM) / T, T, L>(buf, tabs + inv_off(LOGN, 0), op, tid);
+    InvPasses<LOGN, 1, T, L, P>::run(buf, tabs, tid);
+}
+
+// Forward transform alone, result in natural order in buf.
+template <int LOGN, int T, class L, int P>
+__device__ __forceinline__ void forward(float2 *buf, const float2 *tabs, int tid)
+{
+    FwdPasses<LOGN, 0, T, L, P>::run(buf, tabs, tid);
+    constexpr int I = npasses(LOGN) - 1, RM = fwd_rlog(LOGN, I);
+    pass<LOGN, fwd_slog(LOGN, I), RM, false, P / (1 << RM) / T, T, L>(buf, tabs, tid);  // M = 1: no twiddles
+}
+
+// Inverse transform of a natural-order spectrum up to its last pass (left to
+// the caller, as in transform_pair).
+template <int LOGN, int T, class L, int P>
+__device__ __forceinline__ void inverse_open(float2 *buf, const float2 *tabs, int tid)
+{
+    constexpr int RM = fwd_rlog(LOGN, npasses(LOGN) - 1);
+    inverse_first<LOGN, RM, P / (1 << RM) / T, T, L>(buf, tabs + inv_off(LOGN, 0), tid);
+    InvPasses<LOGN, 1, T, L, P>::run(buf, tabs, tid);
+}
+
+// Multiplication by a real per-bin factor table (the Fourier factor of Eq. (8)).
+struct ScaleBins {
+    const float *kf;
+    __device__ __forceinline__ float2 operator()(int, int bin, float2 v) const
+    {
+        const float f = kf[bin];
+        return f2(v.x * f, v.y * f);
+    }
+};
+
+template <int LOGN, int NB, int T, class L>
+__device__ __forceinline__ void last_inverse(const float2 *buf, float2 (&x)[NB][1 << inv_rlog(LOGN, npasses(LOGN) - 1)],
+                                             int (&bb)[NB], int (&tt)[NB], int tid)
+{
+    constexpr int RLOG = inv_rlog(LOGN, npasses(LOGN) - 1), R = 1 << RLOG, PER = (1 << LOGN) / R;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        L::template split<PER>(tid + j * T, bb[j], tt[j]);
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[j][r] = buf[L::at(bb[j], tt[j] + r * PER)];
+        Dft<RLOG, true>::run(x[j]);
+    }
+}
+
+// Fill the twiddle tables of every pass of a length-2^LOGN transform.
+template <int LOGN, int I>
+__device__ __forceinline__ void fill_tables(float2 *tabs, const float2 *tw, int tid, int nthreads)
+{
+    constexpr int NP = npasses(LOGN);
+    if constexpr (I < 2 * (NP - 1)) {
+        constexpr bool INVP = I >= NP - 1;
+        constexpr int PI = INVP ? I - (NP - 1) : I;
+        constexpr int SLOG = INVP ? inv_slog(LOGN, PI) : fwd_slog(LOGN, PI);
+        constexpr int RLOG = INVP ? inv_rlog(LOGN, PI) : fwd_rlog(LOGN, PI);
+        constexpr int OFF = INVP ? inv_off(LOGN, PI) : fwd_off(LOGN, PI);
+        constexpr int M = (1 << LOGN) >> (SLOG + RLOG), LEN = tab_rows(RLOG) * M;
+        for (int e = tid; e < LEN; e += nthreads) {
+            const int row = e / M, p = e % M;
+            const int k = RLOG == 3 ? (1 << row) : row + 1;
+            tabs[OFF + e] = tw[(p << SLOG) * k];
+        }
+        fill_tables<LOGN, I + 1>(tabs, tw, tid, nthreads);
+    }
+}
+
+} // namespace epdlb

@@ -50,6 +50,7 @@
 
 #include "common.cuh"
 #include "engine.h"
+#include "fft8.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -65,252 +66,6 @@ struct PropCK {
     const float2 *twx, *twy;  // exp(-2 pi i j / N), j < N
     const float *kx, *ky;     // exp(-R_G^2 k^2 ds) / N
 };
-
-// Radix plan: passes of radix 8, the last forward pass takes the remainder.
-__host__ __device__ constexpr int npasses(int logn) { return (logn + 2) / 3; }
-__host__ __device__ constexpr int fwd_rlog(int logn, int i) { return i < npasses(logn) - 1 ? 3 : logn - 3 * (npasses(logn) - 1); }
-__host__ __device__ constexpr int fwd_slog(int logn, int i) { return i == 0 ? 0 : fwd_slog(logn, i - 1) + fwd_rlog(logn, i - 1); }
-__host__ __device__ constexpr int inv_rlog(int logn, int i) { return fwd_rlog(logn, npasses(logn) - 1 - i); }
-__host__ __device__ constexpr int inv_slog(int logn, int i) { return i == 0 ? 0 : inv_slog(logn, i - 1) + inv_rlog(logn, i - 1); }
-// Twiddle tables: one per pass that needs twiddles (forward passes
-// 0..np-2, inverse passes 0..np-2), rows x M entries, M = N / (S R): rows
-// k = 1, 2, 4 for radix 8 (the others are products), k = 1..R-1 otherwise.
-__host__ __device__ constexpr int tab_rows(int rlog) { return rlog == 3 ? 3 : (1 << rlog) - 1; }
-__host__ __device__ constexpr int tab_len(int logn, int slog, int rlog) { return tab_rows(rlog) * ((1 << logn) >> (slog + rlog)); }
-__host__ __device__ constexpr int fwd_off(int logn, int i) { return i == 0 ? 0 : fwd_off(logn, i - 1) + tab_len(logn, fwd_slog(logn, i - 1), fwd_rlog(logn, i - 1)); }
-__host__ __device__ constexpr int inv_off(int logn, int i)
-{
-    return i == 0 ? fwd_off(logn, npasses(logn) - 1) : inv_off(logn, i - 1) + tab_len(logn, inv_slog(logn, i - 1), inv_rlog(logn, i - 1));
-}
-__host__ __device__ constexpr int tabs_total(int logn) { return inv_off(logn, npasses(logn) - 1); }
-
-__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
-__device__ __forceinline__ float2 fadd(float2 a, float2 b) { return f2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 fsub(float2 a, float2 b) { return f2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 fmul(float2 a, float2 b) { return f2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
-__device__ __forceinline__ float2 fmulc(float2 a, float2 b) { return f2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y); }  // a * conj(b)
-template <bool INV> __device__ __forceinline__ float2 rot90(float2 a) { return INV ? f2(-a.y, a.x) : f2(a.y, -a.x); }
-
-// In-register DFT of length 2^RLOG, natural order in and out; forward uses
-// exp(-2 pi i / R), inverse exp(+2 pi i / R).
-template <int RLOG, bool INV> struct Dft;
-template <bool INV> struct Dft<1, INV> {
-    static __device__ __forceinline__ void run(float2 *x)
-    {
-        const float2 a = x[0], b = x[1];
-        x[0] = fadd(a, b);
-        x[1] = fsub(a, b);
-    }
-};
-template <bool INV> struct Dft<2, INV> {
-    static __device__ __forceinline__ void run(float2 *x)
-    {
-        const float2 s02 = fadd(x[0], x[2]), d02 = fsub(x[0], x[2]);
-        const float2 s13 = fadd(x[1], x[3]), d13 = rot90<INV>(fsub(x[1], x[3]));
-        x[0] = fadd(s02, s13);
-        x[2] = fsub(s02, s13);
-        x[1] = fadd(d02, d13);
-        x[3] = fsub(d02, d13);
-    }
-};
-template <bool INV> struct Dft<3, INV> {
-    static __device__ __forceinline__ void run(float2 *x)
-    {
-        float2 e[4] = {x[0], x[2], x[4], x[6]};
-        float2 o[4] = {x[1], x[3], x[5], x[7]};
-        Dft<2, INV>::run(e);
-        Dft<2, INV>::run(o);
-        const float h = 0.70710678118654752440f;
-        const float2 o1 = INV ? f2(h * (o[1].x - o[1].y), h * (o[1].x + o[1].y)) : f2(h * (o[1].x + o[1].y), h * (o[1].y - o[1].x));
-        const float2 o2 = rot90<INV>(o[2]);
-        const float2 o3 = INV ? f2(-h * (o[3].x + o[3].y), h * (o[3].x - o[3].y)) : f2(h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y));
-        x[0] = fadd(e[0], o[0]);
-        x[4] = fsub(e[0], o[0]);
-        x[1] = fadd(e[1], o1);
-        x[5] = fsub(e[1], o1);
-        x[2] = fadd(e[2], o2);
-        x[6] = fsub(e[2], o2);
-        x[3] = fadd(e[3], o3);
-        x[7] = fsub(e[3], o3);
-    }
-};
-
-// Shared-memory layouts.  Row layout: sequence b (a packed row), point x.
-// Rows of 128 points or more are unpadded with the low four bits of x
-// XOR-ed by the next four (x ^ ((x >> 4) & 15)): every access pattern of the
-// radix-8 passes then hits each 8-byte bank pair at most twice per warp
-// (almost all once) and 16-point groups stay aligned and contiguous;
-// 64-point rows are padded by one slot per 8 points.  Column layout: point y
-// of sequence c (a packed column) at y * W + c.
-template <int LOGN> struct RowLayout {
-    static constexpr int N = 1 << LOGN, PITCH = LOGN >= 7 ? N : N + N / 8;
-    static __device__ __forceinline__ int at(int b, int x)
-    {
-        if constexpr (LOGN >= 7)
-            return b * PITCH + (x ^ ((x >> 4) & 15));
-        else
-            return b * PITCH + x + (x >> 3);
-    }
-    template <int PER> static __device__ __forceinline__ void split(int bf, int &b, int &t) { b = bf / PER; t = bf % PER; }
-};
-template <int LOGN, int W> struct ColLayout {
-    static __device__ __forceinline__ int at(int c, int y) { return y * W + c; }
-    template <int PER> static __device__ __forceinline__ void split(int bf, int &b, int &t) { b = bf % W; t = bf / W; }
-};
-
-// Twiddles w[k] = w1^k, k = 1..R-1, of one butterfly from a pass table laid
-// out [row][p] (row length M): radix 8 reads w1, w2, w4 and forms the rest by
-// products (at most two roundings more than a table entry).
-template <int R>
-__device__ __forceinline__ void twiddles(float2 (&w)[R], const float2 *tab, int M, int p)
-{
-    if constexpr (R == 8) {
-        w[1] = tab[p];
-        w[2] = tab[M + p];
-        w[4] = tab[2 * M + p];
-        w[3] = fmul(w[1], w[2]);
-        w[5] = fmul(w[1], w[4]);
-        w[6] = fmul(w[2], w[4]);
-        w[7] = fmul(w[3], w[4]);
-    } else {
-#pragma unroll
-        for (int k = 1; k < R; ++k) w[k] = tab[(k - 1) * M + p];
-    }
-}
-
-// One in-place Stockham pass (radix 2^RLOG, stride 2^SLOG): load, wait, write.
-// tab: this pass's twiddles [k-1][p] (unused in a forward last pass).
-template <int LOGN, int SLOG, int RLOG, bool INV, int NB, int T, class L>
-__device__ __forceinline__ void pass(float2 *buf, const float2 *tab, int tid)
-{
-    constexpr int N = 1 << LOGN, R = 1 << RLOG, S = 1 << SLOG, PER = N / R, M = N / (S * R);
-    float2 x[NB][R];
-    int bb[NB], tt[NB];
-#pragma unroll
-    for (int j = 0; j < NB; ++j) {
-        L::template split<PER>(tid + j * T, bb[j], tt[j]);
-#pragma unroll
-        for (int r = 0; r < R; ++r) x[j][r] = buf[L::at(bb[j], tt[j] + r * PER)];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < NB; ++j) {
-        Dft<RLOG, INV>::run(x[j]);
-        const int q = tt[j] & (S - 1), p = tt[j] >> SLOG;
-        if (M > 1) {
-            float2 w[R];
-            twiddles<R>(w, tab, M, p);
-#pragma unroll
-            for (int k = 1; k < R; ++k) x[j][k] = INV ? fmulc(x[j][k], w[k]) : fmul(x[j][k], w[k]);
-        }
-#pragma unroll
-        for (int k = 0; k < R; ++k) buf[L::at(bb[j], q + R * S * p + S * k)] = x[j][k];
-    }
-    __syncthreads();
-}
-
-// Forward last pass, Fourier factor, inverse first pass (same points per thread).
-template <int LOGN, int RLOG, int NB, int T, class L>
-__device__ __forceinline__ void middle(float2 *buf, const float2 *tab_inv0, const float *kf, int tid)
-{
-    constexpr int N = 1 << LOGN, R = 1 << RLOG, PER = N / R;
-    float2 x[NB][R];
-    int bb[NB], tt[NB];
-#pragma unroll
-    for (int j = 0; j < NB; ++j) {
-        L::template split<PER>(tid + j * T, bb[j], tt[j]);
-#pragma unroll
-        for (int r = 0; r < R; ++r) x[j][r] = buf[L::at(bb[j], tt[j] + r * PER)];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < NB; ++j) {
-        Dft<RLOG, false>::run(x[j]);
-#pragma unroll
-        for (int k = 0; k < R; ++k) {
-            const float f = kf[tt[j] + k * PER];
-            x[j][k].x *= f;
-            x[j][k].y *= f;
-        }
-        Dft<RLOG, true>::run(x[j]);
-        float2 w[R];
-        twiddles<R>(w, tab_inv0, PER, tt[j]);
-#pragma unroll
-        for (int k = 1; k < R; ++k) x[j][k] = fmulc(x[j][k], w[k]);
-#pragma unroll
-        for (int k = 0; k < R; ++k) buf[L::at(bb[j], R * tt[j] + k)] = x[j][k];
-    }
-    __syncthreads();
-}
-
-template <int LOGN, int I, int T, class L, int P>
-struct FwdPasses {
-    static __device__ __forceinline__ void run(float2 *buf, const float2 *tabs, int tid)
-    {
-        if constexpr (I < npasses(LOGN) - 1) {
-            constexpr int RLOG = fwd_rlog(LOGN, I);
-            pass<LOGN, fwd_slog(LOGN, I), RLOG, false, P / (1 << RLOG) / T, T, L>(buf, tabs + fwd_off(LOGN, I), tid);
-            FwdPasses<LOGN, I + 1, T, L, P>::run(buf, tabs, tid);
-        }
-    }
-};
-template <int LOGN, int I, int T, class L, int P>
-struct InvPasses {
-    static __device__ __forceinline__ void run(float2 *buf, const float2 *tabs, int tid)
-    {
-        if constexpr (I < npasses(LOGN) - 1) {
-            constexpr int RLOG = inv_rlog(LOGN, I);
-            pass<LOGN, inv_slog(LOGN, I), RLOG, true, P / (1 << RLOG) / T, T, L>(buf, tabs + inv_off(LOGN, I), tid);
-            InvPasses<LOGN, I + 1, T, L, P>::run(buf, tabs, tid);
-        }
-    }
-};
-
-// Full transform pair (forward, Fourier factor, inverse) up to the inverse's
-// last pass, whose loads and DFT are left to the caller.
-template <int LOGN, int T, class L, int P>
-__device__ __forceinline__ void transform_pair(float2 *buf, const float2 *tabs, const float *kf, int tid)
-{
-    FwdPasses<LOGN, 0, T, L, P>::run(buf, tabs, tid);
-    constexpr int RM = fwd_rlog(LOGN, npasses(LOGN) - 1);
-    middle<LOGN, RM, P / (1 << RM) / T, T, L>(buf, tabs + inv_off(LOGN, 0), kf, tid);
-    InvPasses<LOGN, 1, T, L, P>::run(buf, tabs, tid);
-}
-
-template <int LOGN, int NB, int T, class L>
-__device__ __forceinline__ void last_inverse(const float2 *buf, float2 (&x)[NB][1 << inv_rlog(LOGN, npasses(LOGN) - 1)],
-                                             int (&bb)[NB], int (&tt)[NB], int tid)
-{
-    constexpr int RLOG = inv_rlog(LOGN, npasses(LOGN) - 1), R = 1 << RLOG, PER = (1 << LOGN) / R;
-#pragma unroll
-    for (int j = 0; j < NB; ++j) {
-        L::template split<PER>(tid + j * T, bb[j], tt[j]);
-#pragma unroll
-        for (int r = 0; r < R; ++r) x[j][r] = buf[L::at(bb[j], tt[j] + r * PER)];
-        Dft<RLOG, true>::run(x[j]);
-    }
-}
-
-// Fill the twiddle tables of every pass of a length-2^LOGN transform.
-template <int LOGN, int I>
-__device__ __forceinline__ void fill_tables(float2 *tabs, const float2 *tw, int tid, int nthreads)
-{
-    constexpr int NP = npasses(LOGN);
-    if constexpr (I < 2 * (NP - 1)) {
-        constexpr bool INVP = I >= NP - 1;
-        constexpr int PI = INVP ? I - (NP - 1) : I;
-        constexpr int SLOG = INVP ? inv_slog(LOGN, PI) : fwd_slog(LOGN, PI);
-        constexpr int RLOG = INVP ? inv_rlog(LOGN, PI) : fwd_rlog(LOGN, PI);
-        constexpr int OFF = INVP ? inv_off(LOGN, PI) : fwd_off(LOGN, PI);
-        constexpr int M = (1 << LOGN) >> (SLOG + RLOG), LEN = tab_rows(RLOG) * M;
-        for (int e = tid; e < LEN; e += nthreads) {
-            const int row = e / M, p = e % M;
-            const int k = RLOG == 3 ? (1 << row) : row + 1;
-            tabs[OFF + e] = tw[(p << SLOG) * k];
-        }
-        fill_tables<LOGN, I + 1>(tabs, tw, tid, nthreads);
-    }
-}
 
 template <int LOGX, int LOGY, int C, int T>
 struct ClusterGeom {
@@ -489,7 +244,7 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
                     asm volatile("prefetch.global.L1 [%0];" ::"l"(href + (size_t)m * HN + b * NX + t + r * PER_L));
             }
         }
-        transform_pair<LOGY, T, CL, P>(colbuf, taby, ky, tid);
+        transform_pair<LOGY, T, CL, P>(colbuf, taby, ScaleBins{ky}, tid);
         {
             constexpr int RLOG_C = inv_rlog(LOGY, npasses(LOGY) - 1), NB_C = P / (1 << RLOG_C) / T;
             float2 x[NB_C][1 << RLOG_C];
@@ -517,7 +272,7 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
         cluster_arrive();  // my column buffer is read out
         mbar_wait(bar_row, par, failed);
         if (tid == 0 && m < ns) mbar_expect(bar_row, XBYTES);
-        transform_pair<LOGX, T, RL, P>(rowbuf, tabx, kx, tid);
+        transform_pair<LOGX, T, RL, P>(rowbuf, tabx, ScaleBins{kx}, tid);
         float2 h[NB_L][RR];
         int bb[NB_L], tt[NB_L];
         last_inverse<LOGX, NB_L, T, RL>(rowbuf, h, bb, tt, tid);
@@ -690,33 +445,57 @@ __global__ void __launch_bounds__(kThreads) prop_contour(ContourK k)
     double ia0 = 0.0, ib0 = 0.0, ia1 = 0.0, ib1 = 0.0;
     float pa0 = 0.f, pa1 = 0.f, gwa = 0.f, gwb = 0.f;
     int cnt = 0;
-    for (int m = 0; m <= ns; ++m) {
-        float wa, wb;
-        node_weights(m, na, ns, wa, wb);
-        if (cnt > 0 && (wa != gwa || wb != gwb || cnt == 8)) {
-            ia0 += (double)gwa * pa0;
-            ib0 += (double)gwb * pa0;
-            ia1 += (double)gwa * pa1;
-            ib1 += (double)gwb * pa1;
-            pa0 = pa1 = 0.f;
-            cnt = 0;
+    // nodes in chunks of U: all loads of a chunk are issued before its sums
+    constexpr int U = DIFF ? 4 : 8;
+    for (int m0 = 0; m0 <= ns; m0 += U) {
+        float2 av[U], bv[U], dav[U], dbv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int m = m0 + u;
+            if (m <= ns) {
+                av[u] = c0[(size_t)m * k.hn];
+                bv[u] = c1[(size_t)(ns - m) * k.hn];
+                if (DIFF) {
+                    dav[u] = d0[(size_t)m * k.hn];
+                    dbv[u] = d1[(size_t)(ns - m) * k.hn];
+                }
+            }
         }
-        gwa = wa;
-        gwb = wb;
-        ++cnt;
-        const int bk = m >= na ? 1 : 0;  // g at node m and g' at node N_s - m see the same field
-        const float2 a = c0[(size_t)m * k.hn], b = c1[(size_t)(ns - m) * k.hn];
-        if (!DIFF) {
-            pa0 += a.x * b.x * r2[bk][0];
-            pa1 += a.y * b.y * r2[bk][1];
-        } else {
-            const float2 da = d0[(size_t)m * k.hn], db = d1[(size_t)(ns - m) * k.hn];
-            // g~ = a~ / E and dg = (d a - rho a~) / E' of both chains
-            const float ga0 = a.x * ri[bk][0], ga1 = a.y * ri[bk][1], gb0 = b.x * ri[bk][0], gb1 = b.y * ri[bk][1];
-            const float dga0 = (da.x - dd[bk][0] * a.x) * rs[bk][0], dga1 = (da.y - dd[bk][1] * a.y) * rs[bk][1];
-            const float dgb0 = (db.x - dd[bk][0] * b.x) * rs[bk][0], dgb1 = (db.y - dd[bk][1] * b.y) * rs[bk][1];
-            pa0 += ga0 * dgb0 + dga0 * gb0 + dga0 * dgb0;
-            pa1 += ga1 * dgb1 + dga1 * gb1 + dga1 * dgb1;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int m = m0 + u;
+            if (m > ns) break;
+            float wa, wb;
+            node_weights(m, na, ns, wa, wb);
+            if (cnt > 0 && (wa != gwa || wb != gwb || cnt == 8)) {
+                ia0 += (double)gwa * pa0;
+                ib0 += (double)gwb * pa0;
+                ia1 += (double)gwa * pa1;
+                ib1 += (double)gwb * pa1;
+                pa0 = pa1 = 0.f;
+                cnt = 0;
+            }
+            gwa = wa;
+            gwb = wb;
+            ++cnt;
+            // g at node m and g' at node N_s - m see the same field (block B from N_A on)
+            const bool bk = m >= na;
+            const float2 a = av[u], b = bv[u];
+            if (!DIFF) {
+                pa0 += a.x * b.x * (bk ? r2[1][0] : r2[0][0]);
+                pa1 += a.y * b.y * (bk ? r2[1][1] : r2[0][1]);
+            } else {
+                const float2 da = dav[u], db = dbv[u];
+                const float ri0 = bk ? ri[1][0] : ri[0][0], ri1 = bk ? ri[1][1] : ri[0][1];
+                const float q0 = bk ? dd[1][0] : dd[0][0], q1 = bk ? dd[1][1] : dd[0][1];
+                const float rs0 = bk ? rs[1][0] : rs[0][0], rs1 = bk ? rs[1][1] : rs[0][1];
+                // g~ = a~ / E and dg = (d a - rho a~) / E' of both chains
+                const float ga0 = a.x * ri0, ga1 = a.y * ri1, gb0 = b.x * ri0, gb1 = b.y * ri1;
+                const float dga0 = (da.x - q0 * a.x) * rs0, dga1 = (da.y - q1 * a.y) * rs1;
+                const float dgb0 = (db.x - q0 * b.x) * rs0, dgb1 = (db.y - q1 * b.y) * rs1;
+                pa0 += ga0 * dgb0 + dga0 * gb0 + dga0 * dgb0;
+                pa1 += ga1 * dgb1 + dga1 * gb1 + dga1 * dgb1;
+            }
         }
     }
     ia0 += (double)gwa * pa0;
