@@ -55,7 +55,12 @@ enum {
     EPD_LB_PLAIN_FP64 = 0,   /* every field and transform in FP64            */
     EPD_LB_MIXED_FP32 = 1    /* propagators, LB populations and the EPD/force
                                 transforms in FP32; fields omega and Phi,
-                                contour sums, Q and masses in FP64           */
+                                contour sums, Q and masses in FP64.  On grids
+                                of 2^12..2^17 sites with 64..512 points per
+                                axis the step's second solve is computed as
+                                its difference from the first (same result
+                                up to rounding, FP32 relative to the
+                                change)                                      */
 };
 
 /*
@@ -172,7 +177,8 @@ int epd_lb_load(epd_lb *h, const void *buf, size_t len);
  * (ms[4] = 0): ms[0] the row pass of contour node N_s/4 (history store),
  * ms[1] the row pass of node 3 N_s/4 + 1 (contour accumulation), ms[2] the
  * column pass before it.  With the cluster-resident solve (ms[4] = 1): ms[0]
- * its single launch (the whole contour), ms[1] = ms[2] = 0. */
+ * its chain launch (the whole contour of both chains; the differential
+ * solve where the step uses one), ms[1] = ms[2] = 0. */
 int epd_lb_enable_timing(epd_lb *h, int32_t on);
 int epd_lb_kernel_times(epd_lb *h, double *ms);
 
