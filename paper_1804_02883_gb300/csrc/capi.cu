@@ -59,7 +59,8 @@ size_t carve_group(Group &G, char *base, size_t off)
     G.f0_bulk = take(R * tb);
     G.stage = (double *)take(std::max<size_t>(9 * n, 2 * R + 16) * sizeof(double));
     G.chain = take(R * n * 2 * tb);
-    G.hist = take(R * (size_t)(G.g.half_lo + 1) * n * 2 * tb);
+    G.hist_full = stream8_eligible(G.prec, G.g.logx, G.g.logy);
+    G.hist = take(R * (size_t)(G.hist_full ? G.g.ns + 1 : G.g.half_lo + 1) * n * 2 * tb);
     G.efac = take(R * n * 2 * tb);
     G.pop[0] = take(R * 9 * n * tb);
     G.pop[1] = take(R * 9 * n * tb);
@@ -108,7 +109,7 @@ static Group run_view(const Group &G, int r)
     V.f0_lat += r;
     V.f0_bulk = (char *)V.f0_bulk + (size_t)r * tb;
     V.chain = (char *)V.chain + (size_t)r * n * 2 * tb;
-    V.hist = (char *)V.hist + (size_t)r * (G.g.half_lo + 1) * n * 2 * tb;
+    V.hist = (char *)V.hist + (size_t)r * (G.hist_full ? G.g.ns + 1 : G.g.half_lo + 1) * n * 2 * tb;
     V.efac = (char *)V.efac + (size_t)r * n * 2 * tb;
     V.pop[0] = (char *)V.pop[0] + (size_t)r * 9 * n * tb;
     V.pop[1] = (char *)V.pop[1] + (size_t)r * 9 * n * tb;

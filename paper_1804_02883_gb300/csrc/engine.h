@@ -54,6 +54,7 @@ struct Group {
     void *hd = nullptr;       // differential second solve
     void *rho = nullptr;      // (rho_A, rho_B) = expm1(-N d omega ds / 2), [run][n] float2
     bool diff = false;        // the step uses the reference + differential solve pair
+    bool hist_full = false;   // streaming radix-8 solve: hist holds all N_s + 1 nodes
     double2 *cz;       // 4 complex FP64 scratch planes per run: [run][4][n]
     double *part;      // reduction partials, [run][kMaxPart]
     double *f0_lat;    // [run]
@@ -120,6 +121,8 @@ cudaError_t launch_pop_raw(Group &G, int run, int parity, double *dst, const dou
 // shape and precision, its launch, and its CTAs per run.
 bool cluster_solve_supported(const Group &G);
 bool cluster_shape_exists(int logx, int logy);
+// MIXED grids solved by the radix-8 streaming passes with the full history
+bool stream8_eligible(int prec, int logx, int logy);
 size_t cluster_state_floats2(int nx, int ny, int ns);  // per run, both chains
 // Chain launch plus contour sums and normalisation into phi, q (diff: the
 // differential solve into G.phi, G.q).  nprep_blocks: solvent partials.

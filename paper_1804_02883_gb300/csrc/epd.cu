@@ -233,20 +233,8 @@ __global__ void __launch_bounds__(kThreads) epd_col(EpdK k)
 // ---------------------------------------------------------------------------
 // FP32 radix-8 versions of the row and column passes (MIXED_FP32, grids with
 // 64..2048 points per axis): the same operators and data flow as epd_row /
-// epd_col above, transforms from fft8.cuh.  A row tile holds 2048 points
-// (max(1, 2048 / nx) rows), a column tile 16 columns (8 from 1024 rows on).
+// epd_col above, transforms and tiles (RowTile, ColTile) from fft8.cuh.
 // ---------------------------------------------------------------------------
-
-template <int LOGX> struct RowTile {
-    static constexpr int NX = 1 << LOGX, ROWS = NX >= 2048 ? 1 : 2048 / NX, P = ROWS * NX, T = P / 8;
-    static constexpr int TAB = tabs_total(LOGX);
-    static constexpr size_t SMEM = (size_t)(ROWS * RowLayout<LOGX>::PITCH + TAB) * sizeof(float2);
-};
-template <int LOGY> struct ColTile {
-    static constexpr int NY = 1 << LOGY, C = LOGY >= 10 ? 8 : 16, P = C * NY, T = P / 8 > 512 ? 512 : P / 8;
-    static constexpr int TAB = tabs_total(LOGY);
-    static constexpr size_t SMEM = (size_t)(P + TAB) * sizeof(float2);
-};
 
 // i k / n (first derivative, Nyquist bin dropped) and -k^2 / n along one axis
 struct OpGrad {

@@ -20,6 +20,7 @@
 
 #include "common.cuh"
 #include "engine.h"
+#include "fft8.cuh"
 
 namespace epdlb {
 
@@ -238,6 +239,227 @@ __global__ void __launch_bounds__(kThreads) prop_prep_delta(GroupGeom g, const d
     if (threadIdx.x == 0) part[(size_t)run * kMaxPart + kMaxPart / 2 + blockIdx.x] = s;
 }
 
+// ---------------------------------------------------------------------------
+// Streaming passes on radix-8 tiles (MIXED_FP32, grids too large for the
+// cluster-resident solve, 64..2048 points per axis).  The chain z = g + i g'
+// is transformed by column tiles then row tiles per contour step, as above;
+// the row pass stores z at every node (full history, FP32), and the contour
+// sums are one pass over the history afterwards (prop_contour_stream):
+// I(r) = sum_j w_j g(s_j) g'(1 - s_j) with g'(1 - s_j) the g' chain at its
+// node N_s - j.
+// ---------------------------------------------------------------------------
+
+struct Stream8K {
+    GroupGeom g;
+    float2 *chain;        // [run][n]
+    float2 *hist;         // [run][N_s + 1][n]
+    const float2 *efac;   // [run][n]
+    double *part;
+    const float2 *twx, *twy;  // full tables exp(-2 pi i j / N)
+    const float *kx, *ky;
+};
+
+// node 0: g = g' = 1; chain <- E(s_0) z_0
+__global__ void __launch_bounds__(kThreads) prop_start8(Stream8K k)
+{
+    const int run = blockIdx.y;
+    const long long n = k.g.n;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float2 e = k.efac[(size_t)run * n + i];
+        k.hist[(size_t)run * (k.g.ns + 1) * n + i] = make_float2(1.f, 1.f);
+        k.chain[(size_t)run * n + i] = make_float2(fac_g<float>(e, 0, k.g.na), fac_gp<float>(e, 0, k.g.ns, k.g.na));
+    }
+}
+
+template <int LOGY>
+__global__ void __launch_bounds__(ColTile<LOGY>::T) prop_col8(Stream8K k)
+{
+    using CT = ColTile<LOGY>;
+    using CL = ColLayout<LOGY, CT::C>;
+    constexpr int NY = CT::NY, C = CT::C, P = CT::P, T = CT::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *buf = reinterpret_cast<float2 *>(smem_raw);
+    float2 *tab = buf + P;
+    float *ky = reinterpret_cast<float *>(tab + CT::TAB);
+    const int nx = k.g.nx, run = blockIdx.y, x0 = blockIdx.x * C, tid = threadIdx.x;
+    float2 *data = k.chain + (size_t)run * k.g.n;
+    fill_tables<LOGY, 0>(tab, k.twy, tid, T);
+    for (int i = tid; i < NY; i += T) ky[i] = k.ky[i];
+    for (int i = tid; i < P; i += T) buf[i] = data[(size_t)(i / C) * nx + x0 + (i % C)];
+    __syncthreads();
+    transform_pair<LOGY, T, CL, P>(buf, tab, ScaleBins{ky}, tid);
+    constexpr int RLOG_L = inv_rlog(LOGY, npasses(LOGY) - 1), RR = 1 << RLOG_L, PER_L = NY / RR, NB_L = P / RR / T;
+    float2 h[NB_L][RR];
+    int bb[NB_L], tt[NB_L];
+    last_inverse<LOGY, NB_L, T, CL>(buf, h, bb, tt, tid);
+#pragma unroll
+    for (int j = 0; j < NB_L; ++j)
+#pragma unroll
+        for (int r = 0; r < RR; ++r) data[(size_t)(tt[j] + r * PER_L) * nx + x0 + bb[j]] = h[j][r];
+}
+
+// Row pass of contour node m: Tx, node factors, history store, next half
+// step; at m = N_s block sums of g for Q_P.
+template <int LOGX>
+__global__ void __launch_bounds__(RowTile<LOGX>::T) prop_row8(Stream8K k, int m)
+{
+    using RT = RowTile<LOGX>;
+    using RL = RowLayout<LOGX>;
+    constexpr int NX = RT::NX, P = RT::P, T = RT::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[32];
+    float2 *buf = reinterpret_cast<float2 *>(smem_raw);
+    float2 *tab = buf + RT::ROWS * RL::PITCH;
+    float *kx = reinterpret_cast<float *>(tab + RT::TAB);
+    const int run = blockIdx.y, tid = threadIdx.x;
+    const long long n = k.g.n, base = (long long)blockIdx.x * P;
+    const int ns = k.g.ns, na = k.g.na;
+    float2 *data = k.chain + (size_t)run * n + base;
+    fill_tables<LOGX, 0>(tab, k.twx, tid, T);
+    for (int i = tid; i < NX; i += T) kx[i] = k.kx[i];
+    for (int i = tid; i < P; i += T) buf[RL::at(i / NX, i % NX)] = data[i];
+    __syncthreads();
+    transform_pair<LOGX, T, RL, P>(buf, tab, ScaleBins{kx}, tid);
+    constexpr int RLOG_L = inv_rlog(LOGX, npasses(LOGX) - 1), RR = 1 << RLOG_L, PER_L = NX / RR, NB_L = P / RR / T;
+    float2 h[NB_L][RR];
+    int bb[NB_L], tt[NB_L];
+    last_inverse<LOGX, NB_L, T, RL>(buf, h, bb, tt, tid);
+    const float2 *efac = k.efac + (size_t)run * n + base;
+    float2 *hist = k.hist + ((size_t)run * (ns + 1) + m) * n + base;
+    float qsum = 0.f;
+#pragma unroll
+    for (int j = 0; j < NB_L; ++j)
+#pragma unroll
+        for (int r = 0; r < RR; ++r) {
+            const int i = bb[j] * NX + tt[j] + r * PER_L;
+            const float2 e = efac[i];
+            const float eg = fac_g<float>(e, m, na), egp = fac_gp<float>(e, m, ns, na);
+            const float2 z = make_float2(eg * h[j][r].x, egp * h[j][r].y);
+            hist[i] = z;
+            if (m == ns) qsum += z.x;
+            else data[i] = make_float2(eg * z.x, egp * z.y);
+        }
+    if (m == ns) {
+        const double s = block_sum((double)qsum, red);
+        if (tid == 0) k.part[(size_t)run * kMaxPart + blockIdx.x] = s;
+    }
+}
+
+// Contour sums and normalisation over the full history (Eqs. (9)-(11)):
+// FP32 products, partial sums over up to 8 nodes of equal trapezoid weight,
+// FP64 totals; the solvent slot of phi holds exp(-omega_S) from prop_prep.
+__global__ void __launch_bounds__(kThreads) prop_contour_stream(GroupGeom g, const float2 *hist, int nrow_blocks,
+                                                                int nprep_blocks, const double *part, double *phi,
+                                                                double *q, int *err)
+{
+    __shared__ double bc;
+    const int run = blockIdx.y, ns = g.ns, na = g.na;
+    const long long n = g.n;
+    const double *pr = part + (size_t)run * kMaxPart;
+    const double qp = sum_partials(pr, nrow_blocks, 1, &bc) / (double)n;
+    const double qs = sum_partials(pr + kMaxPart / 2, nprep_blocks, 1, &bc) / (double)n;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        q[2 * run] = qp;
+        q[2 * run + 1] = qs;
+        if (!(qp > 0.0) || !(qs > 0.0) || !isfinite(qp) || !isfinite(qs)) atomicOr(err, 1);
+    }
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float2 *hz = hist + (size_t)run * (ns + 1) * n + i;
+    double ia = 0.0, ib = 0.0;
+    float pa = 0.f, gwa = 0.f, gwb = 0.f;
+    int cnt = 0;
+    constexpr int U = 8;
+    for (int m0 = 0; m0 <= ns; m0 += U) {
+        float gv[U], gpv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int m = m0 + u;
+            if (m <= ns) {
+                gv[u] = hz[(size_t)m * n].x;          // g(s_m)
+                gpv[u] = hz[(size_t)(ns - m) * n].y;  // g'(1 - s_m)
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int m = m0 + u;
+            if (m > ns) break;
+            const float wa = (na == 0 || m > na) ? 0.f : ((m == 0 || m == na) ? 0.5f : 1.f);
+            const float wb = (na == ns || m < na) ? 0.f : ((m == na || m == ns) ? 0.5f : 1.f);
+            if (cnt > 0 && (wa != gwa || wb != gwb || cnt == 8)) {
+                ia += (double)gwa * pa;
+                ib += (double)gwb * pa;
+                pa = 0.f;
+                cnt = 0;
+            }
+            gwa = wa;
+            gwb = wb;
+            ++cnt;
+            pa += gv[u] * gpv[u];
+        }
+    }
+    ia += (double)gwa * pa;
+    ib += (double)gwb * pa;
+    const double c = g.phi_p * g.ds / qp;
+    double *ph = phi + (size_t)run * 3 * n;
+    ph[i] = c * ia;
+    ph[n + i] = c * ib;
+    ph[2 * n + i] *= (1.0 - g.phi_p) / qs;
+}
+
+// The contour loop of the radix-8 streaming solve for (LX, LY).
+template <int LX, int LY>
+static void stream8_run(Stream8K &k, const Group &G, cudaStream_t s, const SolveProbe *probe)
+{
+    using RT = RowTile<LX>;
+    using CT = ColTile<LY>;
+    const size_t sr = RT::SMEM + RT::NX * sizeof(float), sc = CT::SMEM + CT::NY * sizeof(float);
+    static bool conf = false;
+    if (!conf) {
+        cudaFuncSetAttribute(prop_row8<LX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
+        cudaFuncSetAttribute(prop_col8<LY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
+        conf = true;
+    }
+    const dim3 gr((unsigned)(G.g.n / RT::P), G.g.nruns), gc(G.g.nx / CT::C, G.g.nruns);
+    for (int m = 1; m <= G.g.ns; ++m) {
+        const bool pa = probe && m == probe->m_acc, ps = probe && m == probe->m_store;
+        if (pa) cudaEventRecordWithFlags(probe->ev[2], s, cudaEventRecordExternal);
+        prop_col8<LY><<<gc, CT::T, sc, s>>>(k);
+        if (pa) cudaEventRecordWithFlags(probe->ev[3], s, cudaEventRecordExternal);
+        if (ps) cudaEventRecordWithFlags(probe->ev[0], s, cudaEventRecordExternal);
+        prop_row8<LX><<<gr, RT::T, sr, s>>>(k, m);
+        if (ps) cudaEventRecordWithFlags(probe->ev[1], s, cudaEventRecordExternal);
+        if (pa) cudaEventRecordWithFlags(probe->ev[4], s, cudaEventRecordExternal);
+    }
+}
+template <int LX, int LY>
+static bool stream8_dispatch_y(int logy, Stream8K &k, const Group &G, cudaStream_t s, const SolveProbe *probe)
+{
+    if constexpr (LY > 11) {
+        return false;
+    } else {
+        if (logy != LY) return stream8_dispatch_y<LX, LY + 1>(logy, k, G, s, probe);
+        stream8_run<LX, LY>(k, G, s, probe);
+        return true;
+    }
+}
+template <int LX>
+static bool stream8_dispatch(int logx, int logy, Stream8K &k, const Group &G, cudaStream_t s, const SolveProbe *probe)
+{
+    if constexpr (LX > 11) {
+        return false;
+    } else {
+        if (logx != LX) return stream8_dispatch<LX + 1>(logx, logy, k, G, s, probe);
+        return stream8_dispatch_y<LX, 6>(logy, k, G, s, probe);
+    }
+}
+
+bool stream8_eligible(int prec, int logx, int logy)
+{
+    return prec == EPD_LB_MIXED_FP32 && !cluster_shape_exists(logx, logy) && logx >= 6 && logy >= 6 && logx <= 11 &&
+           logy <= 11 && logx + logy >= 11;
+}
+
 static int grid_for(long long n)
 {
     long long b = (n + kThreads - 1) / kThreads;
@@ -274,6 +496,25 @@ static cudaError_t solve_t(Group &G, const double *omega, double *phi, double *q
     if (sizeof(T) == sizeof(float) && G.hc && G.twx_full && cluster_solve_supported(G)) {
         // whole contour in one cluster-resident launch, then the contour sums
         return launch_cluster_solve(G, s, false, pg, phi, q, probe);
+    }
+    if (sizeof(T) == sizeof(float) && G.hist_full && G.twx_full) {
+        // radix-8 streaming passes with the full history, then the contour pass
+        Stream8K k8;
+        k8.g = g;
+        k8.chain = reinterpret_cast<float2 *>(G.chain);
+        k8.hist = reinterpret_cast<float2 *>(G.hist);
+        k8.efac = reinterpret_cast<const float2 *>(G.efac);
+        k8.part = G.part;
+        k8.twx = reinterpret_cast<const float2 *>(G.twx_full);
+        k8.twy = reinterpret_cast<const float2 *>(G.twy_full);
+        k8.kx = reinterpret_cast<const float *>(G.kx);
+        k8.ky = reinterpret_cast<const float *>(G.ky);
+        prop_start8<<<dim3(pg, g.nruns), kThreads, 0, s>>>(k8);
+        if (!stream8_dispatch<6>(g.logx, g.logy, k8, G, s, probe)) return cudaErrorInvalidConfiguration;
+        const int nrow = (int)(g.n / (g.nx >= 2048 ? g.nx : 2048));
+        prop_contour_stream<<<dim3((unsigned)((g.n + kThreads - 1) / kThreads), g.nruns), kThreads, 0, s>>>(
+            g, k8.hist, nrow, pg, G.part, phi, q, G.err);
+        return cudaGetLastError();
     }
     prop_start<T><<<dim3(pg, g.nruns), kThreads, 0, s>>>(k);
     const dim3 gc(g.nx / G.sh.cols_prop, g.nruns), gr(g.ny / G.sh.rows_prop, g.nruns);

@@ -18,11 +18,13 @@ def _build(oracle_lib):
     P.lib()
 
 
-# includes every grid of the cluster-resident solve (MIXED_FP32) and grids
-# that take the streaming passes
+# includes every grid of the cluster-resident solve (MIXED_FP32), grids of
+# the radix-8 streaming passes (MIXED_FP32, 64..2048 points per axis, no
+# cluster shape) and grids of the radix-2 streaming passes
 SHAPES = [(8, 8, 4), (16, 32, 8), (64, 64, 32), (32, 256, 16), (256, 16, 12), (8, 2048, 6), (1024, 8, 10),
           (64, 128, 10), (128, 64, 14), (128, 128, 16), (256, 128, 32), (128, 256, 12), (128, 512, 24),
-          (512, 128, 8), (256, 256, 20), (256, 512, 64), (512, 256, 8)]
+          (512, 128, 8), (256, 256, 20), (256, 512, 64), (512, 256, 8),
+          (64, 1024, 8), (1024, 64, 6), (512, 512, 8), (128, 2048, 4), (2048, 64, 4)]
 
 
 @pytest.mark.parametrize("prec", [P.PLAIN_FP64, P.MIXED_FP32])

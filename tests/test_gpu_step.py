@@ -107,6 +107,29 @@ def test_single_step_mixed_differential_solve(ny, nx, ns):
     h.close()
 
 
+def test_single_step_mixed_streaming_radix8():
+    # 64 x 1024 has no cluster shape: radix-8 streaming passes with the full
+    # history; two independent FP32 solves, as in the 32 x 64 case
+    ny, nx, ns = 64, 1024, 8
+    r = P.RunParams(nx=nx, ny=ny, ns=ns, precision=P.MIXED_FP32, f_a=0.5, phi_p=0.2, f0=10.0)
+    omega = W.random_omega(ny, nx, seed=41, amp=0.05)
+    pop = W.random_populations(ny, nx, seed=42)
+    vel = W.random_velocity(ny, nx, seed=43, amp=0.02)
+    h = P.EpdLb([r])
+    h.set_state(0, omega, pop, vel)
+    h.step(1)
+    p, st = oracle_state_from(r, omega, pop, vel)
+    O.step(p, st)
+    gom, gpop, gvel = h.get_state(0)
+    gphi, gq = h.densities(0)
+    assert rel_err(gphi, st.phi) < 2e-6
+    assert rel_err(gq, st.q) < 2e-6
+    assert fluct_err(gom, st.omega) < 2e-6
+    assert rel_err(gvel, st.vel) < 2e-3
+    assert np.abs(gpop - st.pop).max() < 1e-7
+    h.close()
+
+
 def test_mixed_tracks_fp64_over_100_steps():
     # 64 x 64, N_s = 32 from the seeded quench: MIXED and PLAIN_FP64 side by
     # side; the remaining velocity difference comes from the FP32 resolution
