@@ -12,6 +12,7 @@
 
 #include "common.cuh"
 #include "engine.h"
+#include "fft8.cuh"
 #include "surrogate.h"
 
 namespace epdlb {
@@ -74,6 +75,8 @@ size_t carve_group(Group &G, char *base, size_t off)
     G.twy_d = (double2 *)take((size_t)G.g.ny / 2 * sizeof(double2));
     G.twx_full = (float2 *)take((size_t)G.g.nx * sizeof(float2));
     G.twy_full = (float2 *)take((size_t)G.g.ny * sizeof(float2));
+    G.tab8x = (float2 *)take((size_t)tabs_total(G.g.logx) * sizeof(float2));
+    G.tab8y = (float2 *)take((size_t)tabs_total(G.g.logy) * sizeof(float2));
     // cluster solve (MIXED_FP32): stored states of both chains, and the
     // differential second solve's buffers
     G.hc = G.hd = G.rho = nullptr;
@@ -235,6 +238,11 @@ static cudaError_t upload_tables_t(Group &G, cudaStream_t s)
         const std::vector<float> fx = full(G.g.nx), fy = full(G.g.ny);
         if ((e = cudaMemcpyAsync(G.twx_full, fx.data(), fx.size() * sizeof(float), cudaMemcpyHostToDevice, s))) return e;
         if ((e = cudaMemcpyAsync(G.twy_full, fy.data(), fy.size() * sizeof(float), cudaMemcpyHostToDevice, s))) return e;
+        std::vector<float> tx(2 * (size_t)tabs_total(G.g.logx)), ty(2 * (size_t)tabs_total(G.g.logy));
+        build_tables_host(G.g.logx, fx.data(), tx.data());
+        build_tables_host(G.g.logy, fy.data(), ty.data());
+        if ((e = cudaMemcpyAsync(G.tab8x, tx.data(), tx.size() * sizeof(float), cudaMemcpyHostToDevice, s))) return e;
+        if ((e = cudaMemcpyAsync(G.tab8y, ty.data(), ty.size() * sizeof(float), cudaMemcpyHostToDevice, s))) return e;
         if ((e = cudaStreamSynchronize(s))) return e;
     }
     std::vector<double> f0(G.g.nruns);

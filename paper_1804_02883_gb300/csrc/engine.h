@@ -71,6 +71,7 @@ struct Group {
     void *twx, *twy, *kx, *ky;     // bulk precision: twiddles, exp(-rg^2 k^2 ds)/N
     double2 *twx_d, *twy_d;        // FP64 twiddles for the EPD/force passes
     float2 *twx_full, *twy_full;   // FP32 twiddles exp(-2 pi i j/N), j < N (cluster solve); may be null
+    float2 *tab8x = nullptr, *tab8y = nullptr;  // radix-8 pass tables (fft8.cuh layout); null with twx_full
     int *err;                      // device error word (shared by the handle)
 };
 

@@ -34,7 +34,7 @@ struct EpdK {
     void *force;
     int bulk_double;
     const void *twx, *twy;  // twiddles of the transform type
-    const float2 *twx_full, *twy_full;  // exp(-2 pi i j / N), j < N (FP32 radix-8 kernels)
+    const float2 *tab8x, *tab8y;  // radix-8 pass tables (FP32 radix-8 kernels)
     int rows, logc;
     double kunit_x, kunit_y;  // 2 pi / (n dx) per axis
     double mu_ref[3];         // mu_I at the homogeneous composition, omega = 0
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(RowTile<LOGX>::T) epd_row8(EpdK k)
     const long long n = g.n;
     const long long base = (long long)blockIdx.x * P;
     float2 *cz = reinterpret_cast<float2 *>(k.cz);
-    fill_tables<LOGX, 0>(tab, k.twx_full, tid, T);
+    copy_tables(tab, k.tab8x, RT::TAB, tid, T);
     for (int i = tid; i < P; i += T) {
         const long long s = base + i;
         float2 v;
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(ColTile<LOGY>::T) epd_col8(EpdK k)
     const int nx = g.nx, run = blockIdx.y, pair = blockIdx.z, x0 = blockIdx.x * C, tid = threadIdx.x;
     const long long n = g.n;
     float2 *cz = reinterpret_cast<float2 *>(k.cz);
-    fill_tables<LOGY, 0>(tab, k.twy_full, tid, T);
+    copy_tables(tab, k.tab8y, CT::TAB, tid, T);
     for (int i = tid; i < P; i += T) {
         const long long s = (long long)(i / C) * nx + x0 + (i % C);
         float2 v;
@@ -454,7 +454,7 @@ static bool col8_at(int logy, const EpdK &k, dim3 grid_yz, cudaStream_t s)
 // least 2048 sites
 static bool use_r8(const Group &G)
 {
-    return G.prec == EPD_LB_MIXED_FP32 && G.twx_full && G.twy_full && G.g.logx >= 6 && G.g.logy >= 6 && G.g.logx <= 11 &&
+    return G.prec == EPD_LB_MIXED_FP32 && G.tab8x && G.tab8y && G.g.logx >= 6 && G.g.logy >= 6 && G.g.logx <= 11 &&
            G.g.logy <= 11 && G.g.n >= 2048;
 }
 
@@ -474,8 +474,8 @@ static EpdK make_k(Group &G)
     // FP32 transforms use the bulk (FP32) twiddle tables, FP64 ones the FP64 tables
     k.twx = k.bulk_double ? (const void *)G.twx_d : G.twx;
     k.twy = k.bulk_double ? (const void *)G.twy_d : G.twy;
-    k.twx_full = reinterpret_cast<const float2 *>(G.twx_full);
-    k.twy_full = reinterpret_cast<const float2 *>(G.twy_full);
+    k.tab8x = G.tab8x;
+    k.tab8y = G.tab8y;
     k.rows = G.sh.rows_epd;
     k.logc = ilog2(G.sh.cols_epd);
     const double pi = 3.14159265358979323846;

@@ -314,6 +314,35 @@ __device__ __forceinline__ void fill_tables(float2 *tabs, const float2 *tw, int 
     }
 }
 
+// Copy of prebuilt pass tables (built on the host with the same layout as
+// fill_tables) into shared memory: coalesced, no scattered gathers.
+__device__ __forceinline__ void copy_tables(float2 *dst, const float2 *src, int len, int tid, int nthreads)
+{
+    for (int e = tid; e < len; e += nthreads) dst[e] = src[e];
+}
+
+// Host: the pass tables of a length-2^logn transform from the full twiddles
+// tw[j] = exp(-2 pi i j / N) (interleaved re, im), in fill_tables' layout.
+inline void build_tables_host(int logn, const float *tw, float *out)
+{
+    const int np = npasses(logn);
+    for (int I = 0; I < 2 * (np - 1); ++I) {
+        const bool invp = I >= np - 1;
+        const int pi = invp ? I - (np - 1) : I;
+        const int slog = invp ? inv_slog(logn, pi) : fwd_slog(logn, pi);
+        const int rlog = invp ? inv_rlog(logn, pi) : fwd_rlog(logn, pi);
+        const int off = invp ? inv_off(logn, pi) : fwd_off(logn, pi);
+        const int M = (1 << logn) >> (slog + rlog), len = tab_rows(rlog) * M;
+        for (int e = 0; e < len; ++e) {
+            const int row = e / M, p = e % M;
+            const int k = rlog == 3 ? (1 << row) : row + 1;
+            const int j = (p << slog) * k;
+            out[2 * (off + e)] = tw[2 * j];
+            out[2 * (off + e) + 1] = tw[2 * j + 1];
+        }
+    }
+}
+
 // Tiles of the streaming passes (one CTA per tile, in-place transforms): a
 // row tile holds 2048 points (max(1, 2048 / nx) whole rows), a column tile 16
 // whole columns (8 from 1024 rows on).

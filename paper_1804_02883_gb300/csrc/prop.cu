@@ -255,7 +255,7 @@ struct Stream8K {
     float2 *hist;         // [run][N_s + 1][n]
     const float2 *efac;   // [run][n]
     double *part;
-    const float2 *twx, *twy;  // full tables exp(-2 pi i j / N)
+    const float2 *twx, *twy;  // radix-8 pass tables (fft8.cuh layout)
     const float *kx, *ky;
 };
 
@@ -279,15 +279,13 @@ __global__ void __launch_bounds__(ColTile<LOGY>::T) prop_col8(Stream8K k)
     constexpr int NY = CT::NY, C = CT::C, P = CT::P, T = CT::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *buf = reinterpret_cast<float2 *>(smem_raw);
-    float2 *tab = buf + P;
-    float *ky = reinterpret_cast<float *>(tab + CT::TAB);
     const int nx = k.g.nx, run = blockIdx.y, x0 = blockIdx.x * C, tid = threadIdx.x;
     float2 *data = k.chain + (size_t)run * k.g.n;
-    fill_tables<LOGY, 0>(tab, k.twy, tid, T);
-    for (int i = tid; i < NY; i += T) ky[i] = k.ky[i];
     for (int i = tid; i < P; i += T) buf[i] = data[(size_t)(i / C) * nx + x0 + (i % C)];
     __syncthreads();
-    transform_pair<LOGY, T, CL, P>(buf, tab, ScaleBins{ky}, tid);
+    // twiddle tables and Fourier factors straight from global memory (L1):
+    // shared memory holds only the tile, so more tiles are in flight per SM
+    transform_pair<LOGY, T, CL, P>(buf, k.twy, ScaleBins{k.ky}, tid);
     constexpr int RLOG_L = inv_rlog(LOGY, npasses(LOGY) - 1), RR = 1 << RLOG_L, PER_L = NY / RR, NB_L = P / RR / T;
     float2 h[NB_L][RR];
     int bb[NB_L], tt[NB_L];
@@ -309,17 +307,13 @@ __global__ void __launch_bounds__(RowTile<LOGX>::T) prop_row8(Stream8K k, int m)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
     float2 *buf = reinterpret_cast<float2 *>(smem_raw);
-    float2 *tab = buf + RT::ROWS * RL::PITCH;
-    float *kx = reinterpret_cast<float *>(tab + RT::TAB);
     const int run = blockIdx.y, tid = threadIdx.x;
     const long long n = k.g.n, base = (long long)blockIdx.x * P;
     const int ns = k.g.ns, na = k.g.na;
     float2 *data = k.chain + (size_t)run * n + base;
-    fill_tables<LOGX, 0>(tab, k.twx, tid, T);
-    for (int i = tid; i < NX; i += T) kx[i] = k.kx[i];
     for (int i = tid; i < P; i += T) buf[RL::at(i / NX, i % NX)] = data[i];
     __syncthreads();
-    transform_pair<LOGX, T, RL, P>(buf, tab, ScaleBins{kx}, tid);
+    transform_pair<LOGX, T, RL, P>(buf, k.twx, ScaleBins{k.kx}, tid);
     constexpr int RLOG_L = inv_rlog(LOGX, npasses(LOGX) - 1), RR = 1 << RLOG_L, PER_L = NX / RR, NB_L = P / RR / T;
     float2 h[NB_L][RR];
     int bb[NB_L], tt[NB_L];
@@ -366,40 +360,49 @@ __global__ void __launch_bounds__(kThreads) prop_contour_stream(GroupGeom g, con
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float2 *hz = hist + (size_t)run * (ns + 1) * n + i;
+    // Nodes m and N_s - m are read together: z_m = (g_m, g'_m) and z_{N_s-m}
+    // give the terms g_m g'_{N_s-m} (node m) and g_{N_s-m} g'_m (node N_s - m).
+    // Weight-1 terms of each block go through FP32 partial sums of at most 8
+    // terms; the half-weight end and junction nodes straight into FP64.
     double ia = 0.0, ib = 0.0;
-    float pa = 0.f, gwa = 0.f, gwb = 0.f;
-    int cnt = 0;
-    constexpr int U = 8;
-    for (int m0 = 0; m0 <= ns; m0 += U) {
-        float gv[U], gpv[U];
+    float pa = 0.f, pb = 0.f;
+    int ca = 0, cb = 0;
+    auto add = [&](int j, float t) {
+        const float wa = (na == 0 || j > na) ? 0.f : ((j == 0 || j == na) ? 0.5f : 1.f);
+        const float wb = (na == ns || j < na) ? 0.f : ((j == na || j == ns) ? 0.5f : 1.f);
+        if (wa == 1.f) {
+            pa += t;
+            if (++ca == 8) { ia += (double)pa; pa = 0.f; ca = 0; }
+        } else if (wb == 1.f) {
+            pb += t;
+            if (++cb == 8) { ib += (double)pb; pb = 0.f; cb = 0; }
+        } else {
+            ia += (double)wa * (double)t;
+            ib += (double)wb * (double)t;
+        }
+    };
+    const int half = ns / 2;
+    constexpr int U = 4;
+    for (int m0 = 0; m0 <= half; m0 += U) {
+        float2 zl[U], zr[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int m = m0 + u;
-            if (m <= ns) {
-                gv[u] = hz[(size_t)m * n].x;          // g(s_m)
-                gpv[u] = hz[(size_t)(ns - m) * n].y;  // g'(1 - s_m)
+            if (m <= half) {
+                zl[u] = hz[(size_t)m * n];
+                zr[u] = hz[(size_t)(ns - m) * n];
             }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int m = m0 + u;
-            if (m > ns) break;
-            const float wa = (na == 0 || m > na) ? 0.f : ((m == 0 || m == na) ? 0.5f : 1.f);
-            const float wb = (na == ns || m < na) ? 0.f : ((m == na || m == ns) ? 0.5f : 1.f);
-            if (cnt > 0 && (wa != gwa || wb != gwb || cnt == 8)) {
-                ia += (double)gwa * pa;
-                ib += (double)gwb * pa;
-                pa = 0.f;
-                cnt = 0;
-            }
-            gwa = wa;
-            gwb = wb;
-            ++cnt;
-            pa += gv[u] * gpv[u];
+            if (m > half) break;
+            add(m, zl[u].x * zr[u].y);
+            if (ns - m != m) add(ns - m, zr[u].x * zl[u].y);
         }
     }
-    ia += (double)gwa * pa;
-    ib += (double)gwb * pa;
+    ia += (double)pa;
+    ib += (double)pb;
     const double c = g.phi_p * g.ds / qp;
     double *ph = phi + (size_t)run * 3 * n;
     ph[i] = c * ia;
@@ -413,7 +416,7 @@ static void stream8_run(Stream8K &k, const Group &G, cudaStream_t s, const Solve
 {
     using RT = RowTile<LX>;
     using CT = ColTile<LY>;
-    const size_t sr = RT::SMEM + RT::NX * sizeof(float), sc = CT::SMEM + CT::NY * sizeof(float);
+    const size_t sr = (size_t)RT::ROWS * RowLayout<LX>::PITCH * sizeof(float2), sc = (size_t)CT::P * sizeof(float2);
     static bool conf = false;
     if (!conf) {
         cudaFuncSetAttribute(prop_row8<LX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
@@ -497,7 +500,7 @@ static cudaError_t solve_t(Group &G, const double *omega, double *phi, double *q
         // whole contour in one cluster-resident launch, then the contour sums
         return launch_cluster_solve(G, s, false, pg, phi, q, probe);
     }
-    if (sizeof(T) == sizeof(float) && G.hist_full && G.twx_full) {
+    if (sizeof(T) == sizeof(float) && G.hist_full && G.tab8x) {
         // radix-8 streaming passes with the full history, then the contour pass
         Stream8K k8;
         k8.g = g;
@@ -505,8 +508,8 @@ static cudaError_t solve_t(Group &G, const double *omega, double *phi, double *q
         k8.hist = reinterpret_cast<float2 *>(G.hist);
         k8.efac = reinterpret_cast<const float2 *>(G.efac);
         k8.part = G.part;
-        k8.twx = reinterpret_cast<const float2 *>(G.twx_full);
-        k8.twy = reinterpret_cast<const float2 *>(G.twy_full);
+        k8.twx = G.tab8x;
+        k8.twy = G.tab8y;
         k8.kx = reinterpret_cast<const float *>(G.kx);
         k8.ky = reinterpret_cast<const float *>(G.ky);
         prop_start8<<<dim3(pg, g.nruns), kThreads, 0, s>>>(k8);

@@ -63,7 +63,7 @@ struct PropCK {
     const float2 *efac;   // (E_A, E_B) [run][n]
     const float2 *rho;    // (rho_A, rho_B) [run][n] (DIFF)
     int *err;             // bit 2: an exchange wait gave up
-    const float2 *twx, *twy;  // exp(-2 pi i j / N), j < N
+    const float2 *twx, *twy;  // radix-8 pass tables (fft8.cuh layout)
     const float *kx, *ky;     // exp(-R_G^2 k^2 ds) / N
 };
 
@@ -155,8 +155,8 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
     const int n = (int)k.g.n, ns = k.g.ns, na = k.g.na;
     const int krow0 = crank * R2;  // first packed row of this CTA
 
-    fill_tables<LOGX, 0>(tabx, k.twx, tid, T);
-    fill_tables<LOGY, 0>(taby, k.twy, tid, T);
+    copy_tables(tabx, k.twx, G::TABX, tid, T);
+    copy_tables(taby, k.twy, G::TABY, tid, T);
     for (int i = tid; i < NX; i += T) kx[i] = k.kx[i];
     for (int i = tid; i < NY; i += T) ky[i] = k.ky[i];
     const float2 *efac = k.efac + (size_t)run * n;
@@ -620,8 +620,8 @@ cudaError_t launch_cluster_solve(Group &G, cudaStream_t s, bool diff, int nprep_
     k.efac = reinterpret_cast<const float2 *>(G.efac);
     k.rho = reinterpret_cast<const float2 *>(G.rho);
     k.err = G.err;
-    k.twx = reinterpret_cast<const float2 *>(G.twx_full);
-    k.twy = reinterpret_cast<const float2 *>(G.twy_full);
+    k.twx = reinterpret_cast<const float2 *>(G.tab8x);
+    k.twy = reinterpret_cast<const float2 *>(G.tab8y);
     k.kx = reinterpret_cast<const float *>(G.kx);
     k.ky = reinterpret_cast<const float *>(G.ky);
     cudaLaunchConfig_t cfg = {};
