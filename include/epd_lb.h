@@ -182,6 +182,20 @@ int epd_lb_load(epd_lb *h, const void *buf, size_t len);
 int epd_lb_enable_timing(epd_lb *h, int32_t on);
 int epd_lb_kernel_times(epd_lb *h, double *ms);
 
+/* Launch configuration chosen for a run's group (batching and tiling of the
+ * hot path; not in the paper).  out[0]: solve path, 0 = streaming radix-2
+ * passes, 1 = streaming radix-8 passes with the full contour history, 2 =
+ * cluster-resident solve; out[1]: CTAs per cluster (path 2) or 0; out[2]: the
+ * column tile width of the radix-8 column passes (EPD and streaming
+ * propagator; 4, 8 or 16 columns), chosen at epd_lb_init by timing each
+ * width on the group's own state, or 0 where those passes are not used
+ * (EPD_LB_COLUMN_TILE=4|8|16 in the environment forces a width; every width
+ * gives bit-identical results); out[3]: 1 if the step's second solve is the
+ * differential one; out[4]: the column tile width of the streaming
+ * propagator passes (path 1, tuned the same way), else 0.  out holds 5
+ * values.  Returns EPD_LB_EINVAL for a bad run index or NULL out. */
+int epd_lb_tiles(epd_lb *h, int32_t run, int32_t *out);
+
 /*
  * Learned density surrogate: a convolutional network that approximates the
  * map omega -> (Phi_A, Phi_B) of the single-chain solve, Eqs. (6)-(10), with

@@ -34,7 +34,7 @@ SYMBOLS = (
     "epd_lb_velocity", "epd_lb_densities_dev", "epd_lb_velocity_dev", "epd_lb_get_state",
     "epd_lb_set_state", "epd_lb_solve", "epd_lb_observables", "epd_lb_save", "epd_lb_load",
     "epd_lb_last_error", "epd_lb_destroy", "epd_prop_solve_workspace_bytes", "epd_prop_solve",
-    "epd_lb_enable_timing", "epd_lb_kernel_times", "epd_prop_solve_noalloc",
+    "epd_lb_enable_timing", "epd_lb_kernel_times", "epd_prop_solve_noalloc", "epd_lb_tiles",
     "epd_sur_num_params", "epd_sur_workspace_bytes", "epd_sur_forward", "epd_sur_gradients", "epd_sur_train_step",
     "epd_lb_surrogate_workspace_bytes", "epd_lb_set_surrogate", "epd_lb_surrogate_stats", "epd_lb_fields_dev",
 )
@@ -127,6 +127,7 @@ def lib():
             "epd_prop_solve": (ctypes.c_int, [P, vp, vp, vp, vp, ctypes.c_size_t, vp]),
             "epd_lb_enable_timing": (ctypes.c_int, [vp, i32]),
             "epd_lb_kernel_times": (ctypes.c_int, [vp, vp]),
+            "epd_lb_tiles": (ctypes.c_int, [vp, ctypes.c_int32, vp]),
             "epd_prop_solve_noalloc": (ctypes.c_int, [P, vp, vp, vp, vp]),
             "epd_sur_num_params": (ctypes.c_int32, []),
             "epd_sur_workspace_bytes": (ctypes.c_int, [i32, i32, i32, i32, szp]),
@@ -337,6 +338,16 @@ class EpdLb:
         if out[4] == 1.0:
             return {"prop_cluster": float(out[0]), "lb_collide_stream": float(out[3])}
         return dict(zip(("prop_row_store", "prop_row_accumulate", "prop_col", "lb_collide_stream"), out[:4].tolist()))
+
+    def tiles(self, run: int) -> dict:
+        """Launch configuration of a run's group: solve path (0 streaming
+        radix-2, 1 streaming radix-8, 2 cluster), CTAs per cluster, the
+        autotuned column tile widths (EPD passes; streaming propagator
+        passes), and whether the differential second solve is used."""
+        out = np.zeros(5, dtype=np.int32)
+        self._ck(lib().epd_lb_tiles(self.h, run, out.ctypes.data_as(ctypes.c_void_p)), "epd_lb_tiles")
+        return {"path": int(out[0]), "cluster_ctas": int(out[1]), "column_tile": int(out[2]), "differential": bool(out[3]),
+                "stream_column_tile": int(out[4])}
 
     def set_surrogate(self, params, s_in: float, s_out: float, exact_every: int = 8, residual_tol: float = 1e-3):
         """Attach the learned surrogate (FP32 parameters, host array or torch

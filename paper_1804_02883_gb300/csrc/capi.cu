@@ -566,6 +566,8 @@ extern "C" int epd_lb_init(const epd_lb_params *p, int32_t nruns, void *workspac
         if (upload_tables_e(G, h->stream) != cudaSuccess) return bail(EPD_LB_ECUDA);
         if (launch_init_state(G, h->stream) != cudaSuccess) return bail(EPD_LB_ECUDA);
         if (launch_solve(G, G.omega, G.phi, G.q, h->stream) != cudaSuccess) return bail(EPD_LB_ECUDA);
+        if (tune_column_tiles(G, h->stream) != cudaSuccess) return bail(EPD_LB_ECUDA);
+        if (tune_stream_tiles(G, h->stream) != cudaSuccess) return bail(EPD_LB_ECUDA);
         G.diff = G.hd != nullptr && G.twx_full != nullptr && cluster_solve_supported(G);
     }
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(EPD_LB_ECUDA);
@@ -863,6 +865,22 @@ extern "C" int epd_lb_kernel_times(epd_lb *h, double *ms)
         ms[k] = (double)t;
     }
     ms[4] = h->timed_cluster ? 1.0 : 0.0;
+    return EPD_LB_OK;
+}
+
+extern "C" int epd_lb_tiles(epd_lb *h, int32_t run, int32_t *out)
+{
+    Group *G;
+    int m;
+    if (!out) return EPD_LB_EINVAL;
+    if (int rc = locate(h, run, &G, &m)) return rc;
+    (void)m;
+    const bool cluster = G->hc && G->twx_full && cluster_solve_supported(*G);
+    out[0] = cluster ? 2 : (G->hist_full ? 1 : 0);
+    out[1] = cluster ? cluster_ctas(*G) : 0;
+    out[2] = G->colw;
+    out[3] = G->diff ? 1 : 0;
+    out[4] = G->colw_prop;
     return EPD_LB_OK;
 }
 

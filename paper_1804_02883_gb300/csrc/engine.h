@@ -55,6 +55,8 @@ struct Group {
     void *rho = nullptr;      // (rho_A, rho_B) = expm1(-N d omega ds / 2), [run][n] float2
     bool diff = false;        // the step uses the reference + differential solve pair
     bool hist_full = false;   // streaming radix-8 solve: hist holds all N_s + 1 nodes
+    int colw = 0;             // radix-8 EPD column tile width chosen by the autotuner (0: default)
+    int colw_prop = 0;        // radix-8 streaming propagator column tile width (0: default)
     double2 *cz;       // 4 complex FP64 scratch planes per run: [run][4][n]
     double *part;      // reduction partials, [run][kMaxPart]
     double *f0_lat;    // [run]
@@ -102,6 +104,10 @@ cudaError_t launch_solve(Group &G, const double *omega, double *phi, double *q, 
 // Second solve of the step as a difference from the reference solve at
 // omega~ (phi_t, q_t): Phi(t+dt) = Phi~ + dPhi, Q likewise (G.diff only).
 cudaError_t launch_solve_delta(Group &G, cudaStream_t s, const SolveProbe *probe = nullptr);
+
+// Column tile autotuner of the radix-8 column passes (sets G.colw).
+cudaError_t tune_column_tiles(Group &G, cudaStream_t s);
+cudaError_t tune_stream_tiles(Group &G, cudaStream_t s);  // sets G.colw_prop
 
 // EPD parts of the step.
 cudaError_t launch_aux_convection(Group &G, cudaStream_t s);   // omega, vel -> omega_t

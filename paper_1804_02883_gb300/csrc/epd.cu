@@ -15,6 +15,7 @@
 // fluctuations rather than with mu itself), omega (zero-mean noise), and
 // dPhi^D.  Pointwise combinations with the fields are done in FP64.
 #include <cmath>
+#include <cstdlib>
 
 #include "common.cuh"
 #include "engine.h"
@@ -336,10 +337,10 @@ __global__ void __launch_bounds__(RowTile<LOGX>::T) epd_row8(EpdK k)
         }
 }
 
-template <int LOGY, int MODE>
-__global__ void __launch_bounds__(ColTile<LOGY>::T) epd_col8(EpdK k)
+template <int LOGY, int MODE, int CW>
+__global__ void __launch_bounds__(ColTile<LOGY, CW>::T) epd_col8(EpdK k)
 {
-    using CT = ColTile<LOGY>;
+    using CT = ColTile<LOGY, CW>;
     using CL = ColLayout<LOGY, CT::C>;
     constexpr int NY = CT::NY, C = CT::C, P = CT::P, T = CT::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -432,22 +433,33 @@ static bool row8_at(int logx, const EpdK &k, dim3 grid_yz, cudaStream_t s)
         return true;
     }
 }
+template <int MODE, int L, int CW>
+static bool col8_launch(const EpdK &k, dim3 grid_yz, cudaStream_t s)
+{
+    using CT = ColTile<L, CW>;
+    if (k.g.nx % CT::C) return false;
+    static bool conf = false;
+    if (!conf) {
+        conf = cudaFuncSetAttribute(epd_col8<L, MODE, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CT::SMEM) == cudaSuccess;
+        if (!conf) return false;
+    }
+    epd_col8<L, MODE, CW><<<dim3(k.g.nx / CT::C, grid_yz.y, grid_yz.z), CT::T, CT::SMEM, s>>>(k);
+    return true;
+}
+// colw: column tile width (4, 8, 16; 0 = default)
 template <int MODE, int L>
-static bool col8_at(int logy, const EpdK &k, dim3 grid_yz, cudaStream_t s)
+static bool col8_at(int logy, const EpdK &k, dim3 grid_yz, cudaStream_t s, int colw)
 {
     if constexpr (L > 11) {
         return false;
     } else {
-        if (logy != L) return col8_at<MODE, L + 1>(logy, k, grid_yz, s);
-        using CT = ColTile<L>;
-        if (k.g.nx % CT::C) return false;
-        static bool conf = false;
-        if (!conf) {
-            conf = cudaFuncSetAttribute(epd_col8<L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CT::SMEM) == cudaSuccess;
-            if (!conf) return false;
+        if (logy != L) return col8_at<MODE, L + 1>(logy, k, grid_yz, s, colw);
+        switch (colw) {
+        case 4: return col8_launch<MODE, L, 4>(k, grid_yz, s);
+        case 8: return col8_launch<MODE, L, 8>(k, grid_yz, s);
+        case 16: return col8_launch<MODE, L, 16>(k, grid_yz, s);
+        default: return col8_launch<MODE, L, ColTile<L>::C>(k, grid_yz, s);
         }
-        epd_col8<L, MODE><<<dim3(k.g.nx / CT::C, grid_yz.y, grid_yz.z), CT::T, CT::SMEM, s>>>(k);
-        return true;
     }
 }
 // radix-8 passes apply to MIXED_FP32 groups with 64 <= nx, ny <= 2048 and at
@@ -500,7 +512,7 @@ template <typename TT> static cudaError_t aux_t(Group &G, cudaStream_t s)
     k.omega_dst = G.omega_t;
     if (use_r8(G)) {
         const dim3 gz(1, G.g.nruns, 2);
-        if (row8_at<ROW_GRAD, 6>(G.g.logx, k, gz, s) && col8_at<COL_CONVECT, 6>(G.g.logy, k, gz, s)) return cudaGetLastError();
+        if (row8_at<ROW_GRAD, 6>(G.g.logx, k, gz, s) && col8_at<COL_CONVECT, 6>(G.g.logy, k, gz, s, G.colw)) return cudaGetLastError();
         return cudaErrorInvalidConfiguration;
     }
     epd_row<TT, ROW_GRAD><<<dim3(G.g.ny / G.sh.rows_epd, G.g.nruns, 2), kThreads, row_smem<TT>(G), s>>>(k);
@@ -514,7 +526,7 @@ template <typename TT> static cudaError_t diffusion_t(Group &G, cudaStream_t s)
     k.omega_dst = G.omega;
     if (use_r8(G)) {
         const dim3 gz(1, G.g.nruns, 2);
-        if (row8_at<ROW_LAP, 6>(G.g.logx, k, gz, s) && col8_at<COL_DIFFUSE, 6>(G.g.logy, k, gz, s)) return cudaGetLastError();
+        if (row8_at<ROW_LAP, 6>(G.g.logx, k, gz, s) && col8_at<COL_DIFFUSE, 6>(G.g.logy, k, gz, s, G.colw)) return cudaGetLastError();
         return cudaErrorInvalidConfiguration;
     }
     epd_row<TT, ROW_LAP><<<dim3(G.g.ny / G.sh.rows_epd, G.g.nruns, 2), kThreads, row_smem<TT>(G), s>>>(k);
@@ -527,7 +539,7 @@ template <typename TT> static cudaError_t force_t(Group &G, cudaStream_t s)
     EpdK k = make_k(G);
     if (use_r8(G)) {
         const dim3 gz(1, G.g.nruns, 1);
-        if (row8_at<ROW_FWD_S, 6>(G.g.logx, k, gz, s) && col8_at<COL_FORCE, 6>(G.g.logy, k, gz, s) &&
+        if (row8_at<ROW_FWD_S, 6>(G.g.logx, k, gz, s) && col8_at<COL_FORCE, 6>(G.g.logy, k, gz, s, G.colw) &&
             row8_at<ROW_INV_FORCE, 6>(G.g.logx, k, gz, s))
             return cudaGetLastError();
         return cudaErrorInvalidConfiguration;
@@ -535,6 +547,58 @@ template <typename TT> static cudaError_t force_t(Group &G, cudaStream_t s)
     epd_row<TT, ROW_FWD_S><<<dim3(G.g.ny / G.sh.rows_epd, G.g.nruns, 1), kThreads, row_smem<TT>(G), s>>>(k);
     epd_col<TT, COL_FORCE><<<dim3(G.g.nx / G.sh.cols_epd, G.g.nruns, 1), kThreads, col_smem<TT>(G), s>>>(k);
     epd_row<TT, ROW_INV_FORCE><<<dim3(G.g.ny / G.sh.rows_epd, G.g.nruns, 1), kThreads, row_smem<TT>(G), s>>>(k);
+    return cudaGetLastError();
+}
+
+// Column tile autotuner (radix-8 EPD column passes and streaming propagator
+// column passes): each candidate width runs the diffusion column pass a few
+// times on the group's state, writing only scratch (omega~, the EPD scratch);
+// the fastest width is kept in G.colw.  Every width computes the same
+// per-column transforms, so the results do not depend on the choice.
+// EPD_LB_COLUMN_TILE=4|8|16 in the environment forces a width.
+cudaError_t tune_column_tiles(Group &G, cudaStream_t s)
+{
+    if (!use_r8(G)) return cudaSuccess;
+    if (const char *env = std::getenv("EPD_LB_COLUMN_TILE")) {
+        const int w = std::atoi(env);
+        if (w == 4 || w == 8 || w == 16) {
+            G.colw = w;
+            return cudaSuccess;
+        }
+    }
+    EpdK k = make_k(G);
+    k.omega_t = G.omega;      // read the current state ...
+    k.phi_t = G.phi;
+    k.omega_dst = G.omega_t;  // ... write only scratch (rewritten by the next step)
+    const dim3 gz(1, G.g.nruns, 2);
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return cudaGetLastError();
+    float best = 1e30f;
+    int best_w = 0;
+    for (int w : kColWidths) {
+        if (G.g.nx % w) continue;
+        if (!col8_at<COL_DIFFUSE, 6>(G.g.logy, k, gz, s, w)) {
+            cudaGetLastError();
+            continue;
+        }
+        float t = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {
+            cudaEventRecord(a, s);
+            col8_at<COL_DIFFUSE, 6>(G.g.logy, k, gz, s, w);
+            cudaEventRecord(b, s);
+            cudaEventSynchronize(b);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a, b);
+            if (rep > 0 && ms < t) t = ms;  // the first launch is a warm-up
+        }
+        if (t < best) {
+            best = t;
+            best_w = w;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    G.colw = best_w;
     return cudaGetLastError();
 }
 

@@ -344,17 +344,20 @@ inline void build_tables_host(int logn, const float *tw, float *out)
 }
 
 // Tiles of the streaming passes (one CTA per tile, in-place transforms): a
-// row tile holds 2048 points (max(1, 2048 / nx) whole rows), a column tile 16
-// whole columns (8 from 1024 rows on).
+// row tile holds 2048 points (max(1, 2048 / nx) whole rows), a column tile CW
+// whole columns (by default 16, 8 from 1024 rows on; the autotuner picks 4, 8
+// or 16 per grid).
 template <int LOGX> struct RowTile {
     static constexpr int NX = 1 << LOGX, ROWS = NX >= 2048 ? 1 : 2048 / NX, P = ROWS * NX, T = P / 8;
     static constexpr int TAB = tabs_total(LOGX);
     static constexpr size_t SMEM = (size_t)(ROWS * RowLayout<LOGX>::PITCH + TAB) * sizeof(float2);
 };
-template <int LOGY> struct ColTile {
-    static constexpr int NY = 1 << LOGY, C = LOGY >= 10 ? 8 : 16, P = C * NY, T = P / 8 > 512 ? 512 : P / 8;
+template <int LOGY, int CW = (LOGY >= 10 ? 8 : 16)> struct ColTile {
+    static constexpr int NY = 1 << LOGY, C = CW, P = C * NY, T = P / 8 > 512 ? 512 : P / 8;
     static constexpr int TAB = tabs_total(LOGY);
     static constexpr size_t SMEM = (size_t)(P + TAB) * sizeof(float2);
 };
+// column tile widths the autotuner chooses from (0: the default above)
+constexpr int kColWidths[3] = {4, 8, 16};
 
 } // namespace epdlb

@@ -17,6 +17,8 @@
 // the history (and vice versa), and the trapezoid sums of Eqs. (9)-(10) are
 // accumulated in FP64 on the fly.
 #include <cmath>
+#include <cstdlib>
+#include <type_traits>
 
 #include "common.cuh"
 #include "engine.h"
@@ -271,10 +273,10 @@ __global__ void __launch_bounds__(kThreads) prop_start8(Stream8K k)
     }
 }
 
-template <int LOGY>
-__global__ void __launch_bounds__(ColTile<LOGY>::T) prop_col8(Stream8K k)
+template <int LOGY, int CW>
+__global__ void __launch_bounds__(ColTile<LOGY, CW>::T) prop_col8(Stream8K k)
 {
-    using CT = ColTile<LOGY>;
+    using CT = ColTile<LOGY, CW>;
     using CL = ColLayout<LOGY, CT::C>;
     constexpr int NY = CT::NY, C = CT::C, P = CT::P, T = CT::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -410,24 +412,25 @@ __global__ void __launch_bounds__(kThreads) prop_contour_stream(GroupGeom g, con
     ph[2 * n + i] *= (1.0 - g.phi_p) / qs;
 }
 
-// The contour loop of the radix-8 streaming solve for (LX, LY).
-template <int LX, int LY>
+// The contour loop of the radix-8 streaming solve for (LX, LY), column tiles
+// of CW columns.
+template <int LX, int LY, int CW>
 static void stream8_run(Stream8K &k, const Group &G, cudaStream_t s, const SolveProbe *probe)
 {
     using RT = RowTile<LX>;
-    using CT = ColTile<LY>;
+    using CT = ColTile<LY, CW>;
     const size_t sr = (size_t)RT::ROWS * RowLayout<LX>::PITCH * sizeof(float2), sc = (size_t)CT::P * sizeof(float2);
     static bool conf = false;
     if (!conf) {
         cudaFuncSetAttribute(prop_row8<LX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
-        cudaFuncSetAttribute(prop_col8<LY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
+        cudaFuncSetAttribute(prop_col8<LY, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
         conf = true;
     }
     const dim3 gr((unsigned)(G.g.n / RT::P), G.g.nruns), gc(G.g.nx / CT::C, G.g.nruns);
     for (int m = 1; m <= G.g.ns; ++m) {
         const bool pa = probe && m == probe->m_acc, ps = probe && m == probe->m_store;
         if (pa) cudaEventRecordWithFlags(probe->ev[2], s, cudaEventRecordExternal);
-        prop_col8<LY><<<gc, CT::T, sc, s>>>(k);
+        prop_col8<LY, CW><<<gc, CT::T, sc, s>>>(k);
         if (pa) cudaEventRecordWithFlags(probe->ev[3], s, cudaEventRecordExternal);
         if (ps) cudaEventRecordWithFlags(probe->ev[0], s, cudaEventRecordExternal);
         prop_row8<LX><<<gr, RT::T, sr, s>>>(k, m);
@@ -442,7 +445,12 @@ static bool stream8_dispatch_y(int logy, Stream8K &k, const Group &G, cudaStream
         return false;
     } else {
         if (logy != LY) return stream8_dispatch_y<LX, LY + 1>(logy, k, G, s, probe);
-        stream8_run<LX, LY>(k, G, s, probe);
+        switch (G.colw_prop) {
+        case 4: stream8_run<LX, LY, 4>(k, G, s, probe); break;
+        case 8: stream8_run<LX, LY, 8>(k, G, s, probe); break;
+        case 16: stream8_run<LX, LY, 16>(k, G, s, probe); break;
+        default: stream8_run<LX, LY, ColTile<LY>::C>(k, G, s, probe); break;
+        }
         return true;
     }
 }
@@ -455,6 +463,91 @@ static bool stream8_dispatch(int logx, int logy, Stream8K &k, const Group &G, cu
         if (logx != LX) return stream8_dispatch<LX + 1>(logx, logy, k, G, s, probe);
         return stream8_dispatch_y<LX, 6>(logy, k, G, s, probe);
     }
+}
+
+// Column tile autotuner of the streaming propagator column pass (see
+// tune_column_tiles): times prop_col8 at each width on the group's chain
+// buffer (scratch until the next solve starts it) and keeps the fastest.
+template <int LY>
+static float time_col8(int w, Stream8K &k, const Group &G, cudaStream_t s, cudaEvent_t a, cudaEvent_t b)
+{
+    auto one = [&](auto tag) {
+        constexpr int CW = decltype(tag)::value;
+        using CT = ColTile<LY, CW>;
+        const size_t sc = (size_t)CT::P * sizeof(float2);
+        if (sc > 227 * 1024 ||
+            cudaFuncSetAttribute(prop_col8<LY, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc) != cudaSuccess) {
+            cudaGetLastError();  // this width does not fit: not a candidate
+            return 1e30f;
+        }
+        const dim3 gc(G.g.nx / CT::C, G.g.nruns);
+        float best = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {
+            cudaEventRecord(a, s);
+            prop_col8<LY, CW><<<gc, CT::T, sc, s>>>(k);
+            cudaEventRecord(b, s);
+            cudaEventSynchronize(b);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a, b);
+            if (rep > 0 && ms < best) best = ms;
+        }
+        return cudaGetLastError() == cudaSuccess ? best : 1e30f;
+    };
+    switch (w) {
+    case 4: return one(std::integral_constant<int, 4>{});
+    case 8: return one(std::integral_constant<int, 8>{});
+    default: return one(std::integral_constant<int, 16>{});
+    }
+}
+template <int LY>
+static int tune_col8_at(int logy, Stream8K &k, const Group &G, cudaStream_t s)
+{
+    if constexpr (LY > 11) {
+        return 0;
+    } else {
+        if (logy != LY) return tune_col8_at<LY + 1>(logy, k, G, s);
+        cudaEvent_t a, b;
+        if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return 0;
+        float best = 1e30f;
+        int best_w = 0;
+        for (int w : kColWidths) {
+            if (G.g.nx % w) continue;
+            const float t = time_col8<LY>(w, k, G, s, a, b);
+            if (t < best) {
+                best = t;
+                best_w = w;
+            }
+        }
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        return best_w;
+    }
+}
+
+cudaError_t tune_stream_tiles(Group &G, cudaStream_t s)
+{
+    if (!(G.prec == EPD_LB_MIXED_FP32 && G.hist_full && G.tab8x)) return cudaSuccess;
+    if (const char *env = std::getenv("EPD_LB_COLUMN_TILE")) {
+        const int w = std::atoi(env);
+        if (w == 4 || w == 8 || w == 16) {
+            G.colw_prop = w;
+            return cudaSuccess;
+        }
+    }
+    Stream8K k8;
+    k8.g = G.g;
+    k8.chain = reinterpret_cast<float2 *>(G.chain);
+    k8.hist = reinterpret_cast<float2 *>(G.hist);
+    k8.efac = reinterpret_cast<const float2 *>(G.efac);
+    k8.part = G.part;
+    k8.twx = G.tab8x;
+    k8.twy = G.tab8y;
+    k8.kx = reinterpret_cast<const float *>(G.kx);
+    k8.ky = reinterpret_cast<const float *>(G.ky);
+    cudaError_t e = cudaMemsetAsync(G.chain, 0, (size_t)G.g.nruns * G.g.n * sizeof(float2), s);
+    if (e != cudaSuccess) return e;
+    G.colw_prop = tune_col8_at<6>(G.g.logy, k8, G, s);
+    return cudaGetLastError();
 }
 
 bool stream8_eligible(int prec, int logx, int logy)
