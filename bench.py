@@ -325,6 +325,7 @@ def main():
 
     # kernel durations inside the timed steps (event nodes in the step graph)
     nsite = sites_per_step(runs)
+    tiles_path = h.tiles(0)["path"]
     kt = {k: statistics.mean(d[k] for d in kern) for k in kern[0]}
     hbm, peak_kind = peaks()
     kernels = {}
@@ -340,16 +341,22 @@ def main():
         tf = flops / (kt["prop_cluster"] * 1e-3) / 1e12
         peak_tf = FP32_SMS * FP32_LANES * 2 * FP32_MHZ * 1e6 / 1e12
         kernels["prop_cluster"] = {"ms": kt["prop_cluster"], "flops": flops, "achieved_tflops": tf, "frac": tf / peak_tf}
-        roofline = {"bound": "alu", "kernel": "prop_cluster (one single-chain solve of all runs)", "achieved": tf,
+        roofline = {"bound": "alu", "kernel": "prop_chain (the step's second, differential single-chain solve of all runs)", "achieved": tf,
                     "peak": peak_tf, "unit": "TFLOP/s", "frac": tf / peak_tf, "traffic": None,
                     "peak_source": "derived FP32 peak: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
     else:
-        bytes_per_site = {"prop_row_accumulate": 64.0, "prop_row_store": 32.0, "prop_col": 16.0}
+        # streaming passes, per site and contour step (FP32 complex z = g + i g'):
+        # radix-8 row pass = chain read 8 + write 8, factors 8, history store 8;
+        # radix-2 row pass accumulating the contour sums also reads the history
+        # and read-modify-writes the FP64 sums; column pass = chain read + write
+        radix8 = tiles_path == 1
+        bytes_per_site = {"prop_row_accumulate": 32.0 if radix8 else 64.0, "prop_row_store": 32.0, "prop_col": 16.0}
         for k, bps in bytes_per_site.items():
             gbs = bps * nsite / (kt[k] * 1e-3) / 1e9
             kernels[k] = {"ms": kt[k], "bytes_per_site": bps, "achieved_gbs": gbs, "frac": gbs / hbm}
         dom = "prop_row_accumulate"
-        roofline = {"bound": "hbm", "kernel": dom, "achieved": kernels[dom]["achieved_gbs"], "peak": hbm,
+        name = "prop_row8 (row pass of one contour step, radix-8 streaming)" if radix8 else dom
+        roofline = {"bound": "hbm", "kernel": name, "achieved": kernels[dom]["achieved_gbs"], "peak": hbm,
                     "unit": "GB/s", "frac": kernels[dom]["achieved_gbs"] / hbm, "traffic": None,
                     "peak_source": f"{peak_kind} hbm_gbs (copy)"}
 
