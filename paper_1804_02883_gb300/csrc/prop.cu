@@ -364,24 +364,19 @@ __global__ void __launch_bounds__(kThreads) prop_contour_stream(GroupGeom g, con
     const float2 *hz = hist + (size_t)run * (ns + 1) * n + i;
     // Nodes m and N_s - m are read together: z_m = (g_m, g'_m) and z_{N_s-m}
     // give the terms g_m g'_{N_s-m} (node m) and g_{N_s-m} g'_m (node N_s - m).
-    // Weight-1 terms of each block go through FP32 partial sums of at most 8
-    // terms; the half-weight end and junction nodes straight into FP64.
-    double ia = 0.0, ib = 0.0;
-    float pa = 0.f, pb = 0.f;
-    int ca = 0, cb = 0;
+    // Compensated (Kahan) FP32 sums per block (GB300's FP64 rate is a small
+    // fraction of FP32); the trapezoid weights 1 and 1/2 scale terms exactly.
+    float sa = 0.f, ca = 0.f, sb = 0.f, cb = 0.f;
+    auto kadd = [](float &s_, float &c_, float t) {
+        const float y = t - c_, u = s_ + y;
+        c_ = (u - s_) - y;
+        s_ = u;
+    };
     auto add = [&](int j, float t) {
         const float wa = (na == 0 || j > na) ? 0.f : ((j == 0 || j == na) ? 0.5f : 1.f);
         const float wb = (na == ns || j < na) ? 0.f : ((j == na || j == ns) ? 0.5f : 1.f);
-        if (wa == 1.f) {
-            pa += t;
-            if (++ca == 8) { ia += (double)pa; pa = 0.f; ca = 0; }
-        } else if (wb == 1.f) {
-            pb += t;
-            if (++cb == 8) { ib += (double)pb; pb = 0.f; cb = 0; }
-        } else {
-            ia += (double)wa * (double)t;
-            ib += (double)wb * (double)t;
-        }
+        if (wa != 0.f) kadd(sa, ca, wa * t);
+        if (wb != 0.f) kadd(sb, cb, wb * t);
     };
     const int half = ns / 2;
     constexpr int U = 4;
@@ -403,8 +398,7 @@ __global__ void __launch_bounds__(kThreads) prop_contour_stream(GroupGeom g, con
             if (ns - m != m) add(ns - m, zr[u].x * zl[u].y);
         }
     }
-    ia += (double)pa;
-    ib += (double)pb;
+    const double ia = (double)sa - (double)ca, ib = (double)sb - (double)cb;
     const double c = g.phi_p * g.ds / qp;
     double *ph = phi + (size_t)run * 3 * n;
     ph[i] = c * ia;

@@ -343,6 +343,20 @@ struct ContourK {
     int *err;
 };
 
+// Compensated (Kahan) FP32 sum: value() = sum minus the carried rounding
+// error, in FP64.  GB300's FP64 rate is a small fraction of FP32, so per-node
+// FP64 accumulation would bound these passes.
+struct KSum {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float t)
+    {
+        const float y = t - c, u = s + y;
+        c = (u - s) - y;
+        s = u;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 // Trapezoid weights over [0, s_{N_A}] and [s_{N_A}, 1] in units of ds.
 __device__ __forceinline__ void node_weights(int j, int na, int ns, float &wa, float &wb)
 {
@@ -442,9 +456,9 @@ __global__ void __launch_bounds__(kThreads) prop_contour(ContourK k)
                 rs[bk][c] = 1.f / (e[bk][c] * (1.f + q[bk][c]));
             }
     }
-    double ia0 = 0.0, ib0 = 0.0, ia1 = 0.0, ib1 = 0.0;
-    float pa0 = 0.f, pa1 = 0.f, gwa = 0.f, gwb = 0.f;
-    int cnt = 0;
+    // compensated (Kahan) FP32 sums per block and real site; the trapezoid
+    // weights 1 and 1/2 scale the terms exactly
+    KSum sa0, sb0, sa1, sb1;
     // nodes in chunks of U: all loads of a chunk are issued before its sums
     constexpr int U = DIFF ? 4 : 8;
     for (int m0 = 0; m0 <= ns; m0 += U) {
@@ -467,23 +481,13 @@ __global__ void __launch_bounds__(kThreads) prop_contour(ContourK k)
             if (m > ns) break;
             float wa, wb;
             node_weights(m, na, ns, wa, wb);
-            if (cnt > 0 && (wa != gwa || wb != gwb || cnt == 8)) {
-                ia0 += (double)gwa * pa0;
-                ib0 += (double)gwb * pa0;
-                ia1 += (double)gwa * pa1;
-                ib1 += (double)gwb * pa1;
-                pa0 = pa1 = 0.f;
-                cnt = 0;
-            }
-            gwa = wa;
-            gwb = wb;
-            ++cnt;
             // g at node m and g' at node N_s - m see the same field (block B from N_A on)
             const bool bk = m >= na;
             const float2 a = av[u], b = bv[u];
+            float t0, t1;
             if (!DIFF) {
-                pa0 += a.x * b.x * (bk ? r2[1][0] : r2[0][0]);
-                pa1 += a.y * b.y * (bk ? r2[1][1] : r2[0][1]);
+                t0 = a.x * b.x * (bk ? r2[1][0] : r2[0][0]);
+                t1 = a.y * b.y * (bk ? r2[1][1] : r2[0][1]);
             } else {
                 const float2 da = dav[u], db = dbv[u];
                 const float ri0 = bk ? ri[1][0] : ri[0][0], ri1 = bk ? ri[1][1] : ri[0][1];
@@ -493,15 +497,20 @@ __global__ void __launch_bounds__(kThreads) prop_contour(ContourK k)
                 const float ga0 = a.x * ri0, ga1 = a.y * ri1, gb0 = b.x * ri0, gb1 = b.y * ri1;
                 const float dga0 = (da.x - q0 * a.x) * rs0, dga1 = (da.y - q1 * a.y) * rs1;
                 const float dgb0 = (db.x - q0 * b.x) * rs0, dgb1 = (db.y - q1 * b.y) * rs1;
-                pa0 += ga0 * dgb0 + dga0 * gb0 + dga0 * dgb0;
-                pa1 += ga1 * dgb1 + dga1 * gb1 + dga1 * dgb1;
+                t0 = ga0 * dgb0 + dga0 * gb0 + dga0 * dgb0;
+                t1 = ga1 * dgb1 + dga1 * gb1 + dga1 * dgb1;
+            }
+            if (wa != 0.f) {
+                sa0.add(wa * t0);
+                sa1.add(wa * t1);
+            }
+            if (wb != 0.f) {
+                sb0.add(wb * t0);
+                sb1.add(wb * t1);
             }
         }
     }
-    ia0 += (double)gwa * pa0;
-    ib0 += (double)gwb * pa0;
-    ia1 += (double)gwa * pa1;
-    ib1 += (double)gwb * pa1;
+    const double ia0 = sa0.value(), ib0 = sb0.value(), ia1 = sa1.value(), ib1 = sb1.value();
     const double ds = k.g.ds, php = k.g.phi_p;
     double *pa = k.phi + (size_t)run * 3 * n, *pb = pa + n, *ps = pb + n;
     if (!DIFF) {
@@ -516,12 +525,13 @@ __global__ void __launch_bounds__(kThreads) prop_contour(ContourK k)
     } else {
         // Phi = Phi~ + (phi_p dI - Phi~ dQ) / (Q~ + dQ), the solvent with de
         const double *ta = k.phi_t + (size_t)run * 3 * n, *tb = ta + n, *tsol = tb + n;
-        pa[s0] = ta[s0] + (php * ds * ia0 - ta[s0] * sq) / qp;
-        pb[s0] = tb[s0] + (php * ds * ib0 - tb[s0] * sq) / qp;
-        pa[s1] = ta[s1] + (php * ds * ia1 - ta[s1] * sq) / qp;
-        pb[s1] = tb[s1] + (php * ds * ib1 - tb[s1] * sq) / qp;
-        ps[s0] = tsol[s0] + ((1.0 - php) * ps[s0] - tsol[s0] * ss) / qs;
-        ps[s1] = tsol[s1] + ((1.0 - php) * ps[s1] - tsol[s1] * ss) / qs;
+        const double rq = 1.0 / qp, rqs = 1.0 / qs, c = php * ds;
+        pa[s0] = ta[s0] + (c * ia0 - ta[s0] * sq) * rq;
+        pb[s0] = tb[s0] + (c * ib0 - tb[s0] * sq) * rq;
+        pa[s1] = ta[s1] + (c * ia1 - ta[s1] * sq) * rq;
+        pb[s1] = tb[s1] + (c * ib1 - tb[s1] * sq) * rq;
+        ps[s0] = tsol[s0] + ((1.0 - php) * ps[s0] - tsol[s0] * ss) * rqs;
+        ps[s1] = tsol[s1] + ((1.0 - php) * ps[s1] - tsol[s1] * ss) * rqs;
     }
 }
 
