@@ -39,6 +39,7 @@ struct EpdK {
     int rows, logc;
     double kunit_x, kunit_y;  // 2 pi / (n dx) per axis
     double mu_ref[3];         // mu_I at the homogeneous composition, omega = 0
+    double phibar[3];         // the homogeneous composition
 };
 
 // signed wavenumber of bin m; odd operators drop the Nyquist bin
@@ -56,6 +57,21 @@ __device__ __forceinline__ double2 mu_pair(const EpdK &k, const double *phi, con
         return make_double2(g.chi_ab * pb + g.chi_as * ps + inc - om[i] - k.mu_ref[0],
                             g.chi_ab * pa + g.chi_bs * ps + inc - om[n + i] - k.mu_ref[1]);
     return make_double2(g.chi_as * pa + g.chi_bs * pb + inc - om[2 * n + i] - k.mu_ref[2], 0.0);
+}
+
+// The same in FP32 from the FP64 deviations dPhi_J = Phi_J - Phi-bar_J:
+// mu_I - mu_I(Phi-bar, 0) = sum_{J != I} chi_IJ dPhi_J + kappa_H sum_J dPhi_J - omega_I
+// (linear in Phi), so FP32 rounding scales with the fluctuations.
+__device__ __forceinline__ float2 mu_pair_f(const EpdK &k, const double *phi, const double *om, long long n, long long i, int pair)
+{
+    const GroupGeom &g = k.g;
+    const float da = (float)(phi[i] - k.phibar[0]), db = (float)(phi[n + i] - k.phibar[1]),
+                dsv = (float)(phi[2 * n + i] - k.phibar[2]);
+    const float inc = (float)g.kappa_h * (da + db + dsv);
+    if (pair == 0)
+        return make_float2((float)g.chi_ab * db + (float)g.chi_as * dsv + inc - (float)om[i],
+                           (float)g.chi_ab * da + (float)g.chi_bs * dsv + inc - (float)om[n + i]);
+    return make_float2((float)g.chi_as * da + (float)g.chi_bs * db + inc - (float)om[2 * n + i], 0.f);
 }
 
 __device__ __forceinline__ double2 vel_at(const EpdK &k, size_t idx)
@@ -294,12 +310,12 @@ __global__ void __launch_bounds__(RowTile<LOGX>::T) epd_row8(EpdK k)
             const double *om = k.omega + (size_t)run * 3 * n;
             v = pair == 0 ? f2((float)om[s], (float)om[n + s]) : f2((float)om[2 * n + s], 0.f);
         } else if (MODE == ROW_LAP) {
-            const double2 mu = mu_pair(k, k.phi_t + (size_t)run * 3 * n, k.omega_t + (size_t)run * 3 * n, n, s, pair);
-            v = f2((float)mu.x, (float)mu.y);
+            v = mu_pair_f(k, k.phi_t + (size_t)run * 3 * n, k.omega_t + (size_t)run * 3 * n, n, s, pair);
         } else if (MODE == ROW_FWD_S) {
+            // S = sum_I dPhi_I^D / D_I from the FP64 differences, in FP32
             const double *p1 = k.phi + (size_t)run * 3 * n, *p0 = k.phi_t + (size_t)run * 3 * n;
-            const double sa = (p1[s] - p0[s]) + (p1[n + s] - p0[n + s]);
-            v = f2((float)(sa / g.d_p + (p1[2 * n + s] - p0[2 * n + s]) / g.d_s), 0.f);
+            const float da = (float)(p1[s] - p0[s]), db = (float)(p1[n + s] - p0[n + s]), dsv = (float)(p1[2 * n + s] - p0[2 * n + s]);
+            v = f2((da + db) * (float)(1.0 / g.d_p) + dsv * (float)(1.0 / g.d_s), 0.f);
         } else {
             v = cz[((size_t)run * 4 + 2) * n + s];
         }
@@ -358,8 +374,7 @@ __global__ void __launch_bounds__(ColTile<LOGY, CW>::T) epd_col8(EpdK k)
             const double *om = k.omega + (size_t)run * 3 * n;
             v = pair == 0 ? f2((float)om[s], (float)om[n + s]) : f2((float)om[2 * n + s], 0.f);
         } else if (MODE == COL_DIFFUSE) {
-            const double2 mu = mu_pair(k, k.phi_t + (size_t)run * 3 * n, k.omega_t + (size_t)run * 3 * n, n, s, pair);
-            v = f2((float)mu.x, (float)mu.y);
+            v = mu_pair_f(k, k.phi_t + (size_t)run * 3 * n, k.omega_t + (size_t)run * 3 * n, n, s, pair);
         } else {
             v = cz[((size_t)run * 4 + 2) * n + s];
         }
@@ -386,28 +401,29 @@ __global__ void __launch_bounds__(ColTile<LOGY, CW>::T) epd_col8(EpdK k)
             if (MODE == COL_FORCE) {
                 cz[((size_t)run * 4 + 2) * n + s] = h[j][r];
             } else if (MODE == COL_CONVECT) {
-                // omega~ = omega - dt v . grad omega, v = u_lat dx/dt
+                // omega~ = omega - dt v . grad omega, v = u_lat dx/dt (increment in FP32)
                 const float2 dyf = h[j][r], dxf = cz[((size_t)run * 4 + pair) * n + s];
-                const double2 u = vel_at(k, (size_t)run * n + s);
-                const double vx = u.x * g.vscale, vy = u.y * g.vscale;
+                const float2 u = reinterpret_cast<const float2 *>(k.vel)[(size_t)run * n + s];  // FP32 bulk
+                const float cv = (float)(g.vscale * g.dt), vx = u.x * cv, vy = u.y * cv;
                 const double *om = k.omega + (size_t)run * 3 * n;
                 double *ot = k.omega_dst + (size_t)run * 3 * n;
                 if (pair == 0) {
-                    ot[s] = om[s] - g.dt * (vx * (double)dxf.x + vy * (double)dyf.x);
-                    ot[n + s] = om[n + s] - g.dt * (vx * (double)dxf.y + vy * (double)dyf.y);
+                    ot[s] = om[s] - (double)(vx * dxf.x + vy * dyf.x);
+                    ot[n + s] = om[n + s] - (double)(vx * dxf.y + vy * dyf.y);
                 } else {
-                    ot[2 * n + s] = om[2 * n + s] - g.dt * (vx * (double)dxf.x + vy * (double)dyf.x);
+                    ot[2 * n + s] = om[2 * n + s] - (double)(vx * dxf.x + vy * dyf.x);
                 }
             } else {
-                // omega(t+dt) = omega~ - dt D_I Lap mu_I
+                // omega(t+dt) = omega~ - dt D_I Lap mu_I (increment in FP32)
                 const float2 dyf = h[j][r], lxf = cz[((size_t)run * 4 + pair) * n + s];
                 const double *ot = k.omega_t + (size_t)run * 3 * n;
                 double *om = k.omega_dst + (size_t)run * 3 * n;
                 if (pair == 0) {
-                    om[s] = ot[s] - g.dt * g.d_p * ((double)lxf.x + (double)dyf.x);
-                    om[n + s] = ot[n + s] - g.dt * g.d_p * ((double)lxf.y + (double)dyf.y);
+                    const float c = (float)(g.dt * g.d_p);
+                    om[s] = ot[s] - (double)(c * (lxf.x + dyf.x));
+                    om[n + s] = ot[n + s] - (double)(c * (lxf.y + dyf.y));
                 } else {
-                    om[2 * n + s] = ot[2 * n + s] - g.dt * g.d_s * ((double)lxf.x + (double)dyf.x);
+                    om[2 * n + s] = ot[2 * n + s] - (double)((float)(g.dt * g.d_s) * (lxf.x + dyf.x));
                 }
             }
         }
@@ -500,6 +516,9 @@ static EpdK make_k(Group &G)
     k.mu_ref[0] = G.g.chi_ab * pb + G.g.chi_as * ps + inc;
     k.mu_ref[1] = G.g.chi_ab * pa + G.g.chi_bs * ps + inc;
     k.mu_ref[2] = G.g.chi_as * pa + G.g.chi_bs * pb + inc;
+    k.phibar[0] = pa;
+    k.phibar[1] = pb;
+    k.phibar[2] = ps;
     return k;
 }
 
