@@ -72,14 +72,20 @@ def sites_per_step(runs) -> float:
     return float(sum(r.nx * r.ny for r in runs))
 
 
-def launches_per_step(runs) -> int:
-    # per batch of equal runs: aux convection 2, two solves of (2 N_s + 3),
-    # diffusion 2, force 3, LB 1
-    seen = {}
-    for r in runs:
-        key = (r.nx, r.ny, r.ns, r.precision)
-        seen[key] = r.ns
-    return sum(4 * ns + 14 for ns in seen.values())
+def launches_per_step(runs, h) -> int:
+    """Kernel launches of one captured step, per group of equal runs: aux
+    convection 2, diffusion 2, force 3, LB 1, plus the two solves: cluster
+    path 4 each (factors, chain, Q partials, contour sums), streaming paths
+    2 N_s + 3 each (factors, start, N_s column and row passes, contour or
+    finalize)."""
+    first = {}
+    for k, r in enumerate(runs):
+        first.setdefault((r.nx, r.ny, r.ns, r.precision), k)
+    total = 0
+    for (nx, ny, ns, prec), k in first.items():
+        solve = 4 if h.tiles(k)["path"] == 2 else 2 * ns + 3
+        total += 8 + 2 * solve
+    return total
 
 
 class Clocks:
@@ -326,6 +332,7 @@ def main():
     # kernel durations inside the timed steps (event nodes in the step graph)
     nsite = sites_per_step(runs)
     tiles_path = h.tiles(0)["path"]
+    n_launches = launches_per_step(runs, h)
     kt = {k: statistics.mean(d[k] for d in kern) for k in kern[0]}
     hbm, peak_kind = peaks()
     kernels = {}
@@ -439,7 +446,7 @@ def main():
             "surrogate": sur,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": launches_per_step(runs) * args.steps,
+            "gpu_launches": n_launches * args.steps,
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)
