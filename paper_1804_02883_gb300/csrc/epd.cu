@@ -303,7 +303,9 @@ __global__ void __launch_bounds__(RowTile<LOGX>::T) epd_row8(EpdK k)
     const long long base = (long long)blockIdx.x * P;
     float2 *cz = reinterpret_cast<float2 *>(k.cz);
     copy_tables(tab, k.tab8x, RT::TAB, tid, T);
-    for (int i = tid; i < P; i += T) {
+#pragma unroll
+    for (int u = 0; u < P / T; ++u) {
+        const int i = tid + u * T;
         const long long s = base + i;
         float2 v;
         if (MODE == ROW_GRAD) {
@@ -324,7 +326,11 @@ __global__ void __launch_bounds__(RowTile<LOGX>::T) epd_row8(EpdK k)
     __syncthreads();
     if (MODE == ROW_FWD_S) {
         forward<LOGX, T, RL, P>(buf, tab, tid);
-        for (int i = tid; i < P; i += T) cz[((size_t)run * 4 + 2) * n + base + i] = buf[RL::at(i / NX, i % NX)];
+#pragma unroll
+        for (int u = 0; u < P / T; ++u) {
+            const int i = tid + u * T;
+            cz[((size_t)run * 4 + 2) * n + base + i] = buf[RL::at(i / NX, i % NX)];
+        }
         return;
     }
     const float unit = (float)k.kunit_x, inv_n = 1.f / (float)NX;
@@ -367,7 +373,9 @@ __global__ void __launch_bounds__(ColTile<LOGY, CW>::T) epd_col8(EpdK k)
     const long long n = g.n;
     float2 *cz = reinterpret_cast<float2 *>(k.cz);
     copy_tables(tab, k.tab8y, CT::TAB, tid, T);
-    for (int i = tid; i < P; i += T) {
+#pragma unroll
+    for (int u = 0; u < P / T; ++u) {
+        const int i = tid + u * T;
         const long long s = (long long)(i / C) * nx + x0 + (i % C);
         float2 v;
         if (MODE == COL_CONVECT) {

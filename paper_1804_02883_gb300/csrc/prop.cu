@@ -283,7 +283,11 @@ __global__ void __launch_bounds__(ColTile<LOGY, CW>::T) prop_col8(Stream8K k)
     float2 *buf = reinterpret_cast<float2 *>(smem_raw);
     const int nx = k.g.nx, run = blockIdx.y, x0 = blockIdx.x * C, tid = threadIdx.x;
     float2 *data = k.chain + (size_t)run * k.g.n;
-    for (int i = tid; i < P; i += T) buf[i] = data[(size_t)(i / C) * nx + x0 + (i % C)];
+#pragma unroll
+    for (int u = 0; u < P / T; ++u) {
+        const int i = tid + u * T;
+        buf[i] = data[(size_t)(i / C) * nx + x0 + (i % C)];
+    }
     __syncthreads();
     // twiddle tables and Fourier factors straight from global memory (L1):
     // shared memory holds only the tile, so more tiles are in flight per SM
@@ -313,7 +317,11 @@ __global__ void __launch_bounds__(RowTile<LOGX>::T) prop_row8(Stream8K k, int m)
     const long long n = k.g.n, base = (long long)blockIdx.x * P;
     const int ns = k.g.ns, na = k.g.na;
     float2 *data = k.chain + (size_t)run * n + base;
-    for (int i = tid; i < P; i += T) buf[RL::at(i / NX, i % NX)] = data[i];
+#pragma unroll
+    for (int u = 0; u < P / T; ++u) {
+        const int i = tid + u * T;
+        buf[RL::at(i / NX, i % NX)] = data[i];
+    }
     __syncthreads();
     transform_pair<LOGX, T, RL, P>(buf, k.twx, ScaleBins{k.kx}, tid);
     constexpr int RLOG_L = inv_rlog(LOGX, npasses(LOGX) - 1), RR = 1 << RLOG_L, PER_L = NX / RR, NB_L = P / RR / T;
