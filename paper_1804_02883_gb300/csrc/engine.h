@@ -74,6 +74,7 @@ struct Group {
     double2 *twx_d, *twy_d;        // FP64 twiddles for the EPD/force passes
     float2 *twx_full, *twy_full;   // FP32 twiddles exp(-2 pi i j/N), j < N (cluster solve); may be null
     float2 *tab8x = nullptr, *tab8y = nullptr;  // radix-8 pass tables (fft8.cuh layout); null with twx_full
+    float2 *tab16x = nullptr, *tab16y = nullptr;  // radix-16 plan tables of 256-point axes (else null)
     int *err;                      // device error word (shared by the handle)
 };
 

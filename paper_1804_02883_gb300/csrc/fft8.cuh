@@ -6,31 +6,41 @@
 // (RowLayout: sequence-major; ColLayout: point-major).  Passes are in place:
 // every thread loads its points of the pass, the block synchronises, every
 // thread writes its results.  Radix 8, with one radix-2/4 pass where log2 N is
-// not a multiple of 3; twiddles from per-pass tables (fill_tables) laid out
-// [row][p] so that consecutive threads read consecutive entries.
+// not a multiple of 3 (or radix 16 where a kernel asks for it); twiddles from
+// per-pass tables (build_tables_host) laid out [row][p] so that consecutive
+// threads read consecutive entries.
 #pragma once
 
 #include <cuda_runtime.h>
 
 namespace epdlb {
 
-// Radix plan: passes of radix 8, the last forward pass takes the remainder.
-__host__ __device__ constexpr int npasses(int logn) { return (logn + 2) / 3; }
-__host__ __device__ constexpr int fwd_rlog(int logn, int i) { return i < npasses(logn) - 1 ? 3 : logn - 3 * (npasses(logn) - 1); }
-__host__ __device__ constexpr int fwd_slog(int logn, int i) { return i == 0 ? 0 : fwd_slog(logn, i - 1) + fwd_rlog(logn, i - 1); }
-__host__ __device__ constexpr int inv_rlog(int logn, int i) { return fwd_rlog(logn, npasses(logn) - 1 - i); }
-__host__ __device__ constexpr int inv_slog(int logn, int i) { return i == 0 ? 0 : inv_slog(logn, i - 1) + inv_rlog(logn, i - 1); }
+// Radix plan: passes of radix 2^mr (8 by default, 16 where a kernel picks
+// mr = 4), the last forward pass takes the remainder.
+__host__ __device__ constexpr int npasses(int logn, int mr = 3) { return (logn + mr - 1) / mr; }
+__host__ __device__ constexpr int fwd_rlog(int logn, int i, int mr = 3)
+{
+    return i < npasses(logn, mr) - 1 ? mr : logn - mr * (npasses(logn, mr) - 1);
+}
+__host__ __device__ constexpr int fwd_slog(int logn, int i, int mr = 3) { return i == 0 ? 0 : fwd_slog(logn, i - 1, mr) + fwd_rlog(logn, i - 1, mr); }
+__host__ __device__ constexpr int inv_rlog(int logn, int i, int mr = 3) { return fwd_rlog(logn, npasses(logn, mr) - 1 - i, mr); }
+__host__ __device__ constexpr int inv_slog(int logn, int i, int mr = 3) { return i == 0 ? 0 : inv_slog(logn, i - 1, mr) + inv_rlog(logn, i - 1, mr); }
 // Twiddle tables: one per pass that needs twiddles (forward passes
 // 0..np-2, inverse passes 0..np-2), rows x M entries, M = N / (S R): rows
-// k = 1, 2, 4 for radix 8 (the others are products), k = 1..R-1 otherwise.
-__host__ __device__ constexpr int tab_rows(int rlog) { return rlog == 3 ? 3 : (1 << rlog) - 1; }
+// k = 1, 2, 4 for radix 8 and k = 1, 2, 4, 8 for radix 16 (the others are
+// products), k = 1..R-1 otherwise.
+__host__ __device__ constexpr int tab_rows(int rlog) { return rlog >= 3 ? rlog : (1 << rlog) - 1; }
 __host__ __device__ constexpr int tab_len(int logn, int slog, int rlog) { return tab_rows(rlog) * ((1 << logn) >> (slog + rlog)); }
-__host__ __device__ constexpr int fwd_off(int logn, int i) { return i == 0 ? 0 : fwd_off(logn, i - 1) + tab_len(logn, fwd_slog(logn, i - 1), fwd_rlog(logn, i - 1)); }
-__host__ __device__ constexpr int inv_off(int logn, int i)
+__host__ __device__ constexpr int fwd_off(int logn, int i, int mr = 3)
 {
-    return i == 0 ? fwd_off(logn, npasses(logn) - 1) : inv_off(logn, i - 1) + tab_len(logn, inv_slog(logn, i - 1), inv_rlog(logn, i - 1));
+    return i == 0 ? 0 : fwd_off(logn, i - 1, mr) + tab_len(logn, fwd_slog(logn, i - 1, mr), fwd_rlog(logn, i - 1, mr));
 }
-__host__ __device__ constexpr int tabs_total(int logn) { return inv_off(logn, npasses(logn) - 1); }
+__host__ __device__ constexpr int inv_off(int logn, int i, int mr = 3)
+{
+    return i == 0 ? fwd_off(logn, npasses(logn, mr) - 1, mr)
+                  : inv_off(logn, i - 1, mr) + tab_len(logn, inv_slog(logn, i - 1, mr), inv_rlog(logn, i - 1, mr));
+}
+__host__ __device__ constexpr int tabs_total(int logn, int mr = 3) { return inv_off(logn, npasses(logn, mr) - 1, mr); }
 
 __device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
 __device__ __forceinline__ float2 fadd(float2 a, float2 b) { return f2(a.x + b.x, a.y + b.y); }
@@ -83,6 +93,42 @@ template <bool INV> struct Dft<3, INV> {
     }
 };
 
+// 16 points as 4 x 4: DFT4 over n1 of x[4 n1 + n2], twiddles W16^(n2 k1),
+// DFT4 over n2; output X[k1 + 4 k2].
+template <bool INV> struct Dft<4, INV> {
+    static __device__ __forceinline__ void run(float2 *x)
+    {
+        const float c = 0.92387953251128675613f, s = 0.38268343236508977173f, h = 0.70710678118654752440f;
+        float2 y[4][4];
+#pragma unroll
+        for (int n2 = 0; n2 < 4; ++n2) {
+            float2 v[4] = {x[n2], x[4 + n2], x[8 + n2], x[12 + n2]};
+            Dft<2, INV>::run(v);
+#pragma unroll
+            for (int k1 = 0; k1 < 4; ++k1) y[n2][k1] = v[k1];
+        }
+        // W16^m = (cos(2 pi m / 16), -sin(2 pi m / 16)), conjugated for the inverse
+        const float sg = INV ? 1.f : -1.f;
+        const float2 w1 = f2(c, sg * s), w2 = f2(h, sg * h), w3 = f2(s, sg * c), w6 = f2(-h, sg * h), w9 = f2(-c, -sg * s);
+        y[1][1] = fmul(y[1][1], w1);
+        y[1][2] = fmul(y[1][2], w2);
+        y[1][3] = fmul(y[1][3], w3);
+        y[2][1] = fmul(y[2][1], w2);
+        y[2][2] = rot90<INV>(y[2][2]);  // W16^4 = -i (forward)
+        y[2][3] = fmul(y[2][3], w6);
+        y[3][1] = fmul(y[3][1], w3);
+        y[3][2] = fmul(y[3][2], w6);
+        y[3][3] = fmul(y[3][3], w9);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            float2 v[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
+            Dft<2, INV>::run(v);
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) x[k1 + 4 * k2] = v[k2];
+        }
+    }
+};
+
 // Shared-memory layouts.  Row layout: sequence b (a packed row), point x.
 // Rows of 128 points or more are unpadded with the low four bits of x
 // XOR-ed by the next four (x ^ ((x >> 4) & 15)): every access pattern of the
@@ -107,8 +153,9 @@ template <int LOGN, int W> struct ColLayout {
 };
 
 // Twiddles w[k] = w1^k, k = 1..R-1, of one butterfly from a pass table laid
-// out [row][p] (row length M): radix 8 reads w1, w2, w4 and forms the rest by
-// products (at most two roundings more than a table entry).
+// out [row][p] (row length M): radix 8 reads w1, w2, w4 and radix 16 also w8,
+// and forms the rest by products (at most three roundings more than a table
+// entry).
 template <int R>
 __device__ __forceinline__ void twiddles(float2 (&w)[R], const float2 *tab, int M, int p)
 {
@@ -120,6 +167,17 @@ __device__ __forceinline__ void twiddles(float2 (&w)[R], const float2 *tab, int 
         w[5] = fmul(w[1], w[4]);
         w[6] = fmul(w[2], w[4]);
         w[7] = fmul(w[3], w[4]);
+    } else if constexpr (R == 16) {
+        w[1] = tab[p];
+        w[2] = tab[M + p];
+        w[4] = tab[2 * M + p];
+        w[8] = tab[3 * M + p];
+        w[3] = fmul(w[1], w[2]);
+        w[5] = fmul(w[1], w[4]);
+        w[6] = fmul(w[2], w[4]);
+        w[7] = fmul(w[3], w[4]);
+#pragma unroll
+        for (int k = 9; k < 16; ++k) w[k] = fmul(w[k - 8], w[8]);
     } else {
 #pragma unroll
         for (int k = 1; k < R; ++k) w[k] = tab[(k - 1) * M + p];
@@ -216,38 +274,38 @@ __device__ __forceinline__ void inverse_first(float2 *buf, const float2 *tab_inv
     __syncthreads();
 }
 
-template <int LOGN, int I, int T, class L, int P>
+template <int LOGN, int I, int T, class L, int P, int MR = 3>
 struct FwdPasses {
     static __device__ __forceinline__ void run(float2 *buf, const float2 *tabs, int tid)
     {
-        if constexpr (I < npasses(LOGN) - 1) {
-            constexpr int RLOG = fwd_rlog(LOGN, I);
-            pass<LOGN, fwd_slog(LOGN, I), RLOG, false, P / (1 << RLOG) / T, T, L>(buf, tabs + fwd_off(LOGN, I), tid);
-            FwdPasses<LOGN, I + 1, T, L, P>::run(buf, tabs, tid);
+        if constexpr (I < npasses(LOGN, MR) - 1) {
+            constexpr int RLOG = fwd_rlog(LOGN, I, MR);
+            pass<LOGN, fwd_slog(LOGN, I, MR), RLOG, false, P / (1 << RLOG) / T, T, L>(buf, tabs + fwd_off(LOGN, I, MR), tid);
+            FwdPasses<LOGN, I + 1, T, L, P, MR>::run(buf, tabs, tid);
         }
     }
 };
-template <int LOGN, int I, int T, class L, int P>
+template <int LOGN, int I, int T, class L, int P, int MR = 3>
 struct InvPasses {
     static __device__ __forceinline__ void run(float2 *buf, const float2 *tabs, int tid)
     {
-        if constexpr (I < npasses(LOGN) - 1) {
-            constexpr int RLOG = inv_rlog(LOGN, I);
-            pass<LOGN, inv_slog(LOGN, I), RLOG, true, P / (1 << RLOG) / T, T, L>(buf, tabs + inv_off(LOGN, I), tid);
-            InvPasses<LOGN, I + 1, T, L, P>::run(buf, tabs, tid);
+        if constexpr (I < npasses(LOGN, MR) - 1) {
+            constexpr int RLOG = inv_rlog(LOGN, I, MR);
+            pass<LOGN, inv_slog(LOGN, I, MR), RLOG, true, P / (1 << RLOG) / T, T, L>(buf, tabs + inv_off(LOGN, I, MR), tid);
+            InvPasses<LOGN, I + 1, T, L, P, MR>::run(buf, tabs, tid);
         }
     }
 };
 
 // Full transform pair (forward, spectral operator, inverse) up to the
 // inverse's last pass, whose loads and DFT are left to the caller.
-template <int LOGN, int T, class L, int P, class Op>
+template <int LOGN, int T, class L, int P, class Op, int MR = 3>
 __device__ __forceinline__ void transform_pair(float2 *buf, const float2 *tabs, const Op &op, int tid)
 {
-    FwdPasses<LOGN, 0, T, L, P>::run(buf, tabs, tid);
-    constexpr int RM = fwd_rlog(LOGN, npasses(LOGN) - 1);
-    middle<LOGN, RM, P / (1 << RM) / T, T, L>(buf, tabs + inv_off(LOGN, 0), op, tid);
-    InvPasses<LOGN, 1, T, L, P>::run(buf, tabs, tid);
+    FwdPasses<LOGN, 0, T, L, P, MR>::run(buf, tabs, tid);
+    constexpr int RM = fwd_rlog(LOGN, npasses(LOGN, MR) - 1, MR);
+    middle<LOGN, RM, P / (1 << RM) / T, T, L>(buf, tabs + inv_off(LOGN, 0, MR), op, tid);
+    InvPasses<LOGN, 1, T, L, P, MR>::run(buf, tabs, tid);
 }
 
 // Forward transform alone, result in natural order in buf.
@@ -279,11 +337,11 @@ struct ScaleBins {
     }
 };
 
-template <int LOGN, int NB, int T, class L>
-__device__ __forceinline__ void last_inverse(const float2 *buf, float2 (&x)[NB][1 << inv_rlog(LOGN, npasses(LOGN) - 1)],
+template <int LOGN, int NB, int T, class L, int MR = 3>
+__device__ __forceinline__ void last_inverse(const float2 *buf, float2 (&x)[NB][1 << inv_rlog(LOGN, npasses(LOGN, MR) - 1, MR)],
                                              int (&bb)[NB], int (&tt)[NB], int tid)
 {
-    constexpr int RLOG = inv_rlog(LOGN, npasses(LOGN) - 1), R = 1 << RLOG, PER = (1 << LOGN) / R;
+    constexpr int RLOG = inv_rlog(LOGN, npasses(LOGN, MR) - 1, MR), R = 1 << RLOG, PER = (1 << LOGN) / R;
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
         L::template split<PER>(tid + j * T, bb[j], tt[j]);
@@ -293,49 +351,29 @@ __device__ __forceinline__ void last_inverse(const float2 *buf, float2 (&x)[NB][
     }
 }
 
-// Fill the twiddle tables of every pass of a length-2^LOGN transform.
-template <int LOGN, int I>
-__device__ __forceinline__ void fill_tables(float2 *tabs, const float2 *tw, int tid, int nthreads)
-{
-    constexpr int NP = npasses(LOGN);
-    if constexpr (I < 2 * (NP - 1)) {
-        constexpr bool INVP = I >= NP - 1;
-        constexpr int PI = INVP ? I - (NP - 1) : I;
-        constexpr int SLOG = INVP ? inv_slog(LOGN, PI) : fwd_slog(LOGN, PI);
-        constexpr int RLOG = INVP ? inv_rlog(LOGN, PI) : fwd_rlog(LOGN, PI);
-        constexpr int OFF = INVP ? inv_off(LOGN, PI) : fwd_off(LOGN, PI);
-        constexpr int M = (1 << LOGN) >> (SLOG + RLOG), LEN = tab_rows(RLOG) * M;
-        for (int e = tid; e < LEN; e += nthreads) {
-            const int row = e / M, p = e % M;
-            const int k = RLOG == 3 ? (1 << row) : row + 1;
-            tabs[OFF + e] = tw[(p << SLOG) * k];
-        }
-        fill_tables<LOGN, I + 1>(tabs, tw, tid, nthreads);
-    }
-}
-
 // Copy of prebuilt pass tables (built on the host with the same layout as
-// fill_tables) into shared memory: coalesced, no scattered gathers.
+// the layout above) into shared memory: coalesced, no scattered gathers.
 __device__ __forceinline__ void copy_tables(float2 *dst, const float2 *src, int len, int tid, int nthreads)
 {
     for (int e = tid; e < len; e += nthreads) dst[e] = src[e];
 }
 
 // Host: the pass tables of a length-2^logn transform from the full twiddles
-// tw[j] = exp(-2 pi i j / N) (interleaved re, im), in fill_tables' layout.
-inline void build_tables_host(int logn, const float *tw, float *out)
+// tw[j] = exp(-2 pi i j / N) (interleaved re, im), for the plan of radix
+// 2^mr.
+inline void build_tables_host(int logn, const float *tw, float *out, int mr = 3)
 {
-    const int np = npasses(logn);
+    const int np = npasses(logn, mr);
     for (int I = 0; I < 2 * (np - 1); ++I) {
         const bool invp = I >= np - 1;
         const int pi = invp ? I - (np - 1) : I;
-        const int slog = invp ? inv_slog(logn, pi) : fwd_slog(logn, pi);
-        const int rlog = invp ? inv_rlog(logn, pi) : fwd_rlog(logn, pi);
-        const int off = invp ? inv_off(logn, pi) : fwd_off(logn, pi);
+        const int slog = invp ? inv_slog(logn, pi, mr) : fwd_slog(logn, pi, mr);
+        const int rlog = invp ? inv_rlog(logn, pi, mr) : fwd_rlog(logn, pi, mr);
+        const int off = invp ? inv_off(logn, pi, mr) : fwd_off(logn, pi, mr);
         const int M = (1 << logn) >> (slog + rlog), len = tab_rows(rlog) * M;
         for (int e = 0; e < len; ++e) {
             const int row = e / M, p = e % M;
-            const int k = rlog == 3 ? (1 << row) : row + 1;
+            const int k = rlog >= 3 ? (1 << row) : row + 1;
             const int j = (p << slog) * k;
             out[2 * (off + e)] = tw[2 * j];
             out[2 * (off + e) + 1] = tw[2 * j + 1];

@@ -73,7 +73,11 @@ struct ClusterGeom {
     static constexpr int P = R2 * NX;  // complex points per CTA in either packing
     static constexpr int PITCH = RowLayout<LOGX>::PITCH;
     static constexpr int HN = NY / 2 * NX;  // stored complex points per chain and node
-    static constexpr int TABX = tabs_total(LOGX), TABY = tabs_total(LOGY);
+    // radix 16 for 256-point transforms when every thread gets whole
+    // 16-point butterflies (2 smem round trips fewer than 8 x 8 x 4)
+    static constexpr int MRX = (LOGX == 8 && P % (16 * T) == 0) ? 4 : 3;
+    static constexpr int MRY = (LOGY == 8 && P % (16 * T) == 0) ? 4 : 3;
+    static constexpr int TABX = tabs_total(LOGX, MRX), TABY = tabs_total(LOGY, MRY);
     static constexpr size_t SMEM = (size_t)(R2 * PITCH + P + TABX + TABY) * sizeof(float2) + (NX + NY) * sizeof(float);
     // the differential solve adds one float per real site: rho (2 + rho)
     static constexpr size_t SMEM_DIFF = SMEM + (size_t)2 * P * sizeof(float);
@@ -199,7 +203,7 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
     cl.sync();  // every CTA's barriers are initialised, every row buffer holds a_0
 
     // epilogue geometry: the inverse row transform's last pass
-    constexpr int RLOG_L = inv_rlog(LOGX, npasses(LOGX) - 1), RR = 1 << RLOG_L, PER_L = NX / RR;
+    constexpr int RLOG_L = inv_rlog(LOGX, npasses(LOGX, G::MRX) - 1, G::MRX), RR = 1 << RLOG_L, PER_L = NX / RR;
     constexpr int NB_L = P / RR / T;
     // per-site factors of this thread's epilogue sites, reloaded when the
     // block (A or B) changes: E^2 (plain) or E'^2 (DIFF) in registers,
@@ -244,12 +248,12 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
                     asm volatile("prefetch.global.L1 [%0];" ::"l"(href + (size_t)m * HN + b * NX + t + r * PER_L));
             }
         }
-        transform_pair<LOGY, T, CL, P>(colbuf, taby, ScaleBins{ky}, tid);
+        transform_pair<LOGY, T, CL, P, ScaleBins, G::MRY>(colbuf, taby, ScaleBins{ky}, tid);
         {
-            constexpr int RLOG_C = inv_rlog(LOGY, npasses(LOGY) - 1), NB_C = P / (1 << RLOG_C) / T;
+            constexpr int RLOG_C = inv_rlog(LOGY, npasses(LOGY, G::MRY) - 1, G::MRY), NB_C = P / (1 << RLOG_C) / T;
             float2 x[NB_C][1 << RLOG_C];
             int bb[NB_C], tt[NB_C];
-            last_inverse<LOGY, NB_C, T, CL>(colbuf, x, bb, tt, tid);
+            last_inverse<LOGY, NB_C, T, CL, G::MRY>(colbuf, x, bb, tt, tid);
 #pragma unroll
             for (int j = 0; j < NB_C; ++j)
 #pragma unroll
@@ -272,10 +276,10 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
         cluster_arrive();  // my column buffer is read out
         mbar_wait(bar_row, par, failed);
         if (tid == 0 && m < ns) mbar_expect(bar_row, XBYTES);
-        transform_pair<LOGX, T, RL, P>(rowbuf, tabx, ScaleBins{kx}, tid);
+        transform_pair<LOGX, T, RL, P, ScaleBins, G::MRX>(rowbuf, tabx, ScaleBins{kx}, tid);
         float2 h[NB_L][RR];
         int bb[NB_L], tt[NB_L];
-        last_inverse<LOGX, NB_L, T, RL>(rowbuf, h, bb, tt, tid);
+        last_inverse<LOGX, NB_L, T, RL, G::MRX>(rowbuf, h, bb, tt, tid);
 
         const int bm = blk_b(m) ? 1 : 0;
         if (bm != cur_b) {
@@ -544,6 +548,7 @@ struct ClusterShape {
     const void *fn;       // plain and reference solves
     const void *fn_diff;  // differential solve
     size_t smem, smem_diff;
+    int mrx, mry;         // radix plans of the row and column transforms (log2 of the largest radix)
 };
 
 template <int LOGX, int LOGY, int C, int T, int MINB = 1024 / T>
@@ -551,7 +556,8 @@ static ClusterShape shape_of()
 {
     return ClusterShape{LOGX, LOGY, C, T, (const void *)prop_chain<LOGX, LOGY, C, T, MINB, false>,
                         (const void *)prop_chain<LOGX, LOGY, C, T, MINB, true>, ClusterGeom<LOGX, LOGY, C, T>::SMEM,
-                        ClusterGeom<LOGX, LOGY, C, T>::SMEM_DIFF};
+                        ClusterGeom<LOGX, LOGY, C, T>::SMEM_DIFF, ClusterGeom<LOGX, LOGY, C, T>::MRX,
+                        ClusterGeom<LOGX, LOGY, C, T>::MRY};
 }
 
 // Instantiated grids (log2 nx, log2 ny).  Tiles of 4096 points take 256
@@ -634,8 +640,9 @@ cudaError_t launch_cluster_solve(Group &G, cudaStream_t s, bool diff, int nprep_
     k.efac = reinterpret_cast<const float2 *>(G.efac);
     k.rho = reinterpret_cast<const float2 *>(G.rho);
     k.err = G.err;
-    k.twx = reinterpret_cast<const float2 *>(G.tab8x);
-    k.twy = reinterpret_cast<const float2 *>(G.tab8y);
+    k.twx = sh->mrx == 4 ? G.tab16x : G.tab8x;
+    k.twy = sh->mry == 4 ? G.tab16y : G.tab8y;
+    if (!k.twx || !k.twy) return cudaErrorInvalidValue;
     k.kx = reinterpret_cast<const float *>(G.kx);
     k.ky = reinterpret_cast<const float *>(G.ky);
     cudaLaunchConfig_t cfg = {};
