@@ -77,8 +77,8 @@ size_t carve_group(Group &G, char *base, size_t off)
     G.twy_full = (float2 *)take((size_t)G.g.ny * sizeof(float2));
     G.tab8x = (float2 *)take((size_t)tabs_total(G.g.logx) * sizeof(float2));
     G.tab8y = (float2 *)take((size_t)tabs_total(G.g.logy) * sizeof(float2));
-    G.tab16x = G.g.logx == 8 ? (float2 *)take((size_t)tabs_total(8, 4) * sizeof(float2)) : nullptr;
-    G.tab16y = G.g.logy == 8 ? (float2 *)take((size_t)tabs_total(8, 4) * sizeof(float2)) : nullptr;
+    G.tab16x = best_mr(G.g.logx) == 4 ? (float2 *)take((size_t)tabs_total(G.g.logx, 4) * sizeof(float2)) : nullptr;
+    G.tab16y = best_mr(G.g.logy) == 4 ? (float2 *)take((size_t)tabs_total(G.g.logy, 4) * sizeof(float2)) : nullptr;
     // cluster solve (MIXED_FP32): stored states of both chains, and the
     // differential second solve's buffers
     G.hc = G.hd = G.rho = nullptr;
@@ -245,15 +245,14 @@ static cudaError_t upload_tables_t(Group &G, cudaStream_t s)
         build_tables_host(G.g.logy, fy.data(), ty.data());
         if ((e = cudaMemcpyAsync(G.tab8x, tx.data(), tx.size() * sizeof(float), cudaMemcpyHostToDevice, s))) return e;
         if ((e = cudaMemcpyAsync(G.tab8y, ty.data(), ty.size() * sizeof(float), cudaMemcpyHostToDevice, s))) return e;
-        std::vector<float> t16(2 * (size_t)tabs_total(8, 4));
+        std::vector<float> t16x(G.tab16x ? 2 * (size_t)tabs_total(G.g.logx, 4) : 0), t16y(G.tab16y ? 2 * (size_t)tabs_total(G.g.logy, 4) : 0);
         if (G.tab16x) {
-            build_tables_host(8, fx.data(), t16.data(), 4);
-            if ((e = cudaMemcpyAsync(G.tab16x, t16.data(), t16.size() * sizeof(float), cudaMemcpyHostToDevice, s))) return e;
-            if ((e = cudaStreamSynchronize(s))) return e;  // t16 is reused below
+            build_tables_host(G.g.logx, fx.data(), t16x.data(), 4);
+            if ((e = cudaMemcpyAsync(G.tab16x, t16x.data(), t16x.size() * sizeof(float), cudaMemcpyHostToDevice, s))) return e;
         }
         if (G.tab16y) {
-            build_tables_host(8, fy.data(), t16.data(), 4);
-            if ((e = cudaMemcpyAsync(G.tab16y, t16.data(), t16.size() * sizeof(float), cudaMemcpyHostToDevice, s))) return e;
+            build_tables_host(G.g.logy, fy.data(), t16y.data(), 4);
+            if ((e = cudaMemcpyAsync(G.tab16y, t16y.data(), t16y.size() * sizeof(float), cudaMemcpyHostToDevice, s))) return e;
         }
         if ((e = cudaStreamSynchronize(s))) return e;
     }

@@ -35,7 +35,8 @@ struct EpdK {
     void *force;
     int bulk_double;
     const void *twx, *twy;  // twiddles of the transform type
-    const float2 *tab8x, *tab8y;  // radix-8 pass tables (FP32 radix-8 kernels)
+    const float2 *tab8x, *tab8y;  // pass tables of each axis' best radix plan (FP32 radix-8/16 kernels)
+    const float2 *tab16y, *tab8y_r8;  // column tables of the radix-16 and radix-8 plans (tile-dependent)
     int rows, logc;
     double kunit_x, kunit_y;  // 2 pi / (n dx) per axis
     double mu_ref[3];         // mu_I at the homogeneous composition, omega = 0
@@ -325,7 +326,7 @@ __global__ void __launch_bounds__(RowTile<LOGX>::T) epd_row8(EpdK k)
     }
     __syncthreads();
     if (MODE == ROW_FWD_S) {
-        forward<LOGX, T, RL, P>(buf, tab, tid);
+        forward<LOGX, T, RL, P, RT::MR>(buf, tab, tid);
 #pragma unroll
         for (int u = 0; u < P / T; ++u) {
             const int i = tid + u * T;
@@ -335,15 +336,15 @@ __global__ void __launch_bounds__(RowTile<LOGX>::T) epd_row8(EpdK k)
     }
     const float unit = (float)k.kunit_x, inv_n = 1.f / (float)NX;
     if (MODE == ROW_GRAD)
-        transform_pair<LOGX, T, RL, P>(buf, tab, OpGrad{NX, unit, inv_n}, tid);
+        transform_pair<LOGX, T, RL, P, OpGrad, RT::MR>(buf, tab, OpGrad{NX, unit, inv_n}, tid);
     else if (MODE == ROW_LAP)
-        transform_pair<LOGX, T, RL, P>(buf, tab, OpLap{NX, unit, inv_n}, tid);
+        transform_pair<LOGX, T, RL, P, OpLap, RT::MR>(buf, tab, OpLap{NX, unit, inv_n}, tid);
     else
-        inverse_open<LOGX, T, RL, P>(buf, tab, tid);
-    constexpr int RLOG_L = inv_rlog(LOGX, npasses(LOGX) - 1), RR = 1 << RLOG_L, PER_L = NX / RR, NB_L = P / RR / T;
+        inverse_open<LOGX, T, RL, P, RT::MR>(buf, tab, tid);
+    constexpr int RLOG_L = inv_rlog(LOGX, npasses(LOGX, RT::MR) - 1, RT::MR), RR = 1 << RLOG_L, PER_L = NX / RR, NB_L = P / RR / T;
     float2 h[NB_L][RR];
     int bb[NB_L], tt[NB_L];
-    last_inverse<LOGX, NB_L, T, RL>(buf, h, bb, tt, tid);
+    last_inverse<LOGX, NB_L, T, RL, RT::MR>(buf, h, bb, tt, tid);
 #pragma unroll
     for (int j = 0; j < NB_L; ++j)
 #pragma unroll
@@ -372,7 +373,7 @@ __global__ void __launch_bounds__(ColTile<LOGY, CW>::T) epd_col8(EpdK k)
     const int nx = g.nx, run = blockIdx.y, pair = blockIdx.z, x0 = blockIdx.x * C, tid = threadIdx.x;
     const long long n = g.n;
     float2 *cz = reinterpret_cast<float2 *>(k.cz);
-    copy_tables(tab, k.tab8y, CT::TAB, tid, T);
+    copy_tables(tab, CT::MR == 4 ? k.tab16y : k.tab8y_r8, CT::TAB, tid, T);
 #pragma unroll
     for (int u = 0; u < P / T; ++u) {
         const int i = tid + u * T;
@@ -391,16 +392,16 @@ __global__ void __launch_bounds__(ColTile<LOGY, CW>::T) epd_col8(EpdK k)
     __syncthreads();
     const float uy = (float)k.kunit_y, inv_n = 1.f / (float)NY;
     if (MODE == COL_CONVECT)
-        transform_pair<LOGY, T, CL, P>(buf, tab, OpGrad{NY, uy, inv_n}, tid);
+        transform_pair<LOGY, T, CL, P, OpGrad, CT::MR>(buf, tab, OpGrad{NY, uy, inv_n}, tid);
     else if (MODE == COL_DIFFUSE)
-        transform_pair<LOGY, T, CL, P>(buf, tab, OpLap{NY, uy, inv_n}, tid);
+        transform_pair<LOGY, T, CL, P, OpLap, CT::MR>(buf, tab, OpLap{NY, uy, inv_n}, tid);
     else
-        transform_pair<LOGY, T, CL, P>(
+        transform_pair<LOGY, T, CL, P, OpForce, CT::MR>(
             buf, tab, OpForce{nx, NY, x0, (float)k.kunit_x, uy, (float)(g.inv_beta_v * g.fstar / (g.dt * (double)NY))}, tid);
-    constexpr int RLOG_L = inv_rlog(LOGY, npasses(LOGY) - 1), RR = 1 << RLOG_L, PER_L = NY / RR, NB_L = P / RR / T;
+    constexpr int RLOG_L = inv_rlog(LOGY, npasses(LOGY, CT::MR) - 1, CT::MR), RR = 1 << RLOG_L, PER_L = NY / RR, NB_L = P / RR / T;
     float2 h[NB_L][RR];
     int bb[NB_L], tt[NB_L];
-    last_inverse<LOGY, NB_L, T, CL>(buf, h, bb, tt, tid);
+    last_inverse<LOGY, NB_L, T, CL, CT::MR>(buf, h, bb, tt, tid);
 #pragma unroll
     for (int j = 0; j < NB_L; ++j)
 #pragma unroll
@@ -510,8 +511,11 @@ static EpdK make_k(Group &G)
     // FP32 transforms use the bulk (FP32) twiddle tables, FP64 ones the FP64 tables
     k.twx = k.bulk_double ? (const void *)G.twx_d : G.twx;
     k.twy = k.bulk_double ? (const void *)G.twy_d : G.twy;
-    k.tab8x = G.tab8x;
-    k.tab8y = G.tab8y;
+    // tables of each axis' radix plan (RowTile / ColTile pick best_mr)
+    k.tab8x = best_mr(G.g.logx) == 4 ? G.tab16x : G.tab8x;
+    k.tab8y = best_mr(G.g.logy) == 4 ? G.tab16y : G.tab8y;
+    k.tab16y = G.tab16y;
+    k.tab8y_r8 = G.tab8y;
     k.rows = G.sh.rows_epd;
     k.logc = ilog2(G.sh.cols_epd);
     const double pi = 3.14159265358979323846;

@@ -41,6 +41,9 @@ __host__ __device__ constexpr int inv_off(int logn, int i, int mr = 3)
                   : inv_off(logn, i - 1, mr) + tab_len(logn, inv_slog(logn, i - 1, mr), inv_rlog(logn, i - 1, mr));
 }
 __host__ __device__ constexpr int tabs_total(int logn, int mr = 3) { return inv_off(logn, npasses(logn, mr) - 1, mr); }
+// radix 16 where it takes fewer passes than radix 8 (128, 256, 1024, 2048
+// points), else radix 8
+__host__ __device__ constexpr int best_mr(int logn) { return npasses(logn, 4) < npasses(logn, 3) ? 4 : 3; }
 
 __device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
 __device__ __forceinline__ float2 fadd(float2 a, float2 b) { return f2(a.x + b.x, a.y + b.y); }
@@ -309,22 +312,22 @@ __device__ __forceinline__ void transform_pair(float2 *buf, const float2 *tabs, 
 }
 
 // Forward transform alone, result in natural order in buf.
-template <int LOGN, int T, class L, int P>
+template <int LOGN, int T, class L, int P, int MR = 3>
 __device__ __forceinline__ void forward(float2 *buf, const float2 *tabs, int tid)
 {
-    FwdPasses<LOGN, 0, T, L, P>::run(buf, tabs, tid);
-    constexpr int I = npasses(LOGN) - 1, RM = fwd_rlog(LOGN, I);
-    pass<LOGN, fwd_slog(LOGN, I), RM, false, P / (1 << RM) / T, T, L>(buf, tabs, tid);  // M = 1: no twiddles
+    FwdPasses<LOGN, 0, T, L, P, MR>::run(buf, tabs, tid);
+    constexpr int I = npasses(LOGN, MR) - 1, RM = fwd_rlog(LOGN, I, MR);
+    pass<LOGN, fwd_slog(LOGN, I, MR), RM, false, P / (1 << RM) / T, T, L>(buf, tabs, tid);  // M = 1: no twiddles
 }
 
 // Inverse transform of a natural-order spectrum up to its last pass (left to
 // the caller, as in transform_pair).
-template <int LOGN, int T, class L, int P>
+template <int LOGN, int T, class L, int P, int MR = 3>
 __device__ __forceinline__ void inverse_open(float2 *buf, const float2 *tabs, int tid)
 {
-    constexpr int RM = fwd_rlog(LOGN, npasses(LOGN) - 1);
-    inverse_first<LOGN, RM, P / (1 << RM) / T, T, L>(buf, tabs + inv_off(LOGN, 0), tid);
-    InvPasses<LOGN, 1, T, L, P>::run(buf, tabs, tid);
+    constexpr int RM = fwd_rlog(LOGN, npasses(LOGN, MR) - 1, MR);
+    inverse_first<LOGN, RM, P / (1 << RM) / T, T, L>(buf, tabs + inv_off(LOGN, 0, MR), tid);
+    InvPasses<LOGN, 1, T, L, P, MR>::run(buf, tabs, tid);
 }
 
 // Multiplication by a real per-bin factor table (the Fourier factor of Eq. (8)).
@@ -385,14 +388,20 @@ inline void build_tables_host(int logn, const float *tw, float *out, int mr = 3)
 // row tile holds 2048 points (max(1, 2048 / nx) whole rows), a column tile CW
 // whole columns (by default 16, 8 from 1024 rows on; the autotuner picks 4, 8
 // or 16 per grid).
+// Radix plan MR = best_mr(N) (rows; columns where it fits); one butterfly of
+// the largest radix per thread.
 template <int LOGX> struct RowTile {
-    static constexpr int NX = 1 << LOGX, ROWS = NX >= 2048 ? 1 : 2048 / NX, P = ROWS * NX, T = P / 8;
-    static constexpr int TAB = tabs_total(LOGX);
+    static constexpr int MR = best_mr(LOGX);
+    static constexpr int NX = 1 << LOGX, ROWS = NX >= 2048 ? 1 : 2048 / NX, P = ROWS * NX, T = P >> MR;
+    static constexpr int TAB = tabs_total(LOGX, MR);
     static constexpr size_t SMEM = (size_t)(ROWS * RowLayout<LOGX>::PITCH + TAB) * sizeof(float2);
 };
 template <int LOGY, int CW = (LOGY >= 10 ? 8 : 16)> struct ColTile {
-    static constexpr int NY = 1 << LOGY, C = CW, P = C * NY, T = P / 8 > 512 ? 512 : P / 8;
-    static constexpr int TAB = tabs_total(LOGY);
+    static constexpr int NY = 1 << LOGY, C = CW, P = C * NY;
+    // radix 16 only where one 16-point butterfly per thread fits in 512 threads
+    static constexpr int MR = (best_mr(LOGY) == 4 && (P >> 4) <= 512) ? 4 : 3;
+    static constexpr int T = (P >> MR) > 512 ? 512 : (P >> MR);
+    static constexpr int TAB = tabs_total(LOGY, MR);
     static constexpr size_t SMEM = (size_t)(P + TAB) * sizeof(float2);
 };
 // column tile widths the autotuner chooses from (0: the default above)

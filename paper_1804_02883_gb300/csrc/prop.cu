@@ -257,7 +257,8 @@ struct Stream8K {
     float2 *hist;         // [run][N_s + 1][n]
     const float2 *efac;   // [run][n]
     double *part;
-    const float2 *twx, *twy;  // radix-8 pass tables (fft8.cuh layout)
+    const float2 *twx, *twy;  // pass tables of each axis' best radix plan (fft8.cuh layout)
+    const float2 *twy8, *twy16;  // column tables of the radix-8 and radix-16 plans (tile-dependent)
     const float *kx, *ky;
 };
 
@@ -291,11 +292,11 @@ __global__ void __launch_bounds__(ColTile<LOGY, CW>::T) prop_col8(Stream8K k)
     __syncthreads();
     // twiddle tables and Fourier factors straight from global memory (L1):
     // shared memory holds only the tile, so more tiles are in flight per SM
-    transform_pair<LOGY, T, CL, P>(buf, k.twy, ScaleBins{k.ky}, tid);
-    constexpr int RLOG_L = inv_rlog(LOGY, npasses(LOGY) - 1), RR = 1 << RLOG_L, PER_L = NY / RR, NB_L = P / RR / T;
+    transform_pair<LOGY, T, CL, P, ScaleBins, CT::MR>(buf, CT::MR == 4 ? k.twy16 : k.twy8, ScaleBins{k.ky}, tid);
+    constexpr int RLOG_L = inv_rlog(LOGY, npasses(LOGY, CT::MR) - 1, CT::MR), RR = 1 << RLOG_L, PER_L = NY / RR, NB_L = P / RR / T;
     float2 h[NB_L][RR];
     int bb[NB_L], tt[NB_L];
-    last_inverse<LOGY, NB_L, T, CL>(buf, h, bb, tt, tid);
+    last_inverse<LOGY, NB_L, T, CL, CT::MR>(buf, h, bb, tt, tid);
 #pragma unroll
     for (int j = 0; j < NB_L; ++j)
 #pragma unroll
@@ -323,11 +324,11 @@ __global__ void __launch_bounds__(RowTile<LOGX>::T) prop_row8(Stream8K k, int m)
         buf[RL::at(i / NX, i % NX)] = data[i];
     }
     __syncthreads();
-    transform_pair<LOGX, T, RL, P>(buf, k.twx, ScaleBins{k.kx}, tid);
-    constexpr int RLOG_L = inv_rlog(LOGX, npasses(LOGX) - 1), RR = 1 << RLOG_L, PER_L = NX / RR, NB_L = P / RR / T;
+    transform_pair<LOGX, T, RL, P, ScaleBins, RT::MR>(buf, k.twx, ScaleBins{k.kx}, tid);
+    constexpr int RLOG_L = inv_rlog(LOGX, npasses(LOGX, RT::MR) - 1, RT::MR), RR = 1 << RLOG_L, PER_L = NX / RR, NB_L = P / RR / T;
     float2 h[NB_L][RR];
     int bb[NB_L], tt[NB_L];
-    last_inverse<LOGX, NB_L, T, RL>(buf, h, bb, tt, tid);
+    last_inverse<LOGX, NB_L, T, RL, RT::MR>(buf, h, bb, tt, tid);
     const float2 *efac = k.efac + (size_t)run * n + base;
     float2 *hist = k.hist + ((size_t)run * (ns + 1) + m) * n + base;
     float qsum = 0.f;
@@ -542,8 +543,10 @@ cudaError_t tune_stream_tiles(Group &G, cudaStream_t s)
     k8.hist = reinterpret_cast<float2 *>(G.hist);
     k8.efac = reinterpret_cast<const float2 *>(G.efac);
     k8.part = G.part;
-    k8.twx = G.tab8x;
-    k8.twy = G.tab8y;
+    k8.twx = best_mr(G.g.logx) == 4 ? G.tab16x : G.tab8x;
+    k8.twy = best_mr(G.g.logy) == 4 ? G.tab16y : G.tab8y;
+    k8.twy8 = G.tab8y;
+    k8.twy16 = G.tab16y;
     k8.kx = reinterpret_cast<const float *>(G.kx);
     k8.ky = reinterpret_cast<const float *>(G.ky);
     cudaError_t e = cudaMemsetAsync(G.chain, 0, (size_t)G.g.nruns * G.g.n * sizeof(float2), s);
@@ -603,8 +606,10 @@ static cudaError_t solve_t(Group &G, const double *omega, double *phi, double *q
         k8.hist = reinterpret_cast<float2 *>(G.hist);
         k8.efac = reinterpret_cast<const float2 *>(G.efac);
         k8.part = G.part;
-        k8.twx = G.tab8x;
-        k8.twy = G.tab8y;
+        k8.twx = best_mr(g.logx) == 4 ? G.tab16x : G.tab8x;
+        k8.twy = best_mr(g.logy) == 4 ? G.tab16y : G.tab8y;
+        k8.twy8 = G.tab8y;
+        k8.twy16 = G.tab16y;
         k8.kx = reinterpret_cast<const float *>(G.kx);
         k8.ky = reinterpret_cast<const float *>(G.ky);
         prop_start8<<<dim3(pg, g.nruns), kThreads, 0, s>>>(k8);

@@ -73,10 +73,10 @@ struct ClusterGeom {
     static constexpr int P = R2 * NX;  // complex points per CTA in either packing
     static constexpr int PITCH = RowLayout<LOGX>::PITCH;
     static constexpr int HN = NY / 2 * NX;  // stored complex points per chain and node
-    // radix 16 for 256-point transforms when every thread gets whole
-    // 16-point butterflies (2 smem round trips fewer than 8 x 8 x 4)
-    static constexpr int MRX = (LOGX == 8 && P % (16 * T) == 0) ? 4 : 3;
-    static constexpr int MRY = (LOGY == 8 && P % (16 * T) == 0) ? 4 : 3;
+    // radix 16 where it saves passes (fft8.cuh best_mr) and every thread gets
+    // whole 16-point butterflies
+    static constexpr int MRX = (best_mr(LOGX) == 4 && P % (16 * T) == 0) ? 4 : 3;
+    static constexpr int MRY = (best_mr(LOGY) == 4 && P % (16 * T) == 0) ? 4 : 3;
     static constexpr int TABX = tabs_total(LOGX, MRX), TABY = tabs_total(LOGY, MRY);
     static constexpr size_t SMEM = (size_t)(R2 * PITCH + P + TABX + TABY) * sizeof(float2) + (NX + NY) * sizeof(float);
     // the differential solve adds one float per real site: rho (2 + rho)
