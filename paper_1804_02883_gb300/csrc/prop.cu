@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(kThreads) prop_contour_stream(GroupGeom g, con
         if (wb != 0.f) kadd(sb, cb, wb * t);
     };
     const int half = ns / 2;
-    constexpr int U = 4;
+    constexpr int U = 8;
     for (int m0 = 0; m0 <= half; m0 += U) {
         float2 zl[U], zr[U];
 #pragma unroll
