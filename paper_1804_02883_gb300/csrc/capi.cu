@@ -81,12 +81,13 @@ size_t carve_group(Group &G, char *base, size_t off)
     G.tab16y = best_mr(G.g.logy) == 4 ? (float2 *)take((size_t)tabs_total(G.g.logy, 4) * sizeof(float2)) : nullptr;
     // cluster solve (MIXED_FP32): stored states of both chains, and the
     // differential second solve's buffers
-    G.hc = G.hd = G.rho = nullptr;
+    G.hc = G.hd = G.rho = G.c2p = nullptr;
     if (G.prec == EPD_LB_MIXED_FP32 && cluster_shape_exists(G.g.logx, G.g.logy)) {
         const size_t hs = R * cluster_state_floats2(G.g.nx, G.g.ny, G.g.ns) * sizeof(float2);
         G.hc = take(hs);
         G.hd = take(hs);
         G.rho = take(R * n * sizeof(float2));
+        G.c2p = take(R * n * sizeof(float2));
     }
     G.diff = false;  // set once the cluster solve is known to launch
     return align_up(off);
@@ -125,6 +126,7 @@ static Group run_view(const Group &G, int r)
         V.hc = (char *)V.hc + (size_t)r * hs;
         V.hd = (char *)V.hd + (size_t)r * hs;
         V.rho = (char *)V.rho + (size_t)r * n * sizeof(float2);
+        V.c2p = (char *)V.c2p + (size_t)r * n * sizeof(float2);
     }
     return V;
 }

@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(kThreads) prop_finalize(GroupGeom g, int nrow_
 // rounding of FP32 relative to the change itself.  The solvent change de goes
 // to the S slot of phi, its block sums to the S partials.
 __global__ void __launch_bounds__(kThreads) prop_prep_delta(GroupGeom g, const double *omega, const double *omega_t,
-                                                            float2 *rho, double *phi_out, double *part)
+                                                            float2 *rho, float *c2p, double *phi_out, double *part)
 {
     __shared__ double red[32];
     const int run = blockIdx.y;
@@ -230,7 +230,16 @@ __global__ void __launch_bounds__(kThreads) prop_prep_delta(GroupGeom g, const d
     float acc = 0.f;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const float da = (float)(wa[i] - ta[i]), db = (float)(wb[i] - tb[i]);
-        rho[(size_t)run * n + i] = make_float2(expm1f(c * da), expm1f(c * db));
+        const float qa = expm1f(c * da), qb = expm1f(c * db);
+        rho[(size_t)run * n + i] = make_float2(qa, qb);
+        if (c2p) {
+            // rho (2 + rho) per block in the packed-row layout of the cluster
+            // solve: site (y, x) -> packed row y / 2, component y & 1
+            const long long y = i / g.nx, x = i % g.nx, hn = n / 2;
+            const size_t o = (size_t)((y >> 1) * g.nx + x) * 2 + (y & 1);
+            c2p[((size_t)run * 2 + 0) * hn * 2 + o] = qa * (2.f + qa);
+            c2p[((size_t)run * 2 + 1) * hn * 2 + o] = qb * (2.f + qb);
+        }
         // e~_S exactly as the first solve formed it
         const float es = expf(-(float)ts[i]);
         const float de = es * expm1f(-(float)(ws[i] - ts[i]));
@@ -647,8 +656,8 @@ cudaError_t launch_solve_delta(Group &G, cudaStream_t s, const SolveProbe *probe
     if (!G.diff || !G.hd) return cudaErrorInvalidValue;
     const GroupGeom &g = G.g;
     const int pg = grid_for(g.n);
-    prop_prep_delta<<<dim3(pg, g.nruns), kThreads, 0, s>>>(g, G.omega, G.omega_t, reinterpret_cast<float2 *>(G.rho), G.phi,
-                                                          G.part);
+    prop_prep_delta<<<dim3(pg, g.nruns), kThreads, 0, s>>>(g, G.omega, G.omega_t, reinterpret_cast<float2 *>(G.rho),
+                                                          reinterpret_cast<float *>(G.c2p), G.phi, G.part);
     return launch_cluster_solve(G, s, true, pg, G.phi, G.q, probe);
 }
 

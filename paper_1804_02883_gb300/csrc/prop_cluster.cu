@@ -62,6 +62,7 @@ struct PropCK {
     const float2 *href;   // reference states a~_m (DIFF)
     const float2 *efac;   // (E_A, E_B) [run][n]
     const float2 *rho;    // (rho_A, rho_B) [run][n] (DIFF)
+    const float2 *c2p;    // rho (2 + rho) of blocks A, B in the packed-row layout [run][2][NY/2][NX] (DIFF)
     int *err;             // bit 2: an exchange wait gave up
     const float2 *twx, *twy;  // radix-8 pass tables (fft8.cuh layout)
     const float *kx, *ky;     // exp(-R_G^2 k^2 ds) / N
@@ -79,8 +80,7 @@ struct ClusterGeom {
     static constexpr int MRY = (best_mr(LOGY) == 4 && P % (16 * T) == 0) ? 4 : 3;
     static constexpr int TABX = tabs_total(LOGX, MRX), TABY = tabs_total(LOGY, MRY);
     static constexpr size_t SMEM = (size_t)(R2 * PITCH + P + TABX + TABY) * sizeof(float2) + (NX + NY) * sizeof(float);
-    // the differential solve adds one float per real site: rho (2 + rho)
-    static constexpr size_t SMEM_DIFF = SMEM + (size_t)2 * P * sizeof(float);
+    static constexpr size_t SMEM_DIFF = SMEM;
 };
 
 // Distributed-shared-memory pushes: st.async of 8 bytes into a CTA of the
@@ -151,7 +151,6 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
     float2 *taby = tabx + G::TABX;
     float *kx = reinterpret_cast<float *>(taby + G::TABY);
     float *ky = kx + NX;
-    float *c2s = ky + NY;  // DIFF: rho (2 + rho) of the epilogue sites, [(j RR + r) 2 + cp][T]
     cg::cluster_group cl = cg::this_cluster();
     const int crank = (int)cl.block_rank();
     const int cidx = blockIdx.x / C, run = cidx >> 1, chain = cidx & 1;
@@ -165,6 +164,8 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
     for (int i = tid; i < NY; i += T) ky[i] = k.ky[i];
     const float2 *efac = k.efac + (size_t)run * n;
     const float2 *rho = DIFF ? k.rho + (size_t)run * n : nullptr;
+    // rho (2 + rho) of this CTA's packed rows, block A then B (L2-resident, read per step)
+    const float2 *c2p = DIFF ? k.c2p + (size_t)run * 2 * HN + (size_t)krow0 * NX : nullptr;
     // this CTA's block of the stored states of node m: hout + m * HN
     float2 *hout = k.hout + (size_t)(run * 2 + chain) * (ns + 1) * HN + (size_t)krow0 * NX;
     const float2 *href = DIFF ? k.href + (size_t)(run * 2 + chain) * (ns + 1) * HN + (size_t)krow0 * NX : nullptr;
@@ -206,8 +207,7 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
     constexpr int RLOG_L = inv_rlog(LOGX, npasses(LOGX, G::MRX) - 1, G::MRX), RR = 1 << RLOG_L, PER_L = NX / RR;
     constexpr int NB_L = P / RR / T;
     // per-site factors of this thread's epilogue sites, reloaded when the
-    // block (A or B) changes: E^2 (plain) or E'^2 (DIFF) in registers,
-    // rho (2 + rho) (DIFF) in shared memory
+    // block (A or B) changes: E^2 (plain) or E'^2 (DIFF) in registers
     float c1[NB_L][RR][2];
     int cur_b = -1;
     int failed = 0;
@@ -299,7 +299,6 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
                             const float2 rf = rho[site0 + cp * NX];
                             const float q = bm ? rf.y : rf.x, ep = e * (1.f + q);
                             c1[j][r][cp] = ep * ep;
-                            c2s[((j * RR + r) * 2 + cp) * T + tid] = q * (2.f + q);
                         }
                     }
                 }
@@ -314,8 +313,8 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
                     a = f2(c1[j][r][0] * h[j][r].x, c1[j][r][1] * h[j][r].y);
                 } else {
                     const float2 ar = href[(size_t)m * HN + bb[j] * NX + x];  // a~_m
-                    const float q0 = c2s[((j * RR + r) * 2) * T + tid], q1 = c2s[((j * RR + r) * 2 + 1) * T + tid];
-                    a = f2(c1[j][r][0] * h[j][r].x + q0 * ar.x, c1[j][r][1] * h[j][r].y + q1 * ar.y);
+                    const float2 cq = c2p[(size_t)bm * HN + bb[j] * NX + x];    // rho (2 + rho)
+                    a = f2(c1[j][r][0] * h[j][r].x + cq.x * ar.x, c1[j][r][1] * h[j][r].y + cq.y * ar.y);
                 }
                 rowbuf[RL::at(bb[j], x)] = a;
             }
@@ -639,6 +638,7 @@ cudaError_t launch_cluster_solve(Group &G, cudaStream_t s, bool diff, int nprep_
     k.href = reinterpret_cast<const float2 *>(G.hc);
     k.efac = reinterpret_cast<const float2 *>(G.efac);
     k.rho = reinterpret_cast<const float2 *>(G.rho);
+    k.c2p = reinterpret_cast<const float2 *>(G.c2p);
     k.err = G.err;
     k.twx = sh->mrx == 4 ? G.tab16x : G.tab8x;
     k.twy = sh->mry == 4 ? G.tab16y : G.tab8y;
