@@ -119,6 +119,9 @@ def lib():
             "or_init": (None, [P, _DP, _DP, _DP]),
             "or_step": (None, [P, _DP, _DP, _DP, _DP, _DP, _DP, _DP]),
             "or_sigma": (ctypes.c_double, [P, _DP]),
+            "or_convect_phi": (None, [P, _DP, _DP, _DP]),
+            "or_invert": (ctypes.c_int, [P, _DP, _DP, _DP, _DP, ctypes.c_int, ctypes.c_double, _DP]),
+            "or_step_exact": (None, [P, _DP, _DP, _DP, _DP, _DP, _DP, ctypes.c_int, ctypes.c_double, _DP]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -301,6 +304,43 @@ def step(p: Params, st: State, nsteps: int = 1, phi_tilde_out: bool = False):
         lib().or_step(ctypes.byref(p.c()), _d(st.omega), _d(st.pop), _d(st.vel), _d(st.phi),
                       _d(st.q), _d(st.force), None if pt is None else _d(pt))
     return pt
+
+
+# --- the exact step: convection of Phi and the CG inversion (App. C) ------
+
+def convect_phi(p: Params, phi, vel_lat) -> np.ndarray:
+    """Phi~ = Phi - dt div(v Phi) (3, ny, nx), v = u_lat dx/dt."""
+    phi = _f64(phi).reshape(3, p.ny, p.nx)
+    vel = _f64(vel_lat).reshape(2, p.ny, p.nx)
+    out = np.empty_like(phi)
+    lib().or_convect_phi(ctypes.byref(p.c()), _d(phi), _d(vel), _d(out))
+    return out
+
+
+def invert(p: Params, phi_target, omega0, max_iter: int = 50, tol: float = 1e-8):
+    """Fletcher-Reeves inversion Phi(omega) = phi_target from omega0.
+    Returns (omega, Phi(omega), (Q_P, Q_S), iterations, residual before, after)."""
+    target = _f64(phi_target).reshape(3, p.ny, p.nx)
+    omega = _f64(omega0).reshape(3, p.ny, p.nx).copy()
+    phi = np.empty_like(omega)
+    q = np.empty(2)
+    stats = np.empty(2)
+    it = lib().or_invert(ctypes.byref(p.c()), _d(target), _d(omega), _d(phi), _d(q), int(max_iter), float(tol),
+                         _d(stats))
+    return omega, phi, q, it, stats[0], stats[1]
+
+
+def step_exact(p: Params, st: State, nsteps: int = 1, max_iter: int = 50, tol: float = 1e-8):
+    """Advance by nsteps exact steps (the inversion of App. C).  st.phi must
+    hold Phi(t) on entry.  Returns the per-step (iterations, residual before,
+    residual after) as an array (nsteps, 3)."""
+    out = np.empty((nsteps, 3))
+    for k in range(nsteps):
+        stats = np.empty(3)
+        lib().or_step_exact(ctypes.byref(p.c()), _d(st.omega), _d(st.pop), _d(st.vel), _d(st.phi), _d(st.q),
+                            _d(st.force), int(max_iter), float(tol), _d(stats))
+        out[k] = stats
+    return out
 
 
 def sigma(p: Params, phi) -> float:

@@ -624,6 +624,170 @@ void or_step(const or_params *p, double *omega, double *pop, double *vel,
     free(ftot);
 }
 
+/* ------------------------------------------------------------------------ */
+/* The exact step of App. C: convection of the composition fields and the    */
+/* iterative inversion omega = Phi^{-1}(Phi~) by Fletcher-Reeves CG.          */
+/* ------------------------------------------------------------------------ */
+
+/* Convection part of Eq. (2): Phi~_I = Phi_I - dt div(v Phi_I), forward Euler,
+ * the divergence of the flux taken spectrally (READING as for every other
+ * spatial derivative: continuum wavenumbers, Nyquist bin of a first
+ * derivative dropped), v = u_lat dx/dt in physical units. */
+void or_convect_phi(const or_params *p, const double *phi, const double *vel_lat, double *phi_tilde)
+{
+    size_t n = (size_t)p->nx * p->ny;
+    double vscale = p->dx / p->dt;
+    double *fx = (double *)malloc(sizeof(double) * n);
+    double *fy = (double *)malloc(sizeof(double) * n);
+    double *dfx = (double *)malloc(sizeof(double) * n);
+    double *dfy = (double *)malloc(sizeof(double) * n);
+    for (int s = 0; s < 3; s++) {
+        const double *f = phi + (size_t)s * n;
+        for (size_t i = 0; i < n; i++) {
+            fx[i] = vel_lat[i] * vscale * f[i];
+            fy[i] = vel_lat[n + i] * vscale * f[i];
+        }
+        or_spectral_op(p, fx, dfx, 0, 1);
+        or_spectral_op(p, fy, dfy, 1, 1);
+        for (size_t i = 0; i < n; i++) phi_tilde[(size_t)s * n + i] = f[i] - p->dt * (dfx[i] + dfy[i]);
+    }
+    free(fx);
+    free(fy);
+    free(dfx);
+    free(dfy);
+}
+
+static double dot3(const double *a, const double *b, size_t m)
+{
+    double s = 0.0;
+    for (size_t i = 0; i < m; i++) s += a[i] * b[i];
+    return s;
+}
+
+/* Inversion of the density map (Sec. 2, the integrator paragraph; App. C,
+ * items 2 and 3): find omega with Phi(omega) = Phi~ (target, 3n).
+ *
+ * Eqs. (9)-(11) give Phi_{A,B} = -(n phi_p / N) d ln Q_P / d omega_{A,B} and
+ * Phi_S = -n (1 - phi_p) d ln Q_S / d omega_S (for the polymer up to how the
+ * contour quadrature splits the junction node), so the mismatch
+ * g = Phi~ - Phi(omega) is n times the gradient of the convex function
+ *   G(omega) = <sum_I omega_I Phi~_I> + (phi_p / N) ln Q_P + (1 - phi_p) ln Q_S
+ * (<.> the spatial mean), whose Hessian is the two-body correlator P_IJ of
+ * Eq. (4) over n.  Fletcher-Reeves nonlinear CG on G (READING: the paper names the
+ * method only):
+ *   d_0 = -g_0;
+ *   line search along d_k by one secant step on dG/dalpha = -(g . d)/n from
+ *     alpha = 0 and the trial step alpha_t (1 at k = 0, then the previous
+ *     step), falling back to alpha_t when the secant slope is not positive;
+ *   d_{k+1} = -g_{k+1} + beta d_k, beta = |g_{k+1}|^2 / |g_k|^2, restarted
+ *     as -g_{k+1} when it is not a descent direction (g . d >= 0).
+ * Convergence (App. C, item 2): sqrt(sum_I <(Phi~_I - Phi_I)^2>) < tol
+ * (N_tr = 1e-8 in the paper).  tol <= 0 runs exactly max_iter iterations.
+ *
+ * omega: in the starting guess, out the result.  phi (3n), q[2]: out
+ * Phi(omega) and (Q_P, Q_S).  stats[0] = residual at the start,
+ * stats[1] = residual at the end.  Returns the iterations taken. */
+int or_invert(const or_params *p, const double *phi_target, double *omega, double *phi, double *q,
+              int max_iter, double tol, double *stats)
+{
+    size_t n = (size_t)p->nx * p->ny, m = 3 * n;
+    double *g = (double *)malloc(sizeof(double) * m);
+    double *d = (double *)malloc(sizeof(double) * m);
+    double *wtr = (double *)malloc(sizeof(double) * m);
+    double *ptr = (double *)malloc(sizeof(double) * m);
+    double qt[2];
+
+    or_solve(p, omega, phi, q);
+    for (size_t i = 0; i < m; i++) g[i] = phi_target[i] - phi[i];
+    double gg = dot3(g, g, m);
+    double res = sqrt(gg / (double)n);
+    stats[0] = res;
+    for (size_t i = 0; i < m; i++) d[i] = -g[i];
+    double h0 = -gg, alpha_t = 1.0;
+    int it = 0;
+    while (it < max_iter && (tol <= 0.0 || res >= tol)) {
+        /* slope of G at the trial step */
+        for (size_t i = 0; i < m; i++) wtr[i] = omega[i] + alpha_t * d[i];
+        or_solve(p, wtr, ptr, qt);
+        double ht = 0.0;
+        for (size_t i = 0; i < m; i++) ht += (phi_target[i] - ptr[i]) * d[i];
+        double den = h0 - ht;
+        double alpha = den < 0.0 ? alpha_t * h0 / den : alpha_t;
+        /* the step and the new mismatch */
+        for (size_t i = 0; i < m; i++) omega[i] += alpha * d[i];
+        or_solve(p, omega, phi, q);
+        for (size_t i = 0; i < m; i++) g[i] = phi_target[i] - phi[i];
+        double gg_new = dot3(g, g, m), gd = dot3(g, d, m);
+        double beta = gg > 0.0 ? gg_new / gg : 0.0;
+        h0 = -gg_new + beta * gd;
+        if (h0 >= 0.0) {
+            for (size_t i = 0; i < m; i++) d[i] = -g[i];
+            h0 = -gg_new;
+        } else {
+            for (size_t i = 0; i < m; i++) d[i] = -g[i] + beta * d[i];
+        }
+        gg = gg_new;
+        res = sqrt(gg / (double)n);
+        alpha_t = alpha;
+        it++;
+    }
+    stats[1] = res;
+    free(g);
+    free(d);
+    free(wtr);
+    free(ptr);
+    return it;
+}
+
+/* The exact step of App. C: like or_step, but the intermediate fields are
+ * the inversion of the convected densities,
+ *   Phi~ = Phi(t) - dt div(v Phi(t)),  omega~ = Phi^{-1}(Phi~)
+ * (CG started from the auxiliary convection of omega), and the diffusion
+ * step and the force use Phi(omega~).  phi: in Phi(t), out Phi(t + dt).
+ * stats[0..2] = iterations, residual before and after the inversion.
+ * max_iter = 0 gives or_step exactly. */
+void or_step_exact(const or_params *p, double *omega, double *pop, double *vel, double *phi, double *q,
+                   double *force, int max_iter, double tol, double *stats)
+{
+    int nx = p->nx, ny = p->ny;
+    size_t n = (size_t)nx * ny;
+    double *wt = (double *)malloc(sizeof(double) * 3 * n);
+    double *target = (double *)malloc(sizeof(double) * 3 * n);
+    double *pt = (double *)malloc(sizeof(double) * 3 * n);
+    double *mu = (double *)malloc(sizeof(double) * 3 * n);
+    double *dphi = (double *)malloc(sizeof(double) * 3 * n);
+    double *ftot = (double *)malloc(sizeof(double) * 2 * n);
+    double qt[2], rs[2];
+
+    /* (1) convection: the target densities and the starting guess */
+    or_convect_phi(p, phi, vel, target);
+    or_aux_convection(p, omega, vel, wt);
+    /* (2) omega~ = Phi^{-1}(Phi~) and Phi(omega~) */
+    int it = or_invert(p, target, wt, pt, qt, max_iter, tol, rs);
+    /* (3)-(6) as in or_step */
+    or_mu(p, pt, wt, mu);
+    or_diffusion_update(p, wt, mu, omega);
+    or_solve(p, omega, phi, q);
+    for (size_t i = 0; i < 3 * n; i++) dphi[i] = phi[i] - pt[i];
+    or_force(p, dphi, force);
+    for (int y = 0; y < ny; y++)
+        for (int x = 0; x < nx; x++) {
+            size_t s = (size_t)y * nx + x;
+            ftot[s] = force[s] + or_poiseuille_force(p, y);
+            ftot[n + s] = force[n + s];
+        }
+    or_lb_step(p, pop, ftot, vel);
+    stats[0] = (double)it;
+    stats[1] = rs[0];
+    stats[2] = rs[1];
+    free(wt);
+    free(target);
+    free(pt);
+    free(mu);
+    free(dphi);
+    free(ftot);
+}
+
 /* Observables: sigma of Eq. (21) = mean |Phi_A + Phi_B - phi_p|. */
 double or_sigma(const or_params *p, const double *phi)
 {
