@@ -46,7 +46,7 @@ enum {
     EPD_LB_ENONFINITE = -4,  /* non-finite value or Q <= 0 detected on device */
     EPD_LB_EUNSTABLE = -5,   /* Mach-number pre-flight refused the run       */
     EPD_LB_ETIMEOUT = -6,    /* a bounded device wait gave up                */
-    EPD_LB_ENOTCONV = -7,    /* reserved: iterative inversion did not converge */
+    EPD_LB_ENOTCONV = -7,    /* the CG inversion of the exact step did not converge */
     EPD_LB_ETOOLARGE = -8    /* problem needs more than the fixed scratch of
                                 epd_prop_solve_noalloc                        */
 };
@@ -144,8 +144,8 @@ int epd_lb_velocity_dev(epd_lb *h, int32_t run, double *v_dev);
 int epd_lb_get_state(epd_lb *h, int32_t run, double *omega, double *pop, double *vel);
 
 /* Replace the state of a run (same layout as epd_lb_get_state).  A NULL
- * pointer keeps that part of the state.  Phi is not recomputed here: the next
- * epd_lb_step derives it from the new omega (epd_lb_solve gives it at once).
+ * pointer keeps that part of the state.  A new omega also recomputes Phi and
+ * Q of the run (epd_lb_densities then returns Phi(omega)).
  * In EPD_LB_MIXED_FP32 the populations and velocity are rounded to FP32.  Host
  * buffers; the copies are staged through the workspace.  Synchronous. */
 int epd_lb_set_state(epd_lb *h, int32_t run, const double *omega, const double *pop, const double *vel);
@@ -244,6 +244,34 @@ int epd_lb_set_surrogate(epd_lb *h, const float *params_host, double s_in, doubl
  * out[2] surrogate steps, out[3] exact steps forced by a failed check,
  * out[4] last residual, out[5] 1 if currently falling back. */
 int epd_lb_surrogate_stats(epd_lb *h, double *out);
+
+/* Exact step of App. C.  With max_iter > 0, epd_lb_step replaces steps 1-2
+ * above by the convection of the composition fields and the inversion of the
+ * density map (Sec. 2, integrator paragraph; App. C, items 1-3):
+ *   Phi~ = Phi(t) - dt div(v Phi(t))       (convective part of Eq. (2), flux
+ *                                           form, spectral derivatives),
+ *   omega~ = Phi^{-1}(Phi~)                (Fletcher-Reeves CG from the
+ *                                           auxiliary convection of omega),
+ * and steps 3 and 5 use Phi(omega~).  CG minimises the convex function
+ * G(omega) = <sum_I omega_I Phi~_I> + (phi_p/N) ln Q_P + (1 - phi_p) ln Q_S,
+ * whose gradient is the density mismatch Phi~ - Phi(omega) over n; the line
+ * search is one secant step between alpha = 0 and the previous step length
+ * (1 at the first iteration); the direction restarts as the steepest descent
+ * when it is not a descent direction.  Each iteration costs two single-chain
+ * solves.  A run stops iterating when
+ * sqrt(sum_I <(Phi~_I - Phi_I)^2>) < tol (N_tr = 1e-8 in the paper);
+ * tol = 0 runs exactly max_iter iterations.  A step whose runs did not all
+ * converge within max_iter iterations is completed and epd_lb_step returns
+ * EPD_LB_ENOTCONV after it.  Needs PLAIN_FP64 groups or MIXED_FP32 groups on
+ * the cluster-resident solve (there every density of the step is a
+ * difference from the solve at the starting guess; other MIXED grids give
+ * EPD_LB_EINVAL); excludes the surrogate.  The step is then enqueued eagerly
+ * (no graph) and synchronises once per iteration when tol > 0.
+ * max_iter = 0 (the default) restores the truncated step. */
+int epd_lb_set_inversion(epd_lb *h, int32_t max_iter, double tol);
+/* Of the last exact step of run `run`: out[0] CG iterations, out[1] the
+ * residual at the starting guess, out[2] the final residual.  Synchronous. */
+int epd_lb_inversion_stats(epd_lb *h, int32_t run, double *out);
 
 /* Text of the last error on the handle (never NULL). */
 const char *epd_lb_last_error(const epd_lb *h);

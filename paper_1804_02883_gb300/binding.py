@@ -37,6 +37,7 @@ SYMBOLS = (
     "epd_lb_enable_timing", "epd_lb_kernel_times", "epd_prop_solve_noalloc", "epd_lb_tiles",
     "epd_sur_num_params", "epd_sur_workspace_bytes", "epd_sur_forward", "epd_sur_gradients", "epd_sur_train_step",
     "epd_lb_surrogate_workspace_bytes", "epd_lb_set_surrogate", "epd_lb_surrogate_stats", "epd_lb_fields_dev",
+    "epd_lb_set_inversion", "epd_lb_inversion_stats",
 )
 
 
@@ -141,6 +142,8 @@ def lib():
                                                     ctypes.c_size_t]),
             "epd_lb_surrogate_stats": (ctypes.c_int, [vp, vp]),
             "epd_lb_fields_dev": (ctypes.c_int, [vp, i32, vp, vp]),
+            "epd_lb_set_inversion": (ctypes.c_int, [vp, i32, ctypes.c_double]),
+            "epd_lb_inversion_stats": (ctypes.c_int, [vp, i32, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -363,6 +366,19 @@ class EpdLb:
         hp = np.ascontiguousarray(params.detach().cpu().numpy() if hasattr(params, "detach") else params, dtype=np.float32)
         self._ck(lib().epd_lb_set_surrogate(self.h, hp.ctypes.data_as(ctypes.c_void_p), s_in, s_out, exact_every,
                                             residual_tol, ptr, nb.value), "epd_lb_set_surrogate")
+
+    def set_inversion(self, max_iter: int, tol: float = 1e-8):
+        """Exact step of App. C: Fletcher-Reeves inversion of the convected
+        densities with at most max_iter iterations per step down to the RMS
+        residual tol (0: exactly max_iter); max_iter = 0 restores the
+        truncated step."""
+        self._ck(lib().epd_lb_set_inversion(self.h, int(max_iter), float(tol)), "epd_lb_set_inversion")
+
+    def inversion_stats(self, run: int = 0) -> dict:
+        """Iterations and residuals (before, after) of the last exact step."""
+        out = np.empty(3)
+        self._ck(lib().epd_lb_inversion_stats(self.h, run, _ptr(out)), "epd_lb_inversion_stats")
+        return {"iterations": int(out[0]), "residual0": float(out[1]), "residual": float(out[2])}
 
     def surrogate_stats(self) -> dict:
         out = np.empty(6)

@@ -89,6 +89,18 @@ size_t carve_group(Group &G, char *base, size_t off)
         G.rho = take(R * n * sizeof(float2));
         G.c2p = take(R * n * sizeof(float2));
     }
+    // exact step: the inversion's fields and scalars
+    G.cg_target = (double *)take(R * 3 * n * sizeof(double));
+    G.cg_dir = (double *)take(R * 3 * n * sizeof(double));
+    G.cg_trial = (double *)take(R * 3 * n * sizeof(double));
+    G.cg_wref = G.cg_pref = nullptr;
+    if (G.hc) {
+        G.cg_wref = (double *)take(R * 3 * n * sizeof(double));
+        G.cg_pref = (double *)take(R * 3 * n * sizeof(double));
+    }
+    G.cg_qref = (double *)take(R * 2 * sizeof(double));
+    G.cg_part = (double *)take(R * kCgBlocks * 2 * sizeof(double));
+    G.cg = (double *)take(R * kCgSlots * sizeof(double));
     G.diff = false;  // set once the cluster solve is known to launch
     return align_up(off);
 }
@@ -127,7 +139,15 @@ static Group run_view(const Group &G, int r)
         V.hd = (char *)V.hd + (size_t)r * hs;
         V.rho = (char *)V.rho + (size_t)r * n * sizeof(float2);
         V.c2p = (char *)V.c2p + (size_t)r * n * sizeof(float2);
+        V.cg_wref += (size_t)r * 3 * n;
+        V.cg_pref += (size_t)r * 3 * n;
     }
+    V.cg_target += (size_t)r * 3 * n;
+    V.cg_dir += (size_t)r * 3 * n;
+    V.cg_trial += (size_t)r * 3 * n;
+    V.cg_qref += 2 * r;
+    V.cg_part += (size_t)r * kCgBlocks * 2;
+    V.cg += (size_t)r * kCgSlots;
     return V;
 }
 
@@ -372,6 +392,11 @@ struct epd_lb {
     long long sur_steps = 0, sur_exact = 0, sur_used = 0, sur_forced = 0;
     double sur_last = 0.0;
     bool sur_fallback = false;
+    // exact step (epd_lb_set_inversion): CG iterations per step (0: the
+    // inversion truncated to its starting guess) and the residual tolerance
+    int cg_max = 0;
+    double cg_tol = 1e-8;
+    double *cg_host = nullptr;  // pinned copy of one group's per-run scalars
     cudaEvent_t ev[7] = {};
     std::string last_error;
 };
@@ -600,9 +625,119 @@ extern "C" int epd_lb_init(const epd_lb_params *p, int32_t nruns, void *workspac
     return EPD_LB_OK;
 }
 
+// Whether any run of group G is still iterating (reads the per-run scalars).
+static int cg_any_active(epd_lb *h, Group &G, cudaStream_t s, bool *any)
+{
+    const size_t bytes = (size_t)G.g.nruns * kCgSlots * sizeof(double);
+    CK(cudaMemcpyAsync(h->cg_host, G.cg, bytes, cudaMemcpyDeviceToHost, s), "reading the inversion state");
+    CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    *any = false;
+    for (int r = 0; r < G.g.nruns; ++r) *any = *any || h->cg_host[(size_t)r * kCgSlots + CG_ACTIVE] != 0.0;
+    return EPD_LB_OK;
+}
+
+// One exact time step of group gi (App. C with the inversion), enqueued
+// eagerly on s: the iteration count depends on the data.
+//   Phi~ = Phi(t) - dt div(v Phi(t)); omega~ = Phi^{-1}(Phi~) by CG from the
+//   auxiliary convection of omega; then diffusion, second solve, force, LB.
+// MIXED groups (cluster solve) evaluate every density of the step as a
+// difference from the solve at the starting guess, Phi(t) included, so the
+// mismatch carries the FP32 rounding of the changes only.
+static int exact_group_step(epd_lb *h, size_t gi, int parity, cudaStream_t s, bool *notconv)
+{
+    Group &G = h->groups[gi];
+    const bool dif = G.diff;
+    const size_t m = (size_t)G.g.nruns * 3 * (size_t)G.g.n;
+    auto solve_at = [&](const double *om, double *ph, double *q) -> cudaError_t {
+        return dif ? launch_solve_delta_at(G, om, G.cg_wref, G.cg_pref, G.cg_qref, ph, q, s) : launch_solve(G, om, ph, q, s);
+    };
+    CK(launch_aux_convection(G, s), "auxiliary convection");              // starting guess omega~0
+    CK(launch_solve(G, G.omega_t, G.phi_t, G.q_t, s), "solve at the starting guess");
+    if (dif) {
+        CK(cudaMemcpyAsync(G.cg_wref, G.omega_t, m * sizeof(double), cudaMemcpyDeviceToDevice, s), "reference omega");
+        CK(cudaMemcpyAsync(G.cg_pref, G.phi_t, m * sizeof(double), cudaMemcpyDeviceToDevice, s), "reference Phi");
+        CK(cudaMemcpyAsync(G.cg_qref, G.q_t, (size_t)G.g.nruns * 2 * sizeof(double), cudaMemcpyDeviceToDevice, s), "reference Q");
+        CK(solve_at(G.omega, G.phi, G.q), "Phi(t) against the reference");
+    }
+    CK(launch_convect_phi(G, G.phi, G.cg_target, s), "convection of Phi");  // target Phi~
+    CK(cg_begin(G, G.phi_t, h->cg_tol, s), "inversion start");
+    for (int it = 0; it < h->cg_max; ++it) {
+        if (h->cg_tol > 0.0) {
+            bool any = false;
+            if (int rc = cg_any_active(h, G, s, &any)) return rc;
+            if (!any) break;
+        }
+        CK(cg_trial_point(G, G.omega_t, G.cg_trial, s), "trial point");
+        CK(solve_at(G.cg_trial, G.phi, G.q), "solve at the trial point");
+        CK(cg_line_step(G, G.phi, G.omega_t, s), "line step");
+        CK(solve_at(G.omega_t, G.phi_t, G.q_t), "solve at the new iterate");
+        CK(cg_direction(G, G.phi_t, h->cg_tol, s), "new direction");
+    }
+    if (h->cg_tol > 0.0) {
+        bool any = false;
+        if (int rc = cg_any_active(h, G, s, &any)) return rc;
+        *notconv = *notconv || any;
+    }
+    CK(launch_diffusion(G, s), "diffusion");                              // omega(t+dt)
+    CK(solve_at(G.omega, G.phi, G.q), "solve at t + dt");                 // Phi(t+dt)
+    CK(launch_force(G, s), "force");
+    CK(launch_lb(G, parity, s), "collide-stream");
+    return EPD_LB_OK;
+}
+
+extern "C" int epd_lb_set_inversion(epd_lb *h, int32_t max_iter, double tol)
+{
+    if (!h) return EPD_LB_EINVAL;
+    if (max_iter < 0 || max_iter > 100000 || !(tol >= 0.0) || !std::isfinite(tol))
+        return fail(h, EPD_LB_EINVAL, "max_iter must be in [0, 100000] and tol finite and >= 0");
+    if (max_iter > 0) {
+        if (h->sur_on) return fail(h, EPD_LB_EINVAL, "the exact step and the surrogate exclude each other");
+        for (const Group &G : h->groups)
+            if (G.prec != EPD_LB_PLAIN_FP64 && !G.diff)
+                return fail(h, EPD_LB_EINVAL,
+                            "the exact step needs PLAIN_FP64 or a MIXED_FP32 grid with the cluster-resident solve");
+        if (!h->cg_host) {
+            size_t mr = 1;
+            for (const Group &G : h->groups) mr = std::max(mr, (size_t)G.g.nruns);
+            CK(cudaMallocHost(&h->cg_host, mr * kCgSlots * sizeof(double)), "cudaMallocHost");
+        }
+    }
+    h->cg_max = max_iter;
+    h->cg_tol = tol;
+    return EPD_LB_OK;
+}
+
+extern "C" int epd_lb_inversion_stats(epd_lb *h, int32_t run, double *out)
+{
+    Group *G;
+    int mb;
+    if (!out) return fail(h, EPD_LB_EINVAL, "out is NULL");
+    if (!h || run < 0 || run >= h->nruns) return fail(h, EPD_LB_EINVAL, "run index out of range");
+    G = &h->groups[h->where[run].first];
+    mb = h->where[run].second;
+    double c[kCgSlots];
+    CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    CK(cudaMemcpy(c, G->cg + (size_t)mb * kCgSlots, sizeof(c), cudaMemcpyDeviceToHost), "reading the inversion state");
+    out[0] = c[CG_ITERS];
+    out[1] = c[CG_RES0];
+    out[2] = c[CG_RES];
+    return EPD_LB_OK;
+}
+
 extern "C" int epd_lb_step(epd_lb *h, int64_t nsteps)
 {
     if (!h || nsteps < 0) return EPD_LB_EINVAL;
+    if (h->cg_max > 0) {
+        for (int64_t k = 0; k < nsteps; ++k) {
+            bool notconv = false;
+            for (size_t gi = 0; gi < h->groups.size(); ++gi)
+                if (int rc = exact_group_step(h, gi, h->parity, h->stream, &notconv)) return rc;
+            h->parity ^= 1;
+            if (notconv)
+                return fail(h, EPD_LB_ENOTCONV, "the inversion did not reach the tolerance within max_iter iterations");
+        }
+        return EPD_LB_OK;
+    }
     for (int64_t k = 0; k < nsteps; ++k) {
         if (!h->sur_on) {
             CK(cudaGraphLaunch(h->exec[h->parity], h->stream), "cudaGraphLaunch");
@@ -744,6 +879,10 @@ extern "C" int epd_lb_set_state(epd_lb *h, int32_t run, const double *omega, con
         CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
         CK(cudaMemcpyAsync(G->stage, vel, 2 * n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy velocity");
         CK(launch_vel_from_f64(*G, m, G->stage, h->stream), "velocity conversion");
+    }
+    if (omega) {  // Phi(t) of the new fields (the exact step convects it)
+        Group V = run_view(*G, m);
+        CK(launch_solve(V, V.omega, V.phi, V.q, h->stream), "solve");
     }
     CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     return EPD_LB_OK;
@@ -918,6 +1057,7 @@ extern "C" void epd_lb_destroy(epd_lb *h)
     for (auto e : h->join_ev) cudaEventDestroy(e);
     for (auto st : h->side) cudaStreamDestroy(st);
     if (h->own_ws && h->ws) cudaFree(h->ws);
+    if (h->cg_host) cudaFreeHost(h->cg_host);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -1166,6 +1306,7 @@ extern "C" int epd_lb_set_surrogate(epd_lb *h, const float *params_host, double 
         h->sur_on = false;
         return EPD_LB_OK;
     }
+    if (h->cg_max > 0) return fail(h, EPD_LB_EINVAL, "the exact step and the surrogate exclude each other");
     size_t need = 0;
     if (int rc = epd_lb_surrogate_workspace_bytes(h, &need)) return rc;
     if (!params_host || !workspace || workspace_bytes < need || ((uintptr_t)workspace & 255))

@@ -58,6 +58,14 @@ struct Group {
     bool hist_full = false;   // streaming radix-8 solve: hist holds all N_s + 1 nodes
     int colw = 0;             // radix-8 EPD column tile width chosen by the autotuner (0: default)
     int colw_prop = 0;        // radix-8 streaming propagator column tile width (0: default)
+    // exact step (CG inversion of App. C), FP64 [run][3][n] unless noted
+    double *cg_target = nullptr;  // Phi~ = Phi(t) - dt div(v Phi(t))
+    double *cg_dir = nullptr;     // search direction d
+    double *cg_trial = nullptr;   // omega + alpha_t d
+    double *cg_wref = nullptr, *cg_pref = nullptr;  // reference omega, Phi of the differential solves (MIXED)
+    double *cg_qref = nullptr;    // [run][2]
+    double *cg_part = nullptr;    // reduction partials [run][kCgBlocks][2]
+    double *cg = nullptr;         // per-run scalars [run][kCgSlots]
     double2 *cz;       // 4 complex FP64 scratch planes per run: [run][4][n]
     double *part;      // reduction partials, [run][kMaxPart]
     double *f0_lat;    // [run]
@@ -80,6 +88,19 @@ struct Group {
 };
 
 constexpr int kMaxPart = 4096;     // partial sums per run and reduction
+constexpr int kCgBlocks = 304;     // blocks per run of the inversion's dot products (2 per SM)
+constexpr int kCgSlots = 16;       // per-run scalars of the inversion
+
+// Fletcher-Reeves inversion omega~ = Phi^{-1}(Phi~) (invert.cu).  Slots of G.cg.
+enum CgSlot { CG_GG = 0, CG_H0, CG_AT, CG_ALPHA, CG_RES, CG_RES0, CG_ITERS, CG_ACTIVE, CG_BETA };
+// g = target - phi; gg, residual, d = -g, h0 = -gg, alpha_t = 1, iterations 0
+cudaError_t cg_begin(Group &G, const double *phi, double tol, cudaStream_t s);
+// trial point omega + alpha_t d of the active runs (omega itself for the others)
+cudaError_t cg_trial_point(Group &G, const double *omega, double *trial, cudaStream_t s);
+// slope at the trial densities, the secant step alpha, omega += alpha d
+cudaError_t cg_line_step(Group &G, const double *phi_trial, double *omega, cudaStream_t s);
+// new mismatch from phi: residual, beta, the new direction, convergence flags
+cudaError_t cg_direction(Group &G, const double *phi, double tol, cudaStream_t s);
 
 // Workspace layout: compute (dry run with base == nullptr) or carve.
 size_t carve_group(Group &G, char *base, size_t off);
@@ -106,6 +127,12 @@ cudaError_t launch_solve(Group &G, const double *omega, double *phi, double *q, 
 // Second solve of the step as a difference from the reference solve at
 // omega~ (phi_t, q_t): Phi(t+dt) = Phi~ + dPhi, Q likewise (G.diff only).
 cudaError_t launch_solve_delta(Group &G, cudaStream_t s, const SolveProbe *probe = nullptr);
+// The same at any omega against a given reference: omega_ref with its
+// densities phi_ref, q_ref, whose chain states the last plain solve stored
+// (G.hc) and whose Boltzmann factors are in G.efac.
+cudaError_t launch_solve_delta_at(Group &G, const double *omega, const double *omega_ref, const double *phi_ref,
+                                  const double *q_ref, double *phi, double *q, cudaStream_t s,
+                                  const SolveProbe *probe = nullptr);
 
 // Column tile autotuner of the radix-8 column passes (sets G.colw).
 cudaError_t tune_column_tiles(Group &G, cudaStream_t s);
@@ -113,6 +140,7 @@ cudaError_t tune_stream_tiles(Group &G, cudaStream_t s);  // sets G.colw_prop
 
 // EPD parts of the step.
 cudaError_t launch_aux_convection(Group &G, cudaStream_t s);   // omega, vel -> omega_t
+cudaError_t launch_convect_phi(Group &G, const double *phi, double *phi_dst, cudaStream_t s);  // Phi - dt div(v Phi)
 cudaError_t launch_diffusion(Group &G, cudaStream_t s);        // phi_t, omega_t -> omega
 cudaError_t launch_force(Group &G, cudaStream_t s);            // phi, phi_t -> force
 cudaError_t launch_lb(Group &G, int parity, cudaStream_t s);   // pop[parity] -> pop[1-parity], vel
@@ -136,7 +164,7 @@ size_t cluster_state_floats2(int nx, int ny, int ns);  // per run, both chains
 // Chain launch plus contour sums and normalisation into phi, q (diff: the
 // differential solve into G.phi, G.q).  nprep_blocks: solvent partials.
 cudaError_t launch_cluster_solve(Group &G, cudaStream_t s, bool diff, int nprep_blocks, double *phi, double *q,
-                                 const SolveProbe *probe);
+                                 const SolveProbe *probe, const double *phi_ref = nullptr, const double *q_ref = nullptr);
 int cluster_ctas(const Group &G);
 
 // Kernel attributes (dynamic shared memory limits), once per process.

@@ -1,7 +1,9 @@
 // epd.cu -- EPD part of the hybrid LB/EPD step of arXiv:1804.02883 on sm_103a:
 //   auxiliary convection of omega (App. C, item 1),
 //   diffusion step omega <- omega~ - dt D_I Lap mu_I (Sec. 2, Eq. (5); App. C),
-//   force reconstruction from the composition change (Sec. 2, Eqs. (19)-(20)).
+//   force reconstruction from the composition change (Sec. 2, Eqs. (19)-(20)),
+//   convection of the composition fields Phi~ = Phi - dt div(v Phi) (the
+//   convective part of Eq. (2); the exact step of App. C).
 //
 // Spatial derivatives are spectral with continuum wavenumbers; first
 // derivatives drop the Nyquist bin, the Laplacian keeps it.  d/dx and d2/dx2
@@ -23,13 +25,14 @@
 
 namespace epdlb {
 
-enum RowMode { ROW_GRAD = 0, ROW_LAP = 1, ROW_FWD_S = 2, ROW_INV_FORCE = 3 };
-enum ColMode { COL_CONVECT = 0, COL_DIFFUSE = 1, COL_FORCE = 2 };
+enum RowMode { ROW_GRAD = 0, ROW_LAP = 1, ROW_FWD_S = 2, ROW_INV_FORCE = 3, ROW_DIVX = 4 };
+enum ColMode { COL_CONVECT = 0, COL_DIFFUSE = 1, COL_FORCE = 2, COL_DIVY = 3 };
 
 struct EpdK {
     GroupGeom g;
     const double *omega, *omega_t, *phi, *phi_t;
     double *omega_dst;
+    double *phi_dst;  // convected densities (ROW_DIVX / COL_DIVY)
     void *cz;  // [run][4][n] complex of the transform type
     const void *vel;
     void *force;
@@ -113,6 +116,11 @@ __global__ void __launch_bounds__(kThreads) epd_row(EpdK k)
             const double *p1 = k.phi + (size_t)run * 3 * n, *p0 = k.phi_t + (size_t)run * 3 * n;
             const double sa = (p1[s] - p0[s]) + (p1[n + s] - p0[n + s]);
             v = mk<TT>((TT)(sa / g.d_p + (p1[2 * n + s] - p0[2 * n + s]) / g.d_s), (TT)0);
+        } else if (MODE == ROW_DIVX) {
+            // x flux v_x Phi_I, v = u_lat dx/dt
+            const double *ph = k.phi + (size_t)run * 3 * n;
+            const double vx = vel_at(k, (size_t)run * n + s).x * g.vscale;
+            v = pair == 0 ? mk<TT>((TT)(vx * ph[s]), (TT)(vx * ph[n + s])) : mk<TT>((TT)(vx * ph[2 * n + s]), (TT)0);
         } else {
             v = cz[((size_t)run * 4 + 2) * n + s];
         }
@@ -129,7 +137,7 @@ __global__ void __launch_bounds__(kThreads) epd_row(EpdK k)
             for (int i = threadIdx.x; i < tile; i += blockDim.x) {
                 const int m = i & (nx - 1);
                 V2<TT> v = r[i];
-                if (MODE == ROW_GRAD) {  // i kx / nx
+                if (MODE == ROW_GRAD || MODE == ROW_DIVX) {  // i kx / nx
                     const TT kk = kvec_odd<TT>(m, nx, unit) * inv_n;
                     v = mk<TT>(-kk * v.y, kk * v.x);
                 } else {                 // -kx^2 / nx
@@ -177,6 +185,11 @@ __global__ void __launch_bounds__(kThreads) epd_col(EpdK k)
             v = pair == 0 ? mk<TT>((TT)om[s], (TT)om[n + s]) : mk<TT>((TT)om[2 * n + s], (TT)0);
         } else if (MODE == COL_DIFFUSE) {
             v = to_tt<TT>(mu_pair(k, k.phi_t + (size_t)run * 3 * n, k.omega_t + (size_t)run * 3 * n, n, s, pair));
+        } else if (MODE == COL_DIVY) {
+            // y flux v_y Phi_I
+            const double *ph = k.phi + (size_t)run * 3 * n;
+            const double vy = vel_at(k, (size_t)run * n + s).y * g.vscale;
+            v = pair == 0 ? mk<TT>((TT)(vy * ph[s]), (TT)(vy * ph[n + s])) : mk<TT>((TT)(vy * ph[2 * n + s]), (TT)0);
         } else {
             v = cz[((size_t)run * 4 + 2) * n + s];
         }
@@ -190,7 +203,7 @@ __global__ void __launch_bounds__(kThreads) epd_col(EpdK k)
     for (int i = threadIdx.x; i < tile; i += blockDim.x) {
         const int my = i >> logc;
         V2<TT> v = r[i];
-        if (MODE == COL_CONVECT) {       // i ky / ny
+        if (MODE == COL_CONVECT || MODE == COL_DIVY) {  // i ky / ny
             const TT kk = kvec_odd<TT>(my, ny, uy) * inv_n;
             v = mk<TT>(-kk * v.y, kk * v.x);
         } else if (MODE == COL_DIFFUSE) { // -ky^2 / ny
@@ -218,6 +231,18 @@ __global__ void __launch_bounds__(kThreads) epd_col(EpdK k)
         const long long s = (long long)(i >> logc) * nx + x0 + (i & (C - 1));
         if (MODE == COL_FORCE) {
             cz[((size_t)run * 4 + 2) * n + s] = r[i];
+        } else if (MODE == COL_DIVY) {
+            // Phi~ = Phi - dt (d/dx (v_x Phi) + d/dy (v_y Phi))
+            const double2 dy = to_d<TT>(r[i]);
+            const double2 dx = to_d<TT>(cz[((size_t)run * 4 + pair) * n + s]);
+            const double *ph = k.phi + (size_t)run * 3 * n;
+            double *pd = k.phi_dst + (size_t)run * 3 * n;
+            if (pair == 0) {
+                pd[s] = ph[s] - g.dt * (dx.x + dy.x);
+                pd[n + s] = ph[n + s] - g.dt * (dx.y + dy.y);
+            } else {
+                pd[2 * n + s] = ph[2 * n + s] - g.dt * (dx.x + dy.x);
+            }
         } else if (MODE == COL_CONVECT) {
             // omega~ = omega - dt v . grad omega, v = u_lat dx/dt
             const double2 dy = to_d<TT>(r[i]);
@@ -504,6 +529,7 @@ static EpdK make_k(Group &G)
     k.phi = G.phi;
     k.phi_t = G.phi_t;
     k.omega_dst = nullptr;
+    k.phi_dst = nullptr;
     k.cz = G.cz;
     k.vel = G.vel;
     k.force = G.force;
@@ -633,6 +659,21 @@ cudaError_t tune_column_tiles(Group &G, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// Convection of the composition fields, always with FP64 transforms (the
+// FP64 twiddles exist in both precisions; the FP64 scratch planes fit the
+// EPD scratch): the densities of every run of the group.
+cudaError_t launch_convect_phi(Group &G, const double *phi, double *phi_dst, cudaStream_t s)
+{
+    EpdK k = make_k(G);
+    k.phi = phi;
+    k.phi_dst = phi_dst;
+    k.twx = G.twx_d;
+    k.twy = G.twy_d;
+    epd_row<double, ROW_DIVX><<<dim3(G.g.ny / G.sh.rows_epd, G.g.nruns, 2), kThreads, row_smem<double>(G), s>>>(k);
+    epd_col<double, COL_DIVY><<<dim3(G.g.nx / G.sh.cols_epd, G.g.nruns, 2), kThreads, col_smem<double>(G), s>>>(k);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_aux_convection(Group &G, cudaStream_t s)
 {
     return G.prec == EPD_LB_MIXED_FP32 ? aux_t<float>(G, s) : aux_t<double>(G, s);
@@ -664,7 +705,10 @@ template <typename TT> static cudaError_t configure_t()
 cudaError_t configure_epd_kernels()
 {
     cudaError_t e = configure_t<float>();
-    return e ? e : configure_t<double>();
+    if (!e) e = configure_t<double>();
+    if (!e) e = cudaFuncSetAttribute(epd_row<double, ROW_DIVX>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (!e) e = cudaFuncSetAttribute(epd_col<double, COL_DIVY>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    return e;
 }
 
 } // namespace epdlb

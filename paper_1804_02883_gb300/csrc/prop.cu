@@ -651,14 +651,20 @@ cudaError_t launch_solve(Group &G, const double *omega, double *phi, double *q, 
     return solve_t<double>(G, omega, phi, q, s, probe);
 }
 
-cudaError_t launch_solve_delta(Group &G, cudaStream_t s, const SolveProbe *probe)
+cudaError_t launch_solve_delta_at(Group &G, const double *omega, const double *omega_ref, const double *phi_ref,
+                                  const double *q_ref, double *phi, double *q, cudaStream_t s, const SolveProbe *probe)
 {
     if (!G.diff || !G.hd) return cudaErrorInvalidValue;
     const GroupGeom &g = G.g;
     const int pg = grid_for(g.n);
-    prop_prep_delta<<<dim3(pg, g.nruns), kThreads, 0, s>>>(g, G.omega, G.omega_t, reinterpret_cast<float2 *>(G.rho),
-                                                          reinterpret_cast<float *>(G.c2p), G.phi, G.part);
-    return launch_cluster_solve(G, s, true, pg, G.phi, G.q, probe);
+    prop_prep_delta<<<dim3(pg, g.nruns), kThreads, 0, s>>>(g, omega, omega_ref, reinterpret_cast<float2 *>(G.rho),
+                                                          reinterpret_cast<float *>(G.c2p), phi, G.part);
+    return launch_cluster_solve(G, s, true, pg, phi, q, probe, phi_ref, q_ref);
+}
+
+cudaError_t launch_solve_delta(Group &G, cudaStream_t s, const SolveProbe *probe)
+{
+    return launch_solve_delta_at(G, G.omega, G.omega_t, G.phi_t, G.q_t, G.phi, G.q, s, probe);
 }
 
 cudaError_t configure_prop_kernels()

@@ -628,7 +628,7 @@ int cluster_ctas(const Group &G)
 }
 
 cudaError_t launch_cluster_solve(Group &G, cudaStream_t s, bool diff, int nprep_blocks, double *phi, double *q,
-                                 const SolveProbe *probe)
+                                 const SolveProbe *probe, const double *phi_ref, const double *q_ref)
 {
     const ClusterShape *sh = find_shape(G.g.logx, G.g.logy);
     if (!sh || !G.hc || (diff && !G.hd)) return cudaErrorInvalidValue;
@@ -668,8 +668,8 @@ cudaError_t launch_cluster_solve(Group &G, cudaStream_t s, bool diff, int nprep_
     c.efac = reinterpret_cast<const float2 *>(G.efac);
     c.rho = reinterpret_cast<const float2 *>(G.rho);
     c.part = G.part;
-    c.phi_t = G.phi_t;
-    c.q_t = G.q_t;
+    c.phi_t = phi_ref ? phi_ref : G.phi_t;
+    c.q_t = q_ref ? q_ref : G.q_t;
     c.phi = phi;
     c.q = q;
     c.err = G.err;
