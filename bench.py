@@ -267,6 +267,27 @@ def surrogate_section(P, W, torch, runs, h, flush, args):
     return out
 
 
+def exact_section(P, runs, flush, args):
+    """The exact step of App. C (convection of Phi, Fletcher-Reeves inversion
+    to the paper's 1e-8 tolerance) on the same workload: time per step and the
+    iterations each run needed."""
+    h = P.EpdLb(runs)
+    h.step(args.warmup)
+    h.set_inversion(100, 1e-8)
+    h.step(1)
+    h.sync()
+    per, _ = time_steps(h, h.stream, args.exact_steps, flush)
+    h.sync()
+    stats = [h.inversion_stats(r) for r in range(len(runs))]
+    h.close()
+    return {"ms_per_step": float(sum(per) / len(per)), "steps": args.exact_steps, "tol": 1e-8, "max_iter": 100,
+            "iterations_last_step": [s["iterations"] for s in stats],
+            "residual0_last_step": [s["residual0"] for s in stats],
+            "residual_last_step": [s["residual"] for s in stats],
+            "note": "eager enqueue with one host synchronisation per CG iteration; per iteration two "
+                    "single-chain solves (differential against the solve at the starting guess)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -277,6 +298,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--surrogate-steps", type=int, default=40)
+    ap.add_argument("--exact-steps", type=int, default=5,
+                    help="steps of the exact step (CG inversion) timed on the same workload; 0 skips it")
     ap.add_argument("--workload", default="channel", choices=sorted(WORKLOADS),
                     help="channel (default): the 4 x 256x512 batch the metric is quoted on; ensemble32 and "
                          "vesicle are the other configurations")
@@ -411,6 +434,12 @@ def main():
     # FP64-plain path on the same workload
     h.close()
     del h
+    exact = None
+    if args.exact_steps > 0:
+        try:
+            exact = exact_section(P, runs, flush, args)
+        except P.EpdLbError as e:  # grids without an exact MIXED path
+            exact = {"unavailable": str(e)}
     fp64 = None
     if args.fp64_steps > 0:
         runs64 = workload_runs(args.workload, P.PLAIN_FP64, rank)
@@ -452,6 +481,7 @@ def main():
             "kernels": kernels,
             "roofline": roofline,
             "surrogate": sur,
+            "exact_step": exact,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": n_launches * args.steps,

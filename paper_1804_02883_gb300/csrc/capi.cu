@@ -82,7 +82,10 @@ size_t carve_group(Group &G, char *base, size_t off)
     // cluster solve (MIXED_FP32): stored states of both chains, and the
     // differential second solve's buffers
     G.hc = G.hd = G.rho = G.c2p = nullptr;
-    if (G.prec == EPD_LB_MIXED_FP32 && cluster_shape_exists(G.g.logx, G.g.logy)) {
+    // (decided from the parameters, not from a pointer: the dry run that
+    // sizes the workspace carves with null pointers)
+    const bool cluster = G.prec == EPD_LB_MIXED_FP32 && cluster_shape_exists(G.g.logx, G.g.logy);
+    if (cluster) {
         const size_t hs = R * cluster_state_floats2(G.g.nx, G.g.ny, G.g.ns) * sizeof(float2);
         G.hc = take(hs);
         G.hd = take(hs);
@@ -94,7 +97,7 @@ size_t carve_group(Group &G, char *base, size_t off)
     G.cg_dir = (double *)take(R * 3 * n * sizeof(double));
     G.cg_trial = (double *)take(R * 3 * n * sizeof(double));
     G.cg_wref = G.cg_pref = nullptr;
-    if (G.hc) {
+    if (cluster) {
         G.cg_wref = (double *)take(R * 3 * n * sizeof(double));
         G.cg_pref = (double *)take(R * 3 * n * sizeof(double));
     }
@@ -599,6 +602,8 @@ extern "C" int epd_lb_init(const epd_lb_params *p, int32_t nruns, void *workspac
         off = carve_group(G, base, off);
         G.err = h->err;
     }
+    // the carve with real pointers must end where the sizing dry run did
+    if (off > need) return bail(EPD_LB_ENOMEM);
     if (cudaMemsetAsync(h->err, 0, sizeof(int), h->stream) != cudaSuccess) return bail(EPD_LB_ECUDA);
     for (auto &G : h->groups) {
         if (upload_tables_e(G, h->stream) != cudaSuccess) return bail(EPD_LB_ECUDA);
