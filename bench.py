@@ -73,8 +73,8 @@ def sites_per_step(runs) -> float:
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one differential chain
-# launch on the 4 x 256x512, N_s = 64 batch (287.6 + 241.5 MB)
-CHAIN_DIFF_DRAM_BYTES = 529.1e6
+# launch on the 4 x 256x512, N_s = 64 batch (296.0 + 234.2 MB)
+CHAIN_DIFF_DRAM_BYTES = 530.2e6
 
 
 def launches_per_step(runs, h) -> int:

@@ -144,8 +144,9 @@ int epd_lb_velocity_dev(epd_lb *h, int32_t run, double *v_dev);
 int epd_lb_get_state(epd_lb *h, int32_t run, double *omega, double *pop, double *vel);
 
 /* Replace the state of a run (same layout as epd_lb_get_state).  A NULL
- * pointer keeps that part of the state.  A new omega also recomputes Phi and
- * Q of the run (epd_lb_densities then returns Phi(omega)).
+ * pointer keeps that part of the state.  Phi is not recomputed here: the next
+ * epd_lb_step derives it from the new omega (epd_lb_solve gives it at once;
+ * the exact step first recomputes Phi(t) of the new omega).
  * In EPD_LB_MIXED_FP32 the populations and velocity are rounded to FP32.  Host
  * buffers; the copies are staged through the workspace.  Synchronous. */
 int epd_lb_set_state(epd_lb *h, int32_t run, const double *omega, const double *pop, const double *vel);

@@ -656,6 +656,7 @@ static int exact_group_step(epd_lb *h, size_t gi, int parity, cudaStream_t s, bo
     auto solve_at = [&](const double *om, double *ph, double *q) -> cudaError_t {
         return dif ? launch_solve_delta_at(G, om, G.cg_wref, G.cg_pref, G.cg_qref, ph, q, s) : launch_solve(G, om, ph, q, s);
     };
+    if (G.phi_stale && !dif) CK(launch_solve(G, G.omega, G.phi, G.q, s), "Phi(t) of a replaced omega");
     CK(launch_aux_convection(G, s), "auxiliary convection");              // starting guess omega~0
     CK(launch_solve(G, G.omega_t, G.phi_t, G.q_t, s), "solve at the starting guess");
     if (dif) {
@@ -735,8 +736,10 @@ extern "C" int epd_lb_step(epd_lb *h, int64_t nsteps)
     if (h->cg_max > 0) {
         for (int64_t k = 0; k < nsteps; ++k) {
             bool notconv = false;
-            for (size_t gi = 0; gi < h->groups.size(); ++gi)
+            for (size_t gi = 0; gi < h->groups.size(); ++gi) {
                 if (int rc = exact_group_step(h, gi, h->parity, h->stream, &notconv)) return rc;
+                h->groups[gi].phi_stale = false;
+            }
             h->parity ^= 1;
             if (notconv)
                 return fail(h, EPD_LB_ENOTCONV, "the inversion did not reach the tolerance within max_iter iterations");
@@ -764,6 +767,7 @@ extern "C" int epd_lb_step(epd_lb *h, int64_t nsteps)
             ++h->sur_used;
             ++h->sur_steps;
         }
+        for (Group &G : h->groups) G.phi_stale = false;
         h->parity ^= 1;
     }
     return EPD_LB_OK;
@@ -885,10 +889,7 @@ extern "C" int epd_lb_set_state(epd_lb *h, int32_t run, const double *omega, con
         CK(cudaMemcpyAsync(G->stage, vel, 2 * n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy velocity");
         CK(launch_vel_from_f64(*G, m, G->stage, h->stream), "velocity conversion");
     }
-    if (omega) {  // Phi(t) of the new fields (the exact step convects it)
-        Group V = run_view(*G, m);
-        CK(launch_solve(V, V.omega, V.phi, V.q, h->stream), "solve");
-    }
+    if (omega) G->phi_stale = true;  // the exact step recomputes Phi(t) before convecting it
     CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     return EPD_LB_OK;
 }
@@ -993,6 +994,7 @@ extern "C" int epd_lb_load(epd_lb *h, const void *buf, size_t len)
         c += 14 * n * sizeof(double);
         left -= need;
     }
+    for (Group &G : h->groups) G.phi_stale = false;  // every run was solved above
     return EPD_LB_OK;
 }
 

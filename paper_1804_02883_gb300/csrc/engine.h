@@ -55,6 +55,7 @@ struct Group {
     void *rho = nullptr;      // (rho_A, rho_B) = expm1(-N d omega ds / 2), [run][n] float2
     void *c2p = nullptr;      // rho (2 + rho) per block, packed rows [run][2][ny/2][nx] float2
     bool diff = false;        // the step uses the reference + differential solve pair
+    bool phi_stale = false;   // omega was replaced since phi was last computed
     bool hist_full = false;   // streaming radix-8 solve: hist holds all N_s + 1 nodes
     int colw = 0;             // radix-8 EPD column tile width chosen by the autotuner (0: default)
     int colw_prop = 0;        // radix-8 streaming propagator column tile width (0: default)

@@ -72,17 +72,22 @@ __global__ void __launch_bounds__(kCgThreads) cg_dots(long long m, const double 
     }
 }
 
-// Per run (one thread): the sums of the partials and the scalar logic.
+// Per run (one warp): the sums of the partials (lane-strided, then a fixed
+// shuffle tree) and the scalar logic (lane 0).
 template <int STAGE>
 __global__ void cg_scalar(long long n, int nblk, const double *part, double *cg, double tol)
 {
-    if (threadIdx.x) return;
-    const int run = blockIdx.x;
+    const int run = blockIdx.x, lane = threadIdx.x;
     double a = 0.0, b = 0.0;
-    for (int i = 0; i < nblk; ++i) {
+    for (int i = lane; i < nblk; i += 32) {
         a += part[((size_t)run * nblk + i) * 2];
         b += part[((size_t)run * nblk + i) * 2 + 1];
     }
+    for (int o = 16; o; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if (lane) return;
     double *c = cg + (size_t)run * kCgSlots;
     if (STAGE == ST_BEGIN) {
         // g.g at the starting guess; d = -g, so g.d = -g.g
