@@ -122,6 +122,9 @@ def lib():
             "or_convect_phi": (None, [P, _DP, _DP, _DP]),
             "or_invert": (ctypes.c_int, [P, _DP, _DP, _DP, _DP, ctypes.c_int, ctypes.c_double, _DP]),
             "or_step_exact": (None, [P, _DP, _DP, _DP, _DP, _DP, _DP, ctypes.c_int, ctypes.c_double, _DP]),
+            "or_sigma_delta": (ctypes.c_double, [P, _DP, _DP]),
+            "or_width": (ctypes.c_double, [P, _DP]),
+            "or_particles": (ctypes.c_int, [P, _DP, ctypes.c_double, ctypes.POINTER(ctypes.c_int), _DP, ctypes.c_int]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -346,3 +349,31 @@ def step_exact(p: Params, st: State, nsteps: int = 1, max_iter: int = 50, tol: f
 def sigma(p: Params, phi) -> float:
     phi = _f64(phi).reshape(3, p.ny, p.nx)
     return lib().or_sigma(ctypes.byref(p.c()), _d(phi))
+
+
+# --- analysis of Phi_P (Sec. 3, Sec. 4) ------------------------------------
+
+def sigma_delta(p: Params, phi_a, phi_b) -> float:
+    a = _f64(phi_a).reshape(3, p.ny, p.nx)
+    b = _f64(phi_b).reshape(3, p.ny, p.nx)
+    return lib().or_sigma_delta(ctypes.byref(p.c()), _d(a), _d(b))
+
+
+def width(p: Params, phi) -> float:
+    """Y_2^P of Eq. (30) (channel centres at L_y/4 and 3 L_y/4)."""
+    phi = _f64(phi).reshape(3, p.ny, p.nx)
+    return lib().or_width(ctypes.byref(p.c()), _d(phi))
+
+
+PARTICLE_FIELDS = ("sites", "content", "cx", "cy", "gxx", "gxy", "gyy", "R", "c", "c_rel")
+
+
+def particles(p: Params, phi, threshold: float = 0.5, max_out: int = 4096):
+    """(labels (ny, nx) int, stats (count, 10)) of the clusters with
+    Phi_P >= threshold; stats columns as in PARTICLE_FIELDS."""
+    phi = _f64(phi).reshape(3, p.ny, p.nx)
+    labels = np.empty((p.ny, p.nx), dtype=np.int32)
+    stats = np.zeros((max_out, 10))
+    cnt = lib().or_particles(ctypes.byref(p.c()), _d(phi), float(threshold),
+                             labels.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _d(stats), int(max_out))
+    return labels, stats[: min(cnt, max_out)].copy(), cnt

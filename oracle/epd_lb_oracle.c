@@ -796,3 +796,142 @@ double or_sigma(const or_params *p, const double *phi)
     for (size_t i = 0; i < n; i++) s += fabs(phi[i] + phi[n + i] - p->phi_p);
     return s / (double)n;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Analysis of the polymer distribution Phi_P = Phi_A + Phi_B (Sec. 3,       */
+/* Sec. 4): sigma_Delta, the channel width Y_2^P, particles and their        */
+/* gyration tensors.                                                         */
+/* ------------------------------------------------------------------------ */
+
+/* sigma_Delta of Eq. (22): mean |Phi_P^a - Phi_P^b| of two runs on one grid. */
+double or_sigma_delta(const or_params *p, const double *phi_a, const double *phi_b)
+{
+    size_t n = (size_t)p->nx * p->ny;
+    double s = 0.0;
+    for (size_t i = 0; i < n; i++) s += fabs((phi_a[i] + phi_a[n + i]) - (phi_b[i] + phi_b[n + i]));
+    return s / (double)n;
+}
+
+/* Y_2^P of Eq. (30).  READING: the box holds two opposite Poiseuille
+ * channels, y in [0, L_y/2) and [L_y/2, L_y), each of width L_y/2 with its
+ * centre at L_y/4 and 3 L_y/4, and y of Eq. (30) is the distance across the
+ * channel from its centre; site row y sits at (y + 1/2) dx (the LB node
+ * positions), and the integrals are sums over all sites of both channels:
+ *   Y_2^P = sqrt( sum y_c^2 Phi_P / (phi_p sum y_c^2) ). */
+double or_width(const or_params *p, const double *phi)
+{
+    int nx = p->nx, ny = p->ny;
+    size_t n = (size_t)nx * ny;
+    double h = 0.5 * (double)ny;
+    double num = 0.0, den = 0.0;
+    for (int y = 0; y < ny; y++) {
+        double yy = (double)y + 0.5;
+        double centre = yy < h ? 0.5 * h : 1.5 * h;
+        double yc = (yy - centre) * p->dx;
+        for (int x = 0; x < nx; x++) {
+            size_t i = (size_t)y * nx + x;
+            num += yc * yc * (phi[i] + phi[n + i]);
+            den += yc * yc;
+        }
+    }
+    return sqrt(num / (p->phi_p * den));
+}
+
+/* Particles (Sec. 4): connected clusters of sites with Phi_P >= threshold
+ * (0.5 in the paper).  READING: clusters connect nearest neighbours (4 per
+ * site) across the periodic boundaries.  Clusters are numbered in the order
+ * of their first site in row-major order.  labels (n): particle number or -1.
+ * Per particle k < max_out, stats[10 k ...] =
+ *   sites, content N = sum Phi_P, centre x, centre y (in [0, L)), G_xx, G_xy,
+ *   G_yy of Eq. (27), R and c of Eq. (28), c_rel of Eq. (29),
+ * with G from the double sum of Eq. (27) over the particle's sites, r^i - r^j
+ * the shortest periodic separation (READING; exact for particles narrower
+ * than half the box), positions (x, y) dx.  Returns the number of particles. */
+int or_particles(const or_params *p, const double *phi, double threshold, int *labels, double *stats, int max_out)
+{
+    int nx = p->nx, ny = p->ny;
+    size_t n = (size_t)nx * ny;
+    int *queue = (int *)malloc(sizeof(int) * n);
+    int *members = (int *)malloc(sizeof(int) * n);
+    for (size_t i = 0; i < n; i++) labels[i] = -1;
+    int count = 0;
+    for (size_t s0 = 0; s0 < n; s0++) {
+        if (labels[s0] != -1 || phi[s0] + phi[n + s0] < threshold) continue;
+        /* breadth-first search of the cluster of s0 */
+        int head = 0, tail = 0, m = 0;
+        labels[s0] = count;
+        queue[tail++] = (int)s0;
+        while (head < tail) {
+            int s = queue[head++];
+            members[m++] = s;
+            int x = s % nx, y = s / nx;
+            int nb[4] = {y * nx + (x + 1) % nx, y * nx + (x + nx - 1) % nx, ((y + 1) % ny) * nx + x,
+                         ((y + ny - 1) % ny) * nx + x};
+            for (int k = 0; k < 4; k++) {
+                int t = nb[k];
+                if (labels[t] == -1 && phi[t] + phi[n + t] >= threshold) {
+                    labels[t] = count;
+                    queue[tail++] = t;
+                }
+            }
+        }
+        if (count < max_out) {
+            double *st = stats + (size_t)10 * count;
+            double content = 0.0;
+            for (int a = 0; a < m; a++) content += phi[members[a]] + phi[n + members[a]];
+            /* Eq. (27): G_nm = 1/(2 N^2) sum_i sum_j Phi_i Phi_j (r_n^i - r_n^j)(r_m^i - r_m^j) */
+            double gxx = 0.0, gxy = 0.0, gyy = 0.0, mx = 0.0, my = 0.0;
+            int x0 = members[0] % nx, y0 = members[0] / nx;
+            for (int a = 0; a < m; a++) {
+                int ia = members[a];
+                double wa = phi[ia] + phi[n + ia];
+                int xa = ia % nx, ya = ia / nx;
+                /* centre: content-weighted mean of the shortest offsets from the first site */
+                int ox = xa - x0, oy = ya - y0;
+                if (2 * ox > nx) ox -= nx;
+                if (2 * ox <= -nx) ox += nx;
+                if (2 * oy > ny) oy -= ny;
+                if (2 * oy <= -ny) oy += ny;
+                mx += wa * ox;
+                my += wa * oy;
+                for (int b = 0; b < m; b++) {
+                    int ib = members[b];
+                    double wb = phi[ib] + phi[n + ib];
+                    int dxs = xa - ib % nx, dys = ya - ib / nx;
+                    if (2 * dxs > nx) dxs -= nx;
+                    if (2 * dxs <= -nx) dxs += nx;
+                    if (2 * dys > ny) dys -= ny;
+                    if (2 * dys <= -ny) dys += ny;
+                    double rx = dxs * p->dx, ry = dys * p->dx;
+                    gxx += wa * wb * rx * rx;
+                    gxy += wa * wb * rx * ry;
+                    gyy += wa * wb * ry * ry;
+                }
+            }
+            double f = 1.0 / (2.0 * content * content);
+            gxx *= f;
+            gxy *= f;
+            gyy *= f;
+            double cx = fmod(x0 + mx / content + nx, (double)nx) * p->dx;
+            double cy = fmod(y0 + my / content + ny, (double)ny) * p->dx;
+            /* Eq. (28): eigenvalues of the 2 x 2 tensor, c = l+ - l-, R = sqrt(l+ + l-); Eq. (29) */
+            double tr = gxx + gyy, dd = sqrt(0.25 * (gxx - gyy) * (gxx - gyy) + gxy * gxy);
+            double lp = 0.5 * tr + dd, lm = 0.5 * tr - dd;
+            double c = lp - lm, r = sqrt(lp + lm);
+            st[0] = (double)m;
+            st[1] = content;
+            st[2] = cx;
+            st[3] = cy;
+            st[4] = gxx;
+            st[5] = gxy;
+            st[6] = gyy;
+            st[7] = r;
+            st[8] = c;
+            st[9] = r > 0.0 ? c * c / (r * r * r * r) : 0.0;
+        }
+        count++;
+    }
+    free(queue);
+    free(members);
+    return count;
+}
