@@ -274,6 +274,33 @@ int epd_lb_set_inversion(epd_lb *h, int32_t max_iter, double tol);
  * residual at the starting guess, out[2] the final residual.  Synchronous. */
 int epd_lb_inversion_stats(epd_lb *h, int32_t run, double *out);
 
+/* Analysis of the polymer distribution Phi_P = Phi_A + Phi_B of the current
+ * state (Phi is first recomputed if epd_lb_set_state replaced omega).  All
+ * synchronous, host outputs. */
+/* sigma_Delta of Eq. (22): *out = <|Phi_P(run_a) - Phi_P(run_b)|>, e.g. a run
+ * with and one without the LB coupling (inv_beta_v = 0) from the same
+ * initial state.  The runs need the same grid (EPD_LB_EINVAL otherwise). */
+int epd_lb_sigma_delta(epd_lb *h, int32_t run_a, int32_t run_b, double *out);
+/* Y_2^P of Eq. (30): the width of the polymer distribution across the flow,
+ * read for the reverse-Poiseuille box as two channels of width L_y/2 centred
+ * at L_y/4 and 3 L_y/4, y the distance from the nearest centre, rows at
+ * (y + 1/2) dx: *out = sqrt(sum y^2 Phi_P / (phi_p sum y^2)); 1 for a
+ * uniform distribution, below 1 when polymer gathers at the channel centres. */
+int epd_lb_width(epd_lb *h, int32_t run, double *out);
+/* Particles (Sec. 4): connected clusters of sites with Phi_P >= threshold
+ * (0.5 in the paper; must be > 0), sites connected to their 4 nearest
+ * neighbours across the periodic boundaries, numbered in the order of each
+ * cluster's first site (row-major).  *count = the number of particles; for
+ * particle k < max_particles, stats[10 k + 0..9] = sites, content
+ * N = sum Phi_P, centre x, centre y (in R_G, in [0, L)), G_xx, G_xy, G_yy of
+ * the gyration tensor of Eq. (27) (site positions (x, y) dx, separations the
+ * shortest periodic ones: exact for particles narrower than half the box),
+ * R and c of Eq. (28), c_rel of Eq. (29).  labels (ny*nx int32, may be NULL):
+ * each site's particle number or -1.  The tensor's moments are FP64 atomic
+ * sums (order-dependent in the last bits). */
+int epd_lb_particles(epd_lb *h, int32_t run, double threshold, int32_t max_particles, int32_t *count,
+                     double *stats, int32_t *labels);
+
 /* Text of the last error on the handle (never NULL). */
 const char *epd_lb_last_error(const epd_lb *h);
 

@@ -37,7 +37,7 @@ SYMBOLS = (
     "epd_lb_enable_timing", "epd_lb_kernel_times", "epd_prop_solve_noalloc", "epd_lb_tiles",
     "epd_sur_num_params", "epd_sur_workspace_bytes", "epd_sur_forward", "epd_sur_gradients", "epd_sur_train_step",
     "epd_lb_surrogate_workspace_bytes", "epd_lb_set_surrogate", "epd_lb_surrogate_stats", "epd_lb_fields_dev",
-    "epd_lb_set_inversion", "epd_lb_inversion_stats",
+    "epd_lb_set_inversion", "epd_lb_inversion_stats", "epd_lb_sigma_delta", "epd_lb_width", "epd_lb_particles",
 )
 
 
@@ -144,6 +144,9 @@ def lib():
             "epd_lb_fields_dev": (ctypes.c_int, [vp, i32, vp, vp]),
             "epd_lb_set_inversion": (ctypes.c_int, [vp, i32, ctypes.c_double]),
             "epd_lb_inversion_stats": (ctypes.c_int, [vp, i32, vp]),
+            "epd_lb_sigma_delta": (ctypes.c_int, [vp, i32, i32, vp]),
+            "epd_lb_width": (ctypes.c_int, [vp, i32, vp]),
+            "epd_lb_particles": (ctypes.c_int, [vp, i32, ctypes.c_double, i32, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -379,6 +382,35 @@ class EpdLb:
         out = np.empty(3)
         self._ck(lib().epd_lb_inversion_stats(self.h, run, _ptr(out)), "epd_lb_inversion_stats")
         return {"iterations": int(out[0]), "residual0": float(out[1]), "residual": float(out[2])}
+
+    def sigma_delta(self, run_a: int, run_b: int) -> float:
+        """sigma_Delta of Eq. (22) between two runs on the same grid."""
+        out = np.empty(1)
+        self._ck(lib().epd_lb_sigma_delta(self.h, run_a, run_b, _ptr(out)), "epd_lb_sigma_delta")
+        return float(out[0])
+
+    def width(self, run: int = 0) -> float:
+        """Y_2^P of Eq. (30)."""
+        out = np.empty(1)
+        self._ck(lib().epd_lb_width(self.h, run, _ptr(out)), "epd_lb_width")
+        return float(out[0])
+
+    PARTICLE_FIELDS = ("sites", "content", "cx", "cy", "gxx", "gxy", "gyy", "R", "c", "c_rel")
+
+    def particles(self, run: int = 0, threshold: float = 0.5, max_particles: int = 4096, labels: bool = False):
+        """(count, stats (min(count, max_particles), 10), labels (ny, nx) or
+        None) of the clusters with Phi_P >= threshold; columns as in
+        PARTICLE_FIELDS."""
+        ny, nx = self.shape(run)
+        cnt = np.zeros(1, dtype=np.int32)
+        st = np.zeros((max(max_particles, 1), 10))
+        lab = np.empty((ny, nx), dtype=np.int32) if labels else None
+        self._ck(lib().epd_lb_particles(self.h, run, float(threshold), int(max_particles),
+                                        cnt.ctypes.data_as(ctypes.c_void_p), st.ctypes.data_as(ctypes.c_void_p),
+                                        None if lab is None else lab.ctypes.data_as(ctypes.c_void_p)),
+                 "epd_lb_particles")
+        c = int(cnt[0])
+        return c, st[: min(c, max_particles)].copy(), lab
 
     def surrogate_stats(self) -> dict:
         out = np.empty(6)

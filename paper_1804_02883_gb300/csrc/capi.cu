@@ -929,6 +929,79 @@ extern "C" int epd_lb_observables(epd_lb *h, int32_t run, double *out)
 // (2n).
 static const uint64_t kMagic = 0x3130444C42445045ULL;  // "EPDLB01" little-endian
 
+// Phi of the current omega for the analysis calls (set_state leaves it stale).
+static int refresh_phi(epd_lb *h, Group &G)
+{
+    if (!G.phi_stale) return EPD_LB_OK;
+    CK(launch_solve(G, G.omega, G.phi, G.q, h->stream), "solve");
+    G.phi_stale = false;
+    return EPD_LB_OK;
+}
+
+extern "C" int epd_lb_sigma_delta(epd_lb *h, int32_t run_a, int32_t run_b, double *out)
+{
+    Group *Ga, *Gb;
+    int ma, mb;
+    if (!out) return fail(h, EPD_LB_EINVAL, "out is NULL");
+    if (int rc = locate(h, run_a, &Ga, &ma)) return rc;
+    if (int rc = locate(h, run_b, &Gb, &mb)) return rc;
+    if (Ga->g.nx != Gb->g.nx || Ga->g.ny != Gb->g.ny) return fail(h, EPD_LB_EINVAL, "the two runs have different grids");
+    if (int rc = refresh_phi(h, *Ga)) return rc;
+    if (int rc = refresh_phi(h, *Gb)) return rc;
+    const size_t n = (size_t)Ga->g.n;
+    CK(launch_sigma_delta(Ga->phi + (size_t)ma * 3 * n, Gb->phi + (size_t)mb * 3 * n, (long long)n, h->obs, h->stream), "sigma_Delta");
+    CK(cudaMemcpyAsync(out, h->obs, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "reading sigma_Delta");
+    CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    return EPD_LB_OK;
+}
+
+extern "C" int epd_lb_width(epd_lb *h, int32_t run, double *out)
+{
+    Group *G;
+    int m;
+    if (!out) return fail(h, EPD_LB_EINVAL, "out is NULL");
+    if (int rc = locate(h, run, &G, &m)) return rc;
+    if (int rc = refresh_phi(h, *G)) return rc;
+    CK(launch_width(*G, m, h->obs, h->stream), "Y_2^P");
+    CK(cudaMemcpyAsync(out, h->obs, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "reading Y_2^P");
+    CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    return EPD_LB_OK;
+}
+
+extern "C" int epd_lb_particles(epd_lb *h, int32_t run, double threshold, int32_t max_particles, int32_t *count,
+                                double *stats, int32_t *labels)
+{
+    Group *G;
+    int m;
+    if (!count) return fail(h, EPD_LB_EINVAL, "count is NULL");
+    if (!(threshold > 0.0) || !std::isfinite(threshold)) return fail(h, EPD_LB_EINVAL, "threshold must be positive");
+    if (max_particles < 0 || (max_particles > 0 && !stats)) return fail(h, EPD_LB_EINVAL, "bad max_particles or stats");
+    if (int rc = locate(h, run, &G, &m)) return rc;
+    if (int rc = refresh_phi(h, *G)) return rc;
+    const long long n = G->g.n;
+    const int maxp = max_particles;
+    const size_t sb = particles_scratch_bytes(n, std::max(maxp, 1)) + (labels ? (size_t)n * sizeof(int) : 0);
+    void *scratch = nullptr;
+    CK(cudaMallocAsync(&scratch, sb, h->stream), "cudaMallocAsync");
+    int *labels_dev = labels ? (int *)((char *)scratch + particles_scratch_bytes(n, std::max(maxp, 1))) : nullptr;
+    int *total_dev = nullptr;
+    double *stats_dev = nullptr;
+    cudaError_t e = launch_particles(*G, m, threshold, std::max(maxp, 1), scratch, labels_dev, &total_dev, &stats_dev, h->stream);
+    int total = 0, err = 0;
+    if (!e) e = cudaMemcpyAsync(&total, total_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (!e) e = cudaMemcpyAsync(&err, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (!e) e = cudaStreamSynchronize(h->stream);
+    const int nout = std::min(total, maxp);
+    if (!e && nout > 0) e = cudaMemcpy(stats, stats_dev, (size_t)nout * 10 * sizeof(double), cudaMemcpyDeviceToHost);
+    if (!e && labels) e = cudaMemcpy(labels, labels_dev, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFreeAsync(scratch, h->stream);
+    cudaStreamSynchronize(h->stream);
+    if (e) return cuda_fail(h, e, "particle analysis");
+    if (err & 8) return fail(h, EPD_LB_ECUDA, "the cluster labelling did not finish");
+    *count = total;
+    return EPD_LB_OK;
+}
+
 extern "C" int epd_lb_save(epd_lb *h, void *buf, size_t *len)
 {
     if (!h || !len) return EPD_LB_EINVAL;

@@ -146,6 +146,15 @@ cudaError_t launch_diffusion(Group &G, cudaStream_t s);        // phi_t, omega_t
 cudaError_t launch_force(Group &G, cudaStream_t s);            // phi, phi_t -> force
 cudaError_t launch_lb(Group &G, int parity, cudaStream_t s);   // pop[parity] -> pop[1-parity], vel
 
+// Analysis of Phi_P (analysis.cu): sigma_Delta of Eq. (22), Y_2^P of
+// Eq. (30), particles with their gyration tensors (Eqs. (27)-(29)).
+cudaError_t launch_sigma_delta(const double *phi_a, const double *phi_b, long long n, double *out_dev, cudaStream_t s);
+cudaError_t launch_width(const Group &G, int run, double *out_dev, cudaStream_t s);
+size_t particles_scratch_bytes(long long n, int maxp);
+// labels_dev (n int, may be null); *total_dev, *stats_dev point into scratch
+cudaError_t launch_particles(const Group &G, int run, double thr, int maxp, void *scratch, int *labels_dev,
+                             int **total_dev, double **stats_dev, cudaStream_t s);
+
 // State access helpers (one run).
 cudaError_t launch_gather_pre_collision(Group &G, int run, int parity, double *dst, cudaStream_t s);
 cudaError_t launch_scatter_pre_collision(Group &G, int run, int parity, const double *src, cudaStream_t s);
