@@ -31,7 +31,7 @@ typedef double complex cplx;
 /* Parameters of the problem statement (Sec. 2 and Sec. 3).  Lengths in R_G,
  * times in tau = R_G^2/D_S, the LB part in lattice units. */
 typedef struct {
-    int32_t nx, ny;       /* grid sites, each a power of two                 */
+    int32_t nx, ny;       /* grid sites per axis (even)                      */
     int32_t ns;           /* contour steps N_s                               */
     int32_t pad0;
     double dx, dt, rg;    /* grid spacing, time step, gyration radius R_G    */
@@ -52,7 +52,8 @@ typedef struct {
 #endif
 
 /* ------------------------------------------------------------------------ */
-/* FFT (textbook iterative radix-2 Cooley-Tukey) and the naive DFT.          */
+/* FFT (textbook iterative radix-2 Cooley-Tukey; the naive DFT for lengths   */
+/* that are not powers of two).                                               */
 /* Convention: forward  X[k] = sum_n x[n] exp(-2 pi i k n / N),             */
 /*             backward x[n] = sum_k X[k] exp(+2 pi i k n / N)   (no 1/N).  */
 /* ------------------------------------------------------------------------ */
@@ -77,6 +78,25 @@ void or_dft_naive(const cplx *x, cplx *out, int n, int sign)
 void or_fft1d(cplx *x, int n, int sign)
 {
     if (n <= 1) return;
+    if (n & (n - 1)) {
+        /* not a power of two (e.g. the paper's 150-site axes): the DFT by its
+         * definition, with the n roots exp(sign 2 pi i t / n) tabulated */
+        cplx *out = (cplx *)malloc(sizeof(cplx) * (size_t)n);
+        cplx *root = (cplx *)malloc(sizeof(cplx) * (size_t)n);
+        for (int t = 0; t < n; t++) {
+            double ang = sign * 2.0 * M_PI * (double)t / (double)n;
+            root[t] = cos(ang) + I * sin(ang);
+        }
+        for (int k = 0; k < n; k++) {
+            cplx acc = 0.0;
+            for (int j = 0; j < n; j++) acc += x[j] * root[(int)(((long long)k * j) % n)];
+            out[k] = acc;
+        }
+        memcpy(x, out, sizeof(cplx) * (size_t)n);
+        free(out);
+        free(root);
+        return;
+    }
     /* bit-reversal permutation */
     for (int i = 1, j = 0; i < n; i++) {
         int bit = n >> 1;

@@ -34,14 +34,16 @@ def test_homogeneous_closed_form(oracle_lib):
     assert np.allclose(phi[2], 1 - p.phi_p, rtol=1e-14, atol=0)
 
 
-@pytest.mark.parametrize("mode", [(3, 0), (0, 2), (1, 3), (8, 0), (0, 4)])
-def test_single_fourier_mode_decay(oracle_lib, mode):
+@pytest.mark.parametrize("mode,grid", [((3, 0), (16, 8)), ((0, 2), (16, 8)), ((1, 3), (16, 8)), ((8, 0), (16, 8)),
+                                       ((0, 4), (16, 8)), ((15, 0), (30, 20)), ((2, 10), (30, 20)), ((7, 3), (30, 20))])
+def test_single_fourier_mode_decay(oracle_lib, mode, grid):
     # T2: with omega = 0 each contour step multiplies a Fourier mode by
     # exp(-R_G^2 k^2 ds) exactly, so after the whole chain the amplitude is
     # eps exp(-R_G^2 k^2).  A non-square grid separates the two axes; mode
-    # (8, 0) is the x-Nyquist mode of the 16-wide grid (k = pi/dx).
+    # (8, 0) is the x-Nyquist mode of the 16-wide grid (k = pi/dx); the 30 x 20
+    # grid takes the DFT of lengths that are not powers of two.
     mx, my = mode
-    p = O.Params(nx=16, ny=8, ns=10, rg=0.7)
+    p = O.Params(nx=grid[0], ny=grid[1], ns=10, rg=0.7)
     x = np.arange(p.nx) * p.dx
     y = np.arange(p.ny) * p.dx
     kx = 2 * np.pi * mx / (p.nx * p.dx)
@@ -116,11 +118,12 @@ def test_block_boundary_rounding(oracle_lib):
     assert O.n_a(O.Params(ns=64, f_a=0.5)) == 32
 
 
-def test_dense_matrix_brute_force(oracle_lib):
-    # Brute force on a 4x8 grid, N_s = 4: the Laplacian as a dense matrix
-    # built from the DFT definition, exp(R_G^2 ds L) by scipy's expm, the
-    # contour recursion with dense matrices, trapezoid sums.
-    p = O.Params(nx=8, ny=4, ns=4, f_a=0.5, phi_p=0.2, rg=0.9)
+@pytest.mark.parametrize("nx,ny", [(8, 4), (10, 6)])
+def test_dense_matrix_brute_force(oracle_lib, nx, ny):
+    # Brute force on a 4x8 (and a 6x10) grid, N_s = 4: the Laplacian as a
+    # dense matrix built from the DFT definition, exp(R_G^2 ds L) by scipy's
+    # expm, the contour recursion with dense matrices, trapezoid sums.
+    p = O.Params(nx=nx, ny=ny, ns=4, f_a=0.5, phi_p=0.2, rg=0.9)
     n = p.n
     rng = np.random.default_rng(8)
     omega = 0.4 * rng.standard_normal((3, p.ny, p.nx))
