@@ -60,31 +60,35 @@ size_t carve_group(Group &G, char *base, size_t off)
     G.f0_bulk = take(R * tb);
     G.stage = (double *)take(std::max<size_t>(9 * n, 2 * R + 16) * sizeof(double));
     G.chain = take(R * n * 2 * tb);
-    G.hist_full = stream8_eligible(G.prec, G.g.logx, G.g.logy);
+    G.hist_full = G.g.pow2 && stream8_eligible(G.prec, G.g.logx, G.g.logy);
     G.hist = take(R * (size_t)(G.hist_full ? G.g.ns + 1 : G.g.half_lo + 1) * n * 2 * tb);
     G.efac = take(R * n * 2 * tb);
     G.pop[0] = take(R * 9 * n * tb);
     G.pop[1] = take(R * 9 * n * tb);
     G.vel = take(R * n * 2 * tb);
     G.force = take(R * n * 2 * tb);
-    G.twx = take((size_t)G.g.nx / 2 * 2 * tb);
-    G.twy = take((size_t)G.g.ny / 2 * 2 * tb);
+    G.twx = take((size_t)G.g.nx * 2 * tb);
+    G.twy = take((size_t)G.g.ny * 2 * tb);
     G.kx = take((size_t)G.g.nx * tb);
     G.ky = take((size_t)G.g.ny * tb);
-    G.twx_d = (double2 *)take((size_t)G.g.nx / 2 * sizeof(double2));
-    G.twy_d = (double2 *)take((size_t)G.g.ny / 2 * sizeof(double2));
-    G.twx_full = (float2 *)take((size_t)G.g.nx * sizeof(float2));
-    G.twy_full = (float2 *)take((size_t)G.g.ny * sizeof(float2));
-    G.tab8x = (float2 *)take((size_t)tabs_total(G.g.logx) * sizeof(float2));
-    G.tab8y = (float2 *)take((size_t)tabs_total(G.g.logy) * sizeof(float2));
-    G.tab16x = best_mr(G.g.logx) == 4 ? (float2 *)take((size_t)tabs_total(G.g.logx, 4) * sizeof(float2)) : nullptr;
-    G.tab16y = best_mr(G.g.logy) == 4 ? (float2 *)take((size_t)tabs_total(G.g.logy, 4) * sizeof(float2)) : nullptr;
+    G.twx_d = (double2 *)take((size_t)G.g.nx * sizeof(double2));
+    G.twy_d = (double2 *)take((size_t)G.g.ny * sizeof(double2));
+    // radix-8/16 and cluster tables: power-of-two axes only
+    G.twx_full = G.twy_full = G.tab8x = G.tab8y = G.tab16x = G.tab16y = nullptr;
+    if (G.g.pow2) {
+        G.twx_full = (float2 *)take((size_t)G.g.nx * sizeof(float2));
+        G.twy_full = (float2 *)take((size_t)G.g.ny * sizeof(float2));
+        G.tab8x = (float2 *)take((size_t)tabs_total(G.g.logx) * sizeof(float2));
+        G.tab8y = (float2 *)take((size_t)tabs_total(G.g.logy) * sizeof(float2));
+        G.tab16x = best_mr(G.g.logx) == 4 ? (float2 *)take((size_t)tabs_total(G.g.logx, 4) * sizeof(float2)) : nullptr;
+        G.tab16y = best_mr(G.g.logy) == 4 ? (float2 *)take((size_t)tabs_total(G.g.logy, 4) * sizeof(float2)) : nullptr;
+    }
     // cluster solve (MIXED_FP32): stored states of both chains, and the
     // differential second solve's buffers
     G.hc = G.hd = G.rho = G.c2p = nullptr;
     // (decided from the parameters, not from a pointer: the dry run that
     // sizes the workspace carves with null pointers)
-    const bool cluster = G.prec == EPD_LB_MIXED_FP32 && cluster_shape_exists(G.g.logx, G.g.logy);
+    const bool cluster = G.prec == EPD_LB_MIXED_FP32 && G.g.pow2 && cluster_shape_exists(G.g.logx, G.g.logy);
     if (cluster) {
         const size_t hs = R * cluster_state_floats2(G.g.nx, G.g.ny, G.g.ns) * sizeof(float2);
         G.hc = take(hs);
@@ -154,6 +158,28 @@ static Group run_view(const Group &G, int r)
     return V;
 }
 
+static bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// Radix plan of an axis: radix 4 while it divides, then 2, 3, 5.
+static int radix_plan(int n, int *f)
+{
+    int k = 0;
+    for (int p : {4, 2, 3, 5})
+        while (n % p == 0 && k < kMaxFactors) {
+            f[k++] = p;
+            n /= p;
+        }
+    return k;
+}
+
+// Largest divisor of n not above cap (at least 1).
+static int divisor_at_most(int n, int cap)
+{
+    for (int d = std::max(1, std::min(n, cap)); d > 1; --d)
+        if (n % d == 0) return d;
+    return 1;
+}
+
 static double fstar_lattice(const epd_lb_params &p)
 {
     const double tau = p.rg * p.rg / p.d_s;
@@ -167,8 +193,11 @@ static void fill_geom(Group &G)
     GroupGeom &g = G.g;
     g.nx = p.nx;
     g.ny = p.ny;
-    g.logx = ilog2(p.nx);
-    g.logy = ilog2(p.ny);
+    g.pow2 = pow2(p.nx) && pow2(p.ny);
+    g.logx = g.pow2 ? ilog2(p.nx) : 0;
+    g.logy = g.pow2 ? ilog2(p.ny) : 0;
+    g.nfx = radix_plan(p.nx, g.fx);
+    g.nfy = radix_plan(p.ny, g.fy);
     g.ns = p.ns;
     g.na = (int)std::lround(p.f_a * (double)p.ns);
     g.half_lo = p.ns / 2;
@@ -204,19 +233,26 @@ static void default_shapes(Group &G)
     G.sh.cols_prop = std::min(nx, std::max(f32 ? 4 : 2, 2048 / ny));
     G.sh.rows_epd = std::max(1, std::min(ny, 2048 / nx));
     G.sh.cols_epd = std::min(nx, std::max(2, 2048 / ny));
+    if (!G.g.pow2) {  // tiles must divide the axes
+        G.sh.rows_prop = divisor_at_most(ny, G.sh.rows_prop);
+        G.sh.cols_prop = divisor_at_most(nx, G.sh.cols_prop);
+        G.sh.rows_epd = divisor_at_most(ny, G.sh.rows_epd);
+        G.sh.cols_epd = divisor_at_most(nx, G.sh.cols_epd);
+    }
 }
 
-// Twiddles exp(-2 pi i t / n), t < n/2, and Fourier factors
-// exp(-R_G^2 k^2 ds) / n of the propagator (Eq. (8)), on the host in FP64.
+// Twiddles exp(-2 pi i t / n), t < n (the radix-2 passes read t < n/2), and
+// Fourier factors exp(-R_G^2 k^2 ds) / n of the propagator (Eq. (8)), on the
+// host in FP64.
 template <typename T>
 static void host_tables(const Group &G, std::vector<T> &twx, std::vector<T> &twy, std::vector<T> &kx, std::vector<T> &ky,
                         std::vector<double> &twxd, std::vector<double> &twyd)
 {
     const double pi = 3.14159265358979323846;
     auto tw = [&](int n, std::vector<T> &out, std::vector<double> &outd) {
-        out.resize(n);
-        outd.resize(n);
-        for (int t = 0; t < n / 2; ++t) {
+        out.resize(2 * (size_t)n);
+        outd.resize(2 * (size_t)n);
+        for (int t = 0; t < n; ++t) {
             const double a = 2.0 * pi * (double)t / (double)n;
             outd[2 * t] = std::cos(a);
             outd[2 * t + 1] = -std::sin(a);
@@ -296,13 +332,21 @@ static cudaError_t upload_tables_e(Group &G, cudaStream_t s)
 
 void upload_tables(Group &G, cudaStream_t s) { (void)upload_tables_e(G, s); }
 
-static bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+// even lengths of the form 2^a 3^b 5^c (the mixed-radix transforms' radices)
+static bool smooth_even(int v)
+{
+    if (v < 2 || (v & 1)) return false;
+    for (int p : {2, 3, 5})
+        while (v % p == 0) v /= p;
+    return v == 1;
+}
 
 static std::string validate(const epd_lb_params &p)
 {
     char buf[256];
-    if (!pow2(p.nx) || !pow2(p.ny) || p.nx < kMinN || p.ny < kMinN || p.nx > kMaxN || p.ny > kMaxN) {
-        std::snprintf(buf, sizeof buf, "nx=%d, ny=%d: each must be a power of two in [%d, %d]", p.nx, p.ny, kMinN, kMaxN);
+    if (!smooth_even(p.nx) || !smooth_even(p.ny) || p.nx < kMinN || p.ny < kMinN || p.nx > kMaxN || p.ny > kMaxN) {
+        std::snprintf(buf, sizeof buf, "nx=%d, ny=%d: each must be even, of the form 2^a 3^b 5^c, in [%d, %d]", p.nx,
+                      p.ny, kMinN, kMaxN);
         return buf;
     }
     if (p.ns < 2 || p.ns > 512 || (p.ns & 1)) {
@@ -1167,12 +1211,12 @@ static size_t carve_solve(Group &G, char *base)
     G.chain = take(n * 2 * tb);
     G.hist = take((size_t)(G.g.half_lo + 1) * n * 2 * tb);
     G.efac = take(n * 2 * tb);
-    G.twx = take((size_t)G.g.nx / 2 * 2 * tb);
-    G.twy = take((size_t)G.g.ny / 2 * 2 * tb);
+    G.twx = take((size_t)G.g.nx * 2 * tb);
+    G.twy = take((size_t)G.g.ny * 2 * tb);
     G.kx = take((size_t)G.g.nx * tb);
     G.ky = take((size_t)G.g.ny * tb);
-    G.twx_d = (double2 *)take((size_t)G.g.nx / 2 * sizeof(double2));
-    G.twy_d = (double2 *)take((size_t)G.g.ny / 2 * sizeof(double2));
+    G.twx_d = (double2 *)take((size_t)G.g.nx * sizeof(double2));
+    G.twy_d = (double2 *)take((size_t)G.g.ny * sizeof(double2));
     return align_up(off);
 }
 
@@ -1226,7 +1270,7 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 // the symbol itself as an address).
 std::atomic<void *> g_noalloc_addr[kNoallocDevices];
 
-// Twiddles exp(-2 pi i t / n), t < n/2, and Fourier factors
+// Twiddles exp(-2 pi i t / n), t < n, and Fourier factors
 // exp(-R_G^2 k^2 ds) / n (Eq. (8)), computed on the device in FP64.
 template <typename T>
 __global__ void noalloc_tables(int nx, int ny, double dx, double rg, double ds, V2<T> *twx, V2<T> *twy, T *kx, T *ky)
@@ -1241,8 +1285,8 @@ __global__ void noalloc_tables(int nx, int ny, double dx, double rg, double ds, 
         const double k = 2.0 * 3.14159265358979323846 * (double)signed_bin(m, n) / ((double)n * dx);
         out[m] = (T)(exp(-rg * rg * k * k * ds) / (double)n);
     };
-    if (i < nx / 2) twiddle(i, nx, twx);
-    if (i < ny / 2) twiddle(i, ny, twy);
+    if (i < nx) twiddle(i, nx, twx);
+    if (i < ny) twiddle(i, ny, twy);
     if (i < nx) factor(i, nx, kx);
     if (i < ny) factor(i, ny, ky);
 }

@@ -76,6 +76,58 @@ __device__ __forceinline__ V2<T> *fft_smem(V2<T> *x, V2<T> *y, int logN, int log
     return x;
 }
 
+// Mixed-radix (radices 2, 3, 4, 5) Stockham transform of B sequences of
+// length N in shared memory, for axes that are not powers of two: the same
+// data layout as fft_smem (element t of sequence b at b * sb + t * sn).  fac
+// lists the radices (product N); tw holds exp(-2 pi i t / N) for all t < N.
+// Stage with radix p after the radices s = p_1 ... p_{k-1}: butterfly r < N/p
+// (q = r mod s, j = r / s) takes x[r + u N/p], u < p, forms their p-point DFT
+// X_v and writes X_v exp(-+2 pi i v j s / N) to y[j p s + v s + q]; the output
+// ends in natural order.
+template <typename T, bool INVERSE, bool BATCH_FAST>
+__device__ __forceinline__ V2<T> *fft_smem_mr(V2<T> *x, V2<T> *y, int N, int nf, const int *fac, int B, int sb, int sn,
+                                              const V2<T> *tw)
+{
+    int s = 1;
+    for (int st = 0; st < nf; ++st) {
+        const int p = fac[st], m = N / p, total = m * B;
+        for (int t = threadIdx.x; t < total; t += blockDim.x) {
+            int b, r;
+            if (BATCH_FAST) {
+                b = t % B;
+                r = t / B;
+            } else {
+                b = t / m;
+                r = t % m;
+            }
+            const int q = r % s, j = r / s;
+            const int base = b * sb;
+            V2<T> in[5];
+            for (int u = 0; u < p; ++u) in[u] = x[base + (r + u * m) * sn];
+            for (int v = 0; v < p; ++v) {
+                V2<T> acc = in[0];
+                for (int u = 1; u < p; ++u) {
+                    V2<T> w = tw[(u * v * m) % N];  // p-th roots of unity
+                    if (INVERSE) w.y = -w.y;
+                    acc = cadd(acc, cmul(in[u], w));
+                }
+                if (v) {
+                    V2<T> w = tw[(v * j * s) % N];
+                    if (INVERSE) w.y = -w.y;
+                    acc = cmul(acc, w);
+                }
+                y[base + (j * p * s + v * s + q) * sn] = acc;
+            }
+        }
+        __syncthreads();
+        V2<T> *tmp = x;
+        x = y;
+        y = tmp;
+        s *= p;
+    }
+    return x;
+}
+
 // Block-wide sum of one double per thread (blockDim.x a multiple of 32, at
 // most 1024).  Fixed order: deterministic.  Result valid in thread 0.
 __device__ __forceinline__ double block_sum(double v, double *scratch32)

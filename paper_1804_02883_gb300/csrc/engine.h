@@ -14,8 +14,13 @@
 namespace epdlb {
 
 // Parameters every kernel of a group needs, by value.
+constexpr int kMaxFactors = 16;  // radices of one axis (mixed-radix transforms)
+
 struct GroupGeom {
-    int nx, ny, logx, logy;
+    int nx, ny, logx, logy;  // logx, logy: 0 unless both axes are powers of two
+    int pow2;                // both axes powers of two; else the mixed-radix radix-2-family passes
+    int nfx, nfy;            // radix plans (4, 2, 3, 5) of each axis for the mixed-radix transforms
+    int fx[kMaxFactors], fy[kMaxFactors];
     int ns, na;          // contour steps, A-block intervals round(f_a ns)
     int half_lo, half_hi;  // nodes 0..half_lo are stored; nodes >= half_hi accumulate
     int nruns;

@@ -40,7 +40,7 @@ struct EpdK {
     const void *twx, *twy;  // twiddles of the transform type
     const float2 *tab8x, *tab8y;  // pass tables of each axis' best radix plan (FP32 radix-8/16 kernels)
     const float2 *tab16y, *tab8y_r8;  // column tables of the radix-16 and radix-8 plans (tile-dependent)
-    int rows, logc;
+    int rows, logc, cols;  // tile rows (row passes), columns and their log2 (column passes; logc when pow2)
     double kunit_x, kunit_y;  // 2 pi / (n dx) per axis
     double mu_ref[3];         // mu_I at the homogeneous composition, omega = 0
     double phibar[3];         // the homogeneous composition
@@ -93,7 +93,8 @@ __global__ void __launch_bounds__(kThreads) epd_row(EpdK k)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const GroupGeom &g = k.g;
-    const int nx = g.nx, logx = g.logx, rows = k.rows, tile = rows * nx;
+    const bool p2 = g.pow2;
+    const int nx = g.nx, logx = g.logx, rows = k.rows, tile = rows * nx, ntw = p2 ? nx / 2 : nx;
     V2<TT> *a = reinterpret_cast<V2<TT> *>(smem_raw);
     V2<TT> *b = a + tile;
     V2<TT> *tw = b + tile;
@@ -102,7 +103,7 @@ __global__ void __launch_bounds__(kThreads) epd_row(EpdK k)
     const long long base = (long long)blockIdx.x * tile;
     V2<TT> *cz = reinterpret_cast<V2<TT> *>(k.cz);
     const V2<TT> *twg = reinterpret_cast<const V2<TT> *>(k.twx);
-    for (int i = threadIdx.x; i < nx / 2; i += blockDim.x) tw[i] = twg[i];
+    for (int i = threadIdx.x; i < ntw; i += blockDim.x) tw[i] = twg[i];
     for (int i = threadIdx.x; i < tile; i += blockDim.x) {
         const long long s = base + i;
         V2<TT> v;
@@ -127,15 +128,16 @@ __global__ void __launch_bounds__(kThreads) epd_row(EpdK k)
         a[i] = v;
     }
     __syncthreads();
-    const int logb = ilog2(rows);
+    const int logb = p2 ? ilog2(rows) : 0;
     V2<TT> *r = a, *o = b;
     if (MODE != ROW_INV_FORCE) {
-        r = fft_smem<TT, false, false>(a, b, logx, logb, nx, 1, tw);
+        r = p2 ? fft_smem<TT, false, false>(a, b, logx, logb, nx, 1, tw)
+               : fft_smem_mr<TT, false, false>(a, b, nx, g.nfx, g.fx, rows, nx, 1, tw);
         o = (r == a) ? b : a;
         if (MODE != ROW_FWD_S) {
             const TT unit = (TT)k.kunit_x, inv_n = (TT)(1.0 / (double)nx);
             for (int i = threadIdx.x; i < tile; i += blockDim.x) {
-                const int m = i & (nx - 1);
+                const int m = p2 ? i & (nx - 1) : i % nx;
                 V2<TT> v = r[i];
                 if (MODE == ROW_GRAD || MODE == ROW_DIVX) {  // i kx / nx
                     const TT kk = kvec_odd<TT>(m, nx, unit) * inv_n;
@@ -149,7 +151,9 @@ __global__ void __launch_bounds__(kThreads) epd_row(EpdK k)
             __syncthreads();
         }
     }
-    if (MODE != ROW_FWD_S) r = fft_smem<TT, true, false>(r, o, logx, logb, nx, 1, tw);
+    if (MODE != ROW_FWD_S)
+        r = p2 ? fft_smem<TT, true, false>(r, o, logx, logb, nx, 1, tw)
+               : fft_smem_mr<TT, true, false>(r, o, nx, g.nfx, g.fx, rows, nx, 1, tw);
     for (int i = threadIdx.x; i < tile; i += blockDim.x) {
         const long long s = base + i;
         if (MODE == ROW_INV_FORCE) {
@@ -168,17 +172,21 @@ __global__ void __launch_bounds__(kThreads) epd_col(EpdK k)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const GroupGeom &g = k.g;
-    const int ny = g.ny, nx = g.nx, logy = g.logy, logc = k.logc, C = 1 << logc, tile = ny << logc;
+    const bool p2 = g.pow2;
+    const int ny = g.ny, nx = g.nx, logy = g.logy, logc = k.logc, C = k.cols, tile = ny * C, ntw = p2 ? ny / 2 : ny;
     V2<TT> *a = reinterpret_cast<V2<TT> *>(smem_raw);
     V2<TT> *b = a + tile;
     V2<TT> *tw = b + tile;
-    const int run = blockIdx.y, pair = blockIdx.z, x0 = blockIdx.x << logc;
+    const int run = blockIdx.y, pair = blockIdx.z, x0 = blockIdx.x * C;
+    // row and column of tile element i
+    auto row_of = [&](int i) { return p2 ? i >> logc : i / C; };
+    auto col_of = [&](int i) { return p2 ? i & (C - 1) : i % C; };
     const long long n = g.n;
     V2<TT> *cz = reinterpret_cast<V2<TT> *>(k.cz);
     const V2<TT> *twg = reinterpret_cast<const V2<TT> *>(k.twy);
-    for (int i = threadIdx.x; i < ny / 2; i += blockDim.x) tw[i] = twg[i];
+    for (int i = threadIdx.x; i < ntw; i += blockDim.x) tw[i] = twg[i];
     for (int i = threadIdx.x; i < tile; i += blockDim.x) {
-        const long long s = (long long)(i >> logc) * nx + x0 + (i & (C - 1));
+        const long long s = (long long)row_of(i) * nx + x0 + col_of(i);
         V2<TT> v;
         if (MODE == COL_CONVECT) {
             const double *om = k.omega + (size_t)run * 3 * n;
@@ -196,12 +204,13 @@ __global__ void __launch_bounds__(kThreads) epd_col(EpdK k)
         a[i] = v;
     }
     __syncthreads();
-    V2<TT> *r = fft_smem<TT, false, true>(a, b, logy, logc, 1, C, tw);
+    V2<TT> *r = p2 ? fft_smem<TT, false, true>(a, b, logy, logc, 1, C, tw)
+                   : fft_smem_mr<TT, false, true>(a, b, ny, g.nfy, g.fy, C, 1, C, tw);
     V2<TT> *o = (r == a) ? b : a;
     const TT uy = (TT)k.kunit_y, ux = (TT)k.kunit_x, inv_n = (TT)(1.0 / (double)ny);
     const TT cforce = (TT)(g.inv_beta_v * g.fstar / (g.dt * (double)ny));
     for (int i = threadIdx.x; i < tile; i += blockDim.x) {
-        const int my = i >> logc;
+        const int my = row_of(i);
         V2<TT> v = r[i];
         if (MODE == COL_CONVECT || MODE == COL_DIVY) {  // i ky / ny
             const TT kk = kvec_odd<TT>(my, ny, uy) * inv_n;
@@ -213,7 +222,7 @@ __global__ void __launch_bounds__(kThreads) epd_col(EpdK k)
             // f(k) = (1/(beta v)) S(k) / dt * i k / |k|^2, Eq. (20), in lattice units;
             // f_x + i f_y is real + i real, so one transform carries both:
             // multiply by c (i kx - ky) / |k|^2 and invert.
-            const int mx = x0 + (i & (C - 1));
+            const int mx = x0 + col_of(i);
             const TT kx = kvec<TT>(mx, nx, ux), ky = kvec<TT>(my, ny, uy);
             const TT k2 = kx * kx + ky * ky;
             if (k2 == (TT)0) {
@@ -226,9 +235,9 @@ __global__ void __launch_bounds__(kThreads) epd_col(EpdK k)
         r[i] = v;
     }
     __syncthreads();
-    r = fft_smem<TT, true, true>(r, o, logy, logc, 1, C, tw);
+    r = p2 ? fft_smem<TT, true, true>(r, o, logy, logc, 1, C, tw) : fft_smem_mr<TT, true, true>(r, o, ny, g.nfy, g.fy, C, 1, C, tw);
     for (int i = threadIdx.x; i < tile; i += blockDim.x) {
-        const long long s = (long long)(i >> logc) * nx + x0 + (i & (C - 1));
+        const long long s = (long long)row_of(i) * nx + x0 + col_of(i);
         if (MODE == COL_FORCE) {
             cz[((size_t)run * 4 + 2) * n + s] = r[i];
         } else if (MODE == COL_DIVY) {
@@ -543,7 +552,8 @@ static EpdK make_k(Group &G)
     k.tab16y = G.tab16y;
     k.tab8y_r8 = G.tab8y;
     k.rows = G.sh.rows_epd;
-    k.logc = ilog2(G.sh.cols_epd);
+    k.logc = G.g.pow2 ? ilog2(G.sh.cols_epd) : 0;
+    k.cols = G.sh.cols_epd;
     const double pi = 3.14159265358979323846;
     k.kunit_x = 2.0 * pi / ((double)G.g.nx * G.g.dx);
     k.kunit_y = 2.0 * pi / ((double)G.g.ny * G.g.dx);
@@ -560,8 +570,14 @@ static EpdK make_k(Group &G)
     return k;
 }
 
-template <typename TT> static size_t row_smem(const Group &G) { return (size_t)2 * G.sh.rows_epd * G.g.nx * sizeof(V2<TT>) + (G.g.nx / 2) * sizeof(V2<TT>); }
-template <typename TT> static size_t col_smem(const Group &G) { return (size_t)2 * G.sh.cols_epd * G.g.ny * sizeof(V2<TT>) + (G.g.ny / 2) * sizeof(V2<TT>); }
+template <typename TT> static size_t row_smem(const Group &G)
+{
+    return (size_t)2 * G.sh.rows_epd * G.g.nx * sizeof(V2<TT>) + (G.g.pow2 ? G.g.nx / 2 : G.g.nx) * sizeof(V2<TT>);
+}
+template <typename TT> static size_t col_smem(const Group &G)
+{
+    return (size_t)2 * G.sh.cols_epd * G.g.ny * sizeof(V2<TT>) + (G.g.pow2 ? G.g.ny / 2 : G.g.ny) * sizeof(V2<TT>);
+}
 
 template <typename TT> static cudaError_t aux_t(Group &G, cudaStream_t s)
 {

@@ -36,6 +36,20 @@ template <typename T> struct LbK {
     T gs, gb, gg;
 };
 
+// site -> (x, y): shift and mask when the axes are powers of two (logx > 0),
+// division otherwise; periodic neighbour of v on an axis of n sites
+__device__ __forceinline__ void site_xy(long long site, int nx, int logx, int &x, int &y)
+{
+    if (logx > 0) {
+        x = (int)(site & (nx - 1));
+        y = (int)(site >> logx);
+    } else {
+        x = (int)(site % nx);
+        y = (int)(site / nx);
+    }
+}
+__device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
 __host__ __device__ __forceinline__ double lb_weight(int i) { return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0); }
 
 template <typename T>
@@ -44,9 +58,10 @@ __global__ void __launch_bounds__(kThreads) lb_collide_stream(LbK<T> k)
     const int run = blockIdx.y;
     const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (site >= k.n) return;
-    const int x = (int)(site & (k.nx - 1)), y = (int)(site >> k.logx);
-    const int xm = (x - 1) & (k.nx - 1), xp = (x + 1) & (k.nx - 1);
-    const int ym = (y - 1) & (k.ny - 1), yp = (y + 1) & (k.ny - 1);
+    int x, y;
+    site_xy(site, k.nx, k.logx, x, y);
+    const int xm = wrap(x - 1, k.nx), xp = wrap(x + 1, k.nx);
+    const int ym = wrap(y - 1, k.ny), yp = wrap(y + 1, k.ny);
     const long long n = k.n;
     const T *src = k.pin + (size_t)run * 9 * n;
     // pull: population i arrives from site - c_i
@@ -192,7 +207,8 @@ __global__ void __launch_bounds__(kThreads) init_state(InitK k)
     const unsigned long long seed = k.seeds[run];
     const double amp = k.noise[run], a = k.f0_lat[run];
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i & (k.g.nx - 1)), y = (int)(i >> k.g.logx);
+        int x, y;
+        site_xy(i, k.g.nx, k.g.logx, x, y);
         for (int sp = 0; sp < 3; ++sp) {
             const unsigned long long ctr = ((unsigned long long)sp * k.g.ny + y) * (unsigned long long)k.g.nx + x;
             k.omega[((size_t)run * 3 + sp) * n + i] = amp * uniform_pm1(seed, ctr);
@@ -200,7 +216,7 @@ __global__ void __launch_bounds__(kThreads) init_state(InitK k)
         // post-collision populations at t = -1, so that the first pull sees the
         // pre-collision equilibrium with j = v(y) - f_P(y)/2 at every site
         for (int q = 0; q < 9; ++q) {
-            const int yy = (y + c_cy[q]) & (k.g.ny - 1);
+            const int yy = wrap(y + c_cy[q], k.g.ny);
             const double v = steady_profile(k.g, a, yy);
             const double fp = (yy < k.g.ny / 2) ? -a : a;
             const double jx = v - 0.5 * fp;
@@ -260,8 +276,9 @@ __global__ void gather_pre(const T *post, double *dst, int nx, int ny, int logx,
     const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int q = blockIdx.y;
     if (site >= n) return;
-    const int x = (int)(site & (nx - 1)), y = (int)(site >> logx);
-    const int sx = (x - c_cx[q]) & (nx - 1), sy = (y - c_cy[q]) & (ny - 1);
+    int x, y;
+    site_xy(site, nx, logx, x, y);
+    const int sx = wrap(x - c_cx[q], nx), sy = wrap(y - c_cy[q], ny);
     dst[(size_t)q * n + site] = (double)post[(size_t)q * n + (long long)sy * nx + sx] + lb_weight(q);
 }
 
@@ -271,8 +288,9 @@ __global__ void scatter_pre(T *post, const double *src, int nx, int ny, int logx
     const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int q = blockIdx.y;
     if (site >= n) return;
-    const int x = (int)(site & (nx - 1)), y = (int)(site >> logx);
-    const int sx = (x + c_cx[q]) & (nx - 1), sy = (y + c_cy[q]) & (ny - 1);
+    int x, y;
+    site_xy(site, nx, logx, x, y);
+    const int sx = wrap(x + c_cx[q], nx), sy = wrap(y + c_cy[q], ny);
     post[(size_t)q * n + site] = (T)(src[(size_t)q * n + (long long)sy * nx + sx] - lb_weight(q));
 }
 

@@ -34,7 +34,7 @@ template <typename T> struct PropK {
     double *ia, *ib, *part;
     const V2<T> *twx, *twy;
     const T *kx, *ky;
-    int rows, logc;
+    int rows, logc, cols;  // tile rows (row pass), columns and their log2 (column pass; logc when pow2)
 };
 
 // Trapezoid weights on [0, s_{N_A}] (block A) and [s_{N_A}, 1] (block B).
@@ -95,29 +95,33 @@ __global__ void __launch_bounds__(kThreads) prop_start(PropK<T> k)
     }
 }
 
-// Column pass: Ty = IFFT_y Ky FFT_y on a tile of 2^logc adjacent columns.
+// Column pass: Ty = IFFT_y Ky FFT_y on a tile of C adjacent columns (radix-2
+// transforms on power-of-two grids, mixed-radix ones otherwise).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) prop_col(PropK<T> k)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int ny = k.g.ny, nx = k.g.nx, logy = k.g.logy, logc = k.logc, C = 1 << logc;
-    const int tile = ny << logc;
+    const bool p2 = k.g.pow2;
+    const int ny = k.g.ny, nx = k.g.nx, logy = k.g.logy, logc = k.logc, C = k.cols;
+    const int tile = ny * C, ntw = p2 ? ny / 2 : ny;
     V2<T> *a = reinterpret_cast<V2<T> *>(smem_raw);
     V2<T> *b = a + tile;
     V2<T> *tw = b + tile;
-    T *ky = reinterpret_cast<T *>(tw + ny / 2);
-    const int run = blockIdx.y, x0 = blockIdx.x << logc;
+    T *ky = reinterpret_cast<T *>(tw + ntw);
+    const int run = blockIdx.y, x0 = blockIdx.x * C;
     V2<T> *data = k.chain + (size_t)run * k.g.n;
-    for (int i = threadIdx.x; i < tile; i += blockDim.x) a[i] = data[(size_t)(i >> logc) * nx + x0 + (i & (C - 1))];
-    for (int i = threadIdx.x; i < ny / 2; i += blockDim.x) tw[i] = k.twy[i];
+    auto at = [&](int i) { return p2 ? (size_t)(i >> logc) * nx + x0 + (i & (C - 1)) : (size_t)(i / C) * nx + x0 + i % C; };
+    for (int i = threadIdx.x; i < tile; i += blockDim.x) a[i] = data[at(i)];
+    for (int i = threadIdx.x; i < ntw; i += blockDim.x) tw[i] = k.twy[i];
     for (int i = threadIdx.x; i < ny; i += blockDim.x) ky[i] = k.ky[i];
     __syncthreads();
-    V2<T> *r = fft_smem<T, false, true>(a, b, logy, logc, 1, C, tw);
+    V2<T> *r = p2 ? fft_smem<T, false, true>(a, b, logy, logc, 1, C, tw)
+                  : fft_smem_mr<T, false, true>(a, b, ny, k.g.nfy, k.g.fy, C, 1, C, tw);
     V2<T> *o = (r == a) ? b : a;
-    for (int i = threadIdx.x; i < tile; i += blockDim.x) r[i] = cscale(r[i], ky[i >> logc]);
+    for (int i = threadIdx.x; i < tile; i += blockDim.x) r[i] = cscale(r[i], ky[p2 ? i >> logc : i / C]);
     __syncthreads();
-    r = fft_smem<T, true, true>(r, o, logy, logc, 1, C, tw);
-    for (int i = threadIdx.x; i < tile; i += blockDim.x) data[(size_t)(i >> logc) * nx + x0 + (i & (C - 1))] = r[i];
+    r = p2 ? fft_smem<T, true, true>(r, o, logy, logc, 1, C, tw) : fft_smem_mr<T, true, true>(r, o, ny, k.g.nfy, k.g.fy, C, 1, C, tw);
+    for (int i = threadIdx.x; i < tile; i += blockDim.x) data[at(i)] = r[i];
 }
 
 // Row pass producing contour node m (1 <= m <= ns): Tx, node factors, history
@@ -127,26 +131,28 @@ __global__ void __launch_bounds__(kThreads) prop_row(PropK<T> k, int m)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
+    const bool p2 = k.g.pow2;
     const int nx = k.g.nx, logx = k.g.logx, rows = k.rows;
-    const int tile = rows * nx;
+    const int tile = rows * nx, ntw = p2 ? nx / 2 : nx;
     V2<T> *a = reinterpret_cast<V2<T> *>(smem_raw);
     V2<T> *b = a + tile;
     V2<T> *tw = b + tile;
-    T *kx = reinterpret_cast<T *>(tw + nx / 2);
+    T *kx = reinterpret_cast<T *>(tw + ntw);
     const int run = blockIdx.y;
     const long long n = k.g.n;
     const long long base = (long long)blockIdx.x * tile;
     V2<T> *data = k.chain + (size_t)run * n + base;
     for (int i = threadIdx.x; i < tile; i += blockDim.x) a[i] = data[i];
-    for (int i = threadIdx.x; i < nx / 2; i += blockDim.x) tw[i] = k.twx[i];
+    for (int i = threadIdx.x; i < ntw; i += blockDim.x) tw[i] = k.twx[i];
     for (int i = threadIdx.x; i < nx; i += blockDim.x) kx[i] = k.kx[i];
     __syncthreads();
-    const int logb = ilog2(rows);
-    V2<T> *r = fft_smem<T, false, false>(a, b, logx, logb, nx, 1, tw);
+    const int logb = p2 ? ilog2(rows) : 0;
+    V2<T> *r = p2 ? fft_smem<T, false, false>(a, b, logx, logb, nx, 1, tw)
+                  : fft_smem_mr<T, false, false>(a, b, nx, k.g.nfx, k.g.fx, rows, nx, 1, tw);
     V2<T> *o = (r == a) ? b : a;
-    for (int i = threadIdx.x; i < tile; i += blockDim.x) r[i] = cscale(r[i], kx[i & (nx - 1)]);
+    for (int i = threadIdx.x; i < tile; i += blockDim.x) r[i] = cscale(r[i], kx[p2 ? i & (nx - 1) : i % nx]);
     __syncthreads();
-    r = fft_smem<T, true, false>(r, o, logx, logb, nx, 1, tw);
+    r = p2 ? fft_smem<T, true, false>(r, o, logx, logb, nx, 1, tw) : fft_smem_mr<T, true, false>(r, o, nx, k.g.nfx, k.g.fx, rows, nx, 1, tw);
 
     const int ns = k.g.ns, na = k.g.na, hlo = k.g.half_lo, hhi = k.g.half_hi;
     const double ds = k.g.ds;
@@ -578,9 +584,17 @@ static int grid_for(long long n)
 }
 
 template <typename T>
-static size_t col_smem(const Group &G) { return (size_t)2 * (G.g.ny * G.sh.cols_prop) * sizeof(V2<T>) + (G.g.ny / 2) * sizeof(V2<T>) + G.g.ny * sizeof(T); }
+static size_t col_smem(const Group &G)
+{
+    return (size_t)2 * (G.g.ny * G.sh.cols_prop) * sizeof(V2<T>) + (G.g.pow2 ? G.g.ny / 2 : G.g.ny) * sizeof(V2<T>) +
+           G.g.ny * sizeof(T);
+}
 template <typename T>
-static size_t row_smem(const Group &G) { return (size_t)2 * (G.sh.rows_prop * G.g.nx) * sizeof(V2<T>) + (G.g.nx / 2) * sizeof(V2<T>) + G.g.nx * sizeof(T); }
+static size_t row_smem(const Group &G)
+{
+    return (size_t)2 * (G.sh.rows_prop * G.g.nx) * sizeof(V2<T>) + (G.g.pow2 ? G.g.nx / 2 : G.g.nx) * sizeof(V2<T>) +
+           G.g.nx * sizeof(T);
+}
 
 template <typename T>
 static cudaError_t solve_t(Group &G, const double *omega, double *phi, double *q, cudaStream_t s, const SolveProbe *probe)
@@ -599,7 +613,8 @@ static cudaError_t solve_t(Group &G, const double *omega, double *phi, double *q
     k.kx = reinterpret_cast<const T *>(G.kx);
     k.ky = reinterpret_cast<const T *>(G.ky);
     k.rows = G.sh.rows_prop;
-    k.logc = ilog2(G.sh.cols_prop);
+    k.logc = G.g.pow2 ? ilog2(G.sh.cols_prop) : 0;
+    k.cols = G.sh.cols_prop;
 
     const int pg = grid_for(g.n);
     prop_prep<T><<<dim3(pg, g.nruns), kThreads, 0, s>>>(g, omega, reinterpret_cast<V2<T> *>(G.efac), phi, G.part);

@@ -29,6 +29,9 @@
 #include "surrogate.h"
 
 namespace epdlb {
+
+// periodic index of a halo pixel (v in [-1, n]) on an axis of n pixels
+__device__ __forceinline__ int halo_wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 namespace sur {
 
 constexpr int TH = 8, TW = 16, TP = TH * TW;  // pixel tile
@@ -86,7 +89,7 @@ __global__ void __launch_bounds__(128) conv3x3(ConvArgs a)
     for (int e = tid; e < HH * HW * (KP / 8); e += 128) {
         const int pix = e / (KP / 8), ch = (e % (KP / 8)) * 8;
         const int hy = pix / HW, hx = pix % HW;
-        const int gy = (ty0 + hy - 1) & (a.ny - 1), gx = (tx0 + hx - 1) & (a.nx - 1);
+        const int gy = halo_wrap(ty0 + hy - 1, a.ny), gx = halo_wrap(tx0 + hx - 1, a.nx);
         *reinterpret_cast<uint4 *>(&tile[pix * KS + ch]) = *reinterpret_cast<const uint4 *>(&in[((size_t)gy * a.nx + gx) * KP + ch]);
     }
     __syncthreads();
@@ -197,7 +200,7 @@ __global__ void __launch_bounds__(288) conv3x3_dw(const __nv_bfloat16 *x, const 
         for (int e = tid; e < HH * HW * (CI / 8); e += 288) {
             const int pix = e / (CI / 8), ch = (e % (CI / 8)) * 8;
             const int hy = pix / HW, hx = pix % HW;
-            const int gy = (ty0 + hy - 1) & (ny - 1), gx = (tx0 + hx - 1) & (nx - 1);
+            const int gy = halo_wrap(ty0 + hy - 1, ny), gx = halo_wrap(tx0 + hx - 1, nx);
             *reinterpret_cast<uint4 *>(&tile[pix * CS + ch]) = *reinterpret_cast<const uint4 *>(&xin[((size_t)gy * nx + gx) * CI + ch]);
         }
         for (int e = tid; e < TP * CO; e += 288) {

@@ -36,8 +36,14 @@ def test_workspace_sizes_without_gpu():
     assert 3.5 * one < four < 4.5 * one
 
 
-@pytest.mark.parametrize("bad", [dict(nx=96), dict(ny=4), dict(ns=7), dict(ns=0), dict(precision=2),
-                                 dict(phi_p=1.0), dict(gamma_s=1.0), dict(dx=0.0), dict(nx=4096)])
+def test_mixed_radix_grids_accepted():
+    # even lengths of the form 2^a 3^b 5^c: the paper's own 150 x 150 grid
+    for nx, ny in ((150, 150), (96, 60), (30, 20), (2048, 1536)):
+        assert P.epd_lb_workspace_bytes([W.with_(W.plain_small(), nx=nx, ny=ny)]) > 0
+
+
+@pytest.mark.parametrize("bad", [dict(nx=14), dict(nx=75), dict(ny=4), dict(ns=7), dict(ns=0), dict(precision=2),
+                                 dict(phi_p=1.0), dict(gamma_s=1.0), dict(dx=0.0), dict(nx=4096), dict(ny=2250)])
 def test_invalid_parameters_rejected(bad):
     p = W.with_(W.plain_small(), **bad)
     with pytest.raises(P.EpdLbError) as ei:
