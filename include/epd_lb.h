@@ -65,8 +65,12 @@ enum {
 
 /*
  * Parameters of one run (Sec. 2 model, Sec. 3 and Sec. 4 set-up).
- *  nx, ny      grid sites, each a power of two in [8, 2048]; nx is the flow axis
- *  ns          contour steps N_s (even, 2..512)
+ *  nx, ny      grid sites per axis in [8, 2048], even and of the form 2^a 3^b 5^c
+ *              (the paper's 150 x 150 included); nx is the flow axis.  Axes that
+ *              are not powers of two take mixed-radix (2, 3, 4, 5) transforms in
+ *              the streaming passes.
+ *  ns          contour steps N_s in [2, 512]; even for MIXED_FP32 on
+ *              power-of-two grids (the paper's N_s = N = 17 runs elsewhere)
  *  precision   EPD_LB_PLAIN_FP64 or EPD_LB_MIXED_FP32
  *  dx, dt, rg  grid spacing, time step, gyration radius R_G (paper: 1/3, 0.002, 1)
  *  n_seg       segments per chain N (paper: 17); the Boltzmann factor is exp(-N w ds/2)

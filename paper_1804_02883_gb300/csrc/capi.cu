@@ -349,8 +349,13 @@ static std::string validate(const epd_lb_params &p)
                       p.ny, kMinN, kMaxN);
         return buf;
     }
-    if (p.ns < 2 || p.ns > 512 || (p.ns & 1)) {
-        std::snprintf(buf, sizeof buf, "ns=%d: must be even and in [2, 512]", p.ns);
+    // the MIXED power-of-two paths (cluster-resident and radix-8 streaming
+    // solves) pair contour nodes symmetrically and need N_s even; the radix-2
+    // streaming solve (PLAIN_FP64, mixed-radix grids) takes any N_s, such as
+    // the paper's N_s = N = 17
+    const bool any_ns = p.precision == EPD_LB_PLAIN_FP64 || !(pow2(p.nx) && pow2(p.ny));
+    if (p.ns < 2 || p.ns > 512 || ((p.ns & 1) && !any_ns)) {
+        std::snprintf(buf, sizeof buf, "ns=%d: must be in [2, 512] (and even for MIXED_FP32 on power-of-two grids)", p.ns);
         return buf;
     }
     if (p.precision != EPD_LB_PLAIN_FP64 && p.precision != EPD_LB_MIXED_FP32) return "precision must be 0 (PLAIN_FP64) or 1 (MIXED_FP32)";

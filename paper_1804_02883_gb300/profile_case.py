@@ -18,6 +18,7 @@ WORKLOADS = {
     "ensemble32": lambda: W.ensemble_32(B.MIXED_FP32),
     "vesicle": lambda: [W.vesicle_1024x2048(B.MIXED_FP32)],
     "plain_small": lambda: [W.plain_small()],
+    "paper150": lambda: W.paper_150(B.MIXED_FP32),
 }
 
 

@@ -59,6 +59,23 @@ def vesicle_1024x2048(precision: int = MIXED_FP32, seed: int = 4, f0: float = 8e
                      f0=f0, noise_amp=1e-3, seed=seed)
 
 
+def paper_150(precision: int = MIXED_FP32, runs: int = 64, seed: int = 200) -> list[RunParams]:
+    """The paper's own system (Sec. 3, Sec. 4): 50 R_G x 50 R_G boxes of
+    150 x 150 sites, N = N_s = 17, q_A = 0.882 (15 of 17 contour intervals A),
+    polymer fraction 0.1, kappa_H = 1.176, chi_AB = 1.05, chi_AS = 1.20;
+    half droplet systems (chi_BS = 0.75), half vesicle systems
+    (chi_BS = -0.15), reverse-Poiseuille amplitudes log-spaced over the
+    paper's range 1e-5 ... 1e-3 f*, seeded +-1e-3 noise: an ensemble as the
+    paper averages over."""
+    out = []
+    half = runs // 2
+    for k in range(runs):
+        f0 = 1e-5 * 100.0 ** ((k % half) / max(1, half - 1))
+        out.append(RunParams(nx=150, ny=150, ns=17, precision=precision, f_a=0.882, phi_p=0.1,
+                             chi_bs=0.75 if k < half else -0.15, f0=f0, noise_amp=1e-3, seed=seed + k))
+    return out
+
+
 def with_(p: RunParams, **kw) -> RunParams:
     return dataclasses.replace(p, **kw)
 

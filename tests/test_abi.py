@@ -40,9 +40,12 @@ def test_mixed_radix_grids_accepted():
     # even lengths of the form 2^a 3^b 5^c: the paper's own 150 x 150 grid
     for nx, ny in ((150, 150), (96, 60), (30, 20), (2048, 1536)):
         assert P.epd_lb_workspace_bytes([W.with_(W.plain_small(), nx=nx, ny=ny)]) > 0
+    # odd N_s (the paper's N_s = N = 17) on the radix-2 streaming solve
+    assert P.epd_lb_workspace_bytes(W.paper_150(P.MIXED_FP32)) > 0
+    assert P.epd_lb_workspace_bytes([W.with_(W.plain_small(), ns=17)]) > 0
 
 
-@pytest.mark.parametrize("bad", [dict(nx=14), dict(nx=75), dict(ny=4), dict(ns=7), dict(ns=0), dict(precision=2),
+@pytest.mark.parametrize("bad", [dict(nx=14), dict(nx=75), dict(ny=4), dict(ns=7, precision=1), dict(ns=0), dict(precision=2),
                                  dict(phi_p=1.0), dict(gamma_s=1.0), dict(dx=0.0), dict(nx=4096), dict(ny=2250)])
 def test_invalid_parameters_rejected(bad):
     p = W.with_(W.plain_small(), **bad)

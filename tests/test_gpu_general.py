@@ -73,6 +73,30 @@ def test_single_step_fp64(nx, ny, ns):
     h.close()
 
 
+@pytest.mark.parametrize("prec,nx,ny", [(P.PLAIN_FP64, 30, 20), (P.MIXED_FP32, 30, 20), (P.PLAIN_FP64, 32, 32)])
+def test_odd_contour_count_step(prec, nx, ny):
+    # N_s = N = 17 with q_A = 0.882 (15 A intervals), the paper's own chain
+    r = P.RunParams(nx=nx, ny=ny, ns=17, precision=prec, f_a=0.882, phi_p=0.1, f0=10.0)
+    omega = W.random_omega(ny, nx, seed=25, amp=0.05)
+    pop = W.random_populations(ny, nx, seed=26)
+    vel = W.random_velocity(ny, nx, seed=27, amp=0.02)
+    h = P.EpdLb([r])
+    h.set_state(0, omega, pop, vel)
+    h.step(1)
+    h.sync()
+    p = oracle_params(r)
+    phi, q = O.solve(p, omega)
+    st = O.State(omega.copy(), pop.copy(), vel.copy(), phi, q, np.zeros((2, ny, nx)))
+    O.step(p, st)
+    gom, _, _ = h.get_state(0)
+    gphi, gq = h.densities(0)
+    tol = 1e-10 if prec == P.PLAIN_FP64 else 2e-6
+    assert fluct_err(gom, st.omega) < tol
+    assert rel_err(gphi, st.phi) < tol
+    assert rel_err(gq, st.q) < tol
+    h.close()
+
+
 def test_steps_mixed_precision_track_fp64():
     # MIXED against PLAIN on a 96 x 60 grid over 20 steps from the seeded quench
     base = P.RunParams(nx=96, ny=60, ns=12, precision=P.PLAIN_FP64, f_a=0.5, phi_p=0.2, f0=2.0, noise_amp=1e-3, seed=4)
