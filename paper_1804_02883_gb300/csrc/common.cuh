@@ -76,6 +76,34 @@ __device__ __forceinline__ V2<T> *fft_smem(V2<T> *x, V2<T> *y, int logN, int log
     return x;
 }
 
+// One radix-P butterfly of the mixed-radix Stockham transform below.  The
+// p-th roots are tw[k m] (m = N/P); (u v mod P) m and v j s stay below N.
+template <typename T, bool INVERSE, int P>
+__device__ __forceinline__ void fft_mr_butterfly(const V2<T> *x, V2<T> *y, const V2<T> *tw, int base, int r, int m, int s,
+                                                 int sn)
+{
+    const int q = r % s, j = r / s;
+    V2<T> in[P];
+#pragma unroll
+    for (int u = 0; u < P; ++u) in[u] = x[base + (r + u * m) * sn];
+#pragma unroll
+    for (int v = 0; v < P; ++v) {
+        V2<T> acc = in[0];
+#pragma unroll
+        for (int u = 1; u < P; ++u) {
+            V2<T> w = tw[((u * v) % P) * m];
+            if (INVERSE) w.y = -w.y;
+            acc = cadd(acc, cmul(in[u], w));
+        }
+        if (v) {
+            V2<T> w = tw[v * j * s];
+            if (INVERSE) w.y = -w.y;
+            acc = cmul(acc, w);
+        }
+        y[base + (j * P * s + v * s + q) * sn] = acc;
+    }
+}
+
 // Mixed-radix (radices 2, 3, 4, 5) Stockham transform of B sequences of
 // length N in shared memory, for axes that are not powers of two: the same
 // data layout as fft_smem (element t of sequence b at b * sb + t * sn).  fac
@@ -100,23 +128,12 @@ __device__ __forceinline__ V2<T> *fft_smem_mr(V2<T> *x, V2<T> *y, int N, int nf,
                 b = t / m;
                 r = t % m;
             }
-            const int q = r % s, j = r / s;
             const int base = b * sb;
-            V2<T> in[5];
-            for (int u = 0; u < p; ++u) in[u] = x[base + (r + u * m) * sn];
-            for (int v = 0; v < p; ++v) {
-                V2<T> acc = in[0];
-                for (int u = 1; u < p; ++u) {
-                    V2<T> w = tw[(u * v * m) % N];  // p-th roots of unity
-                    if (INVERSE) w.y = -w.y;
-                    acc = cadd(acc, cmul(in[u], w));
-                }
-                if (v) {
-                    V2<T> w = tw[(v * j * s) % N];
-                    if (INVERSE) w.y = -w.y;
-                    acc = cmul(acc, w);
-                }
-                y[base + (j * p * s + v * s + q) * sn] = acc;
+            switch (p) {
+            case 2: fft_mr_butterfly<T, INVERSE, 2>(x, y, tw, base, r, m, s, sn); break;
+            case 3: fft_mr_butterfly<T, INVERSE, 3>(x, y, tw, base, r, m, s, sn); break;
+            case 4: fft_mr_butterfly<T, INVERSE, 4>(x, y, tw, base, r, m, s, sn); break;
+            default: fft_mr_butterfly<T, INVERSE, 5>(x, y, tw, base, r, m, s, sn); break;
             }
         }
         __syncthreads();
