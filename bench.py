@@ -36,6 +36,24 @@ HBM_FALLBACK = 6800.0
 FP32_SMS, FP32_LANES, FP32_MHZ = 152, 128, 2070.0
 
 
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """The slowest rank's value (the MAX over ranks); x itself without a
+    process group."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank_step: float, steps: int, world: int, seconds: float) -> float:
+    """Whole-job throughput: every rank steps its own batch (replicas), so the
+    job processes world x the units of one rank in the slowest rank's time."""
+    return units_per_rank_step * steps * world / seconds
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -355,15 +373,10 @@ def main():
         barrier()
         wall = time.perf_counter() - t0
     h.sync()
-    dev_ms = float(sum(per_step))
-    if dist is not None:
-        t = torch.tensor([dev_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_ms = float(t.item())
-    units = units_per_step(runs) * args.steps * world
-    value = units / (dev_ms * 1e-3)
+    dev_ms = max_over_ranks(float(sum(per_step)), dist, "cuda")
+    value = job_rate(units_per_step(runs), args.steps, world, dev_ms * 1e-3)
     ms_per_step = dev_ms / args.steps
-    lb_mlups = sites_per_step(runs) * args.steps * world / (dev_ms * 1e-3) / 1e6
+    lb_mlups = job_rate(sites_per_step(runs), args.steps, world, dev_ms * 1e-3) / 1e6
 
     # kernel durations inside the timed steps (event nodes in the step graph)
     nsite = sites_per_step(runs)
@@ -426,12 +439,8 @@ def main():
         for k in range(len(runs)):
             h.densities_ptr(k, host_phi[k].data_ptr(), host_q[k].data_ptr())
     barrier()
-    e2e_t = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_t], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_t = float(t.item())
-    e2e = {"value": units_per_step(runs) * args.e2e_steps * world / e2e_t, "unit": UNIT,
+    e2e_t = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    e2e = {"value": job_rate(units_per_step(runs), args.e2e_steps, world, e2e_t), "unit": UNIT,
            "h2d_bytes_per_step": int(sum(3 * r.nx * r.ny * 8 for r in runs)),
            "d2h_bytes_per_step": int(sum(3 * r.nx * r.ny * 8 + 16 for r in runs))}
 
