@@ -123,6 +123,8 @@ def lib():
             "or_invert": (ctypes.c_int, [P, _DP, _DP, _DP, _DP, ctypes.c_int, ctypes.c_double, _DP]),
             "or_step_exact": (None, [P, _DP, _DP, _DP, _DP, _DP, _DP, ctypes.c_int, ctypes.c_double, _DP]),
             "or_sigma_delta": (ctypes.c_double, [P, _DP, _DP]),
+            "or_fft3d": (None, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+            "or_solve3d": (None, [P, ctypes.c_int, _DP, _DP, _DP]),
             "or_width": (ctypes.c_double, [P, _DP]),
             "or_particles": (ctypes.c_int, [P, _DP, ctypes.c_double, ctypes.POINTER(ctypes.c_int), _DP, ctypes.c_int]),
         }
@@ -197,6 +199,23 @@ def solve(p: Params, omega):
     phi = np.empty_like(omega)
     q = np.empty(2)
     lib().or_solve(ctypes.byref(p.c()), _d(omega), _d(phi), _d(q))
+    return phi, q
+
+
+def fft3d(x, sign: int = -1) -> np.ndarray:
+    a = np.ascontiguousarray(x, dtype=np.complex128).copy()
+    nz, ny, nx = a.shape
+    lib().or_fft3d(a.ctypes.data_as(ctypes.c_void_p), nz, ny, nx, sign)
+    return a
+
+
+def solve3d(p: Params, nz: int, omega):
+    """Densities Phi (3, nz, ny, nx) and (Q_P, Q_S) of the 3D single-chain
+    solve for fields omega (3, nz, ny, nx)."""
+    omega = _f64(omega).reshape(3, nz, p.ny, p.nx)
+    phi = np.empty_like(omega)
+    q = np.empty(2)
+    lib().or_solve3d(ctypes.byref(p.c()), int(nz), _d(omega), _d(phi), _d(q))
     return phi, q
 
 

@@ -311,6 +311,99 @@ void or_solve(const or_params *p, const double *omega, double *phi, double *q)
 }
 
 /* ------------------------------------------------------------------------ */
+/* The single-chain solve in three dimensions (the extension the paper names  */
+/* in Sec. 2 and Sec. 5): Eqs. (6)-(11) on an nz x ny x nx box, layout        */
+/* [z][y][x], the Fourier factor exp(-R_G^2 |k|^2 ds) with                    */
+/* |k|^2 = kx^2 + ky^2 + kz^2.                                                 */
+/* ------------------------------------------------------------------------ */
+
+/* 3D transform: all x rows, then all y columns, then all z pillars. */
+void or_fft3d(cplx *a, int nz, int ny, int nx, int sign)
+{
+    size_t plane = (size_t)nx * ny;
+    for (int z = 0; z < nz; z++) or_fft2d(a + (size_t)z * plane, ny, nx, sign);
+    cplx *col = (cplx *)malloc(sizeof(cplx) * (size_t)nz);
+    for (size_t i = 0; i < plane; i++) {
+        for (int z = 0; z < nz; z++) col[z] = a[(size_t)z * plane + i];
+        or_fft1d(col, nz, sign);
+        for (int z = 0; z < nz; z++) a[(size_t)z * plane + i] = col[z];
+    }
+    free(col);
+}
+
+static void propagate_chain3d(const or_params *p, int nz, const double *const *field_of_node, double *hist)
+{
+    int nx = p->nx, ny = p->ny, ns = p->ns;
+    size_t n = (size_t)nx * ny * nz;
+    double ds = 1.0 / (double)ns;
+    cplx *work = (cplx *)malloc(sizeof(cplx) * n);
+    double *kfac = (double *)malloc(sizeof(double) * n);
+    for (int z = 0; z < nz; z++)
+        for (int y = 0; y < ny; y++)
+            for (int x = 0; x < nx; x++) {
+                double kx = wavenumber(x, nx, p->dx), ky = wavenumber(y, ny, p->dx), kz = wavenumber(z, nz, p->dx);
+                kfac[((size_t)z * ny + y) * nx + x] = exp(-p->rg * p->rg * (kx * kx + ky * ky + kz * kz) * ds);
+            }
+    for (size_t i = 0; i < n; i++) hist[i] = 1.0;
+    for (int j = 0; j < ns; j++) {
+        const double *g = hist + (size_t)j * n;
+        double *gnext = hist + (size_t)(j + 1) * n;
+        const double *wj = field_of_node[j], *wj1 = field_of_node[j + 1];
+        for (size_t i = 0; i < n; i++) work[i] = exp(-p->n_seg * wj[i] * ds / 2.0) * g[i];
+        or_fft3d(work, nz, ny, nx, -1);
+        for (size_t i = 0; i < n; i++) work[i] *= kfac[i];
+        or_fft3d(work, nz, ny, nx, +1);
+        for (size_t i = 0; i < n; i++) gnext[i] = exp(-p->n_seg * wj1[i] * ds / 2.0) * creal(work[i]) / (double)n;
+    }
+    free(work);
+    free(kfac);
+}
+
+/* Densities of Eqs. (9)-(11) on the 3D box: omega [A, B, S][z][y][x] ->
+ * phi (same layout), q = (Q_P, Q_S) as spatial means.  The same readings as
+ * or_solve (junction node, trapezoid quadrature, g' from the B end). */
+void or_solve3d(const or_params *p, int nz, const double *omega, double *phi, double *q)
+{
+    int ns = p->ns, na = or_n_a(p);
+    size_t n = (size_t)p->nx * p->ny * nz;
+    double ds = 1.0 / (double)ns;
+    const double *w_a = omega, *w_b = omega + n, *w_s = omega + 2 * n;
+    double *g = (double *)malloc(sizeof(double) * n * (size_t)(ns + 1));
+    double *gp = (double *)malloc(sizeof(double) * n * (size_t)(ns + 1));
+    const double **fw = (const double **)malloc(sizeof(double *) * (size_t)(ns + 1));
+    const double **bw = (const double **)malloc(sizeof(double *) * (size_t)(ns + 1));
+    for (int j = 0; j <= ns; j++) {
+        fw[j] = (j < na) ? w_a : w_b;
+        bw[j] = ((ns - j) < na) ? w_a : w_b;
+    }
+    propagate_chain3d(p, nz, fw, g);
+    propagate_chain3d(p, nz, bw, gp);
+    double q_p = 0.0;
+    for (size_t i = 0; i < n; i++) q_p += g[(size_t)ns * n + i];
+    q_p /= (double)n;
+    for (size_t i = 0; i < n; i++) {
+        double ia = 0.0, ib = 0.0;
+        for (int j = 0; j <= ns; j++) {
+            double prod = g[(size_t)j * n + i] * gp[(size_t)(ns - j) * n + i];
+            ia += weight_a(j, na, ds) * prod;
+            ib += weight_b(j, na, ns, ds) * prod;
+        }
+        phi[i] = p->phi_p * ia / q_p;
+        phi[n + i] = p->phi_p * ib / q_p;
+    }
+    double q_s = 0.0;
+    for (size_t i = 0; i < n; i++) q_s += exp(-w_s[i]);
+    q_s /= (double)n;
+    for (size_t i = 0; i < n; i++) phi[2 * n + i] = (1.0 - p->phi_p) * exp(-w_s[i]) / q_s;
+    q[0] = q_p;
+    q[1] = q_s;
+    free(g);
+    free(gp);
+    free(fw);
+    free(bw);
+}
+
+/* ------------------------------------------------------------------------ */
 /* EPD dynamics: Sec. 2, Eqs. (1), (5), and App. C.                          */
 /* ------------------------------------------------------------------------ */
 
