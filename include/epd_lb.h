@@ -312,6 +312,23 @@ const char *epd_lb_last_error(const epd_lb *h);
 void epd_lb_destroy(epd_lb *h);
 
 /*
+ * Stateless single-chain solve on a 3D box, the extension the paper names in
+ * Sec. 2 and Sec. 5: Eqs. (6)-(11) on nz x ny x nx sites (layout
+ * [species][z][y][x]), the Fourier factor exp(-R_G^2 (kx^2 + ky^2 + kz^2) ds).
+ * p gives nx, ny and every other parameter as for the 2D solve; nz is even,
+ * of the form 2^a 3^b 5^c, at most 2048, and nx ny nz at most 2^22 sites.
+ * omega_dev (3 nz ny nx doubles) -> phi_dev (the same), q_dev[2] = (Q_P, Q_S).
+ * The streaming passes run over three views of the box (z pillars, y columns
+ * of each plane, x rows carrying the node factors, history and contour
+ * sums).  workspace_dev: epd_prop_solve3d_workspace_bytes bytes, 256-byte
+ * aligned; EPD_LB_EINVAL for an unsupported box, EPD_LB_ENOMEM for a short
+ * workspace.  Asynchronous on cuda_stream (may be NULL).
+ */
+int epd_prop_solve3d_workspace_bytes(const epd_lb_params *p, int32_t nz, size_t *bytes);
+int epd_prop_solve3d(const epd_lb_params *p, int32_t nz, const double *omega_dev, double *phi_dev, double *q_dev,
+                     void *workspace_dev, size_t workspace_bytes, void *cuda_stream);
+
+/*
  * Stateless single-chain solve on device pointers (Sec. 2, Eqs. (6)-(11)):
  * omega_dev (3*ny*nx doubles) -> phi_dev (3*ny*nx doubles), q_dev[2] =
  * (Q_P, Q_S).  workspace_dev of epd_prop_solve_workspace_bytes bytes holds the

@@ -16,5 +16,7 @@ from .binding import (  # noqa: F401
     epd_prop_solve,
     epd_prop_solve_noalloc,
     epd_prop_solve_workspace_bytes,
+    epd_prop_solve3d_workspace_bytes,
     lib,
+    prop_solve3d,
 )

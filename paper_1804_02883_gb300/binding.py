@@ -38,6 +38,7 @@ SYMBOLS = (
     "epd_sur_num_params", "epd_sur_workspace_bytes", "epd_sur_forward", "epd_sur_gradients", "epd_sur_train_step",
     "epd_lb_surrogate_workspace_bytes", "epd_lb_set_surrogate", "epd_lb_surrogate_stats", "epd_lb_fields_dev",
     "epd_lb_set_inversion", "epd_lb_inversion_stats", "epd_lb_sigma_delta", "epd_lb_width", "epd_lb_particles",
+    "epd_prop_solve3d_workspace_bytes", "epd_prop_solve3d",
 )
 
 
@@ -126,6 +127,8 @@ def lib():
             "epd_lb_destroy": (None, [vp]),
             "epd_prop_solve_workspace_bytes": (ctypes.c_int, [P, szp]),
             "epd_prop_solve": (ctypes.c_int, [P, vp, vp, vp, vp, ctypes.c_size_t, vp]),
+            "epd_prop_solve3d_workspace_bytes": (ctypes.c_int, [P, i32, szp]),
+            "epd_prop_solve3d": (ctypes.c_int, [P, i32, vp, vp, vp, vp, ctypes.c_size_t, vp]),
             "epd_lb_enable_timing": (ctypes.c_int, [vp, i32]),
             "epd_lb_kernel_times": (ctypes.c_int, [vp, vp]),
             "epd_lb_tiles": (ctypes.c_int, [vp, ctypes.c_int32, vp]),
@@ -197,6 +200,38 @@ def epd_prop_solve(run: RunParams, omega_dev: int, phi_dev: int, q_dev: int, wor
     rc = lib().epd_prop_solve(ctypes.byref(run.c()), omega_dev, phi_dev, q_dev, workspace_dev, workspace_bytes, stream)
     if rc:
         raise EpdLbError(rc, "epd_prop_solve")
+
+
+def epd_prop_solve3d_workspace_bytes(run: RunParams, nz: int) -> int:
+    n = ctypes.c_size_t()
+    rc = lib().epd_prop_solve3d_workspace_bytes(ctypes.byref(run.c()), int(nz), ctypes.byref(n))
+    if rc:
+        raise EpdLbError(rc, "epd_prop_solve3d_workspace_bytes")
+    return n.value
+
+
+def prop_solve3d(run: RunParams, omega):
+    """Single-chain solve on an nz x ny x nx box (omega: (3, nz, ny, nx) host
+    array): (Phi (3, nz, ny, nx), (Q_P, Q_S)).  Device memory from torch,
+    synchronous."""
+    import torch
+
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    nz = om.shape[1]
+    assert om.shape == (3, nz, run.ny, run.nx)
+    nb = epd_prop_solve3d_workspace_bytes(run, nz)
+    ws = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")
+    wptr = (ws.data_ptr() + 255) & ~255
+    od = torch.from_numpy(om).cuda()
+    pd = torch.empty_like(od)
+    qd = torch.empty(2, dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+    rc = lib().epd_prop_solve3d(ctypes.byref(run.c()), nz, od.data_ptr(), pd.data_ptr(), qd.data_ptr(), wptr, nb,
+                                st.cuda_stream)
+    if rc:
+        raise EpdLbError(rc, "epd_prop_solve3d")
+    st.synchronize()
+    return pd.cpu().numpy(), qd.cpu().numpy()
 
 
 def epd_prop_solve_noalloc(run: RunParams, omega_dev: int, phi_dev: int, q_dev: int, stream: int = 0) -> None:

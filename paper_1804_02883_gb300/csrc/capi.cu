@@ -1225,6 +1225,127 @@ static size_t carve_solve(Group &G, char *base)
     return align_up(off);
 }
 
+// ---------------------------------------------------------------------------
+// Stateless single-chain solve on a 3D box (nz x ny x nx).
+// ---------------------------------------------------------------------------
+
+constexpr long long kMaxSites3 = 1LL << 22;  // the row pass keeps one Q partial per 2048-site tile
+
+// Geometry, tiles and (with base) the workspace layout; 0 when the box is
+// not supported.
+static size_t solve3_layout(const epd_lb_params *p, int nz, Solve3 &S, char *base)
+{
+    if (!p || !validate(*p).empty() || !smooth_even(nz) || nz > kMaxN) return 0;
+    Group G = Group();
+    G.p = *p;
+    G.prec = p->precision;
+    fill_geom(G);
+    G.g.nruns = 1;
+    const int nx = p->nx, ny = p->ny;
+    const long long n3 = (long long)nx * ny * nz;
+    if (n3 > kMaxSites3) return 0;
+    const int nyz = ny * nz, nxy = nx * ny;
+    S.vy = G.g;  // y columns: nz planes as runs
+    S.vy.nruns = nz;
+    S.vy.n = (long long)nxy;
+    S.vx = G.g;  // x rows: ny nz rows of nx
+    S.vx.ny = nyz;
+    S.vx.n = n3;
+    S.vx.pow2 = pow2(nx) && pow2(nyz);
+    S.vx.logx = S.vx.pow2 ? ilog2(nx) : 0;
+    S.vx.logy = S.vx.pow2 ? ilog2(nyz) : 0;
+    S.vz = G.g;  // z pillars: nz rows of nx ny
+    S.vz.nx = nxy;
+    S.vz.ny = nz;
+    S.vz.n = n3;
+    S.vz.pow2 = pow2(nxy) && pow2(nz);
+    S.vz.logx = S.vz.pow2 ? ilog2(nxy) : 0;
+    S.vz.logy = S.vz.pow2 ? ilog2(nz) : 0;
+    S.vz.nfy = radix_plan(nz, S.vz.fy);
+    S.rows_x = divisor_at_most(nyz, std::max(1, 2048 / nx));
+    S.cols_y = divisor_at_most(nx, std::max(2, 2048 / ny));
+    S.cols_z = divisor_at_most(nxy, std::max(2, 2048 / nz));
+    if (nyz / S.rows_x > kMaxPart / 2) return 0;  // Q partials of the row pass
+    S.prec = p->precision;
+    if (solve3d_smem_max(S) > 200 * 1024) return 0;
+    const size_t tb = p->precision == EPD_LB_MIXED_FP32 ? sizeof(float) : sizeof(double);
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> void * {
+        off = align_up(off);
+        void *q = base ? base + off : nullptr;
+        off += bytes;
+        return q;
+    };
+    S.err = (int *)take(256);
+    S.ia = (double *)take((size_t)n3 * sizeof(double));
+    S.ib = (double *)take((size_t)n3 * sizeof(double));
+    S.part = (double *)take(kMaxPart * sizeof(double));
+    S.chain = take((size_t)n3 * 2 * tb);
+    S.hist = take((size_t)(G.g.half_lo + 1) * n3 * 2 * tb);
+    S.efac = take((size_t)n3 * 2 * tb);
+    S.twx = take((size_t)nx * 2 * tb);
+    S.twy = take((size_t)ny * 2 * tb);
+    S.twz = take((size_t)nz * 2 * tb);
+    S.kx = take((size_t)nx * tb);
+    S.ky = take((size_t)ny * tb);
+    S.kz = take((size_t)nz * tb);
+    return align_up(off);
+}
+
+// Twiddles exp(-2 pi i t / n), t < n, and factors exp(-R_G^2 k^2 ds) / n of one axis.
+template <typename T>
+static cudaError_t upload_axis(int n, double dx, double rg, double ds, void *tw, void *kf, cudaStream_t s)
+{
+    const double pi = 3.14159265358979323846;
+    std::vector<T> t(2 * (size_t)n), k((size_t)n);
+    for (int j = 0; j < n; ++j) {
+        const double a = 2.0 * pi * (double)j / (double)n;
+        t[2 * j] = (T)std::cos(a);
+        t[2 * j + 1] = (T)-std::sin(a);
+        const int mm = j <= n / 2 ? j : j - n;
+        const double kk = 2.0 * pi * (double)mm / ((double)n * dx);
+        k[j] = (T)(std::exp(-rg * rg * kk * kk * ds) / (double)n);
+    }
+    cudaError_t e = cudaMemcpyAsync(tw, t.data(), t.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(kf, k.data(), k.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaStreamSynchronize(s);  // the host vectors go out of scope
+    return e;
+}
+
+extern "C" int epd_prop_solve3d_workspace_bytes(const epd_lb_params *p, int32_t nz, size_t *bytes)
+{
+    Solve3 S;
+    if (!bytes) return EPD_LB_EINVAL;
+    const size_t b = solve3_layout(p, nz, S, nullptr);
+    if (!b) return EPD_LB_EINVAL;
+    *bytes = b;
+    return EPD_LB_OK;
+}
+
+extern "C" int epd_prop_solve3d(const epd_lb_params *p, int32_t nz, const double *omega_dev, double *phi_dev,
+                                double *q_dev, void *workspace_dev, size_t workspace_bytes, void *cuda_stream)
+{
+    Solve3 S;
+    if (!omega_dev || !phi_dev || !q_dev || !workspace_dev) return EPD_LB_EINVAL;
+    const size_t need = solve3_layout(p, nz, S, nullptr);
+    if (!need) return EPD_LB_EINVAL;
+    if (workspace_bytes < need || ((uintptr_t)workspace_dev & 255)) return EPD_LB_ENOMEM;
+    if (configure_kernels() != cudaSuccess) return EPD_LB_ECUDA;
+    solve3_layout(p, nz, S, (char *)workspace_dev);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const double ds = 1.0 / (double)p->ns;
+    cudaError_t e = cudaMemsetAsync(S.err, 0, sizeof(int), s);
+    auto up = [&](int n, void *tw, void *kf) {
+        return p->precision == EPD_LB_MIXED_FP32 ? upload_axis<float>(n, p->dx, p->rg, ds, tw, kf, s)
+                                                 : upload_axis<double>(n, p->dx, p->rg, ds, tw, kf, s);
+    };
+    if (!e) e = up(p->nx, S.twx, S.kx);
+    if (!e) e = up(p->ny, S.twy, S.ky);
+    if (!e) e = up(nz, S.twz, S.kz);
+    if (!e) e = launch_solve3d(S, omega_dev, phi_dev, q_dev, s);
+    return e ? EPD_LB_ECUDA : EPD_LB_OK;
+}
+
 static bool solve_group(const epd_lb_params *p, Group &G)
 {
     if (!p || !validate(*p).empty()) return false;

@@ -182,6 +182,22 @@ cudaError_t launch_cluster_solve(Group &G, cudaStream_t s, bool diff, int nprep_
                                  const SolveProbe *probe, const double *phi_ref = nullptr, const double *q_ref = nullptr);
 int cluster_ctas(const Group &G);
 
+// Single-chain solve on an nz x ny x nx box (layout [z][y][x]): the
+// streaming passes over three views of one array, z pillars (a 2D view with
+// nz rows of nx ny sites), y columns (nz planes as runs) and x rows (ny nz
+// rows) carrying the node factors, history and contour sums.
+struct Solve3 {
+    GroupGeom vx, vy, vz;        // the three views (vx holds the chain geometry)
+    int rows_x, cols_y, cols_z;  // tiles of the x-row, y-column and z-column passes
+    void *chain, *hist, *efac;   // bulk precision: [n3] complex, [half_lo + 1][n3] complex, [n3] complex
+    double *ia, *ib, *part;
+    void *twx, *twy, *twz, *kx, *ky, *kz;  // bulk precision tables (full twiddle tables)
+    int *err;
+    int prec;
+};
+cudaError_t launch_solve3d(const Solve3 &S, const double *omega, double *phi, double *q, cudaStream_t s);
+size_t solve3d_smem_max(const Solve3 &S);  // largest dynamic shared memory of the three passes
+
 // Kernel attributes (dynamic shared memory limits), once per process.
 cudaError_t configure_kernels();
 

@@ -16,6 +16,7 @@
 // chains run through the second half, node m of g meets node N_s - m of g' from
 // the history (and vice versa), and the trapezoid sums of Eqs. (9)-(10) are
 // accumulated in FP64 on the fly.
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <type_traits>
@@ -680,6 +681,72 @@ cudaError_t launch_solve_delta_at(Group &G, const double *omega, const double *o
 cudaError_t launch_solve_delta(Group &G, cudaStream_t s, const SolveProbe *probe)
 {
     return launch_solve_delta_at(G, G.omega, G.omega_t, G.phi_t, G.q_t, G.phi, G.q, s, probe);
+}
+
+// Single-chain solve on a 3D box: per contour step the z-column, y-column and
+// x-row passes (the Fourier factor exp(-R_G^2 |k|^2 ds) is the product of the
+// three axes' factors, each applied inside its own axis transform), the row
+// pass carrying the node factors, history and contour sums as in 2D.
+template <typename T>
+static size_t smem3(const GroupGeom &g, int rows, int cols, bool row)
+{
+    if (row) return (size_t)2 * rows * g.nx * sizeof(V2<T>) + (g.pow2 ? g.nx / 2 : g.nx) * sizeof(V2<T>) + g.nx * sizeof(T);
+    return (size_t)2 * g.ny * cols * sizeof(V2<T>) + (g.pow2 ? g.ny / 2 : g.ny) * sizeof(V2<T>) + g.ny * sizeof(T);
+}
+
+size_t solve3d_smem_max(const Solve3 &S)
+{
+    auto mx = [&](auto t) {
+        using T = decltype(t);
+        return std::max(smem3<T>(S.vx, S.rows_x, 0, true), std::max(smem3<T>(S.vy, 0, S.cols_y, false), smem3<T>(S.vz, 0, S.cols_z, false)));
+    };
+    return S.prec == EPD_LB_MIXED_FP32 ? mx(0.f) : mx(0.0);
+}
+
+template <typename T>
+static cudaError_t solve3d_t(const Solve3 &S, const double *omega, double *phi, double *q, cudaStream_t s)
+{
+    auto view = [&](const GroupGeom &g, const void *tw_row, const void *tw_col, const void *k_row, const void *k_col,
+                    int rows, int cols) {
+        PropK<T> k;
+        k.g = g;
+        k.chain = reinterpret_cast<V2<T> *>(S.chain);
+        k.hist = reinterpret_cast<V2<T> *>(S.hist);
+        k.efac = reinterpret_cast<const V2<T> *>(S.efac);
+        k.ia = S.ia;
+        k.ib = S.ib;
+        k.part = S.part;
+        k.twx = reinterpret_cast<const V2<T> *>(tw_row);
+        k.twy = reinterpret_cast<const V2<T> *>(tw_col);
+        k.kx = reinterpret_cast<const T *>(k_row);
+        k.ky = reinterpret_cast<const T *>(k_col);
+        k.rows = rows;
+        k.cols = cols;
+        k.logc = g.pow2 ? ilog2(cols) : 0;
+        return k;
+    };
+    const PropK<T> kx = view(S.vx, S.twx, S.twy, S.kx, S.ky, S.rows_x, 1);
+    const PropK<T> ky = view(S.vy, S.twx, S.twy, S.kx, S.ky, 1, S.cols_y);
+    const PropK<T> kz = view(S.vz, S.twx, S.twz, S.kx, S.kz, 1, S.cols_z);
+    const GroupGeom &g = S.vx;
+    const int pg = grid_for(g.n);
+    prop_prep<T><<<dim3(pg, 1), kThreads, 0, s>>>(g, omega, reinterpret_cast<V2<T> *>(S.efac), phi, S.part);
+    prop_start<T><<<dim3(pg, 1), kThreads, 0, s>>>(kx);
+    const dim3 gz(S.vz.nx / S.cols_z, 1), gy(S.vy.nx / S.cols_y, S.vy.nruns), gr(S.vx.ny / S.rows_x, 1);
+    const size_t sz = smem3<T>(S.vz, 0, S.cols_z, false), sy = smem3<T>(S.vy, 0, S.cols_y, false),
+                 sr = smem3<T>(S.vx, S.rows_x, 0, true);
+    for (int m = 1; m <= g.ns; ++m) {
+        prop_col<T><<<gz, kThreads, sz, s>>>(kz);
+        prop_col<T><<<gy, kThreads, sy, s>>>(ky);
+        prop_row<T><<<gr, kThreads, sr, s>>>(kx, m);
+    }
+    prop_finalize<<<dim3(pg, 1), kThreads, 0, s>>>(g, gr.x, pg, S.ia, S.ib, nullptr, nullptr, S.part, phi, q, S.err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solve3d(const Solve3 &S, const double *omega, double *phi, double *q, cudaStream_t s)
+{
+    return S.prec == EPD_LB_MIXED_FP32 ? solve3d_t<float>(S, omega, phi, q, s) : solve3d_t<double>(S, omega, phi, q, s);
 }
 
 cudaError_t configure_prop_kernels()
