@@ -125,6 +125,7 @@ def lib():
             "or_sigma_delta": (ctypes.c_double, [P, _DP, _DP]),
             "or_fft3d": (None, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
             "or_solve3d": (None, [P, ctypes.c_int, _DP, _DP, _DP]),
+            "or_lb3d_step": (None, [P, ctypes.c_int, _DP, _DP, _DP]),
             "or_width": (ctypes.c_double, [P, _DP]),
             "or_particles": (ctypes.c_int, [P, _DP, ctypes.c_double, ctypes.POINTER(ctypes.c_int), _DP, ctypes.c_int]),
         }
@@ -273,6 +274,22 @@ def lb_step(p: Params, pop, force_total):
     f = _f64(force_total).reshape(2, p.ny, p.nx)
     vel = np.empty((2, p.ny, p.nx))
     lib().or_lb_step(ctypes.byref(p.c()), _d(pop), _d(f), _d(vel))
+    return pop, vel
+
+
+D3Q19_C = np.array([(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1),
+                    (1, 1, 0), (-1, -1, 0), (1, -1, 0), (-1, 1, 0), (1, 0, 1), (-1, 0, -1), (1, 0, -1),
+                    (-1, 0, 1), (0, 1, 1), (0, -1, -1), (0, 1, -1), (0, -1, 1)])
+D3Q19_W = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+
+
+def lb3d_step(p: Params, nz: int, pop, force_total):
+    """One D3Q19 collide+stream on an nz x ny x nx box: (populations at t+1
+    (19, nz, ny, nx), velocity at the collision (3, nz, ny, nx))."""
+    pop = _f64(pop).reshape(19, nz, p.ny, p.nx).copy()
+    f = _f64(force_total).reshape(3, nz, p.ny, p.nx)
+    vel = np.empty((3, nz, p.ny, p.nx))
+    lib().or_lb3d_step(ctypes.byref(p.c()), int(nz), _d(pop), _d(f), _d(vel))
     return pop, vel
 
 

@@ -617,6 +617,91 @@ void or_lb_step(const or_params *p, double *pop, const double *force, double *ve
 }
 
 /* ------------------------------------------------------------------------ */
+/* D3Q19 collide-stream: the three-dimensional scheme the paper names for the */
+/* extension to 3D (Sec. 2), in the same mode form as the D2Q9 update above.  */
+/* ------------------------------------------------------------------------ */
+
+static const int C3[19][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0}, {0, 0, 1},  {0, 0, -1},
+                              {1, 1, 0},  {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 0, 1},  {-1, 0, -1}, {1, 0, -1},
+                              {-1, 0, 1}, {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+
+static double w3(int i) { return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0); }
+
+/* The hydrodynamic part of a population: the second-order expansion
+ *   w_i [rho + j.c_i / c_s^2 + (M : (c_i c_i - c_s^2 I)) / (2 c_s^4)]
+ * with M = Pi - rho c_s^2 I, which reproduces rho, j and Pi exactly on D3Q19;
+ * the rest of a population is its ghost part. */
+static double hydro3(int i, double rho, const double *j, const double m[3][3])
+{
+    double cj = 0.0, mq = 0.0;
+    for (int a = 0; a < 3; a++) {
+        cj += j[a] * C3[i][a];
+        for (int b = 0; b < 3; b++) mq += m[a][b] * ((double)(C3[i][a] * C3[i][b]) - (a == b ? CS2 : 0.0));
+    }
+    return w3(i) * (rho + cj / CS2 + mq / (2.0 * CS2 * CS2));
+}
+
+/* One D3Q19 update on an nz x ny x nx box ([19][z][y][x]): the collision of
+ * or_lb_step in d = 3 (u = (j + f/2)/rho; j* = j + f; the stress relaxes
+ * about rho c_s^2 I + rho u u, traceless part by gamma_s, trace by gamma_b;
+ * Sigma of Eq. (15) as printed, with its d = 3 constants 2/3 and 1/3; the
+ * ghost part scaled by gamma_g), then streaming n_i(r + c_i) = n_i*(r),
+ * periodic.  force: total force [3][z][y][x]; vel_out: u [3][z][y][x]. */
+void or_lb3d_step(const or_params *p, int nz, double *pop, const double *force, double *vel_out)
+{
+    int nx = p->nx, ny = p->ny;
+    size_t n = (size_t)nx * ny * nz;
+    double *post = (double *)malloc(sizeof(double) * 19 * n);
+    for (size_t s = 0; s < n; s++) {
+        double nl[19], rho = 0.0, j[3] = {0, 0, 0}, pi[3][3] = {{0}};
+        for (int i = 0; i < 19; i++) {
+            nl[i] = pop[(size_t)i * n + s];
+            rho += nl[i];
+            for (int a = 0; a < 3; a++) {
+                j[a] += nl[i] * C3[i][a];
+                for (int b = 0; b < 3; b++) pi[a][b] += nl[i] * C3[i][a] * C3[i][b];
+            }
+        }
+        double f[3], u[3];
+        for (int a = 0; a < 3; a++) {
+            f[a] = force[(size_t)a * n + s];
+            u[a] = (j[a] + 0.5 * f[a]) / rho;
+            vel_out[(size_t)a * n + s] = u[a];
+        }
+        double m_old[3][3], ms[3][3], js[3], neq[3][3], tr = 0.0, uf = 0.0;
+        for (int a = 0; a < 3; a++) {
+            uf += u[a] * f[a];
+            js[a] = j[a] + f[a];
+            for (int b = 0; b < 3; b++) {
+                m_old[a][b] = pi[a][b] - (a == b ? rho * CS2 : 0.0);
+                neq[a][b] = pi[a][b] - (rho * u[a] * u[b] + (a == b ? rho * CS2 : 0.0));
+            }
+            tr += neq[a][a];
+        }
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++) {
+                double d = a == b ? 1.0 : 0.0;
+                double relax = p->gamma_s * (neq[a][b] - d * tr / 3.0) + p->gamma_b * d * tr / 3.0;
+                double sigma = 0.5 * (1.0 + p->gamma_s) * (u[a] * f[b] + f[a] * u[b] - d * 2.0 / 3.0 * uf) +
+                               d * (1.0 + p->gamma_b) / 3.0 * uf;
+                ms[a][b] = rho * u[a] * u[b] + relax + sigma; /* Pi* - rho c_s^2 I */
+            }
+        for (int i = 0; i < 19; i++) {
+            double ghost = nl[i] - hydro3(i, rho, j, m_old);
+            post[(size_t)i * n + s] = hydro3(i, rho, js, ms) + p->gamma_g * ghost;
+        }
+    }
+    for (int i = 0; i < 19; i++)
+        for (int z = 0; z < nz; z++)
+            for (int y = 0; y < ny; y++)
+                for (int x = 0; x < nx; x++) {
+                    int xd = (x + C3[i][0] + nx) % nx, yd = (y + C3[i][1] + ny) % ny, zd = (z + C3[i][2] + nz) % nz;
+                    pop[(size_t)i * n + ((size_t)zd * ny + yd) * nx + xd] = post[(size_t)i * n + ((size_t)z * ny + y) * nx + x];
+                }
+    free(post);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Initial state: Sec. 3 (quench), Sec. 4 (flow initialised with Eq. (24)).  */
 /* ------------------------------------------------------------------------ */
 
