@@ -329,6 +329,23 @@ int epd_prop_solve3d(const epd_lb_params *p, int32_t nz, const double *omega_dev
                      void *workspace_dev, size_t workspace_bytes, void *cuda_stream);
 
 /*
+ * One D3Q19 collide-stream on an nz x ny x nx box (the three-dimensional LB
+ * scheme the paper names for the extension to 3D, Sec. 2), FP64: the
+ * collision in the mode form of the D2Q9 update (u = (j + f/2)/rho, j* =
+ * j + f, stress relaxed about rho c_s^2 I + rho u u by gamma_s and gamma_b of
+ * p, Sigma of Eq. (15) with its d = 3 constants, ghosts scaled by gamma_g),
+ * then streaming out_i(r + c_i) = n_i*(r), periodic.  pop_in_dev, pop_out_dev:
+ * 19 nz ny nx doubles, [i][z][y][x], velocity order 0:(0,0,0), 1-6:
+ * (+-1,0,0) (0,+-1,0) (0,0,+-1) in that order, 7-18: (1,1,0) (-1,-1,0)
+ * (1,-1,0) (-1,1,0) (1,0,1) (-1,0,-1) (1,0,-1) (-1,0,1) (0,1,1) (0,-1,-1)
+ * (0,1,-1) (0,-1,1); distinct buffers.  force_dev: total force [3][z][y][x]
+ * (lattice units); vel_dev: u at the collision [3][z][y][x].  nz and the
+ * size rules as for epd_prop_solve3d.  Asynchronous on cuda_stream.
+ */
+int epd_lb3d_step(const epd_lb_params *p, int32_t nz, const double *pop_in_dev, const double *force_dev,
+                  double *pop_out_dev, double *vel_dev, void *cuda_stream);
+
+/*
  * Stateless single-chain solve on device pointers (Sec. 2, Eqs. (6)-(11)):
  * omega_dev (3*ny*nx doubles) -> phi_dev (3*ny*nx doubles), q_dev[2] =
  * (Q_P, Q_S).  workspace_dev of epd_prop_solve_workspace_bytes bytes holds the

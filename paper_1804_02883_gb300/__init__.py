@@ -17,6 +17,7 @@ from .binding import (  # noqa: F401
     epd_prop_solve_noalloc,
     epd_prop_solve_workspace_bytes,
     epd_prop_solve3d_workspace_bytes,
+    lb3d_step,
     lib,
     prop_solve3d,
 )

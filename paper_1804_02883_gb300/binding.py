@@ -38,7 +38,7 @@ SYMBOLS = (
     "epd_sur_num_params", "epd_sur_workspace_bytes", "epd_sur_forward", "epd_sur_gradients", "epd_sur_train_step",
     "epd_lb_surrogate_workspace_bytes", "epd_lb_set_surrogate", "epd_lb_surrogate_stats", "epd_lb_fields_dev",
     "epd_lb_set_inversion", "epd_lb_inversion_stats", "epd_lb_sigma_delta", "epd_lb_width", "epd_lb_particles",
-    "epd_prop_solve3d_workspace_bytes", "epd_prop_solve3d",
+    "epd_prop_solve3d_workspace_bytes", "epd_prop_solve3d", "epd_lb3d_step",
 )
 
 
@@ -129,6 +129,7 @@ def lib():
             "epd_prop_solve": (ctypes.c_int, [P, vp, vp, vp, vp, ctypes.c_size_t, vp]),
             "epd_prop_solve3d_workspace_bytes": (ctypes.c_int, [P, i32, szp]),
             "epd_prop_solve3d": (ctypes.c_int, [P, i32, vp, vp, vp, vp, ctypes.c_size_t, vp]),
+            "epd_lb3d_step": (ctypes.c_int, [P, i32, vp, vp, vp, vp, vp]),
             "epd_lb_enable_timing": (ctypes.c_int, [vp, i32]),
             "epd_lb_kernel_times": (ctypes.c_int, [vp, vp]),
             "epd_lb_tiles": (ctypes.c_int, [vp, ctypes.c_int32, vp]),
@@ -232,6 +233,28 @@ def prop_solve3d(run: RunParams, omega):
         raise EpdLbError(rc, "epd_prop_solve3d")
     st.synchronize()
     return pd.cpu().numpy(), qd.cpu().numpy()
+
+
+def lb3d_step(run: RunParams, pop, force):
+    """One D3Q19 collide-stream on an nz x ny x nx box (pop (19, nz, ny, nx),
+    force (3, nz, ny, nx), host arrays): (populations at t + 1, velocity at
+    the collision).  Device memory from torch, synchronous."""
+    import torch
+
+    pin = torch.from_numpy(np.ascontiguousarray(pop, dtype=np.float64)).cuda()
+    nz = pin.shape[1]
+    assert pin.shape == (19, nz, run.ny, run.nx)
+    fd = torch.from_numpy(np.ascontiguousarray(force, dtype=np.float64)).cuda()
+    assert fd.shape == (3, nz, run.ny, run.nx)
+    pout = torch.empty_like(pin)
+    vel = torch.empty_like(fd)
+    st = torch.cuda.current_stream()
+    rc = lib().epd_lb3d_step(ctypes.byref(run.c()), nz, pin.data_ptr(), fd.data_ptr(), pout.data_ptr(), vel.data_ptr(),
+                             st.cuda_stream)
+    if rc:
+        raise EpdLbError(rc, "epd_lb3d_step")
+    st.synchronize()
+    return pout.cpu().numpy(), vel.cpu().numpy()
 
 
 def epd_prop_solve_noalloc(run: RunParams, omega_dev: int, phi_dev: int, q_dev: int, stream: int = 0) -> None:

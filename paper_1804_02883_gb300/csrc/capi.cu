@@ -1346,6 +1346,17 @@ extern "C" int epd_prop_solve3d(const epd_lb_params *p, int32_t nz, const double
     return e ? EPD_LB_ECUDA : EPD_LB_OK;
 }
 
+extern "C" int epd_lb3d_step(const epd_lb_params *p, int32_t nz, const double *pop_in_dev, const double *force_dev,
+                             double *pop_out_dev, double *vel_dev, void *cuda_stream)
+{
+    if (!p || !validate(*p).empty() || !smooth_even(nz) || nz > kMaxN) return EPD_LB_EINVAL;
+    if ((long long)p->nx * p->ny * nz > kMaxSites3) return EPD_LB_EINVAL;
+    if (!pop_in_dev || !force_dev || !pop_out_dev || !vel_dev || pop_in_dev == pop_out_dev) return EPD_LB_EINVAL;
+    const cudaError_t e = launch_lb3d_step(p->nx, p->ny, nz, p->gamma_s, p->gamma_b, p->gamma_g, pop_in_dev, force_dev,
+                                           pop_out_dev, vel_dev, (cudaStream_t)cuda_stream);
+    return e ? EPD_LB_ECUDA : EPD_LB_OK;
+}
+
 static bool solve_group(const epd_lb_params *p, Group &G)
 {
     if (!p || !validate(*p).empty()) return false;

@@ -197,6 +197,9 @@ struct Solve3 {
 };
 cudaError_t launch_solve3d(const Solve3 &S, const double *omega, double *phi, double *q, cudaStream_t s);
 size_t solve3d_smem_max(const Solve3 &S);  // largest dynamic shared memory of the three passes
+// D3Q19 collide-stream on an nz x ny x nx box, FP64 ([19][z][y][x] in, out).
+cudaError_t launch_lb3d_step(int nx, int ny, int nz, double gs, double gb, double gg, const double *in,
+                             const double *force, double *out, double *vel, cudaStream_t s);
 
 // Kernel attributes (dynamic shared memory limits), once per process.
 cudaError_t configure_kernels();

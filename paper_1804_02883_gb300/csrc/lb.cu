@@ -428,4 +428,92 @@ cudaError_t launch_observables(Group &G, int run, int parity, double *out_dev, c
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// D3Q19 collide-stream (the three-dimensional scheme named for the extension
+// to 3D, Sec. 2), FP64, in the mode form of the D2Q9 update above: u =
+// (j + f/2)/rho; j* = j + f; the stress relaxes about rho c_s^2 I + rho u u
+// (traceless part by gamma_s, trace by gamma_b) and gains Sigma of Eq. (15)
+// with its d = 3 constants; the ghost part (what the second-order projection
+// on rho, j, Pi leaves of a population) is scaled by gamma_g.  Push
+// streaming into a second array: out_i(r + c_i) = n_i*(r).
+// ---------------------------------------------------------------------------
+
+__constant__ int c3[19][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},  {0, 0, 1},  {0, 0, -1},
+                              {1, 1, 0},  {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 0, 1},   {-1, 0, -1}, {1, 0, -1},
+                              {-1, 0, 1}, {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+
+__device__ __forceinline__ double lb3_weight(int i) { return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0); }
+
+__global__ void __launch_bounds__(kThreads) lb3d_step_k(int nx, int ny, int nz, double gs, double gb, double gg,
+                                                        const double *in, const double *force, double *out, double *vel)
+{
+    const long long n = (long long)nx * ny * nz;
+    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= n) return;
+    const int x = (int)(site % nx), y = (int)((site / nx) % ny), z = (int)(site / ((long long)nx * ny));
+    double nl[19];
+    double rho = 0.0, jx = 0.0, jy = 0.0, jz = 0.0, pxx = 0.0, pyy = 0.0, pzz = 0.0, pxy = 0.0, pxz = 0.0, pyz = 0.0;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const double v = in[(size_t)i * n + site];
+        const double cx = c3[i][0], cy = c3[i][1], cz = c3[i][2];
+        nl[i] = v;
+        rho += v;
+        jx += v * cx;
+        jy += v * cy;
+        jz += v * cz;
+        pxx += v * cx * cx;
+        pyy += v * cy * cy;
+        pzz += v * cz * cz;
+        pxy += v * cx * cy;
+        pxz += v * cx * cz;
+        pyz += v * cy * cz;
+    }
+    const double fx = force[site], fy = force[n + site], fz = force[2 * n + site];
+    const double ux = (jx + 0.5 * fx) / rho, uy = (jy + 0.5 * fy) / rho, uz = (jz + 0.5 * fz) / rho;
+    vel[site] = ux;
+    vel[n + site] = uy;
+    vel[2 * n + site] = uz;
+    const double cs2 = 1.0 / 3.0;
+    // non-equilibrium stress, its trace, and the post-collision M* = Pi* - rho c_s^2 I
+    const double nxx = pxx - rho * (ux * ux + cs2), nyy = pyy - rho * (uy * uy + cs2), nzz = pzz - rho * (uz * uz + cs2);
+    const double nxy = pxy - rho * ux * uy, nxz = pxz - rho * ux * uz, nyz = pyz - rho * uy * uz;
+    const double t3 = (nxx + nyy + nzz) / 3.0, uf = ux * fx + uy * fy + uz * fz;
+    const double hs = 0.5 * (1.0 + gs), hb = (1.0 + gb) / 3.0;
+    const double dxx = gs * (nxx - t3) + gb * t3 + hs * (2.0 * ux * fx - 2.0 / 3.0 * uf) + hb * uf;
+    const double dyy = gs * (nyy - t3) + gb * t3 + hs * (2.0 * uy * fy - 2.0 / 3.0 * uf) + hb * uf;
+    const double dzz = gs * (nzz - t3) + gb * t3 + hs * (2.0 * uz * fz - 2.0 / 3.0 * uf) + hb * uf;
+    const double sxx = rho * ux * ux + dxx, syy = rho * uy * uy + dyy, szz = rho * uz * uz + dzz;
+    const double sxy = rho * ux * uy + gs * nxy + hs * (ux * fy + uy * fx);
+    const double sxz = rho * ux * uz + gs * nxz + hs * (ux * fz + uz * fx);
+    const double syz = rho * uy * uz + gs * nyz + hs * (uy * fz + uz * fy);
+    // M = Pi - rho c_s^2 I of the incoming populations (for their ghost part)
+    const double mxx = pxx - rho * cs2, myy = pyy - rho * cs2, mzz = pzz - rho * cs2;
+    const double jsx = jx + fx, jsy = jy + fy, jsz = jz + fz;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const double cx = c3[i][0], cy = c3[i][1], cz = c3[i][2], w = lb3_weight(i);
+        // (c c - c_s^2 I) : M for the old and the post-collision moments
+        const double qold = mxx * (cx * cx - cs2) + myy * (cy * cy - cs2) + mzz * (cz * cz - cs2) +
+                            2.0 * (pxy * cx * cy + pxz * cx * cz + pyz * cy * cz);
+        const double qnew = sxx * (cx * cx - cs2) + syy * (cy * cy - cs2) + szz * (cz * cz - cs2) +
+                            2.0 * (sxy * cx * cy + sxz * cx * cz + syz * cy * cz);
+        const double hold = w * (rho + 3.0 * (jx * cx + jy * cy + jz * cz) + 4.5 * qold);
+        const double hnew = w * (rho + 3.0 * (jsx * cx + jsy * cy + jsz * cz) + 4.5 * qnew);
+        int xd = x + c3[i][0], yd = y + c3[i][1], zd = z + c3[i][2];
+        xd = xd < 0 ? xd + nx : (xd >= nx ? xd - nx : xd);
+        yd = yd < 0 ? yd + ny : (yd >= ny ? yd - ny : yd);
+        zd = zd < 0 ? zd + nz : (zd >= nz ? zd - nz : zd);
+        out[(size_t)i * n + ((long long)zd * ny + yd) * nx + xd] = hnew + gg * (nl[i] - hold);
+    }
+}
+
+cudaError_t launch_lb3d_step(int nx, int ny, int nz, double gs, double gb, double gg, const double *in,
+                             const double *force, double *out, double *vel, cudaStream_t s)
+{
+    const long long n = (long long)nx * ny * nz;
+    lb3d_step_k<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(nx, ny, nz, gs, gb, gg, in, force, out, vel);
+    return cudaGetLastError();
+}
+
 } // namespace epdlb
