@@ -126,6 +126,9 @@ def lib():
             "or_fft3d": (None, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
             "or_solve3d": (None, [P, ctypes.c_int, _DP, _DP, _DP]),
             "or_lb3d_step": (None, [P, ctypes.c_int, _DP, _DP, _DP]),
+            "or_spectral_op3d": (None, [P, ctypes.c_int, _DP, _DP, ctypes.c_int]),
+            "or_force3d": (None, [P, ctypes.c_int, _DP, _DP]),
+            "or_step3d": (None, [P, ctypes.c_int, _DP, _DP, _DP, _DP, _DP, _DP]),
             "or_width": (ctypes.c_double, [P, _DP]),
             "or_particles": (ctypes.c_int, [P, _DP, ctypes.c_double, ctypes.POINTER(ctypes.c_int), _DP, ctypes.c_int]),
         }
@@ -291,6 +294,33 @@ def lb3d_step(p: Params, nz: int, pop, force_total):
     vel = np.empty((3, nz, p.ny, p.nx))
     lib().or_lb3d_step(ctypes.byref(p.c()), int(nz), _d(pop), _d(f), _d(vel))
     return pop, vel
+
+
+def spectral_op3d(p: Params, nz: int, f, op: int) -> np.ndarray:
+    """op 0, 1, 2: d/dx, d/dy, d/dz; op 3: the Laplacian, of a real (nz, ny, nx) field."""
+    f = _f64(f).reshape(nz, p.ny, p.nx)
+    out = np.empty_like(f)
+    lib().or_spectral_op3d(ctypes.byref(p.c()), int(nz), _d(f), _d(out), int(op))
+    return out
+
+
+def force3d(p: Params, nz: int, dphi) -> np.ndarray:
+    dphi = _f64(dphi).reshape(3, nz, p.ny, p.nx)
+    out = np.empty((3, nz, p.ny, p.nx))
+    lib().or_force3d(ctypes.byref(p.c()), int(nz), _d(dphi), _d(out))
+    return out
+
+
+def step3d(p: Params, nz: int, omega, pop, vel):
+    """One coupled step on the 3D box: (omega, pop, vel, phi, q, force), all new arrays."""
+    omega = _f64(omega).reshape(3, nz, p.ny, p.nx).copy()
+    pop = _f64(pop).reshape(19, nz, p.ny, p.nx).copy()
+    vel = _f64(vel).reshape(3, nz, p.ny, p.nx).copy()
+    phi = np.empty_like(omega)
+    force = np.empty_like(vel)
+    q = np.empty(2)
+    lib().or_step3d(ctypes.byref(p.c()), int(nz), _d(omega), _d(pop), _d(vel), _d(phi), _d(q), _d(force))
+    return omega, pop, vel, phi, q, force
 
 
 def flow_profile(p: Params, y: float) -> float:

@@ -986,6 +986,137 @@ void or_step_exact(const or_params *p, double *omega, double *pop, double *vel, 
     free(ftot);
 }
 
+/* ------------------------------------------------------------------------ */
+/* The coupled step on a 3D box: the 2D step's operations with spectral       */
+/* derivatives along x, y and z, the 3D single-chain solve and D3Q19.         */
+/* ------------------------------------------------------------------------ */
+
+/* Spectral operator on a real [z][y][x] field: op 0, 1, 2 = d/dx, d/dy, d/dz
+ * (Nyquist bin of the derivative's axis dropped), op 3 = the Laplacian. */
+void or_spectral_op3d(const or_params *p, int nz, const double *f, double *out, int op)
+{
+    int nx = p->nx, ny = p->ny;
+    size_t n = (size_t)nx * ny * nz;
+    cplx *a = (cplx *)malloc(sizeof(cplx) * n);
+    for (size_t i = 0; i < n; i++) a[i] = f[i];
+    or_fft3d(a, nz, ny, nx, -1);
+    for (int z = 0; z < nz; z++)
+        for (int y = 0; y < ny; y++)
+            for (int x = 0; x < nx; x++) {
+                size_t i = ((size_t)z * ny + y) * nx + x;
+                cplx m;
+                if (op == 3) {
+                    double kx = wavenumber(x, nx, p->dx), ky = wavenumber(y, ny, p->dx), kz = wavenumber(z, nz, p->dx);
+                    m = -(kx * kx + ky * ky + kz * kz);
+                } else {
+                    double k = op == 0 ? wavenumber_odd(x, nx, p->dx) : op == 1 ? wavenumber_odd(y, ny, p->dx)
+                                                                          : wavenumber_odd(z, nz, p->dx);
+                    m = I * k;
+                }
+                a[i] *= m;
+            }
+    or_fft3d(a, nz, ny, nx, +1);
+    for (size_t i = 0; i < n; i++) out[i] = creal(a[i]) / (double)n;
+    free(a);
+}
+
+/* Force of Eqs. (19)-(20) on the 3D box: f(k) = (1/(beta v)) sum_I dPhi_I(k) /
+ * (D_I dt) i k / |k|^2, in lattice units, [3][z][y][x]. */
+void or_force3d(const or_params *p, int nz, const double *dphi, double *force_lat)
+{
+    int nx = p->nx, ny = p->ny;
+    size_t n = (size_t)nx * ny * nz;
+    double fstar = or_fstar_lattice(p);
+    cplx *fc[3], *a = (cplx *)malloc(sizeof(cplx) * n);
+    for (int c = 0; c < 3; c++) {
+        fc[c] = (cplx *)malloc(sizeof(cplx) * n);
+        for (size_t i = 0; i < n; i++) fc[c][i] = 0.0;
+    }
+    for (int s = 0; s < 3; s++) {
+        double d = (s == 2) ? p->d_s : p->d_p;
+        for (size_t i = 0; i < n; i++) a[i] = dphi[(size_t)s * n + i];
+        or_fft3d(a, nz, ny, nx, -1);
+        for (int z = 0; z < nz; z++)
+            for (int y = 0; y < ny; y++)
+                for (int x = 0; x < nx; x++) {
+                    size_t i = ((size_t)z * ny + y) * nx + x;
+                    double kx = wavenumber(x, nx, p->dx), ky = wavenumber(y, ny, p->dx), kz = wavenumber(z, nz, p->dx);
+                    double k2 = kx * kx + ky * ky + kz * kz;
+                    if (k2 == 0.0) continue;
+                    cplx c = p->inv_beta_v * a[i] / (d * p->dt) / k2;
+                    fc[0][i] += c * I * wavenumber_odd(x, nx, p->dx);
+                    fc[1][i] += c * I * wavenumber_odd(y, ny, p->dx);
+                    fc[2][i] += c * I * wavenumber_odd(z, nz, p->dx);
+                }
+    }
+    for (int c = 0; c < 3; c++) {
+        or_fft3d(fc[c], nz, ny, nx, +1);
+        for (size_t i = 0; i < n; i++) force_lat[(size_t)c * n + i] = creal(fc[c][i]) / (double)n * fstar;
+        free(fc[c]);
+    }
+    free(a);
+}
+
+/* One coupled step on the 3D box, in the order of or_step: auxiliary
+ * convection of omega with the 3D gradient, the 3D solve at omega~, the
+ * diffusion step with the 3D Laplacian, the 3D solve at omega(t + dt), the
+ * 3D force plus the reverse-Poiseuille body force of Eq. (23) along x
+ * (a function of y), one D3Q19 update.  State: omega (3n), pop (19n,
+ * pre-collision), vel (3n, the velocity handed to the convection); outputs
+ * phi (3n), q[2], force (3n, the polymer force). */
+void or_step3d(const or_params *p, int nz, double *omega, double *pop, double *vel, double *phi, double *q,
+               double *force)
+{
+    int nx = p->nx, ny = p->ny;
+    size_t n = (size_t)nx * ny * nz;
+    double vscale = p->dx / p->dt;
+    double *wt = (double *)malloc(sizeof(double) * 3 * n);
+    double *pt = (double *)malloc(sizeof(double) * 3 * n);
+    double *mu = (double *)malloc(sizeof(double) * 3 * n);
+    double *tmp = (double *)malloc(sizeof(double) * n);
+    double *ftot = (double *)malloc(sizeof(double) * 3 * n);
+    double qt[2];
+    /* (1) auxiliary convection */
+    for (int s = 0; s < 3; s++) {
+        const double *w = omega + (size_t)s * n;
+        for (size_t i = 0; i < n; i++) wt[(size_t)s * n + i] = w[i];
+        for (int a = 0; a < 3; a++) {
+            or_spectral_op3d(p, nz, w, tmp, a);
+            for (size_t i = 0; i < n; i++) wt[(size_t)s * n + i] -= p->dt * vel[(size_t)a * n + i] * vscale * tmp[i];
+        }
+    }
+    /* (2) densities at omega~ */
+    or_solve3d(p, nz, wt, pt, qt);
+    /* (3) mu (as or_mu) and the diffusion step */
+    for (size_t i = 0; i < n; i++) {
+        double pa = pt[i], pb = pt[n + i], ps = pt[2 * n + i];
+        double inc = p->kappa_h * (pa + pb + ps - 1.0);
+        mu[i] = p->chi_ab * pb + p->chi_as * ps + inc - wt[i];
+        mu[n + i] = p->chi_ab * pa + p->chi_bs * ps + inc - wt[n + i];
+        mu[2 * n + i] = p->chi_as * pa + p->chi_bs * pb + inc - wt[2 * n + i];
+    }
+    for (int s = 0; s < 3; s++) {
+        double d = (s == 2) ? p->d_s : p->d_p;
+        or_spectral_op3d(p, nz, mu + (size_t)s * n, tmp, 3);
+        for (size_t i = 0; i < n; i++) omega[(size_t)s * n + i] = wt[(size_t)s * n + i] - p->dt * d * tmp[i];
+    }
+    /* (4) densities at t + dt, (5) force */
+    or_solve3d(p, nz, omega, phi, q);
+    for (size_t i = 0; i < 3 * n; i++) mu[i] = phi[i] - pt[i];
+    or_force3d(p, nz, mu, force);
+    /* (6) D3Q19 with the polymer force plus the body force */
+    for (size_t i = 0; i < 3 * n; i++) ftot[i] = force[i];
+    for (int z = 0; z < nz; z++)
+        for (int y = 0; y < ny; y++)
+            for (int x = 0; x < nx; x++) ftot[((size_t)z * ny + y) * nx + x] += or_poiseuille_force(p, y);
+    or_lb3d_step(p, nz, pop, ftot, vel);
+    free(wt);
+    free(pt);
+    free(mu);
+    free(tmp);
+    free(ftot);
+}
+
 /* Observables: sigma of Eq. (21) = mean |Phi_A + Phi_B - phi_p|. */
 double or_sigma(const or_params *p, const double *phi)
 {
