@@ -329,6 +329,26 @@ int epd_prop_solve3d(const epd_lb_params *p, int32_t nz, const double *omega_dev
                      void *workspace_dev, size_t workspace_bytes, void *cuda_stream);
 
 /*
+ * One coupled step on an nz x ny x nx box (the extension to 3D, Sec. 2 and
+ * Sec. 5), in the order of the 2D step: auxiliary convection of omega with
+ * the 3D spectral gradient, the 3D single-chain solve at omega~, the
+ * diffusion step with the 3D Laplacian, the 3D solve at omega(t + dt), the
+ * force of Eqs. (19)-(20) with i k / |k|^2 in 3D plus the reverse-Poiseuille
+ * body force of Eq. (23) along x (a function of y), one D3Q19 update
+ * (epd_lb3d_step).  EPD transforms in FP64, the solves in p->precision.
+ * State on the device, updated in place: omega_dev [3][z][y][x], pop_dev
+ * [19][z][y][x] (pre-collision, the order of epd_lb3d_step), vel_dev
+ * [3][z][y][x] (the velocity handed to the convection, lattice units).
+ * Outputs: phi_dev [3][z][y][x] = Phi(t + dt), q_dev[2], force_dev
+ * [3][z][y][x] = the polymer force (lattice units).  workspace_dev:
+ * epd_step3d_workspace_bytes bytes, 256-byte aligned.  Size rules of
+ * epd_prop_solve3d.  Asynchronous on cuda_stream.
+ */
+int epd_step3d_workspace_bytes(const epd_lb_params *p, int32_t nz, size_t *bytes);
+int epd_step3d(const epd_lb_params *p, int32_t nz, double *omega_dev, double *pop_dev, double *vel_dev, double *phi_dev,
+               double *q_dev, double *force_dev, void *workspace_dev, size_t workspace_bytes, void *cuda_stream);
+
+/*
  * One D3Q19 collide-stream on an nz x ny x nx box (the three-dimensional LB
  * scheme the paper names for the extension to 3D, Sec. 2), FP64: the
  * collision in the mode form of the D2Q9 update (u = (j + f/2)/rho, j* =

@@ -20,4 +20,5 @@ from .binding import (  # noqa: F401
     lb3d_step,
     lib,
     prop_solve3d,
+    step3d,
 )

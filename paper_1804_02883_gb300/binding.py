@@ -38,7 +38,8 @@ SYMBOLS = (
     "epd_sur_num_params", "epd_sur_workspace_bytes", "epd_sur_forward", "epd_sur_gradients", "epd_sur_train_step",
     "epd_lb_surrogate_workspace_bytes", "epd_lb_set_surrogate", "epd_lb_surrogate_stats", "epd_lb_fields_dev",
     "epd_lb_set_inversion", "epd_lb_inversion_stats", "epd_lb_sigma_delta", "epd_lb_width", "epd_lb_particles",
-    "epd_prop_solve3d_workspace_bytes", "epd_prop_solve3d", "epd_lb3d_step",
+    "epd_prop_solve3d_workspace_bytes", "epd_prop_solve3d", "epd_lb3d_step", "epd_step3d_workspace_bytes",
+    "epd_step3d",
 )
 
 
@@ -130,6 +131,8 @@ def lib():
             "epd_prop_solve3d_workspace_bytes": (ctypes.c_int, [P, i32, szp]),
             "epd_prop_solve3d": (ctypes.c_int, [P, i32, vp, vp, vp, vp, ctypes.c_size_t, vp]),
             "epd_lb3d_step": (ctypes.c_int, [P, i32, vp, vp, vp, vp, vp]),
+            "epd_step3d_workspace_bytes": (ctypes.c_int, [P, i32, szp]),
+            "epd_step3d": (ctypes.c_int, [P, i32, vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]),
             "epd_lb_enable_timing": (ctypes.c_int, [vp, i32]),
             "epd_lb_kernel_times": (ctypes.c_int, [vp, vp]),
             "epd_lb_tiles": (ctypes.c_int, [vp, ctypes.c_int32, vp]),
@@ -255,6 +258,37 @@ def lb3d_step(run: RunParams, pop, force):
         raise EpdLbError(rc, "epd_lb3d_step")
     st.synchronize()
     return pout.cpu().numpy(), vel.cpu().numpy()
+
+
+def step3d(run: RunParams, omega, pop, vel, nsteps: int = 1):
+    """nsteps coupled steps on an nz x ny x nx box from host state omega
+    (3, nz, ny, nx), pop (19, nz, ny, nx, pre-collision), vel (3, nz, ny, nx):
+    (omega, pop, vel, phi, q, force) after the last step.  Synchronous."""
+    import torch
+
+    om = torch.from_numpy(np.ascontiguousarray(omega, dtype=np.float64)).cuda()
+    nz = om.shape[1]
+    assert om.shape == (3, nz, run.ny, run.nx)
+    pd = torch.from_numpy(np.ascontiguousarray(pop, dtype=np.float64)).cuda()
+    vd = torch.from_numpy(np.ascontiguousarray(vel, dtype=np.float64)).cuda()
+    assert pd.shape == (19, nz, run.ny, run.nx) and vd.shape == (3, nz, run.ny, run.nx)
+    phi = torch.empty_like(om)
+    force = torch.empty_like(vd)
+    q = torch.empty(2, dtype=torch.float64, device="cuda")
+    nb = ctypes.c_size_t()
+    rc = lib().epd_step3d_workspace_bytes(ctypes.byref(run.c()), nz, ctypes.byref(nb))
+    if rc:
+        raise EpdLbError(rc, "epd_step3d_workspace_bytes")
+    ws = torch.empty(nb.value + 256, dtype=torch.uint8, device="cuda")
+    wptr = (ws.data_ptr() + 255) & ~255
+    st = torch.cuda.current_stream()
+    for _ in range(nsteps):
+        rc = lib().epd_step3d(ctypes.byref(run.c()), nz, om.data_ptr(), pd.data_ptr(), vd.data_ptr(), phi.data_ptr(),
+                              q.data_ptr(), force.data_ptr(), wptr, nb.value, st.cuda_stream)
+        if rc:
+            raise EpdLbError(rc, "epd_step3d")
+    st.synchronize()
+    return tuple(t.cpu().numpy() for t in (om, pd, vd, phi, q, force))
 
 
 def epd_prop_solve_noalloc(run: RunParams, omega_dev: int, phi_dev: int, q_dev: int, stream: int = 0) -> None:

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libepd_lb.so")
-SOURCES = ["prop_cluster.cu", "prop.cu", "epd.cu", "lb.cu", "surrogate.cu", "invert.cu", "analysis.cu", "capi.cu"]
+SOURCES = ["prop_cluster.cu", "prop.cu", "epd.cu", "lb.cu", "surrogate.cu", "invert.cu", "analysis.cu", "step3d.cu", "capi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -27,6 +27,7 @@ cudaError_t configure_kernels()
     if (done) return status;
     status = configure_prop_kernels();
     if (status == cudaSuccess) status = configure_epd_kernels();
+    if (status == cudaSuccess) status = configure_step3d_kernels();
     done = true;
     return status;
 }
@@ -1292,7 +1293,7 @@ static size_t solve3_layout(const epd_lb_params *p, int nz, Solve3 &S, char *bas
     return align_up(off);
 }
 
-// Twiddles exp(-2 pi i t / n), t < n, and factors exp(-R_G^2 k^2 ds) / n of one axis.
+// Twiddles exp(-2 pi i t / n), t < n, and (kf not null) factors exp(-R_G^2 k^2 ds) / n of one axis.
 template <typename T>
 static cudaError_t upload_axis(int n, double dx, double rg, double ds, void *tw, void *kf, cudaStream_t s)
 {
@@ -1307,7 +1308,7 @@ static cudaError_t upload_axis(int n, double dx, double rg, double ds, void *tw,
         k[j] = (T)(std::exp(-rg * rg * kk * kk * ds) / (double)n);
     }
     cudaError_t e = cudaMemcpyAsync(tw, t.data(), t.size() * sizeof(T), cudaMemcpyHostToDevice, s);
-    if (!e) e = cudaMemcpyAsync(kf, k.data(), k.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+    if (!e && kf) e = cudaMemcpyAsync(kf, k.data(), k.size() * sizeof(T), cudaMemcpyHostToDevice, s);
     if (!e) e = cudaStreamSynchronize(s);  // the host vectors go out of scope
     return e;
 }
@@ -1354,6 +1355,93 @@ extern "C" int epd_lb3d_step(const epd_lb_params *p, int32_t nz, const double *p
     if (!pop_in_dev || !force_dev || !pop_out_dev || !vel_dev || pop_in_dev == pop_out_dev) return EPD_LB_EINVAL;
     const cudaError_t e = launch_lb3d_step(p->nx, p->ny, nz, p->gamma_s, p->gamma_b, p->gamma_g, pop_in_dev, force_dev,
                                            pop_out_dev, vel_dev, (cudaStream_t)cuda_stream);
+    return e ? EPD_LB_ECUDA : EPD_LB_OK;
+}
+
+// The coupled 3D step: the 3D solve's layout plus the step's fields and the
+// FP64 transform buffers and tables.
+static Axis3 axis3(int n)
+{
+    Axis3 a = Axis3();
+    a.n = n;
+    a.pow2 = pow2(n);
+    a.logn = a.pow2 ? ilog2(n) : 0;
+    a.nf = radix_plan(n, a.f);
+    return a;
+}
+
+static size_t step3_layout(const epd_lb_params *p, int nz, Step3 &T, char *base)
+{
+    const size_t sb = solve3_layout(p, nz, T.S, base);
+    if (!sb) return 0;
+    const int nx = p->nx, ny = p->ny;
+    const long long n = (long long)nx * ny * nz;
+    Fft3 &F = T.F;
+    F.ax = axis3(nx);
+    F.ay = axis3(ny);
+    F.az = axis3(nz);
+    F.rows_x = divisor_at_most(ny * nz, std::max(1, 2048 / nx));
+    F.cols_y = divisor_at_most(nx, std::max(1, 2048 / ny));
+    F.cols_z = divisor_at_most(nx * ny, std::max(1, 2048 / nz));
+    if (fft3_smem(F) > 200 * 1024) return 0;
+    size_t off = sb;
+    auto take = [&](size_t bytes) -> void * {
+        off = align_up(off);
+        void *q = base ? base + off : nullptr;
+        off += bytes;
+        return q;
+    };
+    T.wt = (double *)take(3 * n * sizeof(double));
+    T.pt = (double *)take(3 * n * sizeof(double));
+    T.mu = (double *)take(3 * n * sizeof(double));
+    T.qt = (double *)take(2 * sizeof(double));
+    T.ftot = (double *)take(3 * n * sizeof(double));
+    T.pop2 = (double *)take(19 * n * sizeof(double));
+    T.b0 = (double2 *)take(n * sizeof(double2));
+    T.b1 = (double2 *)take(n * sizeof(double2));
+    F.twx = (const double2 *)take(nx * sizeof(double2));
+    F.twy = (const double2 *)take(ny * sizeof(double2));
+    F.twz = (const double2 *)take(nz * sizeof(double2));
+    T.f0_lat = p->f0 * fstar_lattice(*p);
+    return align_up(off);
+}
+
+extern "C" int epd_step3d_workspace_bytes(const epd_lb_params *p, int32_t nz, size_t *bytes)
+{
+    Step3 T;
+    if (!bytes) return EPD_LB_EINVAL;
+    const size_t b = step3_layout(p, nz, T, nullptr);
+    if (!b) return EPD_LB_EINVAL;
+    *bytes = b;
+    return EPD_LB_OK;
+}
+
+extern "C" int epd_step3d(const epd_lb_params *p, int32_t nz, double *omega_dev, double *pop_dev, double *vel_dev,
+                          double *phi_dev, double *q_dev, double *force_dev, void *workspace_dev, size_t workspace_bytes,
+                          void *cuda_stream)
+{
+    Step3 T;
+    if (!omega_dev || !pop_dev || !vel_dev || !phi_dev || !q_dev || !force_dev || !workspace_dev) return EPD_LB_EINVAL;
+    const size_t need = step3_layout(p, nz, T, nullptr);
+    if (!need) return EPD_LB_EINVAL;
+    if (workspace_bytes < need || ((uintptr_t)workspace_dev & 255)) return EPD_LB_ENOMEM;
+    if (configure_kernels() != cudaSuccess) return EPD_LB_ECUDA;
+    step3_layout(p, nz, T, (char *)workspace_dev);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const double ds = 1.0 / (double)p->ns;
+    cudaError_t e = cudaMemsetAsync(T.S.err, 0, sizeof(int), s);
+    auto up = [&](int n, void *tw, void *kf) {
+        return p->precision == EPD_LB_MIXED_FP32 ? upload_axis<float>(n, p->dx, p->rg, ds, tw, kf, s)
+                                                 : upload_axis<double>(n, p->dx, p->rg, ds, tw, kf, s);
+    };
+    if (!e) e = up(p->nx, T.S.twx, T.S.kx);
+    if (!e) e = up(p->ny, T.S.twy, T.S.ky);
+    if (!e) e = up(nz, T.S.twz, T.S.kz);
+    // FP64 twiddles of the EPD transforms
+    if (!e) e = upload_axis<double>(p->nx, p->dx, p->rg, ds, (void *)T.F.twx, nullptr, s);
+    if (!e) e = upload_axis<double>(p->ny, p->dx, p->rg, ds, (void *)T.F.twy, nullptr, s);
+    if (!e) e = upload_axis<double>(nz, p->dx, p->rg, ds, (void *)T.F.twz, nullptr, s);
+    if (!e) e = launch_step3d(T, omega_dev, pop_dev, vel_dev, phi_dev, q_dev, force_dev, s);
     return e ? EPD_LB_ECUDA : EPD_LB_OK;
 }
 

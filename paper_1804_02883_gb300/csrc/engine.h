@@ -197,6 +197,30 @@ struct Solve3 {
 };
 cudaError_t launch_solve3d(const Solve3 &S, const double *omega, double *phi, double *q, cudaStream_t s);
 size_t solve3d_smem_max(const Solve3 &S);  // largest dynamic shared memory of the three passes
+// One axis of the FP64 3D transforms of the coupled 3D step.
+struct Axis3 {
+    int n, pow2, logn, nf;
+    int f[kMaxFactors];
+};
+struct Fft3 {
+    Axis3 ax, ay, az;
+    int rows_x, cols_y, cols_z;    // tiles of the x-row, y-column and z-column transforms
+    const double2 *twx, *twy, *twz;  // FP64 twiddles exp(-2 pi i t / n), t < n
+};
+size_t fft3_smem(const Fft3 &F);
+// The coupled step on a 3D box (step3d.cu): state omega (3n), pop (19n,
+// pre-collision), vel (3n); outputs phi (3n), q (2), force (3n).
+struct Step3 {
+    Solve3 S;
+    Fft3 F;
+    double *wt, *pt, *mu, *qt, *ftot, *pop2;  // omega~, Phi~, mu / dPhi, Q~, total force, populations out
+    double2 *b0, *b1;                         // complex FP64 transform buffers [n]
+    double f0_lat;                            // body-force amplitude, lattice units
+};
+cudaError_t launch_step3d(const Step3 &T, double *omega, double *pop, double *vel, double *phi, double *q, double *force,
+                          cudaStream_t s);
+cudaError_t configure_step3d_kernels();
+
 // D3Q19 collide-stream on an nz x ny x nx box, FP64 ([19][z][y][x] in, out).
 cudaError_t launch_lb3d_step(int nx, int ny, int nz, double gs, double gb, double gg, const double *in,
                              const double *force, double *out, double *vel, cudaStream_t s);
