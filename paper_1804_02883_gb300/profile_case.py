@@ -3,7 +3,8 @@ flushes, for kernel profilers:
 
     python -m paper_1804_02883_gb300.profile_case --workload channel --steps 2
 
---exact N then runs N exact steps (Fletcher-Reeves inversion to the 1e-8
+--workload box3d runs the coupled step on a 128 x 128 x 64 box (--time
+prints CUDA-event milliseconds per step).  --exact N then runs N exact steps (Fletcher-Reeves inversion to the 1e-8
 tolerance, at most 100 iterations each) after the --steps truncated ones.
 """
 from __future__ import annotations
@@ -22,12 +23,64 @@ WORKLOADS = {
 }
 
 
+def box3d(steps: int, timed: bool) -> None:
+    """Coupled steps on a 128 x 128 x 64 box (N_s = 16, FP64, phi_p = 0.2,
+    the reverse-Poiseuille force along x), state resident on the device; with
+    timed, CUDA-event milliseconds per step after one warm-up step."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    nx, ny, nz = 128, 128, 64
+    run = B.RunParams(nx=nx, ny=ny, ns=16, precision=B.PLAIN_FP64, f_a=0.5, phi_p=0.2, f0=2.0, seed=7)
+    rng = np.random.default_rng(7)
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+    om = torch.from_numpy(1e-3 * rng.uniform(-1, 1, (3, nz, ny, nx))).cuda()
+    pop = torch.from_numpy(np.broadcast_to(w[:, None, None, None], (19, nz, ny, nx)).copy()).cuda()
+    vel = torch.zeros((3, nz, ny, nx), dtype=torch.float64, device="cuda")
+    phi, force = torch.empty_like(om), torch.empty_like(vel)
+    q = torch.empty(2, dtype=torch.float64, device="cuda")
+    nb = ctypes.c_size_t()
+    assert B.lib().epd_step3d_workspace_bytes(ctypes.byref(run.c()), nz, ctypes.byref(nb)) == 0
+    ws = torch.empty(nb.value + 256, dtype=torch.uint8, device="cuda")
+    wptr = (ws.data_ptr() + 255) & ~255
+    st = torch.cuda.current_stream()
+
+    def one():
+        rc = B.lib().epd_step3d(ctypes.byref(run.c()), nz, om.data_ptr(), pop.data_ptr(), vel.data_ptr(),
+                                phi.data_ptr(), q.data_ptr(), force.data_ptr(), wptr, nb.value, st.cuda_stream)
+        assert rc == 0, rc
+
+    if not timed:
+        for _ in range(steps):
+            one()
+        st.synchronize()
+        return
+    one()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(steps):
+        one()
+    b.record(st)
+    b.synchronize()
+    ms = a.elapsed_time(b) / steps
+    units = nx * ny * nz * run.ns * 4
+    print(f"box3d {nz}x{ny}x{nx} N_s={run.ns} FP64: {ms:.3f} ms/step, {units / (ms * 1e-3):.3e} site.contour-steps/s,"
+          f" Q = {q[0].item():.12f}")
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="channel", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="channel", choices=sorted(WORKLOADS) + ["box3d"])
+    ap.add_argument("--time", action="store_true", help="box3d: print CUDA-event ms per step")
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--exact", type=int, default=0, help="then this many exact steps (0: none)")
     args = ap.parse_args()
+    if args.workload == "box3d":
+        box3d(args.steps, args.time)
+        print("ok")
+        return
     h = B.EpdLb(WORKLOADS[args.workload]())
     h.step(args.steps)
     if args.exact > 0:
