@@ -166,3 +166,31 @@ def test_exact_step_errors():
     with pytest.raises(P.EpdLbError):
         m.set_inversion(5, 1e-8)
     m.close()
+
+
+def test_exact_step_at_the_benchmark_size():
+    # the benchmark batch's strongest-shear run (256 x 512, N_s = 64, MIXED,
+    # cluster-resident differential solves) from the seeded quench: two
+    # truncated steps, then an exact step with two CG iterations, against the
+    # FP64 oracle doing the same
+    r = W.channel_256x512(P.MIXED_FP32)[3]
+    h = P.EpdLb([r])
+    h.step(2)
+    h.set_inversion(2, 0.0)
+    h.step(1)
+    h.sync()
+    p = oracle_params(r)
+    st = O.initial_state(p)
+    O.step(p, st, 2)
+    stats = O.step_exact(p, st, 1, max_iter=2, tol=0.0)
+    s = h.inversion_stats(0)
+    assert s["iterations"] == 2 == int(stats[0, 0])
+    assert abs(s["residual0"] - stats[0, 1]) <= 2e-3 * stats[0, 1]
+    gom, _, gvel = h.get_state(0)
+    gphi, _ = h.densities(0)
+    # the absolute bound of the 64 x 64 case above (1e-5 of a 0.05 spread):
+    # FP32 density error times the inverse correlator, independent of how
+    # large the fluctuations of omega are (here ~1e-3)
+    assert np.abs(gom - st.omega).max() < 5e-7
+    assert rel_err(gphi, st.phi) < 2e-6
+    h.close()
