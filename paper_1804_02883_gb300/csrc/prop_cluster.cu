@@ -401,12 +401,32 @@ __global__ void __launch_bounds__(kThreads) prop_qsum(ContourK k)
     if (threadIdx.x == 0) k.part[(size_t)run * kMaxPart + blockIdx.x] = s;
 }
 
+// 8-byte asynchronous copy global -> shared (the thread's own staging
+// slot), and the commit / wait of the thread's copy groups
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Contour chunks staged per thread: U nodes of each stream (g, g' and, in the
+// differential pass, their changes), two stages in flight.
+template <bool DIFF> struct ContourStage {
+    static constexpr int U = DIFF ? 4 : 8, NW = DIFF ? 4 : 2, NSTAGE = 2;
+    static constexpr size_t SMEM = (size_t)NSTAGE * U * NW * kThreads * sizeof(float2);
+};
+
 // One thread per packed site (real rows 2kk and 2kk+1 at column x).
 // Products in FP32, partial sums over at most 8 nodes of equal weights in
-// FP32, then FP64.
+// FP32, then FP64.  The node states stream through shared memory by
+// asynchronous copies, each thread staging only its own elements (no
+// barriers), so that the loads in flight do not hold registers.
 template <bool DIFF>
 __global__ void __launch_bounds__(kThreads) prop_contour(ContourK k)
 {
+    extern __shared__ __align__(16) float2 stg[];
     __shared__ double bc;
     const int run = blockIdx.y;
     const int nx = k.g.nx, ny = k.g.ny, ns = k.g.ns, na = k.g.na;
@@ -462,44 +482,56 @@ __global__ void __launch_bounds__(kThreads) prop_contour(ContourK k)
     // compensated (Kahan) FP32 sums per block and real site; the trapezoid
     // weights 1 and 1/2 scale the terms exactly
     KSum sa0, sb0, sa1, sb1;
-    // nodes in chunks of U: all loads of a chunk are issued before its sums
-    constexpr int U = DIFF ? 4 : 8;
-    for (int m0 = 0; m0 <= ns; m0 += U) {
-        float2 av[U], bv[U], dav[U], dbv[U];
+    using CS = ContourStage<DIFF>;
+    constexpr int U = CS::U, NW = CS::NW;
+    const int tid = threadIdx.x;
+    // stage st, node u, stream w: stg[((st U + u) NW + w) kThreads + tid]
+    auto issue = [&](int st, int m0) {
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int m = m0 + u;
             if (m <= ns) {
-                av[u] = c0[(size_t)m * k.hn];
-                bv[u] = c1[(size_t)(ns - m) * k.hn];
+                float2 *b = stg + (size_t)((st * U + u) * NW) * kThreads + tid;
+                cp_async8(b, c0 + (size_t)m * k.hn);
+                cp_async8(b + kThreads, c1 + (size_t)(ns - m) * k.hn);
                 if (DIFF) {
-                    dav[u] = d0[(size_t)m * k.hn];
-                    dbv[u] = d1[(size_t)(ns - m) * k.hn];
+                    cp_async8(b + 2 * kThreads, d0 + (size_t)m * k.hn);
+                    cp_async8(b + 3 * kThreads, d1 + (size_t)(ns - m) * k.hn);
                 }
             }
         }
+        cp_async_commit();
+    };
+    const int nch = (ns + U) / U;  // chunks of U nodes over 0..ns
+    issue(0, 0);
+    if (nch > 1) issue(1, U);
+    for (int ch = 0; ch < nch; ++ch) {
+        if (ch + 1 < nch) cp_async_wait<1>();
+        else cp_async_wait<0>();
+        const int st = ch & 1, m0 = ch * U;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int m = m0 + u;
             if (m > ns) break;
+            const float2 *b = stg + (size_t)((st * U + u) * NW) * kThreads + tid;
             float wa, wb;
             node_weights(m, na, ns, wa, wb);
             // g at node m and g' at node N_s - m see the same field (block B from N_A on)
             const bool bk = m >= na;
-            const float2 a = av[u], b = bv[u];
+            const float2 a = b[0], bb = b[kThreads];
             float t0, t1;
             if (!DIFF) {
-                t0 = a.x * b.x * (bk ? r2[1][0] : r2[0][0]);
-                t1 = a.y * b.y * (bk ? r2[1][1] : r2[0][1]);
+                t0 = a.x * bb.x * (bk ? r2[1][0] : r2[0][0]);
+                t1 = a.y * bb.y * (bk ? r2[1][1] : r2[0][1]);
             } else {
-                const float2 da = dav[u], db = dbv[u];
+                const float2 da = b[2 * kThreads], db = b[3 * kThreads];
                 const float ri0 = bk ? ri[1][0] : ri[0][0], ri1 = bk ? ri[1][1] : ri[0][1];
                 const float q0 = bk ? dd[1][0] : dd[0][0], q1 = bk ? dd[1][1] : dd[0][1];
                 const float rs0 = bk ? rs[1][0] : rs[0][0], rs1 = bk ? rs[1][1] : rs[0][1];
                 // g~ = a~ / E and dg = (d a - rho a~) / E' of both chains
-                const float ga0 = a.x * ri0, ga1 = a.y * ri1, gb0 = b.x * ri0, gb1 = b.y * ri1;
+                const float ga0 = a.x * ri0, ga1 = a.y * ri1, gb0 = bb.x * ri0, gb1 = bb.y * ri1;
                 const float dga0 = (da.x - q0 * a.x) * rs0, dga1 = (da.y - q1 * a.y) * rs1;
-                const float dgb0 = (db.x - q0 * b.x) * rs0, dgb1 = (db.y - q1 * b.y) * rs1;
+                const float dgb0 = (db.x - q0 * bb.x) * rs0, dgb1 = (db.y - q1 * bb.y) * rs1;
                 t0 = ga0 * dgb0 + dga0 * gb0 + dga0 * dgb0;
                 t1 = ga1 * dgb1 + dga1 * gb1 + dga1 * dgb1;
             }
@@ -512,6 +544,7 @@ __global__ void __launch_bounds__(kThreads) prop_contour(ContourK k)
                 sb1.add(wb * t1);
             }
         }
+        if (ch + 2 < nch) issue(st, (ch + 2) * U);  // this stage's values are consumed
     }
     const double ia0 = sa0.value(), ib0 = sb0.value(), ia1 = sa1.value(), ib1 = sb1.value();
     const double ds = k.g.ds, php = k.g.phi_p;
@@ -675,12 +708,21 @@ cudaError_t launch_cluster_solve(Group &G, cudaStream_t s, bool diff, int nprep_
     c.err = G.err;
     const int npk = G.g.nx * G.g.ny / 2;
     const dim3 grid((npk + kThreads - 1) / kThreads, G.g.nruns), gq(kQBlocks, G.g.nruns);
+    static bool conf = false;
+    if (!conf) {
+        cudaError_t e1 = cudaFuncSetAttribute(prop_contour<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)ContourStage<true>::SMEM);
+        cudaError_t e2 = cudaFuncSetAttribute(prop_contour<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)ContourStage<false>::SMEM);
+        if (e1 || e2) return e1 ? e1 : e2;
+        conf = true;
+    }
     if (diff) {
         prop_qsum<true><<<gq, kThreads, 0, s>>>(c);
-        prop_contour<true><<<grid, kThreads, 0, s>>>(c);
+        prop_contour<true><<<grid, kThreads, ContourStage<true>::SMEM, s>>>(c);
     } else {
         prop_qsum<false><<<gq, kThreads, 0, s>>>(c);
-        prop_contour<false><<<grid, kThreads, 0, s>>>(c);
+        prop_contour<false><<<grid, kThreads, ContourStage<false>::SMEM, s>>>(c);
     }
     return cudaGetLastError();
 }
