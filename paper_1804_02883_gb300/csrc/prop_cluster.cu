@@ -502,13 +502,16 @@ __global__ void __launch_bounds__(kThreads) prop_contour(ContourK k)
         }
         cp_async_commit();
     };
+    // a ring of NSTAGE chunks: chunk ch + NSTAGE goes into chunk ch's stage
+    // once ch is consumed; every issue commits a group (empty past N_s), so
+    // waiting until at most NSTAGE - 1 groups are pending completes chunk ch
+    constexpr int NST = CS::NSTAGE;
     const int nch = (ns + U) / U;  // chunks of U nodes over 0..ns
-    issue(0, 0);
-    if (nch > 1) issue(1, U);
+#pragma unroll
+    for (int c = 0; c < NST; ++c) issue(c, c * U);
     for (int ch = 0; ch < nch; ++ch) {
-        if (ch + 1 < nch) cp_async_wait<1>();
-        else cp_async_wait<0>();
-        const int st = ch & 1, m0 = ch * U;
+        cp_async_wait<NST - 1>();
+        const int st = ch % NST, m0 = ch * U;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int m = m0 + u;
@@ -544,7 +547,7 @@ __global__ void __launch_bounds__(kThreads) prop_contour(ContourK k)
                 sb1.add(wb * t1);
             }
         }
-        if (ch + 2 < nch) issue(st, (ch + 2) * U);  // this stage's values are consumed
+        issue(st, (ch + NST) * U);  // this stage's values are consumed
     }
     const double ia0 = sa0.value(), ib0 = sb0.value(), ia1 = sa1.value(), ib1 = sb1.value();
     const double ds = k.g.ds, php = k.g.phi_p;
