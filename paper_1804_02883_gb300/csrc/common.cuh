@@ -145,6 +145,16 @@ __device__ __forceinline__ V2<T> *fft_smem_mr(V2<T> *x, V2<T> *y, int N, int nf,
     return x;
 }
 
+// 8-byte asynchronous copy global -> shared (the thread's own staging
+// slot), and the commit / wait of the thread's copy groups
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // Block-wide sum of one double per thread (blockDim.x a multiple of 32, at
 // most 1024).  Fixed order: deterministic.  Result valid in thread 0.
 __device__ __forceinline__ double block_sum(double v, double *scratch32)

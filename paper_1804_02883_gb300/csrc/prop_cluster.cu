@@ -401,16 +401,6 @@ __global__ void __launch_bounds__(kThreads) prop_qsum(ContourK k)
     if (threadIdx.x == 0) k.part[(size_t)run * kMaxPart + blockIdx.x] = s;
 }
 
-// 8-byte asynchronous copy global -> shared (the thread's own staging
-// slot), and the commit / wait of the thread's copy groups
-__device__ __forceinline__ void cp_async8(void *smem, const void *gmem)
-{
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
 // Contour chunks staged per thread: U nodes of each stream (g, g' and, in the
 // differential pass, their changes), two stages in flight.
 template <bool DIFF> struct ContourStage {
