@@ -76,25 +76,41 @@ __device__ __forceinline__ V2<T> *fft_smem(V2<T> *x, V2<T> *y, int logN, int log
     return x;
 }
 
-// One radix-P butterfly of the mixed-radix Stockham transform below.  The
-// p-th roots are tw[k m] (m = N/P); (u v mod P) m and v j s stay below N.
+// Quotient of 0 <= n < 2^24 by a positive d through the float reciprocal,
+// corrected to the exact integer quotient (a runtime integer division costs
+// tens of instructions; this one a handful).
+struct FastDiv {
+    int d;
+    float inv;
+    __device__ __forceinline__ explicit FastDiv(int d_) : d(d_), inv(1.0f / (float)d_) {}
+    __device__ __forceinline__ int div(int n) const
+    {
+        int q = __float2int_rz((float)n * inv);
+        if ((q + 1) * d <= n) ++q;
+        if (q * d > n) --q;
+        return q;
+    }
+};
+
+// One radix-P butterfly of the mixed-radix Stockham transform below (q = r
+// mod s, j = r / s).  The p-th roots are tw[k m] (m = N/P); (u v mod P) m and
+// v j s stay below N.
 template <typename T, bool INVERSE, int P>
-__device__ __forceinline__ void fft_mr_butterfly(const V2<T> *x, V2<T> *y, const V2<T> *tw, int base, int r, int m, int s,
-                                                 int sn)
+__device__ __forceinline__ void fft_mr_butterfly(const V2<T> *x, V2<T> *y, const V2<T> *tw, int base, int r, int q, int j,
+                                                 int m, int s, int sn)
 {
-    const int q = r % s, j = r / s;
-    V2<T> in[P];
+    V2<T> in[P], root[P];
 #pragma unroll
-    for (int u = 0; u < P; ++u) in[u] = x[base + (r + u * m) * sn];
+    for (int u = 0; u < P; ++u) {
+        in[u] = x[base + (r + u * m) * sn];
+        root[u] = tw[u * m];  // the P-th roots of unity
+        if (INVERSE) root[u].y = -root[u].y;
+    }
 #pragma unroll
     for (int v = 0; v < P; ++v) {
         V2<T> acc = in[0];
 #pragma unroll
-        for (int u = 1; u < P; ++u) {
-            V2<T> w = tw[((u * v) % P) * m];
-            if (INVERSE) w.y = -w.y;
-            acc = cadd(acc, cmul(in[u], w));
-        }
+        for (int u = 1; u < P; ++u) acc = cadd(acc, cmul(in[u], root[(u * v) % P]));
         if (v) {
             V2<T> w = tw[v * j * s];
             if (INVERSE) w.y = -w.y;
@@ -117,23 +133,26 @@ __device__ __forceinline__ V2<T> *fft_smem_mr(V2<T> *x, V2<T> *y, int N, int nf,
                                               const V2<T> *tw)
 {
     int s = 1;
+    const FastDiv fb(B);
     for (int st = 0; st < nf; ++st) {
         const int p = fac[st], m = N / p, total = m * B;
+        const FastDiv fm(m), fs(s);
         for (int t = threadIdx.x; t < total; t += blockDim.x) {
             int b, r;
             if (BATCH_FAST) {
-                b = t % B;
-                r = t / B;
+                r = fb.div(t);
+                b = t - r * B;
             } else {
-                b = t / m;
-                r = t % m;
+                b = fm.div(t);
+                r = t - b * m;
             }
+            const int j = fs.div(r), q = r - j * s;
             const int base = b * sb;
             switch (p) {
-            case 2: fft_mr_butterfly<T, INVERSE, 2>(x, y, tw, base, r, m, s, sn); break;
-            case 3: fft_mr_butterfly<T, INVERSE, 3>(x, y, tw, base, r, m, s, sn); break;
-            case 4: fft_mr_butterfly<T, INVERSE, 4>(x, y, tw, base, r, m, s, sn); break;
-            default: fft_mr_butterfly<T, INVERSE, 5>(x, y, tw, base, r, m, s, sn); break;
+            case 2: fft_mr_butterfly<T, INVERSE, 2>(x, y, tw, base, r, q, j, m, s, sn); break;
+            case 3: fft_mr_butterfly<T, INVERSE, 3>(x, y, tw, base, r, q, j, m, s, sn); break;
+            case 4: fft_mr_butterfly<T, INVERSE, 4>(x, y, tw, base, r, q, j, m, s, sn); break;
+            default: fft_mr_butterfly<T, INVERSE, 5>(x, y, tw, base, r, q, j, m, s, sn); break;
             }
         }
         __syncthreads();
