@@ -305,6 +305,14 @@ int epd_lb_width(epd_lb *h, int32_t run, double *out);
 int epd_lb_particles(epd_lb *h, int32_t run, double threshold, int32_t max_particles, int32_t *count,
                      double *stats, int32_t *labels);
 
+/* Self-test of the failure path of the cluster solve's exchanges: one CTA
+ * waits, with the same bounded wait as every exchange of the solve, on a
+ * barrier that nothing arrives on; after limit_ms milliseconds (1..2000, at
+ * the device's base clock) it gives up and sets the error bit that
+ * epd_lb_sync reports as EPD_LB_ETIMEOUT.  *timed_out = 1 when that bit was
+ * set.  The context stays usable.  Synchronous on cuda_stream. */
+int epd_selftest_bounded_wait(int32_t limit_ms, void *cuda_stream, int32_t *timed_out);
+
 /* Text of the last error on the handle (never NULL). */
 const char *epd_lb_last_error(const epd_lb *h);
 

@@ -39,7 +39,7 @@ SYMBOLS = (
     "epd_lb_surrogate_workspace_bytes", "epd_lb_set_surrogate", "epd_lb_surrogate_stats", "epd_lb_fields_dev",
     "epd_lb_set_inversion", "epd_lb_inversion_stats", "epd_lb_sigma_delta", "epd_lb_width", "epd_lb_particles",
     "epd_prop_solve3d_workspace_bytes", "epd_prop_solve3d", "epd_lb3d_step", "epd_step3d_workspace_bytes",
-    "epd_step3d",
+    "epd_step3d", "epd_selftest_bounded_wait",
 )
 
 
@@ -132,6 +132,7 @@ def lib():
             "epd_prop_solve3d": (ctypes.c_int, [P, i32, vp, vp, vp, vp, ctypes.c_size_t, vp]),
             "epd_lb3d_step": (ctypes.c_int, [P, i32, vp, vp, vp, vp, vp]),
             "epd_step3d_workspace_bytes": (ctypes.c_int, [P, i32, szp]),
+            "epd_selftest_bounded_wait": (ctypes.c_int, [i32, vp, vp]),
             "epd_step3d": (ctypes.c_int, [P, i32, vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]),
             "epd_lb_enable_timing": (ctypes.c_int, [vp, i32]),
             "epd_lb_kernel_times": (ctypes.c_int, [vp, vp]),
@@ -289,6 +290,19 @@ def step3d(run: RunParams, omega, pop, vel, nsteps: int = 1):
             raise EpdLbError(rc, "epd_step3d")
     st.synchronize()
     return tuple(t.cpu().numpy() for t in (om, pd, vd, phi, q, force))
+
+
+def selftest_bounded_wait(limit_ms: int = 50) -> bool:
+    """Whether the cluster solve's bounded exchange wait gives up (and reports
+    it) on a barrier nothing arrives on."""
+    import torch
+
+    out = np.zeros(1, dtype=np.int32)
+    rc = lib().epd_selftest_bounded_wait(int(limit_ms), torch.cuda.current_stream().cuda_stream,
+                                         out.ctypes.data_as(ctypes.c_void_p))
+    if rc:
+        raise EpdLbError(rc, "epd_selftest_bounded_wait")
+    return bool(out[0])
 
 
 def epd_prop_solve_noalloc(run: RunParams, omega_dev: int, phi_dev: int, q_dev: int, stream: int = 0) -> None:

@@ -1445,6 +1445,24 @@ extern "C" int epd_step3d(const epd_lb_params *p, int32_t nz, double *omega_dev,
     return e ? EPD_LB_ECUDA : EPD_LB_OK;
 }
 
+extern "C" int epd_selftest_bounded_wait(int32_t limit_ms, void *cuda_stream, int32_t *timed_out)
+{
+    if (!timed_out || limit_ms < 1 || limit_ms > 2000) return EPD_LB_EINVAL;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int dev = 0, khz = 0;
+    if (cudaGetDevice(&dev) || cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev)) return EPD_LB_ECUDA;
+    int *err = nullptr, host = 0;
+    if (cudaMallocAsync((void **)&err, sizeof(int), s)) return EPD_LB_ECUDA;
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), s);
+    if (!e) e = launch_selftest_wait(err, (long long)limit_ms * (long long)(khz > 0 ? khz : 2000000), s);
+    if (!e) e = cudaMemcpyAsync(&host, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(err, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return EPD_LB_ECUDA;
+    *timed_out = (host & 4) ? 1 : 0;
+    return EPD_LB_OK;
+}
+
 static bool solve_group(const epd_lb_params *p, Group &G)
 {
     if (!p || !validate(*p).empty()) return false;

@@ -181,6 +181,9 @@ size_t cluster_state_floats2(int nx, int ny, int ns);  // per run, both chains
 cudaError_t launch_cluster_solve(Group &G, cudaStream_t s, bool diff, int nprep_blocks, double *phi, double *q,
                                  const SolveProbe *probe, const double *phi_ref = nullptr, const double *q_ref = nullptr);
 int cluster_ctas(const Group &G);
+// The bounded exchange wait of prop_chain on a barrier nothing arrives on:
+// sets bit 2 of *err after limit_cycles (test of the failure path).
+cudaError_t launch_selftest_wait(int *err, long long limit_cycles, cudaStream_t s);
 
 // Single-chain solve on an nz x ny x nx box (layout [z][y][x]): the
 // streaming passes over three views of one array, z pillars (a 2D view with

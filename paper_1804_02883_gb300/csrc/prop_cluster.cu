@@ -116,15 +116,16 @@ __device__ __forceinline__ bool mbar_test(unsigned bar, unsigned parity)
         : "memory");
     return ok != 0;
 }
-// Wait for the phase with the given parity to complete, giving up after about
-// 2^31 cycles: then `failed` is set and every later wait returns at once (the
-// kernel runs to its end with the same barrier sequence and reports the error).
-__device__ __forceinline__ void mbar_wait(unsigned bar, unsigned parity, int &failed)
+// Wait for the phase with the given parity to complete, giving up after
+// `limit` cycles (about 2^31, a second): then `failed` is set and every later
+// wait returns at once (the kernel runs to its end with the same barrier
+// sequence and reports the error).
+__device__ __forceinline__ void mbar_wait(unsigned bar, unsigned parity, int &failed, long long limit = 1ll << 31)
 {
     if (failed) return;
     const long long t0 = clock64();
     while (!mbar_test(bar, parity))
-        if (clock64() - t0 > (1ll << 31)) {
+        if (clock64() - t0 > limit) {
             failed = 1;
             return;
         }
@@ -365,6 +366,25 @@ __device__ __forceinline__ void node_weights(int j, int na, int ns, float &wa, f
 {
     wa = (na == 0 || j > na) ? 0.f : ((j == 0 || j == na) ? 0.5f : 1.f);
     wb = (na == ns || j < na) ? 0.f : ((j == na || j == ns) ? 0.5f : 1.f);
+}
+
+// Self-test of the bounded wait: one CTA waits on an exchange barrier that
+// nothing arrives on, with the given limit, and reports the give-up in the
+// error word exactly as prop_chain does (bit 2).
+__global__ void selftest_wait(int *err, long long limit)
+{
+    __shared__ __align__(8) unsigned long long mbar;
+    const unsigned bar = smem_u32(&mbar);
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    int failed = 0;
+    mbar_wait(bar, 0, failed, limit);  // phase 0 never completes
+    if (failed && threadIdx.x == 0) atomicOr(err, 4);
+    __syncthreads();
+    if (threadIdx.x == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
 }
 
 // Q partials from node N_s of the g chain: Q_P = mean g_{N_s} with
@@ -651,6 +671,12 @@ int cluster_ctas(const Group &G)
 {
     const ClusterShape *sh = find_shape(G.g.logx, G.g.logy);
     return sh ? sh->c : 0;
+}
+
+cudaError_t launch_selftest_wait(int *err, long long limit_cycles, cudaStream_t s)
+{
+    selftest_wait<<<1, 32, 0, s>>>(err, limit_cycles);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_cluster_solve(Group &G, cudaStream_t s, bool diff, int nprep_blocks, double *phi, double *q,
