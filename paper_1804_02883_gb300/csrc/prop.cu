@@ -242,7 +242,8 @@ __global__ void __launch_bounds__(kThreads) prop_prep_delta(GroupGeom g, const d
         if (c2p) {
             // rho (2 + rho) per block in the packed-row layout of the cluster
             // solve: site (y, x) -> packed row y / 2, component y & 1
-            const long long y = i / g.nx, x = i % g.nx, hn = n / 2;
+            // (the cluster solve's grids are powers of two: shift and mask)
+            const long long y = i >> g.logx, x = i & (g.nx - 1), hn = n / 2;
             const size_t o = (size_t)((y >> 1) * g.nx + x) * 2 + (y & 1);
             c2p[((size_t)run * 2 + 0) * hn * 2 + o] = qa * (2.f + qa);
             c2p[((size_t)run * 2 + 1) * hn * 2 + o] = qb * (2.f + qb);

@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(kThreads) prop_qsum(ContourK k)
     const float2 *rho = DIFF ? k.rho + (size_t)run * n : nullptr;
     float acc = 0.f;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npk; i += gridDim.x * blockDim.x) {
-        const int kk = i / nx, x = i % nx, s0 = 2 * kk * nx + x, s1 = s0 + nx;
+        const int kk = i >> k.g.logx, x = i & (nx - 1), s0 = 2 * kk * nx + x, s1 = s0 + nx;
         const float2 e0 = efac[s0], e1 = efac[s1], a = a_ns[i];
         const float E0 = bm ? e0.y : e0.x, E1 = bm ? e1.y : e1.x;
         if (!DIFF) {
@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(kThreads) prop_contour(ContourK k)
     const int npk = nx * ny / 2;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= npk) return;
-    const int kk = i / nx, x = i % nx;
+    const int kk = i >> k.g.logx, x = i & (nx - 1);  // power-of-two grids
     const int s0 = 2 * kk * nx + x, s1 = s0 + nx;
     const int slot = kk * nx + x;
     const float2 *efac = k.efac + (size_t)run * n;
