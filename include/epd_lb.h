@@ -14,6 +14,12 @@
  *   5. polymer force from Phi(t+dt) - Phi~                   (Sec. 2, Eqs. (19)-(20))
  *   6. D2Q9 MRT collide-stream with that force plus the
  *      reverse-Poiseuille body force                         (Eqs. (12), (14)-(16), (23))
+ * epd_lb_set_inversion switches to the exact step of App. C (convection of
+ * Phi and the Fletcher-Reeves inversion in place of steps 1-2); the learned
+ * surrogate (epd_lb_set_surrogate) can stand in for the solves; the analysis
+ * calls (epd_lb_sigma_delta, epd_lb_width, epd_lb_particles) evaluate the
+ * observables of Sec. 3 and Sec. 4; the epd_*3d entry points run the solve,
+ * D3Q19 and the coupled step on 3D boxes with state in caller memory.
  *
  * Conventions for every entry point:
  *  - Return EPD_LB_OK (0) on success or a negative EPD_LB_E* code; the text
