@@ -356,6 +356,9 @@ __global__ void __launch_bounds__(RowTile<LOGX>::T) epd_row8(EpdK k)
         } else {
             v = cz[((size_t)run * 4 + 2) * n + s];
         }
+        // the column pass of the same operator reads this FP32 input from the
+        // free scratch planes 2, 3 instead of forming it again from FP64 fields
+        if (MODE == ROW_GRAD || MODE == ROW_LAP) cz[((size_t)run * 4 + 2 + pair) * n + s] = v;
         buf[RL::at(i / NX, i % NX)] = v;
     }
     __syncthreads();
@@ -413,11 +416,8 @@ __global__ void __launch_bounds__(ColTile<LOGY, CW>::T) epd_col8(EpdK k)
         const int i = tid + u * T;
         const long long s = (long long)(i / C) * nx + x0 + (i % C);
         float2 v;
-        if (MODE == COL_CONVECT) {
-            const double *om = k.omega + (size_t)run * 3 * n;
-            v = pair == 0 ? f2((float)om[s], (float)om[n + s]) : f2((float)om[2 * n + s], 0.f);
-        } else if (MODE == COL_DIFFUSE) {
-            v = mu_pair_f(k, k.phi_t + (size_t)run * 3 * n, k.omega_t + (size_t)run * 3 * n, n, s, pair);
+        if (MODE == COL_CONVECT || MODE == COL_DIFFUSE) {
+            v = cz[((size_t)run * 4 + 2 + pair) * n + s];  // stored by the row pass (omega, mu in FP32)
         } else {
             v = cz[((size_t)run * 4 + 2) * n + s];
         }
