@@ -88,3 +88,16 @@ def test_particles_connectivity_threshold_and_periodic_wrap(oracle_lib):
     L = p.nx * p.dx
     assert abs((a["cx"] - 11 * p.dx) % L - b["cx"]) < 1e-12 and abs((a["cy"] - 7 * p.dx) % L - b["cy"]) < 1e-12
     assert labels[15, 15] == 0 and labels[0, 0] == 0  # wraps in x and y
+
+
+def test_sigma_of_eq21(oracle_lib):
+    # sigma = mean |Phi_P - phi_p|: 0 for the homogeneous state, a for a field
+    # that deviates by +-a everywhere, and a / 2 when half the sites deviate
+    p = O.Params(nx=8, ny=4, phi_p=0.2)
+    assert O.sigma(p, _phi(p, np.full((p.ny, p.nx), 0.2))) == 0.0
+    rng = np.random.default_rng(2)
+    sgn = np.where(rng.random((p.ny, p.nx)) < 0.5, -1.0, 1.0)
+    assert abs(O.sigma(p, _phi(p, 0.2 + 1e-3 * sgn)) - 1e-3) < 1e-17
+    half = np.zeros((p.ny, p.nx))
+    half[:, : p.nx // 2] = 4e-3
+    assert abs(O.sigma(p, _phi(p, 0.2 + half)) - 2e-3) < 1e-17
