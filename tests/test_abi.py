@@ -52,3 +52,60 @@ def test_invalid_parameters_rejected(bad):
     with pytest.raises(P.EpdLbError) as ei:
         P.epd_lb_workspace_bytes([p])
     assert ei.value.code == -1
+
+
+def _rc(fn, *args):
+    return getattr(P.lib(), fn)(*args)
+
+
+def test_empty_and_null_arguments_rejected():
+    import ctypes
+
+    n = ctypes.c_size_t(7)
+    one = P.binding._params_array([W.plain_small()])
+    assert _rc("epd_lb_workspace_bytes", one, 0, ctypes.byref(n)) == -1
+    assert _rc("epd_lb_workspace_bytes", None, 1, ctypes.byref(n)) == -1
+    assert _rc("epd_lb_workspace_bytes", one, 1, None) == -1
+    assert n.value == 7  # nothing written on failure
+    h = ctypes.c_void_p(0)
+    assert _rc("epd_lb_init", one, 0, None, 0, None, ctypes.byref(h)) == -1 and not h.value
+    assert _rc("epd_lb_init", None, 1, None, 0, None, ctypes.byref(h)) == -1 and not h.value
+    assert _rc("epd_lb_init", one, 1, None, 0, None, None) == -1
+    c = W.plain_small().c()
+    assert _rc("epd_prop_solve_workspace_bytes", None, ctypes.byref(n)) == -1
+    assert _rc("epd_prop_solve_workspace_bytes", ctypes.byref(c), None) == -1
+    # the stateless solve checks its pointers before touching the device
+    assert _rc("epd_prop_solve", ctypes.byref(c), None, None, None, None, 0, None) == -1
+    assert _rc("epd_sur_workspace_bytes", 32, 64, 0, 0, ctypes.byref(n)) == -1
+    assert _rc("epd_sur_workspace_bytes", 32, 40, 1, 0, ctypes.byref(n)) == -1
+    assert _rc("epd_sur_workspace_bytes", 36, 64, 1, 0, ctypes.byref(n)) == -1
+    assert _rc("epd_sur_workspace_bytes", 32, 64, 1, 0, None) == -1
+    assert _rc("epd_lb_surrogate_workspace_bytes", None, ctypes.byref(n)) == -1
+    assert n.value == 7
+
+
+def test_mach_preflight_refuses_before_any_device_call():
+    import ctypes
+
+    h = ctypes.c_void_p(0)
+    fast = P.binding._params_array([W.with_(W.plain_small(), f0=1e9)])
+    assert _rc("epd_lb_init", fast, 1, None, 0, None, ctypes.byref(h)) == -5 and not h.value
+
+
+def test_box_rules_of_the_3d_entry_points():
+    run = W.with_(W.plain_small(), nx=32, ny=32, ns=8)
+    solve = P.epd_prop_solve3d_workspace_bytes(run, 16)
+    # the coupled 3D step holds the solve's workspace and more
+    import ctypes
+
+    n = ctypes.c_size_t()
+    assert _rc("epd_step3d_workspace_bytes", ctypes.byref(run.c()), 16, ctypes.byref(n)) == 0
+    assert n.value > solve > 0
+    assert P.epd_prop_solve3d_workspace_bytes(W.with_(run, nx=30, ny=20), 12) > 0  # mixed radix
+    for nz in (0, 7, 14, 4096):  # odd, not 2^a 3^b 5^c, beyond the longest axis
+        with pytest.raises(P.EpdLbError):
+            P.epd_prop_solve3d_workspace_bytes(run, nz)
+    with pytest.raises(P.EpdLbError):  # 2^23 sites: beyond the 2^22-site limit
+        P.epd_prop_solve3d_workspace_bytes(W.with_(run, nx=256, ny=256), 128)
+    assert _rc("epd_step3d_workspace_bytes", ctypes.byref(run.c()), 7, ctypes.byref(n)) == -1
+    assert _rc("epd_prop_solve3d_workspace_bytes", None, 16, ctypes.byref(n)) == -1
