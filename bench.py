@@ -235,6 +235,47 @@ def time_steps(h, stream, steps, flush, with_kernels=False):
     return per_step, kern
 
 
+def analysis_section(torch, h, runs, flush, hbm, calls=20):
+    """The observables (masses, sigma of Eq. (21), max |u|) and the analysis of
+    Secs. 3-4 (sigma_Delta of Eq. (22) between runs 0 and 1, Y_2^P of Eq. (30),
+    the particles of Phi_P >= 0.5 with their gyration tensors) on run 0 of the
+    workload, each a host call that returns its result: CUDA-event time per
+    call on the handle's stream (L2 flushed before each call, the result's
+    device-to-host copy included), and the HBM fraction of the reductions'
+    algorithmic bytes (FP64 fields read once)."""
+    r0 = runs[0]
+    n = r0.nx * r0.ny
+    pop_bytes = 4 if r0.precision == 1 else 8
+    fns = {"observables": (lambda: h.observables(0), 24 + 9 * pop_bytes + 2 * pop_bytes),
+           "width": (lambda: h.width(0), 16),
+           "particles": (lambda: h.particles(0, 0.5, 64), None)}
+    if len(runs) > 1 and (runs[1].nx, runs[1].ny) == (r0.nx, r0.ny):
+        fns["sigma_delta"] = (lambda: h.sigma_delta(0, 1), 32)
+    out = {"sites": n}
+    for name, (fn, bps) in fns.items():
+        fn()
+        ms = []
+        for _ in range(calls):
+            with torch.cuda.stream(h.stream):
+                flush.add_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(h.stream)
+            fn()
+            b.record(h.stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        t = statistics.median(ms)
+        d = {"ms_per_call": t, "calls": calls}
+        if bps is not None:
+            gbs = bps * n / (t * 1e-3) / 1e9
+            d.update({"bytes_per_site": bps, "achieved_gbs": gbs, "frac": gbs / hbm})
+        out[name] = d
+    out["note"] = ("two launches per reduction (a fixed grid of partial sums, then one block summing them in a "
+                   "fixed order) and the copy of the result: launch- and latency-bound at this size")
+    return out
+
+
 def surrogate_section(P, W, torch, runs, h, flush, args):
     """Train the density surrogate on exact pairs from the workload's own
     trajectory, then step it (exact every 8th step) against an exact run from
@@ -444,6 +485,8 @@ def main():
            "h2d_bytes_per_step": int(sum(3 * r.nx * r.ny * 8 for r in runs)),
            "d2h_bytes_per_step": int(sum(3 * r.nx * r.ny * 8 + 16 for r in runs))}
 
+    analysis = analysis_section(torch, h, runs, flush, hbm)
+
     # learned surrogate (exact every 8th step) on the same workload
     sur = None
     if args.surrogate_steps > 0 and all(r.nx % 16 == 0 and r.ny % 8 == 0 for r in runs) and len({(r.nx, r.ny) for r in runs}) == 1:
@@ -499,6 +542,7 @@ def main():
             "roofline": roofline,
             "surrogate": sur,
             "exact_step": exact,
+            "analysis": analysis,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": n_launches * args.steps,

@@ -26,7 +26,6 @@
 namespace epdlb {
 namespace {
 
-constexpr int kAnThreads = 1024;
 constexpr int kScanBlock = 1024;  // sites per block of the root numbering
 constexpr int kMoments = 7;       // sites, N, sum w dx, sum w dy, sum w dx^2, sum w dx dy, sum w dy^2
 
@@ -43,23 +42,40 @@ __device__ double block_sum_an(double v, double *red)
     return r;
 }
 
-// one block: fixed per-thread strides and a fixed tree, so reruns agree bitwise
-__global__ void __launch_bounds__(kAnThreads) an_sigma_delta(const double *pa, const double *pb, long long n, double *out)
+// Stage 1 of the two-stage reductions: a fixed grid of an_blocks(n) blocks of
+// kPartThreads, each writing its block sums into part (slot k of block j at
+// k * kRedBlocks + j); stage 2 (an_finish) sums the partials of every slot in
+// a fixed order, so a rerun is bitwise equal.
+constexpr int kPartThreads = 256;
+
+int an_blocks(long long n)
+{
+    const long long b = (n + kPartThreads - 1) / kPartThreads;
+    return (int)(b < 1 ? 1 : (b > kRedBlocks ? kRedBlocks : b));
+}
+
+// sum |Phi_P^a - Phi_P^b| (Eq. (22))
+__global__ void __launch_bounds__(kPartThreads) an_sigma_delta(const double *pa, const double *pb, long long n, double *part)
 {
     __shared__ double red[32];
     double s = 0.0;
-    for (long long i = threadIdx.x; i < n; i += blockDim.x) s += fabs((pa[i] + pa[n + i]) - (pb[i] + pb[n + i]));
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        s += fabs((pa[i] + pa[n + i]) - (pb[i] + pb[n + i]));
     const double r = block_sum_an(s, red);
-    if (threadIdx.x == 0) *out = r / (double)n;
+    if (threadIdx.x == 0) part[blockIdx.x] = r;
 }
 
-__global__ void __launch_bounds__(kAnThreads) an_width(const double *phi, int nx, int ny, double dx, double phi_p, double *out)
+// sum y_c^2 Phi_P and sum y_c^2 (Eq. (30)), y_c the row's distance from the
+// centre of its channel
+__global__ void __launch_bounds__(kPartThreads) an_width(const double *phi, int nx, int ny, double dx, double *part)
 {
     __shared__ double red[32];
     const long long n = (long long)nx * ny;
     const double h = 0.5 * (double)ny;
     double num = 0.0, den = 0.0;
-    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const double yy = (double)(i / nx) + 0.5;
         const double yc = (yy - (yy < h ? 0.5 * h : 1.5 * h)) * dx;
         num += yc * yc * (phi[i] + phi[n + i]);
@@ -67,7 +83,27 @@ __global__ void __launch_bounds__(kAnThreads) an_width(const double *phi, int nx
     }
     const double a = block_sum_an(num, red);
     const double b = block_sum_an(den, red);
-    if (threadIdx.x == 0) *out = sqrt(a / (phi_p * b));
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = a;
+        part[kRedBlocks + blockIdx.x] = b;
+    }
+}
+
+enum AnKind { AN_SIGMA_DELTA = 0, AN_WIDTH = 1 };
+
+// SIGMA_DELTA: out = sum / n;  WIDTH: out = sqrt(sum_num / (phi_p sum_den))
+template <int KIND>
+__global__ void __launch_bounds__(kPartThreads) an_finish(const double *part, int nb, long long n, double phi_p, double *out)
+{
+    __shared__ double red[32];
+    double a = 0.0, b = 0.0;
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+        a += part[j];
+        if (KIND == AN_WIDTH) b += part[kRedBlocks + j];
+    }
+    const double ra = block_sum_an(a, red);
+    const double rb = KIND == AN_WIDTH ? block_sum_an(b, red) : 0.0;
+    if (threadIdx.x == 0) *out = KIND == AN_WIDTH ? sqrt(ra / (phi_p * rb)) : ra / (double)n;
 }
 
 __device__ __forceinline__ int find_root(const int *lab, int i)
@@ -244,15 +280,21 @@ int grid_of(long long n, int threads)
 
 } // namespace
 
-cudaError_t launch_sigma_delta(const double *phi_a, const double *phi_b, long long n, double *out_dev, cudaStream_t s)
+cudaError_t launch_sigma_delta(const double *phi_a, const double *phi_b, long long n, double *part, double *out_dev,
+                               cudaStream_t s)
 {
-    an_sigma_delta<<<1, kAnThreads, 0, s>>>(phi_a, phi_b, n, out_dev);
+    const int nb = an_blocks(n);
+    an_sigma_delta<<<nb, kPartThreads, 0, s>>>(phi_a, phi_b, n, part);
+    an_finish<AN_SIGMA_DELTA><<<1, kPartThreads, 0, s>>>(part, nb, n, 0.0, out_dev);
     return cudaGetLastError();
 }
 
-cudaError_t launch_width(const Group &G, int run, double *out_dev, cudaStream_t s)
+cudaError_t launch_width(const Group &G, int run, double *part, double *out_dev, cudaStream_t s)
 {
-    an_width<<<1, kAnThreads, 0, s>>>(G.phi + (size_t)run * 3 * G.g.n, G.g.nx, G.g.ny, G.g.dx, G.g.phi_p, out_dev);
+    const long long n = G.g.n;
+    const int nb = an_blocks(n);
+    an_width<<<nb, kPartThreads, 0, s>>>(G.phi + (size_t)run * 3 * n, G.g.nx, G.g.ny, G.g.dx, part);
+    an_finish<AN_WIDTH><<<1, kPartThreads, 0, s>>>(part, nb, n, G.g.phi_p, out_dev);
     return cudaGetLastError();
 }
 

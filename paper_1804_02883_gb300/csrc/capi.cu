@@ -416,6 +416,11 @@ static void form_groups(const epd_lb_params *p, int nruns, std::vector<Group> &g
 
 using namespace epdlb;
 
+// Head of the handle's workspace: the device error word at 0, the observables
+// at 256, the partials of the two-stage reductions at 512.
+constexpr size_t kHeadBytes = 512 + (size_t)kRedSlots * kRedBlocks * sizeof(double);
+static_assert(kHeadBytes % 256 == 0, "workspace head");
+
 struct epd_lb {
     std::vector<Group> groups;
     std::vector<std::pair<int, int>> where;  // run -> (group, member)
@@ -426,6 +431,7 @@ struct epd_lb {
     bool own_ws = false;
     int *err = nullptr;
     double *obs = nullptr;
+    double *part = nullptr;  // partials of the two-stage reductions
     int parity = 0;
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
     bool timing = false;
@@ -479,7 +485,7 @@ extern "C" int epd_lb_workspace_bytes(const epd_lb_params *p, int32_t nruns, siz
     std::vector<Group> groups;
     std::vector<std::pair<int, int>> where;
     form_groups(p, nruns, groups, where);
-    size_t off = 512;  // error word and observables
+    size_t off = kHeadBytes;
     for (auto &G : groups) off = carve_group(G, nullptr, off);
     *bytes = off;
     return EPD_LB_OK;
@@ -618,7 +624,7 @@ extern "C" int epd_lb_init(const epd_lb_params *p, int32_t nruns, void *workspac
     }
     h->nruns = nruns;
     form_groups(p, nruns, h->groups, h->where);
-    size_t need = 512;
+    size_t need = kHeadBytes;
     for (auto &G : h->groups) need = carve_group(G, nullptr, need);
     auto bail = [&](int code) {
         epd_lb_destroy(h);
@@ -647,7 +653,8 @@ extern "C" int epd_lb_init(const epd_lb_params *p, int32_t nruns, void *workspac
     char *base = (char *)h->ws;
     h->err = (int *)base;
     h->obs = (double *)(base + 256);
-    size_t off = 512;
+    h->part = (double *)(base + 512);
+    size_t off = kHeadBytes;
     for (auto &G : h->groups) {
         off = carve_group(G, base, off);
         G.err = h->err;
@@ -967,7 +974,7 @@ extern "C" int epd_lb_observables(epd_lb *h, int32_t run, double *out)
     int m;
     if (int rc = locate(h, run, &G, &m)) return rc;
     if (!out) return fail(h, EPD_LB_EINVAL, "out is NULL");
-    CK(launch_observables(*G, m, h->parity, h->obs, h->stream), "observables");
+    CK(launch_observables(*G, m, h->parity, h->part, h->obs, h->stream), "observables");
     CK(cudaMemcpyAsync(out, h->obs, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy observables");
     CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     return EPD_LB_OK;
@@ -999,7 +1006,7 @@ extern "C" int epd_lb_sigma_delta(epd_lb *h, int32_t run_a, int32_t run_b, doubl
     if (int rc = refresh_phi(h, *Ga)) return rc;
     if (int rc = refresh_phi(h, *Gb)) return rc;
     const size_t n = (size_t)Ga->g.n;
-    CK(launch_sigma_delta(Ga->phi + (size_t)ma * 3 * n, Gb->phi + (size_t)mb * 3 * n, (long long)n, h->obs, h->stream), "sigma_Delta");
+    CK(launch_sigma_delta(Ga->phi + (size_t)ma * 3 * n, Gb->phi + (size_t)mb * 3 * n, (long long)n, h->part, h->obs, h->stream), "sigma_Delta");
     CK(cudaMemcpyAsync(out, h->obs, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "reading sigma_Delta");
     CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     return EPD_LB_OK;
@@ -1012,7 +1019,7 @@ extern "C" int epd_lb_width(epd_lb *h, int32_t run, double *out)
     if (!out) return fail(h, EPD_LB_EINVAL, "out is NULL");
     if (int rc = locate(h, run, &G, &m)) return rc;
     if (int rc = refresh_phi(h, *G)) return rc;
-    CK(launch_width(*G, m, h->obs, h->stream), "Y_2^P");
+    CK(launch_width(*G, m, h->part, h->obs, h->stream), "Y_2^P");
     CK(cudaMemcpyAsync(out, h->obs, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "reading Y_2^P");
     CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     return EPD_LB_OK;

@@ -153,8 +153,8 @@ cudaError_t launch_lb(Group &G, int parity, cudaStream_t s);   // pop[parity] ->
 
 // Analysis of Phi_P (analysis.cu): sigma_Delta of Eq. (22), Y_2^P of
 // Eq. (30), particles with their gyration tensors (Eqs. (27)-(29)).
-cudaError_t launch_sigma_delta(const double *phi_a, const double *phi_b, long long n, double *out_dev, cudaStream_t s);
-cudaError_t launch_width(const Group &G, int run, double *out_dev, cudaStream_t s);
+cudaError_t launch_sigma_delta(const double *phi_a, const double *phi_b, long long n, double *part, double *out_dev, cudaStream_t s);
+cudaError_t launch_width(const Group &G, int run, double *part, double *out_dev, cudaStream_t s);
 size_t particles_scratch_bytes(long long n, int maxp);
 // labels_dev (n int, may be null); *total_dev, *stats_dev point into scratch
 cudaError_t launch_particles(const Group &G, int run, double thr, int maxp, void *scratch, int *labels_dev,
@@ -165,7 +165,13 @@ cudaError_t launch_gather_pre_collision(Group &G, int run, int parity, double *d
 cudaError_t launch_scatter_pre_collision(Group &G, int run, int parity, const double *src, cudaStream_t s);
 cudaError_t launch_vel_to_f64(Group &G, int run, double *dst, cudaStream_t s);
 cudaError_t launch_vel_from_f64(Group &G, int run, const double *src, cudaStream_t s);
-cudaError_t launch_observables(Group &G, int run, int parity, double *out_dev, cudaStream_t s);
+// Two-stage reductions of the observables and the analysis: a fixed grid of
+// at most kRedBlocks blocks writes kRedSlots partials per block into part
+// (kRedSlots * kRedBlocks doubles), one block sums them in a fixed order, so a
+// rerun is bitwise equal.
+constexpr int kRedBlocks = 304;
+constexpr int kRedSlots = 8;
+cudaError_t launch_observables(Group &G, int run, int parity, double *part, double *out_dev, cudaStream_t s);
 // Exact copy of a run's stored populations to (dst) or from (src) FP64.
 cudaError_t launch_pop_raw(Group &G, int run, int parity, double *dst, const double *src, cudaStream_t s);
 

@@ -374,15 +374,25 @@ cudaError_t launch_pop_raw(Group &G, int run, int parity, double *dst, const dou
     return cudaGetLastError();
 }
 
-// Observables of one run, one block, fixed order: <Phi_A>, <Phi_B>, <Phi_S>,
-// sigma (Eq. (21)), LB mass / sites, max |u|, Q_P, Q_S.
+// Observables of one run: <Phi_A>, <Phi_B>, <Phi_S>, sigma (Eq. (21)), LB
+// mass / sites, max |u|, Q_P, Q_S.  Stage 1: each block of a fixed grid of
+// red_blocks(n) blocks writes its five sums and its max into part (slot k of
+// block j at k * kRedBlocks + j); stage 2: one block sums the partials in a
+// fixed order, so a rerun is bitwise equal.
+static int red_blocks(long long n)
+{
+    const long long b = (n + kThreads - 1) / kThreads;
+    return (int)(b < 1 ? 1 : (b > kRedBlocks ? kRedBlocks : b));
+}
+
 template <typename T>
-__global__ void __launch_bounds__(kThreads) observables(const double *phi, const T *post, const V2<T> *vel, const double *q,
-                                                    double phi_p, long long n, double *out)
+__global__ void __launch_bounds__(kThreads) observables_part(const double *phi, const T *post, const V2<T> *vel,
+                                                         double phi_p, long long n, double *part)
 {
     __shared__ double red[32];
     double sa = 0, sb = 0, ss = 0, sg = 0, sm = 0, vmax = 0;
-    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const double a = phi[i], b = phi[n + i];
         sa += a;
         sb += b;
@@ -395,15 +405,38 @@ __global__ void __launch_bounds__(kThreads) observables(const double *phi, const
         const double vv = sqrt((double)v.x * v.x + (double)v.y * v.y);
         vmax = vv > vmax ? vv : vmax;
     }
-    const double inv = 1.0 / (double)n;
+    double *o = part + blockIdx.x;
     double r;
-    r = block_sum(sa, red); if (threadIdx.x == 0) out[0] = r * inv;
-    r = block_sum(sb, red); if (threadIdx.x == 0) out[1] = r * inv;
-    r = block_sum(ss, red); if (threadIdx.x == 0) out[2] = r * inv;
-    r = block_sum(sg, red); if (threadIdx.x == 0) out[3] = r * inv;
-    r = block_sum(sm, red); if (threadIdx.x == 0) out[4] = 1.0 + r * inv;
-    // max reduction
-    for (int o = 16; o > 0; o >>= 1) vmax = fmax(vmax, __shfl_down_sync(0xffffffffu, vmax, o));
+    r = block_sum(sa, red); if (threadIdx.x == 0) o[0 * kRedBlocks] = r;
+    r = block_sum(sb, red); if (threadIdx.x == 0) o[1 * kRedBlocks] = r;
+    r = block_sum(ss, red); if (threadIdx.x == 0) o[2 * kRedBlocks] = r;
+    r = block_sum(sg, red); if (threadIdx.x == 0) o[3 * kRedBlocks] = r;
+    r = block_sum(sm, red); if (threadIdx.x == 0) o[4 * kRedBlocks] = r;
+    for (int w = 16; w > 0; w >>= 1) vmax = fmax(vmax, __shfl_down_sync(0xffffffffu, vmax, w));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = vmax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+        o[5 * kRedBlocks] = m;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) observables_fin(const double *part, int nb, const double *q, long long n,
+                                                        double *out)
+{
+    __shared__ double red[32];
+    const double inv = 1.0 / (double)n;
+    for (int k = 0; k < 5; ++k) {
+        double v = 0;
+        for (int j = threadIdx.x; j < nb; j += blockDim.x) v += part[k * kRedBlocks + j];
+        const double r = block_sum(v, red);
+        if (threadIdx.x == 0) out[k] = k == 4 ? 1.0 + r * inv : r * inv;
+    }
+    double vmax = 0;
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) vmax = fmax(vmax, part[5 * kRedBlocks + j]);
+    for (int w = 16; w > 0; w >>= 1) vmax = fmax(vmax, __shfl_down_sync(0xffffffffu, vmax, w));
     __syncthreads();
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = vmax;
     __syncthreads();
@@ -416,15 +449,17 @@ __global__ void __launch_bounds__(kThreads) observables(const double *phi, const
     }
 }
 
-cudaError_t launch_observables(Group &G, int run, int parity, double *out_dev, cudaStream_t s)
+cudaError_t launch_observables(Group &G, int run, int parity, double *part, double *out_dev, cudaStream_t s)
 {
     const long long n = G.g.n;
+    const int nb = red_blocks(n);
     if (G.prec == EPD_LB_MIXED_FP32)
-        observables<float><<<1, kThreads, 0, s>>>(G.phi + (size_t)run * 3 * n, reinterpret_cast<const float *>(G.pop[parity]) + (size_t)run * 9 * n,
-                                                  reinterpret_cast<const float2 *>(G.vel) + (size_t)run * n, G.q + 2 * run, G.g.phi_p, n, out_dev);
+        observables_part<float><<<nb, kThreads, 0, s>>>(G.phi + (size_t)run * 3 * n, reinterpret_cast<const float *>(G.pop[parity]) + (size_t)run * 9 * n,
+                                                        reinterpret_cast<const float2 *>(G.vel) + (size_t)run * n, G.g.phi_p, n, part);
     else
-        observables<double><<<1, kThreads, 0, s>>>(G.phi + (size_t)run * 3 * n, reinterpret_cast<const double *>(G.pop[parity]) + (size_t)run * 9 * n,
-                                                   reinterpret_cast<const double2 *>(G.vel) + (size_t)run * n, G.q + 2 * run, G.g.phi_p, n, out_dev);
+        observables_part<double><<<nb, kThreads, 0, s>>>(G.phi + (size_t)run * 3 * n, reinterpret_cast<const double *>(G.pop[parity]) + (size_t)run * 9 * n,
+                                                         reinterpret_cast<const double2 *>(G.vel) + (size_t)run * n, G.g.phi_p, n, part);
+    observables_fin<<<1, kThreads, 0, s>>>(part, nb, G.q + 2 * run, n, out_dev);
     return cudaGetLastError();
 }
 

@@ -116,3 +116,28 @@ def test_sigma_delta_coupled_against_uncoupled():
     got = h.sigma_delta(0, 1)
     assert want > 0 and abs(got - want) <= 1e-8 * want
     h.close()
+
+
+def test_observables_and_reruns_on_the_benchmark_batch():
+    # the two-stage reductions: the means, sigma of Eq. (21) and max |u| equal
+    # plain sums over the GPU's own fields, and a rerun of each reduction is
+    # bitwise equal
+    runs = W.channel_256x512(P.MIXED_FP32)
+    h = P.EpdLb(runs)
+    h.step(3)
+    h.sync()
+    p = oracle_params(runs[1])
+    phi, _ = h.densities(1)
+    vel = h.velocity(1)
+    ob = h.observables(1)
+    for k, key in enumerate(("mean_phi_a", "mean_phi_b", "mean_phi_s")):
+        assert abs(ob[key] - phi[k].mean()) < 1e-14
+    s = O.sigma(p, phi)
+    assert s > 0 and abs(ob["sigma"] - s) <= 1e-13 * s
+    vmax = np.sqrt(vel[0] ** 2 + vel[1] ** 2).max()
+    assert vmax > 0 and abs(ob["max_u"] - vmax) <= 1e-15 * vmax
+    assert abs(ob["lb_mass"] - 1) < 1e-6
+    assert ob == h.observables(1)
+    assert h.width(2) == h.width(2)
+    assert h.sigma_delta(0, 3) == h.sigma_delta(0, 3)
+    h.close()
