@@ -94,17 +94,13 @@ def sites_per_step(runs) -> float:
     return float(sum(r.nx * r.ny for r in runs))
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one differential chain
-# launch on the 4 x 256x512, N_s = 64 batch (296.0 + 234.2 MB)
-CHAIN_DIFF_DRAM_BYTES = 530.2e6
-
 
 def launches_per_step(runs, h) -> int:
     """Kernel launches of one captured step, per group of equal runs: aux
     convection 2, diffusion 2, force 3, LB 1, plus the two solves: cluster
-    path 4 each (factors, chain, Q partials, contour sums), streaming paths
-    2 N_s + 3 each (factors, start, N_s column and row passes, contour or
-    finalize)."""
+    path 3 + the chain launches each (factors, chain, Q partials, contour
+    sums), streaming paths 2 N_s + 3 each (factors, start, N_s column and row
+    passes, contour or finalize)."""
     import dataclasses
 
     first = {}
@@ -114,7 +110,8 @@ def launches_per_step(runs, h) -> int:
         first.setdefault(key, k)
     total = 0
     for k in first.values():
-        solve = 4 if h.tiles(k)["path"] == 2 else 2 * runs[k].ns + 3
+        t = h.tiles(k)
+        solve = 3 + t["chain_launches"] if t["path"] == 2 else 2 * runs[k].ns + 3
         total += 8 + 2 * solve
     return total
 
@@ -447,10 +444,12 @@ def main():
         tf = flops / (kt["prop_cluster"] * 1e-3) / 1e12
         peak_tf = FP32_SMS * FP32_LANES * 2 * FP32_MHZ * 1e6 / 1e12
         kernels["prop_cluster"] = {"ms": kt["prop_cluster"], "flops": flops, "achieved_tflops": tf, "frac": tf / peak_tf}
-        # DRAM bytes (read + write) of one launch of this kernel on this
-        # workload, from an ncu capture of the current kernel version
-        traffic = CHAIN_DIFF_DRAM_BYTES if tuple((r.nx, r.ny, r.ns) for r in runs) == ((512, 256, 64),) * 4 else None
-        roofline = {"bound": "alu", "kernel": "prop_chain (the step's second, differential single-chain solve of all runs)", "achieved": tf,
+        # DRAM bytes of the current kernel version: no ncu capture of the
+        # phased chain schedule yet
+        traffic = None
+        launches = h.tiles(0)["chain_launches"]
+        roofline = {"bound": "alu", "kernel": f"prop_chain (the step's second, differential single-chain solve of all "
+                                              f"runs; {launches} launch(es) timed together)", "achieved": tf,
                     "peak": peak_tf, "unit": "TFLOP/s", "frac": tf / peak_tf, "traffic": traffic,
                     "peak_source": "derived FP32 peak: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
     else:

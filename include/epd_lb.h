@@ -203,8 +203,12 @@ int epd_lb_kernel_times(epd_lb *h, double *ms);
  * (EPD_LB_COLUMN_TILE=4|8|16 in the environment forces a width; every width
  * gives bit-identical results); out[3]: 1 if the step's second solve is the
  * differential one; out[4]: the column tile width of the streaming
- * propagator passes (path 1, tuned the same way), else 0.  out holds 5
- * values.  Returns EPD_LB_EINVAL for a bad run index or NULL out. */
+ * propagator passes (path 1, tuned the same way), else 0; out[5]: launches
+ * of the chain kernel per solve on path 2 (1, or 2 nruns when the group's
+ * chains are one more than the 16-CTA clusters that fit at one CTA per SM:
+ * the chains then take turns, each sitting out one launch; results do not
+ * depend on it), else 0.  out holds 6 values.  Returns EPD_LB_EINVAL for a
+ * bad run index or NULL out. */
 int epd_lb_tiles(epd_lb *h, int32_t run, int32_t *out);
 
 /*

@@ -455,11 +455,12 @@ class EpdLb:
         """Launch configuration of a run's group: solve path (0 streaming
         radix-2, 1 streaming radix-8, 2 cluster), CTAs per cluster, the
         autotuned column tile widths (EPD passes; streaming propagator
-        passes), and whether the differential second solve is used."""
-        out = np.zeros(5, dtype=np.int32)
+        passes), whether the differential second solve is used, and the
+        chain-kernel launches per cluster solve."""
+        out = np.zeros(6, dtype=np.int32)
         self._ck(lib().epd_lb_tiles(self.h, run, out.ctypes.data_as(ctypes.c_void_p)), "epd_lb_tiles")
         return {"path": int(out[0]), "cluster_ctas": int(out[1]), "column_tile": int(out[2]), "differential": bool(out[3]),
-                "stream_column_tile": int(out[4])}
+                "stream_column_tile": int(out[4]), "chain_launches": int(out[5])}
 
     def set_surrogate(self, params, s_in: float, s_out: float, exact_every: int = 8, residual_tol: float = 1e-3):
         """Attach the learned surrogate (FP32 parameters, host array or torch

@@ -1170,6 +1170,7 @@ extern "C" int epd_lb_tiles(epd_lb *h, int32_t run, int32_t *out)
     out[2] = G->colw;
     out[3] = G->diff ? 1 : 0;
     out[4] = G->colw_prop;
+    out[5] = cluster ? cluster_chain_launches(*G, G->diff) : 0;
     return EPD_LB_OK;
 }
 

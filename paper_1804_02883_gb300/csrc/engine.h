@@ -179,6 +179,10 @@ cudaError_t launch_pop_raw(Group &G, int run, int parity, double *dst, const dou
 // shape and precision, its launch, and its CTAs per run.
 bool cluster_solve_supported(const Group &G);
 bool cluster_shape_exists(int logx, int logy);
+// Launches of the chain kernel per cluster-resident solve (diff: the
+// differential one): 1, or 2 nruns when the chains are one more than the
+// clusters that fit at one CTA per SM (the phased schedule); 0 without a shape.
+int cluster_chain_launches(const Group &G, bool diff);
 // MIXED grids solved by the radix-8 streaming passes with the full history
 bool stream8_eligible(int prec, int logx, int logy);
 size_t cluster_state_floats2(int nx, int ny, int ns);  // per run, both chains

@@ -46,6 +46,7 @@
 // dg = (d a - rho a~) / E' and sums g~ dg' + dg g~' + dg dg'.  Exact algebra
 // of the second solve; only the rounding changes: FP32 relative to the
 // change, not to Phi.
+#include <algorithm>
 #include <cooperative_groups.h>
 
 #include "common.cuh"
@@ -66,6 +67,12 @@ struct PropCK {
     int *err;             // bit 2: an exchange wait gave up
     const float2 *twx, *twy;  // radix-8 pass tables (fft8.cuh layout)
     const float *kx, *ky;     // exp(-R_G^2 k^2 ds) / N
+    // Phased schedule (nseg > 0): this launch is phase `skip` of nseg + 1;
+    // its nseg clusters take every chain but chain `skip`, each over its next
+    // contour segment (segment s = nodes s N_s / nseg .. (s + 1) N_s / nseg),
+    // resuming from the state the previous phase stored.  nseg = 0: one
+    // launch, every chain over all N_s steps.
+    int nseg, skip;
 };
 
 template <int LOGX, int LOGY, int C, int T>
@@ -154,9 +161,14 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
     float *ky = kx + NX;
     cg::cluster_group cl = cg::this_cluster();
     const int crank = (int)cl.block_rank();
-    const int cidx = blockIdx.x / C, run = cidx >> 1, chain = cidx & 1;
+    const int slot = blockIdx.x / C;
+    const int cidx = (k.nseg == 0 || slot < k.skip) ? slot : slot + 1, run = cidx >> 1, chain = cidx & 1;
     const int tid = threadIdx.x;
     const int n = (int)k.g.n, ns = k.g.ns, na = k.g.na;
+    // contour steps m_begin + 1 .. m_end of this launch (segments in order
+    // over the phases: chain j sits out phase j)
+    const int seg = k.skip < cidx ? k.skip : k.skip - 1;
+    const int m_begin = k.nseg ? seg * ns / k.nseg : 0, m_end = k.nseg ? (seg + 1) * ns / k.nseg : ns;
     const int krow0 = crank * R2;  // first packed row of this CTA
 
     copy_tables(tabx, k.twx, G::TABX, tid, T);
@@ -188,9 +200,15 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
         mbar_expect(bar_row, XBYTES);
     }
 
-    // node 0: g_0 = 1, a_0 = E_0 (d a_0 = rho_0 E_0)
+    // node 0: g_0 = 1, a_0 = E_0 (d a_0 = rho_0 E_0); a later segment resumes
+    // from the state a_{m_begin} its previous phase stored (the same FP32
+    // values, so the result does not depend on the schedule)
     for (int e = tid; e < P; e += T) {
         const int b = e / NX, x = e % NX;
+        if (m_begin > 0) {
+            rowbuf[RL::at(b, x)] = hout[(size_t)m_begin * HN + e];
+            continue;
+        }
         const int site = 2 * (krow0 + b) * NX + x;
         const bool bk = blk_b(0);
         const float2 f0 = efac[site], f1 = efac[site + NX];
@@ -202,7 +220,7 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
         }
         rowbuf[RL::at(b, x)] = a0;
     }
-    cl.sync();  // every CTA's barriers are initialised, every row buffer holds a_0
+    cl.sync();  // every CTA's barriers are initialised, every row buffer holds a_{m_begin}
 
     // epilogue geometry: the inverse row transform's last pass
     constexpr int RLOG_L = inv_rlog(LOGX, npasses(LOGX, G::MRX) - 1, G::MRX), RR = 1 << RLOG_L, PER_L = NX / RR;
@@ -218,9 +236,11 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
     // One contour step.  The two exchanges push (st.async) into the owners'
     // buffers; a buffer is rewritten only after every CTA has arrived at the
     // relaxed cluster barrier that follows its last read of that buffer.
-    for (int m = 1; m <= ns; ++m) {
-        const unsigned par = (unsigned)(m - 1) & 1u;
-        if (m > 1) cluster_wait();  // every column buffer has been read out
+    for (int m = m_begin + 1; m <= m_end; ++m) {
+        // barrier bookkeeping counts this launch's steps
+        const unsigned par = (unsigned)(m - m_begin - 1) & 1u;
+        const bool more = m < m_end;
+        if (m > m_begin + 1) cluster_wait();  // every column buffer has been read out
         // my packed rows -> the owners' packed columns.  Consecutive threads
         // take consecutive real columns x of packed row kk; lanes (2i, 2i+1)
         // hold columns (x0, x0+1) and swap halves, the even lane forming real
@@ -237,7 +257,7 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
         }
         cluster_arrive();  // my row buffer is read out
         mbar_wait(bar_col, par, failed);
-        if (tid == 0 && m < ns) mbar_expect(bar_col, XBYTES);
+        if (tid == 0 && more) mbar_expect(bar_col, XBYTES);
         if (DIFF) {
             // a~_m for this thread's epilogue sites, into L1 ahead of use
 #pragma unroll
@@ -276,7 +296,7 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
         }
         cluster_arrive();  // my column buffer is read out
         mbar_wait(bar_row, par, failed);
-        if (tid == 0 && m < ns) mbar_expect(bar_row, XBYTES);
+        if (tid == 0 && more) mbar_expect(bar_row, XBYTES);
         transform_pair<LOGX, T, RL, P, ScaleBins, G::MRX>(rowbuf, tabx, ScaleBins{kx}, tid);
         float2 h[NB_L][RR];
         int bb[NB_L], tt[NB_L];
@@ -322,7 +342,7 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
         }
         __syncthreads();
     }
-    for (int e = tid; e < P; e += T) hout[(size_t)ns * HN + e] = rowbuf[RL::at(e / NX, e % NX)];  // a_{N_s}
+    for (int e = tid; e < P; e += T) hout[(size_t)m_end * HN + e] = rowbuf[RL::at(e / NX, e % NX)];  // a_{m_end}
     cluster_wait();  // pairs the last arrival
     if (failed) atomicOr(k.err, 4);
     cl.sync();  // no CTA leaves while others may still read its shared memory
@@ -636,6 +656,26 @@ static void set_cluster_cfg(cudaLaunchConfig_t &cfg, cudaLaunchAttribute &attr, 
     cfg.numAttrs = 1;
 }
 
+// Clusters of a shape that fit at once at one CTA per SM (more than half of
+// an SM's shared memory per CTA), per shape and solve kind; 0: unknown or
+// none.  Filled by cluster_solve_supported, outside any stream capture.
+constexpr size_t kSoloSmem = 116 * 1024;
+static int g_solo_clusters[16][16][2];
+
+static int count_solo_clusters(const ClusterShape *s, bool diff)
+{
+    const void *fn = diff ? s->fn_diff : s->fn;
+    const size_t sm = std::max(kSoloSmem, diff ? s->smem_diff : s->smem);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return 0;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr;
+    set_cluster_cfg(cfg, attr, s, 1, diff);
+    cfg.dynamicSmemBytes = sm;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) != cudaSuccess) return 0;
+    return nclusters;
+}
+
 bool cluster_solve_supported(const Group &G)
 {
     if (G.prec != EPD_LB_MIXED_FP32) return false;
@@ -657,13 +697,25 @@ bool cluster_solve_supported(const Group &G)
             int nclusters = 0;
             return cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) == cudaSuccess && nclusters > 0;
         };
-        if (ok(false) && ok(true)) st = 1;
+        if (ok(false) && ok(true)) {
+            st = 1;
+            g_solo_clusters[s->logx][s->logy][0] = count_solo_clusters(s, false);
+            g_solo_clusters[s->logx][s->logy][1] = count_solo_clusters(s, true);
+        }
         cudaGetLastError();
     }
     return st == 1;
 }
 
 bool cluster_shape_exists(int logx, int logy) { return find_shape(logx, logy) != nullptr; }
+
+int cluster_chain_launches(const Group &G, bool diff)
+{
+    const ClusterShape *sh = find_shape(G.g.logx, G.g.logy);
+    if (!sh) return 0;
+    const int nch = 2 * G.g.nruns, solo = g_solo_clusters[sh->logx][sh->logy][diff ? 1 : 0];
+    return (solo > 0 && nch == solo + 1 && G.g.ns >= nch - 1) ? nch : 1;
+}
 
 size_t cluster_state_floats2(int nx, int ny, int ns) { return (size_t)2 * (ns + 1) * (ny / 2) * nx; }
 
@@ -697,17 +749,30 @@ cudaError_t launch_cluster_solve(Group &G, cudaStream_t s, bool diff, int nprep_
     if (!k.twx || !k.twy) return cudaErrorInvalidValue;
     k.kx = reinterpret_cast<const float *>(G.kx);
     k.ky = reinterpret_cast<const float *>(G.ky);
+    // One launch runs every chain, unless the chains are one more than the
+    // clusters that fit at one CTA per SM: then the extra cluster would share
+    // SMs with another and pace the launch, so nch launches of nch - 1
+    // clusters at one CTA per SM take the chains in turns (chain j sits out
+    // launch j and runs N_s / (nch - 1) steps in each of the others).
+    const int nch = 2 * G.g.nruns, launches = cluster_chain_launches(G, diff);
+    const bool phased = launches > 1;
+    k.nseg = phased ? nch - 1 : 0;
+    k.skip = 0;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr;
-    set_cluster_cfg(cfg, attr, sh, 2 * G.g.nruns, diff);
+    set_cluster_cfg(cfg, attr, sh, phased ? nch - 1 : nch, diff);
+    if (phased) cfg.dynamicSmemBytes = std::max(kSoloSmem, cfg.dynamicSmemBytes);
     cfg.stream = s;
     if (probe) {
         probe->cluster = true;
         cudaEventRecordWithFlags(probe->ev[0], s, cudaEventRecordExternal);
     }
     void *args[] = {&k};
-    cudaError_t e = cudaLaunchKernelExC(&cfg, diff ? sh->fn_diff : sh->fn, args);
-    if (e != cudaSuccess) return e;
+    for (int p = 0; p < launches; ++p) {
+        k.skip = p;
+        cudaError_t e = cudaLaunchKernelExC(&cfg, diff ? sh->fn_diff : sh->fn, args);
+        if (e != cudaSuccess) return e;
+    }
     if (probe) cudaEventRecordWithFlags(probe->ev[1], s, cudaEventRecordExternal);
 
     ContourK c;

@@ -208,6 +208,26 @@ def test_batch_equals_single_runs():
     hb.close()
 
 
+def test_phased_chain_schedule_equals_single_runs():
+    # four 256 x 512 runs are 8 chains of 16-CTA clusters; where only 7 fit at
+    # one CTA per SM the chains take turns over 8 launches, resuming from the
+    # FP32 states they stored, so the batch still equals each run stepped
+    # alone (one launch of 2 chains) bit for bit, in both solves
+    runs = W.channel_256x512(P.MIXED_FP32)
+    hb = P.EpdLb(runs)
+    t = hb.tiles(0)
+    assert t["path"] == 2 and t["differential"] and t["chain_launches"] in (1, 2 * len(runs))
+    hb.step(2)
+    for k, r in enumerate(runs):
+        hs = P.EpdLb([r])
+        assert hs.tiles(0)["chain_launches"] == 1
+        hs.step(2)
+        assert np.array_equal(hb.densities(k)[0], hs.densities(0)[0])
+        assert np.array_equal(hb.velocity(k), hs.velocity(0))
+        hs.close()
+    hb.close()
+
+
 def test_uneven_batch_groups_match_single_runs():
     runs = [P.RunParams(nx=32, ny=16, ns=8, precision=P.MIXED_FP32, seed=1),
             P.RunParams(nx=16, ny=32, ns=12, precision=P.MIXED_FP32, seed=2),

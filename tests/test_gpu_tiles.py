@@ -54,6 +54,8 @@ def test_autotuner_picks_a_width_and_paths():
     assert tiles["path"] == 2 and tiles["cluster_ctas"] >= 2 and tiles["differential"]
     assert tiles["column_tile"] in (4, 8, 16)
     t64, *_ = _run(W.plain_small(), 1)
-    assert t64 == {"path": 0, "cluster_ctas": 0, "column_tile": 0, "differential": False, "stream_column_tile": 0}
+    assert t64 == {"path": 0, "cluster_ctas": 0, "column_tile": 0, "differential": False, "stream_column_tile": 0,
+                   "chain_launches": 0}
+    assert tiles["chain_launches"] == 1  # one run: both chains in one launch
     ts, *_ = _run(W.with_(r, nx=1024, ny=64, ns=8), 1)
     assert ts["path"] == 1 and ts["stream_column_tile"] in (4, 8, 16) and not ts["differential"]
