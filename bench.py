@@ -94,7 +94,6 @@ def sites_per_step(runs) -> float:
     return float(sum(r.nx * r.ny for r in runs))
 
 
-
 def launches_per_step(runs, h) -> int:
     """Kernel launches of one captured step, per group of equal runs: aux
     convection 2, diffusion 2, force 3, LB 1, plus the two solves: cluster
