@@ -109,3 +109,22 @@ def test_box_rules_of_the_3d_entry_points():
         P.epd_prop_solve3d_workspace_bytes(W.with_(run, nx=256, ny=256), 128)
     assert _rc("epd_step3d_workspace_bytes", ctypes.byref(run.c()), 7, ctypes.byref(n)) == -1
     assert _rc("epd_prop_solve3d_workspace_bytes", None, 16, ctypes.byref(n)) == -1
+
+
+def test_runs_group_by_everything_but_f0_seed_and_noise():
+    # the workspace of separate groups adds up (one head shared), while runs
+    # of one group share their tables: grouping is visible without a device
+    a = W.with_(W.plain_small(), precision=P.MIXED_FP32)
+    ws = P.epd_lb_workspace_bytes
+    b = W.with_(a, ns=24)
+    c = W.with_(a, phi_p=0.25)
+    head = ws([a]) + ws([b]) - ws([a, b])
+    assert head > 0 and head % 256 == 0
+    assert ws([a]) + ws([c]) - ws([a, c]) == head
+    for field in ("chi_bs", "kappa_h", "d_p", "inv_beta_v", "gamma_s", "dt", "f_a", "precision"):
+        v = getattr(a, field)
+        other = W.with_(a, **{field: P.PLAIN_FP64 if field == "precision" else (0.5 * v if v else 0.1)})
+        assert ws([a]) + ws([other]) - ws([a, other]) == head, field
+    for field, value in (("f0", 3.0), ("seed", 99), ("noise_amp", 2e-3)):
+        same = W.with_(a, **{field: value})
+        assert ws([a, same]) < 2 * ws([a]) - head, field
