@@ -240,6 +240,90 @@ def time_steps(h, stream, steps, flush, with_kernels=False):
     return per_step, kern
 
 
+def cufft_solve(torch, omega, r, dtype, timing=False):
+    """The single-chain solve of Eqs. (6)-(11) written with torch.fft (cuFFT
+    on a GPU), a library comparison for the hand-written transforms and never
+    the product path: omega (R, 3, ny, nx) float64 of R runs with the
+    parameters of r.  Per contour step of both chains of every run (batched),
+    g_{j+1} = E_{j+1} irfft2(K rfft2(E_j g_j)) with E = exp(-N omega ds / 2)
+    of the node's block (g: node j; g': node N_s - j) and
+    K = exp(-R_G^2 |k|^2 ds), every node state stored; then the trapezoid
+    contour sums on [0, s_NA] and [s_NA, 1] (products in dtype, sums in
+    float64), Q_P = <g(1)>, Phi_S from exp(-omega_S).  Returns (phi, q), and
+    with timing also the CUDA-event ms of the propagation and of the whole
+    solve (omega already on the device)."""
+    import math
+
+    dev = omega.device
+    R, _, ny, nx = omega.shape
+    ns, ds = r.ns, 1.0 / r.ns
+    na = int(round(r.f_a * ns))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)] if timing else None
+    if timing:
+        ev[0].record()
+    kx = 2 * math.pi * torch.fft.rfftfreq(nx, d=r.dx, dtype=torch.float64, device=dev)
+    ky = 2 * math.pi * torch.fft.fftfreq(ny, d=r.dx, dtype=torch.float64, device=dev)
+    K = torch.exp(-r.rg ** 2 * (ky[:, None] ** 2 + kx[None, :] ** 2) * ds).to(dtype)
+    e = torch.exp(-r.n_seg * omega[:, :2] * ds / 2).to(dtype)  # (R, 2, ny, nx): E_A, E_B
+    ea, eb = e[:, 0], e[:, 1]
+
+    def node_factor(j):  # (2R, ny, nx): chain g at node j, chain g' at node N_s - j
+        return torch.cat((ea if j < na else eb, ea if ns - j < na else eb))
+
+    hist = torch.empty((ns + 1, 2 * R, ny, nx), dtype=dtype, device=dev)
+    hist[0].fill_(1.0)
+    fac = node_factor(0)
+    for j in range(ns):
+        nxt = node_factor(j + 1)
+        hist[j + 1] = nxt * torch.fft.irfft2(K * torch.fft.rfft2(fac * hist[j]), s=(ny, nx))
+        fac = nxt
+    if timing:
+        ev[1].record()
+    ia = torch.zeros((R, ny, nx), dtype=torch.float64, device=dev)
+    ib = torch.zeros_like(ia)
+    for j in range(ns + 1):
+        prod = (hist[j, :R] * hist[ns - j, R:]).double()
+        if na > 0 and j <= na:
+            ia += (0.5 * ds if j in (0, na) else ds) * prod
+        if na < ns and j >= na:
+            ib += (0.5 * ds if j in (na, ns) else ds) * prod
+    q_p = hist[ns, :R].double().mean(dim=(1, 2))
+    bs = torch.exp(-omega[:, 2])
+    q_s = bs.mean(dim=(1, 2))
+    phi = torch.stack((r.phi_p * ia / q_p[:, None, None], r.phi_p * ib / q_p[:, None, None],
+                       (1 - r.phi_p) * bs / q_s[:, None, None]), dim=1)
+    q = torch.stack((q_p, q_s), dim=1)
+    if not timing:
+        return phi, q
+    ev[2].record()
+    ev[2].synchronize()
+    return phi, q, ev[0].elapsed_time(ev[1]), ev[0].elapsed_time(ev[2])
+
+
+def cufft_section(torch, runs, h, ours_ms, flush, reps=5):
+    """cuFFT comparison on the workload: cufft_solve in FP32 on the runs'
+    current fields (all runs on one grid with one parameter set but f0, seed
+    and noise), L2 flushed before each of reps timed solves (median), beside
+    our chain launch(es) of the step's differential solve, which propagate
+    the same chains over the same contour steps (plus the differential term)."""
+    r0 = runs[0]
+    if any((r.nx, r.ny, r.ns, r.f_a, r.phi_p, r.chi_bs) != (r0.nx, r0.ny, r0.ns, r0.f_a, r0.phi_p, r0.chi_bs)
+           for r in runs):
+        return None
+    om = torch.stack([torch.from_numpy(h.get_state(k)[0]) for k in range(len(runs))]).cuda()
+    cufft_solve(torch, om, r0, torch.float32)
+    prop, whole = [], []
+    for _ in range(reps):
+        flush.add_(1.0)
+        _, _, a, b = cufft_solve(torch, om, r0, torch.float32, timing=True)
+        prop.append(a)
+        whole.append(b)
+    tp, tw = statistics.median(prop), statistics.median(whole)
+    return {"propagation_ms": tp, "solve_ms": tw, "ours_chain_ms": ours_ms, "propagation_vs_ours": tp / ours_ms,
+            "note": "torch.fft (cuFFT) FP32, both chains of every run batched, eager launches; ours = the "
+                    "differential solve's chain launch(es) from the step's timing probes"}
+
+
 def analysis_section(torch, h, runs, flush, hbm, calls=20):
     """The observables (masses, sigma of Eq. (21), max |u|) and the analysis of
     Secs. 3-4 (sigma_Delta of Eq. (22) between runs 0 and 1, Y_2^P of Eq. (30),
@@ -493,6 +577,12 @@ def main():
            "d2h_bytes_per_step": int(sum(3 * r.nx * r.ny * 8 + 16 for r in runs))}
 
     analysis = analysis_section(torch, h, runs, flush, hbm)
+    cufft = None
+    if "prop_cluster" in kt:
+        try:
+            cufft = cufft_section(torch, runs, h, kt["prop_cluster"], flush)
+        except Exception as ex:  # a library comparison never costs the line
+            cufft = {"unavailable": f"{type(ex).__name__}: {ex}"[:200]}
 
     # learned surrogate (exact every 8th step) on the same workload
     sur = None
@@ -550,6 +640,7 @@ def main():
             "surrogate": sur,
             "exact_step": exact,
             "analysis": analysis,
+            "cufft_comparison": cufft,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": n_launches * args.steps,
