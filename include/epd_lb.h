@@ -168,7 +168,8 @@ int epd_lb_solve(epd_lb *h, int32_t run, const double *omega, double *phi, doubl
 
 /* Per-run observables of the current state: out[0] = <Phi_A>, out[1] = <Phi_B>,
  * out[2] = <Phi_S>, out[3] = sigma of Eq. (21), out[4] = LB mass / sites,
- * out[5] = max |u| (lattice), out[6] = Q_P, out[7] = Q_S.  Synchronous. */
+ * out[5] = max |u| (lattice), out[6] = Q_P, out[7] = Q_S.  Sums in a fixed
+ * order: a repeated call returns identical values.  Synchronous. */
 int epd_lb_observables(epd_lb *h, int32_t run, double *out);
 
 /* Checkpoint: serialise every run's state (parameters, omega, the stored LB
@@ -188,8 +189,9 @@ int epd_lb_load(epd_lb *h, const void *buf, size_t len);
  * (ms[4] = 0): ms[0] the row pass of contour node N_s/4 (history store),
  * ms[1] the row pass of node 3 N_s/4 + 1 (contour accumulation), ms[2] the
  * column pass before it.  With the cluster-resident solve (ms[4] = 1): ms[0]
- * its chain launch (the whole contour of both chains; the differential
- * solve where the step uses one), ms[1] = ms[2] = 0. */
+ * its chain launches (the whole contour of both chains of every run, in one
+ * launch or the phased schedule's several, see epd_lb_tiles; the
+ * differential solve where the step uses one), ms[1] = ms[2] = 0. */
 int epd_lb_enable_timing(epd_lb *h, int32_t on);
 int epd_lb_kernel_times(epd_lb *h, double *ms);
 
