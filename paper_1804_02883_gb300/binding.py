@@ -7,8 +7,7 @@ CPU fallback: if the library is missing or no GPU is present the calls raise.
 from __future__ import annotations
 
 import ctypes
-import os
-from dataclasses import dataclass, field, fields
+from dataclasses import dataclass, fields
 
 import numpy as np
 

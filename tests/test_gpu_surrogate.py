@@ -5,12 +5,10 @@ exact-every-k controller of the time stepper."""
 import numpy as np
 import pytest
 
-import oracle as O
 import paper_1804_02883_gb300 as P
 from paper_1804_02883_gb300 import surrogate as S
 from paper_1804_02883_gb300 import workloads as W
 from oracle import surrogate as OS
-from helpers import oracle_params
 
 pytestmark = pytest.mark.gpu
 

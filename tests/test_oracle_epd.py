@@ -3,7 +3,6 @@ free energy of Eq. (1)), spectral derivatives, the auxiliary convection of
 omega (App. C), the diffusion step of Eq. (5), and the force reconstruction
 of Eqs. (19)-(20) (T7: divergence, curl, closed form)."""
 import numpy as np
-import pytest
 
 import oracle as O
 

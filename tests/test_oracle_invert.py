@@ -3,7 +3,6 @@ composition fields (the convective part of Eq. (2)), the Fletcher-Reeves
 inversion omega = Phi^{-1}(Phi~) (Sec. 2, the integrator paragraph; App. C,
 items 2 and 3) and the step built from them."""
 import numpy as np
-import pytest
 
 import oracle as O
 

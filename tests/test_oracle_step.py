@@ -5,7 +5,6 @@ step to a known answer, and the splitmix64 generator's published outputs."""
 import os
 
 import numpy as np
-import pytest
 
 import oracle as O
 

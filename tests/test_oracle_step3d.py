@@ -3,7 +3,6 @@ Fourier modes, the 3D force's divergence and curl (App. A in 3D), and the
 step against the 2D step for fields uniform in z, exact masses and a
 stationary homogeneous state."""
 import numpy as np
-import pytest
 
 import oracle as O
 
