@@ -118,8 +118,8 @@ cudaError_t launch_init_state(Group &G, cudaStream_t s);
 // Optional CUDA events recorded around single launches of a solve (for timing
 // inside a captured step): ev[0], ev[1] bracket the row pass of node m_store;
 // ev[2], ev[3] the column pass before node m_acc and ev[3], ev[4] its row pass.
-// With the cluster-resident solve, ev[0], ev[1] bracket its single launch and
-// `cluster` is set.
+// With the cluster-resident solve, ev[0], ev[1] bracket its chain launch (all
+// launches of the phased schedule) and `cluster` is set.
 struct SolveProbe {
     cudaEvent_t ev[5];
     int m_store, m_acc;

@@ -4,7 +4,9 @@
 //
 // One cluster of C CTAs carries one chain of one run through the whole
 // contour: the forward propagator g (Eq. (6)) or the backward propagator g'
-// (Eq. (7)), so a launch holds 2 x runs clusters.  The real field of the
+// (Eq. (7)), so a launch holds 2 x runs clusters (or, in the phased
+// schedule, 2 x runs - 1 clusters per launch over 2 x runs launches, each
+// chain resuming from the state it stored).  The real field of the
 // chain lives on chip in two packings: CTA c owns complex rows
 // [c R2, (c+1) R2), each holding the real rows (2k, 2k+1) as (re, im), in its
 // row buffer, and complex columns [c W2, (c+1) W2), each holding the real
