@@ -209,7 +209,8 @@ int epd_lb_kernel_times(epd_lb *h, double *ms);
  * of the chain kernel per solve on path 2 (1, or 2 nruns when the group's
  * chains are one more than the 16-CTA clusters that fit at one CTA per SM:
  * the chains then take turns, each sitting out one launch; results do not
- * depend on it), else 0.  out holds 6 values.  Returns EPD_LB_EINVAL for a
+ * depend on it; EPD_LB_CHAIN_SCHEDULE=single|phased in the environment forces
+ * one or the other), else 0.  out holds 6 values.  Returns EPD_LB_EINVAL for a
  * bad run index or NULL out. */
 int epd_lb_tiles(epd_lb *h, int32_t run, int32_t *out);
 

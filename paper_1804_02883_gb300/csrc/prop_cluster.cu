@@ -49,6 +49,8 @@
 // of the second solve; only the rounding changes: FP32 relative to the
 // change, not to Phi.
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
 #include <cooperative_groups.h>
 
 #include "common.cuh"
@@ -716,7 +718,14 @@ int cluster_chain_launches(const Group &G, bool diff)
     const ClusterShape *sh = find_shape(G.g.logx, G.g.logy);
     if (!sh) return 0;
     const int nch = 2 * G.g.nruns, solo = g_solo_clusters[sh->logx][sh->logy][diff ? 1 : 0];
-    return (solo > 0 && nch == solo + 1 && G.g.ns >= nch - 1) ? nch : 1;
+    // solo > 0: the one-CTA-per-SM shared-memory size is set for this shape
+    const bool can = solo > 0 && nch >= 2 && G.g.ns >= nch - 1;
+    // EPD_LB_CHAIN_SCHEDULE=single|phased forces a schedule (the results are
+    // the same either way), e.g. to time one against the other
+    const char *env = std::getenv("EPD_LB_CHAIN_SCHEDULE");
+    if (env && !std::strcmp(env, "single")) return 1;
+    if (env && !std::strcmp(env, "phased")) return can ? nch : 1;
+    return (can && nch == solo + 1) ? nch : 1;
 }
 
 size_t cluster_state_floats2(int nx, int ny, int ns) { return (size_t)2 * (ns + 1) * (ny / 2) * nx; }
