@@ -22,13 +22,14 @@ cudaError_t configure_epd_kernels();
 
 cudaError_t configure_kernels()
 {
-    static bool done = false;
-    static cudaError_t status = cudaSuccess;
-    if (done) return status;
-    status = configure_prop_kernels();
-    if (status == cudaSuccess) status = configure_epd_kernels();
-    if (status == cudaSuccess) status = configure_step3d_kernels();
-    done = true;
+    // once per process (a function-local static is initialised exactly once,
+    // also when handles are created on several threads)
+    static const cudaError_t status = [] {
+        cudaError_t e = configure_prop_kernels();
+        if (e == cudaSuccess) e = configure_epd_kernels();
+        if (e == cudaSuccess) e = configure_step3d_kernels();
+        return e;
+    }();
     return status;
 }
 

@@ -16,6 +16,7 @@
 // out of every derivative, and FP32 rounding then scales with the
 // fluctuations rather than with mu itself), omega (zero-mean noise), and
 // dPhi^D.  Pointwise combinations with the fields are done in FP64.
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 
@@ -482,7 +483,7 @@ static bool row8_at(int logx, const EpdK &k, dim3 grid_yz, cudaStream_t s)
     } else {
         if (logx != L) return row8_at<MODE, L + 1>(logx, k, grid_yz, s);
         using RT = RowTile<L>;
-        static bool conf = false;
+        static std::atomic<bool> conf{false};  // attribute set (idempotent if two threads race)
         if (!conf) {
             conf = cudaFuncSetAttribute(epd_row8<L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RT::SMEM) == cudaSuccess;
             if (!conf) return false;
@@ -497,7 +498,7 @@ static bool col8_launch(const EpdK &k, dim3 grid_yz, cudaStream_t s)
 {
     using CT = ColTile<L, CW>;
     if (k.g.nx % CT::C) return false;
-    static bool conf = false;
+    static std::atomic<bool> conf{false};  // attribute set (idempotent if two threads race)
     if (!conf) {
         conf = cudaFuncSetAttribute(epd_col8<L, MODE, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CT::SMEM) == cudaSuccess;
         if (!conf) return false;

@@ -17,6 +17,7 @@
 // the history (and vice versa), and the trapezoid sums of Eqs. (9)-(10) are
 // accumulated in FP64 on the fly.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <type_traits>
@@ -440,7 +441,7 @@ static void stream8_run(Stream8K &k, const Group &G, cudaStream_t s, const Solve
     using RT = RowTile<LX>;
     using CT = ColTile<LY, CW>;
     const size_t sr = (size_t)RT::ROWS * RowLayout<LX>::PITCH * sizeof(float2), sc = (size_t)CT::P * sizeof(float2);
-    static bool conf = false;
+    static std::atomic<bool> conf{false};  // attribute set (idempotent if two threads race)
     if (!conf) {
         cudaFuncSetAttribute(prop_row8<LX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
         cudaFuncSetAttribute(prop_col8<LY, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);

@@ -49,8 +49,10 @@
 // of the second solve; only the rounding changes: FP32 relative to the
 // change, not to Phi.
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <cooperative_groups.h>
 
 #include "common.cuh"
@@ -685,6 +687,8 @@ bool cluster_solve_supported(const Group &G)
     if (G.prec != EPD_LB_MIXED_FP32) return false;
     const ClusterShape *s = find_shape(G.g.logx, G.g.logy);
     if (!s) return false;
+    static std::mutex mu;  // handles may be created on several threads
+    std::lock_guard<std::mutex> lock(mu);
     static int checked[16][16] = {};  // 0 unknown, 1 ok, 2 not launchable
     int &st = checked[s->logx][s->logy];
     if (st == 0) {
@@ -803,7 +807,7 @@ cudaError_t launch_cluster_solve(Group &G, cudaStream_t s, bool diff, int nprep_
     c.err = G.err;
     const int npk = G.g.nx * G.g.ny / 2;
     const dim3 grid((npk + kThreads - 1) / kThreads, G.g.nruns), gq(kQBlocks, G.g.nruns);
-    static bool conf = false;
+    static std::atomic<bool> conf{false};  // attribute set (idempotent if two threads race)
     if (!conf) {
         cudaError_t e1 = cudaFuncSetAttribute(prop_contour<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)ContourStage<true>::SMEM);
