@@ -128,3 +128,10 @@ def test_runs_group_by_everything_but_f0_seed_and_noise():
     for field, value in (("f0", 3.0), ("seed", 99), ("noise_amp", 2e-3)):
         same = W.with_(a, **{field: value})
         assert ws([a, same]) < 2 * ws([a]) - head, field
+
+
+def test_error_codes_match_the_header():
+    txt = open(os.path.join(ROOT, "include", "epd_lb.h")).read()
+    codes = {int(v): k for k, v in re.findall(r"\b(EPD_LB_E\w+)\s*=\s*(-\d+)", txt)}
+    assert codes == P.binding.ERRORS
+    assert re.search(r"\bEPD_LB_OK\s*=\s*0\b", txt) and P.binding.EPD_LB_OK == 0
