@@ -135,3 +135,21 @@ def test_error_codes_match_the_header():
     codes = {int(v): k for k, v in re.findall(r"\b(EPD_LB_E\w+)\s*=\s*(-\d+)", txt)}
     assert codes == P.binding.ERRORS
     assert re.search(r"\bEPD_LB_OK\s*=\s*0\b", txt) and P.binding.EPD_LB_OK == 0
+
+
+def test_params_struct_matches_the_header():
+    # field names, order and types of epd_lb_params against the ctypes mirror
+    import ctypes
+
+    txt = open(os.path.join(ROOT, "include", "epd_lb.h")).read()
+    body = re.search(r"typedef struct epd_lb_params \{(.*?)\} epd_lb_params;", txt, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    ctype = {"int32_t": ctypes.c_int32, "double": ctypes.c_double, "uint64_t": ctypes.c_uint64}
+    want = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        t, names = decl.split(None, 1)
+        want += [(n.strip(), ctype[t]) for n in names.split(",")]
+    assert [(n, t) for n, t in P.binding.CParams._fields_] == want
