@@ -153,3 +153,32 @@ def test_params_struct_matches_the_header():
         t, names = decl.split(None, 1)
         want += [(n.strip(), ctype[t]) for n in names.split(",")]
     assert [(n, t) for n, t in P.binding.CParams._fields_] == want
+
+
+def test_binding_signatures_match_the_header():
+    # every prototype's parameter count and kinds (pointer or the scalar
+    # type) against the argtypes and restype the binding declares
+    import ctypes
+
+    txt = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "epd_lb.h")).read(), flags=re.S)
+    protos = re.findall(r"(int32_t|int|void|const char\s*\*)\s*(epd_\w+)\s*\(([^)]*)\)\s*;", txt)
+    assert len(protos) == len(declared_symbols())
+    scalar = {"int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "size_t": ctypes.c_size_t,
+              "double": ctypes.c_double, "float": ctypes.c_float}
+    L = P.lib()
+    for ret, name, params in protos:
+        fn = getattr(L, name)
+        params = [p.strip() for p in params.split(",") if p.strip() and p.strip() != "void"]
+        assert len(fn.argtypes) == len(params), name
+        for p, a in zip(params, fn.argtypes):
+            if "*" in p:
+                assert a in (ctypes.c_void_p, ctypes.c_char_p) or hasattr(a, "_type_") and issubclass(a, ctypes._Pointer), (name, p, a)
+            else:
+                base = p.split()[0]
+                assert ctypes.sizeof(a) == ctypes.sizeof(scalar[base]) and (a in (ctypes.c_double, ctypes.c_float)) == (base in ("double", "float")), (name, p, a)
+        if ret == "void":
+            assert fn.restype is None, name
+        elif "char" in ret:
+            assert fn.restype is ctypes.c_char_p, name
+        else:
+            assert ctypes.sizeof(fn.restype) == 4, name
