@@ -240,6 +240,28 @@ def time_steps(h, stream, steps, flush, with_kernels=False):
     return per_step, kern
 
 
+def precision_errors(hm, h64, nruns, np):
+    """Per run, the MIXED handle hm against the PLAIN_FP64 handle h64 after
+    the same steps from the same initial state: max |dPhi| relative to
+    max |Phi| and to the largest fluctuation max |Phi - <Phi>| (over the three
+    species), max |du| relative to max |u|.  The FP64 path matches the FP64
+    oracle to 1e-10 (parity tests), so it stands in for the oracle at the
+    benchmark size."""
+    phi_rel, phi_fluct, vel_rel = [], [], []
+    for k in range(nruns):
+        a, _ = hm.densities(k)
+        b, _ = h64.densities(k)
+        d = np.abs(a - b).max()
+        phi_rel.append(float(d / np.abs(b).max()))
+        fl = max(np.abs(b[i] - b[i].mean()).max() for i in range(b.shape[0]))
+        phi_fluct.append(float(d / fl) if fl > 0 else None)
+        va, vb = hm.velocity(k), h64.velocity(k)
+        vs = np.abs(vb).max()
+        vel_rel.append(float(np.abs(va - vb).max() / vs) if vs > 0 else None)
+    return {"phi_rel": phi_rel, "phi_rel_fluctuation": phi_fluct, "velocity_rel": vel_rel,
+            "reference": "the PLAIN_FP64 GPU path (parity-tested to 1e-10 of the FP64 oracle)"}
+
+
 def cufft_solve(torch, omega, r, dtype, timing=False):
     """The single-chain solve of Eqs. (6)-(11) written with torch.fft (cuFFT
     on a GPU), a library comparison for the hand-written transforms and never
@@ -607,6 +629,16 @@ def main():
         ms64 = sum(per64) / len(per64)
         fp64 = {"value": units_per_step(runs64) / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
                 "lb_mlups": sites_per_step(runs64) / (ms64 * 1e-3) / 1e6, "steps": args.fp64_steps}
+        # the MIXED path's error: a fresh MIXED batch stepped as often from the
+        # same initial state as the FP64 one
+        try:
+            hm = P.EpdLb(runs)
+            hm.step(1 + args.fp64_steps)
+            fp64["mixed_error"] = precision_errors(hm, h64, len(runs), np)
+            fp64["mixed_error"]["steps"] = 1 + args.fp64_steps
+            hm.close()
+        except Exception as ex:  # never costs the line
+            fp64["mixed_error"] = {"unavailable": f"{type(ex).__name__}: {ex}"[:200]}
         h64.close()
 
     if sur is not None:

@@ -55,3 +55,30 @@ def test_units_and_whole_job_rate():
     # K steps on each of N ranks in T seconds (the slowest rank's time)
     assert b.job_rate(100.0, 10, 2, 0.5) == pytest.approx(100.0 * 10 * 2 / 0.5)
     assert b.max_over_ranks(3.5) == 3.5  # no process group: the value itself
+
+
+def test_precision_errors_of_the_mixed_path():
+    import numpy as np
+
+    b = _bench()
+    rng = np.random.default_rng(0)
+    ref_phi = [0.2 + 1e-3 * rng.standard_normal((3, 4, 8)) for _ in range(2)]
+    ref_vel = [np.zeros((2, 4, 8)), 1e-2 * rng.standard_normal((2, 4, 8))]
+
+    class H:
+        def __init__(self, dphi, dvel):
+            self.dphi, self.dvel = dphi, dvel
+
+        def densities(self, k):
+            return ref_phi[k] + self.dphi, None
+
+        def velocity(self, k):
+            return ref_vel[k] + self.dvel
+
+    e = b.precision_errors(H(2e-7, 1e-6), H(0.0, 0.0), 2, np)
+    for k in range(2):
+        assert e["phi_rel"][k] == pytest.approx(2e-7 / np.abs(ref_phi[k]).max(), rel=1e-6)
+        fl = max(np.abs(ref_phi[k][i] - ref_phi[k][i].mean()).max() for i in range(3))
+        assert e["phi_rel_fluctuation"][k] == pytest.approx(2e-7 / fl, rel=1e-6)
+    assert e["velocity_rel"][0] is None  # no flow in the reference: no relative error
+    assert e["velocity_rel"][1] == pytest.approx(1e-6 / np.abs(ref_vel[1]).max(), rel=1e-6)
