@@ -149,20 +149,44 @@ def test_mixed_tracks_fp64_over_100_steps():
 
 
 def test_multi_step_from_init_fp64():
-    # the small FP64 configuration (64 x 64, N_s = 32) for 20 steps
+    # the small FP64 configuration (64 x 64, N_s = 32, f0 = 1e-6) over its
+    # full 200 coupled steps, compared every 20 steps
     r = W.plain_small()
     h = P.EpdLb([r])
     p = oracle_params(r)
     st = O.initial_state(p)
-    for k in range(4):
-        h.step(5)
-        O.step(p, st, 5)
+    for k in range(10):
+        h.step(20)
+        O.step(p, st, 20)
         gphi, gq = h.densities(0)
         gom, gpop, gvel = h.get_state(0)
         assert rel_err(gphi, st.phi) < 1e-10, k
         assert fluct_err(gphi[0] + gphi[1], st.phi[0] + st.phi[1]) < 1e-8, k
         assert fluct_err(gom, st.omega) < 1e-9, k
         assert vel_err(gvel, st.vel, 1e-9) < 1, k
+    h.close()
+
+
+def test_mixed_tracks_the_fp64_oracle_over_1000_steps():
+    # The reduced-precision bar: the mixed-precision path (FP32 propagators,
+    # LB and EPD transforms; FP64 fields, contour sums, Q, masses) against the
+    # FP64 oracle after 1000 coupled steps of the 64 x 64, N_s = 32 quench,
+    # densities within 1e-5 relative.  The velocity follows the density
+    # fluctuations (~1e-4 here), which FP32 resolves to ~3e-4 of themselves,
+    # so it is held to 2e-2 of max |u|.
+    r = W.with_(W.plain_small(), precision=P.MIXED_FP32)
+    h = P.EpdLb([r])
+    p = oracle_params(r)
+    st = O.initial_state(p)
+    for k in range(4):
+        h.step(250)
+        O.step(p, st, 250)
+        gphi, gq = h.densities(0)
+        assert rel_err(gphi, st.phi) < 1e-5, k
+        assert rel_err(gq, st.q) < 1e-5, k
+    gom, _, gvel = h.get_state(0)
+    assert fluct_err(gphi[0] + gphi[1], st.phi[0] + st.phi[1]) < 1e-2
+    assert rel_err(gvel, st.vel) < 2e-2
     h.close()
 
 
