@@ -187,9 +187,30 @@ __device__ __forceinline__ void twiddles(float2 (&w)[R], const float2 *tab, int 
     }
 }
 
+// Butterfly index of thread tid's j-th butterfly (NB per thread) in a pass.
+// WS = false: consecutive threads take consecutive butterflies over the tile.
+// WS = true (warp-private): warp w takes the 32 NB butterflies from 32 NB w
+// on, lane by lane, so that each warp owns whole sequences of a sequence-major
+// layout and the pass needs only warp barriers; within a warp the access
+// pattern is the same as in the tile-wide split.
+template <bool WS, int NB, int T> __device__ __forceinline__ int bfly(int tid, int j)
+{
+    if constexpr (WS)
+        return (tid >> 5) * (32 * NB) + (tid & 31) + 32 * j;
+    else
+        return tid + j * T;
+}
+template <bool WS> __device__ __forceinline__ void pass_sync()
+{
+    if constexpr (WS)
+        __syncwarp();
+    else
+        __syncthreads();
+}
+
 // One in-place Stockham pass (radix 2^RLOG, stride 2^SLOG): load, wait, write.
 // tab: this pass's twiddles [k-1][p] (unused in a forward last pass).
-template <int LOGN, int SLOG, int RLOG, bool INV, int NB, int T, class L>
+template <int LOGN, int SLOG, int RLOG, bool INV, int NB, int T, class L, bool WS = false>
 __device__ __forceinline__ void pass(float2 *buf, const float2 *tab, int tid)
 {
     constexpr int N = 1 << LOGN, R = 1 << RLOG, S = 1 << SLOG, PER = N / R, M = N / (S * R);
@@ -197,11 +218,11 @@ __device__ __forceinline__ void pass(float2 *buf, const float2 *tab, int tid)
     int bb[NB], tt[NB];
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
-        L::template split<PER>(tid + j * T, bb[j], tt[j]);
+        L::template split<PER>(bfly<WS, NB, T>(tid, j), bb[j], tt[j]);
 #pragma unroll
         for (int r = 0; r < R; ++r) x[j][r] = buf[L::at(bb[j], tt[j] + r * PER)];
     }
-    __syncthreads();
+    pass_sync<WS>();
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
         Dft<RLOG, INV>::run(x[j]);
@@ -215,13 +236,13 @@ __device__ __forceinline__ void pass(float2 *buf, const float2 *tab, int tid)
 #pragma unroll
         for (int k = 0; k < R; ++k) buf[L::at(bb[j], q + R * S * p + S * k)] = x[j][k];
     }
-    __syncthreads();
+    pass_sync<WS>();
 }
 
 // Forward last pass, spectral operator, inverse first pass (same points per
 // thread).  op(b, bin, v) returns the operator applied to bin `bin` (natural
 // order) of sequence b.
-template <int LOGN, int RLOG, int NB, int T, class L, class Op>
+template <int LOGN, int RLOG, int NB, int T, class L, class Op, bool WS = false>
 __device__ __forceinline__ void middle(float2 *buf, const float2 *tab_inv0, const Op &op, int tid)
 {
     constexpr int N = 1 << LOGN, R = 1 << RLOG, PER = N / R;
@@ -229,11 +250,11 @@ __device__ __forceinline__ void middle(float2 *buf, const float2 *tab_inv0, cons
     int bb[NB], tt[NB];
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
-        L::template split<PER>(tid + j * T, bb[j], tt[j]);
+        L::template split<PER>(bfly<WS, NB, T>(tid, j), bb[j], tt[j]);
 #pragma unroll
         for (int r = 0; r < R; ++r) x[j][r] = buf[L::at(bb[j], tt[j] + r * PER)];
     }
-    __syncthreads();
+    pass_sync<WS>();
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
         Dft<RLOG, false>::run(x[j]);
@@ -247,11 +268,11 @@ __device__ __forceinline__ void middle(float2 *buf, const float2 *tab_inv0, cons
 #pragma unroll
         for (int k = 0; k < R; ++k) buf[L::at(bb[j], R * tt[j] + k)] = x[j][k];
     }
-    __syncthreads();
+    pass_sync<WS>();
 }
 
 // Inverse first pass alone (input: a spectrum in natural order).
-template <int LOGN, int RLOG, int NB, int T, class L>
+template <int LOGN, int RLOG, int NB, int T, class L, bool WS = false>
 __device__ __forceinline__ void inverse_first(float2 *buf, const float2 *tab_inv0, int tid)
 {
     constexpr int N = 1 << LOGN, R = 1 << RLOG, PER = N / R;
@@ -259,11 +280,11 @@ __device__ __forceinline__ void inverse_first(float2 *buf, const float2 *tab_inv
     int bb[NB], tt[NB];
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
-        L::template split<PER>(tid + j * T, bb[j], tt[j]);
+        L::template split<PER>(bfly<WS, NB, T>(tid, j), bb[j], tt[j]);
 #pragma unroll
         for (int r = 0; r < R; ++r) x[j][r] = buf[L::at(bb[j], tt[j] + r * PER)];
     }
-    __syncthreads();
+    pass_sync<WS>();
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
         Dft<RLOG, true>::run(x[j]);
@@ -274,41 +295,41 @@ __device__ __forceinline__ void inverse_first(float2 *buf, const float2 *tab_inv
 #pragma unroll
         for (int k = 0; k < R; ++k) buf[L::at(bb[j], R * tt[j] + k)] = x[j][k];
     }
-    __syncthreads();
+    pass_sync<WS>();
 }
 
-template <int LOGN, int I, int T, class L, int P, int MR = 3>
+template <int LOGN, int I, int T, class L, int P, int MR = 3, bool WS = false>
 struct FwdPasses {
     static __device__ __forceinline__ void run(float2 *buf, const float2 *tabs, int tid)
     {
         if constexpr (I < npasses(LOGN, MR) - 1) {
             constexpr int RLOG = fwd_rlog(LOGN, I, MR);
-            pass<LOGN, fwd_slog(LOGN, I, MR), RLOG, false, P / (1 << RLOG) / T, T, L>(buf, tabs + fwd_off(LOGN, I, MR), tid);
-            FwdPasses<LOGN, I + 1, T, L, P, MR>::run(buf, tabs, tid);
+            pass<LOGN, fwd_slog(LOGN, I, MR), RLOG, false, P / (1 << RLOG) / T, T, L, WS>(buf, tabs + fwd_off(LOGN, I, MR), tid);
+            FwdPasses<LOGN, I + 1, T, L, P, MR, WS>::run(buf, tabs, tid);
         }
     }
 };
-template <int LOGN, int I, int T, class L, int P, int MR = 3>
+template <int LOGN, int I, int T, class L, int P, int MR = 3, bool WS = false>
 struct InvPasses {
     static __device__ __forceinline__ void run(float2 *buf, const float2 *tabs, int tid)
     {
         if constexpr (I < npasses(LOGN, MR) - 1) {
             constexpr int RLOG = inv_rlog(LOGN, I, MR);
-            pass<LOGN, inv_slog(LOGN, I, MR), RLOG, true, P / (1 << RLOG) / T, T, L>(buf, tabs + inv_off(LOGN, I, MR), tid);
-            InvPasses<LOGN, I + 1, T, L, P, MR>::run(buf, tabs, tid);
+            pass<LOGN, inv_slog(LOGN, I, MR), RLOG, true, P / (1 << RLOG) / T, T, L, WS>(buf, tabs + inv_off(LOGN, I, MR), tid);
+            InvPasses<LOGN, I + 1, T, L, P, MR, WS>::run(buf, tabs, tid);
         }
     }
 };
 
 // Full transform pair (forward, spectral operator, inverse) up to the
 // inverse's last pass, whose loads and DFT are left to the caller.
-template <int LOGN, int T, class L, int P, class Op, int MR = 3>
+template <int LOGN, int T, class L, int P, class Op, int MR = 3, bool WS = false>
 __device__ __forceinline__ void transform_pair(float2 *buf, const float2 *tabs, const Op &op, int tid)
 {
-    FwdPasses<LOGN, 0, T, L, P, MR>::run(buf, tabs, tid);
+    FwdPasses<LOGN, 0, T, L, P, MR, WS>::run(buf, tabs, tid);
     constexpr int RM = fwd_rlog(LOGN, npasses(LOGN, MR) - 1, MR);
-    middle<LOGN, RM, P / (1 << RM) / T, T, L>(buf, tabs + inv_off(LOGN, 0, MR), op, tid);
-    InvPasses<LOGN, 1, T, L, P, MR>::run(buf, tabs, tid);
+    middle<LOGN, RM, P / (1 << RM) / T, T, L, Op, WS>(buf, tabs + inv_off(LOGN, 0, MR), op, tid);
+    InvPasses<LOGN, 1, T, L, P, MR, WS>::run(buf, tabs, tid);
 }
 
 // Forward transform alone, result in natural order in buf.
@@ -340,14 +361,14 @@ struct ScaleBins {
     }
 };
 
-template <int LOGN, int NB, int T, class L, int MR = 3>
+template <int LOGN, int NB, int T, class L, int MR = 3, bool WS = false>
 __device__ __forceinline__ void last_inverse(const float2 *buf, float2 (&x)[NB][1 << inv_rlog(LOGN, npasses(LOGN, MR) - 1, MR)],
                                              int (&bb)[NB], int (&tt)[NB], int tid)
 {
     constexpr int RLOG = inv_rlog(LOGN, npasses(LOGN, MR) - 1, MR), R = 1 << RLOG, PER = (1 << LOGN) / R;
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
-        L::template split<PER>(tid + j * T, bb[j], tt[j]);
+        L::template split<PER>(bfly<WS, NB, T>(tid, j), bb[j], tt[j]);
 #pragma unroll
         for (int r = 0; r < R; ++r) x[j][r] = buf[L::at(bb[j], tt[j] + r * PER)];
         Dft<RLOG, true>::run(x[j]);

@@ -11,17 +11,19 @@
 // [c R2, (c+1) R2), each holding the real rows (2k, 2k+1) as (re, im), in its
 // row buffer, and complex columns [c W2, (c+1) W2), each holding the real
 // columns (2j, 2j+1), in its column buffer.  The Fourier factor of Eq. (8) is
-// real, even and separable, so it acts on each packed row / column as on two
-// real ones.  One contour step:
-//   gather rows -> my columns (distributed shared memory, 2 x 2 re/im
-//   transposes), column transform Ky, cluster barrier, gather columns -> my
-//   rows, row transform Kx, node factors: a_m = E_m g_m = E_m^2 T(a_{m-1}).
-// The exchanges are pushes: each CTA writes its points into the owners'
-// buffers with st.async, counted as transaction bytes on the owner's
-// mbarrier, and a buffer is rewritten only after every CTA has passed the
-// relaxed cluster barrier that follows its last read of that buffer.  The
-// first exchange also stores a_{m-1} (coalesced, fire-and-forget) for the
-// contour sums.
+// real, even and separable, K = Kx(kx) Ky(ky), so it acts on each packed
+// row / column as on two real ones, and its row part Gx = IFFT_x Kx FFT_x and
+// column part Gy commute.  Contour step m computes
+//   a_m = E_m g_m = E_m^2 Gx Gy a_{m-1}
+// as Gy, exchange, Gx on odd steps and Gx, exchange, Gy on even steps: each
+// step ends in the packing the next one starts from, so the field changes
+// packing once per contour step (one all-to-all of the cluster, 2 x 2 re/im
+// transposes by lane-pair shuffles).  The exchange is a push: each CTA
+// writes its points into the owners' buffer with st.async, counted as
+// transaction bytes on the owner's mbarrier; no cluster barrier is needed
+// inside the contour loop (see the ordering note at the loop).  The row
+// transforms are warp-private (each warp owns whole packed rows).  Every
+// step stores a_m in the packed-row layout for the contour sums.
 //
 // The contour sums of Eqs. (9)-(10) pair node m of g with node N_s - m of g'
 // at every site: a separate pass (prop_contour) reads both chains' stored
@@ -92,7 +94,10 @@ struct ClusterGeom {
     static constexpr int MRX = (best_mr(LOGX) == 4 && P % (16 * T) == 0) ? 4 : 3;
     static constexpr int MRY = (best_mr(LOGY) == 4 && P % (16 * T) == 0) ? 4 : 3;
     static constexpr int TABX = tabs_total(LOGX, MRX), TABY = tabs_total(LOGY, MRY);
-    static constexpr size_t SMEM = (size_t)(R2 * PITCH + P + TABX + TABY) * sizeof(float2) + (NX + NY) * sizeof(float);
+    // row buffer, column buffer, pass tables, Fourier factors, the node
+    // factors of the epilogue sites in either packing (P points each)
+    static constexpr size_t SMEM =
+        (size_t)(R2 * PITCH + P + TABX + TABY + 2 * P) * sizeof(float2) + (NX + NY) * sizeof(float);
     static constexpr size_t SMEM_DIFF = SMEM;
 };
 
@@ -143,8 +148,39 @@ __device__ __forceinline__ void mbar_wait(unsigned bar, unsigned parity, int &fa
             return;
         }
 }
-__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory"); }
-__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.aligned;" ::: "memory"); }
+
+// Points of the column transform's last pass for butterfly index bf: packed
+// column c and butterfly t, arranged so that the threads holding real rows y
+// and y + 1 (butterflies t and t + 1, same r) of one column are lanes l and
+// l ^ 16 of a warp; the 2 x 2 re/im transpose between the packings is then
+// one shuffle.  Bijective on [0, W PER) when W PER is a multiple of 32 and
+// PER is even; for W = 16 it is the tile-wide split of the other passes.
+template <int W>
+__device__ __forceinline__ void col_pair_split(int bf, int &c, int &t)
+{
+    const int lin = (bf >> 5) * 16 + (bf & 15), par = (bf >> 4) & 1;
+    c = lin % W;
+    t = 2 * (lin / W) + par;
+}
+
+// The 2 x 2 re/im transpose of a lane pair (partner lane ^ LANES): the lane
+// with odd = false holds (p(2i, r), p(2i+1, r)) and its partner
+// (p(2i, r+1), p(2i+1, r+1)) of one packing; afterwards they hold
+// (p(2i, r), p(2i, r+1)) and (p(2i+1, r), p(2i+1, r+1)) of the other.  The
+// transpose is its own inverse.
+template <int LANES>
+__device__ __forceinline__ float2 pair_transpose(float2 v, bool odd)
+{
+    const float t = __shfl_xor_sync(0xffffffffu, odd ? v.x : v.y, LANES);
+    return odd ? f2(t, v.y) : f2(v.x, t);
+}
+
+// Contour step m applies the Fourier factor of Eq. (8) as its column part Gy
+// (all packed columns) and its row part Gx (all packed rows).  The factor is
+// separable, so Gx and Gy commute: odd steps take Gy first, even steps Gx
+// first, and each step ends in the packing its next step starts from.  One
+// exchange of the field between the packings per contour step.
+__device__ __forceinline__ bool starts_in_columns(int m) { return m & 1; }
 
 // MINB: CTAs per SM the register budget is sized for (65536 / (T MINB) each)
 template <int LOGX, int LOGY, int C, int T, int MINB, bool DIFF>
@@ -152,10 +188,13 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
 {
     using G = ClusterGeom<LOGX, LOGY, C, T>;
     constexpr int NX = G::NX, NY = G::NY, R2 = G::R2, W2 = G::W2, P = G::P, HN = G::HN;
+    constexpr int NWARP = T / 32;
     static_assert(P == W2 * NY, "layout sizes");
     static_assert(P % (8 * T) == 0, "every pass gives each thread whole butterflies");
     static_assert(LOGX >= 4 && LOGY >= 4 && R2 >= 1 && W2 >= 1, "tile shape");
-    static_assert(T % 32 == 0 && P % T == 0 && NX % 2 == 0, "whole warps, whole exchange steps, lane pairs");
+    static_assert(T % 32 == 0 && P % T == 0 && NX % 2 == 0, "whole warps, lane pairs");
+    static_assert(R2 % NWARP == 0, "warp-private row transforms: every warp owns whole packed rows");
+    static_assert(W2 % 16 == 0 || 16 % W2 == 0, "column pairs of the last column pass");
     using RL = RowLayout<LOGX>;
     using CL = ColLayout<LOGY, W2>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -165,6 +204,9 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
     float2 *taby = tabx + G::TABX;
     float *kx = reinterpret_cast<float *>(taby + G::TABY);
     float *ky = kx + NX;
+    // E^2 (or E'^2) of the two real sites of each epilogue point, thread-major
+    // ([point of the thread][thread]: conflict-free), rows then columns
+    float2 *fac_r = reinterpret_cast<float2 *>(ky + NY), *fac_c = fac_r + P;
     cg::cluster_group cl = cg::this_cluster();
     const int crank = (int)cl.block_rank();
     const int slot = blockIdx.x / C;
@@ -175,7 +217,8 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
     // over the phases: chain j sits out phase j)
     const int seg = k.skip < cidx ? k.skip : k.skip - 1;
     const int m_begin = k.nseg ? seg * ns / k.nseg : 0, m_end = k.nseg ? (seg + 1) * ns / k.nseg : ns;
-    const int krow0 = crank * R2;  // first packed row of this CTA
+    const int nsteps = m_end - m_begin;
+    const int krow0 = crank * R2, jcol0 = crank * W2;  // first packed row and packed column of this CTA
 
     copy_tables(tabx, k.twx, G::TABX, tid, T);
     copy_tables(taby, k.twy, G::TABY, tid, T);
@@ -183,18 +226,33 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
     for (int i = tid; i < NY; i += T) ky[i] = k.ky[i];
     const float2 *efac = k.efac + (size_t)run * n;
     const float2 *rho = DIFF ? k.rho + (size_t)run * n : nullptr;
-    // rho (2 + rho) of this CTA's packed rows, block A then B (L2-resident, read per step)
-    const float2 *c2p = DIFF ? k.c2p + (size_t)run * 2 * HN + (size_t)krow0 * NX : nullptr;
-    // this CTA's block of the stored states of node m: hout + m * HN
-    float2 *hout = k.hout + (size_t)(run * 2 + chain) * (ns + 1) * HN + (size_t)krow0 * NX;
-    const float2 *href = DIFF ? k.href + (size_t)(run * 2 + chain) * (ns + 1) * HN + (size_t)krow0 * NX : nullptr;
+    // this chain's stored states of node m at hout + m HN, packed rows
+    // [NY/2][NX]; rho (2 + rho) of blocks A, B in the same layout
+    float2 *hout = k.hout + (size_t)(run * 2 + chain) * (ns + 1) * HN;
+    const float2 *href = DIFF ? k.href + (size_t)(run * 2 + chain) * (ns + 1) * HN : nullptr;
+    const float2 *c2p = DIFF ? k.c2p + (size_t)run * 2 * HN : nullptr;
 
     // node factor of this chain at contour node j: g carries w_A iff j < N_A,
     // g' sees the field of node N_s - j
     auto blk_b = [&](int j) { return (chain == 0 ? j : ns - j) >= na; };
+    // a_0 = E_0 (d a_0 = rho_0 E_0) at the real site of packed row kk,
+    // column x, rows 2kk (re) and 2kk + 1 (im)
+    auto node0 = [&](int kk, int x) {
+        const int site = 2 * kk * NX + x;
+        const bool bk = blk_b(0);
+        const float2 f0 = efac[site], f1 = efac[site + NX];
+        float2 a0 = bk ? f2(f0.y, f1.y) : f2(f0.x, f1.x);
+        if (DIFF) {
+            const float2 r0 = rho[site], r1 = rho[site + NX];
+            a0.x *= bk ? r0.y : r0.x;
+            a0.y *= bk ? r1.y : r1.x;
+        }
+        return a0;
+    };
 
-    // exchange barriers: [0] my column buffer, [1] my row buffer; each
-    // completes once per contour step when all P points have arrived
+    // exchange barriers: [0] my column buffer (filled by the exchange of the
+    // steps that start in rows), [1] my row buffer (steps that start in
+    // columns); each completes once per use, when all P points have arrived
     __shared__ __align__(8) unsigned long long mbar[2];
     const unsigned bar_col = smem_u32(&mbar[0]), bar_row = smem_u32(&mbar[1]);
     constexpr unsigned XBYTES = (unsigned)(P * sizeof(float2));
@@ -206,152 +264,227 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
         mbar_expect(bar_row, XBYTES);
     }
 
-    // node 0: g_0 = 1, a_0 = E_0 (d a_0 = rho_0 E_0); a later segment resumes
-    // from the state a_{m_begin} its previous phase stored (the same FP32
-    // values, so the result does not depend on the schedule)
-    for (int e = tid; e < P; e += T) {
-        const int b = e / NX, x = e % NX;
-        if (m_begin > 0) {
-            rowbuf[RL::at(b, x)] = hout[(size_t)m_begin * HN + e];
-            continue;
-        }
-        const int site = 2 * (krow0 + b) * NX + x;
-        const bool bk = blk_b(0);
-        const float2 f0 = efac[site], f1 = efac[site + NX];
-        float2 a0 = bk ? f2(f0.y, f1.y) : f2(f0.x, f1.x);
-        if (DIFF) {
-            const float2 r0 = rho[site], r1 = rho[site + NX];
-            a0.x *= bk ? r0.y : r0.x;
-            a0.y *= bk ? r1.y : r1.x;
-        }
-        rowbuf[RL::at(b, x)] = a0;
+    // node m_begin into the packing the first step starts from: a_0 from the
+    // node factors (and stored for the contour sums), or the state a_{m_begin}
+    // the previous phase stored (the same FP32 values, so the result does not
+    // depend on the schedule)
+    if (m_begin == 0) {
+        for (int e = tid; e < P; e += T) hout[(size_t)krow0 * NX + e] = node0(krow0 + e / NX, e % NX);
     }
-    cl.sync();  // every CTA's barriers are initialised, every row buffer holds a_{m_begin}
+    if (starts_in_columns(m_begin + 1)) {
+        // packed column jcol0 + c, real row y: (a(2J, y), a(2J + 1, y))
+        for (int e = tid; e < P; e += T) {
+            const int c = e % W2, y = e / W2, jx = 2 * (jcol0 + c), kk = y >> 1;
+            float2 p0, p1;
+            if (m_begin == 0) {
+                p0 = node0(kk, jx);
+                p1 = node0(kk, jx + 1);
+            } else {
+                p0 = hout[(size_t)m_begin * HN + kk * NX + jx];
+                p1 = hout[(size_t)m_begin * HN + kk * NX + jx + 1];
+            }
+            colbuf[CL::at(c, y)] = (y & 1) ? f2(p0.y, p1.y) : f2(p0.x, p1.x);
+        }
+    } else {
+        for (int e = tid; e < P; e += T) {
+            const int b = e / NX, x = e % NX;
+            rowbuf[RL::at(b, x)] = m_begin == 0 ? node0(krow0 + b, x) : hout[(size_t)m_begin * HN + (size_t)krow0 * NX + e];
+        }
+    }
+    cl.sync();  // every CTA's barriers are initialised, the first packing is in place
 
-    // epilogue geometry: the inverse row transform's last pass
+    const bool odd = tid & 1;
+    // last row pass (warp-private) and last column pass geometry
     constexpr int RLOG_L = inv_rlog(LOGX, npasses(LOGX, G::MRX) - 1, G::MRX), RR = 1 << RLOG_L, PER_L = NX / RR;
     constexpr int NB_L = P / RR / T;
-    // per-site factors of this thread's epilogue sites, reloaded when the
-    // block (A or B) changes: E^2 (plain) or E'^2 (DIFF) in registers
-    float c1[NB_L][RR][2];
-    int cur_b = -1;
+    static_assert(PER_L % 2 == 0, "lane pairs (x, x + 1) of the last row pass");
+    constexpr int RLOG_C = inv_rlog(LOGY, npasses(LOGY, G::MRY) - 1, G::MRY), RC = 1 << RLOG_C, PER_C = NY / RC;
+    constexpr int NB_C = P / RC / T;
+    static_assert(PER_C % 2 == 0 && (P / RC) % 32 == 0, "column pairs of the last column pass");
+    // per-site factors E^2 (plain) or E'^2 (DIFF) of this thread's epilogue
+    // sites in either packing (fac_r, fac_c), reloaded when the block (A or
+    // B) changes; each thread reads only what it wrote
+    int cur_r = -1, cur_c = -1;
     int failed = 0;
-    const bool odd = tid & 1;
-    constexpr int NG = P / T;  // points each thread pushes per exchange
+    auto factor = [&](int site, int bm) {
+        const float2 ef = efac[site];
+        const float e = bm ? ef.y : ef.x;
+        if (!DIFF) return e * e;
+        const float2 rf = rho[site];
+        const float q = bm ? rf.y : rf.x, ep = e * (1.f + q);
+        return ep * ep;
+    };
+    // a_m = E_m^2 U (plain) or d a_m = E'^2 U + rho (2 + rho) a~_m (DIFF) at
+    // packed-row point (kk, x), U = T(a_{m-1}) there
+    auto finish = [&](float2 u, float2 f, int m, int bm, int kk, int x) {
+        if (!DIFF) return f2(f.x * u.x, f.y * u.y);
+        const size_t e = (size_t)kk * NX + x;
+        const float2 ar = href[(size_t)m * HN + e];  // a~_m
+        const float2 cq = c2p[(size_t)bm * HN + e];  // rho (2 + rho)
+        return f2(f.x * u.x + cq.x * ar.x, f.y * u.y + cq.y * ar.y);
+    };
 
-    // One contour step.  The two exchanges push (st.async) into the owners'
-    // buffers; a buffer is rewritten only after every CTA has arrived at the
-    // relaxed cluster barrier that follows its last read of that buffer.
-    for (int m = m_begin + 1; m <= m_end; ++m) {
-        // barrier bookkeeping counts this launch's steps
-        const unsigned par = (unsigned)(m - m_begin - 1) & 1u;
-        const bool more = m < m_end;
-        if (m > m_begin + 1) cluster_wait();  // every column buffer has been read out
-        // my packed rows -> the owners' packed columns.  Consecutive threads
-        // take consecutive real columns x of packed row kk; lanes (2i, 2i+1)
-        // hold columns (x0, x0+1) and swap halves, the even lane forming real
-        // row 2kk of packed column x0/2, the odd lane real row 2kk+1.
+    // The contour loop runs over half steps: each applies the transform pair
+    // of its packing, then either hands the field over (first half of a
+    // step) or applies the node factors (second half), so every transform is
+    // compiled once.  Step m's halves are in columns then rows for odd m,
+    // rows then columns for even m.  A buffer is written by the exchange only
+    // every other step, and only by CTAs that have received data which every
+    // owner computed after its last read of that buffer, so the pushes are
+    // ordered behind those reads through the exchange barriers themselves.
+    for (int hs = 0; hs < 2 * nsteps; ++hs) {
+        const int i = hs >> 1, m = m_begin + 1 + i;
+        const bool second = hs & 1, cols = starts_in_columns(m) != second;
+        const unsigned par = (unsigned)(i >> 1) & 1u;  // uses of this step's barrier so far in this launch
+        const bool rearm = i + 2 < nsteps;
+        const int bm = blk_b(m) ? 1 : 0;
+        if (DIFF && !second) {
+            // a~_m and rho (2 + rho) of this step's epilogue sites into L1
+            // ahead of use (the packing the step ends in)
+            auto pf = [&](size_t e) {
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(href + (size_t)m * HN + e));
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(c2p + (size_t)bm * HN + e));
+            };
+            if (cols) {
 #pragma unroll
-        for (int u = 0; u < NG; ++u) {
-            const int e = tid + u * T, bl = e / NX, x = e % NX;
-            const float2 v = rowbuf[RL::at(bl, x)];
-            hout[(size_t)(m - 1) * HN + e] = v;  // a_{m-1} for the contour sums
-            const float t = __shfl_xor_sync(0xffffffffu, odd ? v.x : v.y, 1);
-            const int jj = x >> 1, dst = jj / W2;
-            const unsigned ra = map_rank(smem_u32(colbuf + CL::at(jj % W2, 2 * (krow0 + bl) + (odd ? 1 : 0))), dst);
-            push_f2(ra, odd ? f2(t, v.y) : f2(v.x, t), map_rank(bar_col, dst));
-        }
-        cluster_arrive();  // my row buffer is read out
-        mbar_wait(bar_col, par, failed);
-        if (tid == 0 && more) mbar_expect(bar_col, XBYTES);
-        if (DIFF) {
-            // a~_m for this thread's epilogue sites, into L1 ahead of use
+                for (int j = 0; j < NB_L; ++j) {
+                    int b, t;
+                    RL::template split<PER_L>(bfly<true, NB_L, T>(tid, j), b, t);
 #pragma unroll
-            for (int j = 0; j < NB_L; ++j) {
-                int b, t;
-                RL::template split<PER_L>(tid + j * T, b, t);
+                    for (int r = 0; r < RR; ++r) pf((size_t)(krow0 + b) * NX + t + r * PER_L);
+                }
+            } else {
 #pragma unroll
-                for (int r = 0; r < RR; ++r)
-                    asm volatile("prefetch.global.L1 [%0];" ::"l"(href + (size_t)m * HN + b * NX + t + r * PER_L));
+                for (int j = 0; j < NB_C; ++j) {
+                    int c, t;
+                    col_pair_split<W2>(tid + j * T, c, t);
+#pragma unroll
+                    for (int r = 0; r < RC; ++r)
+                        pf((size_t)((t + r * PER_C) >> 1) * NX + 2 * (jcol0 + c) + (t & 1));
+                }
             }
         }
-        transform_pair<LOGY, T, CL, P, ScaleBins, G::MRY>(colbuf, taby, ScaleBins{ky}, tid);
-        {
-            constexpr int RLOG_C = inv_rlog(LOGY, npasses(LOGY, G::MRY) - 1, G::MRY), NB_C = P / (1 << RLOG_C) / T;
-            float2 x[NB_C][1 << RLOG_C];
-            int bb[NB_C], tt[NB_C];
-            last_inverse<LOGY, NB_C, T, CL, G::MRY>(colbuf, x, bb, tt, tid);
+        if (cols) {
+            // ---- Gy on my packed columns
+            transform_pair<LOGY, T, CL, P, ScaleBins, G::MRY>(colbuf, taby, ScaleBins{ky}, tid);
+            float2 x[NB_C][RC];
+            int cc[NB_C], ct[NB_C];
 #pragma unroll
-            for (int j = 0; j < NB_C; ++j)
+            for (int j = 0; j < NB_C; ++j) {
+                col_pair_split<W2>(tid + j * T, cc[j], ct[j]);
 #pragma unroll
-                for (int r = 0; r < (1 << RLOG_C); ++r) colbuf[CL::at(bb[j], tt[j] + r * (NY >> RLOG_C))] = x[j][r];
-        }
-        __syncthreads();
-        cluster_wait();  // every row buffer has been read out
-        // my packed columns -> the owners' packed rows: lanes (2i, 2i+1) hold
-        // real rows (2kk, 2kk+1) of packed column jl and swap halves, the even
-        // lane forming point x0 = 2 (c W2 + jl) of packed row kk, the odd lane x0+1.
+                for (int r = 0; r < RC; ++r) x[j][r] = colbuf[CL::at(cc[j], ct[j] + r * PER_C)];
+            }
 #pragma unroll
-        for (int u = 0; u < NG; ++u) {
-            const int e = tid + u * T, kk = e / (2 * W2), jl = (e % (2 * W2)) >> 1;
-            const float2 v = colbuf[CL::at(jl, 2 * kk + (odd ? 1 : 0))];
-            const float t = __shfl_xor_sync(0xffffffffu, odd ? v.x : v.y, 1);
-            const int dst = kk / R2;
-            const unsigned ra = map_rank(smem_u32(rowbuf + RL::at(kk % R2, 2 * (crank * W2 + jl) + (odd ? 1 : 0))), dst);
-            push_f2(ra, odd ? f2(t, v.y) : f2(v.x, t), map_rank(bar_row, dst));
-        }
-        cluster_arrive();  // my column buffer is read out
-        mbar_wait(bar_row, par, failed);
-        if (tid == 0 && more) mbar_expect(bar_row, XBYTES);
-        transform_pair<LOGX, T, RL, P, ScaleBins, G::MRX>(rowbuf, tabx, ScaleBins{kx}, tid);
-        float2 h[NB_L][RR];
-        int bb[NB_L], tt[NB_L];
-        last_inverse<LOGX, NB_L, T, RL, G::MRX>(rowbuf, h, bb, tt, tid);
-
-        const int bm = blk_b(m) ? 1 : 0;
-        if (bm != cur_b) {
-            cur_b = bm;
+            for (int j = 0; j < NB_C; ++j) Dft<RLOG_C, true>::run(x[j]);
+            if (!second) {
+                // my columns -> the owners' rows: lanes l (real row y = 2kk)
+                // and l ^ 16 (y + 1) of packed column J form points x = 2J and
+                // 2J + 1 of packed row kk
 #pragma unroll
-            for (int j = 0; j < NB_L; ++j)
+                for (int j = 0; j < NB_C; ++j) {
+                    const bool oy = ct[j] & 1;
 #pragma unroll
-                for (int r = 0; r < RR; ++r) {
-                    const int site0 = 2 * (krow0 + bb[j]) * NX + tt[j] + r * PER_L;
-#pragma unroll
-                    for (int cp = 0; cp < 2; ++cp) {
-                        const float2 ef = efac[site0 + cp * NX];
-                        const float e = bm ? ef.y : ef.x;
-                        if (!DIFF) {
-                            c1[j][r][cp] = e * e;
-                        } else {
-                            const float2 rf = rho[site0 + cp * NX];
-                            const float q = bm ? rf.y : rf.x, ep = e * (1.f + q);
-                            c1[j][r][cp] = ep * ep;
-                        }
+                    for (int r = 0; r < RC; ++r) {
+                        const float2 v = pair_transpose<16>(x[j][r], oy);
+                        const int kk = (ct[j] + r * PER_C) >> 1, dst = kk / R2;
+                        const int xx = 2 * (jcol0 + cc[j]) + (oy ? 1 : 0);
+                        push_f2(map_rank(smem_u32(rowbuf + RL::at(kk % R2, xx)), dst), v, map_rank(bar_row, dst));
                     }
                 }
-        }
+                mbar_wait(bar_row, par, failed);
+                // re-armed before this warp's next warp barrier, which orders
+                // it before every later push of this warp that the barrier's
+                // next use depends on
+                if (tid == 0 && rearm) mbar_expect(bar_row, XBYTES);
+            } else {
+                // node factors in the packed-row form (x = 2J + (y & 1) of
+                // packed row y / 2), the result back in the column buffer
+                if (bm != cur_c) {
+                    cur_c = bm;
 #pragma unroll
-        for (int j = 0; j < NB_L; ++j) {
+                    for (int j = 0; j < NB_C; ++j)
 #pragma unroll
-            for (int r = 0; r < RR; ++r) {
-                const int x = tt[j] + r * PER_L;
-                float2 a;
-                if (!DIFF) {
-                    a = f2(c1[j][r][0] * h[j][r].x, c1[j][r][1] * h[j][r].y);
-                } else {
-                    const float2 ar = href[(size_t)m * HN + bb[j] * NX + x];  // a~_m
-                    const float2 cq = c2p[(size_t)bm * HN + bb[j] * NX + x];    // rho (2 + rho)
-                    a = f2(c1[j][r][0] * h[j][r].x + cq.x * ar.x, c1[j][r][1] * h[j][r].y + cq.y * ar.y);
+                        for (int r = 0; r < RC; ++r) {
+                            const int kk = (ct[j] + r * PER_C) >> 1, xx = 2 * (jcol0 + cc[j]) + (ct[j] & 1);
+                            fac_c[(j * RC + r) * T + tid] =
+                                f2(factor(2 * kk * NX + xx, bm), factor(2 * kk * NX + xx + NX, bm));
+                        }
                 }
-                rowbuf[RL::at(bb[j], x)] = a;
+#pragma unroll
+                for (int j = 0; j < NB_C; ++j)
+#pragma unroll
+                    for (int r = 0; r < RC; ++r) {
+                        const int kk = (ct[j] + r * PER_C) >> 1, xx = 2 * (jcol0 + cc[j]) + (ct[j] & 1);
+                        x[j][r] = finish(pair_transpose<16>(x[j][r], ct[j] & 1), fac_c[(j * RC + r) * T + tid], m, bm, kk, xx);
+                    }
+                __syncthreads();  // every thread has read its columns: they are rewritten below
+#pragma unroll
+                for (int j = 0; j < NB_C; ++j) {
+                    const bool oy = ct[j] & 1;
+#pragma unroll
+                    for (int r = 0; r < RC; ++r) {
+                        const int y = ct[j] + r * PER_C, kk = y >> 1, xx = 2 * (jcol0 + cc[j]) + (oy ? 1 : 0);
+                        hout[(size_t)m * HN + (size_t)kk * NX + xx] = x[j][r];
+                        colbuf[CL::at(cc[j], y)] = pair_transpose<16>(x[j][r], oy);
+                    }
+                }
+                __syncthreads();  // the next step's column passes read every column
+            }
+        } else {
+            // ---- Gx on my packed rows (each warp its own)
+            transform_pair<LOGX, T, RL, P, ScaleBins, G::MRX, true>(rowbuf, tabx, ScaleBins{kx}, tid);
+            float2 h[NB_L][RR];
+            int bb[NB_L], tt[NB_L];
+            last_inverse<LOGX, NB_L, T, RL, G::MRX, true>(rowbuf, h, bb, tt, tid);
+            if (!second) {
+                // my rows -> the owners' columns: lanes (2i, 2i + 1) hold
+                // columns (x0, x0 + 1) of packed row kk; the even lane forms
+                // real row 2kk of packed column x0 / 2, the odd lane real row
+                // 2kk + 1
+#pragma unroll
+                for (int j = 0; j < NB_L; ++j)
+#pragma unroll
+                    for (int r = 0; r < RR; ++r) {
+                        const float2 v = pair_transpose<1>(h[j][r], odd);
+                        const int jj = (tt[j] + r * PER_L) >> 1, dst = jj / W2, y = 2 * (krow0 + bb[j]) + (odd ? 1 : 0);
+                        push_f2(map_rank(smem_u32(colbuf + CL::at(jj % W2, y)), dst), v, map_rank(bar_col, dst));
+                    }
+                mbar_wait(bar_col, par, failed);
+                // re-armed before this step's CTA barriers, so before every later push
+                if (tid == 0 && rearm) mbar_expect(bar_col, XBYTES);
+            } else {
+                // node factors; the result stays in the row buffer
+                if (bm != cur_r) {
+                    cur_r = bm;
+#pragma unroll
+                    for (int j = 0; j < NB_L; ++j)
+#pragma unroll
+                        for (int r = 0; r < RR; ++r) {
+                            const int site = 2 * (krow0 + bb[j]) * NX + tt[j] + r * PER_L;
+                            fac_r[(j * RR + r) * T + tid] = f2(factor(site, bm), factor(site + NX, bm));
+                        }
+                }
+                // every value first: the stores come after
+#pragma unroll
+                for (int j = 0; j < NB_L; ++j)
+#pragma unroll
+                    for (int r = 0; r < RR; ++r)
+                        h[j][r] = finish(h[j][r], fac_r[(j * RR + r) * T + tid], m, bm, krow0 + bb[j], tt[j] + r * PER_L);
+#pragma unroll
+                for (int j = 0; j < NB_L; ++j)
+#pragma unroll
+                    for (int r = 0; r < RR; ++r) {
+                        const int x = tt[j] + r * PER_L;
+                        hout[(size_t)m * HN + (size_t)(krow0 + bb[j]) * NX + x] = h[j][r];
+                        rowbuf[RL::at(bb[j], x)] = h[j][r];
+                    }
+                __syncwarp();  // the next step's row passes read these rows in this warp
             }
         }
-        __syncthreads();
     }
-    for (int e = tid; e < P; e += T) hout[(size_t)m_end * HN + e] = rowbuf[RL::at(e / NX, e % NX)];  // a_{m_end}
-    cluster_wait();  // pairs the last arrival
     if (failed) atomicOr(k.err, 4);
-    cl.sync();  // no CTA leaves while others may still read its shared memory
+    cl.sync();  // no CTA leaves while others may still write into its shared memory
 }
 
 // ---------------------------------------------------------------------------
@@ -632,21 +765,24 @@ static ClusterShape shape_of()
 }
 
 // Instantiated grids (log2 nx, log2 ny).  Tiles of 4096 points take 256
-// threads with 128 registers each (two butterflies per thread and pass, two
-// CTAs per SM): on the 4 x 256 x 512 batch 12% faster than 512 threads with
-// 64 registers, which spilled; the smallest grids keep one butterfly per thread.
+// threads (one or two butterflies per thread and pass) with the SM's whole
+// register file (both packings' per-site factors stay in registers; at 128
+// registers a thread spilled 220-480 bytes); the smaller tiles fit several
+// CTAs per SM.
 static const ClusterShape *find_shape(int logx, int logy)
 {
     static const ClusterShape shapes[] = {
-        shape_of<6, 6, 2, 128>(),     shape_of<7, 6, 2, 256>(),     shape_of<6, 7, 2, 256>(),
-        shape_of<7, 7, 2, 256, 2>(),  shape_of<8, 7, 4, 256, 2>(),  shape_of<7, 8, 4, 256, 2>(),
-        shape_of<8, 8, 8, 256, 2>(),  shape_of<9, 7, 8, 256, 2>(),  shape_of<7, 9, 8, 256, 2>(),
-        shape_of<9, 8, 16, 256, 2>(), shape_of<8, 9, 16, 256, 2>(),
+        shape_of<6, 6, 2, 128, 4>(),  shape_of<7, 6, 2, 256, 2>(),  shape_of<6, 7, 2, 256, 2>(),
+        shape_of<7, 7, 2, 256, 1>(),  shape_of<8, 7, 4, 256, 1>(),  shape_of<7, 8, 4, 256, 1>(),
+        shape_of<8, 8, 8, 256, 1>(),  shape_of<9, 7, 8, 256, 1>(),  shape_of<7, 9, 8, 256, 1>(),
+        shape_of<9, 8, 16, 256, 1>(), shape_of<8, 9, 16, 256, 1>(),
     };
     for (const auto &s : shapes)
         if (s.logx == logx && s.logy == logy) return &s;
     return nullptr;
 }
+
+static const void *chain_fn(const ClusterShape *s, bool diff) { return diff ? s->fn_diff : s->fn; }
 
 static void set_cluster_cfg(cudaLaunchConfig_t &cfg, cudaLaunchAttribute &attr, const ClusterShape *s, int nclusters,
                             bool diff)
@@ -670,7 +806,7 @@ static int g_solo_clusters[16][16][2];
 
 static int count_solo_clusters(const ClusterShape *s, bool diff)
 {
-    const void *fn = diff ? s->fn_diff : s->fn;
+    const void *fn = chain_fn(s, diff);
     const size_t sm = std::max(kSoloSmem, diff ? s->smem_diff : s->smem);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return 0;
     cudaLaunchConfig_t cfg = {};
@@ -694,7 +830,7 @@ bool cluster_solve_supported(const Group &G)
     if (st == 0) {
         st = 2;
         auto ok = [&](bool diff) {
-            const void *fn = diff ? s->fn_diff : s->fn;
+            const void *fn = chain_fn(s, diff);
             const size_t sm = diff ? s->smem_diff : s->smem;
             if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return false;
             if (s->c > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
@@ -785,7 +921,7 @@ cudaError_t launch_cluster_solve(Group &G, cudaStream_t s, bool diff, int nprep_
     void *args[] = {&k};
     for (int p = 0; p < launches; ++p) {
         k.skip = p;
-        cudaError_t e = cudaLaunchKernelExC(&cfg, diff ? sh->fn_diff : sh->fn, args);
+        cudaError_t e = cudaLaunchKernelExC(&cfg, chain_fn(sh, diff), args);
         if (e != cudaSuccess) return e;
     }
     if (probe) cudaEventRecordWithFlags(probe->ev[1], s, cudaEventRecordExternal);
