@@ -90,6 +90,13 @@ enum {
  *  f0          reverse-Poiseuille amplitude of Eq. (23) in units of f* = rho R_G / tau^2
  *  noise_amp   amplitude a of the initial noise omega_I = a U(-1, 1)
  *  seed        seed of the counter-based noise (splitmix64)
+ *  junction_rule  the field at the A/B junction node s = q_A of the split step
+ *              of Eq. (8) (Sec. 2 puts omega_A at s < q_A and omega_B
+ *              otherwise): 0 literal (node j carries omega_A iff j < N_A, so
+ *              the junction node takes omega_B); 1 segment-symmetric (both
+ *              half-steps of the interval [s_j, s_{j+1}] use the field of its
+ *              block, A iff j < N_A, the same from either chain end)
+ *  reserved    0
  */
 typedef struct epd_lb_params {
     int32_t nx, ny, ns, precision;
@@ -100,6 +107,7 @@ typedef struct epd_lb_params {
     double f0;
     double noise_amp;
     uint64_t seed;
+    int32_t junction_rule, reserved;
 } epd_lb_params;
 
 typedef struct epd_lb epd_lb; /* opaque, library-owned */
@@ -422,15 +430,22 @@ int epd_prop_solve(const epd_lb_params *p, const double *omega_dev, double *phi_
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress, which may load the library's device code) with
  *    that device current; make that first call before any stream capture
- *    starts.  Later calls reuse the address.
+ *    starts.  Later calls reuse the address, which belongs to the device's
+ *    current context: after cudaDeviceReset (or any other teardown of that
+ *    context) the stored address is stale and later calls in the same
+ *    process are not valid.
  *  - All calls on one device share the array and it keeps the contents of
  *    the last call; each call re-initialises what it reads.  Two calls that
  *    can overlap on the GPU (different streams without ordering between
  *    them, or different host threads) race on the scratch and give wrong
  *    results: order them on one stream or serialise them.
+ *  - The device-side error word of the solve (Q <= 0 or not finite) lives
+ *    in the private scratch, so this call cannot report it: after the stream
+ *    has completed, check that q_dev holds positive, finite Q_P and Q_S.
  *  - Asynchronous on cuda_stream (NULL: the legacy default stream).  Returns
- *    EPD_LB_EINVAL for bad parameters or NULL pointers, EPD_LB_ECUDA if a
- *    CUDA call fails.
+ *    EPD_LB_EINVAL for bad parameters or NULL pointers, EPD_LB_ETOOLARGE if
+ *    the scratch needed exceeds EPD_PROP_SOLVE_NOALLOC_MAX_BYTES, EPD_LB_ECUDA
+ *    if a CUDA call fails.
  */
 #define EPD_PROP_SOLVE_NOALLOC_MAX_BYTES (16u << 20)
 int epd_prop_solve_noalloc(const epd_lb_params *p, const double *omega_dev, double *phi_dev, double *q_dev,

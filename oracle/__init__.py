@@ -35,7 +35,7 @@ def build(force: bool = False) -> str:
 
 class _Params(ctypes.Structure):
     _fields_ = [
-        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("ns", ctypes.c_int32), ("pad0", ctypes.c_int32),
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("ns", ctypes.c_int32), ("junction_rule", ctypes.c_int32),
         ("dx", ctypes.c_double), ("dt", ctypes.c_double), ("rg", ctypes.c_double),
         ("n_seg", ctypes.c_double), ("f_a", ctypes.c_double), ("phi_p", ctypes.c_double),
         ("chi_ab", ctypes.c_double), ("chi_as", ctypes.c_double), ("chi_bs", ctypes.c_double),
@@ -74,6 +74,10 @@ class Params:
     f0: float = 0.0
     noise_amp: float = 1e-3
     seed: int = 1
+    # field at the A/B junction node: 0 literal (node j carries omega_A iff
+    # j < N_A), 1 segment-symmetric (both half-steps of an interval use its
+    # block's field)
+    junction_rule: int = 0
 
     def c(self) -> _Params:
         p = _Params()

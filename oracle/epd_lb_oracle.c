@@ -33,7 +33,7 @@ typedef double complex cplx;
 typedef struct {
     int32_t nx, ny;       /* grid sites per axis (even)                      */
     int32_t ns;           /* contour steps N_s                               */
-    int32_t pad0;
+    int32_t junction_rule; /* field at the A/B junction node: 0 literal, 1 segment-symmetric */
     double dx, dt, rg;    /* grid spacing, time step, gyration radius R_G    */
     double n_seg;         /* segments per chain N                            */
     double f_a;           /* A-fraction q_A of the diblock                   */
@@ -188,21 +188,46 @@ void or_spectral_op(const or_params *p, const double *f, double *out, int axis, 
 /* Single-chain statistics: Sec. 2, Eqs. (6)-(11).                          */
 /* ------------------------------------------------------------------------ */
 
-/* READING: N_A = round(q_A N_s) contour intervals belong to the A block;
- * contour node j (s_j = j/N_s) carries omega_A iff s_j < q_A, i.e. j < N_A,
- * and omega_B otherwise (the junction node takes omega_B, as the paper's
- * "otherwise" states). */
+/* READING: N_A = round(q_A N_s) contour intervals belong to the A block.
+ * The paper puts omega_A at s < q_A and omega_B otherwise; at the junction
+ * node s_{N_A} = q_A the split step of Eq. (8) can read this two ways:
+ *  - junction_rule 0 (literal, the default): contour node j carries
+ *    omega_A iff j < N_A, so the junction node takes omega_B; the step over
+ *    interval [s_j, s_{j+1}] uses the fields of nodes j and j + 1;
+ *  - junction_rule 1 (segment-symmetric): interval j belongs to block A iff
+ *    j < N_A and both of its half-steps use that block's field, so the
+ *    chain is treated the same way from either end. */
 int or_n_a(const or_params *p)
 {
     return (int)lround(p->f_a * (double)p->ns);
 }
 
+/* Fields of the two half-steps of every contour interval j = 0..ns-1 of one
+ * chain (chain 0: g from the A end; chain 1: g' from the B end, which sees
+ * the field of position 1 - s): first[j] acts at s_j, second[j] at s_{j+1}. */
+static void half_step_fields(const or_params *p, const double *w_a, const double *w_b, int chain,
+                             const double **first, const double **second)
+{
+    int ns = p->ns, na = or_n_a(p);
+    for (int j = 0; j < ns; j++) {
+        if (p->junction_rule == 1) {
+            int jg = chain == 0 ? j : ns - 1 - j; /* the interval of g it covers */
+            first[j] = second[j] = (jg < na) ? w_a : w_b;
+        } else {
+            int j0 = chain == 0 ? j : ns - j, j1 = chain == 0 ? j + 1 : ns - j - 1; /* nodes of g */
+            first[j] = (j0 < na) ? w_a : w_b;
+            second[j] = (j1 < na) ? w_a : w_b;
+        }
+    }
+}
+
 /* Propagate one chain.  Eq. (8): the contour step from s to s + ds is
  *   g(s+ds) = exp(-N w(s+ds) ds / 2) exp(R_G^2 Laplacian ds) exp(-N w(s) ds / 2) g(s),
  * with the Laplacian factor applied in Fourier space as exp(-R_G^2 |k|^2 ds).
- * field_of_node[j] points to the field acting at contour node j.
- * hist receives g at nodes 0..ns; g at node 0 is g0 (1 for Eqs. (6)-(7)). */
-static void propagate_chain(const or_params *p, const double *const *field_of_node,
+ * first[j], second[j]: the fields of the two half-steps of interval j
+ * (half_step_fields).  hist receives g at nodes 0..ns; g at node 0 is g0
+ * (1 for Eqs. (6)-(7)). */
+static void propagate_chain(const or_params *p, const double *const *first, const double *const *second,
                             const double *g0, double *hist)
 {
     int nx = p->nx, ny = p->ny, ns = p->ns;
@@ -220,7 +245,7 @@ static void propagate_chain(const or_params *p, const double *const *field_of_no
     for (int j = 0; j < ns; j++) {
         const double *g = hist + (size_t)j * n;
         double *gnext = hist + (size_t)(j + 1) * n;
-        const double *wj = field_of_node[j], *wj1 = field_of_node[j + 1];
+        const double *wj = first[j], *wj1 = second[j];
         for (size_t i = 0; i < n; i++) work[i] = exp(-nseg * wj[i] * ds / 2.0) * g[i];
         or_fft2d(work, ny, nx, -1);
         for (size_t i = 0; i < n; i++) work[i] *= kfac[i];
@@ -240,22 +265,19 @@ static void propagate_chain(const or_params *p, const double *const *field_of_no
 void or_propagate(const or_params *p, const double *w_a, const double *w_b,
                   const double *g0, double *g_hist, double *gp_hist)
 {
-    int ns = p->ns, na = or_n_a(p);
+    int ns = p->ns;
     size_t n = (size_t)p->nx * p->ny;
-    const double **fw = (const double **)malloc(sizeof(double *) * (size_t)(ns + 1));
-    const double **bw = (const double **)malloc(sizeof(double *) * (size_t)(ns + 1));
-    for (int j = 0; j <= ns; j++) {
-        fw[j] = (j < na) ? w_a : w_b;
-        int jf = ns - j;
-        bw[j] = (jf < na) ? w_a : w_b;
-    }
+    const double **f1 = (const double **)malloc(sizeof(double *) * (size_t)ns);
+    const double **f2 = (const double **)malloc(sizeof(double *) * (size_t)ns);
     double *ones = (double *)malloc(sizeof(double) * n);
     for (size_t i = 0; i < n; i++) ones[i] = 1.0;
-    propagate_chain(p, fw, g0 ? g0 : ones, g_hist);
-    propagate_chain(p, bw, ones, gp_hist);
+    half_step_fields(p, w_a, w_b, 0, f1, f2);
+    propagate_chain(p, f1, f2, g0 ? g0 : ones, g_hist);
+    half_step_fields(p, w_a, w_b, 1, f1, f2);
+    propagate_chain(p, f1, f2, ones, gp_hist);
     free(ones);
-    free(fw);
-    free(bw);
+    free(f1);
+    free(f2);
 }
 
 /* READING (contour quadrature, not stated in the paper): the trapezoid rule on
@@ -331,7 +353,8 @@ void or_fft3d(cplx *a, int nz, int ny, int nx, int sign)
     free(col);
 }
 
-static void propagate_chain3d(const or_params *p, int nz, const double *const *field_of_node, double *hist)
+static void propagate_chain3d(const or_params *p, int nz, const double *const *first, const double *const *second,
+                              double *hist)
 {
     int nx = p->nx, ny = p->ny, ns = p->ns;
     size_t n = (size_t)nx * ny * nz;
@@ -348,7 +371,7 @@ static void propagate_chain3d(const or_params *p, int nz, const double *const *f
     for (int j = 0; j < ns; j++) {
         const double *g = hist + (size_t)j * n;
         double *gnext = hist + (size_t)(j + 1) * n;
-        const double *wj = field_of_node[j], *wj1 = field_of_node[j + 1];
+        const double *wj = first[j], *wj1 = second[j];
         for (size_t i = 0; i < n; i++) work[i] = exp(-p->n_seg * wj[i] * ds / 2.0) * g[i];
         or_fft3d(work, nz, ny, nx, -1);
         for (size_t i = 0; i < n; i++) work[i] *= kfac[i];
@@ -370,14 +393,12 @@ void or_solve3d(const or_params *p, int nz, const double *omega, double *phi, do
     const double *w_a = omega, *w_b = omega + n, *w_s = omega + 2 * n;
     double *g = (double *)malloc(sizeof(double) * n * (size_t)(ns + 1));
     double *gp = (double *)malloc(sizeof(double) * n * (size_t)(ns + 1));
-    const double **fw = (const double **)malloc(sizeof(double *) * (size_t)(ns + 1));
-    const double **bw = (const double **)malloc(sizeof(double *) * (size_t)(ns + 1));
-    for (int j = 0; j <= ns; j++) {
-        fw[j] = (j < na) ? w_a : w_b;
-        bw[j] = ((ns - j) < na) ? w_a : w_b;
-    }
-    propagate_chain3d(p, nz, fw, g);
-    propagate_chain3d(p, nz, bw, gp);
+    const double **f1 = (const double **)malloc(sizeof(double *) * (size_t)ns);
+    const double **f2 = (const double **)malloc(sizeof(double *) * (size_t)ns);
+    half_step_fields(p, w_a, w_b, 0, f1, f2);
+    propagate_chain3d(p, nz, f1, f2, g);
+    half_step_fields(p, w_a, w_b, 1, f1, f2);
+    propagate_chain3d(p, nz, f1, f2, gp);
     double q_p = 0.0;
     for (size_t i = 0; i < n; i++) q_p += g[(size_t)ns * n + i];
     q_p /= (double)n;
@@ -399,8 +420,8 @@ void or_solve3d(const or_params *p, int nz, const double *omega, double *phi, do
     q[1] = q_s;
     free(g);
     free(gp);
-    free(fw);
-    free(bw);
+    free(f1);
+    free(f2);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -52,6 +52,7 @@ class CParams(ctypes.Structure):
         ("d_s", ctypes.c_double), ("d_p", ctypes.c_double), ("inv_beta_v", ctypes.c_double),
         ("gamma_s", ctypes.c_double), ("gamma_b", ctypes.c_double), ("gamma_g", ctypes.c_double),
         ("f0", ctypes.c_double), ("noise_amp", ctypes.c_double), ("seed", ctypes.c_uint64),
+        ("junction_rule", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 
@@ -84,6 +85,7 @@ class RunParams:
     f0: float = 0.0
     noise_amp: float = 1e-3
     seed: int = 1
+    junction_rule: int = 0  # 0 literal, 1 segment-symmetric (see epd_lb_params)
 
     def c(self) -> CParams:
         p = CParams()

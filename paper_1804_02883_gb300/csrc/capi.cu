@@ -87,7 +87,7 @@ size_t carve_group(Group &G, char *base, size_t off)
     }
     // cluster solve (MIXED_FP32): stored states of both chains, and the
     // differential second solve's buffers
-    G.hc = G.hd = G.rho = G.c2p = nullptr;
+    G.hc = G.hd = G.rho = G.cdiff = nullptr;
     // (decided from the parameters, not from a pointer: the dry run that
     // sizes the workspace carves with null pointers)
     const bool cluster = G.prec == EPD_LB_MIXED_FP32 && G.g.pow2 && cluster_shape_exists(G.g.logx, G.g.logy);
@@ -96,7 +96,7 @@ size_t carve_group(Group &G, char *base, size_t off)
         G.hc = take(hs);
         G.hd = take(hs);
         G.rho = take(R * n * sizeof(float2));
-        G.c2p = take(R * n * sizeof(float2));
+        G.cdiff = take(R * 3 * n * sizeof(float));
     }
     // exact step: the inversion's fields and scalars
     G.cg_target = (double *)take(R * 3 * n * sizeof(double));
@@ -147,7 +147,7 @@ static Group run_view(const Group &G, int r)
         V.hc = (char *)V.hc + (size_t)r * hs;
         V.hd = (char *)V.hd + (size_t)r * hs;
         V.rho = (char *)V.rho + (size_t)r * n * sizeof(float2);
-        V.c2p = (char *)V.c2p + (size_t)r * n * sizeof(float2);
+        V.cdiff = (char *)V.cdiff + (size_t)r * 3 * n * sizeof(float);
         V.cg_wref += (size_t)r * 3 * n;
         V.cg_pref += (size_t)r * 3 * n;
     }
@@ -202,6 +202,7 @@ static void fill_geom(Group &G)
     g.nfy = radix_plan(p.ny, g.fy);
     g.ns = p.ns;
     g.na = (int)std::lround(p.f_a * (double)p.ns);
+    g.jr = p.junction_rule;
     g.half_lo = p.ns / 2;
     g.half_hi = (p.ns + 1) / 2;
     g.nruns = (int)G.run_ids.size();
@@ -368,6 +369,8 @@ static std::string validate(const epd_lb_params &p)
     if (!(std::fabs(p.gamma_s) < 1) || !(std::fabs(p.gamma_b) < 1) || !(std::fabs(p.gamma_g) < 1))
         return "gamma_s, gamma_b and gamma_g must be in (-1, 1)";
     if (!std::isfinite(p.f0) || !std::isfinite(p.noise_amp) || !std::isfinite(p.inv_beta_v)) return "f0, noise_amp, inv_beta_v must be finite";
+    if (p.junction_rule != 0 && p.junction_rule != 1) return "junction_rule must be 0 (literal) or 1 (segment-symmetric)";
+    if (p.reserved != 0) return "reserved must be 0";
     return "";
 }
 
@@ -385,7 +388,8 @@ static bool same_group(const epd_lb_params &a, const epd_lb_params &b)
     return a.nx == b.nx && a.ny == b.ny && a.ns == b.ns && a.precision == b.precision && a.dx == b.dx && a.dt == b.dt &&
            a.rg == b.rg && a.n_seg == b.n_seg && a.f_a == b.f_a && a.phi_p == b.phi_p && a.chi_ab == b.chi_ab &&
            a.chi_as == b.chi_as && a.chi_bs == b.chi_bs && a.kappa_h == b.kappa_h && a.d_s == b.d_s && a.d_p == b.d_p &&
-           a.inv_beta_v == b.inv_beta_v && a.gamma_s == b.gamma_s && a.gamma_b == b.gamma_b && a.gamma_g == b.gamma_g;
+           a.inv_beta_v == b.inv_beta_v && a.gamma_s == b.gamma_s && a.gamma_b == b.gamma_b && a.gamma_g == b.gamma_g &&
+           a.junction_rule == b.junction_rule;
 }
 
 static void form_groups(const epd_lb_params *p, int nruns, std::vector<Group> &groups, std::vector<std::pair<int, int>> &where)

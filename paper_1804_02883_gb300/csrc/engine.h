@@ -22,6 +22,7 @@ struct GroupGeom {
     int nfx, nfy;            // radix plans (4, 2, 3, 5) of each axis for the mixed-radix transforms
     int fx[kMaxFactors], fy[kMaxFactors];
     int ns, na;          // contour steps, A-block intervals round(f_a ns)
+    int jr;              // junction rule: 0 literal, 1 segment-symmetric
     int half_lo, half_hi;  // nodes 0..half_lo are stored; nodes >= half_hi accumulate
     int nruns;
     long long n;         // sites per run
@@ -31,6 +32,23 @@ struct GroupGeom {
     double fstar;        // f* in lattice units
     double vscale;       // lattice velocity -> R_G/tau
 };
+
+// Block (0: A, 1: B) whose field acts in a half-step of the split step of
+// Eq. (8) at contour node m of a chain (0: g from the A end; 1: g', which
+// sees the field of position 1 - s).  arriving: the half-step that ends the
+// interval into node m; otherwise the one that starts the interval out of
+// it.  jr = 0 (literal): both take the field of node m, A iff the node of g
+// it corresponds to is below N_A (the junction node takes B).  jr = 1
+// (segment-symmetric): each takes the block of its own interval (A iff that
+// interval of g is below N_A); at the two ends of the chain, which have one
+// interval only, both half-steps take that interval's block.
+__host__ __device__ inline int half_step_block(int jr, int chain, int m, int ns, int na, bool arriving)
+{
+    if (jr == 0) return (chain == 0 ? m : ns - m) >= na;
+    if (arriving ? m == 0 : m == ns) arriving = !arriving;
+    const int j = arriving ? m - 1 : m;  // the interval of this chain
+    return (chain == 0 ? j : ns - 1 - j) >= na;
+}
 
 // Launch shapes of the transform passes (chosen at init, see tune_shapes).
 struct Shapes {
@@ -58,7 +76,7 @@ struct Group {
     void *hc = nullptr;       // plain / reference solve
     void *hd = nullptr;       // differential second solve
     void *rho = nullptr;      // (rho_A, rho_B) = expm1(-N d omega ds / 2), [run][n] float2
-    void *c2p = nullptr;      // rho (2 + rho) per block, packed rows [run][2][ny/2][nx] float2
+    void *cdiff = nullptr;    // (1 + rho_d)(1 + rho_a) - 1 for (A,A), (B,B), (A,B), packed rows [run][3][ny/2][nx] float2
     bool diff = false;        // the step uses the reference + differential solve pair
     bool phi_stale = false;   // omega was replaced since phi was last computed
     bool hist_full = false;   // streaming radix-8 solve: hist holds all N_s + 1 nodes

@@ -52,8 +52,16 @@ __device__ __forceinline__ double weight_b(int j, int na, int ns, double ds)
 }
 
 // Node j of g carries w_A iff j < N_A; node j of g' carries the field of node ns - j.
-template <typename T> __device__ __forceinline__ T fac_g(V2<T> e, int j, int na) { return j < na ? e.x : e.y; }
-template <typename T> __device__ __forceinline__ T fac_gp(V2<T> e, int j, int ns, int na) { return (ns - j) < na ? e.x : e.y; }
+// Boltzmann factor (E_A, E_B) of the half-step at node j of chain g (fac_g)
+// or g' (fac_gp), arriving or departing (half_step_block)
+template <typename T> __device__ __forceinline__ T fac_g(V2<T> e, const GroupGeom &g, int j, bool arriving)
+{
+    return half_step_block(g.jr, 0, j, g.ns, g.na, arriving) ? e.y : e.x;
+}
+template <typename T> __device__ __forceinline__ T fac_gp(V2<T> e, const GroupGeom &g, int j, bool arriving)
+{
+    return half_step_block(g.jr, 1, j, g.ns, g.na, arriving) ? e.y : e.x;
+}
 
 template <typename T> __device__ __forceinline__ T exp_t(T v);
 template <> __device__ __forceinline__ float exp_t<float>(float v) { return expf(v); }
@@ -93,7 +101,7 @@ __global__ void __launch_bounds__(kThreads) prop_start(PropK<T> k)
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const V2<T> e = k.efac[(size_t)run * n + i];
         k.hist[(size_t)run * (k.g.half_lo + 1) * n + i] = mk<T>((T)1, (T)1);
-        k.chain[(size_t)run * n + i] = mk<T>(fac_g<T>(e, 0, k.g.na), fac_gp<T>(e, 0, k.g.ns, k.g.na));
+        k.chain[(size_t)run * n + i] = mk<T>(fac_g<T>(e, k.g, 0, false), fac_gp<T>(e, k.g, 0, false));
     }
 }
 
@@ -164,7 +172,9 @@ __global__ void __launch_bounds__(kThreads) prop_row(PropK<T> k, int m)
     double qsum = 0.0;
     for (int i = threadIdx.x; i < tile; i += blockDim.x) {
         const V2<T> e = efac[i];
-        const T eg = fac_g<T>(e, m, na), egp = fac_gp<T>(e, m, ns, na);
+        // z = (g_m, g'_m): the arriving half-step's factor; the chain goes on
+        // with the departing one
+        const T eg = fac_g<T>(e, k.g, m, true), egp = fac_gp<T>(e, k.g, m, true);
         const V2<T> h = r[i];
         const V2<T> z = mk<T>(eg * h.x, egp * h.y);
         if (m <= hlo) hist[(size_t)m * n + i] = z;
@@ -182,7 +192,7 @@ __global__ void __launch_bounds__(kThreads) prop_row(PropK<T> k, int m)
             else { ia[i] += va; ib[i] += vb; }
         }
         if (m == ns) qsum += (double)z.x;
-        else data[i] = mk<T>(eg * z.x, egp * z.y);
+        else data[i] = mk<T>(fac_g<T>(e, k.g, m, false) * z.x, fac_gp<T>(e, k.g, m, false) * z.y);
     }
     if (m == ns) {
         const double s = block_sum(qsum, red);
@@ -226,7 +236,7 @@ __global__ void __launch_bounds__(kThreads) prop_finalize(GroupGeom g, int nrow_
 // rounding of FP32 relative to the change itself.  The solvent change de goes
 // to the S slot of phi, its block sums to the S partials.
 __global__ void __launch_bounds__(kThreads) prop_prep_delta(GroupGeom g, const double *omega, const double *omega_t,
-                                                            float2 *rho, float *c2p, double *phi_out, double *part)
+                                                            float2 *rho, float *cdiff, double *phi_out, double *part)
 {
     __shared__ double red[32];
     const int run = blockIdx.y;
@@ -240,14 +250,16 @@ __global__ void __launch_bounds__(kThreads) prop_prep_delta(GroupGeom g, const d
         const float da = (float)(wa[i] - ta[i]), db = (float)(wb[i] - tb[i]);
         const float qa = expm1f(c * da), qb = expm1f(c * db);
         rho[(size_t)run * n + i] = make_float2(qa, qb);
-        if (c2p) {
-            // rho (2 + rho) per block in the packed-row layout of the cluster
-            // solve: site (y, x) -> packed row y / 2, component y & 1
-            // (the cluster solve's grids are powers of two: shift and mask)
+        if (cdiff) {
+            // (1 + rho_d)(1 + rho_a) - 1 for the block pairs (A, A), (B, B),
+            // (A, B) of a node's departing and arriving half-steps, in the
+            // packed-row layout of the cluster solve (site (y, x) -> packed
+            // row y / 2, component y & 1; power-of-two grids: shift and mask)
             const long long y = i >> g.logx, x = i & (g.nx - 1), hn = n / 2;
             const size_t o = (size_t)((y >> 1) * g.nx + x) * 2 + (y & 1);
-            c2p[((size_t)run * 2 + 0) * hn * 2 + o] = qa * (2.f + qa);
-            c2p[((size_t)run * 2 + 1) * hn * 2 + o] = qb * (2.f + qb);
+            cdiff[((size_t)run * 3 + 0) * hn * 2 + o] = qa * (2.f + qa);
+            cdiff[((size_t)run * 3 + 1) * hn * 2 + o] = qb * (2.f + qb);
+            cdiff[((size_t)run * 3 + 2) * hn * 2 + o] = qa + qb + qa * qb;
         }
         // e~_S exactly as the first solve formed it
         const float es = expf(-(float)ts[i]);
@@ -288,7 +300,7 @@ __global__ void __launch_bounds__(kThreads) prop_start8(Stream8K k)
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const float2 e = k.efac[(size_t)run * n + i];
         k.hist[(size_t)run * (k.g.ns + 1) * n + i] = make_float2(1.f, 1.f);
-        k.chain[(size_t)run * n + i] = make_float2(fac_g<float>(e, 0, k.g.na), fac_gp<float>(e, 0, k.g.ns, k.g.na));
+        k.chain[(size_t)run * n + i] = make_float2(fac_g<float>(e, k.g, 0, false), fac_gp<float>(e, k.g, 0, false));
     }
 }
 
@@ -334,7 +346,7 @@ __global__ void __launch_bounds__(RowTile<LOGX>::T) prop_row8(Stream8K k, int m)
     float2 *buf = reinterpret_cast<float2 *>(smem_raw);
     const int run = blockIdx.y, tid = threadIdx.x;
     const long long n = k.g.n, base = (long long)blockIdx.x * P;
-    const int ns = k.g.ns, na = k.g.na;
+    const int ns = k.g.ns;
     float2 *data = k.chain + (size_t)run * n + base;
 #pragma unroll
     for (int u = 0; u < P / T; ++u) {
@@ -356,11 +368,11 @@ __global__ void __launch_bounds__(RowTile<LOGX>::T) prop_row8(Stream8K k, int m)
         for (int r = 0; r < RR; ++r) {
             const int i = bb[j] * NX + tt[j] + r * PER_L;
             const float2 e = efac[i];
-            const float eg = fac_g<float>(e, m, na), egp = fac_gp<float>(e, m, ns, na);
+            const float eg = fac_g<float>(e, k.g, m, true), egp = fac_gp<float>(e, k.g, m, true);
             const float2 z = make_float2(eg * h[j][r].x, egp * h[j][r].y);
             hist[i] = z;
             if (m == ns) qsum += z.x;
-            else data[i] = make_float2(eg * z.x, egp * z.y);
+            else data[i] = make_float2(fac_g<float>(e, k.g, m, false) * z.x, fac_gp<float>(e, k.g, m, false) * z.y);
         }
     if (m == ns) {
         const double s = block_sum((double)qsum, red);
@@ -676,7 +688,7 @@ cudaError_t launch_solve_delta_at(Group &G, const double *omega, const double *o
     const GroupGeom &g = G.g;
     const int pg = grid_for(g.n);
     prop_prep_delta<<<dim3(pg, g.nruns), kThreads, 0, s>>>(g, omega, omega_ref, reinterpret_cast<float2 *>(G.rho),
-                                                          reinterpret_cast<float *>(G.c2p), phi, G.part);
+                                                          reinterpret_cast<float *>(G.cdiff), phi, G.part);
     return launch_cluster_solve(G, s, true, pg, phi, q, probe, phi_ref, q_ref);
 }
 

@@ -71,7 +71,7 @@ struct PropCK {
     const float2 *href;   // reference states a~_m (DIFF)
     const float2 *efac;   // (E_A, E_B) [run][n]
     const float2 *rho;    // (rho_A, rho_B) [run][n] (DIFF)
-    const float2 *c2p;    // rho (2 + rho) of blocks A, B in the packed-row layout [run][2][NY/2][NX] (DIFF)
+    const float2 *cdiff;  // (1 + rho_d)(1 + rho_a) - 1 for (A,A), (B,B), (A,B), packed rows [run][3][NY/2][NX] (DIFF)
     int *err;             // bit 2: an exchange wait gave up
     const float2 *twx, *twy;  // radix-8 pass tables (fft8.cuh layout)
     const float *kx, *ky;     // exp(-R_G^2 k^2 ds) / N
@@ -95,7 +95,8 @@ struct ClusterGeom {
     static constexpr int MRY = (best_mr(LOGY) == 4 && P % (16 * T) == 0) ? 4 : 3;
     static constexpr int TABX = tabs_total(LOGX, MRX), TABY = tabs_total(LOGY, MRY);
     // row buffer, column buffer, pass tables, Fourier factors, the node
-    // factors of the epilogue sites in either packing (P points each)
+    // factors of the epilogue sites in either packing (P points each; the
+    // differential solve keeps the coefficient of a~ beside each)
     static constexpr size_t SMEM =
         (size_t)(R2 * PITCH + P + TABX + TABY + 2 * P) * sizeof(float2) + (NX + NY) * sizeof(float);
     static constexpr size_t SMEM_DIFF = SMEM;
@@ -204,8 +205,9 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
     float2 *taby = tabx + G::TABX;
     float *kx = reinterpret_cast<float *>(taby + G::TABY);
     float *ky = kx + NX;
-    // E^2 (or E'^2) of the two real sites of each epilogue point, thread-major
-    // ([point of the thread][thread]: conflict-free), rows then columns
+    // node factors of the two real sites of each epilogue point, thread-major
+    // ([point of the thread][thread]: conflict-free), rows then columns:
+    // E_d E_a (plain) or E'_d E'_a (DIFF)
     float2 *fac_r = reinterpret_cast<float2 *>(ky + NY), *fac_c = fac_r + P;
     cg::cluster_group cl = cg::this_cluster();
     const int crank = (int)cl.block_rank();
@@ -230,16 +232,19 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
     // [NY/2][NX]; rho (2 + rho) of blocks A, B in the same layout
     float2 *hout = k.hout + (size_t)(run * 2 + chain) * (ns + 1) * HN;
     const float2 *href = DIFF ? k.href + (size_t)(run * 2 + chain) * (ns + 1) * HN : nullptr;
-    const float2 *c2p = DIFF ? k.c2p + (size_t)run * 2 * HN : nullptr;
+    const float2 *cdiff = DIFF ? k.cdiff + (size_t)run * 3 * HN : nullptr;
 
-    // node factor of this chain at contour node j: g carries w_A iff j < N_A,
-    // g' sees the field of node N_s - j
-    auto blk_b = [&](int j) { return (chain == 0 ? j : ns - j) >= na; };
+    // blocks of the two half-step factors at contour node j of this chain
+    // (half_step_block: the literal junction rule gives both the block of
+    // node j, g carrying w_A iff j < N_A and g' the field of node N_s - j).
+    // The stored state is a_j = E_dep(j) g_j, so a_j = E_dep(j) E_arr(j) T(a_{j-1}).
+    auto dep_b = [&](int j) { return half_step_block(k.g.jr, chain, j, ns, na, false); };
+    auto arr_b = [&](int j) { return half_step_block(k.g.jr, chain, j, ns, na, true); };
     // a_0 = E_0 (d a_0 = rho_0 E_0) at the real site of packed row kk,
     // column x, rows 2kk (re) and 2kk + 1 (im)
     auto node0 = [&](int kk, int x) {
         const int site = 2 * kk * NX + x;
-        const bool bk = blk_b(0);
+        const bool bk = dep_b(0);
         const float2 f0 = efac[site], f1 = efac[site + NX];
         float2 a0 = bk ? f2(f0.y, f1.y) : f2(f0.x, f1.x);
         if (DIFF) {
@@ -306,22 +311,32 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
     // B) changes; each thread reads only what it wrote
     int cur_r = -1, cur_c = -1;
     int failed = 0;
-    auto factor = [&](int site, int bm) {
-        const float2 ef = efac[site];
-        const float e = bm ? ef.y : ef.x;
-        if (!DIFF) return e * e;
-        const float2 rf = rho[site];
-        const float q = bm ? rf.y : rf.x, ep = e * (1.f + q);
-        return ep * ep;
+    // the factors of packed-row point (kk, x) for blocks d (departing) and a
+    // (arriving): real sites 2kk (re) and 2kk + 1 (im) of column x
+    auto factors = [&](int kk, int x, bool bd, bool ba) {
+        const int s0 = 2 * kk * NX + x;
+        const float2 e0 = efac[s0], e1 = efac[s0 + NX];
+        const float f0 = (bd ? e0.y : e0.x) * (ba ? e0.y : e0.x), f1 = (bd ? e1.y : e1.x) * (ba ? e1.y : e1.x);
+        if constexpr (!DIFF) {
+            return f2(f0, f1);
+        } else {
+            const float2 r0 = rho[s0], r1 = rho[s0 + NX];
+            return f2(f0 * ((1.f + (bd ? r0.y : r0.x)) * (1.f + (ba ? r0.y : r0.x))),
+                      f1 * ((1.f + (bd ? r1.y : r1.x)) * (1.f + (ba ? r1.y : r1.x))));
+        }
     };
-    // a_m = E_m^2 U (plain) or d a_m = E'^2 U + rho (2 + rho) a~_m (DIFF) at
-    // packed-row point (kk, x), U = T(a_{m-1}) there
-    auto finish = [&](float2 u, float2 f, int m, int bm, int kk, int x) {
-        if (!DIFF) return f2(f.x * u.x, f.y * u.y);
-        const size_t e = (size_t)kk * NX + x;
-        const float2 ar = href[(size_t)m * HN + e];  // a~_m
-        const float2 cq = c2p[(size_t)bm * HN + e];  // rho (2 + rho)
-        return f2(f.x * u.x + cq.x * ar.x, f.y * u.y + cq.y * ar.y);
+    // a_m = E_d E_a U (plain) or d a_m = E'_d E'_a U + c a~_m (DIFF) at
+    // packed-row point (kk, x), U = T(a_{m-1}) there, c = (1 + rho_d)(1 +
+    // rho_a) - 1 from plane cp of cdiff (0: A A, 1: B B, 2: A B)
+    auto finish = [&](float2 u, float2 f, int m, int cp, int kk, int x) {
+        if constexpr (!DIFF) {
+            return f2(f.x * u.x, f.y * u.y);
+        } else {
+            const size_t e = (size_t)kk * NX + x;
+            const float2 ar = href[(size_t)m * HN + e];  // a~_m
+            const float2 c = cdiff[(size_t)cp * HN + e];
+            return f2(f.x * u.x + c.x * ar.x, f.y * u.y + c.y * ar.y);
+        }
     };
 
     // The contour loop runs over half steps: each applies the transform pair
@@ -337,13 +352,13 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
         const bool second = hs & 1, cols = starts_in_columns(m) != second;
         const unsigned par = (unsigned)(i >> 1) & 1u;  // uses of this step's barrier so far in this launch
         const bool rearm = i + 2 < nsteps;
-        const int bm = blk_b(m) ? 1 : 0;
+        const int bd = dep_b(m), ba = arr_b(m), key = 2 * bd + ba, cp = bd == ba ? bd : 2;
         if (DIFF && !second) {
-            // a~_m and rho (2 + rho) of this step's epilogue sites into L1
-            // ahead of use (the packing the step ends in)
+            // a~_m and c of this step's epilogue sites into L1 ahead of use
+            // (the packing the step ends in)
             auto pf = [&](size_t e) {
                 asm volatile("prefetch.global.L1 [%0];" ::"l"(href + (size_t)m * HN + e));
-                asm volatile("prefetch.global.L1 [%0];" ::"l"(c2p + (size_t)bm * HN + e));
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(cdiff + (size_t)cp * HN + e));
             };
             if (cols) {
 #pragma unroll
@@ -400,15 +415,14 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
             } else {
                 // node factors in the packed-row form (x = 2J + (y & 1) of
                 // packed row y / 2), the result back in the column buffer
-                if (bm != cur_c) {
-                    cur_c = bm;
+                if (key != cur_c) {
+                    cur_c = key;
 #pragma unroll
                     for (int j = 0; j < NB_C; ++j)
 #pragma unroll
                         for (int r = 0; r < RC; ++r) {
                             const int kk = (ct[j] + r * PER_C) >> 1, xx = 2 * (jcol0 + cc[j]) + (ct[j] & 1);
-                            fac_c[(j * RC + r) * T + tid] =
-                                f2(factor(2 * kk * NX + xx, bm), factor(2 * kk * NX + xx + NX, bm));
+                            fac_c[(j * RC + r) * T + tid] = factors(kk, xx, bd, ba);
                         }
                 }
 #pragma unroll
@@ -416,7 +430,7 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
 #pragma unroll
                     for (int r = 0; r < RC; ++r) {
                         const int kk = (ct[j] + r * PER_C) >> 1, xx = 2 * (jcol0 + cc[j]) + (ct[j] & 1);
-                        x[j][r] = finish(pair_transpose<16>(x[j][r], ct[j] & 1), fac_c[(j * RC + r) * T + tid], m, bm, kk, xx);
+                        x[j][r] = finish(pair_transpose<16>(x[j][r], ct[j] & 1), fac_c[(j * RC + r) * T + tid], m, cp, kk, xx);
                     }
                 __syncthreads();  // every thread has read its columns: they are rewritten below
 #pragma unroll
@@ -455,22 +469,20 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
                 if (tid == 0 && rearm) mbar_expect(bar_col, XBYTES);
             } else {
                 // node factors; the result stays in the row buffer
-                if (bm != cur_r) {
-                    cur_r = bm;
+                if (key != cur_r) {
+                    cur_r = key;
 #pragma unroll
                     for (int j = 0; j < NB_L; ++j)
 #pragma unroll
-                        for (int r = 0; r < RR; ++r) {
-                            const int site = 2 * (krow0 + bb[j]) * NX + tt[j] + r * PER_L;
-                            fac_r[(j * RR + r) * T + tid] = f2(factor(site, bm), factor(site + NX, bm));
-                        }
+                        for (int r = 0; r < RR; ++r)
+                            fac_r[(j * RR + r) * T + tid] = factors(krow0 + bb[j], tt[j] + r * PER_L, bd, ba);
                 }
                 // every value first: the stores come after
 #pragma unroll
                 for (int j = 0; j < NB_L; ++j)
 #pragma unroll
                     for (int r = 0; r < RR; ++r)
-                        h[j][r] = finish(h[j][r], fac_r[(j * RR + r) * T + tid], m, bm, krow0 + bb[j], tt[j] + r * PER_L);
+                        h[j][r] = finish(h[j][r], fac_r[(j * RR + r) * T + tid], m, cp, krow0 + bb[j], tt[j] + r * PER_L);
 #pragma unroll
                 for (int j = 0; j < NB_L; ++j)
 #pragma unroll
@@ -557,7 +569,7 @@ __global__ void __launch_bounds__(kThreads) prop_qsum(ContourK k)
     const int nx = k.g.nx, ns = k.g.ns, na = k.g.na;
     const long long n = k.g.n;
     const int npk = nx * k.g.ny / 2;
-    const bool bm = ns >= na;  // node N_s of g carries w_B unless N_A = N_s
+    const bool bm = half_step_block(k.g.jr, 0, ns, ns, na, false);  // a_{N_s} = E_bm g_{N_s}
     const size_t cs = (size_t)(ns + 1) * k.hn;
     const float2 *a_ns = k.hc + (size_t)run * 2 * cs + (size_t)ns * k.hn;
     const float2 *d_ns = DIFF ? k.hd + (size_t)run * 2 * cs + (size_t)ns * k.hn : nullptr;
@@ -688,22 +700,27 @@ __global__ void __launch_bounds__(kThreads) prop_contour(ContourK k)
             const float2 *b = stg + (size_t)((st * U + u) * NW) * kThreads + tid;
             float wa, wb;
             node_weights(m, na, ns, wa, wb);
-            // g at node m and g' at node N_s - m see the same field (block B from N_A on)
-            const bool bk = m >= na;
+            // the stored states are a = E_dep g: the departing blocks of g at
+            // node m and of g' at node N_s - m (the same, B from N_A on, under
+            // the literal junction rule)
+            const bool bk = half_step_block(k.g.jr, 0, m, ns, na, false);
+            const bool bp = half_step_block(k.g.jr, 1, ns - m, ns, na, false);
+            // (selects: a run-time index would move these small arrays to local memory)
+            auto pick = [](const float (&v)[2][2], bool b, int c) { return b ? v[1][c] : v[0][c]; };
             const float2 a = b[0], bb = b[kThreads];
             float t0, t1;
             if (!DIFF) {
-                t0 = a.x * bb.x * (bk ? r2[1][0] : r2[0][0]);
-                t1 = a.y * bb.y * (bk ? r2[1][1] : r2[0][1]);
+                t0 = a.x * bb.x * (bk == bp ? pick(r2, bk, 0) : ri[0][0] * ri[1][0]);
+                t1 = a.y * bb.y * (bk == bp ? pick(r2, bk, 1) : ri[0][1] * ri[1][1]);
             } else {
                 const float2 da = b[2 * kThreads], db = b[3 * kThreads];
-                const float ri0 = bk ? ri[1][0] : ri[0][0], ri1 = bk ? ri[1][1] : ri[0][1];
-                const float q0 = bk ? dd[1][0] : dd[0][0], q1 = bk ? dd[1][1] : dd[0][1];
-                const float rs0 = bk ? rs[1][0] : rs[0][0], rs1 = bk ? rs[1][1] : rs[0][1];
                 // g~ = a~ / E and dg = (d a - rho a~) / E' of both chains
-                const float ga0 = a.x * ri0, ga1 = a.y * ri1, gb0 = bb.x * ri0, gb1 = bb.y * ri1;
-                const float dga0 = (da.x - q0 * a.x) * rs0, dga1 = (da.y - q1 * a.y) * rs1;
-                const float dgb0 = (db.x - q0 * bb.x) * rs0, dgb1 = (db.y - q1 * bb.y) * rs1;
+                const float ga0 = a.x * pick(ri, bk, 0), ga1 = a.y * pick(ri, bk, 1);
+                const float gb0 = bb.x * pick(ri, bp, 0), gb1 = bb.y * pick(ri, bp, 1);
+                const float dga0 = (da.x - pick(dd, bk, 0) * a.x) * pick(rs, bk, 0);
+                const float dga1 = (da.y - pick(dd, bk, 1) * a.y) * pick(rs, bk, 1);
+                const float dgb0 = (db.x - pick(dd, bp, 0) * bb.x) * pick(rs, bp, 0);
+                const float dgb1 = (db.y - pick(dd, bp, 1) * bb.y) * pick(rs, bp, 1);
                 t0 = ga0 * dgb0 + dga0 * gb0 + dga0 * dgb0;
                 t1 = ga1 * dgb1 + dga1 * gb1 + dga1 * dgb1;
             }
@@ -893,7 +910,7 @@ cudaError_t launch_cluster_solve(Group &G, cudaStream_t s, bool diff, int nprep_
     k.href = reinterpret_cast<const float2 *>(G.hc);
     k.efac = reinterpret_cast<const float2 *>(G.efac);
     k.rho = reinterpret_cast<const float2 *>(G.rho);
-    k.c2p = reinterpret_cast<const float2 *>(G.c2p);
+    k.cdiff = reinterpret_cast<const float2 *>(G.cdiff);
     k.err = G.err;
     k.twx = sh->mrx == 4 ? G.tab16x : G.tab8x;
     k.twy = sh->mry == 4 ? G.tab16y : G.tab8y;

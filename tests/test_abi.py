@@ -46,7 +46,8 @@ def test_mixed_radix_grids_accepted():
 
 
 @pytest.mark.parametrize("bad", [dict(nx=14), dict(nx=75), dict(ny=4), dict(ns=7, precision=1), dict(ns=0), dict(precision=2),
-                                 dict(phi_p=1.0), dict(gamma_s=1.0), dict(dx=0.0), dict(nx=4096), dict(ny=2250)])
+                                 dict(phi_p=1.0), dict(gamma_s=1.0), dict(dx=0.0), dict(nx=4096), dict(ny=2250),
+                                 dict(junction_rule=2), dict(junction_rule=-1)])
 def test_invalid_parameters_rejected(bad):
     p = W.with_(W.plain_small(), **bad)
     with pytest.raises(P.EpdLbError) as ei:
@@ -121,9 +122,10 @@ def test_runs_group_by_everything_but_f0_seed_and_noise():
     head = ws([a]) + ws([b]) - ws([a, b])
     assert head > 0 and head % 256 == 0
     assert ws([a]) + ws([c]) - ws([a, c]) == head
-    for field in ("chi_bs", "kappa_h", "d_p", "inv_beta_v", "gamma_s", "dt", "f_a", "precision"):
+    for field in ("chi_bs", "kappa_h", "d_p", "inv_beta_v", "gamma_s", "dt", "f_a", "precision", "junction_rule"):
         v = getattr(a, field)
-        other = W.with_(a, **{field: P.PLAIN_FP64 if field == "precision" else (0.5 * v if v else 0.1)})
+        other = W.with_(a, **{field: P.PLAIN_FP64 if field == "precision" else
+                              (1 if field == "junction_rule" else (0.5 * v if v else 0.1))})
         assert ws([a]) + ws([other]) - ws([a, other]) == head, field
     for field, value in (("f0", 3.0), ("seed", 99), ("noise_amp", 2e-3)):
         same = W.with_(a, **{field: value})

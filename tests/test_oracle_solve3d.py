@@ -14,9 +14,11 @@ def test_fft3d_matches_numpy(oracle_lib):
         assert np.abs(O.fft3d(a, +1) - np.fft.ifftn(a) * a.size).max() < 1e-12 * np.abs(a).sum()
 
 
-def test_one_plane_is_the_2d_solve(oracle_lib):
+@pytest.mark.parametrize("rule", [0, 1])
+def test_one_plane_is_the_2d_solve(oracle_lib, rule):
     # nz = 1: k_z = 0 only, the same arithmetic as the 2D solve, bit for bit
-    p = O.Params(nx=16, ny=8, ns=8, phi_p=0.2)
+    # (under either junction rule)
+    p = O.Params(nx=16, ny=8, ns=8, phi_p=0.2, f_a=0.375, junction_rule=rule)
     rng = np.random.default_rng(3)
     om = 0.2 * rng.standard_normal((3, p.ny, p.nx))
     phi3, q3 = O.solve3d(p, 1, om[:, None])
