@@ -322,12 +322,47 @@ def cufft_solve(torch, omega, r, dtype, timing=False):
     return phi, q, ev[0].elapsed_time(ev[1]), ev[0].elapsed_time(ev[2])
 
 
+def cufft_transforms_graph(torch, nchains, ny, nx, ns, flush, reps=5):
+    """The transform work of one single-chain solve alone, with cuFFT: N_s
+    forward and inverse real 2D transforms (rfft2, irfft2) of all nchains
+    chains batched, captured once in a CUDA graph (no elementwise work, no
+    launch gaps), FP32.  Returns the median CUDA-event ms of reps replays,
+    L2 flushed before each.  A lower bound for any cuFFT-based solve of the
+    same chains."""
+    x = torch.randn((nchains, ny, nx), dtype=torch.float32, device="cuda")
+    spec = torch.fft.rfft2(x)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):  # warm-up (cuFFT plans) outside the capture
+        for _ in range(2):
+            torch.fft.rfft2(x, out=spec)
+            torch.fft.irfft2(spec, s=(ny, nx), out=x)
+    torch.cuda.current_stream().wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for _ in range(ns):
+            torch.fft.rfft2(x, out=spec)
+            torch.fft.irfft2(spec, s=(ny, nx), out=x)
+    ms = []
+    for _ in range(reps):
+        flush.add_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        g.replay()
+        b.record()
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    return statistics.median(ms)
+
+
 def cufft_section(torch, runs, h, ours_ms, flush, reps=5):
     """cuFFT comparison on the workload: cufft_solve in FP32 on the runs'
     current fields (all runs on one grid with one parameter set but f0, seed
     and noise), L2 flushed before each of reps timed solves (median), beside
     our chain launch(es) of the step's differential solve, which propagate
-    the same chains over the same contour steps (plus the differential term)."""
+    the same chains over the same contour steps (plus the differential term).
+    Also the transforms alone in a captured graph (cufft_transforms_graph)."""
     r0 = runs[0]
     if any((r.nx, r.ny, r.ns, r.f_a, r.phi_p, r.chi_bs) != (r0.nx, r0.ny, r0.ns, r0.f_a, r0.phi_p, r0.chi_bs)
            for r in runs):
@@ -341,9 +376,13 @@ def cufft_section(torch, runs, h, ours_ms, flush, reps=5):
         prop.append(a)
         whole.append(b)
     tp, tw = statistics.median(prop), statistics.median(whole)
-    return {"propagation_ms": tp, "solve_ms": tw, "ours_chain_ms": ours_ms, "propagation_vs_ours": tp / ours_ms,
-            "note": "torch.fft (cuFFT) FP32, both chains of every run batched, eager launches; ours = the "
-                    "differential solve's chain launch(es) from the step's timing probes"}
+    tg = cufft_transforms_graph(torch, 2 * len(runs), r0.ny, r0.nx, r0.ns, flush, reps)
+    return {"transforms_only_graph_ms": tg, "transforms_only_vs_ours": tg / ours_ms,
+            "propagation_ms": tp, "solve_ms": tw, "ours_chain_ms": ours_ms, "propagation_vs_ours": tp / ours_ms,
+            "note": "transforms_only: N_s rfft2 + irfft2 of every chain (batched), captured in one CUDA graph, no "
+                    "elementwise work (a lower bound for a cuFFT solve); propagation/solve: the whole solve with "
+                    "torch.fft and torch elementwise ops, eager launches; ours = the differential solve's chain "
+                    "launch(es) from the step's timing probes (transforms, Fourier and node factors, state stores)"}
 
 
 def analysis_section(torch, h, runs, flush, hbm, calls=20):

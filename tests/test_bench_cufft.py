@@ -62,7 +62,17 @@ def test_timing_branch_and_section(monkeypatch):
         def get_state(self, k):
             return W.random_omega(16, 16, seed=k), None, None
 
+    seen = {}
+
+    def graph_stub(torch_, nchains, ny, nx, ns, flush, reps):
+        seen.update(nchains=nchains, ny=ny, nx=nx, ns=ns)
+        return 0.25
+
+    monkeypatch.setattr(b, "cufft_transforms_graph", graph_stub)
     out = b.cufft_section(torch, runs, H(), 0.5, torch.zeros(4), reps=3)
     assert out["propagation_ms"] == 1.0 and out["solve_ms"] == 2.0 and out["ours_chain_ms"] == 0.5
     assert out["propagation_vs_ours"] == 2.0
+    # the graph-captured transforms cover both chains of every run, N_s steps
+    assert seen == {"nchains": 4, "ny": 16, "nx": 16, "ns": 8}
+    assert out["transforms_only_graph_ms"] == 0.25 and out["transforms_only_vs_ours"] == 0.5
     assert b.cufft_section(torch, [runs[0], W.with_(runs[1], ns=12)], H(), 0.5, torch.zeros(4)) is None
