@@ -43,11 +43,20 @@ def test_noalloc_matches_workspace_solve_twice(prec, ny, nx, ns):
     om_d = torch.from_numpy(W.random_omega(ny, nx, seed=ny + ns)).cuda()
     ref_phi, ref_q = _solve_with_workspace(torch, r, om_d)
     torch.cuda.synchronize()
+    mem = None
     for _ in range(2):
         phi = torch.full_like(om_d, float("nan"))
         q = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
+        before = (torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated())
         P.epd_prop_solve_noalloc(r, om_d.data_ptr(), phi.data_ptr(), q.data_ptr(), 0)
         torch.cuda.synchronize()
+        after = (torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated())
+        # torch's pool is untouched, and from the second call on (the first may
+        # load the library's device image) the device's free memory too
+        assert after[1] == before[1]
+        if mem is not None:
+            assert after[0] == before[0]
+        mem = after[0]
         assert _rel(phi.cpu().numpy(), ref_phi) < TOL[prec]
         assert _rel(q.cpu().numpy(), ref_q) < TOL[prec]
 
