@@ -147,6 +147,15 @@ int epd_lb_densities(epd_lb *h, int32_t run, double *phi, double *q);
  * (FP64, asynchronous on the handle's stream); either pointer may be NULL. */
 int epd_lb_fields_dev(epd_lb *h, int32_t run, double *omega_dev, double *phi_dev);
 
+/* The intermediate fields of the last step of run `run` into caller device
+ * memory (FP64, asynchronous on the handle's stream; either pointer may be
+ * NULL): omega~ (the auxiliary-convected field, App. C item 1) and Phi~, its
+ * densities (Eqs. (6)-(11)).  With epd_lb_fields_dev they give the
+ * composition change Phi(t+dt) - Phi~ of the diffusion step that drives the
+ * force (Eqs. (19)-(20)); on the grids of the differential second solve that
+ * difference carries FP32 precision relative to itself. */
+int epd_lb_step_fields_dev(epd_lb *h, int32_t run, double *omega_tilde_dev, double *phi_tilde_dev);
+
 /* Fluid velocity u = (j + f/2)/rho of the last collision, lattice units,
  * 2*ny*nx doubles.  Synchronous. */
 int epd_lb_velocity(epd_lb *h, int32_t run, double *v);
@@ -226,10 +235,12 @@ int epd_lb_tiles(epd_lb *h, int32_t run, int32_t *out);
  * Learned density surrogate: a convolutional network that approximates the
  * map omega -> (Phi_A, Phi_B) of the single-chain solve, Eqs. (6)-(10), with
  * the exact means and the exact solvent density of Eq. (11).  Network: 3x3
- * convolutions with circular padding, channels 3 -> 32 -> 32 -> 32 -> 2, tanh
- * after the first three; input s_in (omega_c - <omega_c>), output Phi_c =
- * <Phi_c> + s_out (y_c - <y_c>).  Parameters: epd_sur_num_params() FP32
- * values, per layer W[co][ci][3][3] (tap = 3 (dy+1) + (dx+1)) then b[co].
+ * convolutions with circular padding and dilations 1, 2, 2, 4 (tap (dy, dx)
+ * of layer l reads the site r + d_l (dy, dx); receptive field +-9 sites),
+ * channels 3 -> 32 -> 32 -> 32 -> 2, tanh after the first three; input
+ * s_in (omega_c - <omega_c>), output Phi_c = <Phi_c> + s_out (y_c - <y_c>).
+ * Parameters: epd_sur_num_params() FP32 values, per layer W[co][ci][3][3]
+ * (tap = 3 (dy+1) + (dx+1)) then b[co].
  * Tensor-core kernels read BF16 copies of weights and activations and
  * accumulate in FP32.  Fields are [batch][species][ny][nx] FP64 on the device;
  * every call is asynchronous on cuda_stream; the workspace is caller-owned
@@ -242,6 +253,16 @@ int epd_sur_workspace_bytes(int32_t ny, int32_t nx, int32_t batch, int32_t train
  * the grid, phi_p and the A-block fraction of the exact means. */
 int epd_sur_forward(const epd_lb_params *p, int32_t batch, const float *params_dev, double s_in, double s_out,
                     const double *omega_dev, double *phi_dev, void *workspace, size_t workspace_bytes, void *cuda_stream);
+/* Densities at omega_dev from the surrogate at omega0_dev to first order in
+ * the field change: phi0_dev = the forward densities at omega0_dev, and
+ * phi_dev = phi0_dev + s_out (dy_c - <dy_c>) for A and B, dy the network's
+ * directional derivative (tangent pass, forward mode) along
+ * omega_dev - omega0_dev; the solvent density from Eq. (11) at omega_dev.
+ * The time stepper forms Phi(t+dt) from Phi~ this way.  Workspace as for
+ * epd_sur_forward (training = 0). */
+int epd_sur_tangent(const epd_lb_params *p, int32_t batch, const float *params_dev, double s_in, double s_out,
+                    const double *omega0_dev, const double *omega_dev, double *phi0_dev, double *phi_dev, void *workspace,
+                    size_t workspace_bytes, void *cuda_stream);
 /* Loss L = mean over batch, A/B channels and sites of (y_c - (Phi_c - <Phi_c>)/s_out)^2
  * for the target densities phi_dev, and its gradient dL/dparams (FP32,
  * epd_sur_num_params values) to grad_dev; L to loss_dev[0]. */
@@ -255,17 +276,26 @@ int epd_sur_train_step(const epd_lb_params *p, int32_t batch, float *params_dev,
                        double *loss_dev, void *workspace, size_t workspace_bytes, void *cuda_stream);
 
 /* Let the surrogate stand in for both single-chain solves of epd_lb_step:
- * every exact_every-th step (and while falling back) the exact step runs and
- * also evaluates the surrogate at omega~; if the RMS difference of the
- * densities (max over runs) exceeds residual_tol the following steps stay
- * exact until a check passes.  On the other steps both solves are the
- * surrogate (Q_P, Q_S keep their last exact values).  params_host: the
+ * Phi~ is the surrogate at omega~ and Phi(t+dt) = Phi~ plus its tangent along
+ * omega(t+dt) - omega~ (epd_sur_tangent).  Every exact_every-th step (and
+ * while falling back) the exact step runs and also evaluates the surrogate
+ * at omega~; its residual is the RMS difference of the A and B densities
+ * relative to the RMS fluctuation of the exact ones (max over runs), and if
+ * it exceeds residual_tol the following steps stay exact until a check
+ * passes.  On the other steps both solves are the surrogate (Q_P, Q_S keep
+ * their last exact values).  hold_force = 0: the polymer force of a
+ * surrogate step comes from its own composition change Phi(t+dt) - Phi~
+ * (Eqs. (19)-(20)); hold_force = 1: the LB keeps the force of the last exact
+ * step.  (The force is the change over one diffusion step, and mu of
+ * Eq. (1) nearly cancels in the incubation stage, so percent-level density
+ * errors of a surrogate become large force errors, while the exact force
+ * changes on the slow time scale of the composition.)  params_host: the
  * network's FP32 parameters (copied).  workspace: device memory of
  * epd_lb_surrogate_workspace_bytes bytes, caller-owned, kept alive while the
  * surrogate is attached.  exact_every = 0 detaches it. */
 int epd_lb_surrogate_workspace_bytes(epd_lb *h, size_t *bytes);
 int epd_lb_set_surrogate(epd_lb *h, const float *params_host, double s_in, double s_out, int32_t exact_every,
-                         double residual_tol, void *workspace, size_t workspace_bytes);
+                         double residual_tol, int32_t hold_force, void *workspace, size_t workspace_bytes);
 /* out[0] steps taken with the surrogate attached, out[1] exact steps,
  * out[2] surrogate steps, out[3] exact steps forced by a failed check,
  * out[4] last residual, out[5] 1 if currently falling back. */

@@ -34,8 +34,10 @@ SYMBOLS = (
     "epd_lb_set_state", "epd_lb_solve", "epd_lb_observables", "epd_lb_save", "epd_lb_load",
     "epd_lb_last_error", "epd_lb_destroy", "epd_prop_solve_workspace_bytes", "epd_prop_solve",
     "epd_lb_enable_timing", "epd_lb_kernel_times", "epd_prop_solve_noalloc", "epd_lb_tiles",
-    "epd_sur_num_params", "epd_sur_workspace_bytes", "epd_sur_forward", "epd_sur_gradients", "epd_sur_train_step",
+    "epd_sur_num_params", "epd_sur_workspace_bytes", "epd_sur_forward", "epd_sur_tangent", "epd_sur_gradients",
+    "epd_sur_train_step",
     "epd_lb_surrogate_workspace_bytes", "epd_lb_set_surrogate", "epd_lb_surrogate_stats", "epd_lb_fields_dev",
+    "epd_lb_step_fields_dev",
     "epd_lb_set_inversion", "epd_lb_inversion_stats", "epd_lb_sigma_delta", "epd_lb_width", "epd_lb_particles",
     "epd_prop_solve3d_workspace_bytes", "epd_prop_solve3d", "epd_lb3d_step", "epd_step3d_workspace_bytes",
     "epd_step3d", "epd_selftest_bounded_wait",
@@ -142,15 +144,18 @@ def lib():
             "epd_sur_num_params": (ctypes.c_int32, []),
             "epd_sur_workspace_bytes": (ctypes.c_int, [i32, i32, i32, i32, szp]),
             "epd_sur_forward": (ctypes.c_int, [P, i32, vp, ctypes.c_double, ctypes.c_double, vp, vp, vp, ctypes.c_size_t, vp]),
+            "epd_sur_tangent": (ctypes.c_int, [P, i32, vp, ctypes.c_double, ctypes.c_double, vp, vp, vp, vp, vp, ctypes.c_size_t,
+                                               vp]),
             "epd_sur_gradients": (ctypes.c_int, [P, i32, vp, ctypes.c_double, ctypes.c_double, vp, vp, vp, vp, vp,
                                                  ctypes.c_size_t, vp]),
             "epd_sur_train_step": (ctypes.c_int, [P, i32, vp, vp, vp, i32, ctypes.c_float, ctypes.c_double, ctypes.c_double,
                                                   vp, vp, vp, vp, ctypes.c_size_t, vp]),
             "epd_lb_surrogate_workspace_bytes": (ctypes.c_int, [vp, szp]),
-            "epd_lb_set_surrogate": (ctypes.c_int, [vp, vp, ctypes.c_double, ctypes.c_double, i32, ctypes.c_double, vp,
-                                                    ctypes.c_size_t]),
+            "epd_lb_set_surrogate": (ctypes.c_int, [vp, vp, ctypes.c_double, ctypes.c_double, i32, ctypes.c_double, i32,
+                                                    vp, ctypes.c_size_t]),
             "epd_lb_surrogate_stats": (ctypes.c_int, [vp, vp]),
             "epd_lb_fields_dev": (ctypes.c_int, [vp, i32, vp, vp]),
+            "epd_lb_step_fields_dev": (ctypes.c_int, [vp, i32, vp, vp]),
             "epd_lb_set_inversion": (ctypes.c_int, [vp, i32, ctypes.c_double]),
             "epd_lb_inversion_stats": (ctypes.c_int, [vp, i32, vp]),
             "epd_lb_sigma_delta": (ctypes.c_int, [vp, i32, i32, vp]),
@@ -390,6 +395,13 @@ class EpdLb:
         self._ck(lib().epd_lb_fields_dev(self.h, run, None if omega_dev is None else omega_dev.data_ptr(),
                                          None if phi_dev is None else phi_dev.data_ptr()), "epd_lb_fields_dev")
 
+    def step_fields_dev(self, run: int, omega_tilde_dev=None, phi_tilde_dev=None):
+        """omega~ and Phi~ of the last step of a run into device tensors
+        (3, ny, nx) FP64, on the handle's stream."""
+        self._ck(lib().epd_lb_step_fields_dev(self.h, run, None if omega_tilde_dev is None else omega_tilde_dev.data_ptr(),
+                                              None if phi_tilde_dev is None else phi_tilde_dev.data_ptr()),
+                 "epd_lb_step_fields_dev")
+
     def densities_dev(self, run: int, phi_dev, q_dev):
         self._ck(lib().epd_lb_densities_dev(self.h, run, phi_dev.data_ptr(), q_dev.data_ptr()), "epd_lb_densities_dev")
 
@@ -463,12 +475,15 @@ class EpdLb:
         return {"path": int(out[0]), "cluster_ctas": int(out[1]), "column_tile": int(out[2]), "differential": bool(out[3]),
                 "stream_column_tile": int(out[4]), "chain_launches": int(out[5])}
 
-    def set_surrogate(self, params, s_in: float, s_out: float, exact_every: int = 8, residual_tol: float = 1e-3):
+    def set_surrogate(self, params, s_in: float, s_out: float, exact_every: int = 8, residual_tol: float = 0.2,
+                      hold_force: bool = False):
         """Attach the learned surrogate (FP32 parameters, host array or torch
-        tensor) with its workspace on the device; exact_every = 0 detaches."""
+        tensor) with its workspace on the device; exact_every = 0 detaches.
+        residual_tol: relative to the exact density fluctuations; hold_force:
+        surrogate steps keep the last exact step's polymer force."""
         torch = self.torch
         if exact_every <= 0:
-            self._ck(lib().epd_lb_set_surrogate(self.h, None, 0.0, 0.0, 0, 0.0, None, 0), "epd_lb_set_surrogate")
+            self._ck(lib().epd_lb_set_surrogate(self.h, None, 0.0, 0.0, 0, 0.0, 0, None, 0), "epd_lb_set_surrogate")
             return
         nb = ctypes.c_size_t()
         self._ck(lib().epd_lb_surrogate_workspace_bytes(self.h, ctypes.byref(nb)), "epd_lb_surrogate_workspace_bytes")
@@ -476,7 +491,7 @@ class EpdLb:
         ptr = (self.sur_workspace.data_ptr() + 255) & ~255
         hp = np.ascontiguousarray(params.detach().cpu().numpy() if hasattr(params, "detach") else params, dtype=np.float32)
         self._ck(lib().epd_lb_set_surrogate(self.h, hp.ctypes.data_as(ctypes.c_void_p), s_in, s_out, exact_every,
-                                            residual_tol, ptr, nb.value), "epd_lb_set_surrogate")
+                                            residual_tol, int(hold_force), ptr, nb.value), "epd_lb_set_surrogate")
 
     def set_inversion(self, max_iter: int, tol: float = 1e-8):
         """Exact step of App. C: Fletcher-Reeves inversion of the convected

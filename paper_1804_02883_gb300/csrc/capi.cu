@@ -449,6 +449,7 @@ struct epd_lb {
     bool sur_on = false;
     int sur_every = 0;
     double sur_tol = 0.0, sur_s_in = 1.0, sur_s_out = 1.0;
+    bool sur_hold = false;                     // surrogate steps keep the last exact step's polymer force
     float *sur_params = nullptr;               // device copy
     std::vector<epdlb::sur::Work> sur_work;    // one per group
     double *sur_resid = nullptr;               // [groups + 1] device: per group residual, scratch
@@ -518,8 +519,11 @@ static cudaError_t enqueue_group(epd_lb *h, size_t gi, int parity, cudaStream_t 
         if ((e = launch_aux_convection(G, s))) return e;
         if ((e = sur::forward(W, h->sur_params, G.omega_t, G.phi_t, h->sur_s_in, h->sur_s_out, pa, pb, ps, s))) return e;
         if ((e = launch_diffusion(G, s))) return e;
-        if ((e = sur::forward(W, h->sur_params, G.omega, G.phi, h->sur_s_in, h->sur_s_out, pa, pb, ps, s))) return e;
-        if ((e = launch_force(G, s))) return e;
+        // Phi(t+dt) = Phi~ + the surrogate's change along omega(t+dt) - omega~
+        // (tangent pass), which drives the force unless the force of the last
+        // exact step is held
+        if ((e = sur::tangent(W, h->sur_params, G.omega, G.omega_t, G.phi_t, G.phi, h->sur_s_in, h->sur_s_out, ps, s))) return e;
+        if (!h->sur_hold && (e = launch_force(G, s))) return e;
         return launch_lb(G, parity, s);
     }
     SolveProbe probe;
@@ -537,7 +541,7 @@ static cudaError_t enqueue_group(epd_lb *h, size_t gi, int parity, cudaStream_t 
         sur_means(G, pa, pb, ps);
         double *phi_sur = reinterpret_cast<double *>(G.cz);
         if ((e = sur::forward(h->sur_work[gi], h->sur_params, G.omega_t, phi_sur, h->sur_s_in, h->sur_s_out, pa, pb, ps, s))) return e;
-        if ((e = sur::residual_rms(phi_sur, G.phi_t, G.g.n, G.g.nruns, G.part, h->sur_resid + gi, s))) return e;
+        if ((e = sur::residual_rel(phi_sur, G.phi_t, G.g.n, G.g.nruns, G.part, h->sur_resid + gi, s))) return e;
     }
     if ((e = launch_diffusion(G, s))) return e;                           // omega(t+dt)
     if (G.diff) {  // Phi(t+dt) as Phi~ plus the change from the diffusion update
@@ -875,6 +879,22 @@ extern "C" int epd_lb_fields_dev(epd_lb *h, int32_t run, double *omega_dev, doub
         CK(cudaMemcpyAsync(omega_dev, G->omega + (size_t)m * 3 * n, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream), "copy omega");
     if (phi_dev)
         CK(cudaMemcpyAsync(phi_dev, G->phi + (size_t)m * 3 * n, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream), "copy phi");
+    return EPD_LB_OK;
+}
+
+extern "C" int epd_lb_step_fields_dev(epd_lb *h, int32_t run, double *omega_tilde_dev, double *phi_tilde_dev)
+{
+    Group *G;
+    int m;
+    if (int rc = locate(h, run, &G, &m)) return rc;
+    const size_t n = (size_t)G->g.n;
+    if (omega_tilde_dev)
+        CK(cudaMemcpyAsync(omega_tilde_dev, G->omega_t + (size_t)m * 3 * n, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice,
+                           h->stream),
+           "copy omega~");
+    if (phi_tilde_dev)
+        CK(cudaMemcpyAsync(phi_tilde_dev, G->phi_t + (size_t)m * 3 * n, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream),
+           "copy Phi~");
     return EPD_LB_OK;
 }
 
@@ -1629,6 +1649,21 @@ extern "C" int epd_sur_forward(const epd_lb_params *p, int32_t batch, const floa
     return e == cudaSuccess ? EPD_LB_OK : EPD_LB_ECUDA;
 }
 
+extern "C" int epd_sur_tangent(const epd_lb_params *p, int32_t batch, const float *params_dev, double s_in, double s_out,
+                               const double *omega0_dev, const double *omega_dev, double *phi0_dev, double *phi_dev, void *workspace,
+                               size_t workspace_bytes, void *cuda_stream)
+{
+    sur::Work w;
+    if (!params_dev || !omega0_dev || !omega_dev || !phi0_dev || !phi_dev) return EPD_LB_EINVAL;
+    if (int rc = sur_setup(p, batch, false, workspace, workspace_bytes, w)) return rc;
+    const double na = (double)std::lround(p->f_a * (double)p->ns) / (double)p->ns;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaError_t e = sur::forward(w, params_dev, omega0_dev, phi0_dev, s_in, s_out, p->phi_p * na, p->phi_p * (1.0 - na),
+                                 1.0 - p->phi_p, s);
+    if (e == cudaSuccess) e = sur::tangent(w, params_dev, omega_dev, omega0_dev, phi0_dev, phi_dev, s_in, s_out, 1.0 - p->phi_p, s);
+    return e == cudaSuccess ? EPD_LB_OK : EPD_LB_ECUDA;
+}
+
 extern "C" int epd_sur_gradients(const epd_lb_params *p, int32_t batch, const float *params_dev, double s_in, double s_out,
                                  const double *omega_dev, const double *phi_dev, float *grad_dev, double *loss_dev, void *workspace,
                                  size_t workspace_bytes, void *cuda_stream)
@@ -1678,7 +1713,7 @@ extern "C" int epd_lb_surrogate_workspace_bytes(epd_lb *h, size_t *bytes)
 }
 
 extern "C" int epd_lb_set_surrogate(epd_lb *h, const float *params_host, double s_in, double s_out, int32_t exact_every,
-                                    double residual_tol, void *workspace, size_t workspace_bytes)
+                                    double residual_tol, int32_t hold_force, void *workspace, size_t workspace_bytes)
 {
     if (!h) return EPD_LB_EINVAL;
     CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
@@ -1711,6 +1746,7 @@ extern "C" int epd_lb_set_surrogate(epd_lb *h, const float *params_host, double 
     h->sur_tol = residual_tol;
     h->sur_s_in = s_in;
     h->sur_s_out = s_out;
+    h->sur_hold = hold_force != 0;
     h->sur_steps = h->sur_exact = h->sur_used = h->sur_forced = 0;
     h->sur_fallback = false;
     h->sur_last = 0.0;

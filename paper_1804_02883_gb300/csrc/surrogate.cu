@@ -2,10 +2,12 @@
 // convolutional network from the fields omega to the polymer densities) with
 // BF16 tensor-core training and inference kernels, FP32 accumulation.
 //
-// Network (periodic grid, 3x3 kernels, circular padding):
+// Network (periodic grid, 3x3 kernels of dilation d_l = 1, 2, 2, 4, circular
+// padding; receptive field +-9 sites, the range of the single-chain density
+// response at R_G = 3 sites):
 //   x0 = s_in (omega_c - <omega_c>), c = A, B, S          (3 channels)
-//   y_l = tanh(W_l * y_{l-1} + b_l), l = 1, 2, 3          (32 channels)
-//   y_4 = W_4 * y_3 + b_4                                 (2 channels)
+//   y_l = tanh(W_l *_{d_l} y_{l-1} + b_l), l = 1, 2, 3    (32 channels)
+//   y_4 = W_4 *_{d_4} y_3 + b_4                           (2 channels)
 //   Phi_A = <Phi_A> + s_out (y_4,0 - <y_4,0>), Phi_B likewise with y_4,1, where
 //   <Phi_A> = phi_p N_A/N_s and <Phi_B> = phi_p (1 - N_A/N_s) are the exact
 //   means (Sec. 2, Eqs. (9)-(10) conserve them); Phi_S is the exact local
@@ -19,8 +21,17 @@
 // flipped, transposed weights; the weight gradient is a GEMM over pixels per
 // tap.  Rounding to BF16 happens where the tensor cores read: weights,
 // activations and the output gradients.
+//
+// Tangent pass: the change of Phi_A, Phi_B for a small field change domega
+// at omega is the network's directional derivative (forward mode):
+// dx0 = s_in (domega_c - <domega_c>), dy_l = (1 - y_l^2) (W_l *_{d_l}
+// dy_{l-1}), dy_4 = W_4 *_{d_4} dy_3, dPhi_c = s_out (dy_4,c - <dy_4,c>).
+// The time stepper takes Phi(t+dt) = Phi~ + dPhi this way: two separate
+// forward passes at omega~ and omega(t+dt), whose inputs differ by far less
+// than a BF16 step, would not resolve the change that drives the force.
 #include <cstdint>
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cuda_bf16.h>
 
@@ -30,12 +41,15 @@
 
 namespace epdlb {
 
-// periodic index of a halo pixel (v in [-1, n]) on an axis of n pixels
+// periodic index of a halo pixel (v in [-n, 2n)) on an axis of n pixels
 __device__ __forceinline__ int halo_wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 namespace sur {
 
 constexpr int TH = 8, TW = 16, TP = TH * TW;  // pixel tile
-constexpr int HH = TH + 2, HW = TW + 2;       // halo tile
+// halo tile of a 3x3 kernel of dilation D: D pixels on each side
+template <int D> struct Halo {
+    static constexpr int HH = TH + 2 * D, HW = TW + 2 * D;
+};
 
 __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b)
 {
@@ -50,8 +64,10 @@ __device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-// Epilogue modes of the convolution.
-enum { EP_TANH = 0, EP_LINEAR = 1, EP_DX = 2 };
+// Epilogue modes of the convolution: tanh layer, linear layer, input
+// gradient (times 1 - y^2 of the layer below, FP32), tangent (times 1 - y^2
+// of this layer's BF16 output)
+enum { EP_TANH = 0, EP_LINEAR = 1, EP_DX = 2, EP_JVP = 3 };
 
 struct ConvArgs {
     const __nv_bfloat16 *in;    // [b][y][x][KP] (KP = input channels, padded)
@@ -60,18 +76,24 @@ struct ConvArgs {
     __nv_bfloat16 *out_bf;      // [b][y][x][NP] BF16 output (EP_TANH, EP_DX)
     float *out_f;               // [b][y][x][NP] FP32 output (EP_TANH when training, EP_LINEAR)
     const float *yprev;         // EP_DX: tanh output of the layer below, [b][y][x][NP] FP32
+    const __nv_bfloat16 *ycur;  // EP_JVP: this layer's tanh output, [b][y][x][NP] BF16
     int nx, ny, logx, logy, nb;
     int nreal;                  // output channels actually used (the rest are written as 0)
 };
 
 // One 8 x 16 pixel tile, all NP output channels; 4 warps, warp w owns pixel
-// rows 2w and 2w+1 (two m16 tiles).  KP, NP multiples of 16 and 8.
-template <int KP, int NP, int MODE>
+// rows 2w and 2w+1 (two m16 tiles).  KP, NP multiples of 16 and 8; D the
+// dilation (taps at offsets -D, 0, +D).  Dynamic shared memory: conv_smem.
+template <int KP, int NP, int D>
+constexpr size_t conv_smem() { return ((size_t)Halo<D>::HH * Halo<D>::HW + 9 * NP) * (KP + 8) * 2; }
+template <int KP, int NP, int MODE, int D>
 __global__ void __launch_bounds__(128) conv3x3(ConvArgs a)
 {
     constexpr int KS = KP + 8;  // padded channel stride in shared memory (halves)
-    __shared__ __align__(16) __nv_bfloat16 tile[HH * HW * KS];
-    __shared__ __align__(16) __nv_bfloat16 wsm[9 * NP * KS];
+    constexpr int HH = Halo<D>::HH, HW = Halo<D>::HW;
+    extern __shared__ __align__(16) unsigned char conv_raw[];
+    __nv_bfloat16 *tile = reinterpret_cast<__nv_bfloat16 *>(conv_raw);
+    __nv_bfloat16 *wsm = tile + HH * HW * KS;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long n = (long long)a.nx * a.ny;
     // weights once per CTA; the CTA then walks over pixel tiles
@@ -89,7 +111,7 @@ __global__ void __launch_bounds__(128) conv3x3(ConvArgs a)
     for (int e = tid; e < HH * HW * (KP / 8); e += 128) {
         const int pix = e / (KP / 8), ch = (e % (KP / 8)) * 8;
         const int hy = pix / HW, hx = pix % HW;
-        const int gy = halo_wrap(ty0 + hy - 1, a.ny), gx = halo_wrap(tx0 + hx - 1, a.nx);
+        const int gy = halo_wrap(ty0 + hy - D, a.ny), gx = halo_wrap(tx0 + hx - D, a.nx);
         *reinterpret_cast<uint4 *>(&tile[pix * KS + ch]) = *reinterpret_cast<const uint4 *>(&in[((size_t)gy * a.nx + gx) * KP + ch]);
     }
     __syncthreads();
@@ -105,7 +127,7 @@ __global__ void __launch_bounds__(128) conv3x3(ConvArgs a)
 
 #pragma unroll
     for (int tap = 0; tap < 9; ++tap) {
-        const int dy = tap / 3, dx = tap % 3;  // halo offsets 0..2 (i.e. -1..+1)
+        const int dy = (tap / 3) * D, dx = (tap % 3) * D;  // halo offsets 0, D, 2D (i.e. -D, 0, +D)
 #pragma unroll
         for (int kc = 0; kc < KP / 16; ++kc) {
             uint32_t af[2][4];
@@ -155,6 +177,11 @@ __global__ void __launch_bounds__(128) conv3x3(ConvArgs a)
                     const float2 yp = *reinterpret_cast<const float2 *>(&a.yprev[pix * NP + c]);
                     v0 *= 1.f - yp.x * yp.x;
                     v1 *= 1.f - yp.y * yp.y;
+                } else if (MODE == EP_JVP) {
+                    // tangent of this tanh layer: (W * dy) (1 - y^2)
+                    const float y0 = __bfloat162float(a.ycur[pix * NP + c]), y1 = __bfloat162float(a.ycur[pix * NP + c + 1]);
+                    v0 *= 1.f - y0 * y0;
+                    v1 *= 1.f - y1 * y1;
                 }
                 if (c >= a.nreal) v0 = 0.f;
                 if (c + 1 >= a.nreal) v1 = 0.f;
@@ -171,15 +198,16 @@ __global__ void __launch_bounds__(128) conv3x3(ConvArgs a)
 // over an 8 x 16 tile per step, `tiles` consecutive tiles per CTA; 9 warps, warp
 // = tap.  Partial sums per CTA to part[blk][tap][co][ci] (deterministic
 // reduction later).  CO, CI multiples of 16 and 8.
-template <int CI, int CO>
+template <int CI, int CO, int D>
 __global__ void __launch_bounds__(288) conv3x3_dw(const __nv_bfloat16 *x, const __nv_bfloat16 *dz, float *part, int nx, int ny,
                                                  int tiles_x, int tiles_per_cta, int ntiles_total)
 {
     constexpr int CS = CI + 8, DS = TP + 8;
+    constexpr int HH = Halo<D>::HH, HW = Halo<D>::HW;
     __shared__ __align__(16) __nv_bfloat16 tile[HH * HW * CS];
     __shared__ __align__(16) __nv_bfloat16 dzt[CO * DS];  // [co][p], transposed
     const int tid = threadIdx.x, lane = tid & 31, tap = tid >> 5;
-    const int g = lane >> 2, t = lane & 3, dy = tap / 3, dx = tap % 3;
+    const int g = lane >> 2, t = lane & 3, dy = (tap / 3) * D, dx = (tap % 3) * D;
     const long long n = (long long)nx * ny;
     float acc[CO / 16][CI / 8][4];
 #pragma unroll
@@ -200,7 +228,7 @@ __global__ void __launch_bounds__(288) conv3x3_dw(const __nv_bfloat16 *x, const 
         for (int e = tid; e < HH * HW * (CI / 8); e += 288) {
             const int pix = e / (CI / 8), ch = (e % (CI / 8)) * 8;
             const int hy = pix / HW, hx = pix % HW;
-            const int gy = halo_wrap(ty0 + hy - 1, ny), gx = halo_wrap(tx0 + hx - 1, nx);
+            const int gy = halo_wrap(ty0 + hy - D, ny), gx = halo_wrap(tx0 + hx - D, nx);
             *reinterpret_cast<uint4 *>(&tile[pix * CS + ch]) = *reinterpret_cast<const uint4 *>(&xin[((size_t)gy * nx + gx) * CI + ch]);
         }
         for (int e = tid; e < TP * CO; e += 288) {
@@ -306,6 +334,63 @@ __global__ void prep_input(const double *omega, const double *mean, double s_in,
     uint4 *dst = reinterpret_cast<uint4 *>(x0 + (size_t)i * 16);
     dst[0] = *reinterpret_cast<uint4 *>(&v[0]);
     dst[1] = *reinterpret_cast<uint4 *>(&v[8]);
+}
+
+// Tangent input: dx0[b][p][16] = s_in ((omega_c - omega0_c) - <omega_c - omega0_c>)
+// for c < 3 (the FP64 difference of the two fields, then BF16), 0 for the padding.
+__global__ void prep_tangent(const double *omega, const double *omega0, const double *mean, const double *mean0, double s_in,
+                             long long n, int nb, __nv_bfloat16 *t0)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * nb) return;
+    const long long b = i / n, p = i % n;
+    __align__(16) __nv_bfloat16 v[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16_rn(0.f);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const size_t q = (b * 3 + c) * n + p;
+        v[c] = __float2bfloat16_rn((float)(s_in * ((omega[q] - omega0[q]) - (mean[b * 3 + c] - mean0[b * 3 + c]))));
+    }
+    uint4 *dst = reinterpret_cast<uint4 *>(t0 + (size_t)i * 16);
+    dst[0] = *reinterpret_cast<uint4 *>(&v[0]);
+    dst[1] = *reinterpret_cast<uint4 *>(&v[8]);
+}
+
+// Block partials of sum e q over one plane per sample, e = exp(-omega0_S),
+// q = expm1(-(omega_S - omega0_S)) (FP32, accurate relative to the change).
+__global__ void __launch_bounds__(256) solvent_change_partials(const double *omega, const double *omega0, long long n, double *part)
+{
+    __shared__ double red[32];
+    const int b = blockIdx.y;
+    const long long chunk = (n + kRedBlocks - 1) / kRedBlocks, lo = blockIdx.x * chunk;
+    const long long hi = lo + chunk < n ? lo + chunk : n;
+    const double *w = omega + ((size_t)b * 3 + 2) * n, *w0 = omega0 + ((size_t)b * 3 + 2) * n;
+    float acc = 0.f;
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x)
+        acc += expf(-(float)w0[i]) * expm1f(-(float)(w[i] - w0[i]));
+    const double s = block_sum((double)acc, red);
+    if (threadIdx.x == 0) part[(size_t)b * kRedBlocks + blockIdx.x] = s;
+}
+
+// Densities after a field change: Phi_A, Phi_B = the densities at omega0
+// plus s_out (dy4 - <dy4>) (the tangent output); Phi_S of Eq. (11) at omega
+// as the densities at omega0 plus the exact change,
+//   Phi_S = Phi0_S + Phi0_S (q - m) / (1 + m),  m = <e q> / <e>,
+// every term of the size of the change (e, q as in solvent_change_partials).
+__global__ void densities_tangent(const float *t4, const double *tmean, const double *phi0, const double *omega,
+                                  const double *omega0, const double *e_mean, const double *eq_mean, double s_out, long long n,
+                                  int nb, double *phi)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * nb) return;
+    const long long b = i / n, p = i % n;
+    const float2 y = *reinterpret_cast<const float2 *>(&t4[(size_t)i * 8]);
+    phi[(b * 3 + 0) * n + p] = phi0[(b * 3 + 0) * n + p] + s_out * ((double)y.x - tmean[2 * b]);
+    phi[(b * 3 + 1) * n + p] = phi0[(b * 3 + 1) * n + p] + s_out * ((double)y.y - tmean[2 * b + 1]);
+    const size_t q = (b * 3 + 2) * n + p;
+    const double dq = (double)expm1f(-(float)(omega[q] - omega0[q])), m = eq_mean[b] / e_mean[b];
+    phi[q] = phi0[q] + phi0[q] * (dq - m) / (1.0 + m);
 }
 
 // Densities from the network output: Phi_A, Phi_B with exact means, Phi_S from
@@ -429,9 +514,10 @@ __global__ void pack_weights(const float *wm, int co_real, int ci_real, int NP, 
 namespace epdlb {
 namespace sur {
 
-// storage channels (padded) of each layer's input and output
+// storage channels (padded) of each layer's input and output; dilations
 static const int kKP[kLayers] = {16, 32, 32, 32};
 static const int kNP[kLayers] = {32, 32, 32, 8};
+constexpr int kD0 = 1, kD1 = 2, kD2 = 2, kD3 = 4;
 
 int num_params()
 {
@@ -467,6 +553,11 @@ size_t carve(Work &w, char *base, int nb, int ny, int nx, bool training)
     w.x0 = take(np * 16 * 2);
     for (int l = 0; l < 3; ++l) w.y[l] = take(np * 32 * 2);
     w.y4 = take(np * 8 * 4);
+    w.t0 = take(np * 16 * 2);
+    w.t[0] = take(np * 32 * 2);
+    w.t[1] = take(np * 32 * 2);
+    w.t4 = take(np * 8 * 4);
+    w.means2 = (double *)take((size_t)nb * 3 * sizeof(double));
     for (int l = 0; l < kLayers; ++l) w.wf[l] = take((size_t)9 * kNP[l] * kKP[l] * 2);
     w.means = (double *)take((size_t)nb * 3 * sizeof(double));
     w.ymean = (double *)take((size_t)nb * 2 * sizeof(double));
@@ -523,11 +614,18 @@ static cudaError_t pack_all(Work &w, const float *params, bool backward, cudaStr
     return cudaGetLastError();
 }
 
-template <int KP, int NP, int MODE>
+template <int KP, int NP, int MODE, int D>
 static void conv(Work &w, const void *in, const void *wt, const float *bias, void *out_bf, float *out_f, const float *yprev, int nreal,
-                 cudaStream_t s)
+                 cudaStream_t s, const void *ycur = nullptr)
 {
+    constexpr size_t smem = conv_smem<KP, NP, D>();
+    static std::atomic<bool> conf{false};  // attribute set (idempotent if two threads race)
+    if (!conf) {
+        cudaFuncSetAttribute(conv3x3<KP, NP, MODE, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        conf = true;
+    }
     ConvArgs a;
+    a.ycur = reinterpret_cast<const __nv_bfloat16 *>(ycur);
     a.in = reinterpret_cast<const __nv_bfloat16 *>(in);
     a.w = reinterpret_cast<const __nv_bfloat16 *>(wt);
     a.bias = bias;
@@ -541,16 +639,16 @@ static void conv(Work &w, const void *in, const void *wt, const float *bias, voi
     a.nreal = nreal;
     a.nb = w.nb;
     const int tiles = w.nb * (w.nx / TW) * (w.ny / TH);
-    conv3x3<KP, NP, MODE><<<std::min(tiles, 8 * 152), 128, 0, s>>>(a);
+    conv3x3<KP, NP, MODE, D><<<std::min(tiles, 8 * 152), 128, smem, s>>>(a);
 }
 
 static cudaError_t forward_layers(Work &w, const float *params, cudaStream_t s)
 {
     const bool tr = w.training;
-    conv<16, 32, EP_TANH>(w, w.x0, w.wf[0], params + param_offset_b(0), w.y[0], tr ? (float *)w.yf[0] : nullptr, nullptr, 32, s);
-    conv<32, 32, EP_TANH>(w, w.y[0], w.wf[1], params + param_offset_b(1), w.y[1], tr ? (float *)w.yf[1] : nullptr, nullptr, 32, s);
-    conv<32, 32, EP_TANH>(w, w.y[1], w.wf[2], params + param_offset_b(2), w.y[2], tr ? (float *)w.yf[2] : nullptr, nullptr, 32, s);
-    conv<32, 8, EP_LINEAR>(w, w.y[2], w.wf[3], params + param_offset_b(3), nullptr, (float *)w.y4, nullptr, 2, s);
+    conv<16, 32, EP_TANH, kD0>(w, w.x0, w.wf[0], params + param_offset_b(0), w.y[0], tr ? (float *)w.yf[0] : nullptr, nullptr, 32, s);
+    conv<32, 32, EP_TANH, kD1>(w, w.y[0], w.wf[1], params + param_offset_b(1), w.y[1], tr ? (float *)w.yf[1] : nullptr, nullptr, 32, s);
+    conv<32, 32, EP_TANH, kD2>(w, w.y[1], w.wf[2], params + param_offset_b(2), w.y[2], tr ? (float *)w.yf[2] : nullptr, nullptr, 32, s);
+    conv<32, 8, EP_LINEAR, kD3>(w, w.y[2], w.wf[3], params + param_offset_b(3), nullptr, (float *)w.y4, nullptr, 2, s);
     return cudaGetLastError();
 }
 
@@ -569,14 +667,37 @@ cudaError_t forward(Work &w, const float *params, const double *omega, double *p
     return cudaGetLastError();
 }
 
-template <int CI, int CO>
+cudaError_t tangent(Work &w, const float *params, const double *omega, const double *omega0, const double *phi0, double *phi,
+                    double s_in, double s_out, double ps_bar, cudaStream_t s)
+{
+    // the activations y_l of the forward pass at omega0 are in w (BF16)
+    plane_means(omega, 0, w.nb * 3, w.n, w.red, w.means2, s);
+    plane_means(omega0, 0, w.nb * 3, w.n, w.red, w.means, s);
+    prep_tangent<<<blocks(w.n * w.nb), 256, 0, s>>>(omega, omega0, w.means2, w.means, s_in, w.n, w.nb,
+                                                    reinterpret_cast<__nv_bfloat16 *>(w.t0));
+    conv<16, 32, EP_JVP, kD0>(w, w.t0, w.wf[0], nullptr, w.t[0], nullptr, nullptr, 32, s, w.y[0]);
+    conv<32, 32, EP_JVP, kD1>(w, w.t[0], w.wf[1], nullptr, w.t[1], nullptr, nullptr, 32, s, w.y[1]);
+    conv<32, 32, EP_JVP, kD2>(w, w.t[1], w.wf[2], nullptr, w.t[0], nullptr, nullptr, 32, s, w.y[2]);
+    conv<32, 8, EP_LINEAR, kD3>(w, w.t[0], w.wf[3], nullptr, nullptr, (float *)w.t4, nullptr, 2, s);
+    plane_means(w.t4, 2, w.nb * 2, w.n, w.red, w.ymean, s);
+    // <e> at omega0 into qs, <e q> into means2 (free again)
+    plane_means(omega0, 1, w.nb, w.n, w.red, w.qs, s);
+    solvent_change_partials<<<dim3(kRedBlocks, w.nb), 256, 0, s>>>(omega, omega0, w.n, w.red);
+    plane_finish<<<(w.nb + 63) / 64, 64, 0, s>>>(w.red, w.nb, 1.0 / (double)w.n, w.means2);
+    densities_tangent<<<blocks(w.n * w.nb), 256, 0, s>>>((const float *)w.t4, w.ymean, phi0, omega, omega0, w.qs, w.means2, s_out,
+                                                         w.n, w.nb, phi);
+    (void)ps_bar;
+    return cudaGetLastError();
+}
+
+template <int CI, int CO, int D>
 static void dw(Work &w, const void *x, const void *dzp, cudaStream_t s)
 {
     const int tiles_x = w.nx / TW;
     const int ntiles = w.nb * tiles_x * (w.ny / TH);
     const int per = (ntiles + w.nblk_dw - 1) / w.nblk_dw;
     const int nblk = (ntiles + per - 1) / per;
-    conv3x3_dw<CI, CO><<<nblk, 288, 0, s>>>(reinterpret_cast<const __nv_bfloat16 *>(x), reinterpret_cast<const __nv_bfloat16 *>(dzp),
+    conv3x3_dw<CI, CO, D><<<nblk, 288, 0, s>>>(reinterpret_cast<const __nv_bfloat16 *>(x), reinterpret_cast<const __nv_bfloat16 *>(dzp),
                                             w.dwpart, w.nx, w.ny, tiles_x, per, ntiles);
     w.nblk_dw = nblk;
 }
@@ -584,9 +705,10 @@ static void dw(Work &w, const void *x, const void *dzp, cudaStream_t s)
 static void layer_grads(Work &w, int l, const void *x, const void *dzp, int CO, int CI, cudaStream_t s)
 {
     const int ntiles_cap = w.nblk_dw;
-    if (CI == 16 && CO == 32) dw<16, 32>(w, x, dzp, s);
-    else if (CI == 32 && CO == 32) dw<32, 32>(w, x, dzp, s);
-    else dw<32, 16>(w, x, dzp, s);
+    if (l == 0) dw<16, 32, kD0>(w, x, dzp, s);
+    else if (l == 1) dw<32, 32, kD1>(w, x, dzp, s);
+    else if (l == 2) dw<32, 32, kD2>(w, x, dzp, s);
+    else dw<32, 16, kD3>(w, x, dzp, s);
     const int nw = kCout[l] * kCin[l] * 9;
     reduce_dw<<<blocks(nw), 256, 0, s>>>(w.dwpart, w.nblk_dw, kCout[l], kCin[l], CO, CI, w.grad + param_offset_w(l));
     bias_grad<<<CO, 256, 0, s>>>(reinterpret_cast<const __nv_bfloat16 *>(dzp), (long long)w.nb * w.n, CO, kCout[l],
@@ -609,13 +731,13 @@ cudaError_t gradients(Work &w, const float *params, const double *omega, const d
     sum_parts<<<1, 256, 0, s>>>(w.lpart, (int)lb, 2.0 * (double)w.n * w.nb, loss_dev);
     // layer 4: dW from y3 and dZ4; dZ3 = (W4^T dZ4) (1 - y3^2)
     layer_grads(w, 3, w.y[2], w.dz4, 16, 32, s);
-    conv<16, 32, EP_DX>(w, w.dz4, w.wb[3], nullptr, w.dz[0], nullptr, (const float *)w.yf[2], 32, s);
+    conv<16, 32, EP_DX, kD3>(w, w.dz4, w.wb[3], nullptr, w.dz[0], nullptr, (const float *)w.yf[2], 32, s);
     // layer 3
     layer_grads(w, 2, w.y[1], w.dz[0], 32, 32, s);
-    conv<32, 32, EP_DX>(w, w.dz[0], w.wb[2], nullptr, w.dz[1], nullptr, (const float *)w.yf[1], 32, s);
+    conv<32, 32, EP_DX, kD2>(w, w.dz[0], w.wb[2], nullptr, w.dz[1], nullptr, (const float *)w.yf[1], 32, s);
     // layer 2
     layer_grads(w, 1, w.y[0], w.dz[1], 32, 32, s);
-    conv<32, 32, EP_DX>(w, w.dz[1], w.wb[1], nullptr, w.dz[0], nullptr, (const float *)w.yf[0], 32, s);
+    conv<32, 32, EP_DX, kD1>(w, w.dz[1], w.wb[1], nullptr, w.dz[0], nullptr, (const float *)w.yf[0], 32, s);
     // layer 1
     layer_grads(w, 0, w.x0, w.dz[0], 32, 16, s);
     return cudaGetLastError();
@@ -655,6 +777,36 @@ __global__ void max_of(const double *v, int cnt, double *out)
 cudaError_t residual_rms(const double *phi_a, const double *phi_b, long long n, int nb, double *tmp, double *out, cudaStream_t s)
 {
     rms_diff<<<nb, 256, 0, s>>>(phi_a, phi_b, 3 * n, tmp);
+    max_of<<<1, 32, 0, s>>>(tmp, nb, out);
+    return cudaGetLastError();
+}
+
+// Per run (block): sqrt(sum_{c=A,B} |a_c - b_c|^2 / sum_{c=A,B} |b_c - <b_c>|^2).
+__global__ void __launch_bounds__(256) rel_diff(const double *a, const double *b, long long n, double *out)
+{
+    __shared__ double red[32];
+    const double *pa = a + (size_t)blockIdx.x * 3 * n, *pb = b + (size_t)blockIdx.x * 3 * n;
+    double num = 0.0, den = 0.0;
+    for (int c = 0; c < 2; ++c) {
+        double s = 0.0, ss = 0.0, dd = 0.0;
+        for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+            const double v = pb[c * n + i], d = pa[c * n + i] - v;
+            s += v;
+            ss += v * v;
+            dd += d * d;
+        }
+        s = block_sum(s, red);
+        ss = block_sum(ss, red);
+        dd = block_sum(dd, red);
+        num += dd;
+        den += ss - s * s / (double)n;
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = den > 0.0 ? sqrt(num / den) : (num > 0.0 ? INFINITY : 0.0);
+}
+
+cudaError_t residual_rel(const double *phi_a, const double *phi_b, long long n, int nb, double *tmp, double *out, cudaStream_t s)
+{
+    rel_diff<<<nb, 256, 0, s>>>(phi_a, phi_b, n, tmp);
     max_of<<<1, 32, 0, s>>>(tmp, nb, out);
     return cudaGetLastError();
 }

@@ -1,9 +1,10 @@
 """Learned density surrogate: training and inference through the C ABI.
 
-The network (3x3 convolutions, channels 3 -> 32 -> 32 -> 32 -> 2, tanh,
-circular padding) maps the fields omega to the polymer densities; its
-forward, backward and Adam kernels are the library's (epd_sur_*).  This
-module only marshals arguments and holds the parameters in torch tensors.
+The network (3x3 convolutions of dilation 1, 2, 2, 4, channels
+3 -> 32 -> 32 -> 32 -> 2, tanh, circular padding) maps the fields omega to
+the polymer densities; its forward, tangent, backward and Adam kernels are
+the library's (epd_sur_*).  This module only marshals arguments and holds
+the parameters in torch tensors.
 """
 from __future__ import annotations
 
@@ -78,6 +79,19 @@ class Surrogate:
         if rc:
             raise EpdLbError(rc, "epd_sur_forward")
         return phi
+
+    def tangent(self, omega0_dev, omega_dev):
+        """Densities at omega0 (forward) and at omega to first order in
+        omega - omega0 (tangent pass): (phi0, phi), each [batch, 3, ny, nx]."""
+        phi0 = self.torch.empty_like(omega0_dev)
+        phi = self.torch.empty_like(omega_dev)
+        _, ptr, nb = self._ws_f
+        rc = lib().epd_sur_tangent(self._c(), omega0_dev.shape[0], self.params.data_ptr(), self.s_in, self.s_out,
+                                   omega0_dev.data_ptr(), omega_dev.data_ptr(), phi0.data_ptr(), phi.data_ptr(), ptr, nb,
+                                   self.stream.cuda_stream)
+        if rc:
+            raise EpdLbError(rc, "epd_sur_tangent")
+        return phi0, phi
 
     def gradients(self, omega_dev, phi_dev):
         grad = self.torch.empty_like(self.params)

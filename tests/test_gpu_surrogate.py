@@ -72,6 +72,32 @@ def test_gradients_match_oracle(torch):
     assert off == go.size
 
 
+@pytest.mark.parametrize("ny,nx", [(32, 64), (64, 32)])
+def test_tangent_matches_oracle(torch, ny, nx):
+    # the density change along a small field change (the size of one
+    # diffusion update) from the tangent pass, element by element against the
+    # oracle's forward-mode derivative with the same bfloat16 rounding points
+    run = P.RunParams(nx=nx, ny=ny, ns=8, precision=P.MIXED_FP32, phi_p=0.2, f_a=0.5)
+    p = rand_params(13)
+    rng = np.random.default_rng(ny * nx)
+    om0 = 0.01 * rng.standard_normal((2, 3, ny, nx))
+    dom = 1e-5 * rng.standard_normal((2, 3, ny, nx))
+    sur = S.Surrogate(run, 2, params=p, s_in=100.0, s_out=1e-3)
+    phi0, phi = sur.tangent(torch.from_numpy(om0).cuda(), torch.from_numpy(om0 + dom).cuda())
+    phi0, phi = phi0.cpu().numpy(), phi.cpu().numpy()
+    for b in range(2):
+        want0 = OS.densities(p.astype(np.float64), om0[b], 100.0, 1e-3, 0.2, 0.5, emulate_bf16=True)
+        assert np.abs(phi0[b, :2] - want0[:2]).max() < 3e-3 * np.abs(want0[:2] - want0[:2].mean()).max()
+        want = OS.density_change(p.astype(np.float64), om0[b], dom[b], 100.0, 1e-3, emulate_bf16=True)
+        got = phi[b, :2] - phi0[b, :2]
+        # BF16 tangents (relative 2^-8 per stored value) through four layers
+        assert np.abs(got - want).max() < 2e-2 * np.abs(want).max()
+        assert np.corrcoef(got.ravel(), want.ravel())[0, 1] > 0.999
+        # the solvent density is Eq. (11) at the new field
+        es = np.exp(-(om0[b, 2] + dom[b, 2]))
+        assert np.abs(phi[b, 2] - 0.8 * es / es.mean()).max() < 1e-6
+
+
 def exact_pairs(torch, run, count, seed):
     """(omega, Phi) of exact single-chain solves on quench-like fields."""
     h = P.EpdLb([run])
@@ -112,12 +138,21 @@ def test_controller_exact_every_k(torch):
     run = W.with_(W.plain_small(), precision=P.MIXED_FP32, f0=0.0)
     h = P.EpdLb([run])
     params = S.init_params(seed=1, out_scale=0.0)  # predicts the exact means
-    h.set_surrogate(params, s_in=300.0, s_out=1e-3, exact_every=8, residual_tol=1.0)
+    # the residual is relative to the exact density fluctuations: a network
+    # that predicts only the exact means has residual 1
+    h.set_surrogate(params, s_in=300.0, s_out=1e-3, exact_every=8, residual_tol=2.0)
     h.step(24)
     st = h.surrogate_stats()
     assert st["steps"] == 24 and st["exact"] == 3 and st["surrogate"] == 21 and st["forced_exact"] == 0
+    assert abs(st["last_residual"] - 1.0) < 1e-6
     ob = h.observables(0)
     assert abs((ob["mean_phi_a"] + ob["mean_phi_b"]) / run.phi_p - 1) < 1e-12
+    # a network that misses the fluctuations fails a tolerance below 1: the
+    # fallback fires and the steps stay exact
+    h.set_surrogate(params, s_in=300.0, s_out=1e-3, exact_every=8, residual_tol=0.5)
+    h.step(10)
+    st = h.surrogate_stats()
+    assert st["forced_exact"] > 0 and st["falling_back"] == 1 and st["surrogate"] == 0
     # a residual tolerance that cannot be met forces exact steps
     h.set_surrogate(params, s_in=300.0, s_out=1e-3, exact_every=8, residual_tol=0.0)
     h.step(5)
@@ -126,3 +161,28 @@ def test_controller_exact_every_k(torch):
     h.set_surrogate(None, 0, 0, exact_every=0)
     h.step(2)
     h.close()
+
+
+def test_hold_force_keeps_the_exact_force_on_surrogate_steps(torch):
+    # Step 1 is exact in both handles; on step 2 (a surrogate step) both take
+    # the same surrogate densities, but the LB sees the surrogate's own force
+    # in one handle and the held force of step 1 in the other.  The collision
+    # velocity is (j + f/2)/rho with the same j and rho, so the two differ by
+    # half the force difference, and repeating the held step reproduces it.
+    run = W.with_(W.plain_small(), precision=P.MIXED_FP32, f0=0.0, noise_amp=1e-2)
+    params = S.init_params(seed=2, out_scale=0.05)
+    hs = [P.EpdLb([run]) for _ in range(3)]
+    hs[0].set_surrogate(params, s_in=300.0, s_out=1e-3, exact_every=100, residual_tol=1e9, hold_force=False)
+    hs[1].set_surrogate(params, s_in=300.0, s_out=1e-3, exact_every=100, residual_tol=1e9, hold_force=True)
+    hs[2].set_surrogate(params, s_in=300.0, s_out=1e-3, exact_every=100, residual_tol=1e9, hold_force=True)
+    for h in hs:
+        h.step(2)
+    own, held, held2 = (h.velocity(0) for h in hs)
+    pa, pb = hs[0].densities(0)[0], hs[1].densities(0)[0]
+    assert np.array_equal(pa, pb)  # the densities do not depend on the force choice
+    assert np.array_equal(held, held2)
+    assert np.abs(own - held).max() > 1e-3 * np.abs(held).max()
+    for h in hs:
+        st = h.surrogate_stats()
+        assert st["exact"] == 1 and st["surrogate"] == 1
+        h.close()

@@ -32,23 +32,58 @@ def test_gradient_matches_finite_differences():
         assert abs(num - g[i]) < 1e-6 * max(1.0, abs(g[i]))
 
 
-def test_conv_transpose_is_adjoint():
+@pytest.mark.parametrize("d", [1, 2, 4])
+def test_conv_transpose_is_adjoint(d):
     rng = np.random.default_rng(3)
-    x = rng.standard_normal((4, 8, 16))
+    x = rng.standard_normal((4, 16, 32))
     w = rng.standard_normal((5, 4, 3, 3))
-    g = rng.standard_normal((5, 8, 16))
-    assert abs((OS.conv(x, w) * g).sum() - (x * OS.conv_transpose(g, w)).sum()) < 1e-10
+    g = rng.standard_normal((5, 16, 32))
+    assert abs((OS.conv(x, w, d) * g).sum() - (x * OS.conv_transpose(g, w, d)).sum()) < 1e-10
+    # and the weight gradient is the derivative of <conv(x, w), g> in w
+    dw = OS.conv_weight_grad(x, g, d)
+    e = np.zeros_like(w)
+    e[2, 1, 0, 2] = 1.0
+    assert abs((OS.conv(x, e, d) * g).sum() - dw[2, 1, 0, 2]) < 1e-10
 
 
-def test_conv_is_correlation_with_stated_taps():
-    # a single tap W[0,0,dy+1,dx+1] = 1 picks x(r + (dy, dx))
-    x = np.arange(64.0).reshape(1, 8, 8)
+@pytest.mark.parametrize("d", [1, 2, 4])
+def test_conv_is_correlation_with_stated_taps(d):
+    # a single tap W[0,0,dy+1,dx+1] = 1 picks x(r + d (dy, dx)), periodically
+    x = np.arange(16.0 * 16).reshape(1, 16, 16)
     for dy in (-1, 0, 1):
         for dx in (-1, 0, 1):
             w = np.zeros((1, 1, 3, 3))
             w[0, 0, dy + 1, dx + 1] = 1
-            y = OS.conv(x, w)
-            assert y[0, 2, 5] == x[0, 2 + dy, 5 + dx]
+            y = OS.conv(x, w, d)
+            assert y[0, 2, 5] == x[0, (2 + d * dy) % 16, (5 + d * dx) % 16]
+
+
+def test_receptive_field_of_the_dilated_stack():
+    # a unit input at one site reaches exactly the offsets |oy|, |ox| <= 9 of
+    # 1 + 2 + 2 + 4 (every offset in between) through four dilated layers
+    assert OS.DILATIONS == (1, 2, 2, 4)
+    reach = {0}
+    for d in OS.DILATIONS:
+        reach = {r + d * k for r in reach for k in (-1, 0, 1)}
+    assert reach == set(range(-9, 10))
+
+
+def test_jvp_matches_central_differences():
+    # the tangent pass is the derivative of the forward map (FP64)
+    rng = np.random.default_rng(21)
+    p = rand_params(22)
+    om = 0.01 * rng.standard_normal((3, 16, 16))
+    dom = 0.01 * rng.standard_normal((3, 16, 16))
+    h = 1e-4
+    plus = OS.densities(p, om + h * dom, 100.0, 1e-3, 0.2, 0.5)
+    minus = OS.densities(p, om - h * dom, 100.0, 1e-3, 0.2, 0.5)
+    num = (plus[:2] - minus[:2]) / (2 * h)
+    ana = OS.density_change(p, om, dom, 100.0, 1e-3)
+    assert np.abs(num - ana).max() < 1e-6 * np.abs(ana).max()
+    # linear in the field change, blind to a constant shift of omega
+    assert np.abs(OS.density_change(p, om, 3.0 * dom, 100.0, 1e-3) - 3.0 * ana).max() < 1e-12 * np.abs(ana).max()
+    const = np.ones_like(dom) * np.array([0.2, -0.1, 0.3])[:, None, None]
+    assert np.abs(OS.density_change(p, om, const, 100.0, 1e-3)).max() < 1e-14
 
 
 def test_zero_network_gives_exact_means():
