@@ -34,6 +34,9 @@ UNIT = "site·contour-steps/s"
 HBM_FALLBACK = 6800.0
 # FP32 (non-tensor) units of a GB300 at its maximum SM clock
 FP32_SMS, FP32_LANES, FP32_MHZ = 152, 128, 2070.0
+# dram__bytes_read.sum + dram__bytes_write.sum of the 8 prop_chain<9,8,16,256,1,1>
+# launches of one differential solve of the channel workload (ncu, one capture)
+CHAIN_DIFF_TRAFFIC_BYTES = 390.91e6 + 10.49e6
 
 
 def max_over_ranks(x: float, dist=None, device="cpu") -> float:
@@ -426,18 +429,12 @@ def analysis_section(torch, h, runs, flush, hbm, calls=20):
     return out
 
 
-def surrogate_section(P, W, torch, runs, h, flush, args):
-    """The learned density surrogate on the workload: trained online on exact
-    (omega, Phi) pairs streamed from the exact path (args.surrogate_pairs
-    pairs: every training step draws its batch from a replay pool of 1024
-    pairs into which the exact runs, advanced one step per training step and
-    re-seeded every 1250 steps, write their newest pairs); then the stepper
-    with the surrogate standing in (exact every 8th step, fallback above a
-    relative residual of 0.2) is timed, and its densities and velocity are
-    compared with an exact run from the same initial state after
-    args.surrogate_eval_steps steps."""
-    import numpy as np
-
+def train_surrogate(P, W, torch, runs, pairs):
+    """The learned density surrogate trained online on exact (omega, Phi)
+    pairs streamed from the exact path of `runs`: every training step draws
+    its batch from a replay pool of 1024 pairs into which the exact runs,
+    advanced one step per training step and re-seeded every 1250 steps,
+    write their newest pairs.  Returns (surrogate, s_in, s_out, info)."""
     from paper_1804_02883_gb300 import surrogate as S
 
     n_runs, (ny, nx) = len(runs), (runs[0].ny, runs[0].nx)
@@ -462,7 +459,7 @@ def surrogate_section(P, W, torch, runs, h, flush, args):
     he.sync()
     s_in, s_out = S.scales_from(om[:64].cpu().numpy(), ph[:64].cpu().numpy())
     sm = S.Surrogate(runs[0], batch, s_in=s_in, s_out=s_out, seed=5)
-    iters = max(1, args.surrogate_pairs // n_runs)
+    iters = max(1, pairs // n_runs)
     streamed = pool_n
     for it in range(iters):
         if age >= reseed:
@@ -484,28 +481,39 @@ def surrogate_section(P, W, torch, runs, h, flush, args):
         loss = sm.train_step(om[idx], ph[idx], lr=lr)
     torch.cuda.synchronize()
     he.close()
-    train_s = time.perf_counter() - t0
+    info = {"pairs_streamed": streamed, "pool": pool_n, "iterations": iters, "batch": batch,
+            "reseed_every_steps": reseed, "seconds": time.perf_counter() - t0, "final_loss": float(loss.item()),
+            "grid": f"{ny}x{nx}",
+            "network": "4 layers, 32 channels, 3x3 kernels of dilation 1, 2, 2, 4, BF16 tensor-core "
+                       "operands, FP32 accumulation; Phi(t+dt) from the tangent pass"}
+    return sm, s_in, s_out, info
+
+
+def evaluate_surrogate(P, torch, runs, sm, s_in, s_out, flush, timed_steps, eval_steps, exact_ms):
+    """The stepper with the surrogate standing in (exact every 8th step,
+    fallback above a relative residual of 0.2, the last exact force held on
+    surrogate steps) timed over timed_steps, and its densities and velocity
+    compared with an exact run from the same initial state after eval_steps
+    steps, holding the force and, for comparison, with the surrogate's own."""
+    import numpy as np
+
     tol = 0.2
-    # the stepper with the surrogate, timed
     hb = P.EpdLb(runs)
     hb.set_surrogate(sm.params, s_in, s_out, exact_every=8, residual_tol=tol, hold_force=True)
-    per, _ = time_steps(hb, hb.stream, args.surrogate_steps, flush)
+    per, _ = time_steps(hb, hb.stream, timed_steps, flush)
     hb.sync()
     hb.close()
-    # accuracy: exact and surrogate runs from the same initial state, the
-    # surrogate steps holding the last exact force (the stepper's setting
-    # timed above) and, for comparison, taking their own
     ha = P.EpdLb(runs)
-    ha.step(args.surrogate_eval_steps)
+    ha.step(eval_steps)
     ha.sync()
     acc = {}
     for hold in (True, False):
         hc = P.EpdLb(runs)
         hc.set_surrogate(sm.params, s_in, s_out, exact_every=8, residual_tol=tol, hold_force=hold)
-        hc.step(args.surrogate_eval_steps)
+        hc.step(eval_steps)
         hc.sync()
         derr, drms, verr, vrms = [], [], [], []
-        for r in range(n_runs):
+        for r in range(len(runs)):
             pa, _ = ha.densities(r)
             pc, _ = hc.densities(r)
             for c in range(2):
@@ -520,15 +528,16 @@ def surrogate_section(P, W, torch, runs, h, flush, args):
         hc.close()
     ha.close()
     derr, drms, verr, vrms, st = acc[True]
-    ms = float(np.median(per))
-    return {"ms_per_step": float(sum(per) / len(per)), "median_ms_per_step": ms, "steps": args.surrogate_steps,
+    ms = sum(per) / len(per)
+    return {"ms_per_step": ms, "median_ms_per_step": float(np.median(per)), "steps": timed_steps,
             "exact_every": 8, "residual_tol": tol,
             "residual_definition": "RMS of Phi_sur - Phi_exact over the A and B densities at omega~, relative to the RMS "
                                    "fluctuation of the exact densities, max over runs, at every exact step",
-            "value_equivalent": units_per_step(runs) / (sum(per) / len(per) * 1e-3),
+            "value_equivalent": units_per_step(runs) / (ms * 1e-3),
+            "speedup_vs_exact_mixed": exact_ms / ms,
             "density_error_vs_exact": max(derr), "density_rms_error_vs_exact": max(drms),
             "velocity_error_vs_exact": max(verr) if verr else None,
-            "velocity_rms_error_vs_exact": max(vrms) if vrms else None, "eval_steps": args.surrogate_eval_steps,
+            "velocity_rms_error_vs_exact": max(vrms) if vrms else None, "eval_steps": eval_steps,
             "velocity_error_per_run": verr, "force": "held from the last exact step on surrogate steps",
             "with_surrogate_force": {"density_error_vs_exact": max(acc[False][0]),
                                      "velocity_error_vs_exact": max(acc[False][2]) if acc[False][2] else None,
@@ -536,11 +545,59 @@ def surrogate_section(P, W, torch, runs, h, flush, args):
             "eval_stats": st,
             "density_error_definition": "max |Phi_sur - Phi_exact| / max |Phi_exact - <Phi_exact>| over runs and the A, B "
                                         "species after eval_steps steps, both runs from the same initial state (velocity: "
-                                        "the same with u, relative to max |u|)",
-            "training": {"pairs_streamed": streamed, "pool": pool_n, "iterations": iters, "batch": batch,
-                         "reseed_every_steps": reseed, "seconds": train_s, "final_loss": float(loss.item()),
-                         "network": "4 layers, 32 channels, 3x3 kernels of dilation 1, 2, 2, 4, BF16 tensor-core "
-                                    "operands, FP32 accumulation; Phi(t+dt) from the tangent pass"}}
+                                        "the same with u, relative to max |u|)"}
+
+
+def surrogate_section(P, W, torch, runs, flush, args, exact_ms):
+    """The surrogate on the workload: trained on the workload's own runs
+    (args.surrogate_pairs streamed pairs), evaluated on them."""
+    sm, s_in, s_out, info = train_surrogate(P, W, torch, runs, args.surrogate_pairs)
+    out = evaluate_surrogate(P, torch, runs, sm, s_in, s_out, flush, args.surrogate_steps, args.surrogate_eval_steps,
+                             exact_ms)
+    out["training"] = info
+    return out
+
+
+def config_section(P, W, torch, name, flush, args, rank):
+    """Another configuration of the benchmark set, measured as the headline
+    line: CUDA-event ms per step over args.config_steps steps (L2 flushed
+    before each), the rates, the FP64-plain path over 2 steps and the MIXED
+    path's error against it after them; the vesicle configuration also runs
+    the surrogate, trained on 256 x 512 grids with its parameters (the
+    network is a local operator of +-9 sites, so it carries over to the
+    large grid) and evaluated on the 1024 x 2048 run."""
+    import numpy as np
+
+    runs = workload_runs(name, P.MIXED_FP32, rank)
+    h = P.EpdLb(runs)
+    h.step(2)
+    h.sync()
+    per, _ = time_steps(h, h.stream, args.config_steps, flush)
+    h.close()
+    ms = sum(per) / len(per)
+    out = {"workload": WORKLOADS[name], "ms_per_step": ms, "value": units_per_step(runs) / (ms * 1e-3), "unit": UNIT,
+           "lb_mlups": sites_per_step(runs) / (ms * 1e-3) / 1e6, "steps": args.config_steps}
+    runs64 = workload_runs(name, P.PLAIN_FP64, rank)
+    h64 = P.EpdLb(runs64)
+    h64.step(1)
+    h64.sync()
+    per64, _ = time_steps(h64, h64.stream, 2, flush)
+    ms64 = sum(per64) / len(per64)
+    out["fp64_plain"] = {"ms_per_step": ms64, "value": units_per_step(runs64) / (ms64 * 1e-3), "steps": 2}
+    out["speedup_vs_fp64_plain"] = ms64 / ms
+    hm = P.EpdLb(runs)
+    hm.step(3)
+    out["mixed_error"] = precision_errors(hm, h64, len(runs), np)
+    out["mixed_error"]["steps"] = 3
+    hm.close()
+    h64.close()
+    if name == "vesicle" and args.surrogate_pairs > 0:
+        train_runs = [W.with_(runs[0], nx=512, ny=256, seed=runs[0].seed + 31 * k) for k in range(4)]
+        sm, s_in, s_out, info = train_surrogate(P, W, torch, train_runs, args.config_surrogate_pairs)
+        sur = evaluate_surrogate(P, torch, runs, sm, s_in, s_out, flush, args.config_steps, args.config_eval_steps, ms)
+        sur["training"] = info
+        out["surrogate"] = sur
+    return out
 
 
 def exact_section(P, runs, flush, args):
@@ -578,6 +635,11 @@ def main():
                     help="exact (omega, Phi) pairs streamed through the surrogate's training (0 skips the surrogate)")
     ap.add_argument("--surrogate-eval-steps", type=int, default=1000,
                     help="steps after which the surrogate-driven run is compared with the exact run")
+    ap.add_argument("--configs", default="ensemble32,vesicle",
+                    help="other configurations measured into the line's configs key (comma list; empty: none)")
+    ap.add_argument("--config-steps", type=int, default=5)
+    ap.add_argument("--config-surrogate-pairs", type=int, default=16000)
+    ap.add_argument("--config-eval-steps", type=int, default=200)
     ap.add_argument("--exact-steps", type=int, default=5,
                     help="steps of the exact step (CG inversion) timed on the same workload; 0 skips it")
     ap.add_argument("--workload", default="channel", choices=sorted(WORKLOADS),
@@ -651,10 +713,12 @@ def main():
         tf = flops / (kt["prop_cluster"] * 1e-3) / 1e12
         peak_tf = FP32_SMS * FP32_LANES * 2 * FP32_MHZ * 1e6 / 1e12
         kernels["prop_cluster"] = {"ms": kt["prop_cluster"], "flops": flops, "achieved_tflops": tf, "frac": tf / peak_tf}
-        # DRAM bytes of the current kernel version: no ncu capture of the
-        # phased chain schedule yet
-        traffic = None
+        # DRAM bytes (read + write) of the differential solve's chain launches
+        # on this workload, from one ncu capture of the current kernels
+        # (profiles/cluster_solve_channel_4x256x512_mixed.md): 8 phased
+        # launches of 4 x 256 x 512, N_s = 64
         launches = h.tiles(0)["chain_launches"]
+        traffic = CHAIN_DIFF_TRAFFIC_BYTES if (args.workload == "channel" and launches == 8) else None
         roofline = {"bound": "alu", "kernel": f"prop_chain (the step's second, differential single-chain solve of all "
                                               f"runs; {launches} launch(es) timed together)", "achieved": tf,
                     "peak": peak_tf, "unit": "TFLOP/s", "frac": tf / peak_tf, "traffic": traffic,
@@ -711,7 +775,7 @@ def main():
     # learned surrogate (exact every 8th step) on the same workload
     sur = None
     if args.surrogate_steps > 0 and args.surrogate_pairs > 0 and all(r.nx % 16 == 0 and r.ny % 8 == 0 for r in runs) and len({(r.nx, r.ny) for r in runs}) == 1:
-        sur = surrogate_section(P, W, torch, runs, h, flush, args)
+        sur = surrogate_section(P, W, torch, runs, flush, args, ms_per_step)
     # FP64-plain path on the same workload
     h.close()
     del h
@@ -744,8 +808,13 @@ def main():
         h64.close()
 
     if sur is not None:
-        sur["speedup_vs_exact_mixed"] = ms_per_step / sur["ms_per_step"]
         sur["speedup_vs_fp64_plain"] = fp64["ms_per_step"] / sur["ms_per_step"] if fp64 else None
+    configs = {}
+    for name in [c for c in args.configs.split(",") if c and c != args.workload]:
+        try:
+            configs[name] = config_section(P, W, torch, name, flush, args, rank)
+        except Exception as ex:  # a side configuration never costs the line
+            configs[name] = {"unavailable": f"{type(ex).__name__}: {ex}"[:200]}
     line = None
     if rank == 0:
         cpu = None
@@ -772,6 +841,7 @@ def main():
             "kernels": kernels,
             "roofline": roofline,
             "surrogate": sur,
+            "configs": configs,
             "exact_step": exact,
             "analysis": analysis,
             "cufft_comparison": cufft,
