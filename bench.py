@@ -774,7 +774,7 @@ def main():
 
     # learned surrogate (exact every 8th step) on the same workload
     sur = None
-    if args.surrogate_steps > 0 and args.surrogate_pairs > 0 and all(r.nx % 16 == 0 and r.ny % 8 == 0 for r in runs) and len({(r.nx, r.ny) for r in runs}) == 1:
+    if args.surrogate_steps > 0 and args.surrogate_pairs > 0 and all(r.nx % 16 == 0 and r.ny % 16 == 0 for r in runs) and len({(r.nx, r.ny) for r in runs}) == 1:
         sur = surrogate_section(P, W, torch, runs, flush, args, ms_per_step)
     # FP64-plain path on the same workload
     h.close()

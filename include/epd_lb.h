@@ -245,7 +245,7 @@ int epd_lb_tiles(epd_lb *h, int32_t run, int32_t *out);
  * accumulate in FP32.  Fields are [batch][species][ny][nx] FP64 on the device;
  * every call is asynchronous on cuda_stream; the workspace is caller-owned
  * device memory of epd_sur_workspace_bytes (training = 1 for the gradient and
- * training calls).  nx must be a multiple of 16 and ny of 8.
+ * training calls).  nx and ny must be multiples of 16.
  */
 int32_t epd_sur_num_params(void);
 int epd_sur_workspace_bytes(int32_t ny, int32_t nx, int32_t batch, int32_t training, size_t *bytes);

@@ -1616,14 +1616,14 @@ extern "C" int epd_prop_solve_noalloc(const epd_lb_params *p, const double *omeg
 
 static bool sur_shape_ok(const epd_lb_params *p, int batch)
 {
-    return p && validate(*p).empty() && batch > 0 && p->nx % 16 == 0 && p->ny % 8 == 0;
+    return p && validate(*p).empty() && batch > 0 && p->nx % 16 == 0 && p->ny % 16 == 0;
 }
 
 extern "C" int32_t epd_sur_num_params(void) { return sur::num_params(); }
 
 extern "C" int epd_sur_workspace_bytes(int32_t ny, int32_t nx, int32_t batch, int32_t training, size_t *bytes)
 {
-    if (!bytes || batch <= 0 || nx % 16 || ny % 8 || nx <= 0 || ny <= 0) return EPD_LB_EINVAL;
+    if (!bytes || batch <= 0 || nx % 16 || ny % 16 || nx <= 0 || ny <= 0) return EPD_LB_EINVAL;
     sur::Work w;
     *bytes = sur::carve(w, nullptr, batch, ny, nx, training != 0);
     return EPD_LB_OK;
@@ -1707,7 +1707,7 @@ extern "C" int epd_lb_surrogate_workspace_bytes(epd_lb *h, size_t *bytes)
 {
     if (!h || !bytes) return EPD_LB_EINVAL;
     for (auto &G : h->groups)
-        if (G.g.nx % 16 || G.g.ny % 8) return fail(h, EPD_LB_EINVAL, "the surrogate needs nx % 16 == 0 and ny % 8 == 0");
+        if (G.g.nx % 16 || G.g.ny % 16) return fail(h, EPD_LB_EINVAL, "the surrogate needs nx % 16 == 0 and ny % 16 == 0");
     *bytes = handle_sur_bytes(h);
     return EPD_LB_OK;
 }
@@ -1736,6 +1736,7 @@ extern "C" int epd_lb_set_surrogate(epd_lb *h, const float *params_host, double 
     for (size_t gi = 0; gi < h->groups.size(); ++gi) {
         Group &G = h->groups[gi];
         const size_t b = sur::carve(h->sur_work[gi], base + off, G.g.nruns, G.g.ny, G.g.nx, false);
+        h->sur_work[gi].err = h->err;  // epd_lb_sync reports a convolution that gave up a wait
         off = align_up(off + b);
     }
     CK(cudaMemcpyAsync(h->sur_params, params_host, (size_t)sur::num_params() * sizeof(float), cudaMemcpyHostToDevice, h->stream),

@@ -13,14 +13,15 @@
 //   means (Sec. 2, Eqs. (9)-(10) conserve them); Phi_S is the exact local
 //   expression of Eq. (11).
 //
-// Every convolution is an implicit GEMM on mma.sync m16n8k16 (BF16 inputs,
-// FP32 accumulation): activations are NHWC BF16 with the channel count padded
-// to a multiple of 16, a CTA computes an 8 x 16 pixel tile for all output
-// channels from a shared-memory halo tile, K runs over taps x input channels.
-// The input gradient is the same convolution of the output gradient with the
-// flipped, transposed weights; the weight gradient is a GEMM over pixels per
-// tap.  Rounding to BF16 happens where the tensor cores read: weights,
-// activations and the output gradients.
+// Every convolution is an implicit GEMM with BF16 operands and FP32
+// accumulation on activations stored NHWC in BF16 (channels padded to a
+// multiple of 16).  The forward layers, the input gradient (the same
+// convolution of the output gradient with flipped, transposed weights) and
+// the tangent pass run on tcgen05 (conv3x3_tc: a 16 x 8 pixel tile per CTA,
+// M = 128, the accumulator in TMEM); the weight gradient, a GEMM over pixels
+// per tap, runs on mma.sync m16n8k16 (conv3x3_dw).  Rounding to BF16 happens
+// where the tensor cores read: weights, activations and the output
+// gradients.
 //
 // Tangent pass: the change of Phi_A, Phi_B for a small field change domega
 // at omega is the network's directional derivative (forward mode):
@@ -77,95 +78,205 @@ struct ConvArgs {
     float *out_f;               // [b][y][x][NP] FP32 output (EP_TANH when training, EP_LINEAR)
     const float *yprev;         // EP_DX: tanh output of the layer below, [b][y][x][NP] FP32
     const __nv_bfloat16 *ycur;  // EP_JVP: this layer's tanh output, [b][y][x][NP] BF16
+    int *err;                   // bit 2: a bounded wait of the tensor-core kernel gave up
     int nx, ny, logx, logy, nb;
     int nreal;                  // output channels actually used (the rest are written as 0)
 };
 
-// One 8 x 16 pixel tile, all NP output channels; 4 warps, warp w owns pixel
-// rows 2w and 2w+1 (two m16 tiles).  KP, NP multiples of 16 and 8; D the
-// dilation (taps at offsets -D, 0, +D).  Dynamic shared memory: conv_smem.
-template <int KP, int NP, int D>
-constexpr size_t conv_smem() { return ((size_t)Halo<D>::HH * Halo<D>::HW + 9 * NP) * (KP + 8) * 2; }
-template <int KP, int NP, int MODE, int D>
-__global__ void __launch_bounds__(128) conv3x3(ConvArgs a)
+// ---------------------------------------------------------------------------
+// Convolution on the 5th-generation tensor cores (tcgen05, TMEM): forward
+// layers, input gradients and the tangent pass.
+//
+// A CTA of 4 warps computes a 16 x 8 pixel tile (M = 128 rows of the
+// implicit GEMM) for all output channels (N = 32, or 16 for the output
+// layer's 8 stored channels), K = 9 taps x the input channels in steps of 16.
+// Operands are read by the tensor cores from shared memory in the canonical
+// K-major layout without swizzle: core matrices of 8 rows x 16 bytes (8
+// channels), the halo tile stored as one plane per 8 input channels
+// ([c8][halo pixel][8 channels]), so that for tap (dy, dx) the 8 pixels of an
+// output row are one core matrix and consecutive output rows are a halo row
+// apart (stride-byte offset), consecutive channel planes a plane apart
+// (leading-byte offset); the weights as [tap][c8][co][8 channels].  One
+// thread issues the 9 KP / 16 MMAs into a TMEM accumulator (32 columns) and
+// commits them to an mbarrier; every warp then reads its 32 TMEM lanes (one
+// pixel per thread, all channels) for the epilogue of the layer's mode.
+// ---------------------------------------------------------------------------
+
+constexpr int TCH = 16, TCW = 8;  // tensor-core pixel tile (rows x columns)
+template <int D> struct HaloTC {
+    static constexpr int HH = TCH + 2 * D, HW = TCW + 2 * D;
+};
+
+// Shared memory of the tcgen05 convolution: halo planes, then weights.
+template <int KP, int NP, int D> struct ConvTC {
+    static constexpr int N = NP < 16 ? 16 : NP;  // MMA N (multiple of 16 for M = 128)
+    static constexpr int C8 = KP / 8;
+    static constexpr int HW16 = HaloTC<D>::HW * 16;
+    static constexpr int PLANE = HaloTC<D>::HH * HW16;  // bytes per 8-channel plane
+    static constexpr int HALO = C8 * PLANE, WB = 9 * C8 * N * 16;
+    // the furthest byte a descriptor walk reaches (16 core matrices along M,
+    // 2 along K) lies inside the halo planes
+    static_assert((KP / 16 - 1) * 2 * PLANE + (2 * D * HaloTC<D>::HW + 2 * D) * 16 + 15 * HW16 + PLANE + 128 <= HALO,
+                  "A operand walk inside the halo tile");
+    static constexpr int AOFF = (HALO + 1023) / 1024 * 1024;
+    static constexpr size_t SMEM = (size_t)AOFF + WB;
+};
+
+// Shared-memory matrix descriptor: start, leading-byte offset (between core
+// matrices along K), stride-byte offset (along M or N), all >> 4; bit 46 the
+// descriptor version of this architecture; no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
 {
-    constexpr int KS = KP + 8;  // padded channel stride in shared memory (halves)
-    constexpr int HH = Halo<D>::HH, HW = Halo<D>::HW;
-    extern __shared__ __align__(16) unsigned char conv_raw[];
-    __nv_bfloat16 *tile = reinterpret_cast<__nv_bfloat16 *>(conv_raw);
-    __nv_bfloat16 *wsm = tile + HH * HW * KS;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const long long n = (long long)a.nx * a.ny;
-    // weights once per CTA; the CTA then walks over pixel tiles
-    for (int e = tid; e < 9 * NP * (KP / 8); e += 128) {
-        const int row = e / (KP / 8), ch = (e % (KP / 8)) * 8;
-        *reinterpret_cast<uint4 *>(&wsm[row * KS + ch]) = *reinterpret_cast<const uint4 *>(&a.w[(size_t)row * KP + ch]);
-    }
-    const int tiles_x = a.nx / TW, tiles_img = tiles_x * (a.ny / TH);
-    for (int tix = blockIdx.x; tix < tiles_img * a.nb; tix += gridDim.x) {
-    const int b = tix / tiles_img, rr = tix % tiles_img;
-    const int tx0 = (rr % tiles_x) * TW, ty0 = (rr / tiles_x) * TH;
-    const __nv_bfloat16 *in = a.in + (size_t)b * n * KP;
-    __syncthreads();  // the previous tile's reads of `tile` are done
-    // halo tile with circular wrap, 16-byte chunks of channels
-    for (int e = tid; e < HH * HW * (KP / 8); e += 128) {
-        const int pix = e / (KP / 8), ch = (e % (KP / 8)) * 8;
-        const int hy = pix / HW, hx = pix % HW;
-        const int gy = halo_wrap(ty0 + hy - D, a.ny), gx = halo_wrap(tx0 + hx - D, a.nx);
-        *reinterpret_cast<uint4 *>(&tile[pix * KS + ch]) = *reinterpret_cast<const uint4 *>(&in[((size_t)gy * a.nx + gx) * KP + ch]);
-    }
-    __syncthreads();
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t mma_idesc(int m, int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
 
-    const int g = lane >> 2, t = lane & 3;
-    float acc[2][NP / 8][4];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < NP / 8; ++nt)
-#pragma unroll
-            for (int i = 0; i < 4; ++i) acc[mt][nt][i] = 0.f;
 
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-        const int dy = (tap / 3) * D, dx = (tap % 3) * D;  // halo offsets 0, D, 2D (i.e. -D, 0, +D)
-#pragma unroll
-        for (int kc = 0; kc < KP / 16; ++kc) {
-            uint32_t af[2][4];
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const int py = 2 * warp + mt;  // pixel row in the tile
-                const int p0 = ((py + dy) * HW + g + dx) * KS + kc * 16 + 2 * t;
-                const int p1 = ((py + dy) * HW + g + 8 + dx) * KS + kc * 16 + 2 * t;
-                af[mt][0] = *reinterpret_cast<const uint32_t *>(&tile[p0]);
-                af[mt][1] = *reinterpret_cast<const uint32_t *>(&tile[p1]);
-                af[mt][2] = *reinterpret_cast<const uint32_t *>(&tile[p0 + 8]);
-                af[mt][3] = *reinterpret_cast<const uint32_t *>(&tile[p1 + 8]);
-            }
-#pragma unroll
-            for (int nt = 0; nt < NP / 8; ++nt) {
-                uint32_t bf[2];
-                const int q = (tap * NP + nt * 8 + g) * KS + kc * 16 + 2 * t;
-                bf[0] = *reinterpret_cast<const uint32_t *>(&wsm[q]);
-                bf[1] = *reinterpret_cast<const uint32_t *>(&wsm[q + 8]);
-#pragma unroll
-                for (int mt = 0; mt < 2; ++mt) mma16816(acc[mt][nt], af[mt], bf);
-            }
+// Bounded wait for the phase with the given parity of a CTA-local mbarrier
+// (about 2^28 cycles); sets failed on giving up.
+__device__ __forceinline__ void mbar_wait_tc(uint32_t bar, unsigned parity, int &failed)
+{
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t ok;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(ok)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+        if (ok) return;
+        if (clock64() - t0 > (1ll << 28)) {
+            failed = 1;
+            return;
         }
     }
+}
 
-    // epilogue: rows g (c0, c1) and g + 8 (c2, c3) of each m tile, channels 2t, 2t+1
+// N FP32 accumulator columns of this thread's TMEM lane (32x32b shape: warp w
+// reads lanes 32 w .. 32 w + 31 of the address' lane field).
+template <int N> __device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[N]);
+template <> __device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+                   "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr)
+                 : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-        const int py = ty0 + 2 * warp + mt;
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+template <> __device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, float (&v)[32])
+{
+    float lo[16], hi[16];
+    tmem_ld<16>(taddr, lo);
+    tmem_ld<16>(taddr + 16, hi);
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const int px = tx0 + g + 8 * half;
+    for (int i = 0; i < 16; ++i) {
+        v[i] = lo[i];
+        v[16 + i] = hi[i];
+    }
+}
+
+template <int KP, int NP, int MODE, int D>
+__global__ void __launch_bounds__(128) conv3x3_tc(ConvArgs a)
+{
+    using Geo = ConvTC<KP, NP, D>;
+    constexpr int HH = HaloTC<D>::HH, HW = HaloTC<D>::HW, C8 = Geo::C8, N = Geo::N;
+    extern __shared__ __align__(1024) unsigned char tc_raw[];
+    unsigned char *halo = tc_raw;               // [c8][HH*HW][16 B]
+    unsigned char *wsm = tc_raw + Geo::AOFF;    // [tap][c8][N][16 B]
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long n = (long long)a.nx * a.ny;
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&mbar);
+    // weights once per CTA: row co (zero beyond NP), 8 channels per 16 bytes
+    for (int e = tid; e < 9 * C8 * N; e += 128) {
+        const int tap = e / (C8 * N), c8 = (e / N) % C8, co = e % N;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (co < NP) v = *reinterpret_cast<const uint4 *>(&a.w[((size_t)tap * NP + co) * KP + c8 * 8]);
+        *reinterpret_cast<uint4 *>(wsm + ((size_t)(tap * C8 + c8) * N + co) * 16) = v;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(&tmem_base))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    const uint32_t halo_s = (uint32_t)__cvta_generic_to_shared(halo), w_s = (uint32_t)__cvta_generic_to_shared(wsm);
+    constexpr uint32_t IDESC = mma_idesc(128, N);
+    const int tiles_x = a.nx / TCW, tiles_img = tiles_x * (a.ny / TCH);
+    unsigned phase = 0;
+    bool failed = false;
+    for (int tix = blockIdx.x; tix < tiles_img * a.nb && !failed; tix += gridDim.x) {
+        const int b = tix / tiles_img, rr = tix % tiles_img;
+        const int tx0 = (rr % tiles_x) * TCW, ty0 = (rr / tiles_x) * TCH;
+        const __nv_bfloat16 *in = a.in + (size_t)b * n * KP;
+        // halo tile with circular wrap into the channel planes
+        for (int e = tid; e < HH * HW * C8; e += 128) {
+            const int c8 = e % C8, pix = e / C8, hy = pix / HW, hx = pix % HW;
+            const int gy = halo_wrap(ty0 + hy - D, a.ny), gx = halo_wrap(tx0 + hx - D, a.nx);
+            *reinterpret_cast<uint4 *>(halo + (size_t)c8 * Geo::PLANE + (size_t)pix * 16) =
+                *reinterpret_cast<const uint4 *>(&in[((size_t)gy * a.nx + gx) * KP + c8 * 8]);
+        }
+        // generic-proxy writes visible to the tensor cores (async proxy)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap) {
+                const int dy = (tap / 3) * D, dx = (tap % 3) * D;
+#pragma unroll
+                for (int kc = 0; kc < KP / 16; ++kc) {
+                    const uint64_t ad = smem_desc(halo_s + 2 * kc * Geo::PLANE + (uint32_t)(dy * HW + dx) * 16, Geo::PLANE, HW * 16);
+                    const uint64_t bd = smem_desc(w_s + (uint32_t)((tap * C8 + 2 * kc) * N * 16), N * 16, 128);
+                    const uint32_t acc = (tap | kc) ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
+                        : "memory");
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+        }
+        // the MMAs are done (bounded wait; the CTA leaves the tile loop
+        // together if any thread gave up)
+        {
+            int f = 0;
+            mbar_wait_tc(bar, phase, f);
+            failed = __syncthreads_or(f) != 0;
+        }
+        if (!failed) phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!failed) {
+            // thread = TMEM lane = pixel p (row p / 8, column p % 8) of the tile
+            float v[N];
+            const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
+            tmem_ld<N>(taddr, v);
+            const int p = 32 * warp + lane, py = ty0 + p / TCW, px = tx0 + p % TCW;
             const size_t pix = (size_t)b * n + (size_t)py * a.nx + px;
 #pragma unroll
-            for (int nt = 0; nt < NP / 8; ++nt) {
-                const int c = nt * 8 + 2 * t;
-                float v0 = acc[mt][nt][2 * half], v1 = acc[mt][nt][2 * half + 1];
-                if (MODE != EP_DX && a.bias) {
+            for (int c = 0; c < NP; c += 2) {
+                float v0 = v[c], v1 = v[c + 1];
+                if (MODE != EP_DX && MODE != EP_JVP && a.bias) {
                     if (c < a.nreal) v0 += a.bias[c];
                     if (c + 1 < a.nreal) v1 += a.bias[c + 1];
                 }
@@ -173,12 +284,10 @@ __global__ void __launch_bounds__(128) conv3x3(ConvArgs a)
                     v0 = tanhf(v0);
                     v1 = tanhf(v1);
                 } else if (MODE == EP_DX) {
-                    // dZ of the layer below: dY (1 - y^2)
                     const float2 yp = *reinterpret_cast<const float2 *>(&a.yprev[pix * NP + c]);
                     v0 *= 1.f - yp.x * yp.x;
                     v1 *= 1.f - yp.y * yp.y;
                 } else if (MODE == EP_JVP) {
-                    // tangent of this tanh layer: (W * dy) (1 - y^2)
                     const float y0 = __bfloat162float(a.ycur[pix * NP + c]), y1 = __bfloat162float(a.ycur[pix * NP + c + 1]);
                     v0 *= 1.f - y0 * y0;
                     v1 *= 1.f - y1 * y1;
@@ -190,8 +299,20 @@ __global__ void __launch_bounds__(128) conv3x3(ConvArgs a)
                 if (a.out_f) *reinterpret_cast<float2 *>(&a.out_f[pix * NP + c]) = make_float2(v0, v1);
             }
         }
+        // every thread has read the accumulator and the MMAs no longer read
+        // the halo tile: the next tile may overwrite both
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
+    if (failed) {
+        if (tid == 0 && a.err) atomicOr(a.err, 4);
+        // the MMAs of the abandoned tile: wait for them once more (bounded)
+        int f = 0;
+        mbar_wait_tc(bar, phase, f);
+        __syncthreads();
     }
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
 }
 
 // Weight gradient of one layer: dW[tap][co][ci] = sum_p dZ[p][co] x[p + off(tap)][ci]
@@ -550,6 +671,7 @@ size_t carve(Work &w, char *base, int nb, int ny, int nx, bool training)
         off += bytes;
         return p;
     };
+    w.err = (int *)take(256);
     w.x0 = take(np * 16 * 2);
     for (int l = 0; l < 3; ++l) w.y[l] = take(np * 32 * 2);
     w.y4 = take(np * 8 * 4);
@@ -618,14 +740,15 @@ template <int KP, int NP, int MODE, int D>
 static void conv(Work &w, const void *in, const void *wt, const float *bias, void *out_bf, float *out_f, const float *yprev, int nreal,
                  cudaStream_t s, const void *ycur = nullptr)
 {
-    constexpr size_t smem = conv_smem<KP, NP, D>();
+    constexpr size_t smem = ConvTC<KP, NP, D>::SMEM;
     static std::atomic<bool> conf{false};  // attribute set (idempotent if two threads race)
     if (!conf) {
-        cudaFuncSetAttribute(conv3x3<KP, NP, MODE, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(conv3x3_tc<KP, NP, MODE, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         conf = true;
     }
     ConvArgs a;
     a.ycur = reinterpret_cast<const __nv_bfloat16 *>(ycur);
+    a.err = w.err;
     a.in = reinterpret_cast<const __nv_bfloat16 *>(in);
     a.w = reinterpret_cast<const __nv_bfloat16 *>(wt);
     a.bias = bias;
@@ -638,8 +761,9 @@ static void conv(Work &w, const void *in, const void *wt, const float *bias, voi
     a.logy = ilog2(w.ny);
     a.nreal = nreal;
     a.nb = w.nb;
-    const int tiles = w.nb * (w.nx / TW) * (w.ny / TH);
-    conv3x3<KP, NP, MODE, D><<<std::min(tiles, 8 * 152), 128, smem, s>>>(a);
+    const int tiles = w.nb * (w.nx / TCW) * (w.ny / TCH);
+    const int per_sm = std::max(1, (int)((200u << 10) / smem));
+    conv3x3_tc<KP, NP, MODE, D><<<std::min(tiles, per_sm * 152), 128, smem, s>>>(a);
 }
 
 static cudaError_t forward_layers(Work &w, const float *params, cudaStream_t s)

@@ -27,6 +27,7 @@ struct Work {
     void *x0, *y[3], *y4, *yf[3], *dz[2], *dz4;
     void *t0, *t[2], *t4;  // tangent pass: input, hidden tangents (BF16), output (FP32)
     double *means2;
+    int *err;              // device error word: bit 2 = a bounded wait of a convolution gave up
     void *wf[kLayers], *wb[kLayers];
     float *dwpart, *grad;
     double *means, *ymean, *qs, *tmean, *lpart, *red;

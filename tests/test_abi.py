@@ -80,6 +80,7 @@ def test_empty_and_null_arguments_rejected():
     assert _rc("epd_sur_workspace_bytes", 32, 64, 0, 0, ctypes.byref(n)) == -1
     assert _rc("epd_sur_workspace_bytes", 32, 40, 1, 0, ctypes.byref(n)) == -1
     assert _rc("epd_sur_workspace_bytes", 36, 64, 1, 0, ctypes.byref(n)) == -1
+    assert _rc("epd_sur_workspace_bytes", 24, 64, 1, 0, ctypes.byref(n)) == -1  # ny a multiple of 16
     assert _rc("epd_sur_workspace_bytes", 32, 64, 1, 0, None) == -1
     assert _rc("epd_lb_surrogate_workspace_bytes", None, ctypes.byref(n)) == -1
     assert n.value == 7
