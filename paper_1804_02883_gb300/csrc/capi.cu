@@ -62,8 +62,15 @@ size_t carve_group(Group &G, char *base, size_t off)
     G.f0_bulk = take(R * tb);
     G.stage = (double *)take(std::max<size_t>(9 * n, 2 * R + 16) * sizeof(double));
     G.chain = take(R * n * 2 * tb);
+    // (decided from the parameters, not from a pointer: the dry run that
+    // sizes the workspace carves with null pointers)
+    const bool cluster = G.prec == EPD_LB_MIXED_FP32 && G.g.pow2 && cluster_shape_exists(G.g.logx, G.g.logy);
+    // MIXED streaming solves keep every node of the reference history for
+    // the differential second solve
+    const bool stream_diff = G.prec == EPD_LB_MIXED_FP32 && !cluster;
     G.hist_full = G.g.pow2 && stream8_eligible(G.prec, G.g.logx, G.g.logy);
-    G.hist = take(R * (size_t)(G.hist_full ? G.g.ns + 1 : G.g.half_lo + 1) * n * 2 * tb);
+    G.hnodes = stream_diff ? G.g.ns + 1 : G.g.half_lo + 1;
+    G.hist = take(R * (size_t)G.hnodes * n * 2 * tb);
     G.efac = take(R * n * 2 * tb);
     G.pop[0] = take(R * 9 * n * tb);
     G.pop[1] = take(R * 9 * n * tb);
@@ -86,24 +93,25 @@ size_t carve_group(Group &G, char *base, size_t off)
         G.tab16y = best_mr(G.g.logy) == 4 ? (float2 *)take((size_t)tabs_total(G.g.logy, 4) * sizeof(float2)) : nullptr;
     }
     // cluster solve (MIXED_FP32): stored states of both chains, and the
-    // differential second solve's buffers
+    // differential second solve's buffers; streaming MIXED solves: the
+    // changes at every node and the factor changes
     G.hc = G.hd = G.rho = G.cdiff = nullptr;
-    // (decided from the parameters, not from a pointer: the dry run that
-    // sizes the workspace carves with null pointers)
-    const bool cluster = G.prec == EPD_LB_MIXED_FP32 && G.g.pow2 && cluster_shape_exists(G.g.logx, G.g.logy);
     if (cluster) {
         const size_t hs = R * cluster_state_floats2(G.g.nx, G.g.ny, G.g.ns) * sizeof(float2);
         G.hc = take(hs);
         G.hd = take(hs);
         G.rho = take(R * n * sizeof(float2));
         G.cdiff = take(R * 3 * n * sizeof(float));
+    } else if (stream_diff) {
+        G.hd = take(R * (size_t)(G.g.ns + 1) * n * sizeof(float2));
+        G.rho = take(R * n * sizeof(float2));
     }
     // exact step: the inversion's fields and scalars
     G.cg_target = (double *)take(R * 3 * n * sizeof(double));
     G.cg_dir = (double *)take(R * 3 * n * sizeof(double));
     G.cg_trial = (double *)take(R * 3 * n * sizeof(double));
     G.cg_wref = G.cg_pref = nullptr;
-    if (cluster) {
+    if (cluster || stream_diff) {
         G.cg_wref = (double *)take(R * 3 * n * sizeof(double));
         G.cg_pref = (double *)take(R * 3 * n * sizeof(double));
     }
@@ -136,7 +144,7 @@ static Group run_view(const Group &G, int r)
     V.f0_lat += r;
     V.f0_bulk = (char *)V.f0_bulk + (size_t)r * tb;
     V.chain = (char *)V.chain + (size_t)r * n * 2 * tb;
-    V.hist = (char *)V.hist + (size_t)r * (G.hist_full ? G.g.ns + 1 : G.g.half_lo + 1) * n * 2 * tb;
+    V.hist = (char *)V.hist + (size_t)r * G.hnodes * n * 2 * tb;
     V.efac = (char *)V.efac + (size_t)r * n * 2 * tb;
     V.pop[0] = (char *)V.pop[0] + (size_t)r * 9 * n * tb;
     V.pop[1] = (char *)V.pop[1] + (size_t)r * 9 * n * tb;
@@ -148,6 +156,11 @@ static Group run_view(const Group &G, int r)
         V.hd = (char *)V.hd + (size_t)r * hs;
         V.rho = (char *)V.rho + (size_t)r * n * sizeof(float2);
         V.cdiff = (char *)V.cdiff + (size_t)r * 3 * n * sizeof(float);
+    } else if (G.hd) {
+        V.hd = (char *)V.hd + (size_t)r * (G.g.ns + 1) * n * sizeof(float2);
+        V.rho = (char *)V.rho + (size_t)r * n * sizeof(float2);
+    }
+    if (G.cg_wref) {
         V.cg_wref += (size_t)r * 3 * n;
         V.cg_pref += (size_t)r * 3 * n;
     }
@@ -677,7 +690,9 @@ extern "C" int epd_lb_init(const epd_lb_params *p, int32_t nruns, void *workspac
         if (launch_solve(G, G.omega, G.phi, G.q, h->stream) != cudaSuccess) return bail(EPD_LB_ECUDA);
         if (tune_column_tiles(G, h->stream) != cudaSuccess) return bail(EPD_LB_ECUDA);
         if (tune_stream_tiles(G, h->stream) != cudaSuccess) return bail(EPD_LB_ECUDA);
-        G.diff = G.hd != nullptr && G.twx_full != nullptr && cluster_solve_supported(G);
+        // cluster grids: when the cluster solve launches; MIXED streaming
+        // grids always
+        G.diff = G.hd != nullptr && (G.hc ? G.twx_full != nullptr && cluster_solve_supported(G) : true);
     }
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(EPD_LB_ECUDA);
     for (size_t gi = 1; gi < h->groups.size(); ++gi) {
@@ -767,7 +782,7 @@ extern "C" int epd_lb_set_inversion(epd_lb *h, int32_t max_iter, double tol)
         for (const Group &G : h->groups)
             if (G.prec != EPD_LB_PLAIN_FP64 && !G.diff)
                 return fail(h, EPD_LB_EINVAL,
-                            "the exact step needs PLAIN_FP64 or a MIXED_FP32 grid with the cluster-resident solve");
+                            "the exact step needs PLAIN_FP64 or a MIXED_FP32 grid with the differential solve");
         if (!h->cg_host) {
             size_t mr = 1;
             for (const Group &G : h->groups) mr = std::max(mr, (size_t)G.g.nruns);
@@ -1248,7 +1263,8 @@ static size_t carve_solve(Group &G, char *base)
     G.part = (double *)take(kMaxPart * sizeof(double));
     G.f0_lat = (double *)take(sizeof(double));
     G.chain = take(n * 2 * tb);
-    G.hist = take((size_t)(G.g.half_lo + 1) * n * 2 * tb);
+    G.hnodes = G.g.half_lo + 1;
+    G.hist = take((size_t)G.hnodes * n * 2 * tb);
     G.efac = take(n * 2 * tb);
     G.twx = take((size_t)G.g.nx * 2 * tb);
     G.twy = take((size_t)G.g.ny * 2 * tb);

@@ -70,16 +70,20 @@ struct Group {
     double *q, *q_t;   // [run][2]
     double *ia, *ib;   // contour sums, [run][n]
     double *ia2, *ib2; // contour sums of the g' chain's terms (cluster solve), [run][n]
-    // differential second solve (MIXED_FP32 with the cluster solve)
-    // cluster solve (MIXED_FP32): states of both chains at every node, in the
-    // padded row layout [run][chain][ns+1][ny/2][nx + nx/8] float2
-    void *hc = nullptr;       // plain / reference solve
-    void *hd = nullptr;       // differential second solve
+    // differential second solve (MIXED_FP32).  Cluster solve: states of both
+    // chains at every node, in the padded row layout
+    // [run][chain][ns+1][ny/2][nx + nx/8] float2 (hc: plain / reference
+    // solve; hd: differential solve).  Streaming solves: hd holds the changes
+    // (dg, dg') at every node, [run][ns+1][n] float2, against the reference
+    // history in hist.
+    void *hc = nullptr;
+    void *hd = nullptr;
     void *rho = nullptr;      // (rho_A, rho_B) = expm1(-N d omega ds / 2), [run][n] float2
     void *cdiff = nullptr;    // (1 + rho_d)(1 + rho_a) - 1 for (A,A), (B,B), (A,B), packed rows [run][3][ny/2][nx] float2
     bool diff = false;        // the step uses the reference + differential solve pair
     bool phi_stale = false;   // omega was replaced since phi was last computed
-    bool hist_full = false;   // streaming radix-8 solve: hist holds all N_s + 1 nodes
+    bool hist_full = false;   // streaming radix-8 solve (hist holds all N_s + 1 nodes)
+    int hnodes = 0;           // nodes of hist per run: N_s + 1 (MIXED streaming solves) or half_lo + 1
     int colw = 0;             // radix-8 EPD column tile width chosen by the autotuner (0: default)
     int colw_prop = 0;        // radix-8 streaming propagator column tile width (0: default)
     // exact step (CG inversion of App. C), FP64 [run][3][n] unless noted
@@ -97,7 +101,7 @@ struct Group {
     double *stage;     // host<->device staging, 9 n doubles (one run)
     // bulk-precision buffers (float or double, by prec)
     void *chain;       // packed (g, g') of the running contour step, [run][n] complex
-    void *hist;        // (g, g') at nodes 0..half_lo, [run][half_lo+1][n] complex
+    void *hist;        // (g, g') at nodes 0..hnodes-1, [run][hnodes][n] complex
     void *efac;        // (E_A, E_B), [run][n] complex
     void *pop[2];      // post-collision populations, [run][9][n]
     void *vel;         // velocity of the last collision, [run][n] complex (x, y)
@@ -153,7 +157,8 @@ cudaError_t launch_solve(Group &G, const double *omega, double *phi, double *q, 
 cudaError_t launch_solve_delta(Group &G, cudaStream_t s, const SolveProbe *probe = nullptr);
 // The same at any omega against a given reference: omega_ref with its
 // densities phi_ref, q_ref, whose chain states the last plain solve stored
-// (G.hc) and whose Boltzmann factors are in G.efac.
+// (G.hc, or G.hist on the streaming paths) and whose Boltzmann factors are in
+// G.efac.
 cudaError_t launch_solve_delta_at(Group &G, const double *omega, const double *omega_ref, const double *phi_ref,
                                   const double *q_ref, double *phi, double *q, cudaStream_t s,
                                   const SolveProbe *probe = nullptr);

@@ -31,7 +31,10 @@ namespace epdlb {
 template <typename T> struct PropK {
     GroupGeom g;
     V2<T> *chain;
-    V2<T> *hist;
+    V2<T> *hist;          // [run][hnodes][n]: nodes 0..half_lo, or all N_s + 1 (reference of a differential solve)
+    V2<T> *hd;            // differential solve: (dg, dg') at every node, [run][N_s + 1][n]
+    const float2 *rho;    // differential solve: (rho_A, rho_B), [run][n]
+    int hnodes;
     const V2<T> *efac;
     double *ia, *ib, *part;
     const V2<T> *twx, *twy;
@@ -92,16 +95,25 @@ __global__ void __launch_bounds__(kThreads) prop_prep(GroupGeom g, const double 
     if (threadIdx.x == 0) part[(size_t)run * kMaxPart + kMaxPart / 2 + blockIdx.x] = s;
 }
 
-// Node 0: g = g' = 1 stored; chain <- E(s_0) z_0.
-template <typename T>
+// Node 0: g = g' = 1 stored; chain <- E(s_0) z_0.  Differential solve: the
+// change of node 0 is 0, the chain starts from d a_0 = E' - E = E rho of the
+// departing half-step.
+template <typename T, bool DIFF>
 __global__ void __launch_bounds__(kThreads) prop_start(PropK<T> k)
 {
     const int run = blockIdx.y;
     const long long n = k.g.n;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const V2<T> e = k.efac[(size_t)run * n + i];
-        k.hist[(size_t)run * (k.g.half_lo + 1) * n + i] = mk<T>((T)1, (T)1);
-        k.chain[(size_t)run * n + i] = mk<T>(fac_g<T>(e, k.g, 0, false), fac_gp<T>(e, k.g, 0, false));
+        if constexpr (!DIFF) {
+            k.hist[(size_t)run * k.hnodes * n + i] = mk<T>((T)1, (T)1);
+            k.chain[(size_t)run * n + i] = mk<T>(fac_g<T>(e, k.g, 0, false), fac_gp<T>(e, k.g, 0, false));
+        } else {
+            const float2 q = k.rho[(size_t)run * n + i];
+            k.hd[(size_t)run * (k.g.ns + 1) * n + i] = mk<T>((T)0, (T)0);
+            k.chain[(size_t)run * n + i] = mk<T>(fac_g<T>(e, k.g, 0, false) * fac_g<float>(q, k.g, 0, false),
+                                                 fac_gp<T>(e, k.g, 0, false) * fac_gp<float>(q, k.g, 0, false));
+        }
     }
 }
 
@@ -136,7 +148,13 @@ __global__ void __launch_bounds__(kThreads) prop_col(PropK<T> k)
 
 // Row pass producing contour node m (1 <= m <= ns): Tx, node factors, history
 // store / contour accumulation, Q_P partial sums at m = ns, next half step.
-template <typename T>
+// Differential solve (DIFF): the chain carries the change d a of the state
+// E_d g; with U = T(d a_{m-1}) and the reference node g~_m from the history,
+//   dg_m = E'_a U + rho_a g~_m,   d a_m = E'_d dg_m + E_d rho_d g~_m
+// (E' = E (1 + rho)), the exact differences of g_m = E'_a T(a_{m-1}) and
+// a_m = E'_d g_m from the reference solve's g~_m = E_a T(a~_{m-1}) and
+// a~_m = E_d g~_m; dg_m is stored at every node, dQ_P partials at m = ns.
+template <typename T, bool DIFF>
 __global__ void __launch_bounds__(kThreads) prop_row(PropK<T> k, int m)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -167,9 +185,35 @@ __global__ void __launch_bounds__(kThreads) prop_row(PropK<T> k, int m)
     const int ns = k.g.ns, na = k.g.na, hlo = k.g.half_lo, hhi = k.g.half_hi;
     const double ds = k.g.ds;
     const V2<T> *efac = k.efac + (size_t)run * n + base;
-    V2<T> *hist = k.hist + (size_t)run * (hlo + 1) * n + base;
-    double *ia = k.ia + (size_t)run * n + base, *ib = k.ib + (size_t)run * n + base;
+    V2<T> *hist = k.hist + (size_t)run * k.hnodes * n + base;
     double qsum = 0.0;
+    if constexpr (DIFF) {
+        const float2 *rho = k.rho + (size_t)run * n + base;
+        V2<T> *hd = k.hd + ((size_t)run * (ns + 1) + m) * n + base;
+        const V2<T> *gref = hist + (size_t)m * n;
+        const int bag = half_step_block(k.g.jr, 0, m, ns, na, true), bap = half_step_block(k.g.jr, 1, m, ns, na, true);
+        const int bdg = half_step_block(k.g.jr, 0, m, ns, na, false), bdp = half_step_block(k.g.jr, 1, m, ns, na, false);
+        for (int i = threadIdx.x; i < tile; i += blockDim.x) {
+            const V2<T> e = efac[i], gr = gref[i], u = r[i];
+            const float2 q = rho[i];
+            const T ea = bag ? e.y : e.x, eap = bap ? e.y : e.x, qa = bag ? q.y : q.x, qap = bap ? q.y : q.x;
+            const V2<T> dg = mk<T>(ea * ((T)1 + qa) * u.x + qa * gr.x, eap * ((T)1 + qap) * u.y + qap * gr.y);
+            hd[i] = dg;
+            if (m == ns) {
+                qsum += (double)dg.x;
+            } else {
+                const T ed = bdg ? e.y : e.x, edp = bdp ? e.y : e.x, qd = bdg ? q.y : q.x, qdp = bdp ? q.y : q.x;
+                data[i] = mk<T>(ed * ((T)1 + qd) * dg.x + ed * qd * gr.x, edp * ((T)1 + qdp) * dg.y + edp * qdp * gr.y);
+            }
+        }
+        if (m == ns) {
+            const double s = block_sum(qsum, red);
+            if (threadIdx.x == 0) k.part[(size_t)run * kMaxPart + blockIdx.x] = s;
+        }
+        return;
+    }
+    const bool store_all = k.hnodes == ns + 1;
+    double *ia = k.ia + (size_t)run * n + base, *ib = k.ib + (size_t)run * n + base;
     for (int i = threadIdx.x; i < tile; i += blockDim.x) {
         const V2<T> e = efac[i];
         // z = (g_m, g'_m): the arriving half-step's factor; the chain goes on
@@ -177,7 +221,7 @@ __global__ void __launch_bounds__(kThreads) prop_row(PropK<T> k, int m)
         const T eg = fac_g<T>(e, k.g, m, true), egp = fac_gp<T>(e, k.g, m, true);
         const V2<T> h = r[i];
         const V2<T> z = mk<T>(eg * h.x, egp * h.y);
-        if (m <= hlo) hist[(size_t)m * n + i] = z;
+        if (m <= hlo || store_all) hist[(size_t)m * n + i] = z;
         if (m >= hhi) {
             const int s2 = ns - m;
             const V2<T> hv = (s2 == m) ? z : hist[(size_t)s2 * n + i];
@@ -284,7 +328,9 @@ __global__ void __launch_bounds__(kThreads) prop_prep_delta(GroupGeom g, const d
 struct Stream8K {
     GroupGeom g;
     float2 *chain;        // [run][n]
-    float2 *hist;         // [run][N_s + 1][n]
+    float2 *hist;         // [run][N_s + 1][n] (the reference of a differential solve)
+    float2 *hd;           // differential solve: (dg, dg') at every node, [run][N_s + 1][n]
+    const float2 *rho;    // differential solve: (rho_A, rho_B), [run][n]
     const float2 *efac;   // [run][n]
     double *part;
     const float2 *twx, *twy;  // pass tables of each axis' best radix plan (fft8.cuh layout)
@@ -292,15 +338,24 @@ struct Stream8K {
     const float *kx, *ky;
 };
 
-// node 0: g = g' = 1; chain <- E(s_0) z_0
+// node 0: g = g' = 1; chain <- E(s_0) z_0 (differential solve: change 0,
+// chain d a_0 = E rho of the departing half-step)
+template <bool DIFF>
 __global__ void __launch_bounds__(kThreads) prop_start8(Stream8K k)
 {
     const int run = blockIdx.y;
     const long long n = k.g.n;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const float2 e = k.efac[(size_t)run * n + i];
-        k.hist[(size_t)run * (k.g.ns + 1) * n + i] = make_float2(1.f, 1.f);
-        k.chain[(size_t)run * n + i] = make_float2(fac_g<float>(e, k.g, 0, false), fac_gp<float>(e, k.g, 0, false));
+        if (!DIFF) {
+            k.hist[(size_t)run * (k.g.ns + 1) * n + i] = make_float2(1.f, 1.f);
+            k.chain[(size_t)run * n + i] = make_float2(fac_g<float>(e, k.g, 0, false), fac_gp<float>(e, k.g, 0, false));
+        } else {
+            const float2 q = k.rho[(size_t)run * n + i];
+            k.hd[(size_t)run * (k.g.ns + 1) * n + i] = make_float2(0.f, 0.f);
+            k.chain[(size_t)run * n + i] = make_float2(fac_g<float>(e, k.g, 0, false) * fac_g<float>(q, k.g, 0, false),
+                                                       fac_gp<float>(e, k.g, 0, false) * fac_gp<float>(q, k.g, 0, false));
+        }
     }
 }
 
@@ -334,8 +389,10 @@ __global__ void __launch_bounds__(ColTile<LOGY, CW>::T) prop_col8(Stream8K k)
 }
 
 // Row pass of contour node m: Tx, node factors, history store, next half
-// step; at m = N_s block sums of g for Q_P.
-template <int LOGX>
+// step; at m = N_s block sums of g for Q_P.  Differential solve (DIFF): the
+// chain carries d a; dg_m = E'_a U + rho_a g~_m is stored, the chain goes on
+// with d a_m = E'_d dg_m + E_d rho_d g~_m (as in prop_row), dQ_P partials.
+template <int LOGX, bool DIFF>
 __global__ void __launch_bounds__(RowTile<LOGX>::T) prop_row8(Stream8K k, int m)
 {
     using RT = RowTile<LOGX>;
@@ -362,18 +419,41 @@ __global__ void __launch_bounds__(RowTile<LOGX>::T) prop_row8(Stream8K k, int m)
     const float2 *efac = k.efac + (size_t)run * n + base;
     float2 *hist = k.hist + ((size_t)run * (ns + 1) + m) * n + base;
     float qsum = 0.f;
+    if (DIFF) {
+        const float2 *rho = k.rho + (size_t)run * n + base;
+        float2 *hd = k.hd + ((size_t)run * (ns + 1) + m) * n + base;
 #pragma unroll
-    for (int j = 0; j < NB_L; ++j)
+        for (int j = 0; j < NB_L; ++j)
 #pragma unroll
-        for (int r = 0; r < RR; ++r) {
-            const int i = bb[j] * NX + tt[j] + r * PER_L;
-            const float2 e = efac[i];
-            const float eg = fac_g<float>(e, k.g, m, true), egp = fac_gp<float>(e, k.g, m, true);
-            const float2 z = make_float2(eg * h[j][r].x, egp * h[j][r].y);
-            hist[i] = z;
-            if (m == ns) qsum += z.x;
-            else data[i] = make_float2(fac_g<float>(e, k.g, m, false) * z.x, fac_gp<float>(e, k.g, m, false) * z.y);
-        }
+            for (int r = 0; r < RR; ++r) {
+                const int i = bb[j] * NX + tt[j] + r * PER_L;
+                const float2 e = efac[i], q = rho[i], gr = hist[i], u = h[j][r];
+                const float ea = fac_g<float>(e, k.g, m, true), eap = fac_gp<float>(e, k.g, m, true);
+                const float qa = fac_g<float>(q, k.g, m, true), qap = fac_gp<float>(q, k.g, m, true);
+                const float2 dg = make_float2(ea * (1.f + qa) * u.x + qa * gr.x, eap * (1.f + qap) * u.y + qap * gr.y);
+                hd[i] = dg;
+                if (m == ns) {
+                    qsum += dg.x;
+                } else {
+                    const float ed = fac_g<float>(e, k.g, m, false), edp = fac_gp<float>(e, k.g, m, false);
+                    const float qd = fac_g<float>(q, k.g, m, false), qdp = fac_gp<float>(q, k.g, m, false);
+                    data[i] = make_float2(ed * (1.f + qd) * dg.x + ed * qd * gr.x, edp * (1.f + qdp) * dg.y + edp * qdp * gr.y);
+                }
+            }
+    } else {
+#pragma unroll
+        for (int j = 0; j < NB_L; ++j)
+#pragma unroll
+            for (int r = 0; r < RR; ++r) {
+                const int i = bb[j] * NX + tt[j] + r * PER_L;
+                const float2 e = efac[i];
+                const float eg = fac_g<float>(e, k.g, m, true), egp = fac_gp<float>(e, k.g, m, true);
+                const float2 z = make_float2(eg * h[j][r].x, egp * h[j][r].y);
+                hist[i] = z;
+                if (m == ns) qsum += z.x;
+                else data[i] = make_float2(fac_g<float>(e, k.g, m, false) * z.x, fac_gp<float>(e, k.g, m, false) * z.y);
+            }
+    }
     if (m == ns) {
         const double s = block_sum((double)qsum, red);
         if (tid == 0) k.part[(size_t)run * kMaxPart + blockIdx.x] = s;
@@ -383,16 +463,23 @@ __global__ void __launch_bounds__(RowTile<LOGX>::T) prop_row8(Stream8K k, int m)
 // Contour sums and normalisation over the full history (Eqs. (9)-(11)):
 // FP32 products, partial sums over up to 8 nodes of equal trapezoid weight,
 // FP64 totals; the solvent slot of phi holds exp(-omega_S) from prop_prep.
-__global__ void __launch_bounds__(kThreads) prop_contour_stream(GroupGeom g, const float2 *hist, int nrow_blocks,
-                                                                int nprep_blocks, const double *part, double *phi,
-                                                                double *q, int *err)
+// Differential solve (DIFF): the sums of the product's change
+// g~ dg' + dg g~' + dg dg' (reference history hist, changes hd), the
+// partials hold dQ_P and the solvent factor's change, and
+// Phi = Phi~ + (phi_p ds dI - Phi~ dQ) / (Q~ + dQ) per species.
+template <bool DIFF>
+__global__ void __launch_bounds__(kThreads) prop_contour_stream(GroupGeom g, const float2 *hist, const float2 *hd,
+                                                                int nrow_blocks, int nprep_blocks, const double *part,
+                                                                double *phi, double *q, const double *phi_ref,
+                                                                const double *q_ref, int *err)
 {
     __shared__ double bc;
     const int run = blockIdx.y, ns = g.ns, na = g.na;
     const long long n = g.n;
     const double *pr = part + (size_t)run * kMaxPart;
-    const double qp = sum_partials(pr, nrow_blocks, 1, &bc) / (double)n;
-    const double qs = sum_partials(pr + kMaxPart / 2, nprep_blocks, 1, &bc) / (double)n;
+    const double sq = sum_partials(pr, nrow_blocks, 1, &bc) / (double)n;
+    const double ss = sum_partials(pr + kMaxPart / 2, nprep_blocks, 1, &bc) / (double)n;
+    const double qp = DIFF ? q_ref[2 * run] + sq : sq, qs = DIFF ? q_ref[2 * run + 1] + ss : ss;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         q[2 * run] = qp;
         q[2 * run + 1] = qs;
@@ -401,6 +488,7 @@ __global__ void __launch_bounds__(kThreads) prop_contour_stream(GroupGeom g, con
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float2 *hz = hist + (size_t)run * (ns + 1) * n + i;
+    const float2 *dz = DIFF ? hd + (size_t)run * (ns + 1) * n + i : nullptr;
     // Nodes m and N_s - m are read together: z_m = (g_m, g'_m) and z_{N_s-m}
     // give the terms g_m g'_{N_s-m} (node m) and g_{N_s-m} g'_m (node N_s - m).
     // Compensated (Kahan) FP32 sums per block (GB300's FP64 rate is a small
@@ -418,44 +506,63 @@ __global__ void __launch_bounds__(kThreads) prop_contour_stream(GroupGeom g, con
         if (wb != 0.f) kadd(sb, cb, wb * t);
     };
     const int half = ns / 2;
-    constexpr int U = 8;
+    constexpr int U = DIFF ? 4 : 8;
     for (int m0 = 0; m0 <= half; m0 += U) {
-        float2 zl[U], zr[U];
+        float2 zl[U], zr[U], dl[U], dr[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int m = m0 + u;
             if (m <= half) {
                 zl[u] = hz[(size_t)m * n];
                 zr[u] = hz[(size_t)(ns - m) * n];
+                if (DIFF) {
+                    dl[u] = dz[(size_t)m * n];
+                    dr[u] = dz[(size_t)(ns - m) * n];
+                }
             }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int m = m0 + u;
             if (m > half) break;
-            add(m, zl[u].x * zr[u].y);
-            if (ns - m != m) add(ns - m, zr[u].x * zl[u].y);
+            if (!DIFF) {
+                add(m, zl[u].x * zr[u].y);
+                if (ns - m != m) add(ns - m, zr[u].x * zl[u].y);
+            } else {
+                // node m: g_m g'_{ns-m}; node ns - m: g_{ns-m} g'_m
+                add(m, zl[u].x * dr[u].y + dl[u].x * zr[u].y + dl[u].x * dr[u].y);
+                if (ns - m != m) add(ns - m, zr[u].x * dl[u].y + dr[u].x * zl[u].y + dr[u].x * dl[u].y);
+            }
         }
     }
     const double ia = (double)sa - (double)ca, ib = (double)sb - (double)cb;
-    const double c = g.phi_p * g.ds / qp;
     double *ph = phi + (size_t)run * 3 * n;
-    ph[i] = c * ia;
-    ph[n + i] = c * ib;
-    ph[2 * n + i] *= (1.0 - g.phi_p) / qs;
+    if (!DIFF) {
+        const double c = g.phi_p * g.ds / qp;
+        ph[i] = c * ia;
+        ph[n + i] = c * ib;
+        ph[2 * n + i] *= (1.0 - g.phi_p) / qs;
+    } else {
+        const double *pt = phi_ref + (size_t)run * 3 * n;
+        const double rq = 1.0 / qp, c = g.phi_p * g.ds;
+        ph[i] = pt[i] + (c * ia - pt[i] * sq) * rq;
+        ph[n + i] = pt[n + i] + (c * ib - pt[n + i] * sq) * rq;
+        ph[2 * n + i] = pt[2 * n + i] + ((1.0 - g.phi_p) * ph[2 * n + i] - pt[2 * n + i] * ss) / qs;
+    }
 }
 
 // The contour loop of the radix-8 streaming solve for (LX, LY), column tiles
-// of CW columns.
+// of CW columns (diff: the differential solve's row passes).
 template <int LX, int LY, int CW>
-static void stream8_run(Stream8K &k, const Group &G, cudaStream_t s, const SolveProbe *probe)
+static void stream8_run(Stream8K &k, const Group &G, cudaStream_t s, const SolveProbe *probe, bool diff)
 {
     using RT = RowTile<LX>;
     using CT = ColTile<LY, CW>;
     const size_t sr = (size_t)RT::ROWS * RowLayout<LX>::PITCH * sizeof(float2), sc = (size_t)CT::P * sizeof(float2);
     static std::atomic<bool> conf{false};  // attribute set (idempotent if two threads race)
     if (!conf) {
-        cudaFuncSetAttribute(prop_row8<LX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
+        cudaFuncSetAttribute(prop_row8<LX, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
+        cudaFuncSetAttribute(prop_row8<LX, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
         cudaFuncSetAttribute(prop_col8<LY, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
         conf = true;
     }
@@ -466,36 +573,57 @@ static void stream8_run(Stream8K &k, const Group &G, cudaStream_t s, const Solve
         prop_col8<LY, CW><<<gc, CT::T, sc, s>>>(k);
         if (pa) cudaEventRecordWithFlags(probe->ev[3], s, cudaEventRecordExternal);
         if (ps) cudaEventRecordWithFlags(probe->ev[0], s, cudaEventRecordExternal);
-        prop_row8<LX><<<gr, RT::T, sr, s>>>(k, m);
+        if (diff) prop_row8<LX, true><<<gr, RT::T, sr, s>>>(k, m);
+        else prop_row8<LX, false><<<gr, RT::T, sr, s>>>(k, m);
         if (ps) cudaEventRecordWithFlags(probe->ev[1], s, cudaEventRecordExternal);
         if (pa) cudaEventRecordWithFlags(probe->ev[4], s, cudaEventRecordExternal);
     }
 }
 template <int LX, int LY>
-static bool stream8_dispatch_y(int logy, Stream8K &k, const Group &G, cudaStream_t s, const SolveProbe *probe)
+static bool stream8_dispatch_y(int logy, Stream8K &k, const Group &G, cudaStream_t s, const SolveProbe *probe, bool diff)
 {
     if constexpr (LY > 11) {
         return false;
     } else {
-        if (logy != LY) return stream8_dispatch_y<LX, LY + 1>(logy, k, G, s, probe);
+        if (logy != LY) return stream8_dispatch_y<LX, LY + 1>(logy, k, G, s, probe, diff);
         switch (G.colw_prop) {
-        case 4: stream8_run<LX, LY, 4>(k, G, s, probe); break;
-        case 8: stream8_run<LX, LY, 8>(k, G, s, probe); break;
-        case 16: stream8_run<LX, LY, 16>(k, G, s, probe); break;
-        default: stream8_run<LX, LY, ColTile<LY>::C>(k, G, s, probe); break;
+        case 4: stream8_run<LX, LY, 4>(k, G, s, probe, diff); break;
+        case 8: stream8_run<LX, LY, 8>(k, G, s, probe, diff); break;
+        case 16: stream8_run<LX, LY, 16>(k, G, s, probe, diff); break;
+        default: stream8_run<LX, LY, ColTile<LY>::C>(k, G, s, probe, diff); break;
         }
         return true;
     }
 }
 template <int LX>
-static bool stream8_dispatch(int logx, int logy, Stream8K &k, const Group &G, cudaStream_t s, const SolveProbe *probe)
+static bool stream8_dispatch(int logx, int logy, Stream8K &k, const Group &G, cudaStream_t s, const SolveProbe *probe,
+                             bool diff = false)
 {
     if constexpr (LX > 11) {
         return false;
     } else {
-        if (logx != LX) return stream8_dispatch<LX + 1>(logx, logy, k, G, s, probe);
-        return stream8_dispatch_y<LX, 6>(logy, k, G, s, probe);
+        if (logx != LX) return stream8_dispatch<LX + 1>(logx, logy, k, G, s, probe, diff);
+        return stream8_dispatch_y<LX, 6>(logy, k, G, s, probe, diff);
     }
+}
+
+static Stream8K stream8_args(const Group &G)
+{
+    Stream8K k8;
+    k8.g = G.g;
+    k8.chain = reinterpret_cast<float2 *>(G.chain);
+    k8.hist = reinterpret_cast<float2 *>(G.hist);
+    k8.hd = reinterpret_cast<float2 *>(G.hd);
+    k8.rho = reinterpret_cast<const float2 *>(G.rho);
+    k8.efac = reinterpret_cast<const float2 *>(G.efac);
+    k8.part = G.part;
+    k8.twx = best_mr(G.g.logx) == 4 ? G.tab16x : G.tab8x;
+    k8.twy = best_mr(G.g.logy) == 4 ? G.tab16y : G.tab8y;
+    k8.twy8 = G.tab8y;
+    k8.twy16 = G.tab16y;
+    k8.kx = reinterpret_cast<const float *>(G.kx);
+    k8.ky = reinterpret_cast<const float *>(G.ky);
+    return k8;
 }
 
 // Column tile autotuner of the streaming propagator column pass (see
@@ -567,18 +695,7 @@ cudaError_t tune_stream_tiles(Group &G, cudaStream_t s)
             return cudaSuccess;
         }
     }
-    Stream8K k8;
-    k8.g = G.g;
-    k8.chain = reinterpret_cast<float2 *>(G.chain);
-    k8.hist = reinterpret_cast<float2 *>(G.hist);
-    k8.efac = reinterpret_cast<const float2 *>(G.efac);
-    k8.part = G.part;
-    k8.twx = best_mr(G.g.logx) == 4 ? G.tab16x : G.tab8x;
-    k8.twy = best_mr(G.g.logy) == 4 ? G.tab16y : G.tab8y;
-    k8.twy8 = G.tab8y;
-    k8.twy16 = G.tab16y;
-    k8.kx = reinterpret_cast<const float *>(G.kx);
-    k8.ky = reinterpret_cast<const float *>(G.ky);
+    Stream8K k8 = stream8_args(G);
     cudaError_t e = cudaMemsetAsync(G.chain, 0, (size_t)G.g.nruns * G.g.n * sizeof(float2), s);
     if (e != cudaSuccess) return e;
     G.colw_prop = tune_col8_at<6>(G.g.logy, k8, G, s);
@@ -612,13 +729,15 @@ static size_t row_smem(const Group &G)
 }
 
 template <typename T>
-static cudaError_t solve_t(Group &G, const double *omega, double *phi, double *q, cudaStream_t s, const SolveProbe *probe)
+static PropK<T> prop_args(const Group &G)
 {
-    const GroupGeom &g = G.g;
     PropK<T> k;
-    k.g = g;
+    k.g = G.g;
     k.chain = reinterpret_cast<V2<T> *>(G.chain);
     k.hist = reinterpret_cast<V2<T> *>(G.hist);
+    k.hd = reinterpret_cast<V2<T> *>(G.hd);
+    k.rho = reinterpret_cast<const float2 *>(G.rho);
+    k.hnodes = G.hnodes;
     k.efac = reinterpret_cast<const V2<T> *>(G.efac);
     k.ia = G.ia;
     k.ib = G.ib;
@@ -630,6 +749,38 @@ static cudaError_t solve_t(Group &G, const double *omega, double *phi, double *q
     k.rows = G.sh.rows_prop;
     k.logc = G.g.pow2 ? ilog2(G.sh.cols_prop) : 0;
     k.cols = G.sh.cols_prop;
+    return k;
+}
+
+// Q partial blocks of the radix-8 row pass (one per row tile)
+static int stream8_row_blocks(const GroupGeom &g) { return (int)(g.n / (g.nx >= 2048 ? g.nx : 2048)); }
+
+// The contour loop of the generic streaming solve (column pass, row pass per
+// node); returns the row pass grid (its x extent = the Q partial blocks).
+template <typename T, bool DIFF>
+static dim3 generic_loop(const Group &G, PropK<T> &k, cudaStream_t s, const SolveProbe *probe)
+{
+    const GroupGeom &g = G.g;
+    const dim3 gc(g.nx / G.sh.cols_prop, g.nruns), gr(g.ny / G.sh.rows_prop, g.nruns);
+    const size_t sc = col_smem<T>(G), sr = row_smem<T>(G);
+    for (int m = 1; m <= g.ns; ++m) {
+        const bool pa = probe && m == probe->m_acc, ps = probe && m == probe->m_store;
+        if (pa) cudaEventRecordWithFlags(probe->ev[2], s, cudaEventRecordExternal);
+        prop_col<T><<<gc, kThreads, sc, s>>>(k);
+        if (pa) cudaEventRecordWithFlags(probe->ev[3], s, cudaEventRecordExternal);
+        if (ps) cudaEventRecordWithFlags(probe->ev[0], s, cudaEventRecordExternal);
+        prop_row<T, DIFF><<<gr, kThreads, sr, s>>>(k, m);
+        if (ps) cudaEventRecordWithFlags(probe->ev[1], s, cudaEventRecordExternal);
+        if (pa) cudaEventRecordWithFlags(probe->ev[4], s, cudaEventRecordExternal);
+    }
+    return gr;
+}
+
+template <typename T>
+static cudaError_t solve_t(Group &G, const double *omega, double *phi, double *q, cudaStream_t s, const SolveProbe *probe)
+{
+    const GroupGeom &g = G.g;
+    PropK<T> k = prop_args<T>(G);
 
     const int pg = grid_for(g.n);
     prop_prep<T><<<dim3(pg, g.nruns), kThreads, 0, s>>>(g, omega, reinterpret_cast<V2<T> *>(G.efac), phi, G.part);
@@ -639,39 +790,41 @@ static cudaError_t solve_t(Group &G, const double *omega, double *phi, double *q
     }
     if (sizeof(T) == sizeof(float) && G.hist_full && G.tab8x) {
         // radix-8 streaming passes with the full history, then the contour pass
-        Stream8K k8;
-        k8.g = g;
-        k8.chain = reinterpret_cast<float2 *>(G.chain);
-        k8.hist = reinterpret_cast<float2 *>(G.hist);
-        k8.efac = reinterpret_cast<const float2 *>(G.efac);
-        k8.part = G.part;
-        k8.twx = best_mr(g.logx) == 4 ? G.tab16x : G.tab8x;
-        k8.twy = best_mr(g.logy) == 4 ? G.tab16y : G.tab8y;
-        k8.twy8 = G.tab8y;
-        k8.twy16 = G.tab16y;
-        k8.kx = reinterpret_cast<const float *>(G.kx);
-        k8.ky = reinterpret_cast<const float *>(G.ky);
-        prop_start8<<<dim3(pg, g.nruns), kThreads, 0, s>>>(k8);
+        Stream8K k8 = stream8_args(G);
+        prop_start8<false><<<dim3(pg, g.nruns), kThreads, 0, s>>>(k8);
         if (!stream8_dispatch<6>(g.logx, g.logy, k8, G, s, probe)) return cudaErrorInvalidConfiguration;
-        const int nrow = (int)(g.n / (g.nx >= 2048 ? g.nx : 2048));
-        prop_contour_stream<<<dim3((unsigned)((g.n + kThreads - 1) / kThreads), g.nruns), kThreads, 0, s>>>(
-            g, k8.hist, nrow, pg, G.part, phi, q, G.err);
+        prop_contour_stream<false><<<dim3((unsigned)((g.n + kThreads - 1) / kThreads), g.nruns), kThreads, 0, s>>>(
+            g, k8.hist, nullptr, stream8_row_blocks(g), pg, G.part, phi, q, nullptr, nullptr, G.err);
         return cudaGetLastError();
     }
-    prop_start<T><<<dim3(pg, g.nruns), kThreads, 0, s>>>(k);
-    const dim3 gc(g.nx / G.sh.cols_prop, g.nruns), gr(g.ny / G.sh.rows_prop, g.nruns);
-    const size_t sc = col_smem<T>(G), sr = row_smem<T>(G);
-    for (int m = 1; m <= g.ns; ++m) {
-        const bool pa = probe && m == probe->m_acc, ps = probe && m == probe->m_store;
-        if (pa) cudaEventRecordWithFlags(probe->ev[2], s, cudaEventRecordExternal);
-        prop_col<T><<<gc, kThreads, sc, s>>>(k);
-        if (pa) cudaEventRecordWithFlags(probe->ev[3], s, cudaEventRecordExternal);
-        if (ps) cudaEventRecordWithFlags(probe->ev[0], s, cudaEventRecordExternal);
-        prop_row<T><<<gr, kThreads, sr, s>>>(k, m);
-        if (ps) cudaEventRecordWithFlags(probe->ev[1], s, cudaEventRecordExternal);
-        if (pa) cudaEventRecordWithFlags(probe->ev[4], s, cudaEventRecordExternal);
-    }
+    prop_start<T, false><<<dim3(pg, g.nruns), kThreads, 0, s>>>(k);
+    const dim3 gr = generic_loop<T, false>(G, k, s, probe);
     prop_finalize<<<dim3(pg, g.nruns), kThreads, 0, s>>>(g, gr.x, pg, G.ia, G.ib, nullptr, nullptr, G.part, phi, q, G.err);
+    return cudaGetLastError();
+}
+
+// Streaming differential solve (MIXED_FP32 grids without the cluster
+// solve): the changes against the reference history of the last plain
+// solve, then the contour pass of the changes.
+static cudaError_t stream_delta(Group &G, int pg, double *phi, double *q, const double *phi_ref, const double *q_ref,
+                                cudaStream_t s, const SolveProbe *probe)
+{
+    const GroupGeom &g = G.g;
+    const dim3 gcon((unsigned)((g.n + kThreads - 1) / kThreads), g.nruns);
+    if (G.hist_full && G.tab8x) {
+        Stream8K k8 = stream8_args(G);
+        prop_start8<true><<<dim3(pg, g.nruns), kThreads, 0, s>>>(k8);
+        if (!stream8_dispatch<6>(g.logx, g.logy, k8, G, s, probe, true)) return cudaErrorInvalidConfiguration;
+        prop_contour_stream<true><<<gcon, kThreads, 0, s>>>(g, k8.hist, k8.hd, stream8_row_blocks(g), pg, G.part, phi, q,
+                                                           phi_ref, q_ref, G.err);
+        return cudaGetLastError();
+    }
+    PropK<float> k = prop_args<float>(G);
+    prop_start<float, true><<<dim3(pg, g.nruns), kThreads, 0, s>>>(k);
+    const dim3 gr = generic_loop<float, true>(G, k, s, probe);
+    prop_contour_stream<true><<<gcon, kThreads, 0, s>>>(g, reinterpret_cast<const float2 *>(G.hist),
+                                                       reinterpret_cast<const float2 *>(G.hd), (int)gr.x, pg, G.part, phi,
+                                                       q, phi_ref, q_ref, G.err);
     return cudaGetLastError();
 }
 
@@ -689,6 +842,7 @@ cudaError_t launch_solve_delta_at(Group &G, const double *omega, const double *o
     const int pg = grid_for(g.n);
     prop_prep_delta<<<dim3(pg, g.nruns), kThreads, 0, s>>>(g, omega, omega_ref, reinterpret_cast<float2 *>(G.rho),
                                                           reinterpret_cast<float *>(G.cdiff), phi, G.part);
+    if (!G.hc) return stream_delta(G, pg, phi, q, phi_ref, q_ref, s, probe);
     return launch_cluster_solve(G, s, true, pg, phi, q, probe, phi_ref, q_ref);
 }
 
@@ -726,6 +880,9 @@ static cudaError_t solve3d_t(const Solve3 &S, const double *omega, double *phi, 
         k.g = g;
         k.chain = reinterpret_cast<V2<T> *>(S.chain);
         k.hist = reinterpret_cast<V2<T> *>(S.hist);
+        k.hd = nullptr;
+        k.rho = nullptr;
+        k.hnodes = g.half_lo + 1;
         k.efac = reinterpret_cast<const V2<T> *>(S.efac);
         k.ia = S.ia;
         k.ib = S.ib;
@@ -745,14 +902,14 @@ static cudaError_t solve3d_t(const Solve3 &S, const double *omega, double *phi, 
     const GroupGeom &g = S.vx;
     const int pg = grid_for(g.n);
     prop_prep<T><<<dim3(pg, 1), kThreads, 0, s>>>(g, omega, reinterpret_cast<V2<T> *>(S.efac), phi, S.part);
-    prop_start<T><<<dim3(pg, 1), kThreads, 0, s>>>(kx);
+    prop_start<T, false><<<dim3(pg, 1), kThreads, 0, s>>>(kx);
     const dim3 gz(S.vz.nx / S.cols_z, 1), gy(S.vy.nx / S.cols_y, S.vy.nruns), gr(S.vx.ny / S.rows_x, 1);
     const size_t sz = smem3<T>(S.vz, 0, S.cols_z, false), sy = smem3<T>(S.vy, 0, S.cols_y, false),
                  sr = smem3<T>(S.vx, S.rows_x, 0, true);
     for (int m = 1; m <= g.ns; ++m) {
         prop_col<T><<<gz, kThreads, sz, s>>>(kz);
         prop_col<T><<<gy, kThreads, sy, s>>>(ky);
-        prop_row<T><<<gr, kThreads, sr, s>>>(kx, m);
+        prop_row<T, false><<<gr, kThreads, sr, s>>>(kx, m);
     }
     prop_finalize<<<dim3(pg, 1), kThreads, 0, s>>>(g, gr.x, pg, S.ia, S.ib, nullptr, nullptr, S.part, phi, q, S.err);
     return cudaGetLastError();
@@ -769,11 +926,13 @@ cudaError_t configure_prop_kernels()
     const int lim = 200 * 1024;
     e = cudaFuncSetAttribute(prop_col<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (e) return e;
-    e = cudaFuncSetAttribute(prop_row<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    e = cudaFuncSetAttribute(prop_row<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (e) return e;
+    e = cudaFuncSetAttribute(prop_row<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (e) return e;
     e = cudaFuncSetAttribute(prop_col<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (e) return e;
-    return cudaFuncSetAttribute(prop_row<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    return cudaFuncSetAttribute(prop_row<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
 }
 
 } // namespace epdlb

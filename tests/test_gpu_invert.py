@@ -1,7 +1,7 @@
 """GPU exact step (App. C: convection of the composition fields and the
 Fletcher-Reeves inversion omega~ = Phi^{-1}(Phi~)) against the FP64 oracle:
 fixed iteration counts (PLAIN_FP64, element by element), convergence to the
-tolerance (iteration counts and states), the MIXED_FP32 cluster path, the
+tolerance (iteration counts and states), the MIXED_FP32 differential paths, the
 reduction to the truncated step, batches and error handling."""
 import numpy as np
 import pytest
@@ -77,9 +77,11 @@ def test_exact_step_fp64_converges_with_the_oracle():
     h.close()
 
 
-@pytest.mark.parametrize("ny,nx,ns", [(64, 64, 16), (64, 128, 10)])
+@pytest.mark.parametrize("ny,nx,ns", [(64, 64, 16), (64, 128, 10), (32, 64, 8), (64, 1024, 8), (60, 96, 12)])
 def test_exact_step_mixed_cluster_converges(ny, nx, ns):
-    # MIXED_FP32 on the cluster-resident solve: every density of the step is
+    # MIXED_FP32 with the differential solves (cluster-resident on 64 x 64
+    # and 128 x 64; streaming generic, radix-8 and mixed-radix on the
+    # others): every density of the step is
     # a difference from the solve at the starting guess, so the mismatch
     # reaches the paper's 1e-8 although FP32 densities differ from FP64 by
     # ~3e-7.  omega~ inverts the FP32 density map: its distance from the FP64
@@ -161,11 +163,6 @@ def test_exact_step_errors():
     with pytest.raises(P.EpdLbError):
         h.set_inversion(5, float("nan"))
     h.close()
-    # MIXED grids without the cluster-resident solve are refused
-    m = P.EpdLb([W.with_(W.plain_small(), nx=32, ny=16, ns=8, precision=P.MIXED_FP32)])
-    with pytest.raises(P.EpdLbError):
-        m.set_inversion(5, 1e-8)
-    m.close()
 
 
 def test_exact_step_at_the_benchmark_size():
