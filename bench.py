@@ -548,6 +548,53 @@ def evaluate_surrogate(P, torch, runs, sm, s_in, s_out, flush, timed_steps, eval
                                         "the same with u, relative to max |u|)"}
 
 
+def bf16_peak():
+    """(burst dense BF16 TFLOP/s, "measured" or "fallback")."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+def surrogate_rates(torch, sm, runs, flush, reps=10):
+    """The surrogate's network kernels on the workload batch: CUDA-event time
+    of one inference (the four tcgen05 convolutions and their small
+    companions) and of one forward + tangent pass, L2 flushed before each;
+    the convolutions' algorithmic BF16 FLOPs against the tensor-core peak."""
+    import numpy as np
+
+    nb, ny, nx = len(runs), runs[0].ny, runs[0].nx
+    om = torch.from_numpy(1e-3 * np.random.default_rng(3).standard_normal((nb, 3, ny, nx))).cuda()
+    om2 = om + 1e-6
+    for _ in range(3):
+        sm.tangent(om, om2)
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        ts = []
+        for _ in range(reps):
+            flush.add_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts))
+
+    fwd = timed(lambda: sm.forward(om))
+    tan = timed(lambda: sm.tangent(om, om2))
+    # 2 x 9 taps x C_in x C_out per site and layer (the stored channel
+    # counts the network computes: 3, 32, 32, 32 in; 32, 32, 32, 2 out)
+    flops = 2.0 * nb * ny * nx * 9 * (3 * 32 + 32 * 32 + 32 * 32 + 32 * 2)
+    peak, kind = bf16_peak()
+    tf = flops / (fwd * 1e-3) / 1e12
+    return {"batch": f"{nb} x {ny}x{nx}", "forward_ms": fwd, "forward_plus_tangent_ms": tan,
+            "forward_tflops_algorithmic": tf, "bf16_peak_tflops": peak, "peak_kind": kind,
+            "frac_of_bf16_peak": tf / peak}
+
+
 def surrogate_section(P, W, torch, runs, flush, args, exact_ms):
     """The surrogate on the workload: trained on the workload's own runs
     (args.surrogate_pairs streamed pairs), evaluated on them."""
@@ -555,6 +602,7 @@ def surrogate_section(P, W, torch, runs, flush, args, exact_ms):
     out = evaluate_surrogate(P, torch, runs, sm, s_in, s_out, flush, args.surrogate_steps, args.surrogate_eval_steps,
                              exact_ms)
     out["training"] = info
+    out["network_kernels"] = surrogate_rates(torch, sm, runs, flush)
     return out
 
 

@@ -17,9 +17,10 @@
 // accumulation on activations stored NHWC in BF16 (channels padded to a
 // multiple of 16).  The forward layers, the input gradient (the same
 // convolution of the output gradient with flipped, transposed weights) and
-// the tangent pass run on tcgen05 (conv3x3_tc: a 16 x 8 pixel tile per CTA,
-// M = 128, the accumulator in TMEM); the weight gradient, a GEMM over pixels
-// per tap, runs on mma.sync m16n8k16 (conv3x3_dw).  Rounding to BF16 happens
+// the tangent pass run on tcgen05 (conv3x3_tc: 16 x 8 pixel tiles, M = 128,
+// the accumulator in TMEM, halo tiles streamed in by TMA three deep); the
+// weight gradient, a GEMM over pixels per tap, runs on mma.sync m16n8k16
+// (conv3x3_dw).  Rounding to BF16 happens
 // where the tensor cores read: weights, activations and the output
 // gradients.
 //
@@ -31,9 +32,13 @@
 // forward passes at omega~ and omega(t+dt), whose inputs differ by far less
 // than a BF16 step, would not resolve the change that drives the force.
 #include <cstdint>
+#include <cstring>
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <mutex>
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -79,6 +84,7 @@ struct ConvArgs {
     const float *yprev;         // EP_DX: tanh output of the layer below, [b][y][x][NP] FP32
     const __nv_bfloat16 *ycur;  // EP_JVP: this layer's tanh output, [b][y][x][NP] BF16
     int *err;                   // bit 2: a bounded wait of the tensor-core kernel gave up
+    int use_tma;                // interior tiles by TMA (the tensor map encodes `in`)
     int nx, ny, logx, logy, nb;
     int nreal;                  // output channels actually used (the rest are written as 0)
 };
@@ -87,9 +93,11 @@ struct ConvArgs {
 // Convolution on the 5th-generation tensor cores (tcgen05, TMEM): forward
 // layers, input gradients and the tangent pass.
 //
-// A CTA of 4 warps computes a 16 x 8 pixel tile (M = 128 rows of the
+// A CTA of 4 warps computes 16 x 8 pixel tiles (M = 128 rows of the
 // implicit GEMM) for all output channels (N = 32, or 16 for the output
-// layer's 8 stored channels), K = 9 taps x the input channels in steps of 16.
+// layer's 8 stored channels), K = 9 taps x the input channels in steps of 16,
+// looping over tiles with the next two tiles' halos in flight (TMA boxes for
+// tiles inside the grid, periodic per-pixel copies on the border).
 // Operands are read by the tensor cores from shared memory in the canonical
 // K-major layout without swizzle: core matrices of 8 rows x 16 bytes (8
 // channels), the halo tile stored as one plane per 8 input channels
@@ -107,19 +115,24 @@ template <int D> struct HaloTC {
     static constexpr int HH = TCH + 2 * D, HW = TCW + 2 * D;
 };
 
-// Shared memory of the tcgen05 convolution: halo planes, then weights.
+// Shared memory of the tcgen05 convolution: NBUF halo tiles (the one the
+// MMAs read and the next ones, in flight), then the weights.  A halo tile
+// is one plane per 8 input channels, each plane [HH][HW][8 channels] (the
+// box of one TMA load), padded to 128 bytes.
 template <int KP, int NP, int D> struct ConvTC {
     static constexpr int N = NP < 16 ? 16 : NP;  // MMA N (multiple of 16 for M = 128)
     static constexpr int C8 = KP / 8;
     static constexpr int HW16 = HaloTC<D>::HW * 16;
-    static constexpr int PLANE = HaloTC<D>::HH * HW16;  // bytes per 8-channel plane
+    static constexpr int PLANE_USED = HaloTC<D>::HH * HW16;
+    static constexpr int PLANE = (PLANE_USED + 127) / 128 * 128;  // bytes per 8-channel plane
     static constexpr int HALO = C8 * PLANE, WB = 9 * C8 * N * 16;
+    static constexpr int NBUF = 3;
     // the furthest byte a descriptor walk reaches (16 core matrices along M,
-    // 2 along K) lies inside the halo planes
+    // 2 along K) lies inside the halo tile
     static_assert((KP / 16 - 1) * 2 * PLANE + (2 * D * HaloTC<D>::HW + 2 * D) * 16 + 15 * HW16 + PLANE + 128 <= HALO,
                   "A operand walk inside the halo tile");
-    static constexpr int AOFF = (HALO + 1023) / 1024 * 1024;
-    static constexpr size_t SMEM = (size_t)AOFF + WB;
+    static constexpr int AOFF = (NBUF * HALO + 1023) / 1024 * 1024;
+    static constexpr size_t SMEM = (size_t)AOFF + WB + 128;  // + alignment slack of the base
 };
 
 // Shared-memory matrix descriptor: start, leading-byte offset (between core
@@ -184,19 +197,98 @@ template <> __device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, float (&
     }
 }
 
+// tanh(x) = 1 - 2 / (exp(2x) + 1), with |x| clamped at 15 (tanh(15) rounds
+// to 1 in FP32); absolute error a few 1e-7, below the BF16 step of the
+// stored activations
+__device__ __forceinline__ float tanh_fast(float x)
+{
+    x = fminf(fmaxf(x, -15.f), 15.f);
+    return 1.f - __fdividef(2.f, __expf(2.f * x) + 1.f);
+}
+
+// Bounded wait for the phase with the given parity of a CTA-local mbarrier
+// in the tile pipeline: as mbar_wait_tc.
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// TMA load of one box of a 4D tensor map into shared memory, completing
+// its bytes on the mbarrier
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int c0, int c1, int c2, int c3)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+        : "memory");
+}
+
+// Tile pipeline: NBUF halo buffers, each with a "full" mbarrier that all
+// 128 threads arrive on once per tile.  A tile whose halo lies inside the
+// grid is loaded by TMA (thread 0 arrives with the expected bytes, one box
+// per 8-channel plane; the others arrive plainly); a tile on the border,
+// whose halo wraps periodically, by per-pixel asynchronous copies whose
+// completion each thread hands to the barrier (cp.async.mbarrier.arrive).
+// The MMAs of tile i read buffer i % NBUF while tiles i + 1 .. i + NBUF - 1
+// stream in.
 template <int KP, int NP, int MODE, int D>
-__global__ void __launch_bounds__(128) conv3x3_tc(ConvArgs a)
+__global__ void __launch_bounds__(128) conv3x3_tc(ConvArgs a, const __grid_constant__ CUtensorMap tmap)
 {
     using Geo = ConvTC<KP, NP, D>;
-    constexpr int HH = HaloTC<D>::HH, HW = HaloTC<D>::HW, C8 = Geo::C8, N = Geo::N;
-    extern __shared__ __align__(1024) unsigned char tc_raw[];
-    unsigned char *halo = tc_raw;               // [c8][HH*HW][16 B]
-    unsigned char *wsm = tc_raw + Geo::AOFF;    // [tap][c8][N][16 B]
-    __shared__ __align__(8) unsigned long long mbar;
+    constexpr int HH = HaloTC<D>::HH, HW = HaloTC<D>::HW, C8 = Geo::C8, N = Geo::N, NBUF = Geo::NBUF;
+    static_assert(NP % 8 == 0, "epilogue in groups of 8 channels");
+    extern __shared__ __align__(128) unsigned char tc_raw[];
+    // base rounded up to 128 bytes (TMA destinations)
+    unsigned char *halo = tc_raw + ((128u - ((uint32_t)__cvta_generic_to_shared(tc_raw) & 127u)) & 127u);  // [buffer][c8][HH*HW][16 B]
+    unsigned char *wsm = halo + Geo::AOFF;      // [tap][c8][N][16 B]
+    __shared__ __align__(8) unsigned long long mbar, full[NBUF];
     __shared__ uint32_t tmem_base;
+    __shared__ float bias_s[NP];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long n = (long long)a.nx * a.ny;
     const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&mbar);
+    const uint32_t full_s = (uint32_t)__cvta_generic_to_shared(&full[0]);
+    const uint32_t halo_s = (uint32_t)__cvta_generic_to_shared(halo), w_s = (uint32_t)__cvta_generic_to_shared(wsm);
+    const int tiles_x = a.nx / TCW, tiles_img = tiles_x * (a.ny / TCH), ntiles = tiles_img * a.nb;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        for (int i = 0; i < NBUF; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(full_s + 8 * i) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    unsigned pending = 0;  // buffers with a load issued and not yet waited on (bit per buffer)
+    auto issue = [&](int tix, int buf) {
+        pending |= 1u << buf;
+        const int b = tix / tiles_img, rr = tix % tiles_img;
+        const int tx0 = (rr % tiles_x) * TCW, ty0 = (rr / tiles_x) * TCH;
+        const uint32_t fb = full_s + 8 * buf, dst = halo_s + (uint32_t)(buf * Geo::HALO);
+        const bool inside = a.use_tma && tx0 >= D && tx0 + TCW + D <= a.nx && ty0 >= D && ty0 + TCH + D <= a.ny;
+        if (inside) {
+            if (tid == 0) {
+                mbar_arrive_tx(fb, (uint32_t)(C8 * Geo::PLANE_USED));
+#pragma unroll
+                for (int c8 = 0; c8 < C8; ++c8) tma_load_4d(dst + c8 * Geo::PLANE, &tmap, fb, c8 * 8, tx0 - D, ty0 - D, b);
+            } else {
+                mbar_arrive(fb);
+            }
+        } else {
+            const __nv_bfloat16 *in = a.in + (size_t)b * n * KP;
+            unsigned char *d = halo + (size_t)buf * Geo::HALO;
+            for (int pix = tid; pix < HH * HW; pix += 128) {
+                const int hy = pix / HW, hx = pix % HW;
+                const int gy = halo_wrap(ty0 + hy - D, a.ny), gx = halo_wrap(tx0 + hx - D, a.nx);
+                const __nv_bfloat16 *src = in + ((size_t)gy * a.nx + gx) * KP;
+#pragma unroll
+                for (int c8 = 0; c8 < C8; ++c8) cp_async16(d + (size_t)c8 * Geo::PLANE + (size_t)pix * 16, src + c8 * 8);
+            }
+            asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(fb) : "memory");
+        }
+    };
+    for (int i = 0; i < NBUF - 1; ++i)
+        if (blockIdx.x + i * (int)gridDim.x < ntiles) issue(blockIdx.x + i * gridDim.x, i);
     // weights once per CTA: row co (zero beyond NP), 8 channels per 16 bytes
     for (int e = tid; e < 9 * C8 * N; e += 128) {
         const int tap = e / (C8 * N), c8 = (e / N) % C8, co = e % N;
@@ -204,48 +296,52 @@ __global__ void __launch_bounds__(128) conv3x3_tc(ConvArgs a)
         if (co < NP) v = *reinterpret_cast<const uint4 *>(&a.w[((size_t)tap * NP + co) * KP + c8 * 8]);
         *reinterpret_cast<uint4 *>(wsm + ((size_t)(tap * C8 + c8) * N + co) * 16) = v;
     }
+    if (tid < NP) bias_s[tid] = (MODE != EP_DX && MODE != EP_JVP && a.bias && tid < a.nreal) ? a.bias[tid] : 0.f;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(
                          (uint32_t)__cvta_generic_to_shared(&tmem_base))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the weights, for the tensor cores
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
-    const uint32_t halo_s = (uint32_t)__cvta_generic_to_shared(halo), w_s = (uint32_t)__cvta_generic_to_shared(wsm);
     constexpr uint32_t IDESC = mma_idesc(128, N);
-    const int tiles_x = a.nx / TCW, tiles_img = tiles_x * (a.ny / TCH);
-    unsigned phase = 0;
+    unsigned phase = 0, fphase = 0;  // MMA barrier parity; full-barrier parities, one bit per buffer
     bool failed = false;
-    for (int tix = blockIdx.x; tix < tiles_img * a.nb && !failed; tix += gridDim.x) {
+    int buf = 0;
+    for (int tix = blockIdx.x; tix < ntiles && !failed; tix += gridDim.x, buf = buf + 1 == NBUF ? 0 : buf + 1) {
         const int b = tix / tiles_img, rr = tix % tiles_img;
         const int tx0 = (rr % tiles_x) * TCW, ty0 = (rr / tiles_x) * TCH;
-        const __nv_bfloat16 *in = a.in + (size_t)b * n * KP;
-        // halo tile with circular wrap into the channel planes
-        for (int e = tid; e < HH * HW * C8; e += 128) {
-            const int c8 = e % C8, pix = e / C8, hy = pix / HW, hx = pix % HW;
-            const int gy = halo_wrap(ty0 + hy - D, a.ny), gx = halo_wrap(tx0 + hx - D, a.nx);
-            *reinterpret_cast<uint4 *>(halo + (size_t)c8 * Geo::PLANE + (size_t)pix * 16) =
-                *reinterpret_cast<const uint4 *>(&in[((size_t)gy * a.nx + gx) * KP + c8 * 8]);
+        // tile NBUF - 1 ahead into the buffer the previous tile's MMAs read
+        // (complete: its MMA barrier was waited on)
+        {
+            const int ahead = tix + (NBUF - 1) * (int)gridDim.x;
+            if (ahead < ntiles) issue(ahead, buf == 0 ? NBUF - 1 : buf - 1);
         }
-        // generic-proxy writes visible to the tensor cores (async proxy)
+        {
+            int f = 0;
+            mbar_wait_tc(full_s + 8 * buf, (fphase >> buf) & 1u, f);
+            failed = __syncthreads_or(f) != 0;
+        }
+        if (failed) break;
+        fphase ^= 1u << buf;
+        pending &= ~(1u << buf);
+        // asynchronous-copy writes visible to the tensor cores (async proxy)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (tid == 0) {
+            const uint32_t hb = halo_s + (uint32_t)(buf * Geo::HALO);
 #pragma unroll
             for (int tap = 0; tap < 9; ++tap) {
                 const int dy = (tap / 3) * D, dx = (tap % 3) * D;
 #pragma unroll
                 for (int kc = 0; kc < KP / 16; ++kc) {
-                    const uint64_t ad = smem_desc(halo_s + 2 * kc * Geo::PLANE + (uint32_t)(dy * HW + dx) * 16, Geo::PLANE, HW * 16);
+                    const uint64_t ad = smem_desc(hb + 2 * kc * Geo::PLANE + (uint32_t)(dy * HW + dx) * 16, Geo::PLANE, HW * 16);
                     const uint64_t bd = smem_desc(w_s + (uint32_t)((tap * C8 + 2 * kc) * N * 16), N * 16, 128);
                     const uint32_t acc = (tap | kc) ? 1u : 0u;
                     asm volatile(
@@ -274,44 +370,63 @@ __global__ void __launch_bounds__(128) conv3x3_tc(ConvArgs a)
             const int p = 32 * warp + lane, py = ty0 + p / TCW, px = tx0 + p % TCW;
             const size_t pix = (size_t)b * n + (size_t)py * a.nx + px;
 #pragma unroll
-            for (int c = 0; c < NP; c += 2) {
-                float v0 = v[c], v1 = v[c + 1];
-                if (MODE != EP_DX && MODE != EP_JVP && a.bias) {
-                    if (c < a.nreal) v0 += a.bias[c];
-                    if (c + 1 < a.nreal) v1 += a.bias[c + 1];
-                }
-                if (MODE == EP_TANH) {
-                    v0 = tanhf(v0);
-                    v1 = tanhf(v1);
-                } else if (MODE == EP_DX) {
-                    const float2 yp = *reinterpret_cast<const float2 *>(&a.yprev[pix * NP + c]);
-                    v0 *= 1.f - yp.x * yp.x;
-                    v1 *= 1.f - yp.y * yp.y;
+            for (int c0 = 0; c0 < NP; c0 += 8) {
+                float o[8];
+                if (MODE == EP_DX) {
+                    const float4 y0 = *reinterpret_cast<const float4 *>(&a.yprev[pix * NP + c0]);
+                    const float4 y1 = *reinterpret_cast<const float4 *>(&a.yprev[pix * NP + c0 + 4]);
+                    const float yp[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) o[j] = v[c0 + j] * (1.f - yp[j] * yp[j]);
                 } else if (MODE == EP_JVP) {
-                    const float y0 = __bfloat162float(a.ycur[pix * NP + c]), y1 = __bfloat162float(a.ycur[pix * NP + c + 1]);
-                    v0 *= 1.f - y0 * y0;
-                    v1 *= 1.f - y1 * y1;
+                    const uint4 yv = *reinterpret_cast<const uint4 *>(&a.ycur[pix * NP + c0]);
+                    const uint32_t w4[4] = {yv.x, yv.y, yv.z, yv.w};
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float y = __uint_as_float(j & 1 ? (w4[j >> 1] & 0xFFFF0000u) : (w4[j >> 1] << 16));
+                        o[j] = v[c0 + j] * (1.f - y * y);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float z = v[c0 + j] + bias_s[c0 + j];
+                        o[j] = MODE == EP_TANH ? tanh_fast(z) : z;
+                    }
                 }
-                if (c >= a.nreal) v0 = 0.f;
-                if (c + 1 >= a.nreal) v1 = 0.f;
-                if (a.out_bf)
-                    *reinterpret_cast<uint32_t *>(&a.out_bf[pix * NP + c]) = pack2(__float2bfloat16_rn(v0), __float2bfloat16_rn(v1));
-                if (a.out_f) *reinterpret_cast<float2 *>(&a.out_f[pix * NP + c]) = make_float2(v0, v1);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (c0 + j >= a.nreal) o[j] = 0.f;
+                if (a.out_bf) {
+                    uint4 pk;
+                    pk.x = pack2(__float2bfloat16_rn(o[0]), __float2bfloat16_rn(o[1]));
+                    pk.y = pack2(__float2bfloat16_rn(o[2]), __float2bfloat16_rn(o[3]));
+                    pk.z = pack2(__float2bfloat16_rn(o[4]), __float2bfloat16_rn(o[5]));
+                    pk.w = pack2(__float2bfloat16_rn(o[6]), __float2bfloat16_rn(o[7]));
+                    *reinterpret_cast<uint4 *>(&a.out_bf[pix * NP + c0]) = pk;
+                }
+                if (a.out_f) {
+                    *reinterpret_cast<float4 *>(&a.out_f[pix * NP + c0]) = make_float4(o[0], o[1], o[2], o[3]);
+                    *reinterpret_cast<float4 *>(&a.out_f[pix * NP + c0 + 4]) = make_float4(o[4], o[5], o[6], o[7]);
+                }
             }
         }
         // every thread has read the accumulator and the MMAs no longer read
-        // the halo tile: the next tile may overwrite both
+        // this halo tile: the next tiles may overwrite both
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
     if (failed) {
         if (tid == 0 && a.err) atomicOr(a.err, 4);
-        // the MMAs of the abandoned tile: wait for them once more (bounded)
+        // the MMAs of an abandoned tile, and the loads issued ahead of it
+        // into this CTA's shared memory: wait for them once more (bounded)
         int f = 0;
         mbar_wait_tc(bar, phase, f);
-        __syncthreads();
+        for (int i = 0; i < NBUF; ++i)
+            if (pending >> i & 1u) mbar_wait_tc(full_s + 8 * i, (fphase >> i) & 1u, f);
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
 }
 
@@ -569,26 +684,72 @@ __global__ void __launch_bounds__(256) sum_parts(const double *part, int cnt, do
     if (threadIdx.x == 0) out[0] = s / denom;
 }
 
-// Reduce dW partials [nblk][9][CO][CI] and dB (sum of dZ over pixels) into the
-// gradient of the packed master parameters of one layer.
-__global__ void reduce_dw(const float *part, int nblk, int co_real, int ci_real, int CO, int CI, float *gw)
+// Reduce dW partials [nblk][9][CO][CI] into the gradient of the packed
+// master parameters of one layer ([co][ci][tap]).  A block takes 32
+// consecutive entries of a partial (ci fastest: coalesced) and 8 slices of
+// the partials; the slices' FP64 sums are added in a fixed order.
+constexpr int kDwSlices = 8;
+constexpr int kBiasBlocks = 304;  // blocks of the bias-gradient partial sums (2 per SM)
+__global__ void __launch_bounds__(256) reduce_dw(const float *part, int nblk, int co_real, int ci_real, int CO, int CI, float *gw)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;  // over co_real * ci_real * 9 (master layout [co][ci][tap])
-    if (i >= co_real * ci_real * 9) return;
-    const int co = i / (ci_real * 9), ci = (i / 9) % ci_real, tap = i % 9;
+    __shared__ double red[kDwSlices][32];
+    const int e = blockIdx.x * 32 + (threadIdx.x & 31), sl = threadIdx.x >> 5;  // e over [tap][CO][CI]
+    const int per = 9 * CO * CI;
     double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += (double)part[((size_t)b * 9 + tap) * CO * CI + (size_t)co * CI + ci];
-    gw[i] = (float)s;
+    if (e < per)
+        for (int b = sl; b < nblk; b += kDwSlices) s += (double)part[(size_t)b * per + e];
+    red[sl][threadIdx.x & 31] = s;
+    __syncthreads();
+    if (sl == 0 && e < per) {
+        double t = 0.0;
+        for (int k = 0; k < kDwSlices; ++k) t += red[k][threadIdx.x];
+        const int tap = e / (CO * CI), co = (e / CI) % CO, ci = e % CI;
+        if (co < co_real && ci < ci_real) gw[((size_t)co * ci_real + ci) * 9 + tap] = (float)t;
+    }
 }
 
-__global__ void __launch_bounds__(256) bias_grad(const __nv_bfloat16 *dz, long long npix, int CO, int co_real, float *gb)
+// Bias gradient dB[co] = sum over pixels of dZ[p][co] (CO = 16 or 32): each
+// thread reads 8 channels of a pixel per load and keeps FP32 sums over its
+// few pixels; FP64 block sums per channel to part[block][co], then
+// bias_grad_finish adds the blocks in a fixed order.
+__global__ void __launch_bounds__(256) bias_grad_part(const __nv_bfloat16 *dz, long long npix, int CO, double *part)
 {
-    __shared__ double red[32];
-    const int co = blockIdx.x;
-    double s = 0.0;
-    for (long long p = threadIdx.x; p < npix; p += blockDim.x) s += (double)__bfloat162float(dz[(size_t)p * CO + co]);
-    s = block_sum(s, red);
-    if (threadIdx.x == 0 && co < co_real) gb[co] = (float)s;
+    __shared__ double red[256][8];
+    const int c8n = CO / 8, g = threadIdx.x % c8n;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const long long stride = (long long)gridDim.x * (blockDim.x / c8n);
+    for (long long p = (long long)blockIdx.x * (blockDim.x / c8n) + threadIdx.x / c8n; p < npix; p += stride) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(&dz[(size_t)p * CO + g * 8]);
+        const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[j] += __uint_as_float(j & 1 ? (w4[j >> 1] & 0xFFFF0000u) : (w4[j >> 1] << 16));
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) red[threadIdx.x][j] = (double)acc[j];
+    __syncthreads();
+    if (threadIdx.x < CO) {
+        const int c = threadIdx.x, gc = c / 8, j = c % 8;
+        double t = 0.0;
+        for (int k = gc; k < (int)blockDim.x; k += c8n) t += red[k][j];
+        part[(size_t)blockIdx.x * CO + c] = t;
+    }
+}
+// (one block of 256 threads: 8 slices of the blocks per channel, the
+// slices' sums added in a fixed order)
+__global__ void __launch_bounds__(256) bias_grad_finish(const double *part, int nblk, int CO, int co_real, float *gb)
+{
+    __shared__ double red[8][32];
+    const int c = threadIdx.x & 31, sl = threadIdx.x >> 5;
+    double t = 0.0;
+    if (c < CO)
+        for (int b = sl; b < nblk; b += 8) t += part[(size_t)b * CO + c];
+    red[sl][c] = t;
+    __syncthreads();
+    if (sl == 0 && c < co_real) {
+        double u = 0.0;
+        for (int k = 0; k < 8; ++k) u += red[k][c];
+        gb[c] = (float)u;
+    }
 }
 
 // Adam on the FP32 master parameters (Kingma and Ba, 2015).
@@ -697,12 +858,13 @@ size_t carve(Work &w, char *base, int nb, int ny, int nx, bool training)
         w.grad = (float *)take((size_t)num_params() * sizeof(float));
         w.tmean = (double *)take((size_t)nb * 3 * sizeof(double));
         w.lpart = (double *)take((size_t)((np + 255) / 256 + 1) * sizeof(double));
+        w.bpart = (double *)take((size_t)kBiasBlocks * 32 * sizeof(double));
     } else {
         for (int l = 0; l < 3; ++l) w.yf[l] = nullptr;
         w.dz[0] = w.dz[1] = w.dz4 = nullptr;
         for (int l = 0; l < kLayers; ++l) w.wb[l] = nullptr;
         w.dwpart = w.grad = nullptr;
-        w.tmean = w.lpart = nullptr;
+        w.tmean = w.lpart = w.bpart = nullptr;
         w.nblk_dw = 0;
     }
     return al(off);
@@ -736,6 +898,40 @@ static cudaError_t pack_all(Work &w, const float *params, bool backward, cudaStr
     return cudaGetLastError();
 }
 
+// The driver's tensor-map encoder, looked up once through the runtime.
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// Tensor map of a BF16 activation tensor [nb][ny][nx][kp] with boxes of 8
+// channels x hw x hh pixels (one halo plane); false if none can be made
+// (the convolution then loads every tile by asynchronous copies).
+static bool halo_map(CUtensorMap *m, const void *base, int kp, int nx, int ny, int nb, int hw, int hh)
+{
+    std::memset(m, 0, sizeof *m);
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || ((uintptr_t)base & 15)) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)kp, (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nb};
+    const cuuint64_t strides[3] = {(cuuint64_t)kp * 2, (cuuint64_t)nx * kp * 2, (cuuint64_t)nx * ny * kp * 2};
+    const cuuint32_t box[4] = {8, (cuuint32_t)hw, (cuuint32_t)hh, 1};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(base), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int KP, int NP, int MODE, int D>
 static void conv(Work &w, const void *in, const void *wt, const float *bias, void *out_bf, float *out_f, const float *yprev, int nreal,
                  cudaStream_t s, const void *ycur = nullptr)
@@ -747,6 +943,8 @@ static void conv(Work &w, const void *in, const void *wt, const float *bias, voi
         conf = true;
     }
     ConvArgs a;
+    CUtensorMap map;
+    a.use_tma = halo_map(&map, in, KP, w.nx, w.ny, w.nb, HaloTC<D>::HW, HaloTC<D>::HH) ? 1 : 0;
     a.ycur = reinterpret_cast<const __nv_bfloat16 *>(ycur);
     a.err = w.err;
     a.in = reinterpret_cast<const __nv_bfloat16 *>(in);
@@ -762,8 +960,8 @@ static void conv(Work &w, const void *in, const void *wt, const float *bias, voi
     a.nreal = nreal;
     a.nb = w.nb;
     const int tiles = w.nb * (w.nx / TCW) * (w.ny / TCH);
-    const int per_sm = std::max(1, (int)((200u << 10) / smem));
-    conv3x3_tc<KP, NP, MODE, D><<<std::min(tiles, per_sm * 152), 128, smem, s>>>(a);
+    const int per_sm = std::max(1, std::min(16, (int)((220u << 10) / (smem + 1024))));
+    conv3x3_tc<KP, NP, MODE, D><<<std::min(tiles, per_sm * 152), 128, smem, s>>>(a, map);
 }
 
 static cudaError_t forward_layers(Work &w, const float *params, cudaStream_t s)
@@ -833,10 +1031,9 @@ static void layer_grads(Work &w, int l, const void *x, const void *dzp, int CO, 
     else if (l == 1) dw<32, 32, kD1>(w, x, dzp, s);
     else if (l == 2) dw<32, 32, kD2>(w, x, dzp, s);
     else dw<32, 16, kD3>(w, x, dzp, s);
-    const int nw = kCout[l] * kCin[l] * 9;
-    reduce_dw<<<blocks(nw), 256, 0, s>>>(w.dwpart, w.nblk_dw, kCout[l], kCin[l], CO, CI, w.grad + param_offset_w(l));
-    bias_grad<<<CO, 256, 0, s>>>(reinterpret_cast<const __nv_bfloat16 *>(dzp), (long long)w.nb * w.n, CO, kCout[l],
-                                 w.grad + param_offset_b(l));
+    reduce_dw<<<(9 * CO * CI + 31) / 32, 256, 0, s>>>(w.dwpart, w.nblk_dw, kCout[l], kCin[l], CO, CI, w.grad + param_offset_w(l));
+    bias_grad_part<<<kBiasBlocks, 256, 0, s>>>(reinterpret_cast<const __nv_bfloat16 *>(dzp), (long long)w.nb * w.n, CO, w.bpart);
+    bias_grad_finish<<<1, 256, 0, s>>>(w.bpart, kBiasBlocks, CO, kCout[l], w.grad + param_offset_b(l));
     w.nblk_dw = ntiles_cap;
 }
 

@@ -31,6 +31,7 @@ struct Work {
     void *wf[kLayers], *wb[kLayers];
     float *dwpart, *grad;
     double *means, *ymean, *qs, *tmean, *lpart, *red;
+    double *bpart;         // bias-gradient partials [block][32] (training)
     int nblk_dw;
 };
 
