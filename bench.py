@@ -642,7 +642,9 @@ def config_section(P, W, torch, name, flush, args, rank):
     if name == "vesicle" and args.surrogate_pairs > 0:
         train_runs = [W.with_(runs[0], nx=512, ny=256, seed=runs[0].seed + 31 * k) for k in range(4)]
         sm, s_in, s_out, info = train_surrogate(P, W, torch, train_runs, args.config_surrogate_pairs)
-        sur = evaluate_surrogate(P, torch, runs, sm, s_in, s_out, flush, args.config_steps, args.config_eval_steps, ms)
+        # timed over whole cycles of the exact-every-8 schedule
+        sur = evaluate_surrogate(P, torch, runs, sm, s_in, s_out, flush, 8 * max(2, -(-args.config_steps // 8)),
+                                 args.config_eval_steps, ms)
         sur["training"] = info
         out["surrogate"] = sur
     return out
@@ -686,7 +688,7 @@ def main():
     ap.add_argument("--configs", default="ensemble32,vesicle",
                     help="other configurations measured into the line's configs key (comma list; empty: none)")
     ap.add_argument("--config-steps", type=int, default=5)
-    ap.add_argument("--config-surrogate-pairs", type=int, default=16000)
+    ap.add_argument("--config-surrogate-pairs", type=int, default=32000)
     ap.add_argument("--config-eval-steps", type=int, default=200)
     ap.add_argument("--exact-steps", type=int, default=5,
                     help="steps of the exact step (CG inversion) timed on the same workload; 0 skips it")
