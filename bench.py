@@ -778,13 +778,20 @@ def main():
         # radix-8 row pass = chain read 8 + write 8, factors 8, history store 8;
         # radix-2 row pass accumulating the contour sums also reads the history
         # and read-modify-writes the FP64 sums; column pass = chain read + write
+        # MIXED (differential second solve, whose passes are the timed ones):
+        # chain read + write 16, factors 8, rho 8, reference node 8, change
+        # store 8 in every row pass
         radix8 = tiles_path == 1
-        bytes_per_site = {"prop_row_accumulate": 32.0 if radix8 else 64.0, "prop_row_store": 32.0, "prop_col": 16.0}
+        if h.tiles(0)["differential"]:
+            bytes_per_site = {"prop_row_accumulate": 48.0, "prop_row_store": 48.0, "prop_col": 16.0}
+        else:
+            bytes_per_site = {"prop_row_accumulate": 32.0 if radix8 else 64.0, "prop_row_store": 32.0, "prop_col": 16.0}
         for k, bps in bytes_per_site.items():
             gbs = bps * nsite / (kt[k] * 1e-3) / 1e9
             kernels[k] = {"ms": kt[k], "bytes_per_site": bps, "achieved_gbs": gbs, "frac": gbs / hbm}
         dom = "prop_row_accumulate"
-        name = "prop_row8 (row pass of one contour step, radix-8 streaming)" if radix8 else dom
+        name = ("prop_row8 (row pass of one contour step, radix-8 streaming" if radix8 else "prop_row (row pass, streaming") + \
+            (", differential second solve)" if h.tiles(0)["differential"] else ")")
         roofline = {"bound": "hbm", "kernel": name, "achieved": kernels[dom]["achieved_gbs"], "peak": hbm,
                     "unit": "GB/s", "frac": kernels[dom]["achieved_gbs"] / hbm, "traffic": None,
                     "peak_source": f"{peak_kind} hbm_gbs (copy)"}

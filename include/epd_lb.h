@@ -61,12 +61,11 @@ enum {
     EPD_LB_PLAIN_FP64 = 0,   /* every field and transform in FP64            */
     EPD_LB_MIXED_FP32 = 1    /* propagators, LB populations and the EPD/force
                                 transforms in FP32; fields omega and Phi,
-                                contour sums, Q and masses in FP64.  On grids
-                                of 2^12..2^17 sites with 64..512 points per
-                                axis the step's second solve is computed as
-                                its difference from the first (same result
-                                up to rounding, FP32 relative to the
-                                change)                                      */
+                                contour sums, Q and masses in FP64.  The
+                                step's second solve is computed as its
+                                difference from the first (same result up to
+                                rounding, FP32 relative to the change that
+                                drives the force of Eqs. (19)-(20))          */
 };
 
 /*
@@ -113,7 +112,7 @@ typedef struct epd_lb_params {
 typedef struct epd_lb epd_lb; /* opaque, library-owned */
 
 /* Device workspace needed by epd_lb_init for nruns runs described by the
- * array p[0..nruns-1].  Runs may differ in every parameter; runs sharing grid,
+ * array p[0..nruns-1] (memory management, not in the paper).  Runs may differ in every parameter; runs sharing grid,
  * contour length, precision and model parameters are stepped as one batch. */
 int epd_lb_workspace_bytes(const epd_lb_params *p, int32_t nruns, size_t *bytes);
 
@@ -130,12 +129,15 @@ int epd_lb_init(const epd_lb_params *p, int32_t nruns, void *workspace, size_t w
                 void *cuda_stream, epd_lb **out);
 
 /* Advance every run by nsteps time steps (the six operations listed at the
- * top).  Asynchronous on the handle's stream; the step sequence is captured
- * once into a CUDA graph and replayed. */
+ * top, App. C).  Asynchronous on the handle's stream; the step sequence is
+ * captured once into a CUDA graph and replayed. */
 int epd_lb_step(epd_lb *h, int64_t nsteps);
 
-/* Wait for the handle's stream and report device-side errors
- * (EPD_LB_ENONFINITE when a solve produced Q <= 0 or a non-finite Q). */
+/* Wait for the handle's stream and report device-side errors:
+ * EPD_LB_ENONFINITE when a solve produced Q <= 0 or a non-finite Q (Q_P, Q_S
+ * of Eqs. (9)-(11) are spatial means of positive propagators, so a
+ * non-finite field anywhere reaches them), EPD_LB_ETIMEOUT when a bounded
+ * device wait gave up. */
 int epd_lb_sync(epd_lb *h);
 
 /* Phi_{A,B,S}(t) of run `run` (3*ny*nx doubles) and q[0] = Q_P, q[1] = Q_S of
@@ -143,8 +145,9 @@ int epd_lb_sync(epd_lb *h);
  * pointer may be NULL.  Synchronous. */
 int epd_lb_densities(epd_lb *h, int32_t run, double *phi, double *q);
 
-/* omega (3*ny*nx) and Phi (3*ny*nx) of run `run` into caller device memory
- * (FP64, asynchronous on the handle's stream); either pointer may be NULL. */
+/* omega (3*ny*nx; the fields conjugate to the densities, Sec. 2) and Phi
+ * (3*ny*nx; Eqs. (9)-(11)) of run `run` into caller device memory (FP64,
+ * asynchronous on the handle's stream); either pointer may be NULL. */
 int epd_lb_fields_dev(epd_lb *h, int32_t run, double *omega_dev, double *phi_dev);
 
 /* The intermediate fields of the last step of run `run` into caller device
@@ -156,8 +159,9 @@ int epd_lb_fields_dev(epd_lb *h, int32_t run, double *omega_dev, double *phi_dev
  * difference carries FP32 precision relative to itself. */
 int epd_lb_step_fields_dev(epd_lb *h, int32_t run, double *omega_tilde_dev, double *phi_tilde_dev);
 
-/* Fluid velocity u = (j + f/2)/rho of the last collision, lattice units,
- * 2*ny*nx doubles.  Synchronous. */
+/* Fluid velocity u = (j + f/2)/rho of the last collision (the LB moments of
+ * Eq. (12) with the force of Eq. (14), read in the Dunweg-Ladd form), lattice
+ * units, 2*ny*nx doubles.  Synchronous. */
 int epd_lb_velocity(epd_lb *h, int32_t run, double *v);
 
 /* Device-pointer variants of the two calls above: asynchronous copies on the
@@ -165,9 +169,11 @@ int epd_lb_velocity(epd_lb *h, int32_t run, double *v);
 int epd_lb_densities_dev(epd_lb *h, int32_t run, double *phi_dev, double *q_dev);
 int epd_lb_velocity_dev(epd_lb *h, int32_t run, double *v_dev);
 
-/* Full state of a run: omega (3n), pre-collision LB populations (9n, the
+/* Full state of a run, what App. C carries from one step to the next:
+ * omega (3n, Sec. 2), pre-collision LB populations (9n, Eq. (12): the
  * populations about to be collided at the next step) and the velocity handed
- * to the next convection step (2n).  Any pointer may be NULL.  Synchronous. */
+ * to the next convection step (2n, App. C item 1).  Any pointer may be NULL.
+ * Synchronous. */
 int epd_lb_get_state(epd_lb *h, int32_t run, double *omega, double *pop, double *vel);
 
 /* Replace the state of a run (same layout as epd_lb_get_state).  A NULL
@@ -184,28 +190,32 @@ int epd_lb_set_state(epd_lb *h, int32_t run, const double *omega, const double *
 int epd_lb_solve(epd_lb *h, int32_t run, const double *omega, double *phi, double *q);
 
 /* Per-run observables of the current state: out[0] = <Phi_A>, out[1] = <Phi_B>,
- * out[2] = <Phi_S>, out[3] = sigma of Eq. (21), out[4] = LB mass / sites,
- * out[5] = max |u| (lattice), out[6] = Q_P, out[7] = Q_S.  Sums in a fixed
+ * out[2] = <Phi_S> (each conserved by Eqs. (2) and (5)), out[3] = sigma of
+ * Eq. (21), out[4] = LB mass / sites (conserved by Eq. (12)), out[5] = max |u|
+ * (lattice), out[6] = Q_P, out[7] = Q_S (Eqs. (9)-(11)).  Sums in a fixed
  * order: a repeated call returns identical values.  Synchronous. */
 int epd_lb_observables(epd_lb *h, int32_t run, double *out);
 
-/* Checkpoint: serialise every run's state (parameters, omega, the stored LB
- * populations in the library's internal representation, velocity) to buf.
+/* Checkpoint (no counterpart in the paper): serialise every run's state
+ * (parameters, omega, the stored LB populations in the library's internal
+ * representation, velocity; the state of App. C) to buf.
  * With buf == NULL only *len is set to the size needed.  Restoring with
  * epd_lb_load into a handle created with the same parameters recomputes Phi
  * and continues bit-identically. */
 int epd_lb_save(epd_lb *h, void *buf, size_t *len);
 int epd_lb_load(epd_lb *h, const void *buf, size_t len);
 
-/* Kernel timing inside the captured step.  epd_lb_enable_timing(h, 1)
+/* Kernel timing inside the captured step (a measurement service, no
+ * counterpart in the paper).  epd_lb_enable_timing(h, 1)
  * re-captures the step graph with CUDA event-record nodes around launches of
  * the first batch's second single-chain solve and its LB collide-stream.
  * epd_lb_kernel_times waits for the stream and writes the durations of the
  * most recent step in milliseconds: ms[0..2] the propagator kernels, ms[3]
  * the LB collide-stream, ms[4] a flag.  With the streaming transform passes
- * (ms[4] = 0): ms[0] the row pass of contour node N_s/4 (history store),
- * ms[1] the row pass of node 3 N_s/4 + 1 (contour accumulation), ms[2] the
- * column pass before it.  With the cluster-resident solve (ms[4] = 1): ms[0]
+ * (ms[4] = 0): ms[0] the row pass of contour node N_s/4, ms[1] the row pass
+ * of node 3 N_s/4 + 1 (where the PLAIN_FP64 passes accumulate the contour
+ * sums), ms[2] the column pass before it; in MIXED_FP32 these are passes of
+ * the differential second solve.  With the cluster-resident solve (ms[4] = 1): ms[0]
  * its chain launches (the whole contour of both chains of every run, in one
  * launch or the phased schedule's several, see epd_lb_tiles; the
  * differential solve where the step uses one), ms[1] = ms[2] = 0. */
@@ -213,8 +223,8 @@ int epd_lb_enable_timing(epd_lb *h, int32_t on);
 int epd_lb_kernel_times(epd_lb *h, double *ms);
 
 /* Launch configuration chosen for a run's group (batching and tiling of the
- * hot path; not in the paper).  out[0]: solve path, 0 = streaming radix-2
- * passes, 1 = streaming radix-8 passes with the full contour history, 2 =
+ * hot path; not in the paper).  out[0]: solve path, 0 = streaming radix-2 /
+ * mixed-radix passes, 1 = streaming radix-8 passes with the full contour history, 2 =
  * cluster-resident solve; out[1]: CTAs per cluster (path 2) or 0; out[2]: the
  * column tile width of the radix-8 column passes (EPD and streaming
  * propagator; 4, 8 or 16 columns), chosen at epd_lb_init by timing each
@@ -296,9 +306,10 @@ int epd_sur_train_step(const epd_lb_params *p, int32_t batch, float *params_dev,
 int epd_lb_surrogate_workspace_bytes(epd_lb *h, size_t *bytes);
 int epd_lb_set_surrogate(epd_lb *h, const float *params_host, double s_in, double s_out, int32_t exact_every,
                          double residual_tol, int32_t hold_force, void *workspace, size_t workspace_bytes);
-/* out[0] steps taken with the surrogate attached, out[1] exact steps,
- * out[2] surrogate steps, out[3] exact steps forced by a failed check,
- * out[4] last residual, out[5] 1 if currently falling back. */
+/* Controller statistics of epd_lb_set_surrogate (not in the paper): out[0]
+ * steps taken with the surrogate attached, out[1] exact steps, out[2]
+ * surrogate steps, out[3] exact steps forced by a failed check, out[4] last
+ * residual (relative, as above), out[5] 1 if currently falling back. */
 int epd_lb_surrogate_stats(epd_lb *h, double *out);
 
 /* Exact step of App. C.  With max_iter > 0, epd_lb_step replaces steps 1-2
@@ -318,15 +329,16 @@ int epd_lb_surrogate_stats(epd_lb *h, double *out);
  * sqrt(sum_I <(Phi~_I - Phi_I)^2>) < tol (N_tr = 1e-8 in the paper);
  * tol = 0 runs exactly max_iter iterations.  A step whose runs did not all
  * converge within max_iter iterations is completed and epd_lb_step returns
- * EPD_LB_ENOTCONV after it.  Needs PLAIN_FP64 groups or MIXED_FP32 groups on
- * the cluster-resident solve (there every density of the step is a
- * difference from the solve at the starting guess; other MIXED grids give
- * EPD_LB_EINVAL); excludes the surrogate.  The step is then enqueued eagerly
+ * EPD_LB_ENOTCONV after it.  In MIXED_FP32 every density of the step is a
+ * difference from the solve at the starting guess (so the mismatch carries
+ * FP32 rounding relative to the changes only); excludes the surrogate
+ * (EPD_LB_EINVAL).  The step is then enqueued eagerly
  * (no graph) and synchronises once per iteration when tol > 0.
  * max_iter = 0 (the default) restores the truncated step. */
 int epd_lb_set_inversion(epd_lb *h, int32_t max_iter, double tol);
-/* Of the last exact step of run `run`: out[0] CG iterations, out[1] the
- * residual at the starting guess, out[2] the final residual.  Synchronous. */
+/* Of the last exact step of run `run` (App. C items 2-3): out[0] CG
+ * iterations, out[1] the residual at the starting guess, out[2] the final
+ * residual.  Synchronous. */
 int epd_lb_inversion_stats(epd_lb *h, int32_t run, double *out);
 
 /* Analysis of the polymer distribution Phi_P = Phi_A + Phi_B of the current
@@ -356,7 +368,8 @@ int epd_lb_width(epd_lb *h, int32_t run, double *out);
 int epd_lb_particles(epd_lb *h, int32_t run, double threshold, int32_t max_particles, int32_t *count,
                      double *stats, int32_t *labels);
 
-/* Self-test of the failure path of the cluster solve's exchanges: one CTA
+/* Self-test of the failure path of the cluster solve's exchanges (failure
+ * detection, not in the paper): one CTA
  * waits, with the same bounded wait as every exchange of the solve, on a
  * barrier that nothing arrives on; after limit_ms milliseconds (1..2000, at
  * the device's base clock) it gives up and sets the error bit that
@@ -364,10 +377,11 @@ int epd_lb_particles(epd_lb *h, int32_t run, double threshold, int32_t max_parti
  * set.  The context stays usable.  Synchronous on cuda_stream. */
 int epd_selftest_bounded_wait(int32_t limit_ms, void *cuda_stream, int32_t *timed_out);
 
-/* Text of the last error on the handle (never NULL). */
+/* Text of the last error on the handle (never NULL; not in the paper). */
 const char *epd_lb_last_error(const epd_lb *h);
 
-/* Release the handle (and its workspace if the library allocated it). */
+/* Release the handle (and its workspace if the library allocated it; not in
+ * the paper). */
 void epd_lb_destroy(epd_lb *h);
 
 /*
