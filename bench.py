@@ -606,6 +606,32 @@ def surrogate_section(P, W, torch, runs, flush, args, exact_ms):
     return out
 
 
+def group_concurrency(P, runs, flush, steps=10):
+    """How much the step graph's per-group streams overlap: the median step
+    of all runs in one handle (one graph, a stream per group) against the
+    sum of the medians of every group stepped alone (L2 flushed before each
+    timed step)."""
+    import collections
+
+    import numpy as np
+
+    def median_step(rs):
+        h = P.EpdLb(rs)
+        h.step(2)
+        h.sync()
+        per, _ = time_steps(h, h.stream, steps, flush)
+        h.close()
+        return float(np.median(per))
+
+    groups = collections.OrderedDict()
+    for r in runs:
+        groups.setdefault((r.ny, r.nx, r.ns), []).append(r)
+    alone = {f"{ny}x{nx} N_s={ns}": median_step(rs) for (ny, nx, ns), rs in groups.items()}
+    together = median_step(runs)
+    return {"graph_ms": together, "groups": len(groups), "sum_of_groups_alone_ms": sum(alone.values()),
+            "overlap": sum(alone.values()) / together, "groups_alone_ms": alone}
+
+
 def config_section(P, W, torch, name, flush, args, rank):
     """Another configuration of the benchmark set, measured as the headline
     line: CUDA-event ms per step over args.config_steps steps (L2 flushed
@@ -639,6 +665,8 @@ def config_section(P, W, torch, name, flush, args, rank):
     out["mixed_error"]["steps"] = 3
     hm.close()
     h64.close()
+    if name == "ensemble32":
+        out["concurrency"] = group_concurrency(P, runs, flush)
     if name == "vesicle" and args.surrogate_pairs > 0:
         train_runs = [W.with_(runs[0], nx=512, ny=256, seed=runs[0].seed + 31 * k) for k in range(4)]
         sm, s_in, s_out, info = train_surrogate(P, W, torch, train_runs, args.config_surrogate_pairs)

@@ -339,28 +339,42 @@ __global__ void __launch_bounds__(RowTile<LOGX>::T) epd_row8(EpdK k)
     const long long base = (long long)blockIdx.x * P;
     float2 *cz = reinterpret_cast<float2 *>(k.cz);
     copy_tables(tab, k.tab8x, RT::TAB, tid, T);
+    // the inputs of this thread in batches, each batch's loads before its
+    // stores (the scratch planes written below could alias the fields as far
+    // as the compiler knows, so interleaving would serialise the loads
+    // behind the stores)
+    constexpr int UB = P / T < 8 ? P / T : 8;  // inputs per batch
 #pragma unroll
-    for (int u = 0; u < P / T; ++u) {
-        const int i = tid + u * T;
-        const long long s = base + i;
-        float2 v;
-        if (MODE == ROW_GRAD) {
-            const double *om = k.omega + (size_t)run * 3 * n;
-            v = pair == 0 ? f2((float)om[s], (float)om[n + s]) : f2((float)om[2 * n + s], 0.f);
-        } else if (MODE == ROW_LAP) {
-            v = mu_pair_f(k, k.phi_t + (size_t)run * 3 * n, k.omega_t + (size_t)run * 3 * n, n, s, pair);
-        } else if (MODE == ROW_FWD_S) {
-            // S = sum_I dPhi_I^D / D_I from the FP64 differences, in FP32
-            const double *p1 = k.phi + (size_t)run * 3 * n, *p0 = k.phi_t + (size_t)run * 3 * n;
-            const float da = (float)(p1[s] - p0[s]), db = (float)(p1[n + s] - p0[n + s]), dsv = (float)(p1[2 * n + s] - p0[2 * n + s]);
-            v = f2((da + db) * (float)(1.0 / g.d_p) + dsv * (float)(1.0 / g.d_s), 0.f);
-        } else {
-            v = cz[((size_t)run * 4 + 2) * n + s];
+    for (int u0 = 0; u0 < P / T; u0 += UB) {
+        float2 vin[UB];
+#pragma unroll
+        for (int u = u0; u < u0 + UB; ++u) {
+            const int i = tid + u * T;
+            const long long s = base + i;
+            float2 v;
+            if (MODE == ROW_GRAD) {
+                const double *om = k.omega + (size_t)run * 3 * n;
+                v = pair == 0 ? f2((float)om[s], (float)om[n + s]) : f2((float)om[2 * n + s], 0.f);
+            } else if (MODE == ROW_LAP) {
+                v = mu_pair_f(k, k.phi_t + (size_t)run * 3 * n, k.omega_t + (size_t)run * 3 * n, n, s, pair);
+            } else if (MODE == ROW_FWD_S) {
+                // S = sum_I dPhi_I^D / D_I from the FP64 differences, in FP32
+                const double *p1 = k.phi + (size_t)run * 3 * n, *p0 = k.phi_t + (size_t)run * 3 * n;
+                const float da = (float)(p1[s] - p0[s]), db = (float)(p1[n + s] - p0[n + s]), dsv = (float)(p1[2 * n + s] - p0[2 * n + s]);
+                v = f2((da + db) * (float)(1.0 / g.d_p) + dsv * (float)(1.0 / g.d_s), 0.f);
+            } else {
+                v = cz[((size_t)run * 4 + 2) * n + s];
+            }
+            vin[u - u0] = v;
         }
-        // the column pass of the same operator reads this FP32 input from the
-        // free scratch planes 2, 3 instead of forming it again from FP64 fields
-        if (MODE == ROW_GRAD || MODE == ROW_LAP) cz[((size_t)run * 4 + 2 + pair) * n + s] = v;
-        buf[RL::at(i / NX, i % NX)] = v;
+#pragma unroll
+        for (int u = u0; u < u0 + UB; ++u) {
+            const int i = tid + u * T;
+            // the column pass of the same operator reads this FP32 input from the
+            // free scratch planes 2, 3 instead of forming it again from FP64 fields
+            if (MODE == ROW_GRAD || MODE == ROW_LAP) cz[((size_t)run * 4 + 2 + pair) * n + base + i] = vin[u - u0];
+            buf[RL::at(i / NX, i % NX)] = vin[u - u0];
+        }
     }
     __syncthreads();
     if (MODE == ROW_FWD_S) {
@@ -437,37 +451,71 @@ __global__ void __launch_bounds__(ColTile<LOGY, CW>::T) epd_col8(EpdK k)
     float2 h[NB_L][RR];
     int bb[NB_L], tt[NB_L];
     last_inverse<LOGY, NB_L, T, CL, CT::MR>(buf, h, bb, tt, tid);
+    // in batches of SB points: every load first, then the stores (the output
+    // field could alias the inputs as far as the compiler knows, which would
+    // serialise each load behind the previous stores)
+    constexpr int SB = RR < 4 ? RR : 4;
 #pragma unroll
     for (int j = 0; j < NB_L; ++j)
 #pragma unroll
-        for (int r = 0; r < RR; ++r) {
-            const long long s = (long long)(tt[j] + r * PER_L) * nx + x0 + bb[j];
+        for (int r0 = 0; r0 < RR; r0 += SB) {
+            long long sj[SB];
+#pragma unroll
+            for (int b = 0; b < SB; ++b) sj[b] = (long long)(tt[j] + (r0 + b) * PER_L) * nx + x0 + bb[j];
             if (MODE == COL_FORCE) {
-                cz[((size_t)run * 4 + 2) * n + s] = h[j][r];
+#pragma unroll
+                for (int b = 0; b < SB; ++b) cz[((size_t)run * 4 + 2) * n + sj[b]] = h[j][r0 + b];
             } else if (MODE == COL_CONVECT) {
                 // omega~ = omega - dt v . grad omega, v = u_lat dx/dt (increment in FP32)
-                const float2 dyf = h[j][r], dxf = cz[((size_t)run * 4 + pair) * n + s];
-                const float2 u = reinterpret_cast<const float2 *>(k.vel)[(size_t)run * n + s];  // FP32 bulk
-                const float cv = (float)(g.vscale * g.dt), vx = u.x * cv, vy = u.y * cv;
                 const double *om = k.omega + (size_t)run * 3 * n;
                 double *ot = k.omega_dst + (size_t)run * 3 * n;
-                if (pair == 0) {
-                    ot[s] = om[s] - (double)(vx * dxf.x + vy * dyf.x);
-                    ot[n + s] = om[n + s] - (double)(vx * dxf.y + vy * dyf.y);
-                } else {
-                    ot[2 * n + s] = om[2 * n + s] - (double)(vx * dxf.x + vy * dyf.x);
+                const float cv = (float)(g.vscale * g.dt);
+                float2 dxf[SB], u[SB];
+                double o0[SB], o1[SB];
+#pragma unroll
+                for (int b = 0; b < SB; ++b) {
+                    const long long s = sj[b];
+                    dxf[b] = cz[((size_t)run * 4 + pair) * n + s];
+                    u[b] = reinterpret_cast<const float2 *>(k.vel)[(size_t)run * n + s];  // FP32 bulk
+                    o0[b] = pair == 0 ? om[s] : om[2 * n + s];
+                    o1[b] = pair == 0 ? om[n + s] : 0.0;
+                }
+#pragma unroll
+                for (int b = 0; b < SB; ++b) {
+                    const long long s = sj[b];
+                    const float2 dyf = h[j][r0 + b];
+                    const float vx = u[b].x * cv, vy = u[b].y * cv;
+                    if (pair == 0) {
+                        ot[s] = o0[b] - (double)(vx * dxf[b].x + vy * dyf.x);
+                        ot[n + s] = o1[b] - (double)(vx * dxf[b].y + vy * dyf.y);
+                    } else {
+                        ot[2 * n + s] = o0[b] - (double)(vx * dxf[b].x + vy * dyf.x);
+                    }
                 }
             } else {
                 // omega(t+dt) = omega~ - dt D_I Lap mu_I (increment in FP32)
-                const float2 dyf = h[j][r], lxf = cz[((size_t)run * 4 + pair) * n + s];
                 const double *ot = k.omega_t + (size_t)run * 3 * n;
                 double *om = k.omega_dst + (size_t)run * 3 * n;
-                if (pair == 0) {
-                    const float c = (float)(g.dt * g.d_p);
-                    om[s] = ot[s] - (double)(c * (lxf.x + dyf.x));
-                    om[n + s] = ot[n + s] - (double)(c * (lxf.y + dyf.y));
-                } else {
-                    om[2 * n + s] = ot[2 * n + s] - (double)((float)(g.dt * g.d_s) * (lxf.x + dyf.x));
+                float2 lxf[SB];
+                double o0[SB], o1[SB];
+#pragma unroll
+                for (int b = 0; b < SB; ++b) {
+                    const long long s = sj[b];
+                    lxf[b] = cz[((size_t)run * 4 + pair) * n + s];
+                    o0[b] = pair == 0 ? ot[s] : ot[2 * n + s];
+                    o1[b] = pair == 0 ? ot[n + s] : 0.0;
+                }
+#pragma unroll
+                for (int b = 0; b < SB; ++b) {
+                    const long long s = sj[b];
+                    const float2 dyf = h[j][r0 + b];
+                    if (pair == 0) {
+                        const float c = (float)(g.dt * g.d_p);
+                        om[s] = o0[b] - (double)(c * (lxf[b].x + dyf.x));
+                        om[n + s] = o1[b] - (double)(c * (lxf[b].y + dyf.y));
+                    } else {
+                        om[2 * n + s] = o0[b] - (double)((float)(g.dt * g.d_s) * (lxf[b].x + dyf.x));
+                    }
                 }
             }
         }

@@ -154,6 +154,7 @@ __global__ void __launch_bounds__(kThreads) prop_col(PropK<T> k)
 // (E' = E (1 + rho)), the exact differences of g_m = E'_a T(a_{m-1}) and
 // a_m = E'_d g_m from the reference solve's g~_m = E_a T(a~_{m-1}) and
 // a~_m = E_d g~_m; dg_m is stored at every node, dQ_P partials at m = ns.
+constexpr int RB = 4;  // points per thread whose loads the row pass's epilogue issues together
 template <typename T, bool DIFF>
 __global__ void __launch_bounds__(kThreads) prop_row(PropK<T> k, int m)
 {
@@ -193,17 +194,34 @@ __global__ void __launch_bounds__(kThreads) prop_row(PropK<T> k, int m)
         const V2<T> *gref = hist + (size_t)m * n;
         const int bag = half_step_block(k.g.jr, 0, m, ns, na, true), bap = half_step_block(k.g.jr, 1, m, ns, na, true);
         const int bdg = half_step_block(k.g.jr, 0, m, ns, na, false), bdp = half_step_block(k.g.jr, 1, m, ns, na, false);
-        for (int i = threadIdx.x; i < tile; i += blockDim.x) {
-            const V2<T> e = efac[i], gr = gref[i], u = r[i];
-            const float2 q = rho[i];
-            const T ea = bag ? e.y : e.x, eap = bap ? e.y : e.x, qa = bag ? q.y : q.x, qap = bap ? q.y : q.x;
-            const V2<T> dg = mk<T>(ea * ((T)1 + qa) * u.x + qa * gr.x, eap * ((T)1 + qap) * u.y + qap * gr.y);
-            hd[i] = dg;
-            if (m == ns) {
-                qsum += (double)dg.x;
-            } else {
-                const T ed = bdg ? e.y : e.x, edp = bdp ? e.y : e.x, qd = bdg ? q.y : q.x, qdp = bdp ? q.y : q.x;
-                data[i] = mk<T>(ed * ((T)1 + qd) * dg.x + ed * qd * gr.x, edp * ((T)1 + qdp) * dg.y + edp * qdp * gr.y);
+        // batches of RB points per thread: the loads first, then the stores
+        for (int i0 = threadIdx.x; i0 < tile; i0 += RB * blockDim.x) {
+            V2<T> eb[RB], grb[RB];
+            float2 qb[RB];
+#pragma unroll
+            for (int b = 0; b < RB; ++b) {
+                const int i = i0 + b * blockDim.x;
+                if (i < tile) {
+                    eb[b] = efac[i];
+                    grb[b] = gref[i];
+                    qb[b] = rho[i];
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < RB; ++b) {
+                const int i = i0 + b * blockDim.x;
+                if (i >= tile) break;
+                const V2<T> e = eb[b], gr = grb[b], u = r[i];
+                const float2 q = qb[b];
+                const T ea = bag ? e.y : e.x, eap = bap ? e.y : e.x, qa = bag ? q.y : q.x, qap = bap ? q.y : q.x;
+                const V2<T> dg = mk<T>(ea * ((T)1 + qa) * u.x + qa * gr.x, eap * ((T)1 + qap) * u.y + qap * gr.y);
+                hd[i] = dg;
+                if (m == ns) {
+                    qsum += (double)dg.x;
+                } else {
+                    const T ed = bdg ? e.y : e.x, edp = bdp ? e.y : e.x, qd = bdg ? q.y : q.x, qdp = bdp ? q.y : q.x;
+                    data[i] = mk<T>(ed * ((T)1 + qd) * dg.x + ed * qd * gr.x, edp * ((T)1 + qdp) * dg.y + edp * qdp * gr.y);
+                }
             }
         }
         if (m == ns) {
@@ -214,29 +232,49 @@ __global__ void __launch_bounds__(kThreads) prop_row(PropK<T> k, int m)
     }
     const bool store_all = k.hnodes == ns + 1;
     double *ia = k.ia + (size_t)run * n + base, *ib = k.ib + (size_t)run * n + base;
-    for (int i = threadIdx.x; i < tile; i += blockDim.x) {
-        const V2<T> e = efac[i];
-        // z = (g_m, g'_m): the arriving half-step's factor; the chain goes on
-        // with the departing one
-        const T eg = fac_g<T>(e, k.g, m, true), egp = fac_gp<T>(e, k.g, m, true);
-        const V2<T> h = r[i];
-        const V2<T> z = mk<T>(eg * h.x, egp * h.y);
-        if (m <= hlo || store_all) hist[(size_t)m * n + i] = z;
-        if (m >= hhi) {
-            const int s2 = ns - m;
-            const V2<T> hv = (s2 == m) ? z : hist[(size_t)s2 * n + i];
-            const double t1 = (double)z.x * (double)hv.y;  // g(s_m) g'(1 - s_m)
-            double va = weight_a(m, na, ds) * t1, vb = weight_b(m, na, ns, ds) * t1;
-            if (s2 != m) {
-                const double t2 = (double)hv.x * (double)z.y;  // g(s_{ns-m}) g'(s_m)
-                va += weight_a(s2, na, ds) * t2;
-                vb += weight_b(s2, na, ns, ds) * t2;
+    const int s2 = ns - m;
+    // batches of RB points per thread: the loads first, then the stores
+    for (int i0 = threadIdx.x; i0 < tile; i0 += RB * blockDim.x) {
+        V2<T> eb[RB], hvb[RB];
+        double iab[RB], ibb[RB];
+#pragma unroll
+        for (int b = 0; b < RB; ++b) {
+            const int i = i0 + b * blockDim.x;
+            if (i < tile) {
+                eb[b] = efac[i];
+                if (m >= hhi && s2 != m) hvb[b] = hist[(size_t)s2 * n + i];
+                if (m > hhi) {
+                    iab[b] = ia[i];
+                    ibb[b] = ib[i];
+                }
             }
-            if (m == hhi) { ia[i] = va; ib[i] = vb; }
-            else { ia[i] += va; ib[i] += vb; }
         }
-        if (m == ns) qsum += (double)z.x;
-        else data[i] = mk<T>(fac_g<T>(e, k.g, m, false) * z.x, fac_gp<T>(e, k.g, m, false) * z.y);
+#pragma unroll
+        for (int b = 0; b < RB; ++b) {
+            const int i = i0 + b * blockDim.x;
+            if (i >= tile) break;
+            const V2<T> e = eb[b];
+            // z = (g_m, g'_m): the arriving half-step's factor; the chain goes on
+            // with the departing one
+            const T eg = fac_g<T>(e, k.g, m, true), egp = fac_gp<T>(e, k.g, m, true);
+            const V2<T> h = r[i];
+            const V2<T> z = mk<T>(eg * h.x, egp * h.y);
+            if (m <= hlo || store_all) hist[(size_t)m * n + i] = z;
+            if (m >= hhi) {
+                const V2<T> hv = (s2 == m) ? z : hvb[b];
+                const double t1 = (double)z.x * (double)hv.y;  // g(s_m) g'(1 - s_m)
+                double va = weight_a(m, na, ds) * t1, vb = weight_b(m, na, ns, ds) * t1;
+                if (s2 != m) {
+                    const double t2 = (double)hv.x * (double)z.y;  // g(s_{ns-m}) g'(s_m)
+                    va += weight_a(s2, na, ds) * t2;
+                    vb += weight_b(s2, na, ns, ds) * t2;
+                }
+                if (m == hhi) { ia[i] = va; ib[i] = vb; }
+                else { ia[i] = iab[b] + va; ib[i] = ibb[b] + vb; }
+            }
+            if (m == ns) qsum += (double)z.x;
+            else data[i] = mk<T>(fac_g<T>(e, k.g, m, false) * z.x, fac_gp<T>(e, k.g, m, false) * z.y);
+        }
     }
     if (m == ns) {
         const double s = block_sum(qsum, red);
@@ -419,40 +457,56 @@ __global__ void __launch_bounds__(RowTile<LOGX>::T) prop_row8(Stream8K k, int m)
     const float2 *efac = k.efac + (size_t)run * n + base;
     float2 *hist = k.hist + ((size_t)run * (ns + 1) + m) * n + base;
     float qsum = 0.f;
+    // per batch of RR points: every load first, then the stores (the
+    // history and chain stores could alias the inputs as far as the compiler
+    // knows, which would serialise each load behind the previous stores)
     if (DIFF) {
         const float2 *rho = k.rho + (size_t)run * n + base;
         float2 *hd = k.hd + ((size_t)run * (ns + 1) + m) * n + base;
 #pragma unroll
-        for (int j = 0; j < NB_L; ++j)
+        for (int j = 0; j < NB_L; ++j) {
+            float2 e[RR], q[RR], gr[RR];
 #pragma unroll
             for (int r = 0; r < RR; ++r) {
                 const int i = bb[j] * NX + tt[j] + r * PER_L;
-                const float2 e = efac[i], q = rho[i], gr = hist[i], u = h[j][r];
-                const float ea = fac_g<float>(e, k.g, m, true), eap = fac_gp<float>(e, k.g, m, true);
-                const float qa = fac_g<float>(q, k.g, m, true), qap = fac_gp<float>(q, k.g, m, true);
-                const float2 dg = make_float2(ea * (1.f + qa) * u.x + qa * gr.x, eap * (1.f + qap) * u.y + qap * gr.y);
+                e[r] = efac[i];
+                q[r] = rho[i];
+                gr[r] = hist[i];
+            }
+#pragma unroll
+            for (int r = 0; r < RR; ++r) {
+                const int i = bb[j] * NX + tt[j] + r * PER_L;
+                const float2 u = h[j][r];
+                const float ea = fac_g<float>(e[r], k.g, m, true), eap = fac_gp<float>(e[r], k.g, m, true);
+                const float qa = fac_g<float>(q[r], k.g, m, true), qap = fac_gp<float>(q[r], k.g, m, true);
+                const float2 dg = make_float2(ea * (1.f + qa) * u.x + qa * gr[r].x, eap * (1.f + qap) * u.y + qap * gr[r].y);
                 hd[i] = dg;
                 if (m == ns) {
                     qsum += dg.x;
                 } else {
-                    const float ed = fac_g<float>(e, k.g, m, false), edp = fac_gp<float>(e, k.g, m, false);
-                    const float qd = fac_g<float>(q, k.g, m, false), qdp = fac_gp<float>(q, k.g, m, false);
-                    data[i] = make_float2(ed * (1.f + qd) * dg.x + ed * qd * gr.x, edp * (1.f + qdp) * dg.y + edp * qdp * gr.y);
+                    const float ed = fac_g<float>(e[r], k.g, m, false), edp = fac_gp<float>(e[r], k.g, m, false);
+                    const float qd = fac_g<float>(q[r], k.g, m, false), qdp = fac_gp<float>(q[r], k.g, m, false);
+                    data[i] = make_float2(ed * (1.f + qd) * dg.x + ed * qd * gr[r].x,
+                                          edp * (1.f + qdp) * dg.y + edp * qdp * gr[r].y);
                 }
             }
+        }
     } else {
 #pragma unroll
-        for (int j = 0; j < NB_L; ++j)
+        for (int j = 0; j < NB_L; ++j) {
+            float2 e[RR];
+#pragma unroll
+            for (int r = 0; r < RR; ++r) e[r] = efac[bb[j] * NX + tt[j] + r * PER_L];
 #pragma unroll
             for (int r = 0; r < RR; ++r) {
                 const int i = bb[j] * NX + tt[j] + r * PER_L;
-                const float2 e = efac[i];
-                const float eg = fac_g<float>(e, k.g, m, true), egp = fac_gp<float>(e, k.g, m, true);
+                const float eg = fac_g<float>(e[r], k.g, m, true), egp = fac_gp<float>(e[r], k.g, m, true);
                 const float2 z = make_float2(eg * h[j][r].x, egp * h[j][r].y);
                 hist[i] = z;
                 if (m == ns) qsum += z.x;
-                else data[i] = make_float2(fac_g<float>(e, k.g, m, false) * z.x, fac_gp<float>(e, k.g, m, false) * z.y);
+                else data[i] = make_float2(fac_g<float>(e[r], k.g, m, false) * z.x, fac_gp<float>(e[r], k.g, m, false) * z.y);
             }
+        }
     }
     if (m == ns) {
         const double s = block_sum((double)qsum, red);

@@ -4,7 +4,10 @@ flushes, for kernel profilers:
     python -m paper_1804_02883_gb300.profile_case --workload channel --steps 2
 
 --workload box3d runs the coupled step on a 128 x 128 x 64 box (--time
-prints CUDA-event milliseconds per step).  --exact N then runs N exact steps (Fletcher-Reeves inversion to the 1e-8
+prints CUDA-event milliseconds per step).  --workload surrogate runs the
+learned surrogate's network on the benchmark batch (4 x 256 x 512): --steps
+rounds of one forward pass, one forward + tangent pass and one training
+step.  --exact N then runs N exact steps (Fletcher-Reeves inversion to the 1e-8
 tolerance, at most 100 iterations each) after the --steps truncated ones.
 """
 from __future__ import annotations
@@ -70,15 +73,39 @@ def box3d(steps: int, timed: bool) -> None:
           f" Q = {q[0].item():.12f}")
 
 
+def surrogate(steps: int) -> None:
+    """The surrogate network's kernels on a batch of four 256 x 512 fields
+    (random init, seeded inputs of the quench's amplitude)."""
+    import numpy as np
+    import torch
+
+    from . import surrogate as S
+
+    run = B.RunParams(nx=512, ny=256, ns=64, precision=B.MIXED_FP32)
+    sm = S.Surrogate(run, 4, s_in=300.0, s_out=1e-3, seed=1)
+    om = torch.from_numpy(1e-3 * np.random.default_rng(0).standard_normal((4, 3, 256, 512))).cuda()
+    om2 = om + 1e-6
+    ph = sm.forward(om)
+    for _ in range(steps):
+        sm.forward(om)
+        sm.tangent(om, om2)
+        sm.train_step(om, ph, lr=1e-4)
+    torch.cuda.synchronize()
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="channel", choices=sorted(WORKLOADS) + ["box3d"])
+    ap.add_argument("--workload", default="channel", choices=sorted(WORKLOADS) + ["box3d", "surrogate"])
     ap.add_argument("--time", action="store_true", help="box3d: print CUDA-event ms per step")
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--exact", type=int, default=0, help="then this many exact steps (0: none)")
     args = ap.parse_args()
     if args.workload == "box3d":
         box3d(args.steps, args.time)
+        print("ok")
+        return
+    if args.workload == "surrogate":
+        surrogate(args.steps)
         print("ok")
         return
     h = B.EpdLb(WORKLOADS[args.workload]())
