@@ -21,6 +21,9 @@ WORKLOADS = {
     "channel": lambda: W.channel_256x512(B.MIXED_FP32),
     "ensemble32": lambda: W.ensemble_32(B.MIXED_FP32),
     "vesicle": lambda: [W.vesicle_1024x2048(B.MIXED_FP32)],
+    # the vesicle grid with a short contour (N_s = 16): the streaming passes
+    # of the full-size grid with a small history, for counter captures
+    "stream_short": lambda: [W.with_(W.vesicle_1024x2048(B.MIXED_FP32), ns=16)],
     "plain_small": lambda: [W.plain_small()],
     "paper150": lambda: W.paper_150(B.MIXED_FP32),
 }
