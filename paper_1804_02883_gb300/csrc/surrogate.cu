@@ -107,7 +107,9 @@ struct ConvArgs {
 // (leading-byte offset); the weights as [tap][c8][co][8 channels].  One
 // thread issues the 9 KP / 16 MMAs into a TMEM accumulator (32 columns) and
 // commits them to an mbarrier; every warp then reads its 32 TMEM lanes (one
-// pixel per thread, all channels) for the epilogue of the layer's mode.
+// pixel per thread, all channels) for the epilogue of the layer's mode.  Two
+// accumulators alternate between tiles, so the next tile's MMAs run during
+// this tile's epilogue.
 // ---------------------------------------------------------------------------
 
 constexpr int TCH = 16, TCW = 8;  // tensor-core pixel tile (rows x columns)
@@ -205,6 +207,14 @@ __device__ __forceinline__ float tanh_fast(float x)
     x = fminf(fmaxf(x, -15.f), 15.f);
     return 1.f - __fdividef(2.f, __expf(2.f * x) + 1.f);
 }
+// the hardware tanh approximation (one special-function instruction;
+// relative error about 2^-11, below the BF16 step of the stored result)
+__device__ __forceinline__ float tanh_approx(float x)
+{
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 // Bounded wait for the phase with the given parity of a CTA-local mbarrier
 // in the tile pipeline: as mbar_wait_tc.
@@ -244,17 +254,17 @@ __global__ void __launch_bounds__(128) conv3x3_tc(ConvArgs a, const __grid_const
     // base rounded up to 128 bytes (TMA destinations)
     unsigned char *halo = tc_raw + ((128u - ((uint32_t)__cvta_generic_to_shared(tc_raw) & 127u)) & 127u);  // [buffer][c8][HH*HW][16 B]
     unsigned char *wsm = halo + Geo::AOFF;      // [tap][c8][N][16 B]
-    __shared__ __align__(8) unsigned long long mbar, full[NBUF];
+    __shared__ __align__(8) unsigned long long mbar[2], full[NBUF];  // MMA barriers (one per accumulator), load barriers
     __shared__ uint32_t tmem_base;
     __shared__ float bias_s[NP];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long n = (long long)a.nx * a.ny;
-    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&mbar);
+    const uint32_t mbar_s = (uint32_t)__cvta_generic_to_shared(&mbar[0]);
     const uint32_t full_s = (uint32_t)__cvta_generic_to_shared(&full[0]);
     const uint32_t halo_s = (uint32_t)__cvta_generic_to_shared(halo), w_s = (uint32_t)__cvta_generic_to_shared(wsm);
     const int tiles_x = a.nx / TCW, tiles_img = tiles_x * (a.ny / TCH), ntiles = tiles_img * a.nb;
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        for (int i = 0; i < 2; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar_s + 8 * i) : "memory");
         for (int i = 0; i < NBUF; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(full_s + 8 * i) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -298,7 +308,8 @@ __global__ void __launch_bounds__(128) conv3x3_tc(ConvArgs a, const __grid_const
     }
     if (tid < NP) bias_s[tid] = (MODE != EP_DX && MODE != EP_JVP && a.bias && tid < a.nreal) ? a.bias[tid] : 0.f;
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(
+        // two accumulators of 32 FP32 columns
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(
                          (uint32_t)__cvta_generic_to_shared(&tmem_base))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -309,33 +320,28 @@ __global__ void __launch_bounds__(128) conv3x3_tc(ConvArgs a, const __grid_const
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
     constexpr uint32_t IDESC = mma_idesc(128, N);
-    unsigned phase = 0, fphase = 0;  // MMA barrier parity; full-barrier parities, one bit per buffer
-    bool failed = false;
-    int buf = 0;
-    for (int tix = blockIdx.x; tix < ntiles && !failed; tix += gridDim.x, buf = buf + 1 == NBUF ? 0 : buf + 1) {
-        const int b = tix / tiles_img, rr = tix % tiles_img;
-        const int tx0 = (rr % tiles_x) * TCW, ty0 = (rr / tiles_x) * TCH;
-        // tile NBUF - 1 ahead into the buffer the previous tile's MMAs read
-        // (complete: its MMA barrier was waited on)
-        {
-            const int ahead = tix + (NBUF - 1) * (int)gridDim.x;
-            if (ahead < ntiles) issue(ahead, buf == 0 ? NBUF - 1 : buf - 1);
-        }
-        {
-            int f = 0;
-            mbar_wait_tc(full_s + 8 * buf, (fphase >> buf) & 1u, f);
-            failed = __syncthreads_or(f) != 0;
-        }
-        if (failed) break;
-        fphase ^= 1u << buf;
-        pending &= ~(1u << buf);
+    // fphase: full-barrier parities (bit per buffer); mphase: MMA-barrier
+    // parities (bit per accumulator); mpend: accumulators with MMAs issued
+    // and not yet waited on
+    unsigned fphase = 0, mphase = 0, mpend = 0;
+    int failed = 0;
+    const int G = (int)gridDim.x;
+    // the MMAs of tile tix (buffer bf) into accumulator ac: wait for its
+    // halo, make the copies visible to the tensor cores, one thread issues
+    // 9 KP / 16 MMAs and commits them to the accumulator's barrier
+    auto mma_tile = [&](int bf, int ac) {
+        int f = 0;
+        mbar_wait_tc(full_s + 8 * bf, (fphase >> bf) & 1u, f);
+        if (__syncthreads_or(f)) return false;
+        fphase ^= 1u << bf;
+        pending &= ~(1u << bf);
         // asynchronous-copy writes visible to the tensor cores (async proxy)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (tid == 0) {
-            const uint32_t hb = halo_s + (uint32_t)(buf * Geo::HALO);
+            const uint32_t hb = halo_s + (uint32_t)(bf * Geo::HALO), d = tmem + 32u * ac;
 #pragma unroll
             for (int tap = 0; tap < 9; ++tap) {
                 const int dy = (tap / 3) * D, dx = (tap % 3) * D;
@@ -346,29 +352,59 @@ __global__ void __launch_bounds__(128) conv3x3_tc(ConvArgs a, const __grid_const
                     const uint32_t acc = (tap | kc) ? 1u : 0u;
                     asm volatile(
                         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
                         "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
                         : "memory");
                 }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_s + 8 * ac)
+                         : "memory");
         }
-        // the MMAs are done (bounded wait; the CTA leaves the tile loop
+        mpend |= 1u << ac;
+        return true;
+    };
+    // Tile i: buffer i % NBUF, accumulator i % 2.  Its MMAs are issued one
+    // iteration ahead, so the tensor cores work on tile i + 1 while the
+    // threads run tile i's epilogue; the loads run NBUF - 1 tiles ahead.
+    if (blockIdx.x < ntiles && !mma_tile(0, 0)) failed = 1;
+    int buf = 0, i = 0;
+    for (int tix = blockIdx.x; tix < ntiles && !failed; tix += G, ++i, buf = buf + 1 == NBUF ? 0 : buf + 1) {
+        const int ac = i & 1;
+        const int b = tix / tiles_img, rr = tix % tiles_img;
+        const int tx0 = (rr % tiles_x) * TCW, ty0 = (rr / tiles_x) * TCH;
+        // loads of tile i + NBUF - 1 into the buffer tile i - 1's MMAs read
+        // (complete: waited on in the previous iteration)
+        if (tix + (NBUF - 1) * G < ntiles) issue(tix + (NBUF - 1) * G, buf == 0 ? NBUF - 1 : buf - 1);
+        // MMAs of tile i + 1 into the other accumulator (read out by tile
+        // i - 1's epilogue, which every thread finished)
+        if (tix + G < ntiles && !mma_tile(buf + 1 == NBUF ? 0 : buf + 1, ac ^ 1)) {
+            failed = 1;
+            break;
+        }
+        // tile i's MMAs are done (bounded wait; the CTA leaves the tile loop
         // together if any thread gave up)
         {
             int f = 0;
-            mbar_wait_tc(bar, phase, f);
-            failed = __syncthreads_or(f) != 0;
+            mbar_wait_tc(mbar_s + 8 * ac, (mphase >> ac) & 1u, f);
+            if (__syncthreads_or(f)) {
+                failed = 1;
+                break;
+            }
+            mphase ^= 1u << ac;
+            mpend &= ~(1u << ac);
         }
-        if (!failed) phase ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (!failed) {
+        {
             // thread = TMEM lane = pixel p (row p / 8, column p % 8) of the tile
             float v[N];
-            const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
+            const uint32_t taddr = tmem + 32u * ac + ((uint32_t)(32 * warp) << 16);
             tmem_ld<N>(taddr, v);
             const int p = 32 * warp + lane, py = ty0 + p / TCW, px = tx0 + p % TCW;
             const size_t pix = (size_t)b * n + (size_t)py * a.nx + px;
+            // inference (BF16 output only): one-instruction tanh; training
+            // keeps the FP32 activations for the gradient and forms tanh
+            // from exp
+            const bool fast = a.out_f == nullptr;
 #pragma unroll
             for (int c0 = 0; c0 < NP; c0 += 8) {
                 float o[8];
@@ -390,7 +426,7 @@ __global__ void __launch_bounds__(128) conv3x3_tc(ConvArgs a, const __grid_const
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         const float z = v[c0 + j] + bias_s[c0 + j];
-                        o[j] = MODE == EP_TANH ? tanh_fast(z) : z;
+                        o[j] = MODE == EP_TANH ? (fast ? tanh_approx(z) : tanh_fast(z)) : z;
                     }
                 }
 #pragma unroll
@@ -410,25 +446,27 @@ __global__ void __launch_bounds__(128) conv3x3_tc(ConvArgs a, const __grid_const
                 }
             }
         }
-        // every thread has read the accumulator and the MMAs no longer read
-        // this halo tile: the next tiles may overwrite both
+        // every thread has read accumulator ac (tile i + 2's MMAs may
+        // overwrite it) and tile i's buffer is free (its MMAs are done)
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
     if (failed) {
         if (tid == 0 && a.err) atomicOr(a.err, 4);
-        // the MMAs of an abandoned tile, and the loads issued ahead of it
-        // into this CTA's shared memory: wait for them once more (bounded)
+        // MMAs still in flight, and the loads issued ahead into this CTA's
+        // shared memory: wait for them once more (bounded)
         int f = 0;
-        mbar_wait_tc(bar, phase, f);
-        for (int i = 0; i < NBUF; ++i)
-            if (pending >> i & 1u) mbar_wait_tc(full_s + 8 * i, (fphase >> i) & 1u, f);
+        for (int c = 0; c < 2; ++c)
+            if (mpend >> c & 1u) mbar_wait_tc(mbar_s + 8 * c, (mphase >> c) & 1u, f);
+        for (int c = 0; c < NBUF; ++c)
+            if (pending >> c & 1u) mbar_wait_tc(full_s + 8 * c, (fphase >> c) & 1u, f);
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
 }
+
 
 // Weight gradient of one layer: dW[tap][co][ci] = sum_p dZ[p][co] x[p + off(tap)][ci]
 // over an 8 x 16 tile per step, `tiles` consecutive tiles per CTA; 9 warps, warp
@@ -960,7 +998,8 @@ static void conv(Work &w, const void *in, const void *wt, const float *bias, voi
     a.nreal = nreal;
     a.nb = w.nb;
     const int tiles = w.nb * (w.nx / TCW) * (w.ny / TCH);
-    const int per_sm = std::max(1, std::min(16, (int)((220u << 10) / (smem + 1024))));
+    // CTAs per SM: by shared memory, and at most 8 (64 TMEM columns each)
+    const int per_sm = std::max(1, std::min(8, (int)((220u << 10) / (smem + 1024))));
     conv3x3_tc<KP, NP, MODE, D><<<std::min(tiles, per_sm * 152), 128, smem, s>>>(a, map);
 }
 
