@@ -266,6 +266,75 @@ def test_full_size_batch_first_run_matches_oracle():
     h.close()
 
 
+def test_full_size_batch_every_run_matches_oracle():
+    # the benchmark's launch configuration (four 256 x 512 runs, N_s = 64,
+    # the phased differential chain schedule): one step from a random state
+    # of every run against one oracle step of that run
+    runs = W.channel_256x512(P.MIXED_FP32)
+    h = P.EpdLb(runs)
+    states = []
+    for k, r in enumerate(runs):
+        st = (W.random_omega(r.ny, r.nx, seed=60 + k, amp=0.02), W.random_populations(r.ny, r.nx, seed=70 + k, amp=1e-4),
+              W.random_velocity(r.ny, r.nx, seed=80 + k, amp=1e-3))
+        h.set_state(k, *st)
+        states.append(st)
+    h.step(1)
+    for k, r in enumerate(runs):
+        p, st = oracle_state_from(r, *states[k])
+        O.step(p, st)
+        gphi, gq = h.densities(k)
+        gom, gpop, gvel = h.get_state(k)
+        assert rel_err(gphi, st.phi) < 2e-6, k
+        assert rel_err(gq, st.q) < 2e-6, k
+        assert fluct_err(gom, st.omega) < 2e-6, k
+        assert rel_err(gvel, st.vel) < 1e-5, k
+        assert np.abs(gpop - st.pop).max() < 1e-7, k
+    h.close()
+
+
+def test_vesicle_grid_step_matches_oracle():
+    # the 1024 x 2048 vesicle configuration's grid and parameters (radix-8
+    # streaming passes, differential second solve) with a short chain,
+    # N_s = 16, so that the oracle step takes seconds; one step from a
+    # random state against the oracle
+    r = W.with_(W.vesicle_1024x2048(P.MIXED_FP32), ns=16)
+    h = P.EpdLb([r])
+    assert h.tiles(0)["path"] == 1 and h.tiles(0)["differential"]
+    omega = W.random_omega(r.ny, r.nx, seed=91, amp=0.02)
+    pop = W.random_populations(r.ny, r.nx, seed=92, amp=1e-4)
+    vel = W.random_velocity(r.ny, r.nx, seed=93, amp=1e-3)
+    h.set_state(0, omega, pop, vel)
+    h.step(1)
+    p, st = oracle_state_from(r, omega, pop, vel)
+    O.step(p, st)
+    gphi, gq = h.densities(0)
+    gom, gpop, gvel = h.get_state(0)
+    assert rel_err(gphi, st.phi) < 2e-6
+    assert rel_err(gq, st.q) < 2e-6
+    assert fluct_err(gom, st.omega) < 2e-6
+    assert rel_err(gvel, st.vel) < 1e-5
+    assert np.abs(gpop - st.pop).max() < 1e-7
+    h.close()
+
+
+def test_vesicle_configuration_invariants():
+    # the full 1024 x 2048, N_s = 128 configuration the benchmark times:
+    # properties that hold at any size after three steps from the seeded
+    # quench -- each species' mass (Eqs. (2), (5)), the LB mass, Q > 0
+    r = W.vesicle_1024x2048(P.MIXED_FP32)
+    h = P.EpdLb([r])
+    h.step(3)
+    h.sync()
+    ob = h.observables(0)
+    na = round(r.f_a * r.ns)
+    assert abs(ob["mean_phi_a"] / (r.phi_p * na / r.ns) - 1) < 1e-6
+    assert abs(ob["mean_phi_b"] / (r.phi_p * (r.ns - na) / r.ns) - 1) < 1e-6
+    assert abs(ob["mean_phi_s"] / (1 - r.phi_p) - 1) < 1e-6
+    assert abs(ob["lb_mass"] - 1) < 1e-6
+    assert ob["q_p"] > 0 and ob["q_s"] > 0
+    h.close()
+
+
 def test_batch_equals_single_runs():
     runs = [W.with_(W.plain_small(), nx=32, ny=32, ns=8, seed=s, f0=f) for s, f in ((1, 0.0), (2, 20.0), (3, 50.0))]
     hb = P.EpdLb(runs)
