@@ -716,7 +716,7 @@ def main():
     ap.add_argument("--configs", default="ensemble32,vesicle",
                     help="other configurations measured into the line's configs key (comma list; empty: none)")
     ap.add_argument("--config-steps", type=int, default=5)
-    ap.add_argument("--config-surrogate-pairs", type=int, default=32000)
+    ap.add_argument("--config-surrogate-pairs", type=int, default=64000)
     ap.add_argument("--config-eval-steps", type=int, default=200)
     ap.add_argument("--exact-steps", type=int, default=5,
                     help="steps of the exact step (CG inversion) timed on the same workload; 0 skips it")

@@ -269,34 +269,6 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
         mbar_expect(bar_row, XBYTES);
     }
 
-    // node m_begin into the packing the first step starts from: a_0 from the
-    // node factors (and stored for the contour sums), or the state a_{m_begin}
-    // the previous phase stored (the same FP32 values, so the result does not
-    // depend on the schedule)
-    if (m_begin == 0) {
-        for (int e = tid; e < P; e += T) hout[(size_t)krow0 * NX + e] = node0(krow0 + e / NX, e % NX);
-    }
-    if (starts_in_columns(m_begin + 1)) {
-        // packed column jcol0 + c, real row y: (a(2J, y), a(2J + 1, y))
-        for (int e = tid; e < P; e += T) {
-            const int c = e % W2, y = e / W2, jx = 2 * (jcol0 + c), kk = y >> 1;
-            float2 p0, p1;
-            if (m_begin == 0) {
-                p0 = node0(kk, jx);
-                p1 = node0(kk, jx + 1);
-            } else {
-                p0 = hout[(size_t)m_begin * HN + kk * NX + jx];
-                p1 = hout[(size_t)m_begin * HN + kk * NX + jx + 1];
-            }
-            colbuf[CL::at(c, y)] = (y & 1) ? f2(p0.y, p1.y) : f2(p0.x, p1.x);
-        }
-    } else {
-        for (int e = tid; e < P; e += T) {
-            const int b = e / NX, x = e % NX;
-            rowbuf[RL::at(b, x)] = m_begin == 0 ? node0(krow0 + b, x) : hout[(size_t)m_begin * HN + (size_t)krow0 * NX + e];
-        }
-    }
-    cl.sync();  // every CTA's barriers are initialised, the first packing is in place
 
     const bool odd = tid & 1;
     // last row pass (warp-private) and last column pass geometry
@@ -338,6 +310,74 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
             return f2(f.x * u.x + c.x * ar.x, f.y * u.y + c.y * ar.y);
         }
     };
+
+    // per-site factors of this thread's epilogue points in the row packing
+    // (fac_r) and the column packing (fac_c) for blocks (bd, ba)
+    auto fill_r = [&](bool bd, bool ba) {
+#pragma unroll
+        for (int j = 0; j < NB_L; ++j) {
+            int b, t;
+            RL::template split<PER_L>(bfly<true, NB_L, T>(tid, j), b, t);
+#pragma unroll
+            for (int r = 0; r < RR; ++r) fac_r[(j * RR + r) * T + tid] = factors(krow0 + b, t + r * PER_L, bd, ba);
+        }
+    };
+    auto fill_c = [&](bool bd, bool ba) {
+#pragma unroll
+        for (int j = 0; j < NB_C; ++j) {
+            int c, t;
+            col_pair_split<W2>(tid + j * T, c, t);
+#pragma unroll
+            for (int r = 0; r < RC; ++r) {
+                const int kk = (t + r * PER_C) >> 1, xx = 2 * (jcol0 + c) + (t & 1);
+                fac_c[(j * RC + r) * T + tid] = factors(kk, xx, bd, ba);
+            }
+        }
+    };
+    // The factors of the first step (both packings; they depend only on the
+    // fields of this solve, final before the first launch), then the state
+    // the previous launch of a phased schedule stored: a launch made as a
+    // programmatic dependent of the previous one runs this prologue while
+    // that one finishes, and waits for it only here (griddepcontrol.wait
+    // returns at once in a launch without that dependency).
+    if (nsteps > 0) {
+        const int m1 = m_begin + 1;
+        const int bd1 = dep_b(m1), ba1 = arr_b(m1);
+        fill_r(bd1, ba1);
+        fill_c(bd1, ba1);
+        cur_r = cur_c = 2 * bd1 + ba1;
+    }
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+
+    // node m_begin into the packing the first step starts from: a_0 from the
+    // node factors (and stored for the contour sums), or the state a_{m_begin}
+    // the previous phase stored (the same FP32 values, so the result does not
+    // depend on the schedule)
+    if (m_begin == 0) {
+        for (int e = tid; e < P; e += T) hout[(size_t)krow0 * NX + e] = node0(krow0 + e / NX, e % NX);
+    }
+    if (starts_in_columns(m_begin + 1)) {
+        // packed column jcol0 + c, real row y: (a(2J, y), a(2J + 1, y))
+        for (int e = tid; e < P; e += T) {
+            const int c = e % W2, y = e / W2, jx = 2 * (jcol0 + c), kk = y >> 1;
+            float2 p0, p1;
+            if (m_begin == 0) {
+                p0 = node0(kk, jx);
+                p1 = node0(kk, jx + 1);
+            } else {
+                p0 = hout[(size_t)m_begin * HN + kk * NX + jx];
+                p1 = hout[(size_t)m_begin * HN + kk * NX + jx + 1];
+            }
+            colbuf[CL::at(c, y)] = (y & 1) ? f2(p0.y, p1.y) : f2(p0.x, p1.x);
+        }
+    } else {
+        for (int e = tid; e < P; e += T) {
+            const int b = e / NX, x = e % NX;
+            rowbuf[RL::at(b, x)] = m_begin == 0 ? node0(krow0 + b, x) : hout[(size_t)m_begin * HN + (size_t)krow0 * NX + e];
+        }
+    }
+    cl.sync();  // every CTA's barriers are initialised, the first packing is in place
 
     // The contour loop runs over half steps: each applies the transform pair
     // of its packing, then either hands the field over (first half of a
@@ -417,13 +457,7 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
                 // packed row y / 2), the result back in the column buffer
                 if (key != cur_c) {
                     cur_c = key;
-#pragma unroll
-                    for (int j = 0; j < NB_C; ++j)
-#pragma unroll
-                        for (int r = 0; r < RC; ++r) {
-                            const int kk = (ct[j] + r * PER_C) >> 1, xx = 2 * (jcol0 + cc[j]) + (ct[j] & 1);
-                            fac_c[(j * RC + r) * T + tid] = factors(kk, xx, bd, ba);
-                        }
+                    fill_c(bd, ba);
                 }
 #pragma unroll
                 for (int j = 0; j < NB_C; ++j)
@@ -471,11 +505,7 @@ __global__ void __launch_bounds__(T, MINB) prop_chain(PropCK k)
                 // node factors; the result stays in the row buffer
                 if (key != cur_r) {
                     cur_r = key;
-#pragma unroll
-                    for (int j = 0; j < NB_L; ++j)
-#pragma unroll
-                        for (int r = 0; r < RR; ++r)
-                            fac_r[(j * RR + r) * T + tid] = factors(krow0 + bb[j], tt[j] + r * PER_L, bd, ba);
+                    fill_r(bd, ba);
                 }
                 // every value first: the stores come after
 #pragma unroll
@@ -819,6 +849,12 @@ static void set_cluster_cfg(cudaLaunchConfig_t &cfg, cudaLaunchAttribute &attr, 
 // an SM's shared memory per CTA), per shape and solve kind; 0: unknown or
 // none.  Filled by cluster_solve_supported, outside any stream capture.
 constexpr size_t kSoloSmem = 116 * 1024;
+// phased launches as programmatic dependents (EPD_LB_CHAIN_PDL=0 in the
+// environment turns it off, for timing one against the other)
+static const bool g_chain_pdl = [] {
+    const char *e = std::getenv("EPD_LB_CHAIN_PDL");
+    return !(e && e[0] == '0');
+}();
 static int g_solo_clusters[16][16][2];
 
 static int count_solo_clusters(const ClusterShape *s, bool diff)
@@ -936,9 +972,20 @@ cudaError_t launch_cluster_solve(Group &G, cudaStream_t s, bool diff, int nprep_
         cudaEventRecordWithFlags(probe->ev[0], s, cudaEventRecordExternal);
     }
     void *args[] = {&k};
+    // launches after the first of a phased schedule are programmatic
+    // dependents of the one before: their prologue (tables, node factors)
+    // overlaps its end; they wait for it before reading the stored states
+    cudaLaunchAttribute attrs[2] = {attr, {}};
+    attrs[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attrs[1].val.programmaticStreamSerializationAllowed = 1;
     for (int p = 0; p < launches; ++p) {
         k.skip = p;
-        cudaError_t e = cudaLaunchKernelExC(&cfg, chain_fn(sh, diff), args);
+        cudaLaunchConfig_t c2 = cfg;
+        if (p > 0 && g_chain_pdl) {
+            c2.attrs = attrs;
+            c2.numAttrs = 2;
+        }
+        cudaError_t e = cudaLaunchKernelExC(&c2, chain_fn(sh, diff), args);
         if (e != cudaSuccess) return e;
     }
     if (probe) cudaEventRecordWithFlags(probe->ev[1], s, cudaEventRecordExternal);
