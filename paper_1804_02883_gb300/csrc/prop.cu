@@ -530,17 +530,8 @@ __global__ void __launch_bounds__(kThreads) prop_contour_stream(GroupGeom g, con
     __shared__ double bc;
     const int run = blockIdx.y, ns = g.ns, na = g.na;
     const long long n = g.n;
-    const double *pr = part + (size_t)run * kMaxPart;
-    const double sq = sum_partials(pr, nrow_blocks, 1, &bc) / (double)n;
-    const double ss = sum_partials(pr + kMaxPart / 2, nprep_blocks, 1, &bc) / (double)n;
-    const double qp = DIFF ? q_ref[2 * run] + sq : sq, qs = DIFF ? q_ref[2 * run + 1] + ss : ss;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        q[2 * run] = qp;
-        q[2 * run + 1] = qs;
-        if (!(qp > 0.0) || !(qs > 0.0) || !isfinite(qp) || !isfinite(qs)) atomicOr(err, 1);
-    }
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const bool valid = i < n;
     const float2 *hz = hist + (size_t)run * (ns + 1) * n + i;
     const float2 *dz = DIFF ? hd + (size_t)run * (ns + 1) * n + i : nullptr;
     // Nodes m and N_s - m are read together: z_m = (g_m, g'_m) and z_{N_s-m}
@@ -561,7 +552,7 @@ __global__ void __launch_bounds__(kThreads) prop_contour_stream(GroupGeom g, con
     };
     const int half = ns / 2;
     constexpr int U = DIFF ? 4 : 8;
-    for (int m0 = 0; m0 <= half; m0 += U) {
+    for (int m0 = 0; m0 <= (valid ? half : -1); m0 += U) {
         float2 zl[U], zr[U], dl[U], dr[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -589,6 +580,18 @@ __global__ void __launch_bounds__(kThreads) prop_contour_stream(GroupGeom g, con
             }
         }
     }
+    // Q from the partials (after the streaming loop, so that its latency
+    // overlaps other blocks' loads; every thread of the block takes part)
+    const double *pr = part + (size_t)run * kMaxPart;
+    const double sq = sum_partials(pr, nrow_blocks, 1, &bc) / (double)n;
+    const double ss = sum_partials(pr + kMaxPart / 2, nprep_blocks, 1, &bc) / (double)n;
+    const double qp = DIFF ? q_ref[2 * run] + sq : sq, qs = DIFF ? q_ref[2 * run + 1] + ss : ss;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        q[2 * run] = qp;
+        q[2 * run + 1] = qs;
+        if (!(qp > 0.0) || !(qs > 0.0) || !isfinite(qp) || !isfinite(qs)) atomicOr(err, 1);
+    }
+    if (!valid) return;
     const double ia = (double)sa - (double)ca, ib = (double)sb - (double)cb;
     double *ph = phi + (size_t)run * 3 * n;
     if (!DIFF) {

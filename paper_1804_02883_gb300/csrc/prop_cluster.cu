@@ -642,6 +642,44 @@ __global__ void __launch_bounds__(kThreads) prop_contour(ContourK k)
     const int run = blockIdx.y;
     const int nx = k.g.nx, ny = k.g.ny, ns = k.g.ns, na = k.g.na;
     const long long n = k.g.n;
+    const int npk = nx * ny / 2;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < npk;
+    const int kk = i >> k.g.logx, x = i & (nx - 1);  // power-of-two grids
+    const int s0 = 2 * kk * nx + x, s1 = s0 + nx;
+    const int slot = kk * nx + x;
+    const size_t cs = (size_t)(ns + 1) * k.hn;  // one chain's states
+    const float2 *c0 = k.hc + (size_t)run * 2 * cs + slot, *c1 = c0 + cs;
+    const float2 *d0 = DIFF ? k.hd + (size_t)run * 2 * cs + slot : nullptr, *d1 = DIFF ? d0 + cs : nullptr;
+    using CS = ContourStage<DIFF>;
+    constexpr int U = CS::U, NW = CS::NW;
+    const int tid = threadIdx.x;
+    // stage st, node u, stream w: stg[((st U + u) NW + w) kThreads + tid]
+    auto issue = [&](int st, int m0) {
+        if (valid) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int m = m0 + u;
+                if (m <= ns) {
+                    float2 *b = stg + (size_t)((st * U + u) * NW) * kThreads + tid;
+                    cp_async8(b, c0 + (size_t)m * k.hn);
+                    cp_async8(b + kThreads, c1 + (size_t)(ns - m) * k.hn);
+                    if (DIFF) {
+                        cp_async8(b + 2 * kThreads, d0 + (size_t)m * k.hn);
+                        cp_async8(b + 3 * kThreads, d1 + (size_t)(ns - m) * k.hn);
+                    }
+                }
+            }
+        }
+        cp_async_commit();
+    };
+    // a ring of NSTAGE chunks: chunk ch + NSTAGE goes into chunk ch's stage
+    // once ch is consumed; every issue commits a group (empty past N_s), so
+    // waiting until at most NSTAGE - 1 groups are pending completes chunk ch.
+    // The first chunks are in flight while the block sums the Q partials.
+    constexpr int NST = CS::NSTAGE;
+#pragma unroll
+    for (int c = 0; c < NST; ++c) issue(c, c * U);
     const double *pr = k.part + (size_t)run * kMaxPart;
     const double sq = sum_partials(pr, k.nq, 1, &bc) / (double)n;
     const double ss = sum_partials(pr + kMaxPart / 2, k.ns_part, 1, &bc) / (double)n;
@@ -658,17 +696,12 @@ __global__ void __launch_bounds__(kThreads) prop_contour(ContourK k)
         k.q[2 * run + 1] = qs;
         if (!(qp > 0.0) || !(qs > 0.0) || !isfinite(qp) || !isfinite(qs)) atomicOr(k.err, 1);
     }
-    const int npk = nx * ny / 2;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= npk) return;
-    const int kk = i >> k.g.logx, x = i & (nx - 1);  // power-of-two grids
-    const int s0 = 2 * kk * nx + x, s1 = s0 + nx;
-    const int slot = kk * nx + x;
+    if (!valid) {
+        cp_async_wait<0>();
+        return;
+    }
     const float2 *efac = k.efac + (size_t)run * n;
     const float2 e0 = efac[s0], e1 = efac[s1];
-    const size_t cs = (size_t)(ns + 1) * k.hn;  // one chain's states
-    const float2 *c0 = k.hc + (size_t)run * 2 * cs + slot, *c1 = c0 + cs;
-    const float2 *d0 = DIFF ? k.hd + (size_t)run * 2 * cs + slot : nullptr, *d1 = DIFF ? d0 + cs : nullptr;
     // per block (A, B) of the contour: 1 / E^2 (plain); 1 / E, rho, 1 / E' (DIFF)
     float r2[2][2], ri[2][2], dd[2][2], rs[2][2];
     {
@@ -693,33 +726,7 @@ __global__ void __launch_bounds__(kThreads) prop_contour(ContourK k)
     // compensated (Kahan) FP32 sums per block and real site; the trapezoid
     // weights 1 and 1/2 scale the terms exactly
     KSum sa0, sb0, sa1, sb1;
-    using CS = ContourStage<DIFF>;
-    constexpr int U = CS::U, NW = CS::NW;
-    const int tid = threadIdx.x;
-    // stage st, node u, stream w: stg[((st U + u) NW + w) kThreads + tid]
-    auto issue = [&](int st, int m0) {
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int m = m0 + u;
-            if (m <= ns) {
-                float2 *b = stg + (size_t)((st * U + u) * NW) * kThreads + tid;
-                cp_async8(b, c0 + (size_t)m * k.hn);
-                cp_async8(b + kThreads, c1 + (size_t)(ns - m) * k.hn);
-                if (DIFF) {
-                    cp_async8(b + 2 * kThreads, d0 + (size_t)m * k.hn);
-                    cp_async8(b + 3 * kThreads, d1 + (size_t)(ns - m) * k.hn);
-                }
-            }
-        }
-        cp_async_commit();
-    };
-    // a ring of NSTAGE chunks: chunk ch + NSTAGE goes into chunk ch's stage
-    // once ch is consumed; every issue commits a group (empty past N_s), so
-    // waiting until at most NSTAGE - 1 groups are pending completes chunk ch
-    constexpr int NST = CS::NSTAGE;
     const int nch = (ns + U) / U;  // chunks of U nodes over 0..ns
-#pragma unroll
-    for (int c = 0; c < NST; ++c) issue(c, c * U);
     for (int ch = 0; ch < nch; ++ch) {
         cp_async_wait<NST - 1>();
         const int st = ch % NST, m0 = ch * U;
