@@ -36,7 +36,7 @@ HBM_FALLBACK = 6800.0
 FP32_SMS, FP32_LANES, FP32_MHZ = 152, 128, 2070.0
 # dram__bytes_read.sum + dram__bytes_write.sum of the 8 prop_chain<9,8,16,256,1,1>
 # launches of one differential solve of the channel workload (ncu, one capture)
-CHAIN_DIFF_TRAFFIC_BYTES = 390.91e6 + 10.49e6
+CHAIN_DIFF_TRAFFIC_BYTES = 391.25e6 + 7.20e6
 
 
 def max_over_ranks(x: float, dist=None, device="cpu") -> float:
