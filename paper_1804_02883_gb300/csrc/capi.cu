@@ -1757,6 +1757,8 @@ extern "C" int epd_lb_set_surrogate(epd_lb *h, const float *params_host, double 
     }
     CK(cudaMemcpyAsync(h->sur_params, params_host, (size_t)sur::num_params() * sizeof(float), cudaMemcpyHostToDevice, h->stream),
        "copy surrogate parameters");
+    // the parameters stay fixed while attached: pack the weights once, outside the step graphs
+    for (auto &W : h->sur_work) CK(sur::prepare(W, h->sur_params, h->stream), "packing the surrogate weights");
     CK(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     h->sur_on = true;
     h->sur_every = exact_every;

@@ -555,12 +555,33 @@ __global__ void __launch_bounds__(288) conv3x3_dw(const __nv_bfloat16 *x, const 
 
 constexpr int kRedBlocks = 64;  // blocks per plane of the two-pass reductions
 
-// Two-pass, fixed-order sums over planes of n values: pass 1, grid
-// (kRedBlocks, planes), writes part[plane][block]; KIND 0: the FP64 values,
-// 1: exp(-v) in FP32 (solvent weight of Eq. (11)), 2: channel c = plane % 2
-// of the FP32 [sample][pixel][8] network output.
+// Fixed-order sums over planes of n values in one launch, grid (kRedBlocks,
+// planes): every block writes part[plane][block]; the last block to finish
+// (a self-resetting counter) adds each plane's partials in block order and
+// writes out[plane] = sum * scale.  KIND 0: the FP64 values, 1: exp(-v) in
+// FP32 (solvent weight of Eq. (11)), 2: channel c = plane % 2 of the FP32
+// [sample][pixel][8] network output.
+__device__ __forceinline__ void finish_planes(const double *part, int planes, double scale, double *out, unsigned *cnt)
+{
+    __shared__ bool last;
+    __threadfence();  // this block's partial before its arrival
+    if (threadIdx.x == 0) {
+        const unsigned total = gridDim.x * gridDim.y;
+        last = atomicInc(cnt, total - 1) == total - 1;  // wraps to 0 for the next use
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int p = threadIdx.x; p < planes; p += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < kRedBlocks; ++b) s += part[(size_t)p * kRedBlocks + b];
+        out[p] = s * scale;
+    }
+}
+
 template <int KIND>
-__global__ void __launch_bounds__(256) plane_partials(const void *f, long long n, double *part)
+__global__ void __launch_bounds__(256) plane_partials(const void *f, long long n, double *part, double scale, double *out,
+                                                      unsigned *cnt)
 {
     __shared__ double red[32];
     const int plane = blockIdx.y;
@@ -583,15 +604,7 @@ __global__ void __launch_bounds__(256) plane_partials(const void *f, long long n
     }
     s = block_sum(s, red);
     if (threadIdx.x == 0) part[(size_t)plane * kRedBlocks + blockIdx.x] = s;
-}
-
-__global__ void plane_finish(const double *part, int planes, double scale, double *out)
-{
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= planes) return;
-    double s = 0.0;
-    for (int b = 0; b < kRedBlocks; ++b) s += part[(size_t)p * kRedBlocks + b];
-    out[p] = s * scale;
+    finish_planes(part, gridDim.y, scale, out, cnt);
 }
 
 // x0[b][p][16] = s_in (omega_c - <omega_c>) for c < 3, 0 for the padding.
@@ -633,7 +646,8 @@ __global__ void prep_tangent(const double *omega, const double *omega0, const do
 
 // Block partials of sum e q over one plane per sample, e = exp(-omega0_S),
 // q = expm1(-(omega_S - omega0_S)) (FP32, accurate relative to the change).
-__global__ void __launch_bounds__(256) solvent_change_partials(const double *omega, const double *omega0, long long n, double *part)
+__global__ void __launch_bounds__(256) solvent_change_partials(const double *omega, const double *omega0, long long n, double *part,
+                                                               double scale, double *out, unsigned *cnt)
 {
     __shared__ double red[32];
     const int b = blockIdx.y;
@@ -645,6 +659,7 @@ __global__ void __launch_bounds__(256) solvent_change_partials(const double *ome
         acc += expf(-(float)w0[i]) * expm1f(-(float)(w[i] - w0[i]));
     const double s = block_sum((double)acc, red);
     if (threadIdx.x == 0) part[(size_t)b * kRedBlocks + blockIdx.x] = s;
+    finish_planes(part, gridDim.y, scale, out, cnt);
 }
 
 // Densities after a field change: Phi_A, Phi_B = the densities at omega0
@@ -870,7 +885,11 @@ size_t carve(Work &w, char *base, int nb, int ny, int nx, bool training)
         off += bytes;
         return p;
     };
-    w.err = (int *)take(256);
+    {
+        char *hdr = (char *)take(256);
+        w.err = (int *)hdr;
+        w.cnt = hdr ? (unsigned *)(hdr + 128) : nullptr;
+    }
     w.x0 = take(np * 16 * 2);
     for (int l = 0; l < 3; ++l) w.y[l] = take(np * 32 * 2);
     w.y4 = take(np * 8 * 4);
@@ -911,13 +930,13 @@ size_t carve(Work &w, char *base, int nb, int ny, int nx, bool training)
 static unsigned blocks(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 // Means over `planes` planes of n values (kind: see plane_partials).
-static void plane_means(const void *f, int kind, int planes, long long n, double *red, double *out, cudaStream_t s)
+static void plane_means(const Work &w, const void *f, int kind, int planes, double *out, cudaStream_t s)
 {
     const dim3 g(kRedBlocks, planes);
-    if (kind == 0) plane_partials<0><<<g, 256, 0, s>>>(f, n, red);
-    else if (kind == 1) plane_partials<1><<<g, 256, 0, s>>>(f, n, red);
-    else plane_partials<2><<<g, 256, 0, s>>>(f, n, red);
-    plane_finish<<<(planes + 63) / 64, 64, 0, s>>>(red, planes, 1.0 / (double)n, out);
+    const double sc = 1.0 / (double)w.n;
+    if (kind == 0) plane_partials<0><<<g, 256, 0, s>>>(f, w.n, w.red, sc, out, w.cnt);
+    else if (kind == 1) plane_partials<1><<<g, 256, 0, s>>>(f, w.n, w.red, sc, out, w.cnt);
+    else plane_partials<2><<<g, 256, 0, s>>>(f, w.n, w.red, sc, out, w.cnt);
 }
 
 static cudaError_t pack_all(Work &w, const float *params, bool backward, cudaStream_t s)
@@ -1013,16 +1032,36 @@ static cudaError_t forward_layers(Work &w, const float *params, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// zero the one-launch reductions' counter the first time a workspace is used
+static cudaError_t ready_counter(Work &w, cudaStream_t s)
+{
+    if (w.cnt_ready) return cudaSuccess;
+    const cudaError_t e = cudaMemsetAsync(w.cnt, 0, sizeof(unsigned), s);
+    w.cnt_ready = e == cudaSuccess;
+    return e;
+}
+
+cudaError_t prepare(Work &w, const float *params, cudaStream_t s)
+{
+    cudaError_t e;
+    w.cnt_ready = false;
+    if ((e = ready_counter(w, s))) return e;
+    if ((e = pack_all(w, params, false, s))) return e;
+    w.prepacked = true;
+    return cudaSuccess;
+}
+
 cudaError_t forward(Work &w, const float *params, const double *omega, double *phi, double s_in, double s_out, double pa_bar,
                     double pb_bar, double ps_bar, cudaStream_t s)
 {
     cudaError_t e;
-    if ((e = pack_all(w, params, false, s))) return e;
-    plane_means(omega, 0, w.nb * 3, w.n, w.red, w.means, s);
+    if ((e = ready_counter(w, s))) return e;
+    if (!w.prepacked && (e = pack_all(w, params, false, s))) return e;
+    plane_means(w, omega, 0, w.nb * 3, w.means, s);
     prep_input<<<blocks(w.n * w.nb), 256, 0, s>>>(omega, w.means, s_in, w.n, w.nb, reinterpret_cast<__nv_bfloat16 *>(w.x0));
     if ((e = forward_layers(w, params, s))) return e;
-    plane_means(w.y4, 2, w.nb * 2, w.n, w.red, w.ymean, s);
-    plane_means(omega, 1, w.nb, w.n, w.red, w.qs, s);
+    plane_means(w, w.y4, 2, w.nb * 2, w.ymean, s);
+    plane_means(w, omega, 1, w.nb, w.qs, s);
     densities_out<<<blocks(w.n * w.nb), 256, 0, s>>>((const float *)w.y4, w.ymean, omega, w.qs, s_out, pa_bar, pb_bar, ps_bar, w.n, w.nb,
                                                      phi);
     return cudaGetLastError();
@@ -1032,19 +1071,20 @@ cudaError_t tangent(Work &w, const float *params, const double *omega, const dou
                     double s_in, double s_out, double ps_bar, cudaStream_t s)
 {
     // the activations y_l of the forward pass at omega0 are in w (BF16)
-    plane_means(omega, 0, w.nb * 3, w.n, w.red, w.means2, s);
-    plane_means(omega0, 0, w.nb * 3, w.n, w.red, w.means, s);
+    cudaError_t e;
+    if ((e = ready_counter(w, s))) return e;
+    plane_means(w, omega, 0, w.nb * 3, w.means2, s);
+    plane_means(w, omega0, 0, w.nb * 3, w.means, s);
     prep_tangent<<<blocks(w.n * w.nb), 256, 0, s>>>(omega, omega0, w.means2, w.means, s_in, w.n, w.nb,
                                                     reinterpret_cast<__nv_bfloat16 *>(w.t0));
     conv<16, 32, EP_JVP, kD0>(w, w.t0, w.wf[0], nullptr, w.t[0], nullptr, nullptr, 32, s, w.y[0]);
     conv<32, 32, EP_JVP, kD1>(w, w.t[0], w.wf[1], nullptr, w.t[1], nullptr, nullptr, 32, s, w.y[1]);
     conv<32, 32, EP_JVP, kD2>(w, w.t[1], w.wf[2], nullptr, w.t[0], nullptr, nullptr, 32, s, w.y[2]);
     conv<32, 8, EP_LINEAR, kD3>(w, w.t[0], w.wf[3], nullptr, nullptr, (float *)w.t4, nullptr, 2, s);
-    plane_means(w.t4, 2, w.nb * 2, w.n, w.red, w.ymean, s);
+    plane_means(w, w.t4, 2, w.nb * 2, w.ymean, s);
     // <e> at omega0 into qs, <e q> into means2 (free again)
-    plane_means(omega0, 1, w.nb, w.n, w.red, w.qs, s);
-    solvent_change_partials<<<dim3(kRedBlocks, w.nb), 256, 0, s>>>(omega, omega0, w.n, w.red);
-    plane_finish<<<(w.nb + 63) / 64, 64, 0, s>>>(w.red, w.nb, 1.0 / (double)w.n, w.means2);
+    plane_means(w, omega0, 1, w.nb, w.qs, s);
+    solvent_change_partials<<<dim3(kRedBlocks, w.nb), 256, 0, s>>>(omega, omega0, w.n, w.red, 1.0 / (double)w.n, w.means2, w.cnt);
     densities_tangent<<<blocks(w.n * w.nb), 256, 0, s>>>((const float *)w.t4, w.ymean, phi0, omega, omega0, w.qs, w.means2, s_out,
                                                          w.n, w.nb, phi);
     (void)ps_bar;
@@ -1080,11 +1120,12 @@ cudaError_t gradients(Work &w, const float *params, const double *omega, const d
                       double *loss_dev, cudaStream_t s)
 {
     cudaError_t e;
+    if ((e = ready_counter(w, s))) return e;
     if ((e = pack_all(w, params, true, s))) return e;
-    plane_means(omega, 0, w.nb * 3, w.n, w.red, w.means, s);
+    plane_means(w, omega, 0, w.nb * 3, w.means, s);
     prep_input<<<blocks(w.n * w.nb), 256, 0, s>>>(omega, w.means, s_in, w.n, w.nb, reinterpret_cast<__nv_bfloat16 *>(w.x0));
     if ((e = forward_layers(w, params, s))) return e;
-    plane_means(phi_t, 0, w.nb * 3, w.n, w.red, w.tmean, s);
+    plane_means(w, phi_t, 0, w.nb * 3, w.tmean, s);
     const unsigned lb = blocks(w.n * w.nb);
     loss_grad<<<lb, 256, 0, s>>>((const float *)w.y4, phi_t, w.tmean, s_out, w.n, w.nb, reinterpret_cast<__nv_bfloat16 *>(w.dz4),
                                  w.lpart);

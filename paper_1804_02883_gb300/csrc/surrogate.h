@@ -28,6 +28,9 @@ struct Work {
     void *t0, *t[2], *t4;  // tangent pass: input, hidden tangents (BF16), output (FP32)
     double *means2;
     int *err;              // device error word: bit 2 = a bounded wait of a convolution gave up
+    unsigned *cnt;         // arrival counter of the one-launch reductions (0 between launches)
+    bool cnt_ready = false;  // cnt zeroed on this workspace
+    bool prepacked = false;  // forward weights packed for the parameters in use (prepare)
     void *wf[kLayers], *wb[kLayers];
     float *dwpart, *grad;
     double *means, *ymean, *qs, *tmean, *lpart, *red;
@@ -37,6 +40,10 @@ struct Work {
 
 size_t carve(Work &w, char *base, int nb, int ny, int nx, bool training);
 
+// For a fixed parameter set used by many forward / tangent calls (the time
+// stepper): zero the reduction counter and pack the forward weights once;
+// forward then skips the packing.
+cudaError_t prepare(Work &w, const float *params, cudaStream_t s);
 // Forward pass: omega [nb][3][n] FP64 -> phi [nb][3][n] FP64.
 cudaError_t forward(Work &w, const float *params, const double *omega, double *phi, double s_in, double s_out, double pa_bar,
                     double pb_bar, double ps_bar, cudaStream_t s);

@@ -29,17 +29,19 @@ WORKLOADS = {
 }
 
 
-def box3d(steps: int, timed: bool) -> None:
-    """Coupled steps on a 128 x 128 x 64 box (N_s = 16, FP64, phi_p = 0.2,
-    the reverse-Poiseuille force along x), state resident on the device; with
-    timed, CUDA-event milliseconds per step after one warm-up step."""
+def box3d(steps: int, timed: bool, mixed: bool = False) -> None:
+    """Coupled steps on a 128 x 128 x 64 box (N_s = 16, phi_p = 0.2, the
+    reverse-Poiseuille force along x; FP64, or with mixed the FP32 solves),
+    state resident on the device; with timed, CUDA-event milliseconds per
+    step after one warm-up step."""
     import ctypes
 
     import numpy as np
     import torch
 
     nx, ny, nz = 128, 128, 64
-    run = B.RunParams(nx=nx, ny=ny, ns=16, precision=B.PLAIN_FP64, f_a=0.5, phi_p=0.2, f0=2.0, seed=7)
+    run = B.RunParams(nx=nx, ny=ny, ns=16, precision=B.MIXED_FP32 if mixed else B.PLAIN_FP64, f_a=0.5, phi_p=0.2,
+                      f0=2.0, seed=7)
     rng = np.random.default_rng(7)
     w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
     om = torch.from_numpy(1e-3 * rng.uniform(-1, 1, (3, nz, ny, nx))).cuda()
@@ -72,7 +74,8 @@ def box3d(steps: int, timed: bool) -> None:
     b.synchronize()
     ms = a.elapsed_time(b) / steps
     units = nx * ny * nz * run.ns * 4
-    print(f"box3d {nz}x{ny}x{nx} N_s={run.ns} FP64: {ms:.3f} ms/step, {units / (ms * 1e-3):.3e} site.contour-steps/s,"
+    prec = "FP32 solves" if mixed else "FP64"
+    print(f"box3d {nz}x{ny}x{nx} N_s={run.ns} {prec}: {ms:.3f} ms/step, {units / (ms * 1e-3):.3e} site.contour-steps/s,"
           f" Q = {q[0].item():.12f}")
 
 
@@ -100,11 +103,12 @@ def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="channel", choices=sorted(WORKLOADS) + ["box3d", "surrogate"])
     ap.add_argument("--time", action="store_true", help="box3d: print CUDA-event ms per step")
+    ap.add_argument("--mixed", action="store_true", help="box3d: FP32 single-chain solves")
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--exact", type=int, default=0, help="then this many exact steps (0: none)")
     args = ap.parse_args()
     if args.workload == "box3d":
-        box3d(args.steps, args.time)
+        box3d(args.steps, args.time, args.mixed)
         print("ok")
         return
     if args.workload == "surrogate":
