@@ -1070,11 +1070,11 @@ cudaError_t forward(Work &w, const float *params, const double *omega, double *p
 cudaError_t tangent(Work &w, const float *params, const double *omega, const double *omega0, const double *phi0, double *phi,
                     double s_in, double s_out, double ps_bar, cudaStream_t s)
 {
-    // the activations y_l of the forward pass at omega0 are in w (BF16)
+    // the forward pass at omega0 left in w its activations y_l (BF16), the
+    // means of omega0 (w.means) and <exp(-omega0_S)> (w.qs)
     cudaError_t e;
     if ((e = ready_counter(w, s))) return e;
     plane_means(w, omega, 0, w.nb * 3, w.means2, s);
-    plane_means(w, omega0, 0, w.nb * 3, w.means, s);
     prep_tangent<<<blocks(w.n * w.nb), 256, 0, s>>>(omega, omega0, w.means2, w.means, s_in, w.n, w.nb,
                                                     reinterpret_cast<__nv_bfloat16 *>(w.t0));
     conv<16, 32, EP_JVP, kD0>(w, w.t0, w.wf[0], nullptr, w.t[0], nullptr, nullptr, 32, s, w.y[0]);
@@ -1082,8 +1082,7 @@ cudaError_t tangent(Work &w, const float *params, const double *omega, const dou
     conv<32, 32, EP_JVP, kD2>(w, w.t[1], w.wf[2], nullptr, w.t[0], nullptr, nullptr, 32, s, w.y[2]);
     conv<32, 8, EP_LINEAR, kD3>(w, w.t[0], w.wf[3], nullptr, nullptr, (float *)w.t4, nullptr, 2, s);
     plane_means(w, w.t4, 2, w.nb * 2, w.ymean, s);
-    // <e> at omega0 into qs, <e q> into means2 (free again)
-    plane_means(w, omega0, 1, w.nb, w.qs, s);
+    // <e q> into means2 (free again); <e> at omega0 is in qs
     solvent_change_partials<<<dim3(kRedBlocks, w.nb), 256, 0, s>>>(omega, omega0, w.n, w.red, 1.0 / (double)w.n, w.means2, w.cnt);
     densities_tangent<<<blocks(w.n * w.nb), 256, 0, s>>>((const float *)w.t4, w.ymean, phi0, omega, omega0, w.qs, w.means2, s_out,
                                                          w.n, w.nb, phi);

@@ -50,7 +50,8 @@ cudaError_t forward(Work &w, const float *params, const double *omega, double *p
 // Densities at omega from the surrogate at omega0 to first order in the
 // change: phi = phi0 + the tangent pass along omega - omega0 (Phi_A, Phi_B);
 // Phi_S from Eq. (11) at omega.  The forward pass at omega0 must have run on
-// w last (its activations are reused).
+// w last (its activations, the means of omega0 and <exp(-omega0_S)> are
+// reused).
 cudaError_t tangent(Work &w, const float *params, const double *omega, const double *omega0, const double *phi0, double *phi,
                     double s_in, double s_out, double ps_bar, cudaStream_t s);
 // Loss and parameter gradient for targets phi_t; loss to loss_dev[0].
