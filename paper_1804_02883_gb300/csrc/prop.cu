@@ -12,10 +12,13 @@
 //                 z_{j+1} = E(s_{j+1}) h  (g and g' each with its own node field),
 //                 store or consume the contour history,
 //                 z <- E(s_{j+1}) z_{j+1} (first half of the next step)
-// with E = exp(-N w ds / 2).  Only nodes 0..floor(N_s/2) are stored: while the
-// chains run through the second half, node m of g meets node N_s - m of g' from
-// the history (and vice versa), and the trapezoid sums of Eqs. (9)-(10) are
-// accumulated in FP64 on the fly.
+// with E = exp(-N w ds / 2).  The history holds nodes 0..floor(N_s/2): while
+// the chains run through the second half, node m of g meets node N_s - m of g'
+// from the history (and vice versa), and the trapezoid sums of Eqs. (9)-(10)
+// are accumulated in FP64 on the fly.  In MIXED_FP32 every node is stored:
+// the full history is the reference of the differential second solve
+// (prop_row<T, true> and the radix-8 passes below), whose contour sums are a
+// separate pass over the stored nodes (prop_contour_stream).
 #include <algorithm>
 #include <atomic>
 #include <cmath>
