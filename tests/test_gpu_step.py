@@ -369,6 +369,36 @@ def test_phased_chain_schedule_equals_single_runs():
     hb.close()
 
 
+def test_dependent_chain_launches_do_not_change_results():
+    # the phased schedule's launches after the first are programmatic
+    # dependents of the one before; EPD_LB_CHAIN_PDL=0 (read when the library
+    # loads) launches them plainly.  Both give the same bits.
+    import json
+    import os
+    import subprocess
+    import sys
+
+    code = (
+        "import json, numpy as np\n"
+        "import paper_1804_02883_gb300 as P\n"
+        "from paper_1804_02883_gb300 import workloads as W\n"
+        "h = P.EpdLb(W.channel_256x512(P.MIXED_FP32))\n"
+        "assert h.tiles(0)['chain_launches'] in (1, 8)\n"
+        "h.step(3)\n"
+        "phi, q = h.densities(1)\n"
+        "print(json.dumps({'launches': h.tiles(0)['chain_launches'], 'phi': float(np.abs(phi).sum()), "
+        "'first': phi.ravel()[:64].tolist(), 'q': q.tolist(), 'u': h.velocity(1).ravel()[:64].tolist()}))\n"
+        "h.close()\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = []
+    for pdl in ("1", "0"):
+        env = dict(os.environ, EPD_LB_CHAIN_PDL=pdl)
+        r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        out.append(json.loads(r.stdout.strip().splitlines()[-1]))
+    assert out[0] == out[1]
+
+
 def test_uneven_batch_groups_match_single_runs():
     runs = [P.RunParams(nx=32, ny=16, ns=8, precision=P.MIXED_FP32, seed=1),
             P.RunParams(nx=16, ny=32, ns=12, precision=P.MIXED_FP32, seed=2),
