@@ -454,11 +454,9 @@ int epd_prop_solve(const epd_lb_params *p, const double *omega_dev, double *phi_
  * this is a service for callers).
  *
  * Some callers cannot allocate device memory at the moment they need a
- * solve: code running while another part of the program captures a CUDA
- * graph (cudaMalloc and cudaFree are not allowed then), plug-ins whose host
- * framework owns every byte of the device through its own pool, and
- * real-time loops that must not pay for, or be serialised by, cudaMalloc /
- * cudaFree.  This entry point takes the same inputs and outputs as
+ * solve: plug-ins whose host framework owns every byte of the device through
+ * its own pool, and real-time loops that must not pay for, or be serialised
+ * by, cudaMalloc / cudaFree.  This entry point takes the same inputs and outputs as
  * epd_prop_solve (device pointers, caller-owned) but no workspace: its
  * scratch (propagator history, contour sums, transform tables, partial sums)
  * lives in one fixed array of EPD_PROP_SOLVE_NOALLOC_MAX_BYTES in the
@@ -473,8 +471,7 @@ int epd_prop_solve(const epd_lb_params *p, const double *omega_dev, double *phi_
  *    does not fit is rejected with EPD_LB_ETOOLARGE before any work.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress, which may load the library's device code) with
- *    that device current; make that first call before any stream capture
- *    starts.  Later calls reuse the address, which belongs to the device's
+ *    that device current.  Later calls reuse the address, which belongs to the device's
  *    current context: after cudaDeviceReset (or any other teardown of that
  *    context) the stored address is stale and later calls in the same
  *    process are not valid.

@@ -2,8 +2,8 @@
 workspace entry point (epd_prop_solve).
 
 epd_prop_solve_noalloc serves callers that cannot allocate device memory at
-the time of the call (during another component's graph capture, inside a host
-framework that owns the device's memory, in allocation-free real-time loops);
+the time of the call (inside a host framework that owns the device's memory,
+in allocation-free real-time loops);
 its scratch is a fixed array inside the library.  The test calls it twice in
 a row through the C ABI (the second call reuses the scratch left by the
 first) and compares both results with epd_prop_solve, within the tolerances
