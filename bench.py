@@ -706,7 +706,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=3)
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--surrogate-steps", type=int, default=40)
     ap.add_argument("--surrogate-pairs", type=int, default=50000,
@@ -826,6 +826,7 @@ def main():
 
     # end to end through the C ABI with host buffers: upload omega of every
     # run from pinned memory, one step, read Phi and Q of every run back
+    # (the asynchronous host-buffer calls, one synchronisation per step)
     host_om = [torch.empty(3 * r.nx * r.ny, dtype=torch.float64, pin_memory=True) for r in runs]
     host_phi = [torch.empty(3 * r.nx * r.ny, dtype=torch.float64, pin_memory=True) for r in runs]
     host_q = [torch.empty(2, dtype=torch.float64, pin_memory=True) for _ in runs]
@@ -839,10 +840,11 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
         for k in range(len(runs)):
-            h.set_state_ptr(k, host_om[k].data_ptr(), None, None)
+            h.set_omega_async(k, host_om[k].data_ptr())
         h.step(1)
         for k in range(len(runs)):
-            h.densities_ptr(k, host_phi[k].data_ptr(), host_q[k].data_ptr())
+            h.densities_async(k, host_phi[k].data_ptr(), host_q[k].data_ptr())
+        h.sync()
     barrier()
     e2e_t = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     e2e = {"value": job_rate(units_per_step(runs), args.e2e_steps, world, e2e_t), "unit": UNIT,

@@ -164,8 +164,22 @@ int epd_lb_step_fields_dev(epd_lb *h, int32_t run, double *omega_tilde_dev, doub
  * units, 2*ny*nx doubles.  Synchronous. */
 int epd_lb_velocity(epd_lb *h, int32_t run, double *v);
 
-/* Device-pointer variants of the two calls above: asynchronous copies on the
- * handle's stream into caller device memory of the same layout (FP64). */
+/* Asynchronous host-buffer variants for streaming a run's fields through
+ * the step: epd_lb_set_omega_async replaces omega of run `run` (3*ny*nx
+ * doubles, the fields conjugate to the densities, Sec. 2) and
+ * epd_lb_densities_async reads Phi (3*ny*nx; Eqs. (9)-(11)) and q[2] =
+ * (Q_P, Q_S); either output pointer may be NULL.  The copies are only
+ * enqueued on the handle's stream, in order with epd_lb_step: the caller
+ * keeps the host buffers alive and untouched until epd_lb_sync (or any
+ * synchronous call) returns.  Page-locked host memory makes the copies
+ * asynchronous; with pageable memory they complete before the call
+ * returns. */
+int epd_lb_set_omega_async(epd_lb *h, int32_t run, const double *omega);
+int epd_lb_densities_async(epd_lb *h, int32_t run, double *phi, double *q);
+
+/* Device-pointer variants of epd_lb_densities and epd_lb_velocity:
+ * asynchronous copies on the handle's stream into caller device memory of
+ * the same layout (FP64). */
 int epd_lb_densities_dev(epd_lb *h, int32_t run, double *phi_dev, double *q_dev);
 int epd_lb_velocity_dev(epd_lb *h, int32_t run, double *v_dev);
 

@@ -30,7 +30,8 @@ MIXED_FP32 = 1
 # Exported symbols declared in include/epd_lb.h.
 SYMBOLS = (
     "epd_lb_workspace_bytes", "epd_lb_init", "epd_lb_step", "epd_lb_sync", "epd_lb_densities",
-    "epd_lb_velocity", "epd_lb_densities_dev", "epd_lb_velocity_dev", "epd_lb_get_state",
+    "epd_lb_velocity", "epd_lb_set_omega_async", "epd_lb_densities_async", "epd_lb_densities_dev",
+    "epd_lb_velocity_dev", "epd_lb_get_state",
     "epd_lb_set_state", "epd_lb_solve", "epd_lb_observables", "epd_lb_save", "epd_lb_load",
     "epd_lb_last_error", "epd_lb_destroy", "epd_prop_solve_workspace_bytes", "epd_prop_solve",
     "epd_lb_enable_timing", "epd_lb_kernel_times", "epd_prop_solve_noalloc", "epd_lb_tiles",
@@ -119,6 +120,8 @@ def lib():
             "epd_lb_sync": (ctypes.c_int, [vp]),
             "epd_lb_densities": (ctypes.c_int, [vp, i32, vp, vp]),
             "epd_lb_velocity": (ctypes.c_int, [vp, i32, vp]),
+            "epd_lb_set_omega_async": (ctypes.c_int, [vp, i32, vp]),
+            "epd_lb_densities_async": (ctypes.c_int, [vp, i32, vp, vp]),
             "epd_lb_densities_dev": (ctypes.c_int, [vp, i32, vp, vp]),
             "epd_lb_velocity_dev": (ctypes.c_int, [vp, i32, vp]),
             "epd_lb_get_state": (ctypes.c_int, [vp, i32, vp, vp, vp]),
@@ -435,6 +438,16 @@ class EpdLb:
 
     def densities_ptr(self, run: int, phi_ptr: int, q_ptr: int):
         self._ck(lib().epd_lb_densities(self.h, run, phi_ptr, q_ptr), "epd_lb_densities")
+
+    def set_omega_async(self, run: int, omega_ptr: int):
+        """Enqueue omega of `run` from a host pointer (page-locked for overlap);
+        the buffer must stay untouched until sync()."""
+        self._ck(lib().epd_lb_set_omega_async(self.h, run, omega_ptr), "epd_lb_set_omega_async")
+
+    def densities_async(self, run: int, phi_ptr: int, q_ptr: int):
+        """Enqueue the read of Phi and Q of `run` into host pointers; valid
+        after sync()."""
+        self._ck(lib().epd_lb_densities_async(self.h, run, phi_ptr, q_ptr), "epd_lb_densities_async")
 
     def solve(self, run: int, omega):
         ny, nx = self.shape(run)

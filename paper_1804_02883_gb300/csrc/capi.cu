@@ -925,6 +925,29 @@ extern "C" int epd_lb_densities(epd_lb *h, int32_t run, double *phi, double *q)
     return EPD_LB_OK;
 }
 
+extern "C" int epd_lb_set_omega_async(epd_lb *h, int32_t run, const double *omega)
+{
+    Group *G;
+    int m;
+    if (int rc = locate(h, run, &G, &m)) return rc;
+    if (!omega) return fail(h, EPD_LB_EINVAL, "omega is NULL");
+    const size_t n = (size_t)G->g.n;
+    CK(cudaMemcpyAsync(G->omega + (size_t)m * 3 * n, omega, 3 * n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "copy omega");
+    G->phi_stale = true;  // the exact step recomputes Phi(t) before convecting it
+    return EPD_LB_OK;
+}
+
+extern "C" int epd_lb_densities_async(epd_lb *h, int32_t run, double *phi, double *q)
+{
+    Group *G;
+    int m;
+    if (int rc = locate(h, run, &G, &m)) return rc;
+    const size_t n = (size_t)G->g.n;
+    if (phi) CK(cudaMemcpyAsync(phi, G->phi + (size_t)m * 3 * n, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy phi");
+    if (q) CK(cudaMemcpyAsync(q, G->q + 2 * m, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy q");
+    return EPD_LB_OK;
+}
+
 extern "C" int epd_lb_velocity_dev(epd_lb *h, int32_t run, double *v_dev)
 {
     Group *G;

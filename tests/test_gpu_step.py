@@ -454,3 +454,27 @@ def test_decoupled_run_keeps_fluid_at_rest():
     h.step(5)
     assert np.all(h.velocity(0) == 0)
     h.close()
+
+
+def test_async_host_buffer_calls_match_synchronous_ones():
+    # epd_lb_set_omega_async / epd_lb_densities_async enqueue the same copies
+    # as epd_lb_set_state / epd_lb_densities without a synchronisation
+    import torch
+
+    r = W.with_(W.plain_small(), precision=P.MIXED_FP32, nx=64, ny=64)
+    a, b = P.EpdLb([r]), P.EpdLb([r])
+    om = W.random_omega(r.ny, r.nx, seed=71, amp=0.05)
+    host_om = torch.from_numpy(om.ravel().copy()).pin_memory()
+    host_phi = torch.empty(3 * r.nx * r.ny, dtype=torch.float64).pin_memory()
+    host_q = torch.empty(2, dtype=torch.float64).pin_memory()
+    a.set_state(0, om, None, None)
+    a.step(2)
+    phi_a, q_a = a.densities(0)
+    b.set_omega_async(0, host_om.data_ptr())
+    b.step(2)
+    b.densities_async(0, host_phi.data_ptr(), host_q.data_ptr())
+    b.sync()
+    assert np.array_equal(host_phi.numpy().reshape(3, r.ny, r.nx), phi_a)
+    assert np.array_equal(host_q.numpy(), q_a)
+    a.close()
+    b.close()
