@@ -96,9 +96,8 @@ struct ClusterGeom {
     static constexpr int TABX = tabs_total(LOGX, MRX), TABY = tabs_total(LOGY, MRY);
     // row buffer, column buffer, pass tables, Fourier factors, the node
     // factors of the epilogue sites in either packing (P points each; the
-    // differential solve reads the coefficients of a~ from L2: a shared
-    // memory copy beside the factors left less L1 for the prefetched
-    // reference states and was slower)
+    // differential solve reads the coefficients of a~ from L2, which
+    // measured faster than a shared-memory copy beside the factors)
     static constexpr size_t SMEM =
         (size_t)(R2 * PITCH + P + TABX + TABY + 2 * P) * sizeof(float2) + (NX + NY) * sizeof(float);
     static constexpr size_t SMEM_DIFF = SMEM;
